@@ -1,0 +1,111 @@
+"""Planted mistakes: each plausible slip in the C oracle must fail a pin.
+
+A mutated copy of the oracle source is compiled into a temporary library on
+the CPU, swapped in, and the relevant pin is shown to fail.  Nothing here
+touches a GPU.
+"""
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import core, dense
+from paper_1510_03110_gb300 import synth
+
+from test_oracle import _mhe_cost, random_uftoc, rel  # noqa: E402
+
+SRC = open(core._SRC).read()
+
+MUTATIONS = {
+    # Alg 1: F = Q_x + A^T P A loses its Q_x term
+    "drop_Qx_in_F": ("AT(F, i, j, n) += AT(Qt, i, j, nq);", "(void)0;"),
+    # Alg 1: F = Q_x + A P A (transposed operand)
+    "transpose_A_in_F": ("mm(n, n, n, At, n, 1, PA, n, 0, F, n);", "mm(n, n, n, At, n, 0, PA, n, 0, F, n);"),
+    # Alg 1: H = Q_xw + A P B (transposed operand)
+    "wrong_operand_in_H": ("mm(n, mt, n, At, n, 1, PB, n, 0, H, n);", "mm(n, mt, n, At, n, 0, PB, n, 0, H, n);"),
+    # Alg 2: sign of l_x in Psi
+    "sign_lx_in_Psi": ("Psit[i] -= tv[i] + lx[i];", "Psit[i] -= tv[i] - lx[i];"),
+    # Alg 2: the cbar recursion drops -1/2 k^T G k
+    "drop_kGk_in_cbar": ("- 0.5 * kGk", "- 0.0 * kGk"),
+    # Alg 3: lambda_t = P_t x_t + Psi_t
+    "sign_Psi_in_lambda": ("tv[i] - Psi[(size_t)t * n + i]", "tv[i] + Psi[(size_t)t * n + i]"),
+    # Section II: Q_xw = +(S C)^T
+    "sign_Qxw_assembly": ("AT(Q, i, n + j, nq) = -AT(SC, j, i, m);", "AT(Q, i, n + j, nq) = AT(SC, j, i, m);"),
+    # Section II: l_w = S y~ + W w~
+    "sign_lw_assembly": ("l[n + i] = t1[i] - t2[i];", "l[n + i] = t1[i] + t2[i];"),
+    # residual: the -lambda_t term of the x-stationarity row is dropped
+    "drop_lambda_in_residual": ("if (i < n) { s -= ltt[i]; rs += 1.0; }", "if (i < n) { rs += 1.0; }"),
+}
+
+
+@pytest.fixture(scope="module")
+def tmpdir_mod():
+    with tempfile.TemporaryDirectory() as d:
+        yield d
+
+
+def _mutant(tmpdir, name):
+    old, new = MUTATIONS[name]
+    assert SRC.count(old) == 1, name
+    path_c = os.path.join(tmpdir, f"{name}.c")
+    path_so = os.path.join(tmpdir, f"{name}.so")
+    with open(path_c, "w") as f:
+        f.write(SRC.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", path_so, path_c, "-lm"])
+    return core.load(path_so)
+
+
+def _pins_fail(lib_mut) -> list:
+    """Run the core pins against a mutated library; return those that fail."""
+    saved = core._lib
+    core._lib = lib_mut
+    failed = []
+    try:
+        p = random_uftoc(3, 3, 6, [2, 3])
+        r = oracle.riccati(p)
+        d = dense.solve(p)
+        if r["status"] != 0 or rel(r["x"], d["x"]) > 1e-10 or rel(r["lam"], d["lam"]) > 1e-10 \
+                or rel(r["w"], d["w"]) > 1e-10:
+            failed.append("lu")
+        dz = dense.solve(p)
+        z = np.concatenate([dz["x"].ravel(), dz["w"], dz["lam"].ravel()])
+        res = oracle.kkt_residual(p, dz["x"], dz["w"], dz["lam"])
+        if res["relres"] > 1e-12 or abs(res["r_inf"] - np.abs(dz["b"] - dz["K"] @ z).max()) > 1e-12:
+            failed.append("residual")
+        # perturbed point: the residual routine must agree with b - K z
+        zp = z + 1e-3
+        xp = zp[:len(dz["x"].ravel())].reshape(dz["x"].shape)
+        res2 = oracle.kkt_residual(p, xp, zp[xp.size:xp.size + dz["w"].size],
+                                   zp[xp.size + dz["w"].size:].reshape(dz["lam"].shape))
+        if abs(res2["r_inf"] - np.abs(dz["b"] - dz["K"] @ zp).max()) > 1e-10:
+            failed.append("residual_vs_dense")
+        v1 = 0.5 * p.x0 @ r["P0"] @ p.x0 - r["Psi0"] @ p.x0 + r["cbar0"]
+        if abs(v1 - oracle.objective(p, r["x"], r["w"])) > 1e-9 * (1 + abs(v1)):
+            failed.append("objective")
+        q = synth.mhe_instance(8, 3, 2, 2, 6)
+        u = oracle.mhe_to_uftoc(q)
+        rng = np.random.default_rng(0)
+        xm0 = rng.standard_normal(3)
+        wm = [rng.standard_normal(2) for _ in range(5)]
+        xm = [xm0]
+        for k in range(5):
+            xm.append(q["A"][k] @ xm[k] + q["B"][k] @ wm[k] + q["a"][k])
+        xu = np.vstack([q["x0"]] + xm)
+        wu = np.concatenate([xm0 - q["x0"]] + wm)
+        if abs(oracle.objective(u, xu, wu) - _mhe_cost(q, xm, wm)) > 1e-10 * abs(_mhe_cost(q, xm, wm)):
+            failed.append("mhe_cost")
+    finally:
+        core._lib = saved
+    return failed
+
+
+def test_unmutated_oracle_passes_all_pins():
+    assert _pins_fail(core.lib()) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmpdir_mod, name):
+    assert _pins_fail(_mutant(tmpdir_mod, name)) != []
