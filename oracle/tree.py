@@ -63,10 +63,12 @@ def reduce_chunk(prob: Uftoc, t0: int, t1: int) -> dict:
         Psi_new = A.T @ Psi - H @ k - lx - A.T @ P @ a
         cbar = cbar + 0.5 * a @ P @ a - Psi @ a - 0.5 * k @ G @ k + prob.c[t]
         P_new = F - K.T @ G @ K
+        P_new = 0.5 * (P_new + P_new.T)      # P_t is symmetric (Section III)
         L = _cho_solve(Lg, -B.T @ V)
         V_new = (A.T + K.T @ B.T) @ V
         v = v + V.T @ (a + B @ k)
         Qw_hat = Qw_hat + L.T @ G @ L
+        Qw_hat = 0.5 * (Qw_hat + Qw_hat.T)   # Q^_w is symmetric (Eq. Qh_Bh_alternative_def)
         P, Psi, V = P_new, Psi_new, V_new
         i = t - t0
         K_l[i], k_l[i], L_l[i], G_l[i] = K, k, L, G

@@ -185,7 +185,7 @@ void orc_mhe_stage(int n, int m, int q, const double *C, const double *R,
 /* ---------- serial Riccati solve: Algorithms 1, 2 and 3 ----------
  * Alg 1 (factorization), for t = N-1..0 with P_N = Q_{x,N}:
  *   F = Q_x + A^T P A,  G = Q_w + B^T P B,  H = Q_xw + A^T P B,
- *   factor G,  solve G K = -H^T,  P_t = F - K^T G K.
+ *   factor G,  solve G K = -H^T,  P_t = F - K^T G K  (its symmetric part).
  * Alg 2 (backward recursion), with Psi_N = -l_N, cbar_N = c_N:
  *   solve G k = B^T Psi - l_w - B^T P a,
  *   Psi_t = A^T Psi - H k - l_x - A^T P a,
@@ -275,7 +275,13 @@ int orc_riccati(int n, int N, const int *m,
         chol_solve(mt, Lg, n, Kt, mt);
         mm(mt, n, mt, G, mt, 0, Kt, mt, 0, GK, mt);        /* G K */
         mm(n, n, mt, Kt, mt, 1, GK, mt, 0, KGK, n);        /* K^T G K */
-        for (int i = 0; i < n * n; ++i) Pt[i] = F[i] - KGK[i];
+        /* P_t is symmetric by definition (Section III: F_t, P_t in S+^n); keep
+           the symmetric part of F - K^T G K so that rounding cannot feed an
+           antisymmetric part through the recursion */
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+                AT(Pt, i, j, n) = 0.5 * ((AT(F, i, j, n) - AT(KGK, i, j, n)) +
+                                         (AT(F, j, i, n) - AT(KGK, j, i, n)));
 
         /* Alg 2 */
         mv(n, n, P1, n, 0, at, Pa);                         /* P a */
