@@ -1,0 +1,155 @@
+/*
+ * mhe.h -- C-ABI of the GB300 parallel Riccati Newton-step library.
+ *
+ * The library computes the Newton step (the solution of the KKT system) of the
+ * unconstrained finite-time optimal control (UFTOC) problem behind moving
+ * horizon estimation, Eq. org_eqc_problem of Nielsen & Axehill, "An O(log N)
+ * Parallel Algorithm for Newton Step Computations with Applications to Moving
+ * Horizon Estimation" (arXiv 1510.03110):
+ *
+ *   min  sum_{t=0}^{N-1} 1/2 [x_t; w_t]^T Q_t [x_t; w_t] + l_t^T [x_t; w_t]
+ *   s.t. x_0 = x~0,  x_{t+1} = A_t x_t + B_t w_t + a_t,
+ *
+ * with the MHE arrival stage t = 0 built inside the library (Section II:
+ * A_0 = B_0 = I, Q_0 = diag(0, P~0^{-1}), l_0 = 0, a_0 = 0; w_0 has nx
+ * entries) and a zero terminal cost (Q_{x,N} = 0, l_N = 0).  The solve runs
+ * the paper's parallel Riccati tree (Algorithms 4, 5 and 6) on one GPU.
+ *
+ * Conventions for every entry point
+ *   - N is the UFTOC horizon (N = N^mhe + 2).  Instance b has N_b >= 1 and
+ *     S_b = N_b - 1 caller stages t = 1 .. N_b - 1.
+ *   - Stage arrays are instance-major, then stage-major: stage t of instance b
+ *     is block s = sum_{b' < b} S_b' + (t - 1).  Every matrix block is
+ *     column-major with its natural leading dimension.
+ *   - Pointers named "device" must be CUDA device (or managed) memory of the
+ *     current device.  The library never frees caller memory.
+ *   - Calls are asynchronous and ordered on the stream given to mhe_create;
+ *     argument and allocation errors are returned synchronously, errors found
+ *     on the device (a non-positive-definite pivot, non-convergence) are
+ *     reported per instance in mhe_info after the stream reaches them.
+ *   - Return values are mhe_status codes (MHE_OK = 0, errors < 0).  Nothing
+ *     aborts or traps.
+ */
+#ifndef MHE_H
+#define MHE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MHE_OK = 0,
+    MHE_PENDING = 1,          /* serving: result not ready yet */
+    MHE_E_ARG = -1,           /* invalid argument */
+    MHE_E_NOMEM = -2,         /* device allocation failed */
+    MHE_E_NOT_PD = -3,        /* a Cholesky pivot of some G_{t+1} fell below the threshold */
+    MHE_E_NONFINITE = -4,     /* the residual is not finite */
+    MHE_E_NOT_FACTORED = -5,  /* mhe_solve before mhe_factor */
+    MHE_E_NO_CONVERGE = -6,   /* refinement did not reach refine_tol */
+    MHE_E_TIMEOUT = -7,       /* a bounded device wait ran out */
+    MHE_E_CUDA = -8,          /* a CUDA runtime call failed */
+    MHE_E_ADMISSION = -9      /* serving: request cannot be admitted */
+} mhe_status;
+
+typedef enum {
+    MHE_FP64 = 0,     /* every product and factorisation in FP64 */
+    MHE_FP32_IR = 1   /* FP32 tree + iterative refinement against the FP64 KKT residual */
+} mhe_precision;
+
+/* Problem shape and solver options (mhe_create copies it). */
+typedef struct {
+    int nx;              /* state dimension n */
+    int nw;              /* process-noise (input) dimension of stages t >= 1 */
+    int batch;           /* number of independent instances */
+    const int* N;        /* host array [batch]: UFTOC horizon of each instance, >= 1 */
+    int prec;            /* mhe_precision */
+    int leaf_len;        /* level-0 chunk length (0: automatic); leaf_len * nw >= nx */
+    int branching;       /* chunk length at levels >= 1 (0: automatic); >= 2 */
+    int top_len;         /* a level with horizon <= top_len is solved as one chunk (0: automatic).
+                            top_len >= max N gives the plain serial Riccati recursion */
+    double refine_tol;   /* target relative KKT residual (0: 1e-12) */
+    int max_refine;      /* refinement iterations after the first solve (-1: 2 for FP64, 8 for FP32_IR) */
+} mhe_dims;
+
+/* Matrix data of the problem, FP64, device memory, read while the stream
+ * executes mhe_factor and every later mhe_solve: keep them alive and unchanged
+ * until the last mhe_solve that uses this factorisation has completed. */
+typedef struct {
+    const double* A;      /* [S][nx*nx]          A_t */
+    const double* B;      /* [S][nx*nw]          B_t (the MHE process-noise matrix G_t) */
+    const double* Q;      /* [S][(nx+nw)^2]      Q_t = [[Q_x, Q_xw], [Q_xw^T, Q_w]], symmetric */
+    const double* P0inv;  /* [batch][nx*nx]      arrival-cost weight P~0^{-1}, symmetric positive definite */
+} mhe_matrices;
+
+/* Right-hand side, FP64, device memory, read during mhe_solve only. */
+typedef struct {
+    const double* l;      /* [S][nx+nw]   l_t = (l_x, l_w) */
+    const double* a;      /* [S][nx]      a_t */
+    const double* x0;     /* [batch][nx]  x~0 */
+} mhe_rhs;
+
+/* Per-instance result report (device or host memory; written stream-ordered). */
+typedef struct {
+    int status;        /* mhe_status of this instance */
+    int level, chunk, stage;   /* where the first device error happened */
+    int refine_iters;  /* corrections applied */
+    int pad;
+    double relres;     /* ||r||_inf / (||K||_inf ||z||_inf + ||b||_inf) in FP64 */
+    double est_relerr; /* ||dz_last||_inf / ||z||_inf of the last correction (0 without refinement) */
+} mhe_info;
+
+typedef struct mhe_ctx mhe_ctx;
+
+/* Plan the tree (Algorithm 5 levels), allocate all device workspace and bind
+ * the context to `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Errors: MHE_E_ARG (shape not compiled in, bad dims), MHE_E_NOMEM. */
+int mhe_create(const mhe_dims* dims, void* stream, mhe_ctx** out);
+
+/* Bytes of device workspace mhe_create would allocate for dims (0 on error). */
+size_t mhe_workspace_bytes(const mhe_dims* dims);
+
+/* Matrix part of the tree: Algorithm 4 (matrix recursions) on every level,
+ * storing the factors each later solve reuses.  Stream-ordered. */
+int mhe_factor(mhe_ctx* ctx, const mhe_matrices* mats);
+
+/* Solve with the stored factors: the vector part of Algorithm 4 up the tree,
+ * the top problem, the down pass (Algorithm 6 as back-substitution), then
+ * refinement against the FP64 KKT residual.  Outputs (device, FP64):
+ *   x   [batch][N_b+1][nx]
+ *   w   per instance nx + (N_b-1)*nw entries (w_0 has nx entries)
+ *   lam [batch][N_b+1][nx]
+ *   info [batch] (device or host pointer; NULL to skip).
+ * Errors: MHE_E_NOT_FACTORED, MHE_E_ARG. */
+int mhe_solve(mhe_ctx* ctx, const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info);
+
+/* mhe_factor + mhe_solve fused: the vector part of Algorithm 4 runs inside the
+ * matrix pass, so the tree is walked up once. */
+int mhe_factor_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs,
+                     double* x, double* w, double* lam, mhe_info* info);
+
+/* Release the context and its workspace (synchronises its stream). */
+int mhe_destroy(mhe_ctx* ctx);
+
+/* Step a0 (Section II, the stage matrices for t = 1..N-1): from the MHE
+ * weights of S stages -- C (ny x nx), R = [[W, S], [S^T, V]] ((nw+ny)^2, the
+ * inverse joint noise covariance; S is its nw x ny block), y~ (ny), w~ (nw) --
+ * write Q_t = [[C^T V C, -C^T S^T], [-S C, W]], l_t = [C^T (S^T w~ - V y~);
+ * S y~ - W w~] and c_t = 1/2 w~^T W w~ - y~^T S^T w~ + 1/2 y~^T V y~.
+ * All pointers device, FP64, stage-major; c may be NULL. */
+int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const double* R,
+                 const double* yt, const double* wt, double* Q, double* l, double* c, void* stream);
+
+/* Shapes (nx, nw) compiled into this library: writes up to cap pairs into
+ * nx_out / nw_out and returns the number available. */
+int mhe_shapes(int* nx_out, int* nw_out, int cap);
+
+/* Text of the last error reported on this thread. */
+const char* mhe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHE_H */

@@ -1,0 +1,230 @@
+// api.cu -- the C-ABI of include/mhe.h on top of the engine and the compiled shapes.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mhe.h"
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace mhe {
+int shapes_small(ShapeEntry* out, int cap);
+int shapes_mid(ShapeEntry* out, int cap);
+int shapes_big(ShapeEntry* out, int cap);
+int shapes_sq(ShapeEntry* out, int cap);
+}  // namespace mhe
+
+struct mhe_ctx {
+    mhe::Engine eng;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+std::vector<mhe::ShapeEntry>& registry()
+{
+    static std::vector<mhe::ShapeEntry> reg;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        mhe::ShapeEntry buf[32];
+        int k = 0;
+        k += mhe::shapes_small(buf + k, 32 - k);
+        k += mhe::shapes_mid(buf + k, 32 - k);
+        k += mhe::shapes_big(buf + k, 32 - k);
+        k += mhe::shapes_sq(buf + k, 32 - k);
+        reg.assign(buf, buf + k);
+    });
+    return reg;
+}
+
+const mhe::ShapeEntry* find_shape(int nx, int nw)
+{
+    for (auto& e : registry())
+        if (e.ops.nx == nx && e.ops.nw == nw) return &e;
+    return nullptr;
+}
+
+// ---- CUDA runtime hooks of the engine --------------------------------------
+
+void* rt_alloc(size_t bytes)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void rt_release(void* p) { cudaFree(p); }
+int rt_memset0(void* p, size_t bytes, void* s)
+{
+    return cudaMemsetAsync(p, 0, bytes, (cudaStream_t)s) == cudaSuccess ? 0 : -1;
+}
+int rt_copy(void* dst, const void* src, size_t bytes, void* s)
+{
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, (cudaStream_t)s) == cudaSuccess ? 0 : -1;
+}
+int rt_sync(void* s) { return cudaStreamSynchronize((cudaStream_t)s) == cudaSuccess ? 0 : -1; }
+int rt_error() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
+
+// relres = ||r|| / (||K|| ||z|| + ||b||) per instance
+__global__ void k_finalize(int batch, const double* norms, int* active, int* iters, const int* status,
+                           const int* where, double tol, int mode, int refine, mhe_info* info)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double r = norms[4 * b + 0], K = norms[4 * b + 1], z = norms[4 * b + 2], bb = norms[4 * b + 3];
+    const double den = K * z + bb;
+    const double relres = den > 0 ? r / den : r;
+    if (mode < 2) {
+        const int was = (mode == 0) ? 1 : active[b];
+        const int act = was && status[b] == 0 && isfinite(relres) && !(relres <= tol);
+        active[b] = act;
+        if (act) iters[b] += 1;
+        return;
+    }
+    mhe_info o;
+    memset(&o, 0, sizeof(o));
+    int st = status[b];
+    if (st == 0 && !isfinite(relres)) st = MHE_E_NONFINITE;
+    else if (st == 0 && refine && !(relres <= tol)) st = MHE_E_NO_CONVERGE;
+    o.status = st;
+    o.level = where[3 * b + 0];
+    o.chunk = where[3 * b + 1];
+    o.stage = where[3 * b + 2];
+    o.refine_iters = iters[b];
+    o.relres = relres;
+    o.est_relerr = 0.0;
+    info[b] = o;
+}
+
+void rt_finalize(int batch, const double* norms, int* active, int* iters, const int* status, const int* where,
+                 double tol, int mode, int refine, mhe_info* info, void* s)
+{
+    k_finalize<<<(batch + 127) / 128, 128, 0, (cudaStream_t)s>>>(batch, norms, active, iters, status, where, tol,
+                                                                 mode, refine, info);
+}
+
+const mhe::Runtime kRuntime = {rt_alloc, rt_release, rt_memset0, rt_copy, rt_finalize, rt_sync, rt_error};
+
+int check_dims(const mhe_dims* d)
+{
+    if (!d) return fail(MHE_E_ARG, "dims is NULL");
+    if (d->nx < 1 || d->nw < 1 || d->batch < 1 || !d->N) return fail(MHE_E_ARG, "nx, nw, batch >= 1 and N required");
+    if (!find_shape(d->nx, d->nw))
+        return fail(MHE_E_ARG, "shape (nx=" + std::to_string(d->nx) + ", nw=" + std::to_string(d->nw) +
+                                   ") is not compiled into this library");
+    return MHE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhe_create(const mhe_dims* dims, void* stream, mhe_ctx** out)
+{
+    if (!out) return fail(MHE_E_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_dims(dims);
+    if (rc != MHE_OK) return rc;
+    mhe_ctx* c = new (std::nothrow) mhe_ctx;
+    if (!c) return fail(MHE_E_NOMEM, "host allocation failed");
+    rc = c->eng.init(*dims, &find_shape(dims->nx, dims->nw)->ops, &kRuntime, stream);
+    if (rc != MHE_OK) {
+        g_err = c->eng.err;
+        c->eng.release();
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return MHE_OK;
+}
+
+size_t mhe_workspace_bytes(const mhe_dims* dims)
+{
+    if (check_dims(dims) != MHE_OK) return 0;
+    mhe::Engine e;
+    e.prec = dims->prec;
+    const int min_leaf = (dims->nx + dims->nw - 1) / dims->nw;
+    const char* err = nullptr;
+    if (mhe::make_plan(dims->nx, dims->nw, dims->N, dims->batch,
+                       dims->leaf_len > 0 ? dims->leaf_len : (min_leaf > 8 ? min_leaf : 8),
+                       dims->branching > 0 ? dims->branching : 4, dims->top_len > 0 ? dims->top_len : 4, e.plan,
+                       &err) != 0)
+        return 0;
+    return e.layout(nullptr);
+}
+
+int mhe_factor(mhe_ctx* ctx, const mhe_matrices* mats)
+{
+    if (!ctx || !mats) return fail(MHE_E_ARG, "ctx or mats is NULL");
+    int rc = ctx->eng.factor(*mats, nullptr, nullptr, nullptr, nullptr);
+    if (rc != MHE_OK) g_err = ctx->eng.err;
+    return rc;
+}
+
+int mhe_solve(mhe_ctx* ctx, const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info)
+{
+    if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
+    int rc = ctx->eng.solve(rhs, x, w, lam, info, false);
+    if (rc != MHE_OK) g_err = ctx->eng.err;
+    return rc;
+}
+
+int mhe_factor_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs, double* x, double* w,
+                     double* lam, mhe_info* info)
+{
+    if (!ctx || !mats || !rhs) return fail(MHE_E_ARG, "ctx, mats or rhs is NULL");
+    if (!rhs->x0 || (ctx->eng.plan.S_in > 0 && (!rhs->l || !rhs->a))) return fail(MHE_E_ARG, "incomplete right-hand side");
+    int rc = ctx->eng.factor(*mats, rhs, x, w, lam);
+    if (rc == MHE_OK) rc = ctx->eng.solve(rhs, x, w, lam, info, true);
+    if (rc != MHE_OK) g_err = ctx->eng.err;
+    return rc;
+}
+
+int mhe_destroy(mhe_ctx* ctx)
+{
+    if (!ctx) return MHE_OK;
+    cudaStreamSynchronize((cudaStream_t)ctx->eng.stream);
+    ctx->eng.release();
+    delete ctx;
+    return MHE_OK;
+}
+
+int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const double* R, const double* yt,
+                 const double* wt, double* Q, double* l, double* c, void* stream)
+{
+    const mhe::ShapeEntry* e = find_shape(nx, nw);
+    if (!e || e->ny != ny) return fail(MHE_E_ARG, "shape (nx, nw, ny) is not compiled into this library");
+    if (S < 0) return fail(MHE_E_ARG, "S < 0");
+    if (S > 0 && (!C || !R || !yt || !wt || !Q || !l)) return fail(MHE_E_ARG, "NULL input or output");
+    e->assemble(S, C, R, yt, wt, Q, l, c, stream);
+    if (cudaGetLastError() != cudaSuccess) return fail(MHE_E_CUDA, "launch of the assembly kernel failed");
+    return MHE_OK;
+}
+
+int mhe_shapes(int* nx_out, int* nw_out, int cap)
+{
+    auto& r = registry();
+    for (int i = 0; i < (int)r.size() && i < cap; ++i) {
+        if (nx_out) nx_out[i] = r[i].ops.nx;
+        if (nw_out) nw_out[i] = r[i].ops.nw;
+    }
+    return (int)r.size();
+}
+
+const char* mhe_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

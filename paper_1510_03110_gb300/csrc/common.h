@@ -1,0 +1,88 @@
+// common.h -- data structures shared by the host runtime and the kernels.
+#pragma once
+#include <stdint.h>
+
+namespace mhe {
+
+// Flags of one chunk (one subproblem P_i^k of the tree, Section V).
+enum : int {
+    CH_LAST = 1,      // last subproblem of its level: terminal cost known (Section IV-B)
+    CH_TOP = 2,       // the top problem of its instance: x^_0 = x~0 (Algorithm 6 start)
+    CH_ARRIVAL = 4,   // level 0 chunk that contains the arrival stage t = 0
+};
+
+// One subproblem: stages t0 .. t0+len-1 of the level-k problem of instance `inst`.
+struct ChunkDesc {
+    int inst;
+    int t0;
+    int len;
+    int flags;
+    long long g0;       // global stage index of t0 within this level's stage arrays
+    long long parent;   // non-last: global stage index of the master stage it becomes at level k+1
+    long long px;       // parent's state index holding x^_i (non-top); -1 for the top
+};
+
+// Per (level, instance) bookkeeping.
+struct LevelInst {
+    long long gs;   // first global stage index of this instance at this level
+    long long gx;   // first global state index (N+1 states per instance)
+    int N;          // horizon of this instance's problem at this level (0: instance absent)
+    int top;        // 1 when this level is the instance's top level
+};
+
+// Everything a tree kernel of one level reads and writes.  Matrices are
+// column-major.  Level-0 problem data are the caller's FP64 arrays; higher
+// levels read the FP64 master-problem arrays written by the level below.
+template <typename T>
+struct LevelArgs {
+    int level;
+    int nchunks;
+    const ChunkDesc* chunks;
+    const LevelInst* li;           // this level, indexed by instance
+
+    // level-0 problem (stages t >= 1 of instance b at caller stage in_off[b] + t - 1)
+    const double *A, *B, *Q, *P0inv;
+    const long long* in_off;
+    const long long* w_off;        // caller w offset of instance b (w_0 has n entries)
+    // right-hand side of level 0 (l0, a0, lN per instance; nullptr means zero)
+    const double *l, *a, *x0, *l0, *a0, *lN;
+
+    // master-problem stage data of this level (k >= 1), FP64
+    const double *Ah, *Bh, *ah, *Qxh, *lxh;
+    const double *QNk, *lNk;       // terminal cost of this level's problem, per instance
+    // outputs for level k+1
+    double *Ah_up, *Bh_up, *ah_up, *Qxh_up, *lxh_up, *QN_up, *lN_up;
+
+    // stored factors of this level (per stage, natural leading dimensions)
+    T *Pst, *Lgst, *Kst, *kst, *Lst;
+    // the arrival stage of each instance (level 0 only, width n)
+    T *Pst0, *Lgst0, *Kst0, *kst0, *Lst0;
+
+    // down pass
+    const double *xd_up, *wd_up, *ld_up;   // solution of the level above
+    double *xd, *wd, *ld;                  // this level's solution
+    double *zx, *zw, *zl;                  // level 0: accumulate targets (nullptr: none)
+
+    const int* active;     // per instance; nullptr = all active
+    int* status;           // per instance error code
+    int* where;            // per instance (level, chunk, stage) of the first error
+    double piv_rel;        // relative pivot threshold of the Cholesky factorisations
+    int store_P;           // keep P_{t+1} per stage (needed by right-hand-side-only passes)
+};
+
+// Residual / norm kernel arguments (level 0, FP64).
+struct ResidArgs {
+    int batch;
+    long long nstages;            // sum of N_b (arrival stages included)
+    const long long* gs0;         // level-0 first global stage index per instance (size batch+1)
+    const long long* in_off;
+    const long long* w_off;
+    const double *A, *B, *Q, *P0inv;
+    const double *l, *a, *x0, *l0, *a0, *lN;
+    const double *x, *w, *lam;    // current iterate (caller layout)
+    double *rl, *ra, *rl0, *ra0, *rlN, *rx0;   // correction right-hand side (UFTOC form)
+    double* norms;                // per instance [r_inf, K_inf, z_inf, b_inf]
+    const int* active;
+};
+
+}  // namespace mhe

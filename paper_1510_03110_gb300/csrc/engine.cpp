@@ -1,0 +1,313 @@
+// engine.cpp -- workspace layout and the order of the level passes.
+#include "engine.h"
+
+#include <string.h>
+
+namespace mhe {
+
+namespace {
+constexpr size_t kAlign = 256;
+size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename P>
+    void take(P*& p, size_t count)
+    {
+        const size_t bytes = up(count * sizeof(P) + 1);
+        p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+        off += bytes;
+    }
+    void take_raw(void*& p, size_t bytes)
+    {
+        p = base ? base + off : nullptr;
+        off += up(bytes + 1);
+    }
+};
+}  // namespace
+
+size_t Engine::layout(char* base)
+{
+    Carver c{base};
+    const int n = plan.n, m = plan.m, batch = plan.batch;
+    const size_t ts = (prec == MHE_FP64) ? sizeof(double) : sizeof(float);
+    const size_t n2 = (size_t)n * n;
+    lv.resize(plan.levels.size());
+    for (size_t k = 0; k < plan.levels.size(); ++k) {
+        const PlanLevel& L = plan.levels[k];
+        LevelBuf& B_ = lv[k];
+        B_.nchunks = (int)L.chunks.size();
+        c.take(B_.chunks, L.chunks.size());
+        c.take(B_.li, (size_t)batch);
+        const size_t ns = (size_t)L.nstages, nx_ = (size_t)L.nstates;
+        const size_t mk = (k == 0) ? (size_t)m : (size_t)n;
+        c.take_raw(B_.Pst, ns * n2 * ts);
+        c.take_raw(B_.Lgst, ns * mk * mk * ts);
+        c.take_raw(B_.Kst, ns * mk * n * ts);
+        c.take_raw(B_.kst, ns * mk * ts);
+        c.take_raw(B_.Lst, ns * mk * n * ts);
+        if (k >= 1) {
+            c.take(B_.Ah, ns * n2);
+            c.take(B_.Bh, ns * n2);
+            c.take(B_.Qxh, ns * n2);
+            c.take(B_.ah, ns * n);
+            c.take(B_.lxh, ns * n);
+            c.take(B_.QN, (size_t)batch * n2);
+            c.take(B_.lN, (size_t)batch * n);
+            c.take(B_.xd, nx_ * n);
+            c.take(B_.wd, ns * n);
+            c.take(B_.ld, nx_ * n);
+        }
+    }
+    c.take_raw(Pst0, (size_t)batch * n2 * ts);
+    c.take_raw(Lgst0, (size_t)batch * n2 * ts);
+    c.take_raw(Kst0, (size_t)batch * n2 * ts);
+    c.take_raw(kst0, (size_t)batch * n * ts);
+    c.take_raw(Lst0, (size_t)batch * n2 * ts);
+    c.take(in_off, (size_t)batch);
+    c.take(w_off, (size_t)batch);
+    c.take(gs0, (size_t)batch + 1);
+    c.take(dx, (size_t)plan.X_total * n);
+    c.take(dw, (size_t)plan.W_total);
+    c.take(dl, (size_t)plan.X_total * n);
+    c.take(rl, (size_t)plan.S_in * (n + m));
+    c.take(ra, (size_t)plan.S_in * n);
+    c.take(rl0, (size_t)batch * 2 * n);
+    c.take(ra0, (size_t)batch * n);
+    c.take(rlN, (size_t)batch * n);
+    c.take(rx0, (size_t)batch * n);
+    c.take(norms, (size_t)batch * 4);
+    c.take(active, (size_t)batch);
+    c.take(status, (size_t)batch);
+    c.take(where, (size_t)batch * 3);
+    c.take(iters, (size_t)batch);
+    c.take(info_dev, (size_t)batch);
+    return c.off;
+}
+
+int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s)
+{
+    ops = o;
+    rt = r;
+    stream = s;
+    prec = d.prec;
+    if (prec != MHE_FP64 && prec != MHE_FP32_IR) { err = "unknown precision"; return MHE_E_ARG; }
+    tol = d.refine_tol > 0 ? d.refine_tol : 1e-12;
+    max_refine = d.max_refine >= 0 ? d.max_refine : (prec == MHE_FP64 ? 2 : 8);
+    int maxN = 1;
+    for (int b = 0; b < d.batch; ++b) maxN = d.N[b] > maxN ? d.N[b] : maxN;
+    const int min_leaf = (d.nx + d.nw - 1) / d.nw;
+    int leaf = d.leaf_len > 0 ? d.leaf_len : (min_leaf > 8 ? min_leaf : 8);
+    int br = d.branching > 0 ? d.branching : 4;
+    int top = d.top_len > 0 ? d.top_len : 4;
+    const char* e = nullptr;
+    int rc = make_plan(d.nx, d.nw, d.N, d.batch, leaf, br, top, plan, &e);
+    if (rc != 0) { err = e; return MHE_E_ARG; }
+    arena_bytes = layout(nullptr);
+    arena = rt->alloc(arena_bytes);
+    if (!arena) { err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
+    layout(static_cast<char*>(arena));
+    // upload the plan tables
+    for (size_t k = 0; k < plan.levels.size(); ++k) {
+        const PlanLevel& L = plan.levels[k];
+        if (!L.chunks.empty())
+            rt->copy(lv[k].chunks, L.chunks.data(), L.chunks.size() * sizeof(ChunkDesc), stream);
+        rt->copy(lv[k].li, L.li.data(), L.li.size() * sizeof(LevelInst), stream);
+    }
+    rt->copy(in_off, plan.in_off.data(), plan.in_off.size() * sizeof(long long), stream);
+    rt->copy(w_off, plan.w_off.data(), plan.w_off.size() * sizeof(long long), stream);
+    rt->copy(gs0, plan.gs0.data(), plan.gs0.size() * sizeof(long long), stream);
+    if (rt->sync(stream) != 0) { err = "CUDA error while uploading the plan"; return MHE_E_CUDA; }
+    return MHE_OK;
+}
+
+void Engine::release()
+{
+    if (arena) rt->release(arena);
+    arena = nullptr;
+}
+
+template <typename T>
+LevelArgs<T> Engine::args(int k) const
+{
+    LevelArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    const LevelBuf& L = lv[k];
+    a.level = k;
+    a.nchunks = L.nchunks;
+    a.chunks = L.chunks;
+    a.li = L.li;
+    a.A = A; a.B = B; a.Q = Q; a.P0inv = P0inv;
+    a.in_off = in_off;
+    a.w_off = w_off;
+    if (k >= 1) {
+        a.Ah = L.Ah; a.Bh = L.Bh; a.ah = L.ah; a.Qxh = L.Qxh; a.lxh = L.lxh;
+        a.QNk = L.QN; a.lNk = L.lN;
+    }
+    if (k + 1 < (int)lv.size()) {
+        const LevelBuf& U = lv[k + 1];
+        a.Ah_up = U.Ah; a.Bh_up = U.Bh; a.ah_up = U.ah; a.Qxh_up = U.Qxh; a.lxh_up = U.lxh;
+        a.QN_up = U.QN; a.lN_up = U.lN;
+        a.xd_up = U.xd; a.wd_up = U.wd; a.ld_up = U.ld;
+    }
+    a.Pst = static_cast<T*>(L.Pst);
+    a.Lgst = static_cast<T*>(L.Lgst);
+    a.Kst = static_cast<T*>(L.Kst);
+    a.kst = static_cast<T*>(L.kst);
+    a.Lst = static_cast<T*>(L.Lst);
+    if (k == 0) {
+        a.Pst0 = static_cast<T*>(Pst0);
+        a.Lgst0 = static_cast<T*>(Lgst0);
+        a.Kst0 = static_cast<T*>(Kst0);
+        a.kst0 = static_cast<T*>(kst0);
+        a.Lst0 = static_cast<T*>(Lst0);
+    }
+    a.xd = L.xd; a.wd = L.wd; a.ld = L.ld;
+    a.status = status;
+    a.where = where;
+    a.piv_rel = (sizeof(T) == 8) ? 1e-14 : 1e-7;
+    a.store_P = 1;
+    return a;
+}
+
+template <typename T>
+static void launch(void (*f64)(const LevelArgs<double>&, int, void*),
+                   void (*f32)(const LevelArgs<float>&, int, void*), const LevelArgs<T>& a, int upper,
+                   void* s);
+template <>
+void launch<double>(void (*f64)(const LevelArgs<double>&, int, void*),
+                    void (*)(const LevelArgs<float>&, int, void*), const LevelArgs<double>& a, int upper,
+                    void* s)
+{
+    f64(a, upper, s);
+}
+template <>
+void launch<float>(void (*)(const LevelArgs<double>&, int, void*),
+                   void (*f32)(const LevelArgs<float>&, int, void*), const LevelArgs<float>& a, int upper,
+                   void* s)
+{
+    f32(a, upper, s);
+}
+
+// Algorithm 5: reduce level 0, 1, ... (tops included at their level).  With
+// l/a given the vector part of Algorithm 4 runs in the same pass.
+template <typename T>
+void Engine::pass_reduce(const double* l, const double* a)
+{
+    for (int k = 0; k < (int)lv.size(); ++k) {
+        LevelArgs<T> g = args<T>(k);
+        g.l = l;
+        g.a = a;
+        if (k >= 1 && !l) { g.lxh = nullptr; g.ah = nullptr; g.lNk = nullptr; }
+        launch<T>(ops->reduce64, ops->reduce32, g, k >= 1, stream);
+    }
+}
+
+// The vector part of Algorithm 4 alone, level by level, with stored factors.
+template <typename T>
+void Engine::pass_rhs(const double* l, const double* a, const double* l0, const double* a0, const double* lN)
+{
+    for (int k = 0; k < (int)lv.size(); ++k) {
+        LevelArgs<T> g = args<T>(k);
+        g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
+        g.active = active_mask;
+        launch<T>(ops->rhs64, ops->rhs32, g, k >= 1, stream);
+    }
+}
+
+// Algorithm 6 as back-substitution, top level first.
+template <typename T>
+void Engine::pass_down(const double* l, const double* a, const double* l0, const double* a0, const double* x0,
+                       const double* lN, double* x, double* w, double* lam, double* zx, double* zw, double* zl,
+                       const int* act)
+{
+    for (int k = (int)lv.size() - 1; k >= 0; --k) {
+        LevelArgs<T> g = args<T>(k);
+        g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;
+        g.x0 = x0;
+        g.lN = lN;
+        g.active = act;
+        if (k == 0) {
+            g.xd = x; g.wd = w; g.ld = lam;
+            g.zx = zx; g.zw = zw; g.zl = zl;
+        }
+        launch<T>(ops->down64, ops->down32, g, k >= 1, stream);
+    }
+}
+
+void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, const double* lam, const int* act)
+{
+    ResidArgs r;
+    memset(&r, 0, sizeof(r));
+    r.batch = plan.batch;
+    r.nstages = plan.gs0[plan.batch];
+    r.gs0 = gs0;
+    r.in_off = in_off;
+    r.w_off = w_off;
+    r.A = A; r.B = B; r.Q = Q; r.P0inv = P0inv;
+    r.l = rhs->l; r.a = rhs->a; r.x0 = rhs->x0;
+    r.l0 = nullptr; r.a0 = nullptr; r.lN = nullptr;
+    r.x = x; r.w = w; r.lam = lam;
+    r.rl = rl; r.ra = ra; r.rl0 = rl0; r.ra0 = ra0; r.rlN = rlN; r.rx0 = rx0;
+    r.norms = norms;
+    r.active = act;
+    rt->memset0(norms, sizeof(double) * 4 * plan.batch, stream);
+    ops->resid(r, stream);
+}
+
+template <typename T>
+int Engine::run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool fused)
+{
+    active_mask = nullptr;
+    if (!fused) pass_rhs<T>(rhs->l, rhs->a, nullptr, nullptr, nullptr);
+    pass_down<T>(rhs->l, rhs->a, nullptr, nullptr, rhs->x0, nullptr, x, w, lam, nullptr, nullptr, nullptr,
+                 nullptr);
+    rt->memset0(iters, sizeof(int) * plan.batch, stream);
+    for (int it = 0; it < max_refine; ++it) {
+        residual(rhs, x, w, lam, it == 0 ? nullptr : active);
+        rt->finalize(plan.batch, norms, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
+                     stream);
+        // correction problem K dz = r in UFTOC form, then z += dz
+        active_mask = active;
+        pass_rhs<T>(rl, ra, rl0, ra0, rlN);
+        pass_down<T>(rl, ra, rl0, ra0, rx0, rlN, dx, dw, dl, x, w, lam, active);
+        active_mask = nullptr;
+    }
+    residual(rhs, x, w, lam, nullptr);
+    rt->finalize(plan.batch, norms, active, iters, status, where, tol, 2, max_refine > 0 ? 1 : 0, info_dev,
+                 stream);
+    if (info) rt->copy(info, info_dev, sizeof(mhe_info) * plan.batch, stream);
+    if (rt->error() != 0) { err = "CUDA error during the solve"; return MHE_E_CUDA; }
+    return MHE_OK;
+}
+
+int Engine::factor(const mhe_matrices& mt, const mhe_rhs* rhs, double* x, double* w, double* lam)
+{
+    if (!mt.A && plan.S_in > 0) { err = "A is NULL"; return MHE_E_ARG; }
+    if (!mt.B && plan.S_in > 0) { err = "B is NULL"; return MHE_E_ARG; }
+    if (!mt.Q && plan.S_in > 0) { err = "Q is NULL"; return MHE_E_ARG; }
+    if (!mt.P0inv) { err = "P0inv is NULL"; return MHE_E_ARG; }
+    A = mt.A; B = mt.B; Q = mt.Q; P0inv = mt.P0inv;
+    rt->memset0(status, sizeof(int) * plan.batch, stream);
+    rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
+    const double* l = rhs ? rhs->l : nullptr;
+    const double* a = rhs ? rhs->a : nullptr;
+    (void)x; (void)w; (void)lam;
+    if (prec == MHE_FP64) pass_reduce<double>(l, a);
+    else pass_reduce<float>(l, a);
+    factored = true;
+    if (rt->error() != 0) { err = "CUDA error during the factorisation"; return MHE_E_CUDA; }
+    return MHE_OK;
+}
+
+int Engine::solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool fused)
+{
+    if (!factored) { err = "mhe_solve before mhe_factor"; return MHE_E_NOT_FACTORED; }
+    if (!rhs || !rhs->x0 || (plan.S_in > 0 && (!rhs->l || !rhs->a))) { err = "incomplete right-hand side"; return MHE_E_ARG; }
+    if (!x || !w || !lam) { err = "output pointer is NULL"; return MHE_E_ARG; }
+    if (prec == MHE_FP64) return run_solve<double>(rhs, x, w, lam, info, fused);
+    return run_solve<float>(rhs, x, w, lam, info, fused);
+}
+
+}  // namespace mhe

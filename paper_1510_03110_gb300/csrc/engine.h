@@ -1,0 +1,103 @@
+// engine.h -- one solver context: the planned tree, its workspace, and the
+// order of the level passes (Algorithm 5 up, top, Algorithm 6 down, then
+// refinement against the FP64 KKT residual).
+#pragma once
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mhe.h"
+#include "common.h"
+#include "plan.h"
+
+namespace mhe {
+
+// Kernel launchers of one compiled shape (nx, nw).  upper = 1 selects the
+// master-problem variant of a level pass.
+struct ShapeOps {
+    int nx, nw;
+    void (*reduce64)(const LevelArgs<double>&, int upper, void* stream);
+    void (*rhs64)(const LevelArgs<double>&, int upper, void* stream);
+    void (*down64)(const LevelArgs<double>&, int upper, void* stream);
+    void (*reduce32)(const LevelArgs<float>&, int upper, void* stream);
+    void (*rhs32)(const LevelArgs<float>&, int upper, void* stream);
+    void (*down32)(const LevelArgs<float>&, int upper, void* stream);
+    void (*resid)(const ResidArgs&, void* stream);
+};
+
+// Memory and small shape-independent steps.
+struct Runtime {
+    void* (*alloc)(size_t bytes);
+    void (*release)(void* p);
+    int (*memset0)(void* p, size_t bytes, void* stream);
+    int (*copy)(void* dst, const void* src, size_t bytes, void* stream);   // any direction
+    // per instance: relres from norms; mode 0/1 (first/later refinement pass)
+    // sets which instances take another correction, mode 2 fills mhe_info
+    void (*finalize)(int batch, const double* norms, int* active, int* iters, const int* status,
+                     const int* where, double tol, int mode, int refine, mhe_info* info,
+                     void* stream);
+    int (*sync)(void* stream);
+    int (*error)();   // sticky error of the launches so far (0 = none)
+};
+
+struct LevelBuf {
+    ChunkDesc* chunks = nullptr;
+    LevelInst* li = nullptr;
+    int nchunks = 0;
+    void *Pst = nullptr, *Lgst = nullptr, *Kst = nullptr, *kst = nullptr, *Lst = nullptr;
+    double *Ah = nullptr, *Bh = nullptr, *ah = nullptr, *Qxh = nullptr, *lxh = nullptr;
+    double *QN = nullptr, *lN = nullptr;   // terminal of this level (k >= 1)
+    double *xd = nullptr, *wd = nullptr, *ld = nullptr;
+};
+
+class Engine {
+public:
+    Plan plan;
+    const ShapeOps* ops = nullptr;
+    const Runtime* rt = nullptr;
+    void* stream = nullptr;
+    int prec = MHE_FP64;
+    double tol = 1e-10;
+    int max_refine = 0;
+
+    std::vector<LevelBuf> lv;
+    void *Pst0 = nullptr, *Lgst0 = nullptr, *Kst0 = nullptr, *kst0 = nullptr, *Lst0 = nullptr;
+    long long *in_off = nullptr, *w_off = nullptr, *gs0 = nullptr;
+    double *dx = nullptr, *dw = nullptr, *dl = nullptr;
+    double *rl = nullptr, *ra = nullptr, *rl0 = nullptr, *ra0 = nullptr, *rlN = nullptr, *rx0 = nullptr;
+    double* norms = nullptr;
+    int *active = nullptr, *status = nullptr, *where = nullptr, *iters = nullptr;
+    mhe_info* info_dev = nullptr;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+
+    const double *A = nullptr, *B = nullptr, *Q = nullptr, *P0inv = nullptr;
+    const int* active_mask = nullptr;   // instances still refining (nullptr: all)
+    bool factored = false;
+    std::string err;
+
+    // sizes only (arena == nullptr) or carve (arena given)
+    size_t layout(char* base);
+    int init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s);
+    void release();
+    int factor(const mhe_matrices& m, const mhe_rhs* rhs, double* x, double* w, double* lam);
+    int solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool after_fused);
+
+private:
+    template <typename T>
+    LevelArgs<T> args(int k) const;
+    template <typename T>
+    void pass_reduce(const double* l, const double* a);
+    template <typename T>
+    void pass_rhs(const double* l, const double* a, const double* l0, const double* a0, const double* lN);
+    template <typename T>
+    void pass_down(const double* l, const double* a, const double* l0, const double* a0, const double* x0,
+                   const double* lN, double* x, double* w, double* lam, double* zx, double* zw, double* zl,
+                   const int* act);
+    template <typename T>
+    int run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool skip_first_rhs);
+    void residual(const mhe_rhs* rhs, const double* x, const double* w, const double* lam, const int* act);
+};
+
+}  // namespace mhe

@@ -1,0 +1,142 @@
+// kernels.cuh -- __global__ wrappers and launchers of the level passes.
+//
+// Launch shape: one warp per chunk, W warps per CTA where W is the number of
+// per-warp shared-memory workspaces that fit in 200 KB (at most 8).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "engine.h"
+#include "resid.cuh"
+#include "tree.cuh"
+
+namespace mhe {
+
+template <typename T, int NX>
+constexpr int level_warps()
+{
+    return (200 * 1024) / (int)(Ws<T, NX>::count * sizeof(T)) >= 8
+               ? 8
+               : ((200 * 1024) / (int)(Ws<T, NX>::count * sizeof(T)) < 1
+                      ? 1
+                      : (200 * 1024) / (int)(Ws<T, NX>::count * sizeof(T)));
+}
+
+enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2 };
+
+template <typename T, int NX, int NW, int UPPER, int OP>
+__global__ void __launch_bounds__(256) k_level(LevelArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int W = level_warps<T, NX>();
+    const int warp = threadIdx.x >> 5;
+    const int ci = blockIdx.x * W + warp;
+    if (ci >= a.nchunks) return;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * Ws<T, NX>::count;
+    if (OP == OP_REDUCE) reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    else if (OP == OP_RHS) rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    else down_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+}
+
+template <typename T, int NX, int NW, int UPPER, int OP>
+void launch_level_v(const LevelArgs<T>& a, void* stream)
+{
+    constexpr int W = level_warps<T, NX>();
+    const size_t smem = (size_t)W * Ws<T, NX>::count * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_level<T, NX, NW, UPPER, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    const int grid = (a.nchunks + W - 1) / W;
+    k_level<T, NX, NW, UPPER, OP><<<grid, 32 * W, smem, (cudaStream_t)stream>>>(a);
+}
+
+template <typename T, int NX, int NW, int OP>
+void launch_level(const LevelArgs<T>& a, int upper, void* stream)
+{
+    if (a.nchunks <= 0) return;
+    if (upper) launch_level_v<T, NX, NW, 1, OP>(a, stream);
+    else launch_level_v<T, NX, NW, 0, OP>(a, stream);
+}
+
+template <int NX, int NW>
+__global__ void __launch_bounds__(256) k_resid(ResidArgs r)
+{
+    __shared__ double sm[8][ResidSmem<NX, NW>::count];
+    const int warp = threadIdx.x >> 5;
+    const long long g = (long long)blockIdx.x * 8 + warp;
+    if (g >= r.nstages) return;
+    resid_stage<NX, NW>(r, g, sm[warp]);
+}
+
+template <int NX, int NW>
+void launch_resid(const ResidArgs& r, void* stream)
+{
+    if (r.nstages <= 0) return;
+    const long long grid = (r.nstages + 7) / 8;
+    k_resid<NX, NW><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
+}
+
+template <int NX, int NW, int NY>
+constexpr int asm_warps()
+{
+    return (40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8) >= 8
+               ? 8
+               : ((40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8) < 1
+                      ? 1
+                      : (40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8));
+}
+
+template <int NX, int NW, int NY>
+__global__ void __launch_bounds__(256) k_assemble(long long S, const double* C, const double* R,
+                                                   const double* yt, const double* wt, double* Q, double* l,
+                                                   double* c)
+{
+    constexpr int W = asm_warps<NX, NW, NY>();
+    __shared__ double sm[W][AsmSmem<NX, NW, NY>::count];
+    const int warp = threadIdx.x >> 5;
+    const long long s = (long long)blockIdx.x * W + warp;
+    if (s >= S) return;
+    constexpr int NR = NW + NY, NQ = NX + NW;
+    assemble_stage<NX, NW, NY>(C + s * NY * NX, R + s * NR * NR, yt + s * NY, wt + s * NW, Q + s * NQ * NQ,
+                               l + s * NQ, c ? c + s : nullptr, sm[warp]);
+}
+
+template <int NX, int NW, int NY>
+void launch_assemble(long long S, const double* C, const double* R, const double* yt, const double* wt,
+                     double* Q, double* l, double* c, void* stream)
+{
+    if (S <= 0) return;
+    constexpr int W = asm_warps<NX, NW, NY>();
+    const long long grid = (S + W - 1) / W;
+    k_assemble<NX, NW, NY><<<(unsigned)grid, 32 * W, 0, (cudaStream_t)stream>>>(S, C, R, yt, wt, Q, l, c);
+}
+
+// Everything one compiled shape provides.
+struct ShapeEntry {
+    ShapeOps ops;
+    int ny;
+    void (*assemble)(long long, const double*, const double*, const double*, const double*, double*, double*,
+                     double*, void*);
+};
+
+template <int NX, int NW, int NY>
+ShapeEntry make_shape()
+{
+    ShapeEntry e;
+    e.ops.nx = NX;
+    e.ops.nw = NW;
+    e.ops.reduce64 = &launch_level<double, NX, NW, OP_REDUCE>;
+    e.ops.rhs64 = &launch_level<double, NX, NW, OP_RHS>;
+    e.ops.down64 = &launch_level<double, NX, NW, OP_DOWN>;
+    e.ops.reduce32 = &launch_level<float, NX, NW, OP_REDUCE>;
+    e.ops.rhs32 = &launch_level<float, NX, NW, OP_RHS>;
+    e.ops.down32 = &launch_level<float, NX, NW, OP_DOWN>;
+    e.ops.resid = &launch_resid<NX, NW>;
+    e.ny = NY;
+    e.assemble = &launch_assemble<NX, NW, NY>;
+    return e;
+}
+
+}  // namespace mhe

@@ -1,0 +1,793 @@
+// tree.cuh -- warp-per-subproblem bodies of the parallel Riccati tree.
+//
+// One warp owns one subproblem (chunk) of one level and walks its stages
+// serially; inside a stage the lanes share the small dense products.  All
+// per-chunk state (P, Psi, V, v, Q^_w) and the stage's A_t, B_t live in shared
+// memory; Q_t and l_t are read from global memory inside the products.
+//
+//   reduce_chunk  Algorithm 4 (matrix part always; vector part when a
+//                 right-hand side is given).  Non-last chunks emit the master
+//                 stage (A^ = V_0^T, a^ = v_0, Q^_x = P_0, l^_x = -Psi_0, and the
+//                 input part in square-root form B = R^T, Q_w = I with
+//                 R^T R = Q^_w = B^); the last chunk of a level is factored with its
+//                 known terminal (Algorithms 1-2) and emits the next level's
+//                 terminal cost (Q^_x,p = P_0, l^_x,p = -Psi_0); the top chunk
+//                 emits nothing.
+//   rhs_chunk     the vector part of Algorithm 4 alone with stored factors
+//                 (k, Psi, and a^ by simulating the closed loop
+//                 x_{t+1} = (A + B K_0) x_t + a + B k_0 from x = 0, which is
+//                 Eq. a).
+//   down_chunk    the solution of one subproblem from its parent's x^_i, w^_i
+//                 (= R^{-1} w^'_i) and lambda^_{i+1}: w_t = k_0 + K_0 x_t - L_{t+1} w^_i
+//                 (Eq. control_signal_def with the T-form reduced input),
+//                 x_{t+1} = A x + B w + a, then the costate sweep
+//                 lambda_t = Q_x x_t + Q_xw w_t + l_x + A^T lambda_{t+1}.
+//   resid_stage   KKT residual rows of one stage (FP64).
+//   assemble_stage  MHE weights -> UFTOC Q_t, l_t, c_t (Section II).
+#pragma once
+#include "common.h"
+#include "warp.cuh"
+
+namespace mhe {
+
+enum { KIND_LEAF = 0, KIND_ARRIVAL = 1, KIND_UPPER = 2 };
+
+// Shared-memory workspace of one warp (every matrix slot holds up to NX x NX
+// with an odd leading dimension to spread the banks).
+template <typename T, int NX>
+struct Ws {
+    static constexpr int ld = NX | 1;
+    static constexpr int slot = NX * ld;
+    static constexpr int count = ((10 * slot + 8 * NX + 8) + 3) / 4 * 4;
+    T *P, *V, *Qw, *A, *Tt, *B, *PB, *H, *K, *G;
+    T *Psi, *v, *u, *e, *tv, *g, *k, *tmp;
+    T* sc;
+    MHE_DEV void carve(T* base)
+    {
+        T* p = base;
+        P = p; p += slot; V = p; p += slot; Qw = p; p += slot; A = p; p += slot;
+        Tt = p; p += slot; B = p; p += slot; PB = p; p += slot; H = p; p += slot;
+        K = p; p += slot; G = p; p += slot;
+        Psi = p; p += NX; v = p; p += NX; u = p; p += NX; e = p; p += NX;
+        tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
+        sc = p;
+    }
+};
+
+// upper-triangle index -> (i <= j)
+MHE_DEV void tri_ij(int idx, int& i, int& j)
+{
+    int jj = (int)((msqrt(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while ((jj + 1) * (jj + 2) / 2 <= idx) ++jj;
+    while (jj * (jj + 1) / 2 > idx) --jj;
+    j = jj;
+    i = idx - jj * (jj + 1) / 2;
+}
+
+// Data of one stage.  LEAF: the caller's stage arrays (Q is (n+m)^2).
+// ARRIVAL: A = B = I, Q = diag(0, P~0^{-1}).  UPPER: a master-problem stage in
+// square-root form: A = A^, B = R^T, Q = blkdiag(Q^_x, I), l = (l^_x, 0),
+// where R^T R = Q^_w is the Cholesky factorisation of the T-form Q^_w = B^.
+struct StageRef {
+    const double *A, *B, *Q, *Qx, *Qw0, *l, *a;
+};
+
+template <int KIND, int NX, int MT>
+struct Acc {
+    static MHE_DEV double A(const StageRef& s, int i, int j)
+    {
+        return KIND == KIND_ARRIVAL ? (i == j ? 1.0 : 0.0) : s.A[i + j * NX];
+    }
+    static MHE_DEV double B(const StageRef& s, int i, int j)
+    {
+        return KIND == KIND_ARRIVAL ? (i == j ? 1.0 : 0.0) : s.B[i + j * NX];
+    }
+    static MHE_DEV double qx(const StageRef& s, int i, int j)
+    {
+        if (KIND == KIND_LEAF) return s.Q[i + j * (NX + MT)];
+        if (KIND == KIND_UPPER) return s.Qx[i + j * NX];
+        return 0.0;
+    }
+    static MHE_DEV double qxw(const StageRef& s, int i, int j)
+    {
+        return KIND == KIND_LEAF ? s.Q[i + (NX + j) * (NX + MT)] : 0.0;
+    }
+    static MHE_DEV double qw(const StageRef& s, int i, int j)
+    {
+        if (KIND == KIND_LEAF) return s.Q[(NX + i) + (NX + j) * (NX + MT)];
+        if (KIND == KIND_UPPER) return i == j ? 1.0 : 0.0;   // square-root master stage
+        return s.Qw0[i + j * NX];
+    }
+    static MHE_DEV double lx(const StageRef& s, int i) { return s.l ? s.l[i] : 0.0; }
+    static MHE_DEV double lw(const StageRef& s, int j)
+    {
+        return (KIND != KIND_UPPER && s.l) ? s.l[NX + j] : 0.0;
+    }
+    static MHE_DEV double a(const StageRef& s, int i) { return s.a ? s.a[i] : 0.0; }
+};
+
+// A -> s.A, B -> s.B, a -> s.e
+template <typename T, int NX, int MT, int KIND>
+MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef& st)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    using X = Acc<KIND, NX, MT>;
+    wfor(NX * NX + NX * MT + NX, [&](int idx) {
+        if (idx < NX * NX) {
+            int i = idx % NX, j = idx / NX;
+            s.A[i + j * ld] = (T)X::A(st, i, j);
+        } else if (idx < NX * NX + NX * MT) {
+            int r = idx - NX * NX, i = r % NX, j = r / NX;
+            s.B[i + j * ld] = (T)X::B(st, i, j);
+        } else {
+            int i = idx - NX * NX - NX * MT;
+            s.e[i] = (T)X::a(st, i);
+        }
+    });
+}
+
+// In-place lower Cholesky of the M x M matrix Gm (leading dimension ld of the
+// workspace).  Returns true when a pivot fell below piv_rel * max diag (the
+// pivot is then replaced by 1 to stay finite).
+template <typename T, int NX, int M>
+MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    wone([&](int) {
+        T mx = 0;
+        for (int i = 0; i < M; ++i) mx = mmax(mx, mabs(Gm[i + i * ld]));
+        s.sc[0] = (T)(piv_rel * (double)mx);
+        s.sc[1] = 0;
+    });
+    for (int j = 0; j < M; ++j) {
+        wone([&](int) {
+            T d = Gm[j + j * ld];
+            if (!(d > s.sc[0])) { s.sc[1] = 1; d = 1; }
+            Gm[j + j * ld] = msqrt(d);
+        });
+        const T djj = Gm[j + j * ld];
+        wfor(M - j - 1, [&](int r) { Gm[j + 1 + r + j * ld] /= djj; });
+        const int nt = M - j - 1;
+        wfor(nt * nt, [&](int r) {
+            int i = j + 1 + r % nt, c = j + 1 + r / nt;
+            if (i >= c) Gm[i + c * ld] -= Gm[i + j * ld] * Gm[c + j * ld];
+        });
+    }
+    return s.sc[1] != 0;
+}
+
+template <typename T, int NX, int MT>
+MHE_DEV bool chol_G(Ws<T, NX>& s, double piv_rel)
+{
+    return chol_inplace<T, NX, MT>(s, s.G, piv_rel);
+}
+
+// y := (L L^T)^{-1} y with L = lower(s.G), y in registers.
+template <typename T, int NX, int MT>
+MHE_DEV void chol_solve_reg(const Ws<T, NX>& s, T (&y)[MT])
+{
+    constexpr int ld = Ws<T, NX>::ld;
+#pragma unroll
+    for (int j = 0; j < MT; ++j) {
+        T acc = y[j];
+#pragma unroll
+        for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * y[p];
+        y[j] = acc / s.G[j + j * ld];
+    }
+#pragma unroll
+    for (int j = MT - 1; j >= 0; --j) {
+        T acc = y[j];
+#pragma unroll
+        for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * y[p];
+        y[j] = acc / s.G[j + j * ld];
+    }
+}
+
+// One backward stage of Algorithm 4 (or Algorithms 1-2 when want_v is false).
+// On entry s.P = P_{t+1}, s.Psi = Psi_{t+1}, s.V = V_{t+1}, s.v = v_{t+1},
+// s.Qw = partial Q^_w.  Stores P_{t+1}, chol(G_{t+1}), K_{t+1}, k_{t+1},
+// L_{t+1} (nullptr skips a store).  Returns true on a failed pivot.
+template <typename T, int NX, int MT, int KIND>
+MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef& st, T* Pout, T* Lgout, T* Kout,
+                         T* kout, T* Lout, bool want_v, double piv_rel)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    constexpr int NT = NX * (NX + 1) / 2, MTT = MT * (MT + 1) / 2;
+    using X = Acc<KIND, NX, MT>;
+    if (Pout)
+        wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
+    load_AB<T, NX, MT, KIND>(s, st);
+    // P A -> Tt,  P B -> PB,  u = Psi - P a
+    wfor(NX * NX + NX * MT + NX, [&](int idx) {
+        if (idx < NX * NX) {
+            int i = idx % NX, j = idx / NX;
+            T acc = 0;
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.P[i + p * ld] * s.A[p + j * ld];
+            s.Tt[i + j * ld] = acc;
+        } else if (idx < NX * NX + NX * MT) {
+            int r = idx - NX * NX, i = r % NX, j = r / NX;
+            T acc = 0;
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.P[i + p * ld] * s.B[p + j * ld];
+            s.PB[i + j * ld] = acc;
+        } else {
+            int i = idx - NX * NX - NX * MT;
+            T acc = s.Psi[i];
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc -= s.P[i + p * ld] * s.e[p];
+            s.u[i] = acc;
+        }
+    });
+    // F -> P (upper triangle mirrored), G, H,  g = B^T u - l_w,  tv = A^T u
+    wfor(NT + MTT + NX * MT + MT + NX, [&](int idx) {
+        if (idx < NT) {
+            int i, j;
+            tri_ij(idx, i, j);
+            T acc = (T)X::qx(st, i, j);
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.Tt[p + j * ld];
+            s.P[i + j * ld] = acc;
+            s.P[j + i * ld] = acc;
+        } else if (idx < NT + MTT) {
+            int i, j;
+            tri_ij(idx - NT, i, j);
+            T acc = (T)X::qw(st, i, j);
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.B[p + i * ld] * s.PB[p + j * ld];
+            s.G[i + j * ld] = acc;
+            s.G[j + i * ld] = acc;
+        } else if (idx < NT + MTT + NX * MT) {
+            int r = idx - NT - MTT, i = r % NX, j = r / NX;
+            T acc = (T)X::qxw(st, i, j);
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.PB[p + j * ld];
+            s.H[i + j * ld] = acc;
+        } else if (idx < NT + MTT + NX * MT + MT) {
+            int j = idx - NT - MTT - NX * MT;
+            T acc = -(T)X::lw(st, j);
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.B[p + j * ld] * s.u[p];
+            s.g[j] = acc;
+        } else {
+            int i = idx - NT - MTT - NX * MT - MT;
+            T acc = 0;
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.u[p];
+            s.tv[i] = acc;
+        }
+    });
+    const bool bad = chol_G<T, NX, MT>(s, piv_rel);
+    // per column c: y = Lg^{-1} H^T e_c -> Y (in PB), K e_c = -Lg^{-T} y;  lane NX: k = G^{-1} g
+    wfor(NX + 1, [&](int c) {
+        T y[MT];
+        if (c < NX) {
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                T acc = s.H[c + j * ld];
+#pragma unroll
+                for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * y[p];
+                y[j] = acc / s.G[j + j * ld];
+            }
+#pragma unroll
+            for (int j = 0; j < MT; ++j) s.PB[j + c * ld] = y[j];
+#pragma unroll
+            for (int j = MT - 1; j >= 0; --j) {
+                T acc = y[j];
+#pragma unroll
+                for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * y[p];
+                y[j] = acc / s.G[j + j * ld];
+            }
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                s.K[j + c * ld] = -y[j];
+                if (Kout) Kout[j + c * MT] = -y[j];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < MT; ++j) y[j] = s.g[j];
+            chol_solve_reg<T, NX, MT>(s, y);
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                s.k[j] = y[j];
+                if (kout) kout[j] = y[j];
+            }
+        }
+    });
+    // P -= Y^T Y,  Psi = A^T u - l_x + K^T g,  store chol(G)
+    wfor(NT + NX + (Lgout ? MT * MT : 0), [&](int idx) {
+        if (idx < NT) {
+            int i, j;
+            tri_ij(idx, i, j);
+            T acc = s.P[i + j * ld];
+#pragma unroll 8
+            for (int q = 0; q < MT; ++q) acc -= s.PB[q + i * ld] * s.PB[q + j * ld];
+            s.P[i + j * ld] = acc;
+            s.P[j + i * ld] = acc;
+        } else if (idx < NT + NX) {
+            int i = idx - NT;
+            T acc = s.tv[i] - (T)X::lx(st, i);
+#pragma unroll 8
+            for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.g[q];
+            s.Psi[i] = acc;
+        } else {
+            int r = idx - NT - NX, i = r % MT, j = r / MT;
+            Lgout[r] = i >= j ? s.G[i + j * ld] : (T)0;
+        }
+    });
+    if (!want_v) return bad;
+    // e = a + B k
+    wfor(NX, [&](int i) {
+        T acc = s.e[i];
+#pragma unroll 8
+        for (int j = 0; j < MT; ++j) acc += s.B[i + j * ld] * s.k[j];
+        s.tv[i] = acc;
+    });
+    // v += V^T e;  per column c: BV = B^T V e_c (in H), Z = Lg^{-1} BV (in PB), L e_c = -Lg^{-T} Z
+    wfor(2 * NX, [&](int idx) {
+        if (idx < NX) {
+            T acc = s.v[idx];
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.V[p + idx * ld] * s.tv[p];
+            s.v[idx] = acc;
+        } else {
+            const int c = idx - NX;
+            T z[MT];
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                T acc = 0;
+#pragma unroll 8
+                for (int p = 0; p < NX; ++p) acc += s.B[p + j * ld] * s.V[p + c * ld];
+                z[j] = acc;
+                s.H[j + c * ld] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                T acc = z[j];
+#pragma unroll
+                for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * z[p];
+                z[j] = acc / s.G[j + j * ld];
+            }
+#pragma unroll
+            for (int j = 0; j < MT; ++j) s.PB[j + c * ld] = z[j];
+#pragma unroll
+            for (int j = MT - 1; j >= 0; --j) {
+                T acc = z[j];
+#pragma unroll
+                for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * z[p];
+                z[j] = acc / s.G[j + j * ld];
+            }
+            if (Lout) {
+#pragma unroll
+                for (int j = 0; j < MT; ++j) Lout[j + c * MT] = -z[j];
+            }
+        }
+    });
+    // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z
+    wfor(NX * NX + NT, [&](int idx) {
+        if (idx < NX * NX) {
+            int i = idx % NX, j = idx / NX;
+            T acc = 0;
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.V[p + j * ld];
+#pragma unroll 8
+            for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.H[q + j * ld];
+            s.Tt[i + j * ld] = acc;
+        } else {
+            int i, j;
+            tri_ij(idx - NX * NX, i, j);
+            T acc = s.Qw[i + j * ld];
+#pragma unroll 8
+            for (int q = 0; q < MT; ++q) acc += s.PB[q + i * ld] * s.PB[q + j * ld];
+            s.Qw[i + j * ld] = acc;
+            s.Qw[j + i * ld] = acc;
+        }
+    });
+    T* tmp = s.V;
+    s.V = s.Tt;
+    s.Tt = tmp;
+    return bad;
+}
+
+// ---- stage addressing -------------------------------------------------------
+
+template <typename T, int NX, int NW>
+struct Addr {
+    // level-0 stage t >= 1 of instance b
+    static MHE_DEV StageRef leaf(const LevelArgs<T>& a, int b, int t)
+    {
+        const long long s = a.in_off[b] + t - 1;
+        StageRef r;
+        r.A = a.A + s * NX * NX;
+        r.B = a.B + s * NX * NW;
+        r.Q = a.Q + s * (NX + NW) * (NX + NW);
+        r.Qx = nullptr;
+        r.Qw0 = nullptr;
+        r.l = a.l ? a.l + s * (NX + NW) : nullptr;
+        r.a = a.a ? a.a + s * NX : nullptr;
+        return r;
+    }
+    static MHE_DEV StageRef arrival(const LevelArgs<T>& a, int b)
+    {
+        StageRef r;
+        r.A = r.B = r.Q = r.Qx = nullptr;
+        r.Qw0 = a.P0inv + (long long)b * NX * NX;
+        r.l = a.l0 ? a.l0 + (long long)b * 2 * NX : nullptr;
+        r.a = a.a0 ? a.a0 + (long long)b * NX : nullptr;
+        return r;
+    }
+    static MHE_DEV StageRef upper(const LevelArgs<T>& a, long long g)
+    {
+        StageRef r;
+        r.A = a.Ah + g * NX * NX;
+        r.B = a.Bh + g * NX * NX;
+        r.Q = nullptr;
+        r.Qx = a.Qxh + g * NX * NX;
+        r.Qw0 = nullptr;
+        r.l = a.lxh ? a.lxh + g * NX : nullptr;
+        r.a = a.ah ? a.ah + g * NX : nullptr;
+        return r;
+    }
+};
+
+// ---- Algorithm 4 over one chunk ----------------------------------------------
+
+template <typename T, int NX, int NW, bool UPPER>
+MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    const ChunkDesc cd = a.chunks[ci];
+    const int b = cd.inst;
+    const bool last = (cd.flags & CH_LAST) != 0;
+    const bool top = (cd.flags & CH_TOP) != 0;
+    Ws<T, NX> s;
+    s.carve(smem);
+    const double* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;   // level 0: Q_{x,N} = 0
+    const double* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
+                             : (a.lN ? a.lN + (long long)b * NX : nullptr);
+    wfor(NX * NX, [&](int idx) {
+        int i = idx % NX, j = idx / NX;
+        s.P[i + j * ld] = (last && QN) ? (T)QN[idx] : (T)0;
+        s.V[i + j * ld] = (T)(i == j ? 1 : 0);
+        s.Qw[i + j * ld] = 0;
+        if (idx < NX) {
+            s.Psi[idx] = (last && lN) ? (T)(-lN[idx]) : (T)0;
+            s.v[idx] = 0;
+        }
+    });
+    int bad_t = -1;
+    for (int tt = cd.len - 1; tt >= 0; --tt) {
+        const int t = cd.t0 + tt;
+        const long long g = cd.g0 + tt;
+        bool bad;
+        if (UPPER) {
+            bad = reduce_step<T, NX, NX, KIND_UPPER>(
+                s, Addr<T, NX, NW>::upper(a, g), a.store_P ? a.Pst + g * NX * NX : nullptr,
+                a.Lgst + g * NX * NX, a.Kst + g * NX * NX, a.kst + g * NX,
+                last ? nullptr : a.Lst + g * NX * NX, !last, a.piv_rel);
+        } else if (t == 0) {
+            bad = reduce_step<T, NX, NX, KIND_ARRIVAL>(
+                s, Addr<T, NX, NW>::arrival(a, b), a.store_P ? a.Pst0 + (long long)b * NX * NX : nullptr,
+                a.Lgst0 + (long long)b * NX * NX, a.Kst0 + (long long)b * NX * NX, a.kst0 + (long long)b * NX,
+                last ? nullptr : a.Lst0 + (long long)b * NX * NX, !last, a.piv_rel);
+        } else {
+            bad = reduce_step<T, NX, NW, KIND_LEAF>(
+                s, Addr<T, NX, NW>::leaf(a, b, t), a.store_P ? a.Pst + g * NX * NX : nullptr,
+                a.Lgst + g * NW * NW, a.Kst + g * NW * NX, a.kst + g * NW,
+                last ? nullptr : a.Lst + g * NW * NX, !last, a.piv_rel);
+        }
+        if (bad && bad_t < 0) bad_t = t;
+    }
+    if (!last) {
+        // Theorem 1 with the basis U_1 = S^T R^{-1} (orthonormal in the Q-bar^{-1}
+        // inner product): Q^_w = I and B^ = R^T, where R^T R is the T-form
+        // Q^_w = S Qbar^{-1} S^T accumulated above.  Same master problem with
+        // w^' = R w^; its G = I + R P R^T is far better conditioned than
+        // B^ + B^ P B^.
+        if (chol_inplace<T, NX, NX>(s, s.Qw, a.piv_rel) && bad_t < 0) bad_t = cd.t0;
+        const long long gp = cd.parent;
+        wfor(NX * NX, [&](int idx) {
+            int i = idx % NX, j = idx / NX;
+            a.Ah_up[gp * NX * NX + idx] = (double)s.V[j + i * ld];
+            a.Bh_up[gp * NX * NX + idx] = i >= j ? (double)s.Qw[i + j * ld] : 0.0;
+            a.Qxh_up[gp * NX * NX + idx] = (double)s.P[i + j * ld];
+            if (idx < NX) {
+                a.ah_up[gp * NX + idx] = (double)s.v[idx];
+                a.lxh_up[gp * NX + idx] = -(double)s.Psi[idx];
+            }
+        });
+    } else if (!top) {
+        wfor(NX * NX, [&](int idx) {
+            a.QN_up[(long long)b * NX * NX + idx] = (double)s.P[idx % NX + (idx / NX) * ld];
+            if (idx < NX) a.lN_up[(long long)b * NX + idx] = -(double)s.Psi[idx];
+        });
+    }
+    if (bad_t >= 0) wone([&](int) { record_error(a.status, a.where, b, -3, a.level, ci, bad_t); });
+}
+
+// ---- the vector part of Algorithm 4 with stored factors -----------------------
+
+template <typename T, int NX, int MT, int KIND>
+MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef& st, const T* Pin, const T* Lgin,
+                      const T* Kin, T* kout)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    using X = Acc<KIND, NX, MT>;
+    load_AB<T, NX, MT, KIND>(s, st);
+    wfor(MT * MT + MT * NX + NX, [&](int idx) {
+        if (idx < MT * MT) {
+            s.G[idx % MT + (idx / MT) * ld] = Lgin[idx];
+        } else if (idx < MT * MT + MT * NX) {
+            int r = idx - MT * MT;
+            s.K[r % MT + (r / MT) * ld] = Kin[r];
+        } else {
+            int i = idx - MT * MT - MT * NX;
+            T acc = s.Psi[i];
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc -= Pin[i + p * NX] * s.e[p];
+            s.u[i] = acc;
+        }
+    });
+    wfor(MT + NX, [&](int idx) {
+        if (idx < MT) {
+            T acc = -(T)X::lw(st, idx);
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.B[p + idx * ld] * s.u[p];
+            s.g[idx] = acc;
+        } else {
+            int i = idx - MT;
+            T acc = 0;
+#pragma unroll 8
+            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.u[p];
+            s.tv[i] = acc;
+        }
+    });
+    wone([&](int) {
+        T y[MT];
+#pragma unroll
+        for (int j = 0; j < MT; ++j) y[j] = s.g[j];
+        chol_solve_reg<T, NX, MT>(s, y);
+#pragma unroll
+        for (int j = 0; j < MT; ++j) {
+            s.k[j] = y[j];
+            kout[j] = y[j];
+        }
+    });
+    wfor(NX, [&](int i) {
+        T acc = s.tv[i] - (T)X::lx(st, i);
+#pragma unroll 8
+        for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.g[q];
+        s.Psi[i] = acc;
+    });
+}
+
+// closed-loop step x <- A x + B (K x + k) + a, x in s.e (in), result in s.u
+template <typename T, int NX, int MT, int KIND>
+MHE_DEV void closed_loop_step(Ws<T, NX>& s, const StageRef& st, const T* Kin, const T* kin)
+{
+    using X = Acc<KIND, NX, MT>;
+    wfor(MT, [&](int j) {
+        T acc = kin[j];
+#pragma unroll 8
+        for (int i = 0; i < NX; ++i) acc += Kin[j + i * MT] * s.e[i];
+        s.tmp[j] = acc;
+    });
+    wfor(NX, [&](int i) {
+        T acc = (T)X::a(st, i);
+#pragma unroll 8
+        for (int j = 0; j < NX; ++j) acc += (T)X::A(st, i, j) * s.e[j];
+#pragma unroll 8
+        for (int j = 0; j < MT; ++j) acc += (T)X::B(st, i, j) * s.tmp[j];
+        s.u[i] = acc;
+    });
+    wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
+}
+
+template <typename T, int NX, int NW, bool UPPER>
+MHE_DEV void rhs_chunk(const LevelArgs<T>& a, int ci, T* smem)
+{
+    const ChunkDesc cd = a.chunks[ci];
+    const int b = cd.inst;
+    if (a.active && !a.active[b]) return;
+    const bool last = (cd.flags & CH_LAST) != 0;
+    const bool top = (cd.flags & CH_TOP) != 0;
+    Ws<T, NX> s;
+    s.carve(smem);
+    const double* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
+                             : (a.lN ? a.lN + (long long)b * NX : nullptr);
+    wfor(NX, [&](int i) { s.Psi[i] = (last && lN) ? (T)(-lN[i]) : (T)0; });
+    for (int tt = cd.len - 1; tt >= 0; --tt) {
+        const int t = cd.t0 + tt;
+        const long long g = cd.g0 + tt;
+        if (UPPER) {
+            rhs_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), a.Pst + g * NX * NX,
+                                            a.Lgst + g * NX * NX, a.Kst + g * NX * NX, a.kst + g * NX);
+        } else if (t == 0) {
+            rhs_step<T, NX, NX, KIND_ARRIVAL>(s, Addr<T, NX, NW>::arrival(a, b), a.Pst0 + (long long)b * NX * NX,
+                                              a.Lgst0 + (long long)b * NX * NX, a.Kst0 + (long long)b * NX * NX,
+                                              a.kst0 + (long long)b * NX);
+        } else {
+            rhs_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), a.Pst + g * NX * NX,
+                                           a.Lgst + g * NW * NW, a.Kst + g * NW * NX, a.kst + g * NW);
+        }
+    }
+    if (!last) {
+        // a^: closed loop from x = 0 over the chunk
+        wfor(NX, [&](int i) { s.e[i] = 0; });
+        for (int tt = 0; tt < cd.len; ++tt) {
+            const int t = cd.t0 + tt;
+            const long long g = cd.g0 + tt;
+            if (UPPER)
+                closed_loop_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), a.Kst + g * NX * NX,
+                                                        a.kst + g * NX);
+            else if (t == 0)
+                closed_loop_step<T, NX, NX, KIND_ARRIVAL>(s, Addr<T, NX, NW>::arrival(a, b),
+                                                          a.Kst0 + (long long)b * NX * NX, a.kst0 + (long long)b * NX);
+            else
+                closed_loop_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), a.Kst + g * NW * NX,
+                                                       a.kst + g * NW);
+        }
+        const long long gp = cd.parent;
+        wfor(NX, [&](int i) {
+            a.ah_up[gp * NX + i] = (double)s.e[i];
+            a.lxh_up[gp * NX + i] = -(double)s.Psi[i];
+        });
+    } else if (!top) {
+        wfor(NX, [&](int i) { a.lN_up[(long long)b * NX + i] = -(double)s.Psi[i]; });
+    }
+}
+
+// ---- down pass ---------------------------------------------------------------
+
+template <typename T, int NX, int MT, int KIND>
+MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef& st, const T* Kin, const T* kin,
+                           const T* Lin, bool use_wh, double* xo, double* wo)
+{
+    using X = Acc<KIND, NX, MT>;
+    // x_t in s.e, w^ in s.v
+    wfor(MT + NX, [&](int idx) {
+        if (idx < MT) {
+            const int j = idx;
+            T acc = kin[j];
+#pragma unroll 8
+            for (int i = 0; i < NX; ++i) acc += Kin[j + i * MT] * s.e[i];
+            if (use_wh) {
+#pragma unroll 8
+                for (int i = 0; i < NX; ++i) acc -= Lin[j + i * MT] * s.v[i];
+            }
+            s.tmp[j] = acc;
+            wo[j] = (double)acc;
+        } else {
+            xo[idx - MT] = (double)s.e[idx - MT];
+        }
+    });
+    wfor(NX, [&](int i) {
+        T acc = (T)X::a(st, i);
+#pragma unroll 8
+        for (int j = 0; j < NX; ++j) acc += (T)X::A(st, i, j) * s.e[j];
+#pragma unroll 8
+        for (int j = 0; j < MT; ++j) acc += (T)X::B(st, i, j) * s.tmp[j];
+        s.u[i] = acc;
+    });
+    wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
+}
+
+// lambda_t = Q_x x_t + Q_xw w_t + l_x + A^T lambda_{t+1}  (lambda_{t+1} in s.Psi -> result in s.Psi)
+template <typename T, int NX, int MT, int KIND>
+MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef& st, const double* xt, const double* wt,
+                           double* lo, double* zx, double* zw, double* zl)
+{
+    using X = Acc<KIND, NX, MT>;
+    wfor(NX, [&](int i) {
+        T acc = (T)X::lx(st, i);
+#pragma unroll 8
+        for (int j = 0; j < NX; ++j) acc += (T)X::qx(st, i, j) * (T)xt[j];
+#pragma unroll 8
+        for (int j = 0; j < MT; ++j) acc += (T)X::qxw(st, i, j) * (T)wt[j];
+#pragma unroll 8
+        for (int j = 0; j < NX; ++j) acc += (T)X::A(st, j, i) * s.Psi[j];
+        s.u[i] = acc;
+    });
+    wfor(NX + (zx ? NX + MT : 0), [&](int idx) {
+        if (idx < NX) {
+            s.Psi[idx] = s.u[idx];
+            lo[idx] = (double)s.u[idx];
+            if (zl) zl[idx] += (double)s.u[idx];
+        } else if (idx < 2 * NX) {
+            zx[idx - NX] += xt[idx - NX];
+        } else {
+            zw[idx - 2 * NX] += wt[idx - 2 * NX];
+        }
+    });
+}
+
+template <typename T, int NX, int NW, bool UPPER>
+MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
+{
+    const ChunkDesc cd = a.chunks[ci];
+    const int b = cd.inst;
+    if (a.active && !a.active[b]) return;
+    const bool last = (cd.flags & CH_LAST) != 0;
+    const bool top = (cd.flags & CH_TOP) != 0;
+    Ws<T, NX> s;
+    s.carve(smem);
+    const LevelInst li = a.li[b];
+    // x^_i -> s.e, w^_i -> s.v, lambda^_{i+1} -> s.Psi
+    wfor(NX, [&](int i) {
+        s.e[i] = top ? (T)a.x0[(long long)b * NX + i] : (T)a.xd_up[cd.px * NX + i];
+        s.v[i] = last ? (T)0 : (T)a.wd_up[cd.parent * NX + i];
+        s.Psi[i] = last ? (T)0 : (T)a.ld_up[(cd.px + 1) * NX + i];
+    });
+    if (!last) {
+        // the parent solved for w^' = R w^ (square-root master stage): w^ = R^{-1} w^'
+        const double* Lq = a.Bh_up + cd.parent * NX * NX;   // R^T, lower triangular
+        wone([&](int) {
+            for (int i = NX - 1; i >= 0; --i) {
+                T acc = s.v[i];
+                for (int p = i + 1; p < NX; ++p) acc -= (T)Lq[p + i * NX] * s.v[p];
+                s.v[i] = acc / (T)Lq[i + i * NX];
+            }
+        });
+    }
+    auto xo = [&](int t) -> double* { return a.xd + (li.gx + t) * NX; };
+    auto lo = [&](int t) -> double* { return a.ld + (li.gx + t) * NX; };
+    auto wo = [&](int t) -> double* {
+        if (UPPER) return a.wd + (li.gs + t) * NX;
+        return a.wd + a.w_off[b] + (t == 0 ? 0 : NX + (long long)(t - 1) * NW);
+    };
+    auto zxo = [&](int t) -> double* { return a.zx ? a.zx + (li.gx + t) * NX : nullptr; };
+    auto zlo = [&](int t) -> double* { return a.zl ? a.zl + (li.gx + t) * NX : nullptr; };
+    auto zwo = [&](int t) -> double* {
+        return a.zw ? a.zw + a.w_off[b] + (t == 0 ? 0 : NX + (long long)(t - 1) * NW) : nullptr;
+    };
+    for (int tt = 0; tt < cd.len; ++tt) {
+        const int t = cd.t0 + tt;
+        const long long g = cd.g0 + tt;
+        if (UPPER)
+            down_fwd_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), a.Kst + g * NX * NX,
+                                                 a.kst + g * NX, a.Lst + g * NX * NX, !last, xo(t), wo(t));
+        else if (t == 0)
+            down_fwd_step<T, NX, NX, KIND_ARRIVAL>(s, Addr<T, NX, NW>::arrival(a, b),
+                                                   a.Kst0 + (long long)b * NX * NX, a.kst0 + (long long)b * NX,
+                                                   a.Lst0 + (long long)b * NX * NX, !last, xo(t), wo(t));
+        else
+            down_fwd_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), a.Kst + g * NW * NX,
+                                                a.kst + g * NW, a.Lst + g * NW * NX, !last, xo(t), wo(t));
+    }
+    const int t1 = cd.t0 + cd.len;
+    if (last) {
+        // lambda_N = Q_{x,N} x_N + l_N (Q_{x,N} = 0 at level 0)
+        const double* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;
+        const double* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
+                                 : (a.lN ? a.lN + (long long)b * NX : nullptr);
+        wfor(NX, [&](int i) {
+            T acc = lN ? (T)lN[i] : (T)0;
+            if (QN) {
+#pragma unroll 8
+                for (int j = 0; j < NX; ++j) acc += (T)QN[i + j * NX] * s.e[j];
+            }
+            s.Psi[i] = acc;
+            xo(t1)[i] = (double)s.e[i];
+            lo(t1)[i] = (double)acc;
+            if (a.zx) {
+                zxo(t1)[i] += (double)s.e[i];
+                zlo(t1)[i] += (double)acc;
+            }
+        });
+    }
+    for (int tt = cd.len - 1; tt >= 0; --tt) {
+        const int t = cd.t0 + tt;
+        const long long g = cd.g0 + tt;
+        if (UPPER)
+            down_bwd_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), xo(t), wo(t), lo(t),
+                                                 zxo(t), zwo(t), zlo(t));
+        else if (t == 0)
+            down_bwd_step<T, NX, NX, KIND_ARRIVAL>(s, Addr<T, NX, NW>::arrival(a, b), xo(t), wo(t), lo(t),
+                                                   zxo(t), zwo(t), zlo(t));
+        else
+            down_bwd_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), xo(t), wo(t), lo(t),
+                                                zxo(t), zwo(t), zlo(t));
+    }
+}
+
+}  // namespace mhe

@@ -1,0 +1,63 @@
+// warp.cuh -- the warp-cooperative execution layer every tree kernel is written on.
+//
+// A kernel body is a sequence of `wfor(count, f)` steps: the 32 lanes of one warp
+// share the indices 0..count-1 round-robin, and the step ends with __syncwarp(),
+// so shared-memory results of one step are visible to every lane in the next.
+// Scalars and small vectors that one lane computes are written to shared memory
+// and read after the step's barrier.
+#ifndef MHE_WARP_CUH
+#define MHE_WARP_CUH
+#include <cuda_runtime.h>
+#include <math.h>
+
+#define MHE_DEV __device__ __forceinline__
+
+namespace mhe {
+
+MHE_DEV int lane_id() { return threadIdx.x & 31; }
+
+template <class F>
+MHE_DEV void wfor(int count, F&& f)
+{
+    for (int i = lane_id(); i < count; i += 32) f(i);
+    __syncwarp();
+}
+
+// One lane runs f (index 0); barrier afterwards.
+template <class F>
+MHE_DEV void wone(F&& f)
+{
+    if (lane_id() == 0) f(0);
+    __syncwarp();
+}
+
+MHE_DEV double msqrt(double v) { return sqrt(v); }
+MHE_DEV float msqrt(float v) { return sqrtf(v); }
+MHE_DEV double mabs(double v) { return fabs(v); }
+MHE_DEV float mabs(float v) { return fabsf(v); }
+MHE_DEV double mmax(double a, double b) { return fmax(a, b); }
+MHE_DEV float mmax(float a, float b) { return fmaxf(a, b); }
+MHE_DEV bool mfinite(double v) { return isfinite(v); }
+MHE_DEV bool mfinite(float v) { return isfinite(v); }
+
+// Record the first error of an instance: status, then where it happened.
+MHE_DEV void record_error(int* status, int* where, int inst, int code, int level, int chunk, int stage)
+{
+    if (status && atomicCAS(status + inst, 0, code) == 0 && where) {
+        where[3 * inst + 0] = level;
+        where[3 * inst + 1] = chunk;
+        where[3 * inst + 2] = stage;
+    }
+}
+
+// max of non-negative doubles through their bit patterns (ordered like the values)
+MHE_DEV void atomic_max_nonneg(double* addr, double v)
+{
+    if (!(v >= 0.0)) v = __longlong_as_double(0x7ff8000000000000LL);   // NaN: keep it visible
+    atomicMax(reinterpret_cast<unsigned long long*>(addr),
+              static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+}  // namespace mhe
+
+#endif  // MHE_WARP_CUH

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libmhe.so (include/mhe.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch supplies device memory and the current CUDA stream.  The functions
+keep the C names (mhe_create, mhe_factor, mhe_solve, mhe_factor_solve,
+mhe_destroy, mhe_assemble, mhe_workspace_bytes); `Solver` wraps them.
+If libmhe.so cannot be loaded the call raises: there is no other path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhe.so")
+
+MHE_FP64 = 0
+MHE_FP32_IR = 1
+
+STATUS = {0: "MHE_OK", 1: "MHE_PENDING", -1: "MHE_E_ARG", -2: "MHE_E_NOMEM", -3: "MHE_E_NOT_PD",
+          -4: "MHE_E_NONFINITE", -5: "MHE_E_NOT_FACTORED", -6: "MHE_E_NO_CONVERGE",
+          -7: "MHE_E_TIMEOUT", -8: "MHE_E_CUDA", -9: "MHE_E_ADMISSION"}
+
+c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+
+
+class mhe_dims(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("nw", c_int), ("batch", c_int), ("N", ctypes.POINTER(c_int)),
+                ("prec", c_int), ("leaf_len", c_int), ("branching", c_int), ("top_len", c_int),
+                ("refine_tol", c_double), ("max_refine", c_int)]
+
+
+class mhe_matrices(ctypes.Structure):
+    _fields_ = [("A", c_void_p), ("B", c_void_p), ("Q", c_void_p), ("P0inv", c_void_p)]
+
+
+class mhe_rhs(ctypes.Structure):
+    _fields_ = [("l", c_void_p), ("a", c_void_p), ("x0", c_void_p)]
+
+
+class mhe_info(ctypes.Structure):
+    _fields_ = [("status", c_int), ("level", c_int), ("chunk", c_int), ("stage", c_int),
+                ("refine_iters", c_int), ("pad", c_int), ("relres", c_double), ("est_relerr", c_double)]
+
+
+INFO_DTYPE = np.dtype([("status", np.int32), ("level", np.int32), ("chunk", np.int32),
+                       ("stage", np.int32), ("refine_iters", np.int32), ("pad", np.int32),
+                       ("relres", np.float64), ("est_relerr", np.float64)])
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _declare(L):
+    P = ctypes.POINTER
+    L.mhe_create.argtypes = [P(mhe_dims), c_void_p, P(c_void_p)]
+    L.mhe_create.restype = c_int
+    L.mhe_workspace_bytes.argtypes = [P(mhe_dims)]
+    L.mhe_workspace_bytes.restype = ctypes.c_size_t
+    L.mhe_factor.argtypes = [c_void_p, P(mhe_matrices)]
+    L.mhe_factor.restype = c_int
+    L.mhe_solve.argtypes = [c_void_p, P(mhe_rhs), c_void_p, c_void_p, c_void_p, c_void_p]
+    L.mhe_solve.restype = c_int
+    L.mhe_factor_solve.argtypes = [c_void_p, P(mhe_matrices), P(mhe_rhs), c_void_p, c_void_p,
+                                   c_void_p, c_void_p]
+    L.mhe_factor_solve.restype = c_int
+    L.mhe_destroy.argtypes = [c_void_p]
+    L.mhe_destroy.restype = c_int
+    L.mhe_assemble.argtypes = [c_int, c_int, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_void_p]
+    L.mhe_assemble.restype = c_int
+    L.mhe_shapes.argtypes = [P(c_int), P(c_int), c_int]
+    L.mhe_shapes.restype = c_int
+    L.mhe_last_error.argtypes = []
+    L.mhe_last_error.restype = ctypes.c_char_p
+    return L
+
+
+def lib():
+    """Load libmhe.so (raises if it is missing: build it with build.py)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_1510_03110_gb300/build.py")
+            _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+class MheError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib().mhe_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise MheError(rc, where)
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), \
+        "expected a contiguous float64 CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def shapes():
+    L = lib()
+    nx = (c_int * 64)()
+    nw = (c_int * 64)()
+    k = L.mhe_shapes(nx, nw, 64)
+    return [(nx[i], nw[i]) for i in range(k)]
+
+
+def make_dims(nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0, refine_tol=0.0,
+              max_refine=-1):
+    N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).reshape(-1))
+    d = mhe_dims(int(nx), int(nw), int(N.size), N.ctypes.data_as(ctypes.POINTER(c_int)), int(prec),
+                 int(leaf_len), int(branching), int(top_len), float(refine_tol), int(max_refine))
+    return d, N
+
+
+def mhe_create(dims, stream=None):
+    ctx = c_void_p()
+    _check(lib().mhe_create(ctypes.byref(dims), _stream(stream), ctypes.byref(ctx)), "mhe_create")
+    return ctx
+
+
+def mhe_workspace_bytes(dims):
+    return int(lib().mhe_workspace_bytes(ctypes.byref(dims)))
+
+
+def mhe_factor(ctx, A, B, Q, P0inv):
+    m = mhe_matrices(_ptr(A), _ptr(B), _ptr(Q), _ptr(P0inv))
+    return _check(lib().mhe_factor(ctx, ctypes.byref(m)), "mhe_factor")
+
+
+def mhe_solve(ctx, l, a, x0, x, w, lam, info=None):
+    r = mhe_rhs(_ptr(l), _ptr(a), _ptr(x0))
+    ip = ctypes.c_void_p(info.data_ptr()) if info is not None else None
+    return _check(lib().mhe_solve(ctx, ctypes.byref(r), _ptr(x), _ptr(w), _ptr(lam), ip), "mhe_solve")
+
+
+def mhe_factor_solve(ctx, A, B, Q, P0inv, l, a, x0, x, w, lam, info=None):
+    m = mhe_matrices(_ptr(A), _ptr(B), _ptr(Q), _ptr(P0inv))
+    r = mhe_rhs(_ptr(l), _ptr(a), _ptr(x0))
+    ip = ctypes.c_void_p(info.data_ptr()) if info is not None else None
+    return _check(lib().mhe_factor_solve(ctx, ctypes.byref(m), ctypes.byref(r), _ptr(x), _ptr(w),
+                                         _ptr(lam), ip), "mhe_factor_solve")
+
+
+def mhe_destroy(ctx):
+    return _check(lib().mhe_destroy(ctx), "mhe_destroy")
+
+
+def mhe_assemble(nx, nw, ny, C, R, yt, wt, Q, l, c=None, stream=None):
+    S = C.shape[0] if C is not None else 0
+    return _check(lib().mhe_assemble(int(nx), int(nw), int(ny), int(S), _ptr(C), _ptr(R), _ptr(yt),
+                                     _ptr(wt), _ptr(Q), _ptr(l), _ptr(c), _stream(stream)),
+                  "mhe_assemble")
+
+
+def info_array(t):
+    """Device/host byte tensor of mhe_info records -> numpy structured array."""
+    return t.cpu().numpy().view(INFO_DTYPE)
+
+
+class Solver:
+    """One context: dims fixed at construction, tensors passed per call.
+
+    Output sizes: x and lam (sum_b (N_b + 1), nx); w sum_b (nx + (N_b - 1) nw).
+    """
+
+    def __init__(self, nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0,
+                 refine_tol=0.0, max_refine=-1, stream=None):
+        import torch
+        self.nx, self.nw = int(nx), int(nw)
+        self.N = np.asarray(N, dtype=np.int64).reshape(-1)
+        self.batch = int(self.N.size)
+        self.dims, self._N32 = make_dims(nx, nw, self.N, prec, leaf_len, branching, top_len,
+                                         refine_tol, max_refine)
+        self.stream = stream
+        self.ctx = mhe_create(self.dims, stream)
+        self.X = int(np.sum(self.N + 1))
+        self.W = int(np.sum(self.nx + (self.N - 1) * self.nw))
+        self.S = int(np.sum(self.N - 1))
+        self.info = torch.zeros(self.batch * INFO_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+    def outputs(self):
+        import torch
+        x = torch.empty(self.X, self.nx, dtype=torch.float64, device="cuda")
+        w = torch.empty(max(1, self.W), dtype=torch.float64, device="cuda")
+        lam = torch.empty(self.X, self.nx, dtype=torch.float64, device="cuda")
+        return x, w, lam
+
+    def factor(self, A, B, Q, P0inv):
+        mhe_factor(self.ctx, A, B, Q, P0inv)
+
+    def solve(self, l, a, x0, out=None):
+        x, w, lam = out if out is not None else self.outputs()
+        mhe_solve(self.ctx, l, a, x0, x, w, lam, self.info)
+        return x, w, lam
+
+    def factor_solve(self, A, B, Q, P0inv, l, a, x0, out=None):
+        x, w, lam = out if out is not None else self.outputs()
+        mhe_factor_solve(self.ctx, A, B, Q, P0inv, l, a, x0, x, w, lam, self.info)
+        return x, w, lam
+
+    def infos(self):
+        return info_array(self.info)
+
+    def close(self):
+        if self.ctx is not None:
+            mhe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

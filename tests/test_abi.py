@@ -1,0 +1,63 @@
+"""CPU checks of the C-ABI library: it loads without a GPU, exports every
+symbol include/mhe.h declares, and its host-side planning answers."""
+import os
+import re
+
+import pytest
+
+from paper_1510_03110_gb300 import build, mhe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return mhe.lib()
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "mhe.h")).read()
+    return sorted(set(re.findall(r"\b(mhe_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_symbols_are_exported(L):
+    names = declared()
+    assert "mhe_create" in names and "mhe_solve" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_shapes_listed(L):
+    s = mhe.shapes()
+    for need in [(4, 2), (6, 3), (12, 6), (20, 10), (24, 12)]:
+        assert need in s
+
+
+def test_workspace_bytes_host_only(L):
+    d, _ = mhe.make_dims(20, 10, [131072], prec=mhe.MHE_FP64, leaf_len=16, branching=8, top_len=4)
+    b64 = mhe.mhe_workspace_bytes(d)
+    d32, _ = mhe.make_dims(20, 10, [131072], prec=mhe.MHE_FP32_IR, leaf_len=16, branching=8, top_len=4)
+    b32 = mhe.mhe_workspace_bytes(d32)
+    # stored factors per stage: P n^2, chol G m^2, K and L m n, k m  (FP64: 8 bytes)
+    per_stage = (400 + 100 + 200 + 200 + 10) * 8
+    assert b64 > 131072 * per_stage
+    assert b32 < b64
+    assert b64 < 4 * 131072 * per_stage
+
+
+def test_bad_dims_rejected_on_host(L):
+    d, _ = mhe.make_dims(5, 4, [10])        # shape not compiled
+    assert mhe.mhe_workspace_bytes(d) == 0
+    d, _ = mhe.make_dims(4, 2, [10], leaf_len=1)   # leaf_len * nw < nx
+    assert mhe.mhe_workspace_bytes(d) == 0
+    d, _ = mhe.make_dims(4, 2, [0])         # horizon must be >= 1
+    assert mhe.mhe_workspace_bytes(d) == 0
+
+
+def test_product_path_has_no_fallback(tmp_path, monkeypatch):
+    """Without libmhe.so the binding raises instead of computing anything."""
+    monkeypatch.setattr(mhe, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mhe, "_lib", None)
+    with pytest.raises(RuntimeError):
+        mhe.lib()
