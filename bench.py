@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""KKT solves/s and p99 latency of the parallel Riccati tree on one GB300,
+against the plain per-instance serial Riccati recursion on the same GPU, at a
+relative KKT residual <= 1e-8.
+
+Workloads (seeded, synthetic; shapes and distributions of the paper's MHE
+problems):
+  batch (default)  4096 MHE instances, nx ~ U{6, 12, 24}, nw = ny = nx / 2,
+                   UFTOC horizon N ~ U[32, 2048]; FP32 tree + refinement
+                   against the FP64 KKT residual.
+  long             one instance nx = 20, nw = ny = 10, N = 131072, FP64.
+A step is the whole hot path over the workload: per shape bucket the stage
+assembly (Section II) and the factor + solve + refinement of the tree.
+
+Arms: default = the CUDA library; --impl reference = the serial FP64 CPU
+oracle on a bounded sample of the same workload (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1510_03110_gb300 import synth  # noqa: E402
+
+METRIC = "KKT solves/s and p99 latency vs plain batched serial Riccati, same GPU, rel-res<=1e-8"
+RELRES_BAR = 1e-8
+
+
+def flops_leaf_stage(n, m):
+    """Algorithm 4 per stage (matrix and vector part), the count used for the roofline."""
+    return 6 * n ** 3 + 12 * n ** 2 * m + 6 * n * m ** 2 + m ** 3 / 3.0
+
+
+def flops_serial_stage(n, m):
+    """Algorithms 1-3 per stage."""
+    return 4 * n ** 3 + 6 * n ** 2 * m + 4 * n * m ** 2 + m ** 3 / 3.0
+
+
+# ---------------------------------------------------------------- workload
+
+def make_workload(name):
+    if name == "batch":
+        w = synth.batch_uneven(seed=3)
+        desc = dict(workload="batched uneven MHE instances", instances=4096, nx="U{6,12,24}",
+                    nw_ny="nx/2", N="U[32,2048] (UFTOC horizon)", precision="FP32 tree + FP64 refinement",
+                    seed=3, l2="inputs larger than L2 (tens of GB resident)")
+        buckets = []
+        for n, b in sorted(w["buckets"].items()):
+            buckets.append(dict(n=n, m=b["m"], q=b["q"], N=b["N"], pool=b["pool"], idx=b["idx"], x0=b["x0"]))
+        return desc, buckets, 1   # prec FP32_IR
+    if name == "long":
+        p = synth.mhe_instance(1, 20, 10, 10, 131072)
+        pool = {k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")}
+        desc = dict(workload="long-horizon single MHE instance", instances=1, nx=20, nw=10, ny=10,
+                    N=131072, precision="FP64", seed=1, l2="inputs larger than L2")
+        return desc, [dict(n=20, m=10, q=10, N=np.array([131072]), pool=pool,
+                           idx=np.arange(131071), x0=p["x0"][None, :])], 0
+    raise SystemExit(f"unknown workload {name}")
+
+
+def to_device(bk):
+    """Pool -> device, expanded to every stage by an index gather (column-major blocks)."""
+    import torch
+    dev = "cuda"
+    idx = torch.from_numpy(np.asarray(bk["idx"], dtype=np.int64)).to(dev)
+    out = {}
+    for k in ("A", "B", "C", "R"):
+        pool = torch.from_numpy(synth.colmajor(bk["pool"][k]).reshape(len(bk["pool"][k]), -1)).to(dev)
+        out[k] = pool.index_select(0, idx).contiguous()
+        del pool
+    for k in ("a", "yt", "wt"):
+        pool = torch.from_numpy(np.ascontiguousarray(bk["pool"][k])).to(dev)
+        out[k] = pool.index_select(0, idx).contiguous()
+        del pool
+    n, m = bk["n"], bk["m"]
+    S = int(len(bk["idx"]))
+    out["x0"] = torch.from_numpy(np.ascontiguousarray(bk["x0"]).reshape(-1)).to(dev)
+    out["P0inv"] = torch.eye(n, dtype=torch.float64, device=dev).reshape(1, -1).repeat(len(bk["N"]), 1).contiguous()
+    out["Q"] = torch.empty(S, (n + m) ** 2, dtype=torch.float64, device=dev)
+    out["l"] = torch.empty(S, n + m, dtype=torch.float64, device=dev)
+    out["S"] = S
+    return out
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(rows))
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def peaks():
+    p = {}
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(p.get("sm_max_mhz", 2070.0))
+    return dict(hbm_gbs=float(p.get("hbm_gbs", 6800.0)), sm_max_mhz=sm_max,
+                src="measured" if p else "fallback",
+                # ALU peaks from unit counts x clock: 152 SMs x 128 FP32 lanes x 2 flop x clock;
+                # FP64: the part's nominal 1.25 TFLOP/s
+                fp32_tflops=152 * 128 * 2 * sm_max * 1e6 / 1e12, fp64_tflops=1.25)
+
+
+def read_traffic():
+    """DRAM bytes per stage of the leaf reduction from the committed ncu summary (or None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                try:
+                    out[k.strip()] = float(v.split()[0])
+                except Exception:
+                    pass
+    return out
+
+
+def run_gpu(args):
+    import torch
+    from paper_1510_03110_gb300 import build, mhe
+    build.build()
+    torch.cuda.set_device(0)
+    desc, buckets, prec = make_workload(args.workload)
+    t0 = time.time()
+    for bk in buckets:
+        bk["dev"] = to_device(bk)
+    gen_s = time.time() - t0
+    refine_tol = 1e-10
+    solvers, serial = [], []
+    for bk in buckets:
+        s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=prec, refine_tol=refine_tol,
+                       max_refine=8 if prec == 1 else 2,
+                       leaf_len=16 if prec == 0 else 8, branching=8 if prec == 0 else 4, top_len=4)
+        s.out = s.outputs()
+        solvers.append(s)
+    stream = torch.cuda.current_stream()
+
+    def step(ss, timing=False):
+        for bk, s in zip(buckets, ss):
+            d = bk["dev"]
+            if d["S"] > 0:
+                mhe.mhe_assemble(bk["n"], bk["m"], bk["q"], d["C"], d["R"], d["yt"], d["wt"], d["Q"], d["l"])
+            s.factor_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], out=s.out)
+
+    for _ in range(args.warmup):
+        step(solvers)
+    torch.cuda.synchronize()
+    launches0 = sum(mhe.mhe_launch_count(s.ctx) for s in solvers) + mhe.mhe_assemble_count()
+    clocks = Clocks()
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_host = time.time()
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        step(solvers)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.time() - t_host
+    clk = clocks.stop()
+    launches = sum(mhe.mhe_launch_count(s.ctx) for s in solvers) + mhe.mhe_assemble_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    instances = int(sum(len(bk["N"]) for bk in buckets))
+    infos = np.concatenate([s.infos() for s in solvers])
+    relres_max = float(np.max(infos["relres"]))
+    ok = bool(np.all(infos["status"] == 0) and relres_max <= RELRES_BAR)
+
+    # per-pass timing of one more step: the dominant kernel and its roofline
+    for s in solvers:
+        mhe.mhe_timing_enable(s.ctx, True)
+    step(solvers)
+    passes = []
+    for bk, s in zip(buckets, solvers):
+        for (ph, lvl, calls, tms) in mhe.mhe_timing_read(s.ctx):
+            passes.append(dict(nx=bk["n"], phase=ph, level=lvl, calls=calls, ms=tms))
+        mhe.mhe_timing_enable(s.ctx, False)
+    dom = max(passes, key=lambda r: r["ms"])
+    pk = peaks()
+    dbk = [bk for bk in buckets if bk["n"] == dom["nx"]][0]
+    n, m = dbk["n"], dbk["m"]
+    roofline = None
+    if dom["phase"] == "reduce" and dom["level"] == 0:
+        stages = int(np.sum(dbk["N"]))
+        fl = stages * flops_leaf_stage(n, m) - len(dbk["N"]) * (flops_leaf_stage(n, m) - flops_leaf_stage(n, n))
+        achieved = fl / (dom["ms"] / dom["calls"] * 1e-3) / 1e12
+        peak = pk["fp32_tflops"] if prec == 1 else pk["fp64_tflops"]
+        tr = read_traffic().get(f"reduce_leaf_nx{n}_{'fp32' if prec == 1 else 'fp64'}_bytes_per_stage")
+        roofline = dict(bound="alu", kernel=f"k_level<{'float' if prec == 1 else 'double'},{n},{m},0,REDUCE>",
+                        achieved=round(achieved, 3), peak=round(peak, 2), unit="TFLOP/s",
+                        frac=round(achieved / peak, 4),
+                        traffic=(tr * stages if tr else None),
+                        peak_src=("FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % pk["sm_max_mhz"]) if prec == 1
+                        else "FP64: nominal 1.25 TFLOP/s of the part",
+                        flops_per_launch=fl, ms_per_launch=dom["ms"] / dom["calls"])
+
+    # plain serial Riccati on the same GPU: one chunk per instance (top_len >= N)
+    base = {}
+    for name, bprec, mref in [("serial_same_precision", prec, 8 if prec == 1 else 0)] + \
+            ([("serial_fp64", 0, 0)] if (prec == 1 and args.serial_fp64) else []):
+        ss = []
+        for bk in buckets:
+            s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
+                           top_len=int(np.max(bk["N"])) + 1)
+            s.out = s.outputs()
+            ss.append(s)
+        step(ss)
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, args.baseline_steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step(ss)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / k
+        binf = np.concatenate([s.infos() for s in ss])
+        base[name] = dict(value=round(instances / (bms * 1e-3), 3), ms_per_step=round(bms, 3),
+                          relres_max=float(np.max(binf["relres"])), steps=k)
+        for s in ss:
+            s.close()
+
+    # end to end: inputs from pinned host memory every step, the solution back to the host
+    e2e = None
+    if args.e2e:
+        e2e = run_e2e(args, buckets, solvers, step, stream, instances)
+
+    cpu = cpu_baseline(buckets, args) if not args.no_cpu else None
+    value = instances / (ms * 1e-3)
+    step_sorted = sorted(step_ms)
+    p99 = step_sorted[min(len(step_sorted) - 1, int(np.ceil(0.99 * len(step_sorted))) - 1)]
+    line = dict(metric=METRIC, value=round(value, 3), unit="KKT solves/s", n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=round(ms, 4), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32+f64" if prec == 1 else "f64", data="synthetic",
+                config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, generation_s=round(gen_s, 1)),
+                latency_ms=dict(p50=round(statistics.median(step_ms), 4), p99=round(p99, 4),
+                                note="one step solves every instance; latency = step time"),
+                relres_max=relres_max, all_ok=ok,
+                refine_iters_max=int(np.max(infos["refine_iters"])),
+                serial_gpu=base,
+                speedup_vs_serial={k: round(value / v["value"], 2) for k, v in base.items()},
+                roofline=roofline, passes=sorted(passes, key=lambda r: -r["ms"])[:8],
+                cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clk,
+                wall_s=round(wall, 3))
+    print(json.dumps(line))
+    for s in solvers:
+        s.close()
+
+
+def run_e2e(args, buckets, solvers, step, stream, instances):
+    import torch
+    from paper_1510_03110_gb300 import mhe
+    host = []
+    h2d = d2h = 0
+    for bk in buckets:
+        d = bk["dev"]
+        hb = {}
+        for k in ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv"):
+            t = torch.empty(d[k].shape, dtype=d[k].dtype, pin_memory=True)
+            t.copy_(d[k])
+            hb[k] = t
+            h2d += t.numel() * t.element_size()
+        host.append(hb)
+    outs = []
+    for s in solvers:
+        x, w, lam = s.out
+        hx = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (x, w, lam)]
+        outs.append(hx)
+        d2h += sum(t.numel() * t.element_size() for t in hx) + s.info.numel()
+    k = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        for bk, hb in zip(buckets, host):
+            for key, t in hb.items():
+                bk["dev"][key].copy_(t, non_blocking=True)
+        step(solvers)
+        for s, hx in zip(solvers, outs):
+            for dst, src in zip(hx, s.out):
+                dst.copy_(src, non_blocking=True)
+            s.infos()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    del mhe
+    return dict(value=round(instances / (ms * 1e-3), 3), unit="KKT solves/s", h2d_bytes_per_step=int(h2d),
+                d2h_bytes_per_step=int(d2h), ms_per_step=round(ms, 3), steps=k)
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def _sample(buckets, count):
+    """A bounded, seeded sample of instances across the buckets (MHE-form dicts)."""
+    rng = np.random.default_rng(11)
+    out = []
+    per = max(1, count // len(buckets))
+    for bk in buckets:
+        offs = np.concatenate([[0], np.cumsum(bk["N"] - 1)])
+        for j in rng.choice(len(bk["N"]), size=min(per, len(bk["N"])), replace=False):
+            idx = bk["idx"][offs[j]:offs[j + 1]]
+            out.append(synth.instance_from_pool(bk["pool"], idx, bk["x0"][j], bk["n"], bk["m"], bk["q"]))
+    return out
+
+
+def _oracle_solve(p):
+    import oracle
+    r = oracle.riccati(oracle.mhe_to_uftoc(p))
+    return r["status"]
+
+
+def cpu_baseline(buckets, args, seconds=15.0):
+    """The FP64 oracle (serial Riccati, plain C) on host cores, on a bounded sample."""
+    import concurrent.futures as cf
+    cores = os.cpu_count() or 1
+    sample = _sample(buckets, max(cores, 6) if len(buckets) > 1 else 1)
+    cores = min(cores, len(sample))
+    t0 = time.time()
+    done = 0
+    with cf.ThreadPoolExecutor(cores) as ex:
+        while time.time() - t0 < seconds and done < 4 * len(sample):
+            list(ex.map(_oracle_solve, sample))
+            done += len(sample)
+            if len(buckets) == 1:
+                break
+    dt = time.time() - t0
+    stages = sum(p["N"] for p in sample) * (done // len(sample))
+    return dict(value=round(done / dt, 4), unit="KKT solves/s", cores=cores, kind="oracle",
+                sample=f"{len(sample)} instances of the workload ({stages} stages solved), {done} solves "
+                       f"in {dt:.1f} s on a thread pool (ctypes releases the GIL)")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    desc, buckets, prec = make_workload(args.workload)
+    import concurrent.futures as cf
+    cores = os.cpu_count() or 1
+    sample = _sample(buckets, max(cores, 6) if len(buckets) > 1 else 1)
+    cores = min(cores, len(sample))
+    with cf.ThreadPoolExecutor(cores) as ex:
+        for _ in range(args.warmup if len(buckets) > 1 else 0):
+            list(ex.map(_oracle_solve, sample))
+        times = []
+        for _ in range(args.steps):
+            t0 = time.time()
+            list(ex.map(_oracle_solve, sample))
+            times.append(time.time() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = len(sample) / (ms * 1e-3)
+    cpu = dict(kind="oracle", cores=cores, value=round(value, 4),
+               sample=f"{len(sample)} instances of the workload per step, serial FP64 Riccati in plain C")
+    print(json.dumps(dict(metric=METRIC, impl="reference", value=round(value, 4), unit="KKT solves/s",
+                          n_gpus=int(os.environ.get("WORLD_SIZE", "1")), steps=args.steps, warmup=args.warmup,
+                          ms_per_step=round(ms, 3), higher_is_better=True, scaling="weak", vs_baseline=None,
+                          dtype="f64", data="synthetic", config=desc, cpu_baseline=cpu,
+                          e2e=dict(value=round(value, 4), unit="KKT solves/s", h2d_bytes_per_step=0,
+                                   d2h_bytes_per_step=0))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "long"])
+    ap.add_argument("--baseline-steps", type=int, default=2)
+    ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.gpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # replicas only: every rank solves its own copy of the workload
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

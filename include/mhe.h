@@ -145,6 +145,27 @@ int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const dou
  * nx_out / nw_out and returns the number available. */
 int mhe_shapes(int* nx_out, int* nw_out, int cap);
 
+/* Profiling aid: enable = 1 records a pair of CUDA events around every level
+ * pass (reduce, right-hand side, down, residual) on the context's stream;
+ * enable = 0 stops recording.  No counterpart in the paper, whose Matlab
+ * experiment timed each tree level the same way (Section VI). */
+int mhe_timing_enable(mhe_ctx* ctx, int enable);
+
+/* Synchronises the stream and writes, per (phase, level), 4 doubles
+ * {phase (0 reduce, 1 rhs, 2 down, 3 residual), level, passes, total ms}
+ * accumulated since the last read; returns the number of records (which may
+ * exceed cap; only cap are written). */
+int mhe_timing_read(mhe_ctx* ctx, double* out, int cap);
+
+/* The planned tree: per level 3 long longs {level, chunks, stages}; returns
+ * the number of levels (Algorithm 5's m + 1). */
+int mhe_plan_info(mhe_ctx* ctx, long long* out, int cap);
+
+/* Kernels launched so far by this context (all passes, residuals included),
+ * and by mhe_assemble in this process. */
+long long mhe_launch_count(mhe_ctx* ctx);
+long long mhe_assemble_count(void);
+
 /* Text of the last error reported on this thread. */
 const char* mhe_last_error(void);
 

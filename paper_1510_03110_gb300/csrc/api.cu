@@ -19,13 +19,39 @@ int shapes_big(ShapeEntry* out, int cap);
 int shapes_sq(ShapeEntry* out, int cap);
 }  // namespace mhe
 
+// CUDA events around each level pass, recorded on the context's stream.
+struct PassTiming {
+    struct Rec {
+        int phase, level;
+        cudaEvent_t b, e;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    cudaEvent_t get()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            pool.push_back(ev);
+        }
+        return pool[used++];
+    }
+    ~PassTiming()
+    {
+        for (auto ev : pool) cudaEventDestroy(ev);
+    }
+};
+
 struct mhe_ctx {
     mhe::Engine eng;
+    PassTiming timing;
 };
 
 namespace {
 
 thread_local std::string g_err;
+long long g_assemble_launches = 0;
 
 int fail(int code, const std::string& msg)
 {
@@ -117,7 +143,23 @@ void rt_finalize(int batch, const double* norms, int* active, int* iters, const 
                                                                  mode, refine, info);
 }
 
-const mhe::Runtime kRuntime = {rt_alloc, rt_release, rt_memset0, rt_copy, rt_finalize, rt_sync, rt_error};
+void rt_mark(void* user, int phase, int level, int begin, void* s)
+{
+    PassTiming* t = static_cast<PassTiming*>(user);
+    if (begin) {
+        PassTiming::Rec r;
+        r.phase = phase;
+        r.level = level;
+        r.b = t->get();
+        r.e = t->get();
+        cudaEventRecord(r.b, (cudaStream_t)s);
+        t->recs.push_back(r);
+    } else if (!t->recs.empty()) {
+        cudaEventRecord(t->recs.back().e, (cudaStream_t)s);
+    }
+}
+
+const mhe::Runtime kRuntime = {rt_alloc, rt_release, rt_memset0, rt_copy, rt_finalize, rt_sync, rt_error, rt_mark};
 
 int check_dims(const mhe_dims* d)
 {
@@ -211,6 +253,7 @@ int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const dou
     if (S < 0) return fail(MHE_E_ARG, "S < 0");
     if (S > 0 && (!C || !R || !yt || !wt || !Q || !l)) return fail(MHE_E_ARG, "NULL input or output");
     e->assemble(S, C, R, yt, wt, Q, l, c, stream);
+    g_assemble_launches += S > 0;
     if (cudaGetLastError() != cudaSuccess) return fail(MHE_E_CUDA, "launch of the assembly kernel failed");
     return MHE_OK;
 }
@@ -224,6 +267,66 @@ int mhe_shapes(int* nx_out, int* nw_out, int cap)
     }
     return (int)r.size();
 }
+
+int mhe_timing_enable(mhe_ctx* ctx, int enable)
+{
+    if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
+    ctx->eng.mark_user = enable ? &ctx->timing : nullptr;
+    return MHE_OK;
+}
+
+int mhe_timing_read(mhe_ctx* ctx, double* out, int cap)
+{
+    if (!ctx || (!out && cap > 0)) return fail(MHE_E_ARG, "ctx or out is NULL");
+    if (cudaStreamSynchronize((cudaStream_t)ctx->eng.stream) != cudaSuccess)
+        return fail(MHE_E_CUDA, "stream synchronisation failed");
+    struct Agg {
+        int phase, level, calls;
+        double ms;
+    };
+    std::vector<Agg> agg;
+    for (auto& r : ctx->timing.recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.b, r.e);
+        bool found = false;
+        for (auto& g : agg)
+            if (g.phase == r.phase && g.level == r.level) { g.calls++; g.ms += ms; found = true; break; }
+        if (!found) agg.push_back(Agg{r.phase, r.level, 1, (double)ms});
+    }
+    ctx->timing.recs.clear();
+    ctx->timing.used = 0;
+    int k = 0;
+    for (auto& g : agg) {
+        if (k < cap) {
+            out[4 * k + 0] = g.phase;
+            out[4 * k + 1] = g.level;
+            out[4 * k + 2] = g.calls;
+            out[4 * k + 3] = g.ms;
+        }
+        ++k;
+    }
+    return k;
+}
+
+long long mhe_launch_count(mhe_ctx* ctx) { return ctx ? ctx->eng.launches : -1; }
+
+int mhe_plan_info(mhe_ctx* ctx, long long* out, int cap)
+{
+    if (!ctx || (!out && cap > 0)) return fail(MHE_E_ARG, "ctx or out is NULL");
+    const mhe::Plan& p = ctx->eng.plan;
+    int k = 0;
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+        if (k < cap) {
+            out[3 * k + 0] = (long long)l;
+            out[3 * k + 1] = (long long)p.levels[l].chunks.size();
+            out[3 * k + 2] = p.levels[l].nstages;
+        }
+        ++k;
+    }
+    return k;
+}
+
+long long mhe_assemble_count(void) { return g_assemble_launches; }
 
 const char* mhe_last_error(void) { return g_err.c_str(); }
 

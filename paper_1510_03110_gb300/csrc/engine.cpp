@@ -122,6 +122,11 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     return MHE_OK;
 }
 
+void Engine::mark(int phase, int level, int begin)
+{
+    if (mark_user && rt->mark) rt->mark(mark_user, phase, level, begin, stream);
+}
+
 void Engine::release()
 {
     if (arena) rt->release(arena);
@@ -200,7 +205,10 @@ void Engine::pass_reduce(const double* l, const double* a)
         g.l = l;
         g.a = a;
         if (k >= 1 && !l) { g.lxh = nullptr; g.ah = nullptr; g.lNk = nullptr; }
+        mark(PH_REDUCE, k, 1);
+        launches += g.nchunks > 0;
         launch<T>(ops->reduce64, ops->reduce32, g, k >= 1, stream);
+        mark(PH_REDUCE, k, 0);
     }
 }
 
@@ -212,7 +220,10 @@ void Engine::pass_rhs(const double* l, const double* a, const double* l0, const 
         LevelArgs<T> g = args<T>(k);
         g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
         g.active = active_mask;
+        mark(PH_RHS, k, 1);
+        launches += g.nchunks > 0;
         launch<T>(ops->rhs64, ops->rhs32, g, k >= 1, stream);
+        mark(PH_RHS, k, 0);
     }
 }
 
@@ -232,7 +243,10 @@ void Engine::pass_down(const double* l, const double* a, const double* l0, const
             g.xd = x; g.wd = w; g.ld = lam;
             g.zx = zx; g.zw = zw; g.zl = zl;
         }
+        mark(PH_DOWN, k, 1);
+        launches += g.nchunks > 0;
         launch<T>(ops->down64, ops->down32, g, k >= 1, stream);
+        mark(PH_DOWN, k, 0);
     }
 }
 
@@ -253,7 +267,10 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
     r.norms = norms;
     r.active = act;
     rt->memset0(norms, sizeof(double) * 4 * plan.batch, stream);
+    mark(PH_RESID, 0, 1);
+    launches += r.nstages > 0;
     ops->resid(r, stream);
+    mark(PH_RESID, 0, 0);
 }
 
 template <typename T>
@@ -268,6 +285,7 @@ int Engine::run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe
         residual(rhs, x, w, lam, it == 0 ? nullptr : active);
         rt->finalize(plan.batch, norms, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
                      stream);
+        ++launches;
         // correction problem K dz = r in UFTOC form, then z += dz
         active_mask = active;
         pass_rhs<T>(rl, ra, rl0, ra0, rlN);
@@ -277,6 +295,7 @@ int Engine::run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe
     residual(rhs, x, w, lam, nullptr);
     rt->finalize(plan.batch, norms, active, iters, status, where, tol, 2, max_refine > 0 ? 1 : 0, info_dev,
                  stream);
+    ++launches;
     if (info) rt->copy(info, info_dev, sizeof(mhe_info) * plan.batch, stream);
     if (rt->error() != 0) { err = "CUDA error during the solve"; return MHE_E_CUDA; }
     return MHE_OK;

@@ -39,7 +39,11 @@ struct Runtime {
                      void* stream);
     int (*sync)(void* stream);
     int (*error)();   // sticky error of the launches so far (0 = none)
+    // optional per-pass timing marks (begin = 1 before a launch, 0 after)
+    void (*mark)(void* user, int phase, int level, int begin, void* stream);
 };
+
+enum { PH_REDUCE = 0, PH_RHS = 1, PH_DOWN = 2, PH_RESID = 3, PH_COUNT = 4 };
 
 struct LevelBuf {
     ChunkDesc* chunks = nullptr;
@@ -74,6 +78,8 @@ public:
 
     const double *A = nullptr, *B = nullptr, *Q = nullptr, *P0inv = nullptr;
     const int* active_mask = nullptr;   // instances still refining (nullptr: all)
+    void* mark_user = nullptr;          // non-null: record per-pass timing marks
+    long long launches = 0;             // kernels launched by this context so far
     bool factored = false;
     std::string err;
 
@@ -83,6 +89,7 @@ public:
     void release();
     int factor(const mhe_matrices& m, const mhe_rhs* rhs, double* x, double* w, double* lam);
     int solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool after_fused);
+    void mark(int phase, int level, int begin);
 
 private:
     template <typename T>

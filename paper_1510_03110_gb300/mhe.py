@@ -74,6 +74,16 @@ def _declare(L):
     L.mhe_assemble.restype = c_int
     L.mhe_shapes.argtypes = [P(c_int), P(c_int), c_int]
     L.mhe_shapes.restype = c_int
+    L.mhe_timing_enable.argtypes = [c_void_p, c_int]
+    L.mhe_timing_enable.restype = c_int
+    L.mhe_timing_read.argtypes = [c_void_p, ctypes.POINTER(c_double), c_int]
+    L.mhe_timing_read.restype = c_int
+    L.mhe_plan_info.argtypes = [c_void_p, ctypes.POINTER(c_ll), c_int]
+    L.mhe_plan_info.restype = c_int
+    L.mhe_launch_count.argtypes = [c_void_p]
+    L.mhe_launch_count.restype = c_ll
+    L.mhe_assemble_count.argtypes = []
+    L.mhe_assemble_count.restype = c_ll
     L.mhe_last_error.argtypes = []
     L.mhe_last_error.restype = ctypes.c_char_p
     return L
@@ -165,6 +175,38 @@ def mhe_factor_solve(ctx, A, B, Q, P0inv, l, a, x0, x, w, lam, info=None):
 
 def mhe_destroy(ctx):
     return _check(lib().mhe_destroy(ctx), "mhe_destroy")
+
+
+PHASES = {0: "reduce", 1: "rhs", 2: "down", 3: "resid"}
+
+
+def mhe_timing_enable(ctx, enable=True):
+    return _check(lib().mhe_timing_enable(ctx, int(bool(enable))), "mhe_timing_enable")
+
+
+def mhe_timing_read(ctx):
+    """[(phase name, level, passes, total ms)] since the last read (synchronises)."""
+    buf = (c_double * 4096)()
+    k = lib().mhe_timing_read(ctx, buf, 1024)
+    if k < 0:
+        raise MheError(k, "mhe_timing_read")
+    return [(PHASES[int(buf[4 * i])], int(buf[4 * i + 1]), int(buf[4 * i + 2]), float(buf[4 * i + 3]))
+            for i in range(min(k, 1024))]
+
+
+def mhe_launch_count(ctx):
+    return int(lib().mhe_launch_count(ctx))
+
+
+def mhe_assemble_count():
+    return int(lib().mhe_assemble_count())
+
+
+def mhe_plan_info(ctx):
+    """[(level, chunks, stages)] of the planned tree."""
+    buf = (c_ll * 3 * 256)()
+    k = lib().mhe_plan_info(ctx, buf, 256)
+    return [(int(buf[3 * i]), int(buf[3 * i + 1]), int(buf[3 * i + 2])) for i in range(min(k, 256))]
 
 
 def mhe_assemble(nx, nw, ny, C, R, yt, wt, Q, l, c=None, stream=None):
