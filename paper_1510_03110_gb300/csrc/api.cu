@@ -173,6 +173,10 @@ int check_dims(const mhe_dims* d)
 
 }  // namespace
 
+namespace mhe {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace mhe
+
 extern "C" {
 
 int mhe_create(const mhe_dims* dims, void* stream, mhe_ctx** out)

@@ -84,6 +84,8 @@ def _declare(L):
     L.mhe_launch_count.restype = c_ll
     L.mhe_assemble_count.argtypes = []
     L.mhe_assemble_count.restype = c_ll
+    L.mhe_solve_serial_noalloc.argtypes = [c_int, c_int, c_int] + [c_void_p] * 12
+    L.mhe_solve_serial_noalloc.restype = c_int
     L.mhe_last_error.argtypes = []
     L.mhe_last_error.restype = ctypes.c_char_p
     return L
@@ -192,6 +194,16 @@ def mhe_timing_read(ctx):
         raise MheError(k, "mhe_timing_read")
     return [(PHASES[int(buf[4 * i])], int(buf[4 * i + 1]), int(buf[4 * i + 2]), float(buf[4 * i + 3]))
             for i in range(min(k, 1024))]
+
+
+def mhe_solve_serial_noalloc(nx, nw, N, A, B, Q, P0inv, l, a, x0, x, w, lam, status=None,
+                             stream=None):
+    """One instance, serial plan, FP64, no device allocation (fixed library scratch)."""
+    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    return _check(lib().mhe_solve_serial_noalloc(int(nx), int(nw), int(N), _ptr(A), _ptr(B), _ptr(Q),
+                                                 _ptr(P0inv), _ptr(l), _ptr(a), _ptr(x0), _ptr(x), _ptr(w),
+                                                 _ptr(lam), sp, _stream(stream)),
+                  "mhe_solve_serial_noalloc")
 
 
 def mhe_launch_count(ctx):
