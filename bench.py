@@ -59,6 +59,14 @@ def make_workload(name):
         for n, b in sorted(w["buckets"].items()):
             buckets.append(dict(n=n, m=b["m"], q=b["q"], N=b["N"], pool=b["pool"], idx=b["idx"], x0=b["x0"]))
         return desc, buckets, 1   # prec FP32_IR
+    if name == "profile":
+        # a small case of the same kernels for ncu captures: 192 instances of nx = 24
+        w = synth.batch_uneven(seed=5, count=192, nx_choices=(24,))
+        desc = dict(workload="profile case: 192 batched uneven MHE instances", instances=192, nx=24,
+                    nw_ny=12, N="U[32,2048] (UFTOC horizon)", precision="FP32 tree + FP64 refinement",
+                    seed=5, l2="inputs larger than L2 (a few GB)")
+        b = w["buckets"][24]
+        return desc, [dict(n=24, m=12, q=12, N=b["N"], pool=b["pool"], idx=b["idx"], x0=b["x0"])], 1
     if name == "long":
         p = synth.mhe_instance(1, 20, 10, 10, 131072)
         pool = {k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")}
@@ -211,11 +219,13 @@ def run_gpu(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     t_host = time.time()
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         evs[i][0].record(stream)
         step(solvers)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall = time.time() - t_host
     clk = clocks.stop()
     launches = sum(mhe.mhe_launch_count(s.ctx) for s in solvers) + mhe.mhe_assemble_count() - launches0
@@ -256,8 +266,9 @@ def run_gpu(args):
 
     # plain serial Riccati on the same GPU: one chunk per instance (top_len >= N)
     base = {}
-    for name, bprec, mref in [("serial_same_precision", prec, 8 if prec == 1 else 0)] + \
-            ([("serial_fp64", 0, 0)] if (prec == 1 and args.serial_fp64) else []):
+    arms = [] if args.no_baseline else [("serial_same_precision", prec, 8 if prec == 1 else 0)] + \
+        ([("serial_fp64", 0, 0)] if (prec == 1 and args.serial_fp64) else [])
+    for name, bprec, mref in arms:
         ss = []
         for bk in buckets:
             s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
@@ -430,7 +441,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "long"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile"])
+    ap.add_argument("--no-baseline", action="store_true", help="skip the serial-plan GPU baseline")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
