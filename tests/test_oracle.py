@@ -326,6 +326,16 @@ def test_backsubstitution_equals_literal_alg6():
         assert rel(b["P"][t] @ b["x"][t] - b["Psi"][t], b["lam"][t]) < 1e-9
 
 
+def test_long_horizon_stays_accurate():
+    """Section III: P_t is symmetric positive semidefinite; with it kept symmetric the
+    recursion stays backward stable over long horizons (nx=20, N=600)."""
+    p = synth.mhe_instance(105, 20, 10, 10, 600)
+    u = oracle.mhe_to_uftoc(p)
+    r = oracle.riccati(u)
+    assert r["status"] == 0
+    assert oracle.relres(u, r["x"], r["w"], r["lam"]) <= 1e-13
+
+
 def test_non_pd_stage_reports_status():
     p = random_uftoc(5, 2, 4, [2], terminal=False)
     p.Q[2] = -np.eye(4)

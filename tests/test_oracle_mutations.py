@@ -36,6 +36,9 @@ MUTATIONS = {
     "sign_Qxw_assembly": ("AT(Q, i, n + j, nq) = -AT(SC, j, i, m);", "AT(Q, i, n + j, nq) = AT(SC, j, i, m);"),
     # Section II: l_w = S y~ + W w~
     "sign_lw_assembly": ("l[n + i] = t1[i] - t2[i];", "l[n + i] = t1[i] + t2[i];"),
+    # Alg 1: P_t = F - K^T G K stored as computed, not its symmetric part
+    "drop_symmetrisation_of_P": ("0.5 * ((AT(F, i, j, n) - AT(KGK, i, j, n)) +\n                                         (AT(F, j, i, n) - AT(KGK, j, i, n)));",
+                                 "(AT(F, i, j, n) - AT(KGK, i, j, n));"),
     # residual: the -lambda_t term of the x-stationarity row is dropped
     "drop_lambda_in_residual": ("if (i < n) { s -= ltt[i]; rs += 1.0; }", "if (i < n) { rs += 1.0; }"),
 }
@@ -97,6 +100,10 @@ def _pins_fail(lib_mut) -> list:
         wu = np.concatenate([xm0 - q["x0"]] + wm)
         if abs(oracle.objective(u, xu, wu) - _mhe_cost(q, xm, wm)) > 1e-10 * abs(_mhe_cost(q, xm, wm)):
             failed.append("mhe_cost")
+        lp = oracle.mhe_to_uftoc(synth.mhe_instance(105, 20, 10, 10, 600))
+        lr = oracle.riccati(lp)
+        if lr["status"] != 0 or oracle.relres(lp, lr["x"], lr["w"], lr["lam"]) > 1e-13:
+            failed.append("long_horizon")
     finally:
         core._lib = saved
     return failed
