@@ -193,7 +193,7 @@ def run_gpu(args):
     for bk in buckets:
         bk["dev"] = to_device(bk)
     gen_s = time.time() - t0
-    refine_tol = 1e-10
+    refine_tol = 1e-9
     solvers, serial = [], []
     for bk in buckets:
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=prec, refine_tol=refine_tol,

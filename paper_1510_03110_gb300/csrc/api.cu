@@ -106,12 +106,16 @@ int rt_sync(void* s) { return cudaStreamSynchronize((cudaStream_t)s) == cudaSucc
 int rt_error() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
 
 // relres = ||r|| / (||K|| ||z|| + ||b||) per instance
-__global__ void k_finalize(int batch, const double* norms, int* active, int* iters, const int* status,
-                           const int* where, double tol, int mode, int refine, mhe_info* info)
+__global__ void k_finalize(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
+                           int* iters, const int* status, const int* where, double tol, int mode, int refine,
+                           mhe_info* info)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
-    const double r = norms[4 * b + 0], K = norms[4 * b + 1], z = norms[4 * b + 2], bb = norms[4 * b + 3];
+    const double r = __longlong_as_double((long long)norms[3 * b + 0]);
+    const double z = __longlong_as_double((long long)norms[3 * b + 1]);
+    const double bb = __longlong_as_double((long long)norms[3 * b + 2]);
+    const double K = (double)__uint_as_float(kinf[b]);
     const double den = K * z + bb;
     const double relres = den > 0 ? r / den : r;
     if (mode < 2) {
@@ -136,11 +140,27 @@ __global__ void k_finalize(int batch, const double* norms, int* active, int* ite
     info[b] = o;
 }
 
-void rt_finalize(int batch, const double* norms, int* active, int* iters, const int* status, const int* where,
-                 double tol, int mode, int refine, mhe_info* info, void* s)
+void rt_finalize(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active, int* iters,
+                 const int* status, const int* where, double tol, int mode, int refine, mhe_info* info, void* s)
 {
-    k_finalize<<<(batch + 127) / 128, 128, 0, (cudaStream_t)s>>>(batch, norms, active, iters, status, where, tol,
-                                                                 mode, refine, info);
+    k_finalize<<<(batch + 127) / 128, 128, 0, (cudaStream_t)s>>>(batch, norms, kinf, active, iters, status, where,
+                                                                 tol, mode, refine, info);
+}
+
+// FP64 -> FP32 copy (round to nearest)
+__global__ void k_convert(float* dst, const double* src, long long count)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        dst[i] = __double2float_rn(src[i]);
+}
+
+void rt_convert(float* dst, const double* src, long long count, void* s)
+{
+    if (count <= 0) return;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_convert<<<(unsigned)blocks, 256, 0, (cudaStream_t)s>>>(dst, src, count);
 }
 
 void rt_mark(void* user, int phase, int level, int begin, void* s)
@@ -159,7 +179,8 @@ void rt_mark(void* user, int phase, int level, int begin, void* s)
     }
 }
 
-const mhe::Runtime kRuntime = {rt_alloc, rt_release, rt_memset0, rt_copy, rt_finalize, rt_sync, rt_error, rt_mark};
+const mhe::Runtime kRuntime = {rt_alloc, rt_release, rt_memset0, rt_copy, rt_finalize, rt_convert, rt_sync,
+                               rt_error, rt_mark};
 
 int check_dims(const mhe_dims* d)
 {

@@ -31,8 +31,9 @@ struct LevelInst {
 };
 
 // Everything a tree kernel of one level reads and writes.  Matrices are
-// column-major.  Level-0 problem data are the caller's FP64 arrays; higher
-// levels read the FP64 master-problem arrays written by the level below.
+// column-major.  All problem data are of the compute type T: in FP64 mode the
+// caller's arrays, in FP32 mode the library's FP32 copies of them.  Higher
+// levels read the master-problem arrays written by the level below.
 template <typename T>
 struct LevelArgs {
     int level;
@@ -41,17 +42,17 @@ struct LevelArgs {
     const LevelInst* li;           // this level, indexed by instance
 
     // level-0 problem (stages t >= 1 of instance b at caller stage in_off[b] + t - 1)
-    const double *A, *B, *Q, *P0inv;
+    const T *A, *B, *Q, *P0inv;
     const long long* in_off;
     const long long* w_off;        // caller w offset of instance b (w_0 has n entries)
     // right-hand side of level 0 (l0, a0, lN per instance; nullptr means zero)
-    const double *l, *a, *x0, *l0, *a0, *lN;
+    const T *l, *a, *x0, *l0, *a0, *lN;
 
-    // master-problem stage data of this level (k >= 1), FP64
-    const double *Ah, *Bh, *ah, *Qxh, *lxh;
-    const double *QNk, *lNk;       // terminal cost of this level's problem, per instance
+    // master-problem stage data of this level (k >= 1)
+    const T *Ah, *Bh, *ah, *Qxh, *lxh;
+    const T *QNk, *lNk;            // terminal cost of this level's problem, per instance
     // outputs for level k+1
-    double *Ah_up, *Bh_up, *ah_up, *Qxh_up, *lxh_up, *QN_up, *lN_up;
+    T *Ah_up, *Bh_up, *ah_up, *Qxh_up, *lxh_up, *QN_up, *lN_up;
 
     // stored factors of this level (per stage, natural leading dimensions)
     T *Pst, *Lgst, *Kst, *kst, *Lst;
@@ -59,9 +60,9 @@ struct LevelArgs {
     T *Pst0, *Lgst0, *Kst0, *kst0, *Lst0;
 
     // down pass
-    const double *xd_up, *wd_up, *ld_up;   // solution of the level above
-    double *xd, *wd, *ld;                  // this level's solution
-    double *zx, *zw, *zl;                  // level 0: accumulate targets (nullptr: none)
+    const T *xd_up, *wd_up, *ld_up;        // solution of the level above
+    T *xd, *wd, *ld;                       // this level's solution
+    double *zx, *zw, *zl;                  // level 0: FP64 accumulate targets (nullptr: none)
 
     const int* active;     // per instance; nullptr = all active
     int* status;           // per instance error code
@@ -70,7 +71,10 @@ struct LevelArgs {
     int store_P;           // keep P_{t+1} per stage (needed by right-hand-side-only passes)
 };
 
-// Residual / norm kernel arguments (level 0, FP64).
+// Residual kernel arguments (level 0).  Reads the caller's FP64 problem and
+// the FP64 iterate; writes the correction right-hand side in the compute type
+// of the tree (TR = double or float).
+template <typename TR>
 struct ResidArgs {
     int batch;
     long long nstages;            // sum of N_b (arrival stages included)
@@ -78,11 +82,22 @@ struct ResidArgs {
     const long long* in_off;
     const long long* w_off;
     const double *A, *B, *Q, *P0inv;
-    const double *l, *a, *x0, *l0, *a0, *lN;
+    const double *l, *a, *x0;     // the problem's right-hand side (l_0 = a_0 = l_N = 0)
     const double *x, *w, *lam;    // current iterate (caller layout)
-    double *rl, *ra, *rl0, *ra0, *rlN, *rx0;   // correction right-hand side (UFTOC form)
-    double* norms;                // per instance [r_inf, K_inf, z_inf, b_inf]
+    TR *rl, *ra, *rl0, *ra0, *rlN, *rx0;   // correction right-hand side (UFTOC form)
+    unsigned long long* norms;    // per instance [r_inf, z_inf, b_inf] as bit patterns of |.|
     const int* active;
+};
+
+// ||K||_inf per instance (max absolute row sum of the KKT matrix), once per
+// factorisation; float accumulation of |entries| is ample for a norm.
+struct KnormArgs {
+    int batch;
+    long long nstages;
+    const long long* gs0;
+    const long long* in_off;
+    const double *A, *B, *Q, *P0inv;
+    unsigned int* kinf;           // per instance, bit pattern of a non-negative float
 };
 
 }  // namespace mhe

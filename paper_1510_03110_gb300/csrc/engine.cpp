@@ -48,16 +48,16 @@ size_t Engine::layout(char* base)
         c.take_raw(B_.kst, ns * mk * ts);
         c.take_raw(B_.Lst, ns * mk * n * ts);
         if (k >= 1) {
-            c.take(B_.Ah, ns * n2);
-            c.take(B_.Bh, ns * n2);
-            c.take(B_.Qxh, ns * n2);
-            c.take(B_.ah, ns * n);
-            c.take(B_.lxh, ns * n);
-            c.take(B_.QN, (size_t)batch * n2);
-            c.take(B_.lN, (size_t)batch * n);
-            c.take(B_.xd, nx_ * n);
-            c.take(B_.wd, ns * n);
-            c.take(B_.ld, nx_ * n);
+            c.take_raw(B_.Ah, ns * n2 * ts);
+            c.take_raw(B_.Bh, ns * n2 * ts);
+            c.take_raw(B_.Qxh, ns * n2 * ts);
+            c.take_raw(B_.ah, ns * n * ts);
+            c.take_raw(B_.lxh, ns * n * ts);
+            c.take_raw(B_.QN, (size_t)batch * n2 * ts);
+            c.take_raw(B_.lN, (size_t)batch * n * ts);
+            c.take_raw(B_.xd, nx_ * n * ts);
+            c.take_raw(B_.wd, ns * n * ts);
+            c.take_raw(B_.ld, nx_ * n * ts);
         }
     }
     c.take_raw(Pst0, (size_t)batch * n2 * ts);
@@ -68,16 +68,26 @@ size_t Engine::layout(char* base)
     c.take(in_off, (size_t)batch);
     c.take(w_off, (size_t)batch);
     c.take(gs0, (size_t)batch + 1);
-    c.take(dx, (size_t)plan.X_total * n);
-    c.take(dw, (size_t)plan.W_total);
-    c.take(dl, (size_t)plan.X_total * n);
-    c.take(rl, (size_t)plan.S_in * (n + m));
-    c.take(ra, (size_t)plan.S_in * n);
-    c.take(rl0, (size_t)batch * 2 * n);
-    c.take(ra0, (size_t)batch * n);
-    c.take(rlN, (size_t)batch * n);
-    c.take(rx0, (size_t)batch * n);
-    c.take(norms, (size_t)batch * 4);
+    c.take_raw(dx, (size_t)plan.X_total * n * ts);
+    c.take_raw(dw, (size_t)plan.W_total * ts);
+    c.take_raw(dl, (size_t)plan.X_total * n * ts);
+    c.take_raw(rl, (size_t)plan.S_in * (n + m) * ts);
+    c.take_raw(ra, (size_t)plan.S_in * n * ts);
+    c.take_raw(rl0, (size_t)batch * 2 * n * ts);
+    c.take_raw(ra0, (size_t)batch * n * ts);
+    c.take_raw(rlN, (size_t)batch * n * ts);
+    c.take_raw(rx0, (size_t)batch * n * ts);
+    if (prec != MHE_FP64) {
+        c.take(A32, (size_t)plan.S_in * n2);
+        c.take(B32, (size_t)plan.S_in * n * m);
+        c.take(Q32, (size_t)plan.S_in * (n + m) * (n + m));
+        c.take(P0_32, (size_t)batch * n2);
+        c.take(l32, (size_t)plan.S_in * (n + m));
+        c.take(a32, (size_t)plan.S_in * n);
+        c.take(x0_32, (size_t)batch * n);
+    }
+    c.take(norms, (size_t)batch * 3);
+    c.take(kinf, (size_t)batch);
     c.take(active, (size_t)batch);
     c.take(status, (size_t)batch);
     c.take(where, (size_t)batch * 3);
@@ -143,18 +153,21 @@ LevelArgs<T> Engine::args(int k) const
     a.nchunks = L.nchunks;
     a.chunks = L.chunks;
     a.li = L.li;
-    a.A = A; a.B = B; a.Q = Q; a.P0inv = P0inv;
     a.in_off = in_off;
     a.w_off = w_off;
     if (k >= 1) {
-        a.Ah = L.Ah; a.Bh = L.Bh; a.ah = L.ah; a.Qxh = L.Qxh; a.lxh = L.lxh;
-        a.QNk = L.QN; a.lNk = L.lN;
+        a.Ah = static_cast<const T*>(L.Ah); a.Bh = static_cast<const T*>(L.Bh);
+        a.ah = static_cast<const T*>(L.ah); a.Qxh = static_cast<const T*>(L.Qxh);
+        a.lxh = static_cast<const T*>(L.lxh);
+        a.QNk = static_cast<const T*>(L.QN); a.lNk = static_cast<const T*>(L.lN);
     }
     if (k + 1 < (int)lv.size()) {
         const LevelBuf& U = lv[k + 1];
-        a.Ah_up = U.Ah; a.Bh_up = U.Bh; a.ah_up = U.ah; a.Qxh_up = U.Qxh; a.lxh_up = U.lxh;
-        a.QN_up = U.QN; a.lN_up = U.lN;
-        a.xd_up = U.xd; a.wd_up = U.wd; a.ld_up = U.ld;
+        a.Ah_up = static_cast<T*>(U.Ah); a.Bh_up = static_cast<T*>(U.Bh); a.ah_up = static_cast<T*>(U.ah);
+        a.Qxh_up = static_cast<T*>(U.Qxh); a.lxh_up = static_cast<T*>(U.lxh);
+        a.QN_up = static_cast<T*>(U.QN); a.lN_up = static_cast<T*>(U.lN);
+        a.xd_up = static_cast<const T*>(U.xd); a.wd_up = static_cast<const T*>(U.wd);
+        a.ld_up = static_cast<const T*>(U.ld);
     }
     a.Pst = static_cast<T*>(L.Pst);
     a.Lgst = static_cast<T*>(L.Lgst);
@@ -168,7 +181,7 @@ LevelArgs<T> Engine::args(int k) const
         a.kst0 = static_cast<T*>(kst0);
         a.Lst0 = static_cast<T*>(Lst0);
     }
-    a.xd = L.xd; a.wd = L.wd; a.ld = L.ld;
+    a.xd = static_cast<T*>(L.xd); a.wd = static_cast<T*>(L.wd); a.ld = static_cast<T*>(L.ld);
     a.status = status;
     a.where = where;
     a.piv_rel = (sizeof(T) == 8) ? 1e-14 : 1e-7;
@@ -198,10 +211,11 @@ void launch<float>(void (*)(const LevelArgs<double>&, int, void*),
 // Algorithm 5: reduce level 0, 1, ... (tops included at their level).  With
 // l/a given the vector part of Algorithm 4 runs in the same pass.
 template <typename T>
-void Engine::pass_reduce(const double* l, const double* a)
+void Engine::pass_reduce(const T* A_, const T* B_, const T* Q_, const T* P0_, const T* l, const T* a)
 {
     for (int k = 0; k < (int)lv.size(); ++k) {
         LevelArgs<T> g = args<T>(k);
+        g.A = A_; g.B = B_; g.Q = Q_; g.P0inv = P0_;
         g.l = l;
         g.a = a;
         if (k >= 1 && !l) { g.lxh = nullptr; g.ah = nullptr; g.lNk = nullptr; }
@@ -214,10 +228,12 @@ void Engine::pass_reduce(const double* l, const double* a)
 
 // The vector part of Algorithm 4 alone, level by level, with stored factors.
 template <typename T>
-void Engine::pass_rhs(const double* l, const double* a, const double* l0, const double* a0, const double* lN)
+void Engine::pass_rhs(const T* l, const T* a, const T* l0, const T* a0, const T* lN)
 {
     for (int k = 0; k < (int)lv.size(); ++k) {
         LevelArgs<T> g = args<T>(k);
+        g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
+        g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
         g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
         g.active = active_mask;
         mark(PH_RHS, k, 1);
@@ -227,14 +243,16 @@ void Engine::pass_rhs(const double* l, const double* a, const double* l0, const 
     }
 }
 
-// Algorithm 6 as back-substitution, top level first.
+// Algorithm 6 as back-substitution, top level first.  With FP64 targets z
+// given, the level-0 solution (x, w, lam of type T) is added into them.
 template <typename T>
-void Engine::pass_down(const double* l, const double* a, const double* l0, const double* a0, const double* x0,
-                       const double* lN, double* x, double* w, double* lam, double* zx, double* zw, double* zl,
-                       const int* act)
+void Engine::pass_down(const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x, T* w,
+                       T* lam, double* zx, double* zw, double* zl, const int* act)
 {
     for (int k = (int)lv.size() - 1; k >= 0; --k) {
         LevelArgs<T> g = args<T>(k);
+        g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
+        g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
         g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;
         g.x0 = x0;
         g.lN = lN;
@@ -250,9 +268,10 @@ void Engine::pass_down(const double* l, const double* a, const double* l0, const
     }
 }
 
+template <typename T>
 void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, const double* lam, const int* act)
 {
-    ResidArgs r;
+    ResidArgs<T> r;
     memset(&r, 0, sizeof(r));
     r.batch = plan.batch;
     r.nstages = plan.gs0[plan.batch];
@@ -261,39 +280,73 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
     r.w_off = w_off;
     r.A = A; r.B = B; r.Q = Q; r.P0inv = P0inv;
     r.l = rhs->l; r.a = rhs->a; r.x0 = rhs->x0;
-    r.l0 = nullptr; r.a0 = nullptr; r.lN = nullptr;
     r.x = x; r.w = w; r.lam = lam;
-    r.rl = rl; r.ra = ra; r.rl0 = rl0; r.ra0 = ra0; r.rlN = rlN; r.rx0 = rx0;
+    r.rl = static_cast<T*>(rl); r.ra = static_cast<T*>(ra); r.rl0 = static_cast<T*>(rl0);
+    r.ra0 = static_cast<T*>(ra0); r.rlN = static_cast<T*>(rlN); r.rx0 = static_cast<T*>(rx0);
     r.norms = norms;
     r.active = act;
-    rt->memset0(norms, sizeof(double) * 4 * plan.batch, stream);
+    rt->memset0(norms, sizeof(unsigned long long) * 3 * plan.batch, stream);
     mark(PH_RESID, 0, 1);
     launches += r.nstages > 0;
-    ops->resid(r, stream);
+    launch_resid<T>(r);
     mark(PH_RESID, 0, 0);
+}
+
+template <>
+void Engine::launch_resid<double>(const ResidArgs<double>& r) { ops->resid64(r, stream); }
+template <>
+void Engine::launch_resid<float>(const ResidArgs<float>& r) { ops->resid32(r, stream); }
+
+void Engine::convert_rhs(const mhe_rhs* rhs)
+{
+    rt->convert(l32, rhs->l, plan.S_in * (plan.n + plan.m), stream);
+    rt->convert(a32, rhs->a, plan.S_in * plan.n, stream);
+    rt->convert(x0_32, rhs->x0, (long long)plan.batch * plan.n, stream);
+    launches += 3;
 }
 
 template <typename T>
 int Engine::run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool fused)
 {
+    const bool fp64 = sizeof(T) == 8;
+    const T* l = fp64 ? reinterpret_cast<const T*>(rhs->l) : reinterpret_cast<const T*>(l32);
+    const T* a = fp64 ? reinterpret_cast<const T*>(rhs->a) : reinterpret_cast<const T*>(a32);
+    const T* x0 = fp64 ? reinterpret_cast<const T*>(rhs->x0) : reinterpret_cast<const T*>(x0_32);
     active_mask = nullptr;
-    if (!fused) pass_rhs<T>(rhs->l, rhs->a, nullptr, nullptr, nullptr);
-    pass_down<T>(rhs->l, rhs->a, nullptr, nullptr, rhs->x0, nullptr, x, w, lam, nullptr, nullptr, nullptr,
-                 nullptr);
+    if (!fp64 && !fused) convert_rhs(rhs);
+    if (!fused) pass_rhs<T>(l, a, nullptr, nullptr, nullptr);
+    if (fp64) {
+        pass_down<T>(l, a, nullptr, nullptr, x0, nullptr, reinterpret_cast<T*>(x), reinterpret_cast<T*>(w),
+                     reinterpret_cast<T*>(lam), nullptr, nullptr, nullptr, nullptr);
+    } else {
+        // the FP32 solution is added into zeroed FP64 outputs
+        rt->memset0(x, sizeof(double) * plan.X_total * plan.n, stream);
+        rt->memset0(w, sizeof(double) * plan.W_total, stream);
+        rt->memset0(lam, sizeof(double) * plan.X_total * plan.n, stream);
+        pass_down<T>(l, a, nullptr, nullptr, x0, nullptr, static_cast<T*>(dx), static_cast<T*>(dw),
+                     static_cast<T*>(dl), x, w, lam, nullptr);
+    }
     rt->memset0(iters, sizeof(int) * plan.batch, stream);
+    const T* crl = static_cast<const T*>(rl);
+    const T* cra = static_cast<const T*>(ra);
+    const T* crl0 = static_cast<const T*>(rl0);
+    const T* cra0 = static_cast<const T*>(ra0);
+    const T* crlN = static_cast<const T*>(rlN);
+    const T* crx0 = static_cast<const T*>(rx0);
     for (int it = 0; it < max_refine; ++it) {
-        residual(rhs, x, w, lam, it == 0 ? nullptr : active);
-        rt->finalize(plan.batch, norms, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
+        residual<T>(rhs, x, w, lam, it == 0 ? nullptr : active);
+        rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
                      stream);
         ++launches;
         // correction problem K dz = r in UFTOC form, then z += dz
         active_mask = active;
-        pass_rhs<T>(rl, ra, rl0, ra0, rlN);
-        pass_down<T>(rl, ra, rl0, ra0, rx0, rlN, dx, dw, dl, x, w, lam, active);
+        pass_rhs<T>(crl, cra, crl0, cra0, crlN);
+        pass_down<T>(crl, cra, crl0, cra0, crx0, crlN, static_cast<T*>(dx), static_cast<T*>(dw),
+                     static_cast<T*>(dl), x, w, lam, active);
         active_mask = nullptr;
     }
-    residual(rhs, x, w, lam, nullptr);
-    rt->finalize(plan.batch, norms, active, iters, status, where, tol, 2, max_refine > 0 ? 1 : 0, info_dev,
+    residual<T>(rhs, x, w, lam, nullptr);
+    rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, 2, max_refine > 0 ? 1 : 0, info_dev,
                  stream);
     ++launches;
     if (info) rt->copy(info, info_dev, sizeof(mhe_info) * plan.batch, stream);
@@ -308,13 +361,36 @@ int Engine::factor(const mhe_matrices& mt, const mhe_rhs* rhs, double* x, double
     if (!mt.Q && plan.S_in > 0) { err = "Q is NULL"; return MHE_E_ARG; }
     if (!mt.P0inv) { err = "P0inv is NULL"; return MHE_E_ARG; }
     A = mt.A; B = mt.B; Q = mt.Q; P0inv = mt.P0inv;
+    (void)x; (void)w; (void)lam;
     rt->memset0(status, sizeof(int) * plan.batch, stream);
     rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
-    const double* l = rhs ? rhs->l : nullptr;
-    const double* a = rhs ? rhs->a : nullptr;
-    (void)x; (void)w; (void)lam;
-    if (prec == MHE_FP64) pass_reduce<double>(l, a);
-    else pass_reduce<float>(l, a);
+    // ||K||_inf of the new matrices (the residual's scale), once per factorisation
+    {
+        KnormArgs kn;
+        kn.batch = plan.batch;
+        kn.nstages = plan.gs0[plan.batch];
+        kn.gs0 = gs0;
+        kn.in_off = in_off;
+        kn.A = A; kn.B = B; kn.Q = Q; kn.P0inv = P0inv;
+        kn.kinf = kinf;
+        rt->memset0(kinf, sizeof(unsigned int) * plan.batch, stream);
+        launches += 1;
+        ops->knorm(kn, stream);
+    }
+    if (prec == MHE_FP64) {
+        mA = A; mB = B; mQ = Q; mP0 = P0inv;
+        pass_reduce<double>(A, B, Q, P0inv, rhs ? rhs->l : nullptr, rhs ? rhs->a : nullptr);
+    } else {
+        const int n = plan.n, m = plan.m;
+        rt->convert(A32, A, plan.S_in * n * n, stream);
+        rt->convert(B32, B, plan.S_in * n * m, stream);
+        rt->convert(Q32, Q, plan.S_in * (n + m) * (n + m), stream);
+        rt->convert(P0_32, P0inv, (long long)plan.batch * n * n, stream);
+        launches += 4;
+        mA = A32; mB = B32; mQ = Q32; mP0 = P0_32;
+        if (rhs) convert_rhs(rhs);
+        pass_reduce<float>(A32, B32, Q32, P0_32, rhs ? l32 : nullptr, rhs ? a32 : nullptr);
+    }
     factored = true;
     if (rt->error() != 0) { err = "CUDA error during the factorisation"; return MHE_E_CUDA; }
     return MHE_OK;

@@ -23,7 +23,9 @@ struct ShapeOps {
     void (*reduce32)(const LevelArgs<float>&, int upper, void* stream);
     void (*rhs32)(const LevelArgs<float>&, int upper, void* stream);
     void (*down32)(const LevelArgs<float>&, int upper, void* stream);
-    void (*resid)(const ResidArgs&, void* stream);
+    void (*resid64)(const ResidArgs<double>&, void* stream);
+    void (*resid32)(const ResidArgs<float>&, void* stream);
+    void (*knorm)(const KnormArgs&, void* stream);
 };
 
 // Memory and small shape-independent steps.
@@ -34,9 +36,11 @@ struct Runtime {
     int (*copy)(void* dst, const void* src, size_t bytes, void* stream);   // any direction
     // per instance: relres from norms; mode 0/1 (first/later refinement pass)
     // sets which instances take another correction, mode 2 fills mhe_info
-    void (*finalize)(int batch, const double* norms, int* active, int* iters, const int* status,
-                     const int* where, double tol, int mode, int refine, mhe_info* info,
-                     void* stream);
+    void (*finalize)(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
+                     int* iters, const int* status, const int* where, double tol, int mode, int refine,
+                     mhe_info* info, void* stream);
+    // FP64 -> FP32 copy of count elements (FP32 mode keeps FP32 copies of the problem)
+    void (*convert)(float* dst, const double* src, long long count, void* stream);
     int (*sync)(void* stream);
     int (*error)();   // sticky error of the launches so far (0 = none)
     // optional per-pass timing marks (begin = 1 before a launch, 0 after)
@@ -45,14 +49,14 @@ struct Runtime {
 
 enum { PH_REDUCE = 0, PH_RHS = 1, PH_DOWN = 2, PH_RESID = 3, PH_COUNT = 4 };
 
-struct LevelBuf {
+struct LevelBuf {   // every array of the compute type T
     ChunkDesc* chunks = nullptr;
     LevelInst* li = nullptr;
     int nchunks = 0;
     void *Pst = nullptr, *Lgst = nullptr, *Kst = nullptr, *kst = nullptr, *Lst = nullptr;
-    double *Ah = nullptr, *Bh = nullptr, *ah = nullptr, *Qxh = nullptr, *lxh = nullptr;
-    double *QN = nullptr, *lN = nullptr;   // terminal of this level (k >= 1)
-    double *xd = nullptr, *wd = nullptr, *ld = nullptr;
+    void *Ah = nullptr, *Bh = nullptr, *ah = nullptr, *Qxh = nullptr, *lxh = nullptr;
+    void *QN = nullptr, *lN = nullptr;   // terminal of this level (k >= 1)
+    void *xd = nullptr, *wd = nullptr, *ld = nullptr;
 };
 
 class Engine {
@@ -68,15 +72,19 @@ public:
     std::vector<LevelBuf> lv;
     void *Pst0 = nullptr, *Lgst0 = nullptr, *Kst0 = nullptr, *kst0 = nullptr, *Lst0 = nullptr;
     long long *in_off = nullptr, *w_off = nullptr, *gs0 = nullptr;
-    double *dx = nullptr, *dw = nullptr, *dl = nullptr;
-    double *rl = nullptr, *ra = nullptr, *rl0 = nullptr, *ra0 = nullptr, *rlN = nullptr, *rx0 = nullptr;
-    double* norms = nullptr;
+    void *dx = nullptr, *dw = nullptr, *dl = nullptr;            // T: corrections of the level-0 solution
+    void *rl = nullptr, *ra = nullptr, *rl0 = nullptr, *ra0 = nullptr, *rlN = nullptr, *rx0 = nullptr;   // T
+    float *A32 = nullptr, *B32 = nullptr, *Q32 = nullptr, *P0_32 = nullptr;   // FP32 mode: problem copies
+    float *l32 = nullptr, *a32 = nullptr, *x0_32 = nullptr;
+    unsigned long long* norms = nullptr;   // per instance |r|, |z|, |b| maxima (bit patterns)
+    unsigned int* kinf = nullptr;          // per instance ||K||_inf (float bit pattern)
     int *active = nullptr, *status = nullptr, *where = nullptr, *iters = nullptr;
     mhe_info* info_dev = nullptr;
     void* arena = nullptr;
     size_t arena_bytes = 0;
 
-    const double *A = nullptr, *B = nullptr, *Q = nullptr, *P0inv = nullptr;
+    const double *A = nullptr, *B = nullptr, *Q = nullptr, *P0inv = nullptr;   // the caller's FP64 problem
+    const void *mA = nullptr, *mB = nullptr, *mQ = nullptr, *mP0 = nullptr;    // the problem in the compute type
     const int* active_mask = nullptr;   // instances still refining (nullptr: all)
     void* mark_user = nullptr;          // non-null: record per-pass timing marks
     long long launches = 0;             // kernels launched by this context so far
@@ -95,16 +103,19 @@ private:
     template <typename T>
     LevelArgs<T> args(int k) const;
     template <typename T>
-    void pass_reduce(const double* l, const double* a);
+    void pass_reduce(const T* A_, const T* B_, const T* Q_, const T* P0_, const T* l, const T* a);
     template <typename T>
-    void pass_rhs(const double* l, const double* a, const double* l0, const double* a0, const double* lN);
+    void pass_rhs(const T* l, const T* a, const T* l0, const T* a0, const T* lN);
     template <typename T>
-    void pass_down(const double* l, const double* a, const double* l0, const double* a0, const double* x0,
-                   const double* lN, double* x, double* w, double* lam, double* zx, double* zw, double* zl,
-                   const int* act);
+    void pass_down(const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x, T* w,
+                   T* lam, double* zx, double* zw, double* zl, const int* act);
     template <typename T>
     int run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool skip_first_rhs);
+    template <typename T>
     void residual(const mhe_rhs* rhs, const double* x, const double* w, const double* lam, const int* act);
+    template <typename T>
+    void launch_resid(const ResidArgs<T>& r);
+    void convert_rhs(const mhe_rhs* rhs);
 };
 
 }  // namespace mhe

@@ -11,27 +11,35 @@
 
 namespace mhe {
 
-template <typename T, int NX>
-constexpr int level_warps()
+enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2 };
+
+// shared-memory workspace (elements of T) one warp of a pass needs
+template <typename T, int NX, int OP>
+constexpr int op_count()
 {
-    return (200 * 1024) / (int)(Ws<T, NX>::count * sizeof(T)) >= 8
-               ? 8
-               : ((200 * 1024) / (int)(Ws<T, NX>::count * sizeof(T)) < 1
-                      ? 1
-                      : (200 * 1024) / (int)(Ws<T, NX>::count * sizeof(T)));
+    return OP == OP_REDUCE ? Ws<T, NX>::count : (OP == OP_RHS ? Ws<T, NX>::count_rhs : Ws<T, NX>::count_vec);
 }
 
-enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2 };
+// warps per CTA: as many per-warp workspaces as fit in 200 KB, at most 8
+template <typename T, int NX, int OP>
+constexpr int level_warps()
+{
+    return (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) >= 8
+               ? 8
+               : ((200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) < 1
+                      ? 1
+                      : (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)));
+}
 
 template <typename T, int NX, int NW, int UPPER, int OP>
 __global__ void __launch_bounds__(256) k_level(LevelArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int W = level_warps<T, NX>();
+    constexpr int W = level_warps<T, NX, OP>();
     const int warp = threadIdx.x >> 5;
     const int ci = blockIdx.x * W + warp;
     if (ci >= a.nchunks) return;
-    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * Ws<T, NX>::count;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * op_count<T, NX, OP>();
     if (OP == OP_REDUCE) reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     else if (OP == OP_RHS) rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     else down_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
@@ -40,8 +48,8 @@ __global__ void __launch_bounds__(256) k_level(LevelArgs<T> a)
 template <typename T, int NX, int NW, int UPPER, int OP>
 void launch_level_v(const LevelArgs<T>& a, void* stream)
 {
-    constexpr int W = level_warps<T, NX>();
-    const size_t smem = (size_t)W * Ws<T, NX>::count * sizeof(T);
+    constexpr int W = level_warps<T, NX, OP>();
+    const size_t smem = (size_t)W * op_count<T, NX, OP>() * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_level<T, NX, NW, UPPER, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -60,22 +68,40 @@ void launch_level(const LevelArgs<T>& a, int upper, void* stream)
     else launch_level_v<T, NX, NW, 0, OP>(a, stream);
 }
 
-template <int NX, int NW>
-__global__ void __launch_bounds__(256) k_resid(ResidArgs r)
+template <int NX, int NW, typename TR>
+__global__ void __launch_bounds__(256) k_resid(ResidArgs<TR> r)
 {
-    __shared__ double sm[8][ResidSmem<NX, NW>::count];
+    __shared__ unsigned long long sm[8][ResidSmem<NX, NW>::count];
     const int warp = threadIdx.x >> 5;
     const long long g = (long long)blockIdx.x * 8 + warp;
     if (g >= r.nstages) return;
-    resid_stage<NX, NW>(r, g, sm[warp]);
+    resid_stage<NX, NW, TR>(r, g, sm[warp]);
 }
 
-template <int NX, int NW>
-void launch_resid(const ResidArgs& r, void* stream)
+template <int NX, int NW, typename TR>
+void launch_resid(const ResidArgs<TR>& r, void* stream)
 {
     if (r.nstages <= 0) return;
     const long long grid = (r.nstages + 7) / 8;
-    k_resid<NX, NW><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
+    k_resid<NX, NW, TR><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
+}
+
+template <int NX, int NW>
+__global__ void __launch_bounds__(256) k_knorm(KnormArgs r)
+{
+    __shared__ float sm[8][2 * NX + NW + 4];
+    const int warp = threadIdx.x >> 5;
+    const long long g = (long long)blockIdx.x * 8 + warp;
+    if (g >= r.nstages) return;
+    knorm_stage<NX, NW>(r, g, sm[warp]);
+}
+
+template <int NX, int NW>
+void launch_knorm(const KnormArgs& r, void* stream)
+{
+    if (r.nstages <= 0) return;
+    const long long grid = (r.nstages + 7) / 8;
+    k_knorm<NX, NW><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
 }
 
 template <int NX, int NW, int NY>
@@ -133,7 +159,9 @@ ShapeEntry make_shape()
     e.ops.reduce32 = &launch_level<float, NX, NW, OP_REDUCE>;
     e.ops.rhs32 = &launch_level<float, NX, NW, OP_RHS>;
     e.ops.down32 = &launch_level<float, NX, NW, OP_DOWN>;
-    e.ops.resid = &launch_resid<NX, NW>;
+    e.ops.resid64 = &launch_resid<NX, NW, double>;
+    e.ops.resid32 = &launch_resid<NX, NW, float>;
+    e.ops.knorm = &launch_knorm<NX, NW>;
     e.ny = NY;
     e.assemble = &launch_assemble<NX, NW, NY>;
     return e;

@@ -19,15 +19,19 @@ namespace mhe {
 template <int NX, int NW>
 struct ResidSmem {
     static constexpr int rows = 5 * NX + NW;
-    static constexpr int count = 4 * rows + 8;
+    static constexpr int count = 3 * rows + 4;   // unsigned long long entries
 };
 
 // One stage t of instance b: rows of stationarity in x_t and w_t, dynamics
 // t -> t+1, plus the initial rows (t = 0) and the terminal rows (t = N-1).
-template <int NX, int NW, int KIND>
-MHE_DEV void resid_rows(const ResidArgs& r, int b, int t, int N, double* sm)
+// The FP64 work is the products of the rows alone; the maxima of |r|, |z|,
+// |b| are taken on bit patterns (integer operations).
+template <int NX, int NW, int KIND, typename TR>
+MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned long long* sm)
 {
-    constexpr int MT = (KIND == 1) ? NX : NW;   // arrival stage has width n
+    constexpr int MT = (KIND == 1) ? NX : NW;   // the arrival stage has width n
+    constexpr int NQ = NX + MT;
+    constexpr int ROWS = ResidSmem<NX, NW>::rows;
     const long long gx = r.gs0[b] + b;
     const double* xt = r.x + (gx + t) * NX;
     const double* xn = xt + NX;
@@ -39,105 +43,159 @@ MHE_DEV void resid_rows(const ResidArgs& r, int b, int t, int N, double* sm)
     const double* B = (KIND == 1) ? nullptr : r.B + s * NX * NW;
     const double* Q = (KIND == 1) ? nullptr : r.Q + s * (NX + NW) * (NX + NW);
     const double* P0 = r.P0inv + (long long)b * NX * NX;
-    const double* l = (KIND == 1) ? (r.l0 ? r.l0 + (long long)b * 2 * NX : nullptr)
-                                  : (r.l ? r.l + s * (NX + NW) : nullptr);
-    const double* a = (KIND == 1) ? (r.a0 ? r.a0 + (long long)b * NX : nullptr)
-                                  : (r.a ? r.a + s * NX : nullptr);
-    double* rl = (KIND == 1) ? r.rl0 + (long long)b * 2 * NX : r.rl + s * (NX + NW);
-    double* ra = (KIND == 1) ? r.ra0 + (long long)b * NX : r.ra + s * NX;
+    const double* l = (KIND == 1) ? nullptr : (r.l ? r.l + s * (NX + NW) : nullptr);
+    const double* a = (KIND == 1) ? nullptr : (r.a ? r.a + s * NX : nullptr);
+    TR* rl = (KIND == 1) ? r.rl0 + (long long)b * 2 * NX : r.rl + s * (NX + NW);
+    TR* ra = (KIND == 1) ? r.ra0 + (long long)b * NX : r.ra + s * NX;
     const bool first = (t == 0), lastst = (t == N - 1);
-    constexpr int NQ = NX + MT;
-    auto Aij = [&](int i, int j) -> double { return KIND == 1 ? (i == j ? 1.0 : 0.0) : A[i + j * NX]; };
-    auto Bij = [&](int i, int j) -> double { return KIND == 1 ? (i == j ? 1.0 : 0.0) : B[i + j * NX]; };
-    auto Qij = [&](int i, int j) -> double {
-        if (KIND != 1) return Q[i + j * NQ];
-        return (i >= NX && j >= NX) ? P0[(i - NX) + (j - NX) * NX] : 0.0;
-    };
     const int nrow = NQ + NX + (first ? NX : 0) + (lastst ? NX : 0);
-    double* sr = sm;            // |r| per row
-    double* sk = sm + 5 * NX + NW;   // row sums of |K|
-    double* sz = sk + 5 * NX + NW;   // |z| entries
-    double* sb = sz + 5 * NX + NW;   // |b| entries
+    unsigned long long* sr = sm;
+    unsigned long long* sz = sm + ROWS;
+    unsigned long long* sb = sm + 2 * ROWS;
     wfor(nrow, [&](int i) {
-        double res, rs, zz = 0.0, bb = 0.0;
+        double res;
+        unsigned long long zz = 0, bb = 0;
         if (i < NQ) {
             // stationarity rows of stage t
-            double acc = 0.0;
-            rs = 0.0;
-            for (int j = 0; j < NX; ++j) { acc += Qij(i, j) * xt[j]; rs += fabs(Qij(i, j)); }
-            for (int j = 0; j < MT; ++j) { acc += Qij(i, NX + j) * wt[j]; rs += fabs(Qij(i, NX + j)); }
-            for (int j = 0; j < NX; ++j) {
-                double cj = (i < NX) ? Aij(j, i) : Bij(j, i - NX);
-                acc += cj * ln[j];
-                rs += fabs(cj);
+            double acc;
+            if (KIND == 1) {
+                // arrival: Q_0 = diag(0, P~0^{-1}), A_0 = B_0 = I
+                if (i < NX) {
+                    acc = ln[i] - lt[i];
+                } else {
+                    acc = ln[i - NX];
+                    for (int j = 0; j < NX; ++j) acc = fma(P0[(i - NX) + j * NX], wt[j], acc);
+                }
+            } else {
+                acc = 0.0;
+                for (int j = 0; j < NX; ++j) acc = fma(Q[i + j * NQ], xt[j], acc);
+                for (int j = 0; j < MT; ++j) acc = fma(Q[i + (NX + j) * NQ], wt[j], acc);
+                if (i < NX) {
+                    for (int j = 0; j < NX; ++j) acc = fma(A[j + i * NX], ln[j], acc);
+                    acc -= lt[i];
+                } else {
+                    for (int j = 0; j < NX; ++j) acc = fma(B[j + (i - NX) * NX], ln[j], acc);
+                }
             }
-            if (i < NX) { acc -= lt[i]; rs += 1.0; zz = fmax(fabs(xt[i]), fabs(lt[i])); }
-            else zz = fabs(wt[i - NX]);
             const double li = l ? l[i] : 0.0;
             res = -li - acc;
-            rl[i] = -res;
-            bb = fabs(li);
+            rl[i] = (TR)(li + acc);
+            zz = (i < NX) ? (abs_bits(xt[i]) > abs_bits(lt[i]) ? abs_bits(xt[i]) : abs_bits(lt[i]))
+                          : abs_bits(wt[i - NX]);
+            bb = abs_bits(li);
         } else if (i < NQ + NX) {
             const int ii = i - NQ;
             double acc = -xn[ii];
-            rs = 1.0;
-            for (int j = 0; j < NX; ++j) { acc += Aij(ii, j) * xt[j]; rs += fabs(Aij(ii, j)); }
-            for (int j = 0; j < MT; ++j) { acc += Bij(ii, j) * wt[j]; rs += fabs(Bij(ii, j)); }
+            if (KIND == 1) {
+                acc += xt[ii] + wt[ii];
+            } else {
+                for (int j = 0; j < NX; ++j) acc = fma(A[ii + j * NX], xt[j], acc);
+                for (int j = 0; j < MT; ++j) acc = fma(B[ii + j * NX], wt[j], acc);
+            }
             const double ai = a ? a[ii] : 0.0;
             res = -ai - acc;
-            ra[ii] = -res;
-            bb = fabs(ai);
+            ra[ii] = (TR)(ai + acc);
+            bb = abs_bits(ai);
         } else if (first && i < NQ + 2 * NX) {
             const int ii = i - NQ - NX;
-            res = r.x0[(long long)b * NX + ii] - xt[ii];
-            r.rx0[(long long)b * NX + ii] = res;
-            rs = 1.0;
-            bb = fabs(r.x0[(long long)b * NX + ii]);
+            const double x0i = r.x0[(long long)b * NX + ii];
+            res = x0i - xt[ii];
+            r.rx0[(long long)b * NX + ii] = (TR)res;
+            bb = abs_bits(x0i);
         } else {
+            // terminal rows with Q_{x,N} = 0, l_N = 0:  -(0 - lambda_N)
             const int ii = i - NQ - NX - (first ? NX : 0);
             const double* xN = r.x + (gx + N) * NX;
-            const double* lN_ = r.lam + (gx + N) * NX;
-            const double lNi = r.lN ? r.lN[(long long)b * NX + ii] : 0.0;
-            res = -lNi - (-lN_[ii]);
-            r.rlN[(long long)b * NX + ii] = -res;
-            rs = 1.0;
-            zz = fmax(fabs(xN[ii]), fabs(lN_[ii]));
-            bb = fabs(lNi);
+            const double* lamN = r.lam + (gx + N) * NX;
+            res = lamN[ii];
+            r.rlN[(long long)b * NX + ii] = (TR)(-res);
+            zz = abs_bits(xN[ii]) > abs_bits(lamN[ii]) ? abs_bits(xN[ii]) : abs_bits(lamN[ii]);
         }
-        sr[i] = fabs(res);
-        sk[i] = rs;
+        sr[i] = abs_bits(res);
         sz[i] = zz;
         sb[i] = bb;
     });
     wone([&](int) {
-        double m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        unsigned long long m0 = 0, m1 = 0, m2 = 0;
         for (int i = 0; i < nrow; ++i) {
-            m0 = (sr[i] > m0 || sr[i] != sr[i]) ? sr[i] : m0;
-            m1 = fmax(m1, sk[i]);
-            m2 = (sz[i] > m2 || sz[i] != sz[i]) ? sz[i] : m2;
-            m3 = fmax(m3, sb[i]);
+            m0 = sr[i] > m0 ? sr[i] : m0;
+            m1 = sz[i] > m1 ? sz[i] : m1;
+            m2 = sb[i] > m2 ? sb[i] : m2;
         }
-        atomic_max_nonneg(r.norms + 4LL * b + 0, m0);
-        atomic_max_nonneg(r.norms + 4LL * b + 1, m1);
-        atomic_max_nonneg(r.norms + 4LL * b + 2, m2);
-        atomic_max_nonneg(r.norms + 4LL * b + 3, m3);
+        atomic_max_u64(r.norms + 3LL * b + 0, m0);
+        atomic_max_u64(r.norms + 3LL * b + 1, m1);
+        atomic_max_u64(r.norms + 3LL * b + 2, m2);
     });
 }
 
-template <int NX, int NW>
-MHE_DEV void resid_stage(const ResidArgs& r, long long gstage, double* sm)
+MHE_DEV int stage_instance(const long long* gs0, int batch, long long gstage)
 {
-    int lo = 0, hi = r.batch;
+    int lo = 0, hi = batch;
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (r.gs0[mid] <= gstage) lo = mid; else hi = mid;
+        if (gs0[mid] <= gstage) lo = mid; else hi = mid;
     }
-    const int b = lo;
+    return lo;
+}
+
+template <int NX, int NW, typename TR>
+MHE_DEV void resid_stage(const ResidArgs<TR>& r, long long gstage, unsigned long long* sm)
+{
+    const int b = stage_instance(r.gs0, r.batch, gstage);
     if (r.active && !r.active[b]) return;
     const int t = (int)(gstage - r.gs0[b]);
     const int N = (int)(r.gs0[b + 1] - r.gs0[b]);
-    if (t == 0) resid_rows<NX, NW, 1>(r, b, t, N, sm);
-    else resid_rows<NX, NW, 0>(r, b, t, N, sm);
+    if (t == 0) resid_rows<NX, NW, 1, TR>(r, b, t, N, sm);
+    else resid_rows<NX, NW, 0, TR>(r, b, t, N, sm);
+}
+
+// ||K||_inf contribution of one stage: absolute row sums (in float) of the KKT
+// rows the residual above evaluates; one atomic max per stage.
+template <int NX, int NW>
+MHE_DEV void knorm_stage(const KnormArgs& r, long long gstage, float* sm)
+{
+    const int b = stage_instance(r.gs0, r.batch, gstage);
+    const int t = (int)(gstage - r.gs0[b]);
+    constexpr int NQ = NX + NW;
+    if (t == 0) {
+        // arrival stage: x rows 1 + 1, w rows |P~0^{-1} row| + 1, dynamics rows 3, initial row 1
+        const double* P0 = r.P0inv + (long long)b * NX * NX;
+        wfor(NX, [&](int i) {
+            float rs = 1.f;
+            for (int j = 0; j < NX; ++j) rs += abs_to_float(P0[i + j * NX]);
+            sm[i] = rs > 3.f ? rs : 3.f;
+        });
+        wone([&](int) {
+            float m = 0.f;
+            for (int i = 0; i < NX; ++i) m = sm[i] > m ? sm[i] : m;
+            atomic_max_u32(r.kinf + b, float_bits(m));
+        });
+        return;
+    }
+    const long long s = r.in_off[b] + t - 1;
+    const double* A = r.A + s * NX * NX;
+    const double* B = r.B + s * NX * NW;
+    const double* Q = r.Q + s * NQ * NQ;
+    wfor(NQ + NX, [&](int i) {
+        float rs;
+        if (i < NQ) {
+            rs = (i < NX) ? 1.f : 0.f;
+            for (int j = 0; j < NQ; ++j) rs += abs_to_float(Q[i + j * NQ]);
+            if (i < NX) for (int j = 0; j < NX; ++j) rs += abs_to_float(A[j + i * NX]);
+            else for (int j = 0; j < NX; ++j) rs += abs_to_float(B[j + (i - NX) * NX]);
+        } else {
+            const int ii = i - NQ;
+            rs = 1.f;
+            for (int j = 0; j < NX; ++j) rs += abs_to_float(A[ii + j * NX]);
+            for (int j = 0; j < NW; ++j) rs += abs_to_float(B[ii + j * NX]);
+        }
+        sm[i] = rs;
+    });
+    wone([&](int) {
+        float m = 1.f;
+        for (int i = 0; i < NQ + NX; ++i) m = sm[i] > m ? sm[i] : m;
+        atomic_max_u32(r.kinf + b, float_bits(m));
+    });
 }
 
 // ---- Section II: MHE stage weights -> UFTOC Q_t, l_t, c_t ---------------------

@@ -52,6 +52,27 @@ struct Ws {
         tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
         sc = p;
     }
+    // right-hand-side pass: only A, B, K, G and the vectors
+    static constexpr int count_rhs = ((4 * slot + 8 * NX + 8) + 3) / 4 * 4;
+    MHE_DEV void carve_rhs(T* base)
+    {
+        T* p = base;
+        P = V = Qw = Tt = PB = H = nullptr;
+        A = p; p += slot; B = p; p += slot; K = p; p += slot; G = p; p += slot;
+        Psi = p; p += NX; v = p; p += NX; u = p; p += NX; e = p; p += NX;
+        tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
+        sc = p;
+    }
+    // down pass: the vectors only
+    static constexpr int count_vec = ((8 * NX + 8) + 3) / 4 * 4;
+    MHE_DEV void carve_vectors(T* base)
+    {
+        T* p = base;
+        P = V = Qw = A = Tt = B = PB = H = K = G = nullptr;
+        Psi = p; p += NX; v = p; p += NX; u = p; p += NX; e = p; p += NX;
+        tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
+        sc = p;
+    }
 };
 
 // upper-triangle index -> (i <= j)
@@ -68,60 +89,61 @@ MHE_DEV void tri_ij(int idx, int& i, int& j)
 // ARRIVAL: A = B = I, Q = diag(0, P~0^{-1}).  UPPER: a master-problem stage in
 // square-root form: A = A^, B = R^T, Q = blkdiag(Q^_x, I), l = (l^_x, 0),
 // where R^T R = Q^_w is the Cholesky factorisation of the T-form Q^_w = B^.
+template <typename T>
 struct StageRef {
-    const double *A, *B, *Q, *Qx, *Qw0, *l, *a;
+    const T *A, *B, *Q, *Qx, *Qw0, *l, *a;
 };
 
-template <int KIND, int NX, int MT>
+template <typename T, int KIND, int NX, int MT>
 struct Acc {
-    static MHE_DEV double A(const StageRef& s, int i, int j)
+    static MHE_DEV T A(const StageRef<T>& s, int i, int j)
     {
-        return KIND == KIND_ARRIVAL ? (i == j ? 1.0 : 0.0) : s.A[i + j * NX];
+        return KIND == KIND_ARRIVAL ? (T)(i == j ? 1 : 0) : s.A[i + j * NX];
     }
-    static MHE_DEV double B(const StageRef& s, int i, int j)
+    static MHE_DEV T B(const StageRef<T>& s, int i, int j)
     {
-        return KIND == KIND_ARRIVAL ? (i == j ? 1.0 : 0.0) : s.B[i + j * NX];
+        return KIND == KIND_ARRIVAL ? (T)(i == j ? 1 : 0) : s.B[i + j * NX];
     }
-    static MHE_DEV double qx(const StageRef& s, int i, int j)
+    static MHE_DEV T qx(const StageRef<T>& s, int i, int j)
     {
         if (KIND == KIND_LEAF) return s.Q[i + j * (NX + MT)];
         if (KIND == KIND_UPPER) return s.Qx[i + j * NX];
-        return 0.0;
+        return (T)0;
     }
-    static MHE_DEV double qxw(const StageRef& s, int i, int j)
+    static MHE_DEV T qxw(const StageRef<T>& s, int i, int j)
     {
-        return KIND == KIND_LEAF ? s.Q[i + (NX + j) * (NX + MT)] : 0.0;
+        return KIND == KIND_LEAF ? s.Q[i + (NX + j) * (NX + MT)] : (T)0;
     }
-    static MHE_DEV double qw(const StageRef& s, int i, int j)
+    static MHE_DEV T qw(const StageRef<T>& s, int i, int j)
     {
         if (KIND == KIND_LEAF) return s.Q[(NX + i) + (NX + j) * (NX + MT)];
-        if (KIND == KIND_UPPER) return i == j ? 1.0 : 0.0;   // square-root master stage
+        if (KIND == KIND_UPPER) return (T)(i == j ? 1 : 0);   // square-root master stage
         return s.Qw0[i + j * NX];
     }
-    static MHE_DEV double lx(const StageRef& s, int i) { return s.l ? s.l[i] : 0.0; }
-    static MHE_DEV double lw(const StageRef& s, int j)
+    static MHE_DEV T lx(const StageRef<T>& s, int i) { return s.l ? s.l[i] : (T)0; }
+    static MHE_DEV T lw(const StageRef<T>& s, int j)
     {
-        return (KIND != KIND_UPPER && s.l) ? s.l[NX + j] : 0.0;
+        return (KIND != KIND_UPPER && s.l) ? s.l[NX + j] : (T)0;
     }
-    static MHE_DEV double a(const StageRef& s, int i) { return s.a ? s.a[i] : 0.0; }
+    static MHE_DEV T a(const StageRef<T>& s, int i) { return s.a ? s.a[i] : (T)0; }
 };
 
 // A -> s.A, B -> s.B, a -> s.e
 template <typename T, int NX, int MT, int KIND>
-MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef& st)
+MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef<T>& st)
 {
     constexpr int ld = Ws<T, NX>::ld;
-    using X = Acc<KIND, NX, MT>;
+    using X = Acc<T, KIND, NX, MT>;
     wfor(NX * NX + NX * MT + NX, [&](int idx) {
         if (idx < NX * NX) {
             int i = idx % NX, j = idx / NX;
-            s.A[i + j * ld] = (T)X::A(st, i, j);
+            s.A[i + j * ld] = X::A(st, i, j);
         } else if (idx < NX * NX + NX * MT) {
             int r = idx - NX * NX, i = r % NX, j = r / NX;
-            s.B[i + j * ld] = (T)X::B(st, i, j);
+            s.B[i + j * ld] = X::B(st, i, j);
         } else {
             int i = idx - NX * NX - NX * MT;
-            s.e[i] = (T)X::a(st, i);
+            s.e[i] = X::a(st, i);
         }
     });
 }
@@ -188,12 +210,12 @@ MHE_DEV void chol_solve_reg(const Ws<T, NX>& s, T (&y)[MT])
 // s.Qw = partial Q^_w.  Stores P_{t+1}, chol(G_{t+1}), K_{t+1}, k_{t+1},
 // L_{t+1} (nullptr skips a store).  Returns true on a failed pivot.
 template <typename T, int NX, int MT, int KIND>
-MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef& st, T* Pout, T* Lgout, T* Kout,
+MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout, T* Kout,
                          T* kout, T* Lout, bool want_v, double piv_rel)
 {
     constexpr int ld = Ws<T, NX>::ld;
     constexpr int NT = NX * (NX + 1) / 2, MTT = MT * (MT + 1) / 2;
-    using X = Acc<KIND, NX, MT>;
+    using X = Acc<T, KIND, NX, MT>;
     if (Pout)
         wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
     load_AB<T, NX, MT, KIND>(s, st);
@@ -224,7 +246,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef& st, T* Pout, T* Lgout, T*
         if (idx < NT) {
             int i, j;
             tri_ij(idx, i, j);
-            T acc = (T)X::qx(st, i, j);
+            T acc = X::qx(st, i, j);
 #pragma unroll 8
             for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.Tt[p + j * ld];
             s.P[i + j * ld] = acc;
@@ -232,20 +254,20 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef& st, T* Pout, T* Lgout, T*
         } else if (idx < NT + MTT) {
             int i, j;
             tri_ij(idx - NT, i, j);
-            T acc = (T)X::qw(st, i, j);
+            T acc = X::qw(st, i, j);
 #pragma unroll 8
             for (int p = 0; p < NX; ++p) acc += s.B[p + i * ld] * s.PB[p + j * ld];
             s.G[i + j * ld] = acc;
             s.G[j + i * ld] = acc;
         } else if (idx < NT + MTT + NX * MT) {
             int r = idx - NT - MTT, i = r % NX, j = r / NX;
-            T acc = (T)X::qxw(st, i, j);
+            T acc = X::qxw(st, i, j);
 #pragma unroll 8
             for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.PB[p + j * ld];
             s.H[i + j * ld] = acc;
         } else if (idx < NT + MTT + NX * MT + MT) {
             int j = idx - NT - MTT - NX * MT;
-            T acc = -(T)X::lw(st, j);
+            T acc = -X::lw(st, j);
 #pragma unroll 8
             for (int p = 0; p < NX; ++p) acc += s.B[p + j * ld] * s.u[p];
             s.g[j] = acc;
@@ -306,7 +328,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef& st, T* Pout, T* Lgout, T*
             s.P[j + i * ld] = acc;
         } else if (idx < NT + NX) {
             int i = idx - NT;
-            T acc = s.tv[i] - (T)X::lx(st, i);
+            T acc = s.tv[i] - X::lx(st, i);
 #pragma unroll 8
             for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.g[q];
             s.Psi[i] = acc;
@@ -394,10 +416,10 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef& st, T* Pout, T* Lgout, T*
 template <typename T, int NX, int NW>
 struct Addr {
     // level-0 stage t >= 1 of instance b
-    static MHE_DEV StageRef leaf(const LevelArgs<T>& a, int b, int t)
+    static MHE_DEV StageRef<T> leaf(const LevelArgs<T>& a, int b, int t)
     {
         const long long s = a.in_off[b] + t - 1;
-        StageRef r;
+        StageRef<T> r;
         r.A = a.A + s * NX * NX;
         r.B = a.B + s * NX * NW;
         r.Q = a.Q + s * (NX + NW) * (NX + NW);
@@ -407,18 +429,18 @@ struct Addr {
         r.a = a.a ? a.a + s * NX : nullptr;
         return r;
     }
-    static MHE_DEV StageRef arrival(const LevelArgs<T>& a, int b)
+    static MHE_DEV StageRef<T> arrival(const LevelArgs<T>& a, int b)
     {
-        StageRef r;
+        StageRef<T> r;
         r.A = r.B = r.Q = r.Qx = nullptr;
         r.Qw0 = a.P0inv + (long long)b * NX * NX;
         r.l = a.l0 ? a.l0 + (long long)b * 2 * NX : nullptr;
         r.a = a.a0 ? a.a0 + (long long)b * NX : nullptr;
         return r;
     }
-    static MHE_DEV StageRef upper(const LevelArgs<T>& a, long long g)
+    static MHE_DEV StageRef<T> upper(const LevelArgs<T>& a, long long g)
     {
-        StageRef r;
+        StageRef<T> r;
         r.A = a.Ah + g * NX * NX;
         r.B = a.Bh + g * NX * NX;
         r.Q = nullptr;
@@ -442,16 +464,16 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
     const bool top = (cd.flags & CH_TOP) != 0;
     Ws<T, NX> s;
     s.carve(smem);
-    const double* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;   // level 0: Q_{x,N} = 0
-    const double* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
-                             : (a.lN ? a.lN + (long long)b * NX : nullptr);
+    const T* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;   // level 0: Q_{x,N} = 0
+    const T* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
+                        : (a.lN ? a.lN + (long long)b * NX : nullptr);
     wfor(NX * NX, [&](int idx) {
         int i = idx % NX, j = idx / NX;
-        s.P[i + j * ld] = (last && QN) ? (T)QN[idx] : (T)0;
+        s.P[i + j * ld] = (last && QN) ? QN[idx] : (T)0;
         s.V[i + j * ld] = (T)(i == j ? 1 : 0);
         s.Qw[i + j * ld] = 0;
         if (idx < NX) {
-            s.Psi[idx] = (last && lN) ? (T)(-lN[idx]) : (T)0;
+            s.Psi[idx] = (last && lN) ? -lN[idx] : (T)0;
             s.v[idx] = 0;
         }
     });
@@ -488,18 +510,18 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
         const long long gp = cd.parent;
         wfor(NX * NX, [&](int idx) {
             int i = idx % NX, j = idx / NX;
-            a.Ah_up[gp * NX * NX + idx] = (double)s.V[j + i * ld];
-            a.Bh_up[gp * NX * NX + idx] = i >= j ? (double)s.Qw[i + j * ld] : 0.0;
-            a.Qxh_up[gp * NX * NX + idx] = (double)s.P[i + j * ld];
+            a.Ah_up[gp * NX * NX + idx] = s.V[j + i * ld];
+            a.Bh_up[gp * NX * NX + idx] = i >= j ? s.Qw[i + j * ld] : (T)0;
+            a.Qxh_up[gp * NX * NX + idx] = s.P[i + j * ld];
             if (idx < NX) {
-                a.ah_up[gp * NX + idx] = (double)s.v[idx];
-                a.lxh_up[gp * NX + idx] = -(double)s.Psi[idx];
+                a.ah_up[gp * NX + idx] = s.v[idx];
+                a.lxh_up[gp * NX + idx] = -s.Psi[idx];
             }
         });
     } else if (!top) {
         wfor(NX * NX, [&](int idx) {
-            a.QN_up[(long long)b * NX * NX + idx] = (double)s.P[idx % NX + (idx / NX) * ld];
-            if (idx < NX) a.lN_up[(long long)b * NX + idx] = -(double)s.Psi[idx];
+            a.QN_up[(long long)b * NX * NX + idx] = s.P[idx % NX + (idx / NX) * ld];
+            if (idx < NX) a.lN_up[(long long)b * NX + idx] = -s.Psi[idx];
         });
     }
     if (bad_t >= 0) wone([&](int) { record_error(a.status, a.where, b, -3, a.level, ci, bad_t); });
@@ -508,11 +530,11 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
 // ---- the vector part of Algorithm 4 with stored factors -----------------------
 
 template <typename T, int NX, int MT, int KIND>
-MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef& st, const T* Pin, const T* Lgin,
+MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Pin, const T* Lgin,
                       const T* Kin, T* kout)
 {
     constexpr int ld = Ws<T, NX>::ld;
-    using X = Acc<KIND, NX, MT>;
+    using X = Acc<T, KIND, NX, MT>;
     load_AB<T, NX, MT, KIND>(s, st);
     wfor(MT * MT + MT * NX + NX, [&](int idx) {
         if (idx < MT * MT) {
@@ -530,7 +552,7 @@ MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef& st, const T* Pin, const T* L
     });
     wfor(MT + NX, [&](int idx) {
         if (idx < MT) {
-            T acc = -(T)X::lw(st, idx);
+            T acc = -X::lw(st, idx);
 #pragma unroll 8
             for (int p = 0; p < NX; ++p) acc += s.B[p + idx * ld] * s.u[p];
             s.g[idx] = acc;
@@ -554,7 +576,7 @@ MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef& st, const T* Pin, const T* L
         }
     });
     wfor(NX, [&](int i) {
-        T acc = s.tv[i] - (T)X::lx(st, i);
+        T acc = s.tv[i] - X::lx(st, i);
 #pragma unroll 8
         for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.g[q];
         s.Psi[i] = acc;
@@ -563,9 +585,9 @@ MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef& st, const T* Pin, const T* L
 
 // closed-loop step x <- A x + B (K x + k) + a, x in s.e (in), result in s.u
 template <typename T, int NX, int MT, int KIND>
-MHE_DEV void closed_loop_step(Ws<T, NX>& s, const StageRef& st, const T* Kin, const T* kin)
+MHE_DEV void closed_loop_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin, const T* kin)
 {
-    using X = Acc<KIND, NX, MT>;
+    using X = Acc<T, KIND, NX, MT>;
     wfor(MT, [&](int j) {
         T acc = kin[j];
 #pragma unroll 8
@@ -573,11 +595,11 @@ MHE_DEV void closed_loop_step(Ws<T, NX>& s, const StageRef& st, const T* Kin, co
         s.tmp[j] = acc;
     });
     wfor(NX, [&](int i) {
-        T acc = (T)X::a(st, i);
+        T acc = X::a(st, i);
 #pragma unroll 8
-        for (int j = 0; j < NX; ++j) acc += (T)X::A(st, i, j) * s.e[j];
+        for (int j = 0; j < NX; ++j) acc += X::A(st, i, j) * s.e[j];
 #pragma unroll 8
-        for (int j = 0; j < MT; ++j) acc += (T)X::B(st, i, j) * s.tmp[j];
+        for (int j = 0; j < MT; ++j) acc += X::B(st, i, j) * s.tmp[j];
         s.u[i] = acc;
     });
     wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
@@ -592,10 +614,10 @@ MHE_DEV void rhs_chunk(const LevelArgs<T>& a, int ci, T* smem)
     const bool last = (cd.flags & CH_LAST) != 0;
     const bool top = (cd.flags & CH_TOP) != 0;
     Ws<T, NX> s;
-    s.carve(smem);
-    const double* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
-                             : (a.lN ? a.lN + (long long)b * NX : nullptr);
-    wfor(NX, [&](int i) { s.Psi[i] = (last && lN) ? (T)(-lN[i]) : (T)0; });
+    s.carve_rhs(smem);
+    const T* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
+                        : (a.lN ? a.lN + (long long)b * NX : nullptr);
+    wfor(NX, [&](int i) { s.Psi[i] = (last && lN) ? -lN[i] : (T)0; });
     for (int tt = cd.len - 1; tt >= 0; --tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
@@ -629,21 +651,21 @@ MHE_DEV void rhs_chunk(const LevelArgs<T>& a, int ci, T* smem)
         }
         const long long gp = cd.parent;
         wfor(NX, [&](int i) {
-            a.ah_up[gp * NX + i] = (double)s.e[i];
-            a.lxh_up[gp * NX + i] = -(double)s.Psi[i];
+            a.ah_up[gp * NX + i] = s.e[i];
+            a.lxh_up[gp * NX + i] = -s.Psi[i];
         });
     } else if (!top) {
-        wfor(NX, [&](int i) { a.lN_up[(long long)b * NX + i] = -(double)s.Psi[i]; });
+        wfor(NX, [&](int i) { a.lN_up[(long long)b * NX + i] = -s.Psi[i]; });
     }
 }
 
 // ---- down pass ---------------------------------------------------------------
 
 template <typename T, int NX, int MT, int KIND>
-MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef& st, const T* Kin, const T* kin,
-                           const T* Lin, bool use_wh, double* xo, double* wo)
+MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin, const T* kin,
+                           const T* Lin, bool use_wh, T* xo, T* wo)
 {
-    using X = Acc<KIND, NX, MT>;
+    using X = Acc<T, KIND, NX, MT>;
     // x_t in s.e, w^ in s.v
     wfor(MT + NX, [&](int idx) {
         if (idx < MT) {
@@ -656,47 +678,48 @@ MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef& st, const T* Kin, const
                 for (int i = 0; i < NX; ++i) acc -= Lin[j + i * MT] * s.v[i];
             }
             s.tmp[j] = acc;
-            wo[j] = (double)acc;
+            wo[j] = acc;
         } else {
-            xo[idx - MT] = (double)s.e[idx - MT];
+            xo[idx - MT] = s.e[idx - MT];
         }
     });
     wfor(NX, [&](int i) {
-        T acc = (T)X::a(st, i);
+        T acc = X::a(st, i);
 #pragma unroll 8
-        for (int j = 0; j < NX; ++j) acc += (T)X::A(st, i, j) * s.e[j];
+        for (int j = 0; j < NX; ++j) acc += X::A(st, i, j) * s.e[j];
 #pragma unroll 8
-        for (int j = 0; j < MT; ++j) acc += (T)X::B(st, i, j) * s.tmp[j];
+        for (int j = 0; j < MT; ++j) acc += X::B(st, i, j) * s.tmp[j];
         s.u[i] = acc;
     });
     wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
 }
 
-// lambda_t = Q_x x_t + Q_xw w_t + l_x + A^T lambda_{t+1}  (lambda_{t+1} in s.Psi -> result in s.Psi)
+// lambda_t = Q_x x_t + Q_xw w_t + l_x + A^T lambda_{t+1}  (lambda_{t+1} in s.Psi -> result in s.Psi);
+// with FP64 targets z given, z += (x_t, w_t, lambda_t)
 template <typename T, int NX, int MT, int KIND>
-MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef& st, const double* xt, const double* wt,
-                           double* lo, double* zx, double* zw, double* zl)
+MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* xt, const T* wt, T* lo,
+                           double* zx, double* zw, double* zl)
 {
-    using X = Acc<KIND, NX, MT>;
+    using X = Acc<T, KIND, NX, MT>;
     wfor(NX, [&](int i) {
-        T acc = (T)X::lx(st, i);
+        T acc = X::lx(st, i);
 #pragma unroll 8
-        for (int j = 0; j < NX; ++j) acc += (T)X::qx(st, i, j) * (T)xt[j];
+        for (int j = 0; j < NX; ++j) acc += X::qx(st, i, j) * xt[j];
 #pragma unroll 8
-        for (int j = 0; j < MT; ++j) acc += (T)X::qxw(st, i, j) * (T)wt[j];
+        for (int j = 0; j < MT; ++j) acc += X::qxw(st, i, j) * wt[j];
 #pragma unroll 8
-        for (int j = 0; j < NX; ++j) acc += (T)X::A(st, j, i) * s.Psi[j];
+        for (int j = 0; j < NX; ++j) acc += X::A(st, j, i) * s.Psi[j];
         s.u[i] = acc;
     });
     wfor(NX + (zx ? NX + MT : 0), [&](int idx) {
         if (idx < NX) {
             s.Psi[idx] = s.u[idx];
-            lo[idx] = (double)s.u[idx];
+            lo[idx] = s.u[idx];
             if (zl) zl[idx] += (double)s.u[idx];
         } else if (idx < 2 * NX) {
-            zx[idx - NX] += xt[idx - NX];
+            zx[idx - NX] += (double)xt[idx - NX];
         } else {
-            zw[idx - 2 * NX] += wt[idx - 2 * NX];
+            zw[idx - 2 * NX] += (double)wt[idx - 2 * NX];
         }
     });
 }
@@ -710,28 +733,28 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     const bool last = (cd.flags & CH_LAST) != 0;
     const bool top = (cd.flags & CH_TOP) != 0;
     Ws<T, NX> s;
-    s.carve(smem);
+    s.carve_vectors(smem);
     const LevelInst li = a.li[b];
     // x^_i -> s.e, w^_i -> s.v, lambda^_{i+1} -> s.Psi
     wfor(NX, [&](int i) {
-        s.e[i] = top ? (T)a.x0[(long long)b * NX + i] : (T)a.xd_up[cd.px * NX + i];
-        s.v[i] = last ? (T)0 : (T)a.wd_up[cd.parent * NX + i];
-        s.Psi[i] = last ? (T)0 : (T)a.ld_up[(cd.px + 1) * NX + i];
+        s.e[i] = top ? a.x0[(long long)b * NX + i] : a.xd_up[cd.px * NX + i];
+        s.v[i] = last ? (T)0 : a.wd_up[cd.parent * NX + i];
+        s.Psi[i] = last ? (T)0 : a.ld_up[(cd.px + 1) * NX + i];
     });
     if (!last) {
         // the parent solved for w^' = R w^ (square-root master stage): w^ = R^{-1} w^'
-        const double* Lq = a.Bh_up + cd.parent * NX * NX;   // R^T, lower triangular
+        const T* Lq = a.Bh_up + cd.parent * NX * NX;   // R^T, lower triangular
         wone([&](int) {
             for (int i = NX - 1; i >= 0; --i) {
                 T acc = s.v[i];
-                for (int p = i + 1; p < NX; ++p) acc -= (T)Lq[p + i * NX] * s.v[p];
-                s.v[i] = acc / (T)Lq[i + i * NX];
+                for (int p = i + 1; p < NX; ++p) acc -= Lq[p + i * NX] * s.v[p];
+                s.v[i] = acc / Lq[i + i * NX];
             }
         });
     }
-    auto xo = [&](int t) -> double* { return a.xd + (li.gx + t) * NX; };
-    auto lo = [&](int t) -> double* { return a.ld + (li.gx + t) * NX; };
-    auto wo = [&](int t) -> double* {
+    auto xo = [&](int t) -> T* { return a.xd + (li.gx + t) * NX; };
+    auto lo = [&](int t) -> T* { return a.ld + (li.gx + t) * NX; };
+    auto wo = [&](int t) -> T* {
         if (UPPER) return a.wd + (li.gs + t) * NX;
         return a.wd + a.w_off[b] + (t == 0 ? 0 : NX + (long long)(t - 1) * NW);
     };
@@ -757,18 +780,18 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     const int t1 = cd.t0 + cd.len;
     if (last) {
         // lambda_N = Q_{x,N} x_N + l_N (Q_{x,N} = 0 at level 0)
-        const double* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;
-        const double* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
-                                 : (a.lN ? a.lN + (long long)b * NX : nullptr);
+        const T* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;
+        const T* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
+                            : (a.lN ? a.lN + (long long)b * NX : nullptr);
         wfor(NX, [&](int i) {
-            T acc = lN ? (T)lN[i] : (T)0;
+            T acc = lN ? lN[i] : (T)0;
             if (QN) {
 #pragma unroll 8
-                for (int j = 0; j < NX; ++j) acc += (T)QN[i + j * NX] * s.e[j];
+                for (int j = 0; j < NX; ++j) acc += QN[i + j * NX] * s.e[j];
             }
             s.Psi[i] = acc;
-            xo(t1)[i] = (double)s.e[i];
-            lo(t1)[i] = (double)acc;
+            xo(t1)[i] = s.e[i];
+            lo(t1)[i] = acc;
             if (a.zx) {
                 zxo(t1)[i] += (double)s.e[i];
                 zlo(t1)[i] += (double)acc;

@@ -50,6 +50,29 @@ MHE_DEV void record_error(int* status, int* where, int inst, int code, int level
     }
 }
 
+// |v| as the bit pattern of a non-negative double: unsigned comparison of these
+// orders them like the values (NaN above infinity), so maxima need no FP64 work
+MHE_DEV unsigned long long abs_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// |v| rounded towards zero to float, from the bit pattern alone (integer
+// operations; flushes below FLT_MIN to 0 and saturates at FLT_MAX) -- enough
+// for norms, and it keeps the FP64 pipe free
+MHE_DEV float abs_to_float(double v)
+{
+    const unsigned long long b = abs_bits(v);
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e <= 0) return 0.f;
+    if (e >= 255) return 3.4028234e38f;
+    return __uint_as_float(((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffULL));
+}
+
+MHE_DEV void atomic_max_u64(unsigned long long* addr, unsigned long long v) { atomicMax(addr, v); }
+MHE_DEV void atomic_max_u32(unsigned int* addr, unsigned int v) { atomicMax(addr, v); }
+MHE_DEV unsigned int float_bits(float v) { return __float_as_uint(v); }
+
 // max of non-negative doubles through their bit patterns (ordered like the values)
 MHE_DEV void atomic_max_nonneg(double* addr, double v)
 {

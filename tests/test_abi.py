@@ -39,11 +39,14 @@ def test_workspace_bytes_host_only(L):
     b64 = mhe.mhe_workspace_bytes(d)
     d32, _ = mhe.make_dims(20, 10, [131072], prec=mhe.MHE_FP32_IR, leaf_len=16, branching=8, top_len=4)
     b32 = mhe.mhe_workspace_bytes(d32)
-    # stored factors per stage: P n^2, chol G m^2, K and L m n, k m  (FP64: 8 bytes)
-    per_stage = (400 + 100 + 200 + 200 + 10) * 8
-    assert b64 > 131072 * per_stage
-    assert b32 < b64
-    assert b64 < 4 * 131072 * per_stage
+    # stored factors per stage: P n^2, chol G m^2, K and L m n, k m
+    per_stage = 400 + 100 + 200 + 200 + 10
+    assert b64 > 131072 * per_stage * 8
+    assert b64 < 4 * 131072 * per_stage * 8
+    # FP32 mode: the factors in FP32 plus FP32 copies of A, B, Q (n^2 + nm + (n+m)^2 per stage)
+    copies = 131071 * (400 + 200 + 900) * 4
+    assert b32 > 131072 * per_stage * 4 + copies
+    assert b32 < 4 * 131072 * per_stage * 4 + 2 * copies
 
 
 def test_bad_dims_rejected_on_host(L):
