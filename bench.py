@@ -194,13 +194,29 @@ def run_gpu(args):
         bk["dev"] = to_device(bk)
     gen_s = time.time() - t0
     refine_tol = 1e-9
-    solvers, serial = [], []
+    solvers, plans = [], []
+    t_tune = time.time()
     for bk in buckets:
+        plan = dict(leaf_len=16 if prec == 0 else 8, branching=8 if prec == 0 else 4, top_len=4)
+        if args.autotune:
+            # the library's autotuner on the first instances of the bucket (a contiguous prefix)
+            d = bk["dev"]
+            k = min(len(bk["N"]), args.tune_instances)
+            S = int(np.sum(bk["N"][:k] - 1))
+            n, m = bk["n"], bk["m"]
+            dims, _keep = mhe.make_dims(n, m, bk["N"][:k], prec, 0, 0, 0, refine_tol, 8 if prec == 1 else 2)
+            if d["S"] > 0:
+                mhe.mhe_assemble(n, m, bk["q"], d["C"], d["R"], d["yt"], d["wt"], d["Q"], d["l"])
+            r = mhe.mhe_autotune(dims, d["A"][:S].contiguous(), d["B"][:S].contiguous(), d["Q"][:S].contiguous(),
+                                 d["P0inv"][:k].contiguous(), d["l"][:S].contiguous(), d["a"][:S].contiguous(),
+                                 d["x0"][:k * n].contiguous())
+            plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"])
+        plans.append(dict(nx=bk["n"], **plan))
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=prec, refine_tol=refine_tol,
-                       max_refine=8 if prec == 1 else 2,
-                       leaf_len=16 if prec == 0 else 8, branching=8 if prec == 0 else 4, top_len=4)
+                       max_refine=8 if prec == 1 else 2, **plan)
         s.out = s.outputs()
         solvers.append(s)
+    tune_s = time.time() - t_tune
     stream = torch.cuda.current_stream()
 
     def step(ss, timing=False):
@@ -303,7 +319,8 @@ def run_gpu(args):
     line = dict(metric=METRIC, value=round(value, 3), unit="KKT solves/s", n_gpus=1, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(ms, 4), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f32+f64" if prec == 1 else "f64", data="synthetic",
-                config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, generation_s=round(gen_s, 1)),
+                config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, generation_s=round(gen_s, 1),
+                            plans=plans, autotune_s=round(tune_s, 1)),
                 latency_ms=dict(p50=round(statistics.median(step_ms), 4), p99=round(p99, 4),
                                 note="one step solves every instance; latency = step time"),
                 relres_max=relres_max, all_ok=ok,
@@ -447,6 +464,8 @@ def main():
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--tune-instances", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

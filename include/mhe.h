@@ -145,6 +145,16 @@ int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const dou
  * nx_out / nw_out and returns the number available. */
 int mhe_shapes(int* nx_out, int* nw_out, int cap);
 
+/* Autotuner for the batch lengths the paper leaves to the user (Section VI,
+ * remark on batch lengths): times candidate plans (leaf_len, branching,
+ * top_len; the serial plan top_len > max N included) of mhe_factor_solve on
+ * the given problem -- leaf_len first, then branching, then top_len, each
+ * the best of `reps` runs after a warm-up, CUDA events on `stream` -- and
+ * writes dims with the fastest plan into *best (time in *best_ms).  Allocates
+ * one context per candidate in turn.  Errors: MHE_E_ARG, MHE_E_NOMEM. */
+int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* rhs, void* stream, int reps,
+                 mhe_dims* best, double* best_ms);
+
 /* Profiling aid: enable = 1 records a pair of CUDA events around every level
  * pass (reduce, right-hand side, down, residual) on the context's stream;
  * enable = 0 stops recording.  No counterpart in the paper, whose Matlab

@@ -335,6 +335,86 @@ int mhe_timing_read(mhe_ctx* ctx, double* out, int cap)
 
 long long mhe_launch_count(mhe_ctx* ctx) { return ctx ? ctx->eng.launches : -1; }
 
+// ---- autotuner ----------------------------------------------------------------
+// Coordinate search over the plan: leaf_len first (branching 4, top_len 4),
+// then branching, then top_len (including the serial plan, top_len >= max N),
+// each candidate timed as the best of `reps` fused factor+solve calls after one
+// warm-up, with CUDA events on the caller's stream.  Candidates whose context
+// cannot be created (memory) are skipped.
+int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* rhs, void* stream, int reps,
+                 mhe_dims* best, double* best_ms)
+{
+    int rc = check_dims(dims);
+    if (rc != MHE_OK) return rc;
+    if (!mats || !rhs || !best) return fail(MHE_E_ARG, "mats, rhs or best is NULL");
+    if (reps < 1) reps = 1;
+    mhe::Plan probe;
+    const char* perr = nullptr;
+    const int min_leaf = (dims->nx + dims->nw - 1) / dims->nw;
+    if (mhe::make_plan(dims->nx, dims->nw, dims->N, dims->batch, min_leaf > 1 ? min_leaf : 2, 2, 1, probe, &perr) != 0)
+        return fail(MHE_E_ARG, perr);
+    const int maxN = probe.max_N;
+    double *x = nullptr, *w = nullptr, *lam = nullptr;
+    if (cudaMalloc(&x, sizeof(double) * probe.X_total * dims->nx) != cudaSuccess ||
+        cudaMalloc(&w, sizeof(double) * (probe.W_total + 1)) != cudaSuccess ||
+        cudaMalloc(&lam, sizeof(double) * probe.X_total * dims->nx) != cudaSuccess) {
+        cudaFree(x); cudaFree(w); cudaFree(lam);
+        cudaGetLastError();
+        return fail(MHE_E_NOMEM, "autotune output buffers");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_plan = [&](int leaf, int br, int top) -> double {
+        mhe_dims d = *dims;
+        d.leaf_len = leaf;
+        d.branching = br;
+        d.top_len = top;
+        mhe_ctx* c = nullptr;
+        if (mhe_create(&d, stream, &c) != MHE_OK) return -1.0;
+        double bestt = -1.0;
+        if (mhe_factor_solve(c, mats, rhs, x, w, lam, nullptr) == MHE_OK) {
+            for (int r = 0; r < reps; ++r) {
+                cudaEventRecord(e0, (cudaStream_t)stream);
+                mhe_factor_solve(c, mats, rhs, x, w, lam, nullptr);
+                cudaEventRecord(e1, (cudaStream_t)stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (bestt < 0 || ms < bestt) bestt = ms;
+            }
+        }
+        mhe_destroy(c);
+        return bestt;
+    };
+    int bl = min_leaf > 8 ? min_leaf : 8, bb = 4, bt = 4;
+    double bms = time_plan(bl, bb, bt);
+    for (int leaf : {4, 8, 16, 32, 64}) {
+        if (leaf < min_leaf || leaf == bl) continue;
+        double t = time_plan(leaf, bb, bt);
+        if (t > 0 && (bms < 0 || t < bms)) { bms = t; bl = leaf; }
+    }
+    for (int br : {2, 8, 16}) {
+        double t = time_plan(bl, br, bt);
+        if (t > 0 && (bms < 0 || t < bms)) { bms = t; bb = br; }
+    }
+    for (int top : {1, 16, 64, 256, maxN + 1}) {
+        if (top == bt) continue;
+        double t = time_plan(bl, bb, top);
+        if (t > 0 && (bms < 0 || t < bms)) { bms = t; bt = top; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x); cudaFree(w); cudaFree(lam);
+    *best = *dims;
+    best->leaf_len = bl;
+    best->branching = bb;
+    best->top_len = bt;
+    if (best_ms) *best_ms = bms;
+    if (bms < 0) return fail(MHE_E_NOMEM, "no candidate plan could run");
+    return MHE_OK;
+}
+
 int mhe_plan_info(mhe_ctx* ctx, long long* out, int cap)
 {
     if (!ctx || (!out && cap > 0)) return fail(MHE_E_ARG, "ctx or out is NULL");

@@ -86,6 +86,9 @@ def _declare(L):
     L.mhe_assemble_count.restype = c_ll
     L.mhe_solve_serial_noalloc.argtypes = [c_int, c_int, c_int] + [c_void_p] * 12
     L.mhe_solve_serial_noalloc.restype = c_int
+    L.mhe_autotune.argtypes = [P(mhe_dims), P(mhe_matrices), P(mhe_rhs), c_void_p, c_int, P(mhe_dims),
+                               P(c_double)]
+    L.mhe_autotune.restype = c_int
     L.mhe_last_error.argtypes = []
     L.mhe_last_error.restype = ctypes.c_char_p
     return L
@@ -204,6 +207,17 @@ def mhe_solve_serial_noalloc(nx, nw, N, A, B, Q, P0inv, l, a, x0, x, w, lam, sta
                                                  _ptr(P0inv), _ptr(l), _ptr(a), _ptr(x0), _ptr(x), _ptr(w),
                                                  _ptr(lam), sp, _stream(stream)),
                   "mhe_solve_serial_noalloc")
+
+
+def mhe_autotune(dims, A, B, Q, P0inv, l, a, x0, reps=2, stream=None):
+    """Fastest plan (leaf_len, branching, top_len) for this problem and its time in ms."""
+    m = mhe_matrices(_ptr(A), _ptr(B), _ptr(Q), _ptr(P0inv))
+    r = mhe_rhs(_ptr(l), _ptr(a), _ptr(x0))
+    best = mhe_dims()
+    ms = c_double()
+    _check(lib().mhe_autotune(ctypes.byref(dims), ctypes.byref(m), ctypes.byref(r), _stream(stream), int(reps),
+                              ctypes.byref(best), ctypes.byref(ms)), "mhe_autotune")
+    return dict(leaf_len=best.leaf_len, branching=best.branching, top_len=best.top_len, ms=ms.value)
 
 
 def mhe_launch_count(ctx):

@@ -149,3 +149,17 @@ def test_non_pd_stage_is_reported():
     assert info["status"][0] == -3
     assert info["stage"][0] == 11
     s.close()
+
+
+def test_autotuner_returns_a_working_plan():
+    insts = [synth.mhe_instance(300 + i, 6, 3, 3, N) for i, N in enumerate([40, 90, 130, 257])]
+    d = device_inputs(insts)
+    dims, _keep = mhe.make_dims(6, 3, d["N"], mhe.MHE_FP64)
+    best = mhe.mhe_autotune(dims, d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], reps=1)
+    assert best["ms"] > 0
+    assert best["leaf_len"] * 3 >= 6 and best["branching"] >= 2 and best["top_len"] >= 1
+    sols, info = _run(insts, prec=mhe.MHE_FP64, leaf_len=best["leaf_len"], branching=best["branching"],
+                      top_len=best["top_len"])
+    ref = _oracle(insts)
+    for b in range(len(insts)):
+        assert rel_err(sols[b], ref[b]) <= 1e-10
