@@ -155,6 +155,43 @@ int mhe_shapes(int* nx_out, int* nw_out, int cap);
 int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* rhs, void* stream, int reps,
                  mhe_dims* best, double* best_ms);
 
+/* ---- serving: continuous batching of receding-horizon MHE requests ----
+ * One MHE stage is passed packed, host FP64, column-major blocks:
+ *   [A (nx*nx) | B (nx*nw) | C (ny*nx) | R ((nw+ny)^2) | a (nx) | y~ (ny) | w~ (nw)]. */
+typedef struct mhe_server mhe_server;
+
+/* A server on the current device with a device-memory budget for estimator
+ * windows and workspaces (admission control), the precision of its solves,
+ * and the refinement target.  Starts one worker thread. */
+int mhe_server_create(size_t device_bytes, int prec, double refine_tol, int max_refine, mhe_server** out);
+
+/* Admit an estimator with horizon N >= 3 (UFTOC; N-1 measured stages): its
+ * initial window of N-1 stages (host arrays, stage-major, the field layouts
+ * of the packed stage above), arrival state x~0 and weight P~0^{-1}.  The
+ * window is assembled (Section II) and kept on the device.  Returns
+ * MHE_E_ADMISSION when the budget cannot hold it. */
+int mhe_estimator_open(mhe_server* s, int nx, int nw, int ny, int N, const double* A, const double* B,
+                       const double* C, const double* R, const double* a, const double* yt, const double* wt,
+                       const double* x0, const double* P0inv, int* id_out);
+
+/* Queue one request: shift estimator `est`'s window by one sample with the
+ * new packed stage (copied before return).  The arrival state becomes the
+ * previous solution's estimate of the new first state (UFTOC x_2; the given
+ * x~0 before the first solve).  Thread-safe. */
+int mhe_submit(mhe_server* s, int est, const double* stage, unsigned long long* ticket);
+
+/* MHE_PENDING until the request's round has finished; then writes the
+ * estimate of the newest measured state (UFTOC x_{N-1}, nx doubles, host),
+ * its mhe_info and the latency from submission to completion in seconds,
+ * releases the ticket and returns the request's status. */
+int mhe_poll(mhe_server* s, unsigned long long ticket, double* x_est, mhe_info* info, double* latency_s);
+
+/* Device bytes the server holds. */
+size_t mhe_server_used_bytes(mhe_server* s);
+
+/* Finish the rounds in flight, stop the worker, free everything. */
+int mhe_server_destroy(mhe_server* s);
+
 /* Profiling aid: enable = 1 records a pair of CUDA events around every level
  * pass (reduce, right-hand side, down, residual) on the context's stream;
  * enable = 0 stops recording.  No counterpart in the paper, whose Matlab

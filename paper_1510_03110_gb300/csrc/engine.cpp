@@ -114,11 +114,18 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     const char* e = nullptr;
     int rc = make_plan(d.nx, d.nw, d.N, d.batch, leaf, br, top, plan, &e);
     if (rc != 0) { err = e; return MHE_E_ARG; }
+    this->leaf = leaf;
+    this->br = br;
+    this->topl = top;
     arena_bytes = layout(nullptr);
     arena = rt->alloc(arena_bytes);
     if (!arena) { err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
     layout(static_cast<char*>(arena));
-    // upload the plan tables
+    return upload_plan();
+}
+
+int Engine::upload_plan()
+{
     for (size_t k = 0; k < plan.levels.size(); ++k) {
         const PlanLevel& L = plan.levels[k];
         if (!L.chunks.empty())
@@ -130,6 +137,56 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     rt->copy(gs0, plan.gs0.data(), plan.gs0.size() * sizeof(long long), stream);
     if (rt->sync(stream) != 0) { err = "CUDA error while uploading the plan"; return MHE_E_CUDA; }
     return MHE_OK;
+}
+
+int Engine::replan(const int* N, int batch, const long long* in_off_custom)
+{
+    const char* e = nullptr;
+    Plan p;
+    if (make_plan(plan.n, plan.m, N, batch, leaf, br, topl, p, &e) != 0) { err = e; return MHE_E_ARG; }
+    if (in_off_custom) p.in_off.assign(in_off_custom, in_off_custom + batch);
+    plan = p;
+    factored = false;
+    const size_t need = layout(nullptr);
+    if (need > arena_bytes) {
+        rt->sync(stream);
+        rt->release(arena);
+        arena = rt->alloc(need + need / 4);
+        if (!arena) { arena_bytes = 0; err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
+        arena_bytes = need + need / 4;
+    }
+    layout(static_cast<char*>(arena));
+    return upload_plan();
+}
+
+int Engine::solve_resident(const Resident& r, double* x, double* w, double* lam, mhe_info* info)
+{
+    A = r.A; B = r.B; Q = r.Q; P0inv = r.P0inv;
+    mA = r.At; mB = r.Bt; mQ = r.Qt; mP0 = r.P0t;
+    rt->memset0(status, sizeof(int) * plan.batch, stream);
+    rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
+    KnormArgs kn;
+    kn.batch = plan.batch;
+    kn.nstages = plan.gs0[plan.batch];
+    kn.gs0 = gs0;
+    kn.in_off = in_off;
+    kn.A = A; kn.B = B; kn.Q = Q; kn.P0inv = P0inv;
+    kn.kinf = kinf;
+    rt->memset0(kinf, sizeof(unsigned int) * plan.batch, stream);
+    launches += 1;
+    ops->knorm(kn, stream);
+    mhe_rhs rh;
+    rh.l = r.l; rh.a = r.a; rh.x0 = r.x0;
+    factored = true;
+    if (prec == MHE_FP64) {
+        pass_reduce<double>(r.A, r.B, r.Q, r.P0inv, r.l, r.a);
+        return run_solve<double>(&rh, r.l, r.a, r.x0, x, w, lam, info, true);
+    }
+    pass_reduce<float>(static_cast<const float*>(r.At), static_cast<const float*>(r.Bt),
+                       static_cast<const float*>(r.Qt), static_cast<const float*>(r.P0t),
+                       static_cast<const float*>(r.lt), static_cast<const float*>(r.at));
+    return run_solve<float>(&rh, static_cast<const float*>(r.lt), static_cast<const float*>(r.at),
+                            static_cast<const float*>(r.x0t), x, w, lam, info, true);
 }
 
 void Engine::mark(int phase, int level, int begin)
@@ -306,14 +363,11 @@ void Engine::convert_rhs(const mhe_rhs* rhs)
 }
 
 template <typename T>
-int Engine::run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool fused)
+int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, double* x, double* w, double* lam,
+                      mhe_info* info, bool fused)
 {
     const bool fp64 = sizeof(T) == 8;
-    const T* l = fp64 ? reinterpret_cast<const T*>(rhs->l) : reinterpret_cast<const T*>(l32);
-    const T* a = fp64 ? reinterpret_cast<const T*>(rhs->a) : reinterpret_cast<const T*>(a32);
-    const T* x0 = fp64 ? reinterpret_cast<const T*>(rhs->x0) : reinterpret_cast<const T*>(x0_32);
     active_mask = nullptr;
-    if (!fp64 && !fused) convert_rhs(rhs);
     if (!fused) pass_rhs<T>(l, a, nullptr, nullptr, nullptr);
     if (fp64) {
         pass_down<T>(l, a, nullptr, nullptr, x0, nullptr, reinterpret_cast<T*>(x), reinterpret_cast<T*>(w),
@@ -401,8 +455,9 @@ int Engine::solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_inf
     if (!factored) { err = "mhe_solve before mhe_factor"; return MHE_E_NOT_FACTORED; }
     if (!rhs || !rhs->x0 || (plan.S_in > 0 && (!rhs->l || !rhs->a))) { err = "incomplete right-hand side"; return MHE_E_ARG; }
     if (!x || !w || !lam) { err = "output pointer is NULL"; return MHE_E_ARG; }
-    if (prec == MHE_FP64) return run_solve<double>(rhs, x, w, lam, info, fused);
-    return run_solve<float>(rhs, x, w, lam, info, fused);
+    if (prec == MHE_FP64) return run_solve<double>(rhs, rhs->l, rhs->a, rhs->x0, x, w, lam, info, fused);
+    if (!fused) convert_rhs(rhs);
+    return run_solve<float>(rhs, l32, a32, x0_32, x, w, lam, info, fused);
 }
 
 }  // namespace mhe

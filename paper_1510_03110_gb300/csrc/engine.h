@@ -59,6 +59,14 @@ struct LevelBuf {   // every array of the compute type T
     void *xd = nullptr, *wd = nullptr, *ld = nullptr;
 };
 
+// A problem already resident on the device: FP64 arrays (the residual, and
+// FP64 mode) and the same data in the compute type (FP32 mode; the FP64
+// pointers again in FP64 mode).
+struct Resident {
+    const double *A, *B, *Q, *P0inv, *l, *a, *x0;
+    const void *At, *Bt, *Qt, *P0t, *lt, *at, *x0t;
+};
+
 class Engine {
 public:
     Plan plan;
@@ -97,6 +105,12 @@ public:
     void release();
     int factor(const mhe_matrices& m, const mhe_rhs* rhs, double* x, double* w, double* lam);
     int solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool after_fused);
+    // serving: re-plan this context for a new batch whose caller stages start at
+    // in_off[b] (any offsets into the resident arrays); grows the arena if needed
+    int replan(const int* N, int batch, const long long* in_off_custom);
+    // serving: factor + solve + refinement of a resident problem
+    int solve_resident(const Resident& r, double* x, double* w, double* lam, mhe_info* info);
+    int leaf = 0, br = 0, topl = 0;
     void mark(int phase, int level, int begin);
 
 private:
@@ -110,7 +124,9 @@ private:
     void pass_down(const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x, T* w,
                    T* lam, double* zx, double* zw, double* zl, const int* act);
     template <typename T>
-    int run_solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool skip_first_rhs);
+    int run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, double* x, double* w, double* lam,
+                  mhe_info* info, bool skip_first_rhs);
+    int upload_plan();
     template <typename T>
     void residual(const mhe_rhs* rhs, const double* x, const double* w, const double* lam, const int* act);
     template <typename T>

@@ -89,6 +89,18 @@ def _declare(L):
     L.mhe_autotune.argtypes = [P(mhe_dims), P(mhe_matrices), P(mhe_rhs), c_void_p, c_int, P(mhe_dims),
                                P(c_double)]
     L.mhe_autotune.restype = c_int
+    L.mhe_server_create.argtypes = [ctypes.c_size_t, c_int, c_double, c_int, P(c_void_p)]
+    L.mhe_server_create.restype = c_int
+    L.mhe_estimator_open.argtypes = [c_void_p, c_int, c_int, c_int, c_int] + [c_void_p] * 9 + [P(c_int)]
+    L.mhe_estimator_open.restype = c_int
+    L.mhe_submit.argtypes = [c_void_p, c_int, c_void_p, P(ctypes.c_ulonglong)]
+    L.mhe_submit.restype = c_int
+    L.mhe_poll.argtypes = [c_void_p, ctypes.c_ulonglong, c_void_p, P(mhe_info), P(c_double)]
+    L.mhe_poll.restype = c_int
+    L.mhe_server_used_bytes.argtypes = [c_void_p]
+    L.mhe_server_used_bytes.restype = ctypes.c_size_t
+    L.mhe_server_destroy.argtypes = [c_void_p]
+    L.mhe_server_destroy.restype = c_int
     L.mhe_last_error.argtypes = []
     L.mhe_last_error.restype = ctypes.c_char_p
     return L
@@ -295,6 +307,80 @@ class Solver:
         if self.ctx is not None:
             mhe_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- serving -------------------------------------------------------------------
+
+def pack_stage(A, B, C, R, a, yt, wt):
+    """One MHE stage (math orientation) -> the packed host layout of mhe_submit."""
+    cm = lambda M: np.ascontiguousarray(np.asarray(M, np.float64).T).reshape(-1)  # noqa: E731
+    return np.concatenate([cm(A), cm(B), cm(C), cm(R), np.asarray(a, np.float64).reshape(-1),
+                           np.asarray(yt, np.float64).reshape(-1), np.asarray(wt, np.float64).reshape(-1)])
+
+
+class Server:
+    """Continuous-batching server of receding-horizon MHE estimators (C-ABI mhe_server_*)."""
+
+    def __init__(self, device_bytes, prec=MHE_FP32_IR, refine_tol=0.0, max_refine=-1):
+        self.s = c_void_p()
+        _check(lib().mhe_server_create(int(device_bytes), int(prec), float(refine_tol), int(max_refine),
+                                       ctypes.byref(self.s)), "mhe_server_create")
+        self.nx = {}
+
+    def open(self, p):
+        """Admit an estimator whose initial window is the N-1 stages of p (mhe_instance format)."""
+        cm = lambda X: np.ascontiguousarray(np.swapaxes(np.asarray(X, np.float64), -1, -2))  # noqa: E731
+        arrs = [cm(p["A"]), cm(p["B"]), cm(p["C"]), cm(p["R"]), np.ascontiguousarray(p["a"], np.float64),
+                np.ascontiguousarray(p["yt"], np.float64), np.ascontiguousarray(p["wt"], np.float64),
+                np.ascontiguousarray(p["x0"], np.float64), cm(p["P0inv"])]
+        ptrs = [a.ctypes.data_as(c_void_p) for a in arrs]
+        eid = c_int()
+        _check(lib().mhe_estimator_open(self.s, int(p["n"]), int(p["m"]), int(p["q"]), int(p["N"]), *ptrs,
+                                        ctypes.byref(eid)), "mhe_estimator_open")
+        self.nx[eid.value] = int(p["n"])
+        return eid.value
+
+    def submit(self, est, packed):
+        t = ctypes.c_ulonglong()
+        _check(lib().mhe_submit(self.s, int(est), packed.ctypes.data_as(c_void_p), ctypes.byref(t)), "mhe_submit")
+        return t.value
+
+    def poll(self, ticket, nx):
+        x = np.zeros(nx)
+        info = mhe_info()
+        lat = c_double()
+        rc = lib().mhe_poll(self.s, ctypes.c_ulonglong(ticket), x.ctypes.data_as(c_void_p), ctypes.byref(info),
+                            ctypes.byref(lat))
+        if rc == 1:
+            return None
+        if rc not in (0, -6):
+            raise MheError(rc, "mhe_poll")
+        return dict(x=x, status=rc, relres=info.relres, iters=info.refine_iters, latency=lat.value)
+
+    def wait(self, ticket, nx, timeout=60.0):
+        import time
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket, nx)
+            if r is not None:
+                return r
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} not served within {timeout} s")
+            time.sleep(0.0002)
+
+    def used_bytes(self):
+        return int(lib().mhe_server_used_bytes(self.s))
+
+    def close(self):
+        if self.s:
+            lib().mhe_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

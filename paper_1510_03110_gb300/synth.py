@@ -100,3 +100,39 @@ def bucket_instance(b: dict, j: int) -> dict:
     off = int(np.sum(b["N"][:j] - 1))
     S = int(b["N"][j] - 1)
     return instance_from_pool(b["pool"], b["idx"][off:off + S], b["x0"][j], b["n"], b["m"], b["q"])
+
+
+def plant_stream(seed, n: int, m: int, q: int, length: int, meas_var: float = 0.01) -> dict:
+    """A receding-horizon MHE stream: `length` stages of a simulated plant.
+
+    A_k, B_k, C_k as in stage_pool; W_k = M M^T + 0.1 I (nw x nw), R_k =
+    blkdiag(W_k, (1/meas_var) I) (uncorrelated noises, V = (0.01 I)^{-1});
+    the plant x_{k+1} = A_k x_k + B_k w_k + a_k with w_k ~ N(0, W_k^{-1}),
+    measured y_k = C_k x_k + v_k with v_k ~ N(0, meas_var I); y~_k = y_k,
+    w~_k = 0.  Fields as in stage_pool, plus x_true (length + 1, n)."""
+    rng = np.random.default_rng(seed)
+    A = _spectral_scale(rng.standard_normal((length, n, n)))
+    B = rng.standard_normal((length, n, m))
+    C = rng.standard_normal((length, q, n))
+    Mw = rng.standard_normal((length, m, m))
+    W = Mw @ Mw.transpose(0, 2, 1) + 0.1 * np.eye(m)
+    R = np.zeros((length, m + q, m + q))
+    R[:, :m, :m] = W
+    R[:, m:, m:] = np.eye(q) / meas_var
+    a = 0.1 * rng.standard_normal((length, n))
+    x = np.zeros((length + 1, n))
+    x[0] = rng.standard_normal(n)
+    yt = np.zeros((length, q))
+    for k in range(length):
+        Lw = np.linalg.cholesky(np.linalg.inv(W[k]))
+        w = Lw @ rng.standard_normal(m)
+        yt[k] = C[k] @ x[k] + np.sqrt(meas_var) * rng.standard_normal(q)
+        x[k + 1] = A[k] @ x[k] + B[k] @ w + a[k]
+    return dict(A=A, B=B, C=C, R=R, a=a, yt=yt, wt=np.zeros((length, m)), x_true=x)
+
+
+def window_of(stream: dict, start: int, N: int, x0, n: int, m: int, q: int) -> dict:
+    """The MHE problem over stream stages start .. start+N-2 with arrival x~0 (P~0 = I)."""
+    sl = slice(start, start + N - 1)
+    return dict(n=n, m=m, q=q, N=N, x0=np.asarray(x0, float), P0inv=np.eye(n),
+                **{k: stream[k][sl] for k in ("A", "B", "C", "R", "a", "yt", "wt")})
