@@ -335,6 +335,89 @@ def run_gpu(args):
         s.close()
 
 
+def run_serve(args):
+    """Receding-horizon serving: Poisson arrivals at args.rate requests/s for args.duration s over a pool
+    of estimators (nx ~ U{6,12,24}, nw = ny = nx/2, N ~ U{50,200,1000}); every request shifts one
+    estimator's window by one new stage of its simulated plant (y ~ N(C x, 0.01 I), R = blkdiag(W, 100 I)).
+    Run once with the tree plan and once with the serial plan (top_len above every N)."""
+    import torch
+    from paper_1510_03110_gb300 import build, mhe
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    E = args.estimators
+    nxs = rng.choice(np.array([6, 12, 24]), size=E)
+    Ns = rng.choice(np.array([50, 200, 1000]), size=E)
+    T = args.duration
+    count = int(args.rate * T * 1.05) + 16
+    gaps = rng.exponential(1.0 / args.rate, size=count)
+    t_arr = np.cumsum(gaps)
+    count = int(np.searchsorted(t_arr, T))
+    t_arr = t_arr[:count]
+    who = rng.integers(0, E, size=count)
+    per = np.bincount(who, minlength=E)
+    t0 = time.time()
+    streams = {}
+    for n in (6, 12, 24):
+        ids = np.nonzero(nxs == n)[0]
+        if len(ids) == 0:
+            continue
+        L = int(np.max(Ns[ids] - 1 + per[ids])) + 1
+        ps = synth.plant_streams([5, n], n, n // 2, n // 2, len(ids), L)
+        for j, e in enumerate(ids):
+            streams[int(e)] = synth.stream_of(ps, j)
+    # pre-packed requests in arrival order
+    nxt = np.zeros(E, dtype=np.int64)
+    packed = []
+    for i in range(count):
+        e = int(who[i])
+        st = streams[e]
+        k = int(Ns[e] - 1 + nxt[e])
+        nxt[e] += 1
+        packed.append(mhe.pack_stage(st["A"][k], st["B"][k], st["C"][k], st["R"][k], st["a"][k], st["yt"][k],
+                                     st["wt"][k]))
+    gen_s = time.time() - t0
+    out = {}
+    for plan_name, plan in [("tree", dict(leaf_len=0, branching=0, top_len=0)),
+                            ("serial", dict(leaf_len=0, branching=0, top_len=1 << 20))]:
+        srv = mhe.Server(args.serve_bytes, prec=mhe.MHE_FP32_IR, refine_tol=1e-9)
+        srv.set_plan(**plan)
+        ids = []
+        for e in range(E):
+            n = int(nxs[e])
+            ids.append(srv.open(synth.window_of(streams[e], 0, int(Ns[e]), np.zeros(n), n, n // 2, n // 2)))
+        # warm-up: one request per estimator (engines, workspaces, first rounds)
+        warm = [srv.submit(ids[e], mhe.pack_stage(*(np.asarray(streams[e][f][0]) for f in
+                                                   ("A", "B", "C", "R", "a", "yt", "wt")))) for e in range(E)]
+        for e, tk in enumerate(warm):
+            srv.wait(tk, int(nxs[e]), timeout=120)
+        tickets = []
+        tstart = time.perf_counter()
+        for i in range(count):
+            target = tstart + t_arr[i]
+            while time.perf_counter() < target:
+                pass
+            tickets.append(srv.submit(ids[int(who[i])], packed[i]))
+        t_sub_end = time.perf_counter()
+        lat, bad, relres = [], 0, 0.0
+        for i, tk in enumerate(tickets):
+            r = srv.wait(tk, int(nxs[int(who[i])]), timeout=300)
+            lat.append(r["latency"])
+            bad += r["status"] != 0
+            relres = max(relres, r["relres"])
+        t_end = time.perf_counter()
+        srv.close()
+        lat = np.array(lat)
+        span = max(t_end - tstart, 1e-9)
+        out[plan_name] = dict(solves_per_s=round(count / span, 1), p50_ms=round(1e3 * float(np.median(lat)), 3),
+                              p99_ms=round(1e3 * float(np.quantile(lat, 0.99)), 3),
+                              mean_ms=round(1e3 * float(lat.mean()), 3), requests=count, failed=int(bad),
+                              relres_max=relres, submit_s=round(t_sub_end - tstart, 3), span_s=round(span, 3))
+    return dict(estimators=E, rate=args.rate, duration_s=T, generation_s=round(gen_s, 1),
+                nx="U{6,12,24}", N="U{50,200,1000}", precision="FP32 tree + FP64 refinement, relres<=1e-9",
+                **out)
+
+
 def run_e2e(args, buckets, solvers, step, stream, instances):
     import torch
     from paper_1510_03110_gb300 import mhe
@@ -458,7 +541,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile", "serve"])
+    ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
+    ap.add_argument("--estimators", type=int, default=1024, help="serving: estimator pool")
+    ap.add_argument("--serve-bytes", type=int, default=96 << 30, help="serving: device-memory budget")
     ap.add_argument("--no-baseline", action="store_true", help="skip the serial-plan GPU baseline")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
@@ -469,6 +556,19 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        res = run_serve(args)
+        tree, ser = res["tree"], res["serial"]
+        print(json.dumps(dict(metric=METRIC, value=tree["solves_per_s"], unit="KKT solves/s", n_gpus=1,
+                              steps=tree["requests"], warmup=1, ms_per_step=tree["mean_ms"], higher_is_better=True,
+                              scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic",
+                              config=dict(workload="receding-horizon serving, Poisson arrivals", **{
+                                  k: v for k, v in res.items() if k not in ("tree", "serial")}),
+                              latency_ms=dict(p50=tree["p50_ms"], p99=tree["p99_ms"]),
+                              serving=res, speedup_vs_serial=dict(
+                                  solves_per_s=round(tree["solves_per_s"] / max(ser["solves_per_s"], 1e-9), 3),
+                                  p99=round(ser["p99_ms"] / max(tree["p99_ms"], 1e-9), 3)))))
+        return
     if args.gpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
         # replicas only: every rank solves its own copy of the workload
         rank = int(os.environ.get("RANK", "0"))

@@ -176,6 +176,7 @@ struct Bucket {
 
 struct mhe_server {
     int prec = MHE_FP32_IR;
+    int leaf_len = 0, branching = 0, top_len = 0;   // plan of every round (0: automatic)
     size_t budget = 0, used = 0;
     double refine_tol = 1e-9;
     int max_refine = 8;
@@ -347,7 +348,7 @@ int launch_round(mhe_server* s, Bucket& bk, Bucket::Slot& sl)
         mhe_dims d;
         memset(&d, 0, sizeof(d));
         d.nx = n; d.nw = m; d.batch = batch; d.N = Nv.data(); d.prec = s->prec;
-        d.leaf_len = 0; d.branching = 0; d.top_len = 0;
+        d.leaf_len = s->leaf_len; d.branching = s->branching; d.top_len = s->top_len;
         d.refine_tol = s->refine_tol; d.max_refine = s->max_refine;
         int rc = sl.eng.init(d, &bk.shape->ops, mhe::cuda_runtime(), sl.stream);
         if (rc != MHE_OK) return rc;
@@ -645,6 +646,25 @@ int mhe_poll(mhe_server* s, unsigned long long ticket, double* x_est, mhe_info* 
 }
 
 size_t mhe_server_used_bytes(mhe_server* s) { return s ? s->used : 0; }
+
+int mhe_server_set_plan(mhe_server* s, int leaf_len, int branching, int top_len)
+{
+    if (!s || leaf_len < 0 || branching < 0 || top_len < 0) {
+        mhe::set_last_error("bad arguments to mhe_server_set_plan");
+        return MHE_E_ARG;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto& b : s->buckets)
+        for (auto& sl : b->slot)
+            if (sl.ready || sl.busy) {
+                mhe::set_last_error("mhe_server_set_plan must precede the first request");
+                return MHE_E_ARG;
+            }
+    s->leaf_len = leaf_len;
+    s->branching = branching;
+    s->top_len = top_len;
+    return MHE_OK;
+}
 
 int mhe_server_destroy(mhe_server* s)
 {

@@ -97,6 +97,8 @@ def _declare(L):
     L.mhe_submit.restype = c_int
     L.mhe_poll.argtypes = [c_void_p, ctypes.c_ulonglong, c_void_p, P(mhe_info), P(c_double)]
     L.mhe_poll.restype = c_int
+    L.mhe_server_set_plan.argtypes = [c_void_p, c_int, c_int, c_int]
+    L.mhe_server_set_plan.restype = c_int
     L.mhe_server_used_bytes.argtypes = [c_void_p]
     L.mhe_server_used_bytes.restype = ctypes.c_size_t
     L.mhe_server_destroy.argtypes = [c_void_p]
@@ -373,6 +375,9 @@ class Server:
             if time.time() - t0 > timeout:
                 raise TimeoutError(f"ticket {ticket} not served within {timeout} s")
             time.sleep(0.0002)
+
+    def set_plan(self, leaf_len=0, branching=0, top_len=0):
+        _check(lib().mhe_server_set_plan(self.s, int(leaf_len), int(branching), int(top_len)), "mhe_server_set_plan")
 
     def used_bytes(self):
         return int(lib().mhe_server_used_bytes(self.s))

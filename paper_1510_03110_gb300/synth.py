@@ -136,3 +136,39 @@ def window_of(stream: dict, start: int, N: int, x0, n: int, m: int, q: int) -> d
     sl = slice(start, start + N - 1)
     return dict(n=n, m=m, q=q, N=N, x0=np.asarray(x0, float), P0inv=np.eye(n),
                 **{k: stream[k][sl] for k in ("A", "B", "C", "R", "a", "yt", "wt")})
+
+
+def plant_streams(seed, n: int, m: int, q: int, E: int, length: int, meas_var: float = 0.01,
+                  pool_size: int = 1 << 14) -> dict:
+    """E simulated plants of one shape, `length` stages each, vectorised over the
+    plants; A_k, B_k, C_k, W_k drawn from a seeded pool (construction as in
+    plant_stream), the plants' noises and measurements drawn per stage."""
+    rng = np.random.default_rng(seed)
+    P = pool_size
+    A = _spectral_scale(rng.standard_normal((P, n, n)))
+    B = rng.standard_normal((P, n, m))
+    C = rng.standard_normal((P, q, n))
+    Mw = rng.standard_normal((P, m, m))
+    W = Mw @ Mw.transpose(0, 2, 1) + 0.1 * np.eye(m)
+    Lw = np.linalg.cholesky(np.linalg.inv(W))
+    a = 0.1 * rng.standard_normal((P, n))
+    idx = rng.integers(0, P, size=(E, length))
+    x = rng.standard_normal((E, n))
+    yt = np.zeros((E, length, q))
+    for k in range(length):
+        i = idx[:, k]
+        w = np.einsum("eij,ej->ei", Lw[i], rng.standard_normal((E, m)))
+        yt[:, k] = np.einsum("eij,ej->ei", C[i], x) + np.sqrt(meas_var) * rng.standard_normal((E, q))
+        x = np.einsum("eij,ej->ei", A[i], x) + np.einsum("eij,ej->ei", B[i], w) + a[i]
+    R = np.zeros((P, m + q, m + q))
+    R[:, :m, :m] = W
+    R[:, m:, m:] = np.eye(q) / meas_var
+    return dict(pool=dict(A=A, B=B, C=C, R=R, a=a), idx=idx, yt=yt, wt=np.zeros(m))
+
+
+def stream_of(ps: dict, e: int) -> dict:
+    """Plant e of plant_streams as a plant_stream-style dict."""
+    i = ps["idx"][e]
+    L = len(i)
+    return dict(A=ps["pool"]["A"][i], B=ps["pool"]["B"][i], C=ps["pool"]["C"][i], R=ps["pool"]["R"][i],
+                a=ps["pool"]["a"][i], yt=ps["yt"][e], wt=np.zeros((L, len(ps["wt"]))))
