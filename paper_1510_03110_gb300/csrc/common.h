@@ -45,8 +45,11 @@ struct LevelArgs {
     const T *A, *B, *Q, *P0inv;
     const long long* in_off;
     const long long* w_off;        // caller w offset of instance b (w_0 has n entries)
-    // right-hand side of level 0 (l0, a0, lN per instance; nullptr means zero)
+    // right-hand side of level 0 (l0, a0, lN per instance; nullptr means zero);
+    // l and a of stage t >= 1 at rhs_off[b] + t - 1 (the input layout for the
+    // problem's own right-hand side, the compact layout for corrections)
     const T *l, *a, *x0, *l0, *a0, *lN;
+    const long long* rhs_off;
 
     // master-problem stage data of this level (k >= 1)
     const T *Ah, *Bh, *ah, *Qxh, *lxh;
@@ -85,6 +88,7 @@ struct ResidArgs {
     const double *l, *a, *x0;     // the problem's right-hand side (l_0 = a_0 = l_N = 0)
     const double *x, *w, *lam;    // current iterate (caller layout)
     TR *rl, *ra, *rl0, *ra0, *rlN, *rx0;   // correction right-hand side (UFTOC form)
+    const long long* out_off;     // rl, ra of stage t >= 1 at out_off[b] + t - 1 (compact layout)
     unsigned long long* norms;    // per instance [r_inf, z_inf, b_inf] as bit patterns of |.|
     const int* active;
 };

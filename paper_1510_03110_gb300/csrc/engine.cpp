@@ -66,6 +66,7 @@ size_t Engine::layout(char* base)
     c.take_raw(kst0, (size_t)batch * n * ts);
     c.take_raw(Lst0, (size_t)batch * n2 * ts);
     c.take(in_off, (size_t)batch);
+    c.take(cmp_off, (size_t)batch);
     c.take(w_off, (size_t)batch);
     c.take(gs0, (size_t)batch + 1);
     c.take_raw(dx, (size_t)plan.X_total * n * ts);
@@ -133,6 +134,7 @@ int Engine::upload_plan()
         rt->copy(lv[k].li, L.li.data(), L.li.size() * sizeof(LevelInst), stream);
     }
     rt->copy(in_off, plan.in_off.data(), plan.in_off.size() * sizeof(long long), stream);
+    rt->copy(cmp_off, plan.cmp_off.data(), plan.cmp_off.size() * sizeof(long long), stream);
     rt->copy(w_off, plan.w_off.data(), plan.w_off.size() * sizeof(long long), stream);
     rt->copy(gs0, plan.gs0.data(), plan.gs0.size() * sizeof(long long), stream);
     if (rt->sync(stream) != 0) { err = "CUDA error while uploading the plan"; return MHE_E_CUDA; }
@@ -211,6 +213,7 @@ LevelArgs<T> Engine::args(int k) const
     a.chunks = L.chunks;
     a.li = L.li;
     a.in_off = in_off;
+    a.rhs_off = in_off;
     a.w_off = w_off;
     if (k >= 1) {
         a.Ah = static_cast<const T*>(L.Ah); a.Bh = static_cast<const T*>(L.Bh);
@@ -289,6 +292,7 @@ void Engine::pass_rhs(const T* l, const T* a, const T* l0, const T* a0, const T*
 {
     for (int k = 0; k < (int)lv.size(); ++k) {
         LevelArgs<T> g = args<T>(k);
+        g.rhs_off = rhs_compact ? cmp_off : in_off;
         g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
         g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
         g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
@@ -308,6 +312,7 @@ void Engine::pass_down(const T* l, const T* a, const T* l0, const T* a0, const T
 {
     for (int k = (int)lv.size() - 1; k >= 0; --k) {
         LevelArgs<T> g = args<T>(k);
+        g.rhs_off = rhs_compact ? cmp_off : in_off;
         g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
         g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
         g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;
@@ -338,6 +343,7 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
     r.A = A; r.B = B; r.Q = Q; r.P0inv = P0inv;
     r.l = rhs->l; r.a = rhs->a; r.x0 = rhs->x0;
     r.x = x; r.w = w; r.lam = lam;
+    r.out_off = cmp_off;
     r.rl = static_cast<T*>(rl); r.ra = static_cast<T*>(ra); r.rl0 = static_cast<T*>(rl0);
     r.ra0 = static_cast<T*>(ra0); r.rlN = static_cast<T*>(rlN); r.rx0 = static_cast<T*>(rx0);
     r.norms = norms;
@@ -392,11 +398,13 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
         rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
                      stream);
         ++launches;
-        // correction problem K dz = r in UFTOC form, then z += dz
+        // correction problem K dz = r in UFTOC form (compact layout), then z += dz
         active_mask = active;
+        rhs_compact = true;
         pass_rhs<T>(crl, cra, crl0, cra0, crlN);
         pass_down<T>(crl, cra, crl0, cra0, crx0, crlN, static_cast<T*>(dx), static_cast<T*>(dw),
                      static_cast<T*>(dl), x, w, lam, active);
+        rhs_compact = false;
         active_mask = nullptr;
     }
     residual<T>(rhs, x, w, lam, nullptr);

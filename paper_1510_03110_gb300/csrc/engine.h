@@ -80,6 +80,8 @@ public:
     std::vector<LevelBuf> lv;
     void *Pst0 = nullptr, *Lgst0 = nullptr, *Kst0 = nullptr, *kst0 = nullptr, *Lst0 = nullptr;
     long long *in_off = nullptr, *w_off = nullptr, *gs0 = nullptr;
+    long long* cmp_off = nullptr;       // compact stage offsets of the internal per-stage arrays
+    bool rhs_compact = false;           // passes read l, a in the compact layout (corrections)
     void *dx = nullptr, *dw = nullptr, *dl = nullptr;            // T: corrections of the level-0 solution
     void *rl = nullptr, *ra = nullptr, *rl0 = nullptr, *ra0 = nullptr, *rlN = nullptr, *rx0 = nullptr;   // T
     float *A32 = nullptr, *B32 = nullptr, *Q32 = nullptr, *P0_32 = nullptr;   // FP32 mode: problem copies

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(32) k_serial_noalloc(int N, const double* A, c
     g.li = &li;
     g.A = A; g.B = B; g.Q = Q; g.P0inv = P0inv;
     g.in_off = &off[0];
+    g.rhs_off = &off[0];
     g.w_off = &off[1];
     g.l = l; g.a = a; g.x0 = x0;
     double* p = scratch;

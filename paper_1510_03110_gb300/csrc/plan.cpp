@@ -42,6 +42,7 @@ int make_plan(int n, int m, const int* N, int batch, int leaf_len, int branching
         if (N[b] > plan.max_N) plan.max_N = N[b];
     }
     plan.gs0[batch] = g0;
+    plan.cmp_off = plan.in_off;
     plan.S_in = so;
     plan.W_total = wo;
     plan.X_total = xo;

@@ -26,6 +26,7 @@ struct Plan {
     int leaf_len = 0, branching = 0, top_len = 0;
     std::vector<int> N;
     std::vector<long long> in_off;   // caller stage offset of stage t = 1 of each instance
+    std::vector<long long> cmp_off;  // the compact offsets (prefix sums of N_b - 1): internal per-stage arrays
     std::vector<long long> w_off;    // caller offset of w_0 of each instance
     std::vector<long long> gs0;      // batch + 1 prefix sums of N (level-0 global stage base)
     long long S_in = 0;              // caller stages: sum (N_b - 1)

@@ -45,8 +45,9 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
     const double* P0 = r.P0inv + (long long)b * NX * NX;
     const double* l = (KIND == 1) ? nullptr : (r.l ? r.l + s * (NX + NW) : nullptr);
     const double* a = (KIND == 1) ? nullptr : (r.a ? r.a + s * NX : nullptr);
-    TR* rl = (KIND == 1) ? r.rl0 + (long long)b * 2 * NX : r.rl + s * (NX + NW);
-    TR* ra = (KIND == 1) ? r.ra0 + (long long)b * NX : r.ra + s * NX;
+    const long long so = r.out_off[b] + t - 1;
+    TR* rl = (KIND == 1) ? r.rl0 + (long long)b * 2 * NX : r.rl + so * (NX + NW);
+    TR* ra = (KIND == 1) ? r.ra0 + (long long)b * NX : r.ra + so * NX;
     const bool first = (t == 0), lastst = (t == N - 1);
     const int nrow = NQ + NX + (first ? NX : 0) + (lastst ? NX : 0);
     unsigned long long* sr = sm;

@@ -419,14 +419,15 @@ struct Addr {
     static MHE_DEV StageRef<T> leaf(const LevelArgs<T>& a, int b, int t)
     {
         const long long s = a.in_off[b] + t - 1;
+        const long long sr = a.rhs_off[b] + t - 1;
         StageRef<T> r;
         r.A = a.A + s * NX * NX;
         r.B = a.B + s * NX * NW;
         r.Q = a.Q + s * (NX + NW) * (NX + NW);
         r.Qx = nullptr;
         r.Qw0 = nullptr;
-        r.l = a.l ? a.l + s * (NX + NW) : nullptr;
-        r.a = a.a ? a.a + s * NX : nullptr;
+        r.l = a.l ? a.l + sr * (NX + NW) : nullptr;
+        r.a = a.a ? a.a + sr * NX : nullptr;
         return r;
     }
     static MHE_DEV StageRef<T> arrival(const LevelArgs<T>& a, int b)
