@@ -313,6 +313,18 @@ def run_gpu(args):
         e2e = run_e2e(args, buckets, solvers, step, stream, instances)
 
     cpu = cpu_baseline(buckets, args) if not args.no_cpu else None
+    serving = None
+    if args.serve_duration > 0:
+        # free the batch workload first: the serving run holds its own windows
+        for s_ in solvers:
+            s_.close()
+        solvers = []
+        for bk in buckets:
+            bk.pop("dev", None)
+        torch.cuda.empty_cache()
+        sa = argparse.Namespace(**vars(args))
+        sa.duration = args.serve_duration
+        serving = run_serve(sa)
     value = instances / (ms * 1e-3)
     step_sorted = sorted(step_ms)
     p99 = step_sorted[min(len(step_sorted) - 1, int(np.ceil(0.99 * len(step_sorted))) - 1)]
@@ -326,7 +338,13 @@ def run_gpu(args):
                 relres_max=relres_max, all_ok=ok,
                 refine_iters_max=int(np.max(infos["refine_iters"])),
                 serial_gpu=base,
-                speedup_vs_serial={k: round(value / v["value"], 2) for k, v in base.items()},
+                speedup_vs_serial=dict({k: round(value / v["value"], 2) for k, v in base.items()},
+                                       **({} if serving is None else dict(
+                                           serving_solves_per_s=round(serving["tree"]["solves_per_s"] /
+                                                                      max(serving["serial"]["solves_per_s"], 1e-9), 2),
+                                           serving_p99=round(serving["serial"]["p99_ms"] /
+                                                             max(serving["tree"]["p99_ms"], 1e-9), 2)))),
+                serving=serving,
                 roofline=roofline, passes=sorted(passes, key=lambda r: -r["ms"])[:8],
                 cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clk,
                 wall_s=round(wall, 3))
@@ -546,6 +564,8 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
     ap.add_argument("--estimators", type=int, default=1024, help="serving: estimator pool")
     ap.add_argument("--serve-bytes", type=int, default=96 << 30, help="serving: device-memory budget")
+    ap.add_argument("--serve-duration", type=float, default=2.0,
+                    help="batch workload: seconds of a serving run appended to the line (0: none)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the serial-plan GPU baseline")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
