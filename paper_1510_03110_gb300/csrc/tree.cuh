@@ -75,6 +75,24 @@ struct Ws {
     }
 };
 
+// init + sum_{p<K} fa(p) fb(p) with four independent accumulators (the
+// products of one stage are short dot products; four chains hide the FMA latency)
+template <int K, typename T, class FA, class FB>
+MHE_DEV T dot4(T init, FA&& fa, FB&& fb)
+{
+    T a0 = init, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+    for (int p = 0; p + 3 < K; p += 4) {
+        a0 += fa(p) * fb(p);
+        a1 += fa(p + 1) * fb(p + 1);
+        a2 += fa(p + 2) * fb(p + 2);
+        a3 += fa(p + 3) * fb(p + 3);
+    }
+#pragma unroll
+    for (int p = K & ~3; p < K; ++p) a0 += fa(p) * fb(p);
+    return (a0 + a1) + (a2 + a3);
+}
+
 // upper-triangle index -> (i <= j)
 MHE_DEV void tri_ij(int idx, int& i, int& j)
 {
@@ -223,22 +241,16 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
     wfor(NX * NX + NX * MT + NX, [&](int idx) {
         if (idx < NX * NX) {
             int i = idx % NX, j = idx / NX;
-            T acc = 0;
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.P[i + p * ld] * s.A[p + j * ld];
-            s.Tt[i + j * ld] = acc;
+            s.Tt[i + j * ld] = dot4<NX>((T)0, [&](int p) { return s.P[i + p * ld]; },
+                                        [&](int p) { return s.A[p + j * ld]; });
         } else if (idx < NX * NX + NX * MT) {
             int r = idx - NX * NX, i = r % NX, j = r / NX;
-            T acc = 0;
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.P[i + p * ld] * s.B[p + j * ld];
-            s.PB[i + j * ld] = acc;
+            s.PB[i + j * ld] = dot4<NX>((T)0, [&](int p) { return s.P[i + p * ld]; },
+                                        [&](int p) { return s.B[p + j * ld]; });
         } else {
             int i = idx - NX * NX - NX * MT;
-            T acc = s.Psi[i];
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc -= s.P[i + p * ld] * s.e[p];
-            s.u[i] = acc;
+            s.u[i] = s.Psi[i] - dot4<NX>((T)0, [&](int p) { return s.P[i + p * ld]; },
+                                         [&](int p) { return s.e[p]; });
         }
     });
     // F -> P (upper triangle mirrored), G, H,  g = B^T u - l_w,  tv = A^T u
@@ -246,37 +258,27 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         if (idx < NT) {
             int i, j;
             tri_ij(idx, i, j);
-            T acc = X::qx(st, i, j);
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.Tt[p + j * ld];
+            const T acc = dot4<NX>(X::qx(st, i, j), [&](int p) { return s.A[p + i * ld]; },
+                                   [&](int p) { return s.Tt[p + j * ld]; });
             s.P[i + j * ld] = acc;
             s.P[j + i * ld] = acc;
         } else if (idx < NT + MTT) {
             int i, j;
             tri_ij(idx - NT, i, j);
-            T acc = X::qw(st, i, j);
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.B[p + i * ld] * s.PB[p + j * ld];
+            const T acc = dot4<NX>(X::qw(st, i, j), [&](int p) { return s.B[p + i * ld]; },
+                                   [&](int p) { return s.PB[p + j * ld]; });
             s.G[i + j * ld] = acc;
             s.G[j + i * ld] = acc;
         } else if (idx < NT + MTT + NX * MT) {
             int r = idx - NT - MTT, i = r % NX, j = r / NX;
-            T acc = X::qxw(st, i, j);
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.PB[p + j * ld];
-            s.H[i + j * ld] = acc;
+            s.H[i + j * ld] = dot4<NX>(X::qxw(st, i, j), [&](int p) { return s.A[p + i * ld]; },
+                                       [&](int p) { return s.PB[p + j * ld]; });
         } else if (idx < NT + MTT + NX * MT + MT) {
             int j = idx - NT - MTT - NX * MT;
-            T acc = -X::lw(st, j);
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.B[p + j * ld] * s.u[p];
-            s.g[j] = acc;
+            s.g[j] = dot4<NX>(-X::lw(st, j), [&](int p) { return s.B[p + j * ld]; }, [&](int p) { return s.u[p]; });
         } else {
             int i = idx - NT - MTT - NX * MT - MT;
-            T acc = 0;
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.u[p];
-            s.tv[i] = acc;
+            s.tv[i] = dot4<NX>((T)0, [&](int p) { return s.A[p + i * ld]; }, [&](int p) { return s.u[p]; });
         }
     });
     const bool bad = chol_G<T, NX, MT>(s, piv_rel);
@@ -321,9 +323,8 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         if (idx < NT) {
             int i, j;
             tri_ij(idx, i, j);
-            T acc = s.P[i + j * ld];
-#pragma unroll 8
-            for (int q = 0; q < MT; ++q) acc -= s.PB[q + i * ld] * s.PB[q + j * ld];
+            const T acc = s.P[i + j * ld] - dot4<MT>((T)0, [&](int q) { return s.PB[q + i * ld]; },
+                                                   [&](int q) { return s.PB[q + j * ld]; });
             s.P[i + j * ld] = acc;
             s.P[j + i * ld] = acc;
         } else if (idx < NT + NX) {
@@ -389,18 +390,13 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
     wfor(NX * NX + NT, [&](int idx) {
         if (idx < NX * NX) {
             int i = idx % NX, j = idx / NX;
-            T acc = 0;
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.A[p + i * ld] * s.V[p + j * ld];
-#pragma unroll 8
-            for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.H[q + j * ld];
-            s.Tt[i + j * ld] = acc;
+            const T av = dot4<NX>((T)0, [&](int p) { return s.A[p + i * ld]; }, [&](int p) { return s.V[p + j * ld]; });
+            s.Tt[i + j * ld] = dot4<MT>(av, [&](int q) { return s.K[q + i * ld]; }, [&](int q) { return s.H[q + j * ld]; });
         } else {
             int i, j;
             tri_ij(idx - NX * NX, i, j);
-            T acc = s.Qw[i + j * ld];
-#pragma unroll 8
-            for (int q = 0; q < MT; ++q) acc += s.PB[q + i * ld] * s.PB[q + j * ld];
+            const T acc = dot4<MT>(s.Qw[i + j * ld], [&](int q) { return s.PB[q + i * ld]; },
+                                   [&](int q) { return s.PB[q + j * ld]; });
             s.Qw[i + j * ld] = acc;
             s.Qw[j + i * ld] = acc;
         }
@@ -453,6 +449,19 @@ struct Addr {
     }
 };
 
+// L2 prefetch of the blocks of level-0 stage t of instance b (t >= 1)
+template <typename T, int NX, int NW>
+MHE_DEV void prefetch_leaf(const LevelArgs<T>& a, int b, int t)
+{
+    if (t < 1) return;
+    const long long s = a.in_off[b] + t - 1;
+    prefetch_l2(a.A + s * NX * NX, (int)(sizeof(T) * NX * NX));
+    prefetch_l2(a.B + s * NX * NW, (int)(sizeof(T) * NX * NW));
+    prefetch_l2(a.Q + s * (NX + NW) * (NX + NW), (int)(sizeof(T) * (NX + NW) * (NX + NW)));
+    if (a.l) prefetch_l2(a.l + (a.rhs_off[b] + t - 1) * (NX + NW), (int)(sizeof(T) * (NX + NW)));
+    if (a.a) prefetch_l2(a.a + (a.rhs_off[b] + t - 1) * NX, (int)(sizeof(T) * NX));
+}
+
 // ---- Algorithm 4 over one chunk ----------------------------------------------
 
 template <typename T, int NX, int NW, bool UPPER>
@@ -479,9 +488,11 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
         }
     });
     int bad_t = -1;
+    if (!UPPER) prefetch_leaf<T, NX, NW>(a, b, cd.t0 + cd.len - 1);
     for (int tt = cd.len - 1; tt >= 0; --tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
+        if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1);   // the next stage of the sweep
         bool bad;
         if (UPPER) {
             bad = reduce_step<T, NX, NX, KIND_UPPER>(
@@ -619,9 +630,11 @@ MHE_DEV void rhs_chunk(const LevelArgs<T>& a, int ci, T* smem)
     const T* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
                         : (a.lN ? a.lN + (long long)b * NX : nullptr);
     wfor(NX, [&](int i) { s.Psi[i] = (last && lN) ? -lN[i] : (T)0; });
+    if (!UPPER) prefetch_leaf<T, NX, NW>(a, b, cd.t0 + cd.len - 1);
     for (int tt = cd.len - 1; tt >= 0; --tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
+        if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1);
         if (UPPER) {
             rhs_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), a.Pst + g * NX * NX,
                                             a.Lgst + g * NX * NX, a.Kst + g * NX * NX, a.kst + g * NX);

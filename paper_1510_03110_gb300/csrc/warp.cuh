@@ -31,6 +31,15 @@ MHE_DEV void wone(F&& f)
     __syncwarp();
 }
 
+// Ask L2 to fetch `bytes` starting at p (one prefetch per 128-byte line, the
+// lines shared round-robin by the lanes); no registers or shared memory used.
+MHE_DEV void prefetch_l2(const void* p, int bytes)
+{
+    const char* c = static_cast<const char*>(p);
+    for (int off = lane_id() * 128; off < bytes; off += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
+}
+
 MHE_DEV double msqrt(double v) { return sqrt(v); }
 MHE_DEV float msqrt(float v) { return sqrtf(v); }
 MHE_DEV double mabs(double v) { return fabs(v); }
