@@ -42,6 +42,47 @@ def flops_leaf_stage(n, m):
     return 6 * n ** 3 + 12 * n ** 2 * m + 6 * n * m ** 2 + m ** 3 / 3.0
 
 
+def pass_model(ph, lvl, n, m, q, prec, N):
+    """Algorithmic work of one full pass of a level-0 kernel over a bucket:
+    (bound, work, unit) with work in TFLOP or GB.  The counts:
+      reduce  Algorithm 4 per stage (flops_leaf_stage; the arrival stage has width n)
+      resid   FP64 FMAs of the KKT rows per stage: dynamics A x + B w, costate
+              A^T lam + B^T lam, and Q z in the MHE factors (FP32_IR: C x, V u, S^T w,
+              C^T e, W w, S u) or with the assembled Q (FP64)
+      prep    bytes: FP64 A, B, C, R, a, y~, w~ read; FP32 A, B, Q, a, l and FP64 l written
+              (FP64 mode: C, R, y~, w~ read, FP64 Q, l written)
+      rhs     bytes: stored P, chol(G), K and FP32 A, B, a, l read per stage
+      down    bytes: stored K, k, L and FP32 A, B, Q, a, l read; x, w, lam written (FP32)
+              and accumulated into FP64 z"""
+    stages = int(np.sum(N))
+    inst = len(N)
+    if lvl != 0:
+        return None
+    if ph == "reduce":
+        fl = stages * flops_leaf_stage(n, m) - inst * (flops_leaf_stage(n, m) - flops_leaf_stage(n, n))
+        return ("alu", fl / 1e12, "TFLOP/s")
+    if ph == "resid":
+        qz = (2 * n * q + q * q + q * m + m * m + m * q) if prec == 1 else (n + m) ** 2
+        fma = qz + 2 * (n * n + n * m)
+        return ("alu", 2.0 * fma * stages / 1e12, "TFLOP/s")
+    if ph == "prep":
+        if prec == 1:
+            b = 8 * (n * n + n * m + q * n + (m + q) ** 2 + n + q + m) + 4 * (n * n + n * m + (n + m) ** 2 + 2 * n + m) \
+                + 8 * (n + m)
+        else:
+            b = 8 * (q * n + (m + q) ** 2 + q + m) + 8 * ((n + m) ** 2 + n + m)
+        return ("hbm", b * stages / 1e9, "GB/s")
+    ts = 4 if prec == 1 else 8
+    if ph == "rhs":
+        return ("hbm", ts * (2 * n * n + m * m + 2 * m * n + 2 * n + m) * stages / 1e9, "GB/s")
+    if ph == "down":
+        b = ts * (2 * m * n + m + n * n + n * m + (n + m) ** 2 + 2 * n + m + 3 * n + m)
+        if prec == 1:
+            b += 2 * 8 * (2 * n + m)
+        return ("hbm", b * stages / 1e9, "GB/s")
+    return None
+
+
 def flops_serial_stage(n, m):
     """Algorithms 1-3 per stage."""
     return 4 * n ** 3 + 6 * n ** 2 * m + 4 * n * m ** 2 + m ** 3 / 3.0
@@ -222,9 +263,9 @@ def run_gpu(args):
     def step(ss, timing=False):
         for bk, s in zip(buckets, ss):
             d = bk["dev"]
-            if d["S"] > 0:
-                mhe.mhe_assemble(bk["n"], bk["m"], bk["q"], d["C"], d["R"], d["yt"], d["wt"], d["Q"], d["l"])
-            s.factor_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], out=s.out)
+            # steps a0..a7 from the MHE data (stage assembly inside the library)
+            s.estimate(bk["q"], d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"],
+                       out=s.out)
 
     for _ in range(args.warmup):
         step(solvers)
@@ -233,6 +274,10 @@ def run_gpu(args):
     clocks = Clocks()
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # per-pass CUDA events on the contexts' stream during the timed steps (the roofline's durations)
+    for s in solvers:
+        mhe.mhe_timing_read(s.ctx)
+        mhe.mhe_timing_enable(s.ctx, True)
     torch.cuda.synchronize()
     t_host = time.time()
     torch.cuda.nvtx.range_push("timed")
@@ -252,33 +297,46 @@ def run_gpu(args):
     relres_max = float(np.max(infos["relres"]))
     ok = bool(np.all(infos["status"] == 0) and relres_max <= RELRES_BAR)
 
-    # per-pass timing of one more step: the dominant kernel and its roofline
-    for s in solvers:
-        mhe.mhe_timing_enable(s.ctx, True)
-    step(solvers)
+    # per-pass timing of the timed steps: the dominant kernel and its roofline
     passes = []
     for bk, s in zip(buckets, solvers):
-        for (ph, lvl, calls, tms) in mhe.mhe_timing_read(s.ctx):
-            passes.append(dict(nx=bk["n"], phase=ph, level=lvl, calls=calls, ms=tms))
+        for (ph, lvl, calls, tms, tmax) in mhe.mhe_timing_read(s.ctx):
+            passes.append(dict(nx=bk["n"], phase=ph, level=lvl, calls=calls // args.steps,
+                               ms=tms / args.steps, ms_max=tmax))
         mhe.mhe_timing_enable(s.ctx, False)
-    dom = max(passes, key=lambda r: r["ms"])
     pk = peaks()
-    dbk = [bk for bk in buckets if bk["n"] == dom["nx"]][0]
-    n, m = dbk["n"], dbk["m"]
-    roofline = None
-    if dom["phase"] == "reduce" and dom["level"] == 0:
-        stages = int(np.sum(dbk["N"]))
-        fl = stages * flops_leaf_stage(n, m) - len(dbk["N"]) * (flops_leaf_stage(n, m) - flops_leaf_stage(n, n))
-        achieved = fl / (dom["ms"] / dom["calls"] * 1e-3) / 1e12
-        peak = pk["fp32_tflops"] if prec == 1 else pk["fp64_tflops"]
-        tr = read_traffic().get(f"reduce_leaf_nx{n}_{'fp32' if prec == 1 else 'fp64'}_bytes_per_stage")
-        roofline = dict(bound="alu", kernel=f"k_level<{'float' if prec == 1 else 'double'},{n},{m},0,REDUCE>",
-                        achieved=round(achieved, 3), peak=round(peak, 2), unit="TFLOP/s",
-                        frac=round(achieved / peak, 4),
-                        traffic=(tr * stages if tr else None),
-                        peak_src=("FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % pk["sm_max_mhz"]) if prec == 1
-                        else "FP64: nominal 1.25 TFLOP/s of the part",
-                        flops_per_launch=fl, ms_per_launch=dom["ms"] / dom["calls"])
+    traffic = read_traffic()
+    kern = {"reduce": "k_level<{t},{n},{m},0,REDUCE>", "rhs": "k_level<{t},{n},{m},0,RHS>",
+            "down": "k_level<{t},{n},{m},0,DOWN>", "resid": "k_resid<{n},{m},{t},{y}>",
+            "prep": "k_prep<{n},{m},{q}>" if prec == 1 else "k_assemble<{n},{m},{q}>"}
+
+    def roof(r):
+        bk = [b for b in buckets if b["n"] == r["nx"]][0]
+        n, m, q = bk["n"], bk["m"], bk["q"]
+        mod = pass_model(r["phase"], r["level"], n, m, q, prec, bk["N"])
+        if mod is None:
+            return None
+        bound, work, unit = mod
+        full_ms = r["ms_max"]   # the longest pass covers every instance
+        achieved = work / (full_ms * 1e-3)
+        if bound == "hbm":
+            peak, src = pk["hbm_gbs"], "HBM copy bandwidth, %s" % pk["src"]
+        elif r["phase"] == "resid" or prec == 0:
+            peak, src = pk["fp64_tflops"], "FP64: nominal 1.25 TFLOP/s of the part"
+        else:
+            peak, src = pk["fp32_tflops"], "FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % pk["sm_max_mhz"]
+        tkey = f"{r['phase']}_nx{n}_{'fp32' if prec == 1 else 'fp64'}_bytes_per_stage"
+        tr = traffic.get(tkey)
+        name = kern[r["phase"]].format(t="float" if prec == 1 else "double", n=n, m=m, q=q,
+                                       y=(q if prec == 1 else 0))
+        return dict(bound=bound, kernel=name, achieved=round(achieved, 3), peak=round(peak, 2), unit=unit,
+                    frac=round(achieved / peak, 4), traffic=(tr * int(np.sum(bk["N"])) if tr else None),
+                    peak_src=src, work_per_launch=work, ms_per_launch=round(full_ms, 4),
+                    launches_per_step=r["calls"], ms_per_step=round(r["ms"], 4))
+
+    ranked = sorted(passes, key=lambda r: -r["ms"])
+    kernels = [x for x in (roof(r) for r in ranked[:6]) if x]
+    roofline = kernels[0] if kernels else None
 
     # plain serial Riccati on the same GPU: one chunk per instance (top_len >= N)
     base = {}
@@ -345,7 +403,7 @@ def run_gpu(args):
                                            serving_p99=round(serving["serial"]["p99_ms"] /
                                                              max(serving["tree"]["p99_ms"], 1e-9), 2)))),
                 serving=serving,
-                roofline=roofline, passes=sorted(passes, key=lambda r: -r["ms"])[:8],
+                roofline=roofline, kernels=kernels[1:], passes=sorted(passes, key=lambda r: -r["ms"])[:8],
                 cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clk,
                 wall_s=round(wall, 3))
     print(json.dumps(line))

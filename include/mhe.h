@@ -141,6 +141,36 @@ int mhe_destroy(mhe_ctx* ctx);
 int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const double* R,
                  const double* yt, const double* wt, double* Q, double* l, double* c, void* stream);
 
+/* One batch of MHE problems in the form of Eq. org_mhe (Section II), FP64,
+ * device memory.  Stage k = 0 .. N_b - 2 of instance b is UFTOC stage
+ * t = k + 1, stored as block s of the conventions above.  Read while the
+ * stream executes mhe_estimate and every later mhe_solve on the context: keep
+ * them alive and unchanged until the last of those has completed. */
+typedef struct {
+    int ny;               /* measurements per stage; must be the compiled shape's ny */
+    const double* A;      /* [S][nx*nx]          A_t */
+    const double* B;      /* [S][nx*nw]          B_t (noise input matrix of the dynamics) */
+    const double* C;      /* [S][ny*nx]          C_t (measurement matrix) */
+    const double* R;      /* [S][(nw+ny)^2]      [[W, S], [S^T, V]], symmetric positive definite */
+    const double* a;      /* [S][nx]             a_t */
+    const double* yt;     /* [S][ny]             y~_t = y - d - v~ */
+    const double* wt;     /* [S][nw]             w~_t */
+    const double* x0;     /* [batch][nx]         x~0 */
+    const double* P0inv;  /* [batch][nx*nx]      P~0^{-1}, symmetric positive definite */
+} mhe_problem;
+
+/* Steps a0..a7 on MHE data: the result mhe_assemble followed by
+ * mhe_factor_solve with {A, B, Q, P0inv} and {l, a, x0} gives, without the
+ * caller forming Q.  An FP32_IR context never forms Q in FP64: one pass over
+ * the stages writes the FP32 working copies (Q rounded from FP32 products of
+ * C and R), the FP64 l and ||K||_inf, and the FP64 residual applies Q in its
+ * factors C and R (u = C x, e = V u - S^T w; C^T e and W w - S u).  An FP64
+ * context assembles Q and l into internal FP64 buffers (allocated on first
+ * use, grown when needed, freed by mhe_destroy).  A later mhe_solve reuses the
+ * factorisation with the caller's right-hand side.  Outputs as mhe_solve.
+ * Errors: MHE_E_ARG (NULL pointer, ny not compiled), MHE_E_NOMEM. */
+int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info);
+
 /* Shapes (nx, nw) compiled into this library: writes up to cap pairs into
  * nx_out / nw_out and returns the number available. */
 int mhe_shapes(int* nx_out, int* nw_out, int cap);
@@ -203,10 +233,11 @@ int mhe_server_destroy(mhe_server* s);
  * experiment timed each tree level the same way (Section VI). */
 int mhe_timing_enable(mhe_ctx* ctx, int enable);
 
-/* Synchronises the stream and writes, per (phase, level), 4 doubles
- * {phase (0 reduce, 1 rhs, 2 down, 3 residual), level, passes, total ms}
- * accumulated since the last read; returns the number of records (which may
- * exceed cap; only cap are written). */
+/* Synchronises the stream and writes, per (phase, level), 5 doubles
+ * {phase (0 reduce, 1 rhs, 2 down, 3 residual, 4 stage preparation of
+ * mhe_estimate), level, passes, total ms, longest single pass ms} accumulated
+ * since the last read; returns the number of records (which may exceed cap;
+ * only cap are written). */
 int mhe_timing_read(mhe_ctx* ctx, double* out, int cap);
 
 /* The planned tree: per level 3 long longs {level, chunks, stages}; returns

@@ -117,19 +117,25 @@ __global__ void k_finalize(int batch, const unsigned long long* norms, const uns
     const double bb = __longlong_as_double((long long)norms[3 * b + 2]);
     const double K = (double)__uint_as_float(kinf[b]);
     const double den = K * z + bb;
-    const double relres = den > 0 ? r / den : r;
+    double relres = den > 0 ? r / den : r;
     if (mode < 2) {
         const int was = (mode == 0) ? 1 : active[b];
-        const int act = was && status[b] == 0 && isfinite(relres) && !(relres <= tol);
+        if (!was) return;
+        // the residual of the current iterate; final if no correction follows
+        info[b].relres = relres;
+        const int act = status[b] == 0 && isfinite(relres) && !(relres <= tol);
         active[b] = act;
         if (act) iters[b] += 1;
         return;
     }
+    // partial final pass: only instances corrected since their last check were
+    // re-evaluated; the others keep the residual recorded at that check
+    if ((refine & 2) && !active[b]) relres = info[b].relres;
     mhe_info o;
     memset(&o, 0, sizeof(o));
     int st = status[b];
     if (st == 0 && !isfinite(relres)) st = MHE_E_NONFINITE;
-    else if (st == 0 && refine && !(relres <= tol)) st = MHE_E_NO_CONVERGE;
+    else if (st == 0 && (refine & 1) && !(relres <= tol)) st = MHE_E_NO_CONVERGE;
     o.status = st;
     o.level = where[3 * b + 0];
     o.chunk = where[3 * b + 1];
@@ -263,6 +269,14 @@ int mhe_factor_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs,
     return rc;
 }
 
+int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info)
+{
+    if (!ctx || !prob) return fail(MHE_E_ARG, "ctx or prob is NULL");
+    const int rc = ctx->eng.estimate(*prob, x, w, lam, info);
+    if (rc != MHE_OK) g_err = ctx->eng.err;
+    return rc;
+}
+
 int mhe_destroy(mhe_ctx* ctx)
 {
     if (!ctx) return MHE_OK;
@@ -309,7 +323,7 @@ int mhe_timing_read(mhe_ctx* ctx, double* out, int cap)
         return fail(MHE_E_CUDA, "stream synchronisation failed");
     struct Agg {
         int phase, level, calls;
-        double ms;
+        double ms, ms_max;
     };
     std::vector<Agg> agg;
     for (auto& r : ctx->timing.recs) {
@@ -317,18 +331,25 @@ int mhe_timing_read(mhe_ctx* ctx, double* out, int cap)
         cudaEventElapsedTime(&ms, r.b, r.e);
         bool found = false;
         for (auto& g : agg)
-            if (g.phase == r.phase && g.level == r.level) { g.calls++; g.ms += ms; found = true; break; }
-        if (!found) agg.push_back(Agg{r.phase, r.level, 1, (double)ms});
+            if (g.phase == r.phase && g.level == r.level) {
+                g.calls++;
+                g.ms += ms;
+                g.ms_max = ms > g.ms_max ? ms : g.ms_max;
+                found = true;
+                break;
+            }
+        if (!found) agg.push_back(Agg{r.phase, r.level, 1, (double)ms, (double)ms});
     }
     ctx->timing.recs.clear();
     ctx->timing.used = 0;
     int k = 0;
     for (auto& g : agg) {
         if (k < cap) {
-            out[4 * k + 0] = g.phase;
-            out[4 * k + 1] = g.level;
-            out[4 * k + 2] = g.calls;
-            out[4 * k + 3] = g.ms;
+            out[5 * k + 0] = g.phase;
+            out[5 * k + 1] = g.level;
+            out[5 * k + 2] = g.calls;
+            out[5 * k + 3] = g.ms;
+            out[5 * k + 4] = g.ms_max;
         }
         ++k;
     }

@@ -91,6 +91,23 @@ struct ResidArgs {
     const long long* out_off;     // rl, ra of stage t >= 1 at out_off[b] + t - 1 (compact layout)
     unsigned long long* norms;    // per instance [r_inf, z_inf, b_inf] as bit patterns of |.|
     const int* active;
+    // MHE form (Eq. org_mhe): when C is set, Q of stage t >= 1 is applied in its
+    // factors [[C^T V C, -C^T S^T], [-S C, W]] from C (ny x n) and
+    // R = [[W, S], [S^T, V]] at the input offsets, and Q is not read
+    const double *C, *R;
+};
+
+// MHE data (Eq. org_mhe, Section II) -> the FP32 working copies of the UFTOC
+// problem, its FP64 linear term l, and ||K||_inf, in one pass over the stages.
+struct PrepArgs {
+    int batch;
+    long long nstages;            // sum of N_b (arrival stages included)
+    const long long* gs0;
+    const long long* in_off;      // stage t >= 1 of instance b at in_off[b] + t - 1 (inputs and outputs)
+    const double *A, *B, *C, *R, *a, *yt, *wt, *x0, *P0inv;
+    float *A32, *B32, *Q32, *l32, *a32, *x0_32, *P0_32;
+    double* l;                    // FP64 l = [C^T (S^T w~ - V y~); S y~ - W w~]
+    unsigned int* kinf;           // per instance, bit pattern of a non-negative float
 };
 
 // ||K||_inf per instance (max absolute row sum of the KKT matrix), once per

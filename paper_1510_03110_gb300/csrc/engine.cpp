@@ -164,6 +164,7 @@ int Engine::replan(const int* N, int batch, const long long* in_off_custom)
 int Engine::solve_resident(const Resident& r, double* x, double* w, double* lam, mhe_info* info)
 {
     A = r.A; B = r.B; Q = r.Q; P0inv = r.P0inv;
+    mheC = mheR = nullptr;
     mA = r.At; mB = r.Bt; mQ = r.Qt; mP0 = r.P0t;
     rt->memset0(status, sizeof(int) * plan.batch, stream);
     rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
@@ -200,6 +201,10 @@ void Engine::release()
 {
     if (arena) rt->release(arena);
     arena = nullptr;
+    if (l64) rt->release(l64);
+    if (Q64) rt->release(Q64);
+    l64 = Q64 = nullptr;
+    l64_bytes = Q64_bytes = 0;
 }
 
 template <typename T>
@@ -348,6 +353,8 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
     r.ra0 = static_cast<T*>(ra0); r.rlN = static_cast<T*>(rlN); r.rx0 = static_cast<T*>(rx0);
     r.norms = norms;
     r.active = act;
+    r.C = mheC;
+    r.R = mheR;
     rt->memset0(norms, sizeof(unsigned long long) * 3 * plan.batch, stream);
     mark(PH_RESID, 0, 1);
     launches += r.nstages > 0;
@@ -358,7 +365,11 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
 template <>
 void Engine::launch_resid<double>(const ResidArgs<double>& r) { ops->resid64(r, stream); }
 template <>
-void Engine::launch_resid<float>(const ResidArgs<float>& r) { ops->resid32(r, stream); }
+void Engine::launch_resid<float>(const ResidArgs<float>& r)
+{
+    if (r.C) ops->resid_mhe32(r, stream);
+    else ops->resid32(r, stream);
+}
 
 void Engine::convert_rhs(const mhe_rhs* rhs)
 {
@@ -407,8 +418,10 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
         rhs_compact = false;
         active_mask = nullptr;
     }
-    residual<T>(rhs, x, w, lam, nullptr);
-    rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, 2, max_refine > 0 ? 1 : 0, info_dev,
+    // final check: after a refinement loop only the instances corrected since
+    // their last residual (still active) need one
+    residual<T>(rhs, x, w, lam, max_refine > 0 ? active : nullptr);
+    rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, 2, max_refine > 0 ? 3 : 0, info_dev,
                  stream);
     ++launches;
     if (info) rt->copy(info, info_dev, sizeof(mhe_info) * plan.batch, stream);
@@ -423,6 +436,7 @@ int Engine::factor(const mhe_matrices& mt, const mhe_rhs* rhs, double* x, double
     if (!mt.Q && plan.S_in > 0) { err = "Q is NULL"; return MHE_E_ARG; }
     if (!mt.P0inv) { err = "P0inv is NULL"; return MHE_E_ARG; }
     A = mt.A; B = mt.B; Q = mt.Q; P0inv = mt.P0inv;
+    mheC = mheR = nullptr;
     (void)x; (void)w; (void)lam;
     rt->memset0(status, sizeof(int) * plan.batch, stream);
     rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
@@ -466,6 +480,80 @@ int Engine::solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_inf
     if (prec == MHE_FP64) return run_solve<double>(rhs, rhs->l, rhs->a, rhs->x0, x, w, lam, info, fused);
     if (!fused) convert_rhs(rhs);
     return run_solve<float>(rhs, l32, a32, x0_32, x, w, lam, info, fused);
+}
+
+namespace {
+// (re)allocate an internal buffer to at least `need` bytes
+bool reserve(const Runtime* rt, void* stream, double*& p, size_t& have, size_t need)
+{
+    if (need <= have && p) return true;
+    if (p) {
+        rt->sync(stream);
+        rt->release(p);
+    }
+    p = static_cast<double*>(rt->alloc(need > 0 ? need : 8));
+    have = p ? need : 0;
+    return p != nullptr;
+}
+}  // namespace
+
+int Engine::estimate(const mhe_problem& p, double* x, double* w, double* lam, mhe_info* info)
+{
+    if (p.ny != ops->ny) { err = "ny is not the compiled shape's"; return MHE_E_ARG; }
+    if (plan.S_in > 0 && (!p.A || !p.B || !p.C || !p.R || !p.a || !p.yt || !p.wt)) {
+        err = "a stage array of the MHE problem is NULL";
+        return MHE_E_ARG;
+    }
+    if (!p.x0 || !p.P0inv) { err = "x0 or P0inv is NULL"; return MHE_E_ARG; }
+    if (!x || !w || !lam) { err = "output pointer is NULL"; return MHE_E_ARG; }
+    const int n = plan.n, m = plan.m;
+    const long long S = plan.S_in;
+    if (!reserve(rt, stream, l64, l64_bytes, sizeof(double) * (size_t)S * (n + m))) {
+        err = "device allocation of l failed";
+        return MHE_E_NOMEM;
+    }
+    mhe_rhs rhs;
+    rhs.l = l64; rhs.a = p.a; rhs.x0 = p.x0;
+    if (prec == MHE_FP64) {
+        if (!reserve(rt, stream, Q64, Q64_bytes, sizeof(double) * (size_t)S * (n + m) * (n + m))) {
+            err = "device allocation of Q failed";
+            return MHE_E_NOMEM;
+        }
+        mark(PH_PREP, 0, 1);
+        ops->assemble(S, p.C, p.R, p.yt, p.wt, Q64, l64, nullptr, stream);
+        mark(PH_PREP, 0, 0);
+        launches += S > 0;
+        mhe_matrices mt;
+        mt.A = p.A; mt.B = p.B; mt.Q = Q64; mt.P0inv = p.P0inv;
+        const int rc = factor(mt, &rhs, x, w, lam);
+        if (rc != MHE_OK) return rc;
+        return solve(&rhs, x, w, lam, info, true);
+    }
+    A = p.A; B = p.B; Q = nullptr; P0inv = p.P0inv;
+    mheC = p.C; mheR = p.R;
+    rt->memset0(status, sizeof(int) * plan.batch, stream);
+    rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
+    rt->memset0(kinf, sizeof(unsigned int) * plan.batch, stream);
+    PrepArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.batch = plan.batch;
+    pa.nstages = plan.gs0[plan.batch];
+    pa.gs0 = gs0;
+    pa.in_off = in_off;
+    pa.A = p.A; pa.B = p.B; pa.C = p.C; pa.R = p.R; pa.a = p.a; pa.yt = p.yt; pa.wt = p.wt;
+    pa.x0 = p.x0; pa.P0inv = p.P0inv;
+    pa.A32 = A32; pa.B32 = B32; pa.Q32 = Q32; pa.l32 = l32; pa.a32 = a32; pa.x0_32 = x0_32; pa.P0_32 = P0_32;
+    pa.l = l64;
+    pa.kinf = kinf;
+    mark(PH_PREP, 0, 1);
+    ops->prep32(pa, stream);
+    mark(PH_PREP, 0, 0);
+    launches += 1;
+    mA = A32; mB = B32; mQ = Q32; mP0 = P0_32;
+    pass_reduce<float>(A32, B32, Q32, P0_32, l32, a32);
+    factored = true;
+    if (rt->error() != 0) { err = "CUDA error during the factorisation"; return MHE_E_CUDA; }
+    return run_solve<float>(&rhs, l32, a32, x0_32, x, w, lam, info, true);
 }
 
 }  // namespace mhe

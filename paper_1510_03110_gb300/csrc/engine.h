@@ -26,6 +26,12 @@ struct ShapeOps {
     void (*resid64)(const ResidArgs<double>&, void* stream);
     void (*resid32)(const ResidArgs<float>&, void* stream);
     void (*knorm)(const KnormArgs&, void* stream);
+    // the MHE form (Eq. org_mhe) of this shape, ny measurements per stage
+    int ny;
+    void (*assemble)(long long S, const double* C, const double* R, const double* yt, const double* wt,
+                     double* Q, double* l, double* c, void* stream);
+    void (*prep32)(const PrepArgs&, void* stream);
+    void (*resid_mhe32)(const ResidArgs<float>&, void* stream);
 };
 
 // Memory and small shape-independent steps.
@@ -35,7 +41,10 @@ struct Runtime {
     int (*memset0)(void* p, size_t bytes, void* stream);
     int (*copy)(void* dst, const void* src, size_t bytes, void* stream);   // any direction
     // per instance: relres from norms; mode 0/1 (first/later refinement pass)
-    // sets which instances take another correction, mode 2 fills mhe_info
+    // records relres in info and sets which instances take another correction;
+    // mode 2 fills mhe_info.  refine: bit 0 = refinement ran (a residual above
+    // tol is NO_CONVERGE), bit 1 = the final residual covered only the instances
+    // still active (the others keep the relres recorded by modes 0/1)
     void (*finalize)(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
                      int* iters, const int* status, const int* where, double tol, int mode, int refine,
                      mhe_info* info, void* stream);
@@ -47,7 +56,7 @@ struct Runtime {
     void (*mark)(void* user, int phase, int level, int begin, void* stream);
 };
 
-enum { PH_REDUCE = 0, PH_RHS = 1, PH_DOWN = 2, PH_RESID = 3, PH_COUNT = 4 };
+enum { PH_REDUCE = 0, PH_RHS = 1, PH_DOWN = 2, PH_RESID = 3, PH_PREP = 4, PH_COUNT = 5 };
 
 struct LevelBuf {   // every array of the compute type T
     ChunkDesc* chunks = nullptr;
@@ -94,6 +103,9 @@ public:
     size_t arena_bytes = 0;
 
     const double *A = nullptr, *B = nullptr, *Q = nullptr, *P0inv = nullptr;   // the caller's FP64 problem
+    const double *mheC = nullptr, *mheR = nullptr;   // set: the residual applies Q in its MHE factors
+    double *l64 = nullptr, *Q64 = nullptr;           // mhe_estimate's FP64 l (and Q in FP64 mode)
+    size_t l64_bytes = 0, Q64_bytes = 0;
     const void *mA = nullptr, *mB = nullptr, *mQ = nullptr, *mP0 = nullptr;    // the problem in the compute type
     const int* active_mask = nullptr;   // instances still refining (nullptr: all)
     void* mark_user = nullptr;          // non-null: record per-pass timing marks
@@ -107,6 +119,8 @@ public:
     void release();
     int factor(const mhe_matrices& m, const mhe_rhs* rhs, double* x, double* w, double* lam);
     int solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info, bool after_fused);
+    // steps a0..a7 from MHE data (Eq. org_mhe)
+    int estimate(const mhe_problem& p, double* x, double* w, double* lam, mhe_info* info);
     // serving: re-plan this context for a new batch whose caller stages start at
     // in_off[b] (any offsets into the resident arrays); grows the arena if needed
     int replan(const int* N, int batch, const long long* in_off_custom);

@@ -31,8 +31,9 @@ constexpr int level_warps()
                       : (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)));
 }
 
+// the vector passes keep to 128 registers so that two CTAs fit on an SM
 template <typename T, int NX, int NW, int UPPER, int OP>
-__global__ void __launch_bounds__(256) k_level(LevelArgs<T> a)
+__global__ void __launch_bounds__(256, OP == OP_REDUCE ? 1 : 2) k_level(LevelArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = level_warps<T, NX, OP>();
@@ -68,22 +69,54 @@ void launch_level(const LevelArgs<T>& a, int upper, void* stream)
     else launch_level_v<T, NX, NW, 0, OP>(a, stream);
 }
 
-template <int NX, int NW, typename TR>
+template <int NX, int NW, typename TR, int NY>
 __global__ void __launch_bounds__(256) k_resid(ResidArgs<TR> r)
 {
-    __shared__ unsigned long long sm[8][ResidSmem<NX, NW>::count];
+    __shared__ unsigned long long sm[8][ResidSmem<NX, NW, NY>::count];
     const int warp = threadIdx.x >> 5;
     const long long g = (long long)blockIdx.x * 8 + warp;
     if (g >= r.nstages) return;
-    resid_stage<NX, NW, TR>(r, g, sm[warp]);
+    resid_stage<NX, NW, TR, NY>(r, g, sm[warp]);
 }
 
-template <int NX, int NW, typename TR>
+// NY = 0: Q form; NY > 0: MHE form (C, R)
+template <int NX, int NW, typename TR, int NY = 0>
 void launch_resid(const ResidArgs<TR>& r, void* stream)
 {
     if (r.nstages <= 0) return;
     const long long grid = (r.nstages + 7) / 8;
-    k_resid<NX, NW, TR><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
+    k_resid<NX, NW, TR, NY><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
+}
+
+// warps per block of the one-pass MHE preparation: static shared memory <= 40 KB
+template <int NX, int NW, int NY>
+constexpr int prep_warps()
+{
+    return (40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8) >= 8
+               ? 8
+               : ((40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8) < 1
+                      ? 1
+                      : (40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8));
+}
+
+template <int NX, int NW, int NY>
+__global__ void __launch_bounds__(256) k_prep(PrepArgs p)
+{
+    constexpr int W = prep_warps<NX, NW, NY>();
+    __shared__ double sm[W][PrepSmem<NX, NW, NY>::count];
+    const int warp = threadIdx.x >> 5;
+    const long long g = (long long)blockIdx.x * W + warp;
+    if (g >= p.nstages) return;
+    prep_stage<NX, NW, NY>(p, g, sm[warp]);
+}
+
+template <int NX, int NW, int NY>
+void launch_prep(const PrepArgs& p, void* stream)
+{
+    if (p.nstages <= 0) return;
+    constexpr int W = prep_warps<NX, NW, NY>();
+    const long long grid = (p.nstages + W - 1) / W;
+    k_prep<NX, NW, NY><<<(unsigned)grid, 32 * W, 0, (cudaStream_t)stream>>>(p);
 }
 
 template <int NX, int NW>
@@ -162,6 +195,10 @@ ShapeEntry make_shape()
     e.ops.resid64 = &launch_resid<NX, NW, double>;
     e.ops.resid32 = &launch_resid<NX, NW, float>;
     e.ops.knorm = &launch_knorm<NX, NW>;
+    e.ops.ny = NY;
+    e.ops.assemble = &launch_assemble<NX, NW, NY>;
+    e.ops.prep32 = &launch_prep<NX, NW, NY>;
+    e.ops.resid_mhe32 = &launch_resid<NX, NW, float, NY>;
     e.ny = NY;
     e.assemble = &launch_assemble<NX, NW, NY>;
     return e;

@@ -93,6 +93,75 @@ MHE_DEV T dot4(T init, FA&& fa, FB&& fb)
     return (a0 + a1) + (a2 + a3);
 }
 
+// ---- register-tiled warp products -------------------------------------------
+// Lane tile of a warp product with M x N outputs: the smallest TM x TN whose
+// ceil(M/TM) ceil(N/TN) tiles fit in the 32 lanes (ties: fewest operand loads
+// TM + TN).  A lane keeps its TM x TN accumulators in registers and loads
+// TM + TN operands per step of the inner dimension, so a 24 x 24 product costs
+// 9 shared-memory loads per 18 FMAs instead of two loads per FMA.
+constexpr int tile_pick(int M, int N)
+{
+    int best = 0, cost = 1 << 30;
+    for (int tm = 1; tm <= M; ++tm)
+        for (int tn = 1; tn <= N; ++tn) {
+            if (((M + tm - 1) / tm) * ((N + tn - 1) / tn) > 32) continue;
+            const int c = tm * tn * 256 + tm + tn;
+            if (c < cost) { cost = c; best = tm * 1024 + tn; }
+        }
+    return best;
+}
+
+template <int M, int N>
+struct Tile {
+    static constexpr int TM = tile_pick(M, N) / 1024;
+    static constexpr int TN = tile_pick(M, N) % 1024;
+    static constexpr int GM = (M + TM - 1) / TM;
+    static constexpr int GN = (N + TN - 1) / TN;
+};
+
+// out(i, j, init(i, j) + sum_{p<K} a(i, p) b(p, j)) for i < M, j < N.
+// SYM: only i <= j is formed (init read, out written); the caller mirrors.
+// No lane reads what another lane writes: out may overwrite init's entry.
+template <typename T, int M, int N, int K, bool SYM = false, class FI, class FA, class FB, class FO>
+MHE_DEV void wgemm(FI&& init, FA&& a, FB&& b, FO&& out)
+{
+    using TL = Tile<M, N>;
+    constexpr int TM = TL::TM, TN = TL::TN, GM = TL::GM, GN = TL::GN;
+    constexpr bool em = (M % TM) == 0, en = (N % TN) == 0;
+    wlanes([&](int lane) {
+        if (lane >= GM * GN) return;
+        const int i0 = (lane % GM) * TM, j0 = (lane / GM) * TN;
+        T acc[TM][TN];
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int i = i0 + r, j = j0 + c;
+                const bool in = (em || i < M) && (en || j < N) && (!SYM || i <= j);
+                acc[r][c] = in ? init(i, j) : (T)0;
+            }
+#pragma unroll 4
+        for (int p = 0; p < K; ++p) {
+            T av[TM], bv[TN];
+#pragma unroll
+            for (int r = 0; r < TM; ++r) av[r] = (em || i0 + r < M) ? a(i0 + r, p) : (T)0;
+#pragma unroll
+            for (int c = 0; c < TN; ++c) bv[c] = (en || j0 + c < N) ? b(p, j0 + c) : (T)0;
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[r][c] += av[r] * bv[c];
+        }
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int i = i0 + r, j = j0 + c;
+                if ((em || i < M) && (en || j < N) && (!SYM || i <= j)) out(i, j, acc[r][c]);
+            }
+    });
+}
+
 // upper-triangle index -> (i <= j)
 MHE_DEV void tri_ij(int idx, int& i, int& j)
 {
@@ -152,18 +221,11 @@ MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef<T>& st)
 {
     constexpr int ld = Ws<T, NX>::ld;
     using X = Acc<T, KIND, NX, MT>;
-    wfor(NX * NX + NX * MT + NX, [&](int idx) {
-        if (idx < NX * NX) {
-            int i = idx % NX, j = idx / NX;
-            s.A[i + j * ld] = X::A(st, i, j);
-        } else if (idx < NX * NX + NX * MT) {
-            int r = idx - NX * NX, i = r % NX, j = r / NX;
-            s.B[i + j * ld] = X::B(st, i, j);
-        } else {
-            int i = idx - NX * NX - NX * MT;
-            s.e[i] = X::a(st, i);
-        }
-    });
+    wcopy<NX * NX>([&](int idx) { return X::A(st, idx % NX, idx / NX); },
+                   [&](int idx, T v) { s.A[idx % NX + (idx / NX) * ld] = v; });
+    wcopy<NX * MT>([&](int idx) { return X::B(st, idx % NX, idx / NX); },
+                   [&](int idx, T v) { s.B[idx % NX + (idx / NX) * ld] = v; });
+    wcopy<NX>([&](int i) { return X::a(st, i); }, [&](int i, T v) { s.e[i] = v; });
 }
 
 // In-place lower Cholesky of the M x M matrix Gm (leading dimension ld of the
@@ -238,49 +300,32 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
     load_AB<T, NX, MT, KIND>(s, st);
     // P A -> Tt,  P B -> PB,  u = Psi - P a
-    wfor(NX * NX + NX * MT + NX, [&](int idx) {
-        if (idx < NX * NX) {
-            int i = idx % NX, j = idx / NX;
-            s.Tt[i + j * ld] = dot4<NX>((T)0, [&](int p) { return s.P[i + p * ld]; },
-                                        [&](int p) { return s.A[p + j * ld]; });
-        } else if (idx < NX * NX + NX * MT) {
-            int r = idx - NX * NX, i = r % NX, j = r / NX;
-            s.PB[i + j * ld] = dot4<NX>((T)0, [&](int p) { return s.P[i + p * ld]; },
-                                        [&](int p) { return s.B[p + j * ld]; });
-        } else {
-            int i = idx - NX * NX - NX * MT;
-            s.u[i] = s.Psi[i] - dot4<NX>((T)0, [&](int p) { return s.P[i + p * ld]; },
-                                         [&](int p) { return s.e[p]; });
-        }
-    });
-    // F -> P (upper triangle mirrored), G, H,  g = B^T u - l_w,  tv = A^T u
-    wfor(NT + MTT + NX * MT + MT + NX, [&](int idx) {
-        if (idx < NT) {
-            int i, j;
-            tri_ij(idx, i, j);
-            const T acc = dot4<NX>(X::qx(st, i, j), [&](int p) { return s.A[p + i * ld]; },
-                                   [&](int p) { return s.Tt[p + j * ld]; });
-            s.P[i + j * ld] = acc;
-            s.P[j + i * ld] = acc;
-        } else if (idx < NT + MTT) {
-            int i, j;
-            tri_ij(idx - NT, i, j);
-            const T acc = dot4<NX>(X::qw(st, i, j), [&](int p) { return s.B[p + i * ld]; },
-                                   [&](int p) { return s.PB[p + j * ld]; });
-            s.G[i + j * ld] = acc;
-            s.G[j + i * ld] = acc;
-        } else if (idx < NT + MTT + NX * MT) {
-            int r = idx - NT - MTT, i = r % NX, j = r / NX;
-            s.H[i + j * ld] = dot4<NX>(X::qxw(st, i, j), [&](int p) { return s.A[p + i * ld]; },
-                                       [&](int p) { return s.PB[p + j * ld]; });
-        } else if (idx < NT + MTT + NX * MT + MT) {
-            int j = idx - NT - MTT - NX * MT;
-            s.g[j] = dot4<NX>(-X::lw(st, j), [&](int p) { return s.B[p + j * ld]; }, [&](int p) { return s.u[p]; });
-        } else {
-            int i = idx - NT - MTT - NX * MT - MT;
-            s.tv[i] = dot4<NX>((T)0, [&](int p) { return s.A[p + i * ld]; }, [&](int p) { return s.u[p]; });
-        }
-    });
+    wgemm<T, NX, NX, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.P[i + p * ld]; },
+                         [&](int p, int j) { return s.A[p + j * ld]; },
+                         [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+    wgemm<T, NX, MT, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.P[i + p * ld]; },
+                         [&](int p, int j) { return s.B[p + j * ld]; },
+                         [&](int i, int j, T v) { s.PB[i + j * ld] = v; });
+    wgemm<T, NX, 1, NX>([&](int i, int) { return s.Psi[i]; }, [&](int i, int p) { return -s.P[i + p * ld]; },
+                        [&](int p, int) { return s.e[p]; }, [&](int i, int, T v) { s.u[i] = v; });
+    // F = Q_x + A^T P A -> P (symmetric),  G = Q_w + B^T P B (symmetric),  H = Q_xw + A^T P B,
+    // g = B^T u - l_w,  tv = A^T u
+    wgemm<T, NX, NX, NX, true>([&](int i, int j) { return X::qx(st, i, j); },
+                               [&](int i, int p) { return s.A[p + i * ld]; },
+                               [&](int p, int j) { return s.Tt[p + j * ld]; },
+                               [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
+    wgemm<T, MT, MT, NX, true>([&](int i, int j) { return X::qw(st, i, j); },
+                               [&](int i, int p) { return s.B[p + i * ld]; },
+                               [&](int p, int j) { return s.PB[p + j * ld]; },
+                               [&](int i, int j, T v) { s.G[i + j * ld] = v; s.G[j + i * ld] = v; });
+    wgemm<T, NX, MT, NX>([&](int i, int j) { return X::qxw(st, i, j); },
+                         [&](int i, int p) { return s.A[p + i * ld]; },
+                         [&](int p, int j) { return s.PB[p + j * ld]; },
+                         [&](int i, int j, T v) { s.H[i + j * ld] = v; });
+    wgemm<T, MT, 1, NX>([&](int j, int) { return -X::lw(st, j); }, [&](int j, int p) { return s.B[p + j * ld]; },
+                        [&](int p, int) { return s.u[p]; }, [&](int j, int, T v) { s.g[j] = v; });
+    wgemm<T, NX, 1, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.A[p + i * ld]; },
+                        [&](int p, int) { return s.u[p]; }, [&](int i, int, T v) { s.tv[i] = v; });
     const bool bad = chol_G<T, NX, MT>(s, piv_rel);
     // per column c: y = Lg^{-1} H^T e_c -> Y (in PB), K e_c = -Lg^{-T} y;  lane NX: k = G^{-1} g
     wfor(NX + 1, [&](int c) {
@@ -318,52 +363,35 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
             }
         }
     });
-    // P -= Y^T Y,  Psi = A^T u - l_x + K^T g,  store chol(G)
-    wfor(NT + NX + (Lgout ? MT * MT : 0), [&](int idx) {
-        if (idx < NT) {
-            int i, j;
-            tri_ij(idx, i, j);
-            const T acc = s.P[i + j * ld] - dot4<MT>((T)0, [&](int q) { return s.PB[q + i * ld]; },
-                                                   [&](int q) { return s.PB[q + j * ld]; });
-            s.P[i + j * ld] = acc;
-            s.P[j + i * ld] = acc;
-        } else if (idx < NT + NX) {
-            int i = idx - NT;
-            T acc = s.tv[i] - X::lx(st, i);
-#pragma unroll 8
-            for (int q = 0; q < MT; ++q) acc += s.K[q + i * ld] * s.g[q];
-            s.Psi[i] = acc;
-        } else {
-            int r = idx - NT - NX, i = r % MT, j = r / MT;
+    // P -= Y^T Y (symmetric),  Psi = A^T u - l_x + K^T g,  store chol(G)
+    wgemm<T, NX, NX, MT, true>([&](int i, int j) { return s.P[i + j * ld]; },
+                               [&](int i, int q) { return -s.PB[q + i * ld]; },
+                               [&](int q, int j) { return s.PB[q + j * ld]; },
+                               [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
+    wgemm<T, NX, 1, MT>([&](int i, int) { return s.tv[i] - X::lx(st, i); },
+                        [&](int i, int q) { return s.K[q + i * ld]; }, [&](int q, int) { return s.g[q]; },
+                        [&](int i, int, T v) { s.Psi[i] = v; });
+    if (Lgout)
+        wfor(MT * MT, [&](int r) {
+            const int i = r % MT, j = r / MT;
             Lgout[r] = i >= j ? s.G[i + j * ld] : (T)0;
-        }
-    });
+        });
     if (!want_v) return bad;
     // e = a + B k
-    wfor(NX, [&](int i) {
-        T acc = s.e[i];
-#pragma unroll 8
-        for (int j = 0; j < MT; ++j) acc += s.B[i + j * ld] * s.k[j];
-        s.tv[i] = acc;
-    });
-    // v += V^T e;  per column c: BV = B^T V e_c (in H), Z = Lg^{-1} BV (in PB), L e_c = -Lg^{-T} Z
-    wfor(2 * NX, [&](int idx) {
-        if (idx < NX) {
-            T acc = s.v[idx];
-#pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc += s.V[p + idx * ld] * s.tv[p];
-            s.v[idx] = acc;
-        } else {
-            const int c = idx - NX;
+    wgemm<T, NX, 1, MT>([&](int i, int) { return s.e[i]; }, [&](int i, int j) { return s.B[i + j * ld]; },
+                        [&](int j, int) { return s.k[j]; }, [&](int i, int, T v) { s.tv[i] = v; });
+    // v += V^T e;  BV = B^T V (in H)
+    wgemm<T, NX, 1, NX>([&](int i, int) { return s.v[i]; }, [&](int i, int p) { return s.V[p + i * ld]; },
+                        [&](int p, int) { return s.tv[p]; }, [&](int i, int, T v) { s.v[i] = v; });
+    wgemm<T, MT, NX, NX>([&](int, int) { return (T)0; }, [&](int j, int p) { return s.B[p + j * ld]; },
+                         [&](int p, int c) { return s.V[p + c * ld]; },
+                         [&](int j, int c, T v) { s.H[j + c * ld] = v; });
+    // per column c: Z = Lg^{-1} BV e_c (in PB), L e_c = -Lg^{-T} Z
+    wfor(NX, [&](int c) {
+        {
             T z[MT];
 #pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                T acc = 0;
-#pragma unroll 8
-                for (int p = 0; p < NX; ++p) acc += s.B[p + j * ld] * s.V[p + c * ld];
-                z[j] = acc;
-                s.H[j + c * ld] = acc;
-            }
+            for (int j = 0; j < MT; ++j) z[j] = s.H[j + c * ld];
 #pragma unroll
             for (int j = 0; j < MT; ++j) {
                 T acc = z[j];
@@ -386,21 +414,18 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
             }
         }
     });
-    // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z
-    wfor(NX * NX + NT, [&](int idx) {
-        if (idx < NX * NX) {
-            int i = idx % NX, j = idx / NX;
-            const T av = dot4<NX>((T)0, [&](int p) { return s.A[p + i * ld]; }, [&](int p) { return s.V[p + j * ld]; });
-            s.Tt[i + j * ld] = dot4<MT>(av, [&](int q) { return s.K[q + i * ld]; }, [&](int q) { return s.H[q + j * ld]; });
-        } else {
-            int i, j;
-            tri_ij(idx - NX * NX, i, j);
-            const T acc = dot4<MT>(s.Qw[i + j * ld], [&](int q) { return s.PB[q + i * ld]; },
-                                   [&](int q) { return s.PB[q + j * ld]; });
-            s.Qw[i + j * ld] = acc;
-            s.Qw[j + i * ld] = acc;
-        }
-    });
+    // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z (symmetric)
+    wgemm<T, NX, NX, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.A[p + i * ld]; },
+                         [&](int p, int j) { return s.V[p + j * ld]; },
+                         [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+    wgemm<T, NX, NX, MT>([&](int i, int j) { return s.Tt[i + j * ld]; },
+                         [&](int i, int q) { return s.K[q + i * ld]; },
+                         [&](int q, int j) { return s.H[q + j * ld]; },
+                         [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+    wgemm<T, NX, NX, MT, true>([&](int i, int j) { return s.Qw[i + j * ld]; },
+                               [&](int i, int q) { return s.PB[q + i * ld]; },
+                               [&](int q, int j) { return s.PB[q + j * ld]; },
+                               [&](int i, int j, T v) { s.Qw[i + j * ld] = v; s.Qw[j + i * ld] = v; });
     T* tmp = s.V;
     s.V = s.Tt;
     s.Tt = tmp;
@@ -548,19 +573,13 @@ MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Pin, const T
     constexpr int ld = Ws<T, NX>::ld;
     using X = Acc<T, KIND, NX, MT>;
     load_AB<T, NX, MT, KIND>(s, st);
-    wfor(MT * MT + MT * NX + NX, [&](int idx) {
-        if (idx < MT * MT) {
-            s.G[idx % MT + (idx / MT) * ld] = Lgin[idx];
-        } else if (idx < MT * MT + MT * NX) {
-            int r = idx - MT * MT;
-            s.K[r % MT + (r / MT) * ld] = Kin[r];
-        } else {
-            int i = idx - MT * MT - MT * NX;
-            T acc = s.Psi[i];
+    wcopy<MT * MT>([&](int idx) { return Lgin[idx]; }, [&](int idx, T v) { s.G[idx % MT + (idx / MT) * ld] = v; });
+    wcopy<MT * NX>([&](int idx) { return Kin[idx]; }, [&](int idx, T v) { s.K[idx % MT + (idx / MT) * ld] = v; });
+    wfor(NX, [&](int i) {
+        T acc = s.Psi[i];
 #pragma unroll 8
-            for (int p = 0; p < NX; ++p) acc -= Pin[i + p * NX] * s.e[p];
-            s.u[i] = acc;
-        }
+        for (int p = 0; p < NX; ++p) acc -= Pin[i + p * NX] * s.e[p];
+        s.u[i] = acc;
     });
     wfor(MT + NX, [&](int idx) {
         if (idx < MT) {

@@ -23,6 +23,40 @@ MHE_DEV void wfor(int count, F&& f)
     __syncwarp();
 }
 
+// store(i, load(i)) for i < COUNT, lanes round-robin.  Each lane issues up to
+// 16 loads before its first store, so a block copy has its loads in flight
+// together instead of one memory round trip per element; barrier afterwards.
+template <int COUNT, class L, class S>
+MHE_DEV void wcopy(L&& load, S&& store)
+{
+    constexpr int PER = (COUNT + 31) / 32;
+    constexpr int CH = PER < 16 ? PER : 16;
+    using V = decltype(load(0));
+#pragma unroll
+    for (int k0 = 0; k0 < PER; k0 += CH) {
+        V v[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const int i = lane_id() + 32 * (k0 + k);
+            if (k0 + k < PER && i < COUNT) v[k] = load(i);
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const int i = lane_id() + 32 * (k0 + k);
+            if (k0 + k < PER && i < COUNT) store(i, v[k]);
+        }
+    }
+    __syncwarp();
+}
+
+// Every lane runs f(lane); barrier afterwards.
+template <class F>
+MHE_DEV void wlanes(F&& f)
+{
+    f(lane_id());
+    __syncwarp();
+}
+
 // One lane runs f (index 0); barrier afterwards.
 template <class F>
 MHE_DEV void wone(F&& f)

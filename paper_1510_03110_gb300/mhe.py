@@ -41,6 +41,11 @@ class mhe_rhs(ctypes.Structure):
     _fields_ = [("l", c_void_p), ("a", c_void_p), ("x0", c_void_p)]
 
 
+class mhe_problem(ctypes.Structure):
+    _fields_ = [("ny", c_int), ("A", c_void_p), ("B", c_void_p), ("C", c_void_p), ("R", c_void_p),
+                ("a", c_void_p), ("yt", c_void_p), ("wt", c_void_p), ("x0", c_void_p), ("P0inv", c_void_p)]
+
+
 class mhe_info(ctypes.Structure):
     _fields_ = [("status", c_int), ("level", c_int), ("chunk", c_int), ("stage", c_int),
                 ("refine_iters", c_int), ("pad", c_int), ("relres", c_double), ("est_relerr", c_double)]
@@ -67,6 +72,8 @@ def _declare(L):
     L.mhe_factor_solve.argtypes = [c_void_p, P(mhe_matrices), P(mhe_rhs), c_void_p, c_void_p,
                                    c_void_p, c_void_p]
     L.mhe_factor_solve.restype = c_int
+    L.mhe_estimate.argtypes = [c_void_p, P(mhe_problem), c_void_p, c_void_p, c_void_p, c_void_p]
+    L.mhe_estimate.restype = c_int
     L.mhe_destroy.argtypes = [c_void_p]
     L.mhe_destroy.restype = c_int
     L.mhe_assemble.argtypes = [c_int, c_int, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -192,11 +199,18 @@ def mhe_factor_solve(ctx, A, B, Q, P0inv, l, a, x0, x, w, lam, info=None):
                                          _ptr(lam), ip), "mhe_factor_solve")
 
 
+def mhe_estimate(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info=None):
+    p = mhe_problem(int(ny), _ptr(A), _ptr(B), _ptr(C), _ptr(R), _ptr(a), _ptr(yt), _ptr(wt), _ptr(x0),
+                    _ptr(P0inv))
+    ip = ctypes.c_void_p(info.data_ptr()) if info is not None else None
+    return _check(lib().mhe_estimate(ctx, ctypes.byref(p), _ptr(x), _ptr(w), _ptr(lam), ip), "mhe_estimate")
+
+
 def mhe_destroy(ctx):
     return _check(lib().mhe_destroy(ctx), "mhe_destroy")
 
 
-PHASES = {0: "reduce", 1: "rhs", 2: "down", 3: "resid"}
+PHASES = {0: "reduce", 1: "rhs", 2: "down", 3: "resid", 4: "prep"}
 
 
 def mhe_timing_enable(ctx, enable=True):
@@ -204,13 +218,13 @@ def mhe_timing_enable(ctx, enable=True):
 
 
 def mhe_timing_read(ctx):
-    """[(phase name, level, passes, total ms)] since the last read (synchronises)."""
-    buf = (c_double * 4096)()
+    """[(phase name, level, passes, total ms, longest pass ms)] since the last read (synchronises)."""
+    buf = (c_double * 5120)()
     k = lib().mhe_timing_read(ctx, buf, 1024)
     if k < 0:
         raise MheError(k, "mhe_timing_read")
-    return [(PHASES[int(buf[4 * i])], int(buf[4 * i + 1]), int(buf[4 * i + 2]), float(buf[4 * i + 3]))
-            for i in range(min(k, 1024))]
+    return [(PHASES[int(buf[5 * i])], int(buf[5 * i + 1]), int(buf[5 * i + 2]), float(buf[5 * i + 3]),
+             float(buf[5 * i + 4])) for i in range(min(k, 1024))]
 
 
 def mhe_solve_serial_noalloc(nx, nw, N, A, B, Q, P0inv, l, a, x0, x, w, lam, status=None,
@@ -300,6 +314,12 @@ class Solver:
     def factor_solve(self, A, B, Q, P0inv, l, a, x0, out=None):
         x, w, lam = out if out is not None else self.outputs()
         mhe_factor_solve(self.ctx, A, B, Q, P0inv, l, a, x0, x, w, lam, self.info)
+        return x, w, lam
+
+    def estimate(self, ny, A, B, C, R, a, yt, wt, x0, P0inv, out=None):
+        """Steps a0..a7 from MHE data (mhe_estimate)."""
+        x, w, lam = out if out is not None else self.outputs()
+        mhe_estimate(self.ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, self.info)
         return x, w, lam
 
     def infos(self):

@@ -1,0 +1,108 @@
+"""mhe_estimate (steps a0..a7 from the MHE data of Eq. org_mhe) on the GPU.
+
+FP64 contexts assemble Q and l internally and run the same kernels as
+mhe_assemble + mhe_factor_solve, so their results are bit-identical to that
+path.  FP32_IR contexts form Q only in FP32 and apply it in its factors C, R
+in the FP64 residual: checked against the FP64 oracle at 1e-8 relative error
+and the requested relative residual.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_03110_gb300 import mhe, synth
+
+from gpu_util import device_inputs, rel_err, split
+
+pytestmark = pytest.mark.gpu
+
+
+def _estimate(d, s):
+    return s.estimate(d["q"], d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"])
+
+
+def _oracle(insts):
+    out = []
+    for p in insts:
+        r = oracle.riccati(oracle.mhe_to_uftoc(p))
+        assert r["status"] == 0
+        out.append(r)
+    return out
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (3, 2), (6, 3), (24, 12)])
+def test_fp64_estimate_is_assemble_plus_factor_solve(n, m):
+    import torch
+    Ns = [1, 2, 3, 9, 40, 130]
+    insts = [synth.mhe_instance(300 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    plan = dict(leaf_len=max(4, -(-n // m)), branching=3, top_len=2)
+    s1 = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP64, **plan)
+    x1, w1, l1 = _estimate(d, s1)
+    s2 = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP64, **plan)
+    x2, w2, l2 = s2.factor_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"])
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2) and torch.equal(w1, w2) and torch.equal(l1, l2)
+    ref = _oracle(insts)
+    sols = split(x1, w1, l1, d["N"], n, m)
+    info = s1.infos()
+    for b in range(len(Ns)):
+        assert info["status"][b] == 0
+        assert rel_err(sols[b], ref[b]) <= 1e-10
+    s1.close()
+    s2.close()
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (4, 2), (6, 3), (12, 6), (20, 10), (24, 12)])
+@pytest.mark.parametrize("s_zero", [False, True])
+def test_fp32_estimate_matches_oracle(n, m, s_zero):
+    import torch
+    Ns = [1, 2, 3, 33, 64, 257]
+    insts = [synth.mhe_instance(400 + i, n, m, m, N, s_zero=s_zero) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP32_IR, refine_tol=1e-12, max_refine=8)
+    x, w, lam = _estimate(d, s)
+    torch.cuda.synchronize()
+    sols = split(x, w, lam, d["N"], n, m)
+    info = s.infos()
+    ref = _oracle(insts)
+    for b in range(len(Ns)):
+        assert info["status"][b] == 0, (b, info[b])
+        assert info["relres"][b] <= 1e-12
+        assert rel_err(sols[b], ref[b]) <= 1e-8, (b, rel_err(sols[b], ref[b]))
+    s.close()
+
+
+def test_fp32_estimate_then_solve_new_rhs():
+    """The factorisation from mhe_estimate serves mhe_solve; the residual still
+    applies Q in its factors C, R, against the caller's l."""
+    import torch
+    insts = [synth.mhe_instance(9, 12, 6, 6, 150), synth.mhe_instance(10, 12, 6, 6, 31)]
+    d = device_inputs(insts)
+    s = mhe.Solver(12, 6, d["N"], prec=mhe.MHE_FP32_IR, refine_tol=1e-12, max_refine=8)
+    _estimate(d, s)
+    x, w, lam = s.solve(-0.5 * d["l"], 3.0 * d["a"], d["x0"] + 1.0)
+    torch.cuda.synchronize()
+    info = s.infos()
+    sols = split(x, w, lam, d["N"], 12, 6)
+    for b, p in enumerate(insts):
+        u = oracle.mhe_to_uftoc(p)
+        u2 = u.with_rhs(l=[-0.5 * v for v in u.l], a=[3.0 * v for v in u.a], x0=u.x0 + 1.0)
+        r = oracle.riccati(u2)
+        assert info["status"][b] == 0
+        assert info["relres"][b] <= 1e-12
+        assert rel_err(sols[b], r) <= 1e-8
+    s.close()
+
+
+def test_estimate_argument_errors():
+    insts = [synth.mhe_instance(1, 6, 3, 3, 20)]
+    d = device_inputs(insts)
+    s = mhe.Solver(6, 3, d["N"], prec=mhe.MHE_FP32_IR)
+    with pytest.raises(mhe.MheError) as e:
+        s.estimate(4, d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"])
+    assert e.value.code == -1
+    with pytest.raises(mhe.MheError) as e:
+        s.estimate(3, d["A"], d["B"], None, d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"])
+    assert e.value.code == -1
+    s.close()
