@@ -20,19 +20,16 @@ namespace mhe {
 template <int NX, int NW, int NY = 0>
 struct ResidSmem {
     static constexpr int rows = 5 * NX + NW;
-    static constexpr int count = 3 * rows + 4 + 2 * NY;   // 8-byte entries (the last 2 NY: u, e of the MHE form)
+    static constexpr int q_form = 3 * rows + 4;                      // resid_rows
+    static constexpr int mhe_form = 4 * NX + 3 * NW + 3 * NY + 5;    // resid_mhe
+    static constexpr int count = q_form > mhe_form ? q_form : mhe_form;   // 8-byte entries
 };
 
 // One stage t of instance b: rows of stationarity in x_t and w_t, dynamics
 // t -> t+1, plus the initial rows (t = 0) and the terminal rows (t = N-1).
 // The FP64 work is the products of the rows alone; the maxima of |r|, |z|,
 // |b| are taken on bit patterns (integer operations).
-// NY > 0: the MHE form, Q z of stage t >= 1 from C and R (Section II):
-//   u = C x_t,  e = V u - S^T w_t,
-//   [Q z]_x = C^T e,  [Q z]_w = W w_t - S u,
-// the same product as with the assembled Q at 2 n ny + 2 ny nw + ny^2 + nw^2
-// FMAs instead of (n + nw)^2.
-template <int NX, int NW, int KIND, typename TR, int NY = 0>
+template <int NX, int NW, int KIND, typename TR>
 MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned long long* sm)
 {
     constexpr int MT = (KIND == 1) ? NX : NW;   // the arrival stage has width n
@@ -47,26 +44,7 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
     const long long s = r.in_off[b] + t - 1;
     const double* A = (KIND == 1) ? nullptr : r.A + s * NX * NX;
     const double* B = (KIND == 1) ? nullptr : r.B + s * NX * NW;
-    const double* Q = (KIND == 1 || NY > 0) ? nullptr : r.Q + s * (NX + NW) * (NX + NW);
-    constexpr int NR = NW + NY;
-    const double* C = (KIND == 1 || NY == 0) ? nullptr : r.C + s * NY * NX;
-    const double* R = (KIND == 1 || NY == 0) ? nullptr : r.R + s * NR * NR;
-    double* su = reinterpret_cast<double*>(sm + 3 * ROWS + 4);
-    double* se = su + NY;
-    if (KIND == 0 && NY > 0) {
-        // V(p,q) = R[NW+p + (NW+q) NR], S(i,q) = R[i + (NW+q) NR], W(i,j) = R[i + j NR]
-        wfor(NY, [&](int p) {
-            double acc = 0.0;
-            for (int j = 0; j < NX; ++j) acc = fma(C[p + j * NY], xt[j], acc);
-            su[p] = acc;
-        });
-        wfor(NY, [&](int p) {
-            double acc = 0.0;
-            for (int q = 0; q < NY; ++q) acc = fma(R[NW + p + (NW + q) * NR], su[q], acc);
-            for (int i = 0; i < NW; ++i) acc = fma(-R[i + (NW + p) * NR], wt[i], acc);
-            se[p] = acc;
-        });
-    }
+    const double* Q = (KIND == 1) ? nullptr : r.Q + s * (NX + NW) * (NX + NW);
     const double* P0 = r.P0inv + (long long)b * NX * NX;
     const double* l = (KIND == 1) ? nullptr : (r.l ? r.l + s * (NX + NW) : nullptr);
     const double* a = (KIND == 1) ? nullptr : (r.a ? r.a + s * NX : nullptr);
@@ -94,18 +72,8 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
                 }
             } else {
                 acc = 0.0;
-                if (NY > 0) {
-                    if (i < NX) {
-                        for (int p = 0; p < NY; ++p) acc = fma(C[p + i * NY], se[p], acc);
-                    } else {
-                        const int ii = i - NX;
-                        for (int j = 0; j < NW; ++j) acc = fma(R[ii + j * NR], wt[j], acc);
-                        for (int p = 0; p < NY; ++p) acc = fma(-R[ii + (NW + p) * NR], su[p], acc);
-                    }
-                } else {
-                    for (int j = 0; j < NX; ++j) acc = fma(Q[i + j * NQ], xt[j], acc);
-                    for (int j = 0; j < MT; ++j) acc = fma(Q[i + (NX + j) * NQ], wt[j], acc);
-                }
+                for (int j = 0; j < NX; ++j) acc = fma(Q[i + j * NQ], xt[j], acc);
+                for (int j = 0; j < MT; ++j) acc = fma(Q[i + (NX + j) * NQ], wt[j], acc);
                 if (i < NX) {
                     for (int j = 0; j < NX; ++j) acc = fma(A[j + i * NX], ln[j], acc);
                     acc -= lt[i];
@@ -164,6 +132,134 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
     });
 }
 
+// Stage t >= 1 in the MHE form (Section II): Q z from C and R,
+//   u = C x_t,  e = V u - S^T w_t,  [Q z]_x = C^T e,  [Q z]_w = W w_t - S u,
+// the same rows as resid_rows.  The FP64 work is cut into dot products dealt
+// round-robin to the lanes; a lane only selects the pointers, stride and length
+// of its dot product, and all lanes then run one predicated FMA loop, so the
+// FP64 instructions (the pipe that bounds this kernel) issue without branch
+// divergence:
+//   1. length n : A x, u = C x, A^T lam_{t+1}, B^T lam_{t+1};
+//      length nw: B w, W w, S^T w
+//   2. e = V u - S^T w, S u          3. C^T e
+//   4. the rows  p1 + p2 - p3 + p4:  C^T e + A^T lam - lam_t + l_x;
+//      W w + B^T lam - S u + l_w;  A x + B w - x_{t+1} + a;  terminal rows
+// Each lane keeps its maxima of |r|, |z|, |b| and merges them once.
+template <int KMAX>
+MHE_DEV double dot_pred(const double* m, int sm, const double* v, int k, double acc)
+{
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j < k) acc = fma(m[j * sm], v[j], acc);
+    return acc;
+}
+
+template <int NX, int NW, int NY, typename TR>
+MHE_DEV void resid_mhe(const ResidArgs<TR>& r, int b, int t, int N, unsigned long long* sm)
+{
+    constexpr int NR = NW + NY, NQ = NX + NW;
+    const long long gx = r.gs0[b] + b;
+    const double* xt = r.x + (gx + t) * NX;
+    const double* xn = xt + NX;
+    const double* lt = r.lam + (gx + t) * NX;
+    const double* ln = lt + NX;
+    const double* wt = r.w + r.w_off[b] + NX + (long long)(t - 1) * NW;
+    const long long s = r.in_off[b] + t - 1;
+    const double* A = r.A + s * NX * NX;
+    const double* B = r.B + s * NX * NW;
+    const double* C = r.C + s * NY * NX;
+    const double* R = r.R + s * NR * NR;
+    const double* l = r.l ? r.l + s * NQ : nullptr;
+    const double* a = r.a ? r.a + s * NX : nullptr;
+    const long long so = r.out_off[b] + t - 1;
+    TR* rl = r.rl + so * NQ;
+    TR* ra = r.ra + so * NX;
+    const bool lastst = (t == N - 1);
+    double* dA = reinterpret_cast<double*>(sm);   // A x
+    double* dB = dA + NX;                         // B w
+    double* atl = dB + NX;                        // A^T lam_{t+1}
+    double* cte = atl + NX;                       // C^T e
+    double* u = cte + NX;                         // C x
+    double* sw = u + NY;                          // S^T w
+    double* e = sw + NY;                          // V u - S^T w
+    double* btl = e + NY;                         // B^T lam_{t+1}
+    double* ww = btl + NW;                        // W w
+    double* su = ww + NW;                         // S u
+    double* zero = su + NW;
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(zero + 1);
+    wone([&](int) {
+        zero[0] = 0.0;
+        mx[0] = mx[1] = mx[2] = 0ULL;
+    });
+    // V(p,q) = R[NW+p + (NW+q) NR], S(k,p) = R[k + (NW+p) NR], W(k,j) = R[k + j NR]
+    constexpr int T1 = NX + NY + NX + NW;   // length-n tasks, then length-nw tasks
+    wfor(T1 + NX + NW + NY, [&](int k) {
+        const double* m;
+        const double* v;
+        double* o;
+        int st, len = NX;
+        if (k < NX) { m = A + k; st = NX; v = xt; o = dA + k; }
+        else if (k < NX + NY) { m = C + (k - NX); st = NY; v = xt; o = u + (k - NX); }
+        else if (k < 2 * NX + NY) { m = A + (k - NX - NY) * NX; st = 1; v = ln; o = atl + (k - NX - NY); }
+        else if (k < T1) { m = B + (k - 2 * NX - NY) * NX; st = 1; v = ln; o = btl + (k - 2 * NX - NY); }
+        else if (k < T1 + NX) { m = B + (k - T1); st = NX; v = wt; o = dB + (k - T1); len = NW; }
+        else if (k < T1 + NX + NW) { m = R + (k - T1 - NX); st = NR; v = wt; o = ww + (k - T1 - NX); len = NW; }
+        else { m = R + (NW + k - T1 - NX - NW) * NR; st = 1; v = wt; o = sw + (k - T1 - NX - NW); len = NW; }
+        *o = dot_pred<(NX > NW ? NX : NW)>(m, st, v, len, 0.0);
+    });
+    wfor(NY + NW, [&](int k) {
+        const double* m;
+        double* o;
+        double init;
+        if (k < NY) { m = R + NW + k + NW * NR; o = e + k; init = -sw[k]; }
+        else { m = R + (k - NY) + NW * NR; o = su + (k - NY); init = 0.0; }
+        *o = dot_pred<NY>(m, NR, u, NY, init);
+    });
+    wfor(NX, [&](int i) { cte[i] = dot_pred<NY>(C + i * NY, 1, e, NY, 0.0); });
+    unsigned long long m0 = 0, m1 = 0, m2 = 0;
+    const int nrow = NQ + NX + (lastst ? NX : 0);
+    const double* xN = r.x + (gx + N) * NX;
+    const double* lamN = r.lam + (gx + N) * NX;
+    wfor(nrow, [&](int i) {
+        const double *p1, *p2, *p3, *p4, *z1, *z2;
+        TR* dst;
+        if (i < NX) {
+            p1 = cte + i; p2 = atl + i; p3 = lt + i; p4 = l ? l + i : zero;
+            z1 = xt + i; z2 = lt + i; dst = rl + i;
+        } else if (i < NQ) {
+            const int q = i - NX;
+            p1 = ww + q; p2 = btl + q; p3 = su + q; p4 = l ? l + i : zero;
+            z1 = wt + q; z2 = zero; dst = rl + i;
+        } else if (i < NQ + NX) {
+            const int ii = i - NQ;
+            p1 = dA + ii; p2 = dB + ii; p3 = xn + ii; p4 = a ? a + ii : zero;
+            z1 = zero; z2 = zero; dst = ra + ii;
+        } else {
+            // terminal rows with Q_{x,N} = 0, l_N = 0: r = lambda_N
+            const int ii = i - NQ - NX;
+            p1 = zero; p2 = zero; p3 = lamN + ii; p4 = zero;
+            z1 = xN + ii; z2 = lamN + ii; dst = r.rlN + (long long)b * NX + ii;
+        }
+        const double sum = *p4 + ((*p1 + *p2) - *p3);   // r = -(l + K z) for the stationarity and dynamics rows
+        *dst = (TR)sum;
+        const unsigned long long rr = abs_bits(sum), bb = abs_bits(*p4);
+        const unsigned long long za = abs_bits(*z1), zb = abs_bits(*z2);
+        const unsigned long long zz = za > zb ? za : zb;
+        m0 = rr > m0 ? rr : m0;
+        m1 = zz > m1 ? zz : m1;
+        m2 = bb > m2 ? bb : m2;
+    });
+    atomic_max_u64(mx + 0, m0);
+    atomic_max_u64(mx + 1, m1);
+    atomic_max_u64(mx + 2, m2);
+    wsync();
+    wone([&](int) {
+        atomic_max_u64(r.norms + 3LL * b + 0, mx[0]);
+        atomic_max_u64(r.norms + 3LL * b + 1, mx[1]);
+        atomic_max_u64(r.norms + 3LL * b + 2, mx[2]);
+    });
+}
+
 MHE_DEV int stage_instance(const long long* gs0, int batch, long long gstage)
 {
     int lo = 0, hi = batch;
@@ -181,8 +277,12 @@ MHE_DEV void resid_stage(const ResidArgs<TR>& r, long long gstage, unsigned long
     if (r.active && !r.active[b]) return;
     const int t = (int)(gstage - r.gs0[b]);
     const int N = (int)(r.gs0[b + 1] - r.gs0[b]);
-    if (t == 0) resid_rows<NX, NW, 1, TR, NY>(r, b, t, N, sm);
-    else resid_rows<NX, NW, 0, TR, NY>(r, b, t, N, sm);
+    if (t == 0) {
+        resid_rows<NX, NW, 1, TR>(r, b, t, N, sm);
+    } else {
+        if constexpr (NY > 0) resid_mhe<NX, NW, NY, TR>(r, b, t, N, sm);
+        else resid_rows<NX, NW, 0, TR>(r, b, t, N, sm);
+    }
 }
 
 // ||K||_inf contribution of one stage: absolute row sums (in float) of the KKT

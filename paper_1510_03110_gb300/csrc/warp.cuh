@@ -49,6 +49,9 @@ MHE_DEV void wcopy(L&& load, S&& store)
     __syncwarp();
 }
 
+// Barrier of the warp's lanes.
+MHE_DEV void wsync() { __syncwarp(); }
+
 // Every lane runs f(lane); barrier afterwards.
 template <class F>
 MHE_DEV void wlanes(F&& f)
