@@ -14,6 +14,7 @@
 #include "common.h"
 #include "f32conv.h"
 #include "warp.cuh"
+#include "wgemm.cuh"
 
 namespace mhe {
 
@@ -427,12 +428,15 @@ MHE_DEV void assemble_stage(const double* C, const double* R, const double* yt, 
 // the right-hand side the residual is measured against) and its FP32 copy; the
 // stage's rows of ||K||_inf.  Per arrival stage: FP32 copies of P~0^{-1} and
 // x~0 and their rows of ||K||_inf.  The constant c is not formed.
+// One batched load of every input block, register-tiled FP32 products, and the
+// FP64 dot products of l dealt to lanes without branch divergence.
 template <int NX, int NW, int NY>
 struct PrepSmem {
     static constexpr int NR = NW + NY;
-    static constexpr int nd = NY * NX + NR * NR + NY + NW + NY;                          // doubles
-    static constexpr int nf = NY * NX + NR * NR + NY * NX + NW * NX + NX * NX + 2 * NX + NW + 1;   // floats
-    static constexpr int count = nd + (nf + 1) / 2;                                      // 8-byte words
+    static constexpr int nd = NY + NW + NY;   // doubles: y~, w~, t = S^T w~ - V y~
+    // floats: C, R, V C, S C, Q_x, A, B, row sums
+    static constexpr int nf = NY * NX + NR * NR + NY * NX + NW * NX + NX * NX + NX * NX + NX * NW + 2 * NX + NW + 1;
+    static constexpr int count = nd + (nf + 1) / 2;   // 8-byte words
 };
 
 template <int NX, int NW, int NY>
@@ -441,17 +445,26 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
     constexpr int NR = NW + NY, NQ = NX + NW;
     const int b = stage_instance(p.gs0, p.batch, gstage);
     const int t = (int)(gstage - p.gs0[b]);
-    float* rsum = reinterpret_cast<float*>(sm + PrepSmem<NX, NW, NY>::nd) + NY * NX + NR * NR + NY * NX +
-                  NW * NX + NX * NX;
+    double* dy = sm;
+    double* dw = dy + NY;
+    double* dt = dw + NW;
+    float* fC = reinterpret_cast<float*>(sm + PrepSmem<NX, NW, NY>::nd);
+    float* fR = fC + NY * NX;
+    float* fVC = fR + NR * NR;
+    float* fSC = fVC + NY * NX;
+    float* fQx = fSC + NW * NX;
+    float* fA = fQx + NX * NX;
+    float* fB = fA + NX * NX;
+    float* rsum = fB + NX * NW;
     if (t == 0) {
         // arrival stage: x rows 1 + 1, w rows |P~0^{-1} row| + 1, dynamics rows 3, initial row 1
         const double* P0 = p.P0inv + (long long)b * NX * NX;
         float* P0f = p.P0_32 + (long long)b * NX * NX;
-        wfor(NX * NX, [&](int i) { P0f[i] = f32_rn(P0[i]); });
+        wcopy<NX * NX>([&](int i) { return P0[i]; }, [&](int i, double v) { P0f[i] = f32_rn(v); fA[i] = f32_rn(v); });
         wfor(NX, [&](int i) {
             p.x0_32[(long long)b * NX + i] = f32_rn(p.x0[(long long)b * NX + i]);
             float rs = 1.f;
-            for (int j = 0; j < NX; ++j) rs += abs_to_float(P0[i + j * NX]);
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[i + j * NX]);
             rsum[i] = rs > 3.f ? rs : 3.f;
         });
         wone([&](int) {
@@ -468,69 +481,72 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
     const double* R = p.R + s * NR * NR;
     const double* yt = p.yt + s * NY;
     const double* wt = p.wt + s * NW;
-    double* dC = sm;
-    double* dR = dC + NY * NX;
-    double* dy = dR + NR * NR;
-    double* dw = dy + NY;
-    double* dt = dw + NW;   // S^T w~ - V y~ (ny)
-    float* fC = reinterpret_cast<float*>(sm + PrepSmem<NX, NW, NY>::nd);
-    float* fR = fC + NY * NX;
-    float* fVC = fR + NR * NR;
-    float* fSC = fVC + NY * NX;
-    float* fQx = fSC + NW * NX;
+    const double* av = p.a + s * NX;
+    float* A32 = p.A32 + s * NX * NX;
+    float* B32 = p.B32 + s * NX * NW;
+    float* a32 = p.a32 + s * NX;
     float* Qo = p.Q32 + s * NQ * NQ;
     double* lo = p.l + s * NQ;
     float* lo32 = p.l32 + s * NQ;
-    // inputs to shared memory; A, B, a straight to their FP32 copies
-    wcopy<NY * NX>([&](int i) { return C[i]; }, [&](int i, double v) { dC[i] = v; fC[i] = f32_rn(v); });
-    wcopy<NR * NR>([&](int i) { return R[i]; }, [&](int i, double v) { dR[i] = v; fR[i] = f32_rn(v); });
-    wcopy<NY + NW>([&](int i) { return i < NY ? yt[i] : wt[i - NY]; }, [&](int i, double v) { dy[i] = v; });
-    wcopy<NX * NX>([&](int i) { return A[i]; }, [&](int i, double v) { p.A32[s * NX * NX + i] = f32_rn(v); });
-    wcopy<NX * NW>([&](int i) { return B[i]; }, [&](int i, double v) { p.B32[s * NX * NW + i] = f32_rn(v); });
-    wcopy<NX>([&](int i) { return p.a[s * NX + i]; }, [&](int i, double v) { p.a32[s * NX + i] = f32_rn(v); });
-    // V(p,q) = R[NW+p + (NW+q) NR], S(i,q) = R[i + (NW+q) NR], W(i,j) = R[i + j NR]
-    wfor(NY * NX + NW * NX + NY + NW, [&](int idx) {
-        if (idx < NY * NX) {
-            const int pp = idx % NY, j = idx / NY;
-            float acc = 0.f;
-            for (int q = 0; q < NY; ++q) acc += fR[NW + pp + (NW + q) * NR] * fC[q + j * NY];
-            fVC[idx] = acc;
-        } else if (idx < NY * NX + NW * NX) {
-            const int r = idx - NY * NX, i = r % NW, j = r / NW;
-            float acc = 0.f;
-            for (int q = 0; q < NY; ++q) acc += fR[i + (NW + q) * NR] * fC[q + j * NY];
-            fSC[r] = acc;
-        } else if (idx < NY * NX + NW * NX + NY) {
-            const int pp = idx - NY * NX - NW * NX;
-            double acc = 0.0;
-            for (int q = 0; q < NW; ++q) acc = fma(dR[q + (NW + pp) * NR], dw[q], acc);
-            for (int q = 0; q < NY; ++q) acc = fma(-dR[NW + pp + (NW + q) * NR], dy[q], acc);
-            dt[pp] = acc;
+    // every input block of the stage in one batched load: [C | R | A | B | y~ | w~ | a]
+    constexpr int O1 = NY * NX, O2 = O1 + NR * NR, O3 = O2 + NX * NX, O4 = O3 + NX * NW, O5 = O4 + NY + NW;
+    constexpr int TOT = O5 + NX;
+    constexpr int PER = (TOT + 31) / 32;
+    wcopy<TOT, (PER + 1) / 2>(
+        [&](int i) {
+            if (i < O1) return C[i];
+            if (i < O2) return R[i - O1];
+            if (i < O3) return A[i - O2];
+            if (i < O4) return B[i - O3];
+            if (i < O4 + NY) return yt[i - O4];
+            if (i < O5) return wt[i - O4 - NY];
+            return av[i - O5];
+        },
+        [&](int i, double v) {
+            const float f = f32_rn(v);
+            if (i < O1) fC[i] = f;
+            else if (i < O2) fR[i - O1] = f;
+            else if (i < O3) { A32[i - O2] = f; fA[i - O2] = f; }
+            else if (i < O4) { B32[i - O3] = f; fB[i - O3] = f; }
+            else if (i < O5) dy[i - O4] = v;   // y~ then w~ (contiguous)
+            else a32[i - O5] = f;
+        });
+    // FP32: V C and S C;  V(p,q) = R[NW+p + (NW+q) NR], S(k,q) = R[k + (NW+q) NR], W(k,j) = R[k + j NR]
+    wgemm<float, NY, NX, NY>([&](int, int) { return 0.f; }, [&](int i, int q) { return fR[NW + i + (NW + q) * NR]; },
+                             [&](int q, int j) { return fC[q + j * NY]; },
+                             [&](int i, int j, float v) { fVC[i + j * NY] = v; });
+    wgemm<float, NW, NX, NY>([&](int, int) { return 0.f; }, [&](int k, int q) { return fR[k + (NW + q) * NR]; },
+                             [&](int q, int j) { return fC[q + j * NY]; },
+                             [&](int k, int j, float v) { fSC[k + j * NW] = v; });
+    // FP64: t = S^T w~ - V y~ (ny) and l_w = S y~ - W w~ (nw): two dot products per lane
+    wfor(NY + NW, [&](int k) {
+        const double *m1, *v1, *m2, *v2;
+        int s1, k1, s2, k2;
+        if (k < NY) {
+            m1 = R + (NW + k) * NR; s1 = 1; v1 = dw; k1 = NW;          // S^T w~
+            m2 = R + NW + k + NW * NR; s2 = NR; v2 = dy; k2 = NY;      // V y~
         } else {
-            const int i = idx - NY * NX - NW * NX - NY;
-            double acc = 0.0;
-            for (int q = 0; q < NY; ++q) acc = fma(dR[i + (NW + q) * NR], dy[q], acc);
-            for (int q = 0; q < NW; ++q) acc = fma(-dR[i + q * NR], dw[q], acc);
-            lo[NX + i] = acc;
-            lo32[NX + i] = f32_rn(acc);
+            const int q = k - NY;
+            m1 = R + q + NW * NR; s1 = NR; v1 = dy; k1 = NY;           // S y~
+            m2 = R + q; s2 = NR; v2 = dw; k2 = NW;                     // W w~
+        }
+        const double d = dot_pred<(NW > NY ? NW : NY)>(m1, s1, v1, k1, 0.0) -
+                         dot_pred<(NW > NY ? NW : NY)>(m2, s2, v2, k2, 0.0);
+        if (k < NY) {
+            dt[k] = d;
+        } else {
+            lo[NX + k - NY] = d;
+            lo32[NX + k - NY] = f32_rn(d);
         }
     });
-    // Q_x = C^T (V C) (one triangle, mirrored) and l_x = C^T t
-    wfor(NX * NX + NX, [&](int idx) {
-        if (idx < NX * NX) {
-            const int i = idx % NX, j = idx / NX;
-            if (i > j) return;
-            float acc = 0.f;
-            for (int q = 0; q < NY; ++q) acc += fC[q + i * NY] * fVC[q + j * NY];
-            fQx[i + j * NX] = acc;
-            fQx[j + i * NX] = acc;
-        } else {
-            const int i = idx - NX * NX;
-            double acc = 0.0;
-            for (int q = 0; q < NY; ++q) acc = fma(dC[q + i * NY], dt[q], acc);
-            lo[i] = acc;
-            lo32[i] = f32_rn(acc);
-        }
+    // FP32: Q_x = C^T (V C) (one triangle, mirrored);  FP64: l_x = C^T t
+    wgemm<float, NX, NX, NY, true>([&](int, int) { return 0.f; }, [&](int i, int q) { return fC[q + i * NY]; },
+                                   [&](int q, int j) { return fVC[q + j * NY]; },
+                                   [&](int i, int j, float v) { fQx[i + j * NX] = v; fQx[j + i * NX] = v; });
+    wfor(NX, [&](int i) {
+        const double d = dot_pred<NY>(C + i * NY, 1, dt, NY, 0.0);
+        lo[i] = d;
+        lo32[i] = f32_rn(d);
     });
     auto qf = [&](int i, int j) -> float {
         if (i < NX && j < NX) return fQx[i + j * NX];
@@ -545,13 +561,13 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
         if (i < NQ) {
             rs = (i < NX) ? 1.f : 0.f;
             for (int j = 0; j < NQ; ++j) rs += mabs(qf(i, j));
-            if (i < NX) for (int j = 0; j < NX; ++j) rs += abs_to_float(A[j + i * NX]);
-            else for (int j = 0; j < NX; ++j) rs += abs_to_float(B[j + (i - NX) * NX]);
+            if (i < NX) for (int j = 0; j < NX; ++j) rs += mabs(fA[j + i * NX]);
+            else for (int j = 0; j < NX; ++j) rs += mabs(fB[j + (i - NX) * NX]);
         } else {
             const int ii = i - NQ;
             rs = 1.f;
-            for (int j = 0; j < NX; ++j) rs += abs_to_float(A[ii + j * NX]);
-            for (int j = 0; j < NW; ++j) rs += abs_to_float(B[ii + j * NX]);
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[ii + j * NX]);
+            for (int j = 0; j < NW; ++j) rs += mabs(fB[ii + j * NX]);
         }
         rsum[i] = rs;
     });

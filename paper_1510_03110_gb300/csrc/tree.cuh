@@ -27,6 +27,7 @@
 #pragma once
 #include "common.h"
 #include "warp.cuh"
+#include "wgemm.cuh"
 
 namespace mhe {
 
@@ -91,75 +92,6 @@ MHE_DEV T dot4(T init, FA&& fa, FB&& fb)
 #pragma unroll
     for (int p = K & ~3; p < K; ++p) a0 += fa(p) * fb(p);
     return (a0 + a1) + (a2 + a3);
-}
-
-// ---- register-tiled warp products -------------------------------------------
-// Lane tile of a warp product with M x N outputs: the smallest TM x TN whose
-// ceil(M/TM) ceil(N/TN) tiles fit in the 32 lanes (ties: fewest operand loads
-// TM + TN).  A lane keeps its TM x TN accumulators in registers and loads
-// TM + TN operands per step of the inner dimension, so a 24 x 24 product costs
-// 9 shared-memory loads per 18 FMAs instead of two loads per FMA.
-constexpr int tile_pick(int M, int N)
-{
-    int best = 0, cost = 1 << 30;
-    for (int tm = 1; tm <= M; ++tm)
-        for (int tn = 1; tn <= N; ++tn) {
-            if (((M + tm - 1) / tm) * ((N + tn - 1) / tn) > 32) continue;
-            const int c = tm * tn * 256 + tm + tn;
-            if (c < cost) { cost = c; best = tm * 1024 + tn; }
-        }
-    return best;
-}
-
-template <int M, int N>
-struct Tile {
-    static constexpr int TM = tile_pick(M, N) / 1024;
-    static constexpr int TN = tile_pick(M, N) % 1024;
-    static constexpr int GM = (M + TM - 1) / TM;
-    static constexpr int GN = (N + TN - 1) / TN;
-};
-
-// out(i, j, init(i, j) + sum_{p<K} a(i, p) b(p, j)) for i < M, j < N.
-// SYM: only i <= j is formed (init read, out written); the caller mirrors.
-// No lane reads what another lane writes: out may overwrite init's entry.
-template <typename T, int M, int N, int K, bool SYM = false, class FI, class FA, class FB, class FO>
-MHE_DEV void wgemm(FI&& init, FA&& a, FB&& b, FO&& out)
-{
-    using TL = Tile<M, N>;
-    constexpr int TM = TL::TM, TN = TL::TN, GM = TL::GM, GN = TL::GN;
-    constexpr bool em = (M % TM) == 0, en = (N % TN) == 0;
-    wlanes([&](int lane) {
-        if (lane >= GM * GN) return;
-        const int i0 = (lane % GM) * TM, j0 = (lane / GM) * TN;
-        T acc[TM][TN];
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-            for (int c = 0; c < TN; ++c) {
-                const int i = i0 + r, j = j0 + c;
-                const bool in = (em || i < M) && (en || j < N) && (!SYM || i <= j);
-                acc[r][c] = in ? init(i, j) : (T)0;
-            }
-#pragma unroll 4
-        for (int p = 0; p < K; ++p) {
-            T av[TM], bv[TN];
-#pragma unroll
-            for (int r = 0; r < TM; ++r) av[r] = (em || i0 + r < M) ? a(i0 + r, p) : (T)0;
-#pragma unroll
-            for (int c = 0; c < TN; ++c) bv[c] = (en || j0 + c < N) ? b(p, j0 + c) : (T)0;
-#pragma unroll
-            for (int r = 0; r < TM; ++r)
-#pragma unroll
-                for (int c = 0; c < TN; ++c) acc[r][c] += av[r] * bv[c];
-        }
-#pragma unroll
-        for (int r = 0; r < TM; ++r)
-#pragma unroll
-            for (int c = 0; c < TN; ++c) {
-                const int i = i0 + r, j = j0 + c;
-                if ((em || i < M) && (en || j < N) && (!SYM || i <= j)) out(i, j, acc[r][c]);
-            }
-    });
 }
 
 // upper-triangle index -> (i <= j)

@@ -24,13 +24,13 @@ MHE_DEV void wfor(int count, F&& f)
 }
 
 // store(i, load(i)) for i < COUNT, lanes round-robin.  Each lane issues up to
-// 16 loads before its first store, so a block copy has its loads in flight
+// MAXCH loads before its first store, so a block copy has its loads in flight
 // together instead of one memory round trip per element; barrier afterwards.
-template <int COUNT, class L, class S>
+template <int COUNT, int MAXCH = 16, class L, class S>
 MHE_DEV void wcopy(L&& load, S&& store)
 {
     constexpr int PER = (COUNT + 31) / 32;
-    constexpr int CH = PER < 16 ? PER : 16;
+    constexpr int CH = PER < MAXCH ? PER : MAXCH;
     using V = decltype(load(0));
 #pragma unroll
     for (int k0 = 0; k0 < PER; k0 += CH) {
