@@ -31,9 +31,19 @@ constexpr int level_warps()
                       : (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)));
 }
 
-// the vector passes keep to 128 registers so that two CTAs fit on an SM
+// CTAs of 256 threads per SM the register allocation is sized for: the small
+// shapes' workspaces are small, so their occupancy is set by registers (64 or
+// 80 per thread keep 32 or 24 warps per SM); the n = 24 reduction keeps its
+// 255 registers (shared memory allows one CTA anyway), its vector passes 128.
+template <typename T, int NX, int OP>
+constexpr int level_min_blocks()
+{
+    return sizeof(T) == 4 ? (NX <= 8 ? 4 : (NX <= 12 ? 3 : (OP == OP_REDUCE ? 1 : 2)))
+                          : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2));
+}
+
 template <typename T, int NX, int NW, int UPPER, int OP>
-__global__ void __launch_bounds__(256, OP == OP_REDUCE ? 1 : 2) k_level(LevelArgs<T> a)
+__global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(LevelArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = level_warps<T, NX, OP>();

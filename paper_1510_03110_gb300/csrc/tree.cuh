@@ -162,10 +162,24 @@ MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef<T>& st)
 
 // In-place lower Cholesky of the M x M matrix Gm (leading dimension ld of the
 // workspace).  Returns true when a pivot fell below piv_rel * max diag (the
-// pivot is then replaced by 1 to stay finite).
-template <typename T, int NX, int M>
+// pivot is then replaced by 1 to stay finite).  Lane i owns row i of the lower
+// triangle: at column j lane j takes the square root, the lanes below scale
+// their entry of column j and update their own row, so no two lanes write the
+// same entry and a column costs two barriers.  INV (FP32 only) stores 1 / L_jj
+// on the diagonal, the form the FP32 triangular solves use (a multiply per
+// pivot; the refinement absorbs the extra rounding).  FP64 keeps L_jj and
+// divides, which keeps the unrefined FP64 tree within 1e-10 of the oracle.
+template <typename T>
+MHE_DEV T pivot_div(T acc, T gjj)
+{
+    if constexpr (sizeof(T) == 4) return acc * gjj;   // gjj = 1 / L_jj
+    else return acc / gjj;
+}
+
+template <typename T, int NX, int M, bool INV = false>
 MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
 {
+    static_assert(M <= 32 && M <= NX, "one lane per row");
     constexpr int ld = Ws<T, NX>::ld;
     wone([&](int) {
         T mx = 0;
@@ -177,14 +191,21 @@ MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
         wone([&](int) {
             T d = Gm[j + j * ld];
             if (!(d > s.sc[0])) { s.sc[1] = 1; d = 1; }
-            Gm[j + j * ld] = msqrt(d);
+            const T l = msqrt(d);
+            s.sc[2] = l;
+            Gm[j + j * ld] = (INV && sizeof(T) == 4) ? (T)1 / l : l;
         });
-        const T djj = Gm[j + j * ld];
-        wfor(M - j - 1, [&](int r) { Gm[j + 1 + r + j * ld] /= djj; });
-        const int nt = M - j - 1;
-        wfor(nt * nt, [&](int r) {
-            int i = j + 1 + r % nt, c = j + 1 + r / nt;
-            if (i >= c) Gm[i + c * ld] -= Gm[i + j * ld] * Gm[c + j * ld];
+        const T ljj = s.sc[2];
+        wlanes([&](int i) {
+            if (i <= j || i >= M) return;
+            const T lij = Gm[i + j * ld] / ljj;
+            Gm[i + j * ld] = lij;
+            s.tmp[i] = lij;
+        });
+        wlanes([&](int i) {
+            if (i <= j || i >= M) return;
+            const T lij = s.tmp[i];
+            for (int c = j + 1; c <= i; ++c) Gm[i + c * ld] -= lij * s.tmp[c];
         });
     }
     return s.sc[1] != 0;
@@ -193,7 +214,7 @@ MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
 template <typename T, int NX, int MT>
 MHE_DEV bool chol_G(Ws<T, NX>& s, double piv_rel)
 {
-    return chol_inplace<T, NX, MT>(s, s.G, piv_rel);
+    return chol_inplace<T, NX, MT, true>(s, s.G, piv_rel);
 }
 
 // y := (L L^T)^{-1} y with L = lower(s.G), y in registers.
@@ -206,14 +227,14 @@ MHE_DEV void chol_solve_reg(const Ws<T, NX>& s, T (&y)[MT])
         T acc = y[j];
 #pragma unroll
         for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * y[p];
-        y[j] = acc / s.G[j + j * ld];
+        y[j] = pivot_div(acc, s.G[j + j * ld]);
     }
 #pragma unroll
     for (int j = MT - 1; j >= 0; --j) {
         T acc = y[j];
 #pragma unroll
         for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * y[p];
-        y[j] = acc / s.G[j + j * ld];
+        y[j] = pivot_div(acc, s.G[j + j * ld]);
     }
 }
 
@@ -268,7 +289,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
                 T acc = s.H[c + j * ld];
 #pragma unroll
                 for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * y[p];
-                y[j] = acc / s.G[j + j * ld];
+                y[j] = pivot_div(acc, s.G[j + j * ld]);
             }
 #pragma unroll
             for (int j = 0; j < MT; ++j) s.PB[j + c * ld] = y[j];
@@ -277,7 +298,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
                 T acc = y[j];
 #pragma unroll
                 for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * y[p];
-                y[j] = acc / s.G[j + j * ld];
+                y[j] = pivot_div(acc, s.G[j + j * ld]);
             }
 #pragma unroll
             for (int j = 0; j < MT; ++j) {
@@ -329,7 +350,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
                 T acc = z[j];
 #pragma unroll
                 for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * z[p];
-                z[j] = acc / s.G[j + j * ld];
+                z[j] = pivot_div(acc, s.G[j + j * ld]);
             }
 #pragma unroll
             for (int j = 0; j < MT; ++j) s.PB[j + c * ld] = z[j];
@@ -338,7 +359,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
                 T acc = z[j];
 #pragma unroll
                 for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * z[p];
-                z[j] = acc / s.G[j + j * ld];
+                z[j] = pivot_div(acc, s.G[j + j * ld]);
             }
             if (Lout) {
 #pragma unroll
