@@ -43,9 +43,38 @@ struct PassTiming {
     }
 };
 
+// Host-buffer pipeline of mhe_estimate_host: two engines on two streams take
+// the pieces of the batch in turn; each has its device copies of a piece's
+// inputs and outputs.
+struct HostPipe {
+    struct Buf {
+        void* p = nullptr;
+        size_t bytes = 0;
+    };
+    mhe::Engine eng[2];
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    bool inited[2] = {false, false};
+    bool used[2] = {false, false};
+    Buf in[2][9];    // A B C R a y~ w~ x~0 P~0^{-1}
+    Buf out[2][3];   // x w lambda
+    ~HostPipe()
+    {
+        for (int e = 0; e < 2; ++e) {
+            if (st[e]) cudaStreamSynchronize(st[e]);
+            if (inited[e]) eng[e].release();
+            for (auto& b : in[e]) if (b.p) cudaFree(b.p);
+            for (auto& b : out[e]) if (b.p) cudaFree(b.p);
+            if (done[e]) cudaEventDestroy(done[e]);
+            if (st[e]) cudaStreamDestroy(st[e]);
+        }
+    }
+};
+
 struct mhe_ctx {
     mhe::Engine eng;
     PassTiming timing;
+    HostPipe* pipe = nullptr;
 };
 
 namespace {
@@ -277,10 +306,128 @@ int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, do
     return rc;
 }
 
+namespace {
+int reserve_buf(HostPipe::Buf& b, size_t need)
+{
+    if (b.p && need <= b.bytes) return 0;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, need > 0 ? need : 8) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    b.bytes = need;
+    return 0;
+}
+}  // namespace
+
+int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info,
+                      int pieces)
+{
+    if (!ctx || !prob) return fail(MHE_E_ARG, "ctx or prob is NULL");
+    if (!x || !w || !lam) return fail(MHE_E_ARG, "output pointer is NULL");
+    mhe::Engine& E = ctx->eng;
+    const mhe::Plan& P = E.plan;
+    const int n = P.n, m = P.m, q = prob->ny, batch = P.batch;
+    if (q != E.ops->ny) return fail(MHE_E_ARG, "ny is not the compiled shape's");
+    if (P.S_in > 0 && (!prob->A || !prob->B || !prob->C || !prob->R || !prob->a || !prob->yt || !prob->wt))
+        return fail(MHE_E_ARG, "a stage array of the MHE problem is NULL");
+    if (!prob->x0 || !prob->P0inv) return fail(MHE_E_ARG, "x0 or P0inv is NULL");
+    if (pieces < 1) pieces = 1;
+    if (pieces > batch) pieces = batch;
+    if (!ctx->pipe) {
+        HostPipe* hp = new (std::nothrow) HostPipe;
+        if (!hp) return fail(MHE_E_NOMEM, "host allocation failed");
+        for (int e = 0; e < 2; ++e)
+            if (cudaStreamCreateWithFlags(&hp->st[e], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&hp->done[e], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                delete hp;
+                return fail(MHE_E_CUDA, "stream or event creation failed");
+            }
+        ctx->pipe = hp;
+    }
+    HostPipe& hp = *ctx->pipe;
+    // pieces of consecutive instances with about equal stage counts
+    std::vector<int> cut(1, 0);
+    const long long per = (P.S_in + P.batch) / pieces + 1;
+    long long acc = 0;
+    for (int b = 0; b < batch; ++b) {
+        acc += P.N[b];
+        if (acc >= per * (long long)cut.size() && b + 1 < batch && (int)cut.size() < pieces) cut.push_back(b + 1);
+    }
+    cut.push_back(batch);
+    const int R = (m + q) * (m + q);
+    int rc = MHE_OK;
+    for (size_t k = 0; k + 1 < cut.size() && rc == MHE_OK; ++k) {
+        const int e = (int)(k & 1);
+        const int b0 = cut[k], b1 = cut[k + 1], cnt = b1 - b0;
+        if (hp.used[e] && cudaEventSynchronize(hp.done[e]) != cudaSuccess) { rc = MHE_E_CUDA; break; }
+        const long long s0 = P.in_off[b0], x0s = P.gs0[b0] + b0, w0 = P.w_off[b0];
+        long long S = 0, X = 0, W = 0;
+        for (int b = b0; b < b1; ++b) {
+            S += P.N[b] - 1;
+            X += P.N[b] + 1;
+            W += n + (long long)(P.N[b] - 1) * m;
+        }
+        if (!hp.inited[e]) {
+            mhe_dims d;
+            memset(&d, 0, sizeof(d));
+            d.nx = n; d.nw = m; d.batch = cnt; d.N = P.N.data() + b0; d.prec = E.prec;
+            d.leaf_len = E.leaf; d.branching = E.br; d.top_len = E.topl;
+            d.refine_tol = E.tol; d.max_refine = E.max_refine;
+            rc = hp.eng[e].init(d, E.ops, &kRuntime, hp.st[e]);
+            if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
+            hp.inited[e] = true;
+        } else {
+            rc = hp.eng[e].replan(P.N.data() + b0, cnt, nullptr);
+            if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
+        }
+        const size_t sz_in[9] = {(size_t)S * n * n, (size_t)S * n * m, (size_t)S * q * n, (size_t)S * R,
+                                 (size_t)S * n, (size_t)S * q, (size_t)S * m, (size_t)cnt * n,
+                                 (size_t)cnt * n * n};
+        const double* src[9] = {prob->A + s0 * n * n, prob->B + s0 * n * m, prob->C + s0 * q * n, prob->R + s0 * R,
+                                prob->a + s0 * n, prob->yt + s0 * q, prob->wt + s0 * m, prob->x0 + (long long)b0 * n,
+                                prob->P0inv + (long long)b0 * n * n};
+        const size_t sz_out[3] = {(size_t)X * n, (size_t)W, (size_t)X * n};
+        for (int i = 0; i < 9 && rc == MHE_OK; ++i)
+            if (reserve_buf(hp.in[e][i], sizeof(double) * sz_in[i]) != 0) rc = MHE_E_NOMEM;
+        for (int i = 0; i < 3 && rc == MHE_OK; ++i)
+            if (reserve_buf(hp.out[e][i], sizeof(double) * sz_out[i]) != 0) rc = MHE_E_NOMEM;
+        if (rc != MHE_OK) { g_err = "device allocation of a pipeline buffer failed"; break; }
+        for (int i = 0; i < 9; ++i)
+            if (sz_in[i] > 0)
+                cudaMemcpyAsync(hp.in[e][i].p, src[i], sizeof(double) * sz_in[i], cudaMemcpyHostToDevice, hp.st[e]);
+        mhe_problem dp;
+        dp.ny = q;
+        dp.A = (const double*)hp.in[e][0].p; dp.B = (const double*)hp.in[e][1].p;
+        dp.C = (const double*)hp.in[e][2].p; dp.R = (const double*)hp.in[e][3].p;
+        dp.a = (const double*)hp.in[e][4].p; dp.yt = (const double*)hp.in[e][5].p;
+        dp.wt = (const double*)hp.in[e][6].p; dp.x0 = (const double*)hp.in[e][7].p;
+        dp.P0inv = (const double*)hp.in[e][8].p;
+        rc = hp.eng[e].estimate(dp, (double*)hp.out[e][0].p, (double*)hp.out[e][1].p, (double*)hp.out[e][2].p,
+                                info ? info + b0 : nullptr);
+        if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
+        cudaMemcpyAsync(x + x0s * n, hp.out[e][0].p, sizeof(double) * sz_out[0], cudaMemcpyDeviceToHost, hp.st[e]);
+        cudaMemcpyAsync(w + w0, hp.out[e][1].p, sizeof(double) * sz_out[1], cudaMemcpyDeviceToHost, hp.st[e]);
+        cudaMemcpyAsync(lam + x0s * n, hp.out[e][2].p, sizeof(double) * sz_out[2], cudaMemcpyDeviceToHost, hp.st[e]);
+        cudaEventRecord(hp.done[e], hp.st[e]);
+        hp.used[e] = true;
+    }
+    for (int e = 0; e < 2; ++e)
+        if (cudaStreamSynchronize(hp.st[e]) != cudaSuccess && rc == MHE_OK) rc = MHE_E_CUDA;
+    if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
+    if (rc == MHE_E_CUDA && g_err.empty()) g_err = "CUDA error in the host-buffer pipeline";
+    return rc;
+}
+
 int mhe_destroy(mhe_ctx* ctx)
 {
     if (!ctx) return MHE_OK;
     cudaStreamSynchronize((cudaStream_t)ctx->eng.stream);
+    delete ctx->pipe;
+    ctx->pipe = nullptr;
     ctx->eng.release();
     delete ctx;
     return MHE_OK;
@@ -356,7 +503,14 @@ int mhe_timing_read(mhe_ctx* ctx, double* out, int cap)
     return k;
 }
 
-long long mhe_launch_count(mhe_ctx* ctx) { return ctx ? ctx->eng.launches : -1; }
+long long mhe_launch_count(mhe_ctx* ctx)
+{
+    if (!ctx) return -1;
+    long long l = ctx->eng.launches;
+    if (ctx->pipe)
+        for (int e = 0; e < 2; ++e) l += ctx->pipe->inited[e] ? ctx->pipe->eng[e].launches : 0;
+    return l;
+}
 
 // ---- autotuner ----------------------------------------------------------------
 // Coordinate search over the plan: leaf_len first (branching 4, top_len 4),

@@ -74,6 +74,8 @@ def _declare(L):
     L.mhe_factor_solve.restype = c_int
     L.mhe_estimate.argtypes = [c_void_p, P(mhe_problem), c_void_p, c_void_p, c_void_p, c_void_p]
     L.mhe_estimate.restype = c_int
+    L.mhe_estimate_host.argtypes = [c_void_p, P(mhe_problem), c_void_p, c_void_p, c_void_p, c_void_p, c_int]
+    L.mhe_estimate_host.restype = c_int
     L.mhe_destroy.argtypes = [c_void_p]
     L.mhe_destroy.restype = c_int
     L.mhe_assemble.argtypes = [c_int, c_int, c_int, c_ll, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -204,6 +206,32 @@ def mhe_estimate(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info=None
                     _ptr(P0inv))
     ip = ctypes.c_void_p(info.data_ptr()) if info is not None else None
     return _check(lib().mhe_estimate(ctx, ctypes.byref(p), _ptr(x), _ptr(w), _ptr(lam), ip), "mhe_estimate")
+
+
+def _hptr(t):
+    """Host array (contiguous float64 numpy array or CPU torch tensor) -> pointer."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.float64 and t.flags["C_CONTIGUOUS"], "expected a contiguous float64 array"
+        return ctypes.c_void_p(t.ctypes.data)
+    assert (not t.is_cuda) and str(t.dtype) == "torch.float64" and t.is_contiguous(), \
+        "expected a contiguous float64 CPU tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mhe_estimate_host(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info=None, pieces=8):
+    """mhe_estimate_host: problem and outputs in host memory (pinned for overlap)."""
+    p = mhe_problem(int(ny), _hptr(A), _hptr(B), _hptr(C), _hptr(R), _hptr(a), _hptr(yt), _hptr(wt), _hptr(x0),
+                    _hptr(P0inv))
+    if info is None:
+        ip = None
+    elif isinstance(info, np.ndarray):
+        ip = ctypes.c_void_p(info.ctypes.data)
+    else:
+        ip = ctypes.c_void_p(info.data_ptr())
+    return _check(lib().mhe_estimate_host(ctx, ctypes.byref(p), _hptr(x), _hptr(w), _hptr(lam), ip, int(pieces)),
+                  "mhe_estimate_host")
 
 
 def mhe_destroy(ctx):

@@ -106,3 +106,41 @@ def test_estimate_argument_errors():
         s.estimate(3, d["A"], d["B"], None, d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"])
     assert e.value.code == -1
     s.close()
+
+
+@pytest.mark.parametrize("prec,pieces", [(mhe.MHE_FP32_IR, 3), (mhe.MHE_FP32_IR, 1), (mhe.MHE_FP64, 4),
+                                         (mhe.MHE_FP32_IR, 100)])
+def test_estimate_host_equals_device(prec, pieces):
+    """mhe_estimate_host (host buffers, pieces pipelined over two streams) gives
+    the device-buffer result bit for bit: every instance's computation depends
+    on its own data and plan only."""
+    import torch
+    n, m = 6, 3
+    Ns = [1, 2, 40, 77, 3, 130, 64, 9, 200, 31]
+    insts = [synth.mhe_instance(500 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    kw = dict(prec=prec, refine_tol=1e-12, leaf_len=4, branching=3, top_len=2)
+    s1 = mhe.Solver(n, m, d["N"], **kw)
+    x1, w1, l1 = _estimate(d, s1)
+    torch.cuda.synchronize()
+    info1 = s1.infos()
+    s2 = mhe.Solver(n, m, d["N"], **kw)
+    h = {k: d[k].cpu().pin_memory() for k in ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv")}
+    x2 = torch.zeros(x1.shape, dtype=torch.float64).pin_memory()
+    w2 = torch.zeros(w1.shape, dtype=torch.float64).pin_memory()
+    l2 = torch.zeros(l1.shape, dtype=torch.float64).pin_memory()
+    info2 = np.zeros(len(Ns), dtype=mhe.INFO_DTYPE)
+    mhe.mhe_estimate_host(s2.ctx, m, h["A"], h["B"], h["C"], h["R"], h["a"], h["yt"], h["wt"], h["x0"], h["P0inv"],
+                          x2, w2, l2, info2, pieces=pieces)
+    assert torch.equal(x1.cpu(), x2) and torch.equal(w1.cpu(), w2) and torch.equal(l1.cpu(), l2)
+    assert np.array_equal(info1["status"], info2["status"]) and np.array_equal(info1["relres"], info2["relres"])
+    ref = _oracle(insts)
+    sols = split(x2, w2, l2, d["N"], n, m)
+    for b in range(len(Ns)):
+        assert rel_err(sols[b], ref[b]) <= (1e-10 if prec == mhe.MHE_FP64 else 1e-8)
+    # a second call reuses the pipeline's engines and buffers
+    mhe.mhe_estimate_host(s2.ctx, m, h["A"], h["B"], h["C"], h["R"], h["a"], h["yt"], h["wt"], h["x0"], h["P0inv"],
+                          x2, w2, l2, info2, pieces=pieces)
+    assert torch.equal(x1.cpu(), x2)
+    s1.close()
+    s2.close()
