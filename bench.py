@@ -42,7 +42,7 @@ def flops_leaf_stage(n, m):
     return 6 * n ** 3 + 12 * n ** 2 * m + 6 * n * m ** 2 + m ** 3 / 3.0
 
 
-def pass_model(ph, lvl, n, m, q, prec, N):
+def pass_model(ph, lvl, n, m, q, prec, N, serial=False):
     """Algorithmic work of one full pass of a level-0 kernel over a bucket:
     (bound, work, unit) with work in TFLOP or GB.  The counts:
       reduce  Algorithm 4 per stage (flops_leaf_stage; the arrival stage has width n)
@@ -59,7 +59,8 @@ def pass_model(ph, lvl, n, m, q, prec, N):
     if lvl != 0:
         return None
     if ph == "reduce":
-        fl = stages * flops_leaf_stage(n, m) - inst * (flops_leaf_stage(n, m) - flops_leaf_stage(n, n))
+        f = flops_serial_stage if serial else flops_leaf_stage   # a serial plan runs Algorithms 1-2 only
+        fl = stages * f(n, m) - inst * (f(n, m) - f(n, n))
         return ("alu", fl / 1e12, "TFLOP/s")
     if ph == "resid":
         qz = (2 * n * q + q * q + q * m + m * m + m * q) if prec == 1 else (n + m) ** 2
@@ -108,6 +109,18 @@ def make_workload(name):
                     seed=5, l2="inputs larger than L2 (a few GB)")
         b = w["buckets"][24]
         return desc, [dict(n=24, m=12, q=12, N=b["N"], pool=b["pool"], idx=b["idx"], x0=b["x0"])], 1
+    if name == "xl":
+        # 256 instances of nx = 64, nw = ny = 32, N = 1024 (262,144 stages); stages drawn from a seeded pool of
+        # 2048 independent stages (the eigenvalue scaling of 64 x 64 draws dominates generation time)
+        rng = np.random.default_rng(5)
+        count, N, n, m = 256, 1024, 64, 32
+        pool = synth.stage_pool(np.random.default_rng([5, n]), n, m, m, 2048)
+        idx = rng.integers(0, 2048, size=count * (N - 1))
+        x0 = rng.standard_normal((count, n))
+        desc = dict(workload="256 MHE instances of nx=64, nw=ny=32, N=1024", instances=count, nx=n, nw_ny=m,
+                    N=N, precision="FP32 tree (128-thread teams) + FP64 refinement", seed=5,
+                    l2="inputs larger than L2 (26 GB resident)")
+        return desc, [dict(n=n, m=m, q=m, N=np.full(count, N, dtype=np.int64), pool=pool, idx=idx, x0=x0)], 1
     if name == "long":
         p = synth.mhe_instance(1, 20, 10, 10, 131072)
         pool = {k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")}
@@ -136,8 +149,6 @@ def to_device(bk):
     S = int(len(bk["idx"]))
     out["x0"] = torch.from_numpy(np.ascontiguousarray(bk["x0"]).reshape(-1)).to(dev)
     out["P0inv"] = torch.eye(n, dtype=torch.float64, device=dev).reshape(1, -1).repeat(len(bk["N"]), 1).contiguous()
-    out["Q"] = torch.empty(S, (n + m) ** 2, dtype=torch.float64, device=dev)
-    out["l"] = torch.empty(S, n + m, dtype=torch.float64, device=dev)
     out["S"] = S
     return out
 
@@ -235,6 +246,7 @@ def run_gpu(args):
         bk["dev"] = to_device(bk)
     gen_s = time.time() - t0
     refine_tol = 1e-9
+    max_refine = 16 if prec == 1 else 2
     solvers, plans = [], []
     t_tune = time.time()
     for bk in buckets:
@@ -242,19 +254,25 @@ def run_gpu(args):
         if args.autotune:
             # the library's autotuner on the first instances of the bucket (a contiguous prefix)
             d = bk["dev"]
-            k = min(len(bk["N"]), args.tune_instances)
+            # a prefix of the bucket; nx = 64 tunes on the whole batch (its instances fill the SMs, which
+            # changes the best plan, and 256 instances are a small batch)
+            k = min(len(bk["N"]), args.tune_instances if bk["n"] < 48 else len(bk["N"]))
             S = int(np.sum(bk["N"][:k] - 1))
             n, m = bk["n"], bk["m"]
-            dims, _keep = mhe.make_dims(n, m, bk["N"][:k], prec, 0, 0, 0, refine_tol, 8 if prec == 1 else 2)
-            if d["S"] > 0:
-                mhe.mhe_assemble(n, m, bk["q"], d["C"], d["R"], d["yt"], d["wt"], d["Q"], d["l"])
-            r = mhe.mhe_autotune(dims, d["A"][:S].contiguous(), d["B"][:S].contiguous(), d["Q"][:S].contiguous(),
-                                 d["P0inv"][:k].contiguous(), d["l"][:S].contiguous(), d["a"][:S].contiguous(),
+            dims, _keep = mhe.make_dims(n, m, bk["N"][:k], prec, 0, 0, 0, refine_tol, max_refine)
+            Qp = torch.empty(max(S, 1), (n + m) ** 2, dtype=torch.float64, device="cuda")
+            lp = torch.empty(max(S, 1), n + m, dtype=torch.float64, device="cuda")
+            if S > 0:
+                mhe.mhe_assemble(n, m, bk["q"], d["C"][:S].contiguous(), d["R"][:S].contiguous(),
+                                 d["yt"][:S].contiguous(), d["wt"][:S].contiguous(), Qp, lp)
+            r = mhe.mhe_autotune(dims, d["A"][:S].contiguous(), d["B"][:S].contiguous(), Qp,
+                                 d["P0inv"][:k].contiguous(), lp, d["a"][:S].contiguous(),
                                  d["x0"][:k * n].contiguous())
+            del Qp, lp
             plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"])
         plans.append(dict(nx=bk["n"], **plan))
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=prec, refine_tol=refine_tol,
-                       max_refine=8 if prec == 1 else 2, **plan)
+                       max_refine=max_refine, **plan)
         s.out = s.outputs()
         solvers.append(s)
     tune_s = time.time() - t_tune
@@ -313,7 +331,8 @@ def run_gpu(args):
     def roof(r):
         bk = [b for b in buckets if b["n"] == r["nx"]][0]
         n, m, q = bk["n"], bk["m"], bk["q"]
-        mod = pass_model(r["phase"], r["level"], n, m, q, prec, bk["N"])
+        pl = [p for p in plans if p["nx"] == n][0]
+        mod = pass_model(r["phase"], r["level"], n, m, q, prec, bk["N"], serial=pl["top_len"] > int(np.max(bk["N"])))
         if mod is None:
             return None
         bound, work, unit = mod
@@ -340,7 +359,7 @@ def run_gpu(args):
 
     # plain serial Riccati on the same GPU: one chunk per instance (top_len >= N)
     base = {}
-    arms = [] if args.no_baseline else [("serial_same_precision", prec, 8 if prec == 1 else 0)] + \
+    arms = [] if args.no_baseline else [("serial_same_precision", prec, max_refine if prec == 1 else 0)] + \
         ([("serial_fp64", 0, 0)] if (prec == 1 and args.serial_fp64) else [])
     for name, bprec, mref in arms:
         ss = []
@@ -623,7 +642,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile", "serve"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile", "serve", "xl"])
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
     ap.add_argument("--estimators", type=int, default=1024, help="serving: estimator pool")

@@ -193,8 +193,11 @@ int mhe_shapes(int* nx_out, int* nw_out, int cap);
  * top_len; the serial plan top_len > max N included) of mhe_factor_solve on
  * the given problem -- leaf_len first, then branching, then top_len, each
  * the best of `reps` runs after a warm-up, CUDA events on `stream` -- and
- * writes dims with the fastest plan into *best (time in *best_ms).  Allocates
- * one context per candidate in turn.  Errors: MHE_E_ARG, MHE_E_NOMEM. */
+ * writes dims with the fastest plan into *best (time in *best_ms).  A plan
+ * whose warm-up leaves any instance with a non-zero status (a failed pivot,
+ * no convergence) is not a candidate.  Allocates one context per candidate in
+ * turn.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_NO_CONVERGE (no plan solved
+ * every instance). */
 int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* rhs, void* stream, int reps,
                  mhe_dims* best, double* best_ms);
 

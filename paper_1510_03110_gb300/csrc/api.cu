@@ -17,6 +17,7 @@ int shapes_small(ShapeEntry* out, int cap);
 int shapes_mid(ShapeEntry* out, int cap);
 int shapes_big(ShapeEntry* out, int cap);
 int shapes_sq(ShapeEntry* out, int cap);
+int shapes_xl(ShapeEntry* out, int cap);
 }  // namespace mhe
 
 // CUDA events around each level pass, recorded on the context's stream.
@@ -99,6 +100,7 @@ std::vector<mhe::ShapeEntry>& registry()
         k += mhe::shapes_mid(buf + k, 32 - k);
         k += mhe::shapes_big(buf + k, 32 - k);
         k += mhe::shapes_sq(buf + k, 32 - k);
+        k += mhe::shapes_xl(buf + k, 32 - k);
         reg.assign(buf, buf + k);
     });
     return reg;
@@ -137,7 +139,7 @@ int rt_error() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
 // relres = ||r|| / (||K|| ||z|| + ||b||) per instance
 __global__ void k_finalize(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
                            int* iters, const int* status, const int* where, double tol, int mode, int refine,
-                           mhe_info* info)
+                           mhe_info* info, int* any)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
@@ -154,7 +156,10 @@ __global__ void k_finalize(int batch, const unsigned long long* norms, const uns
         info[b].relres = relres;
         const int act = status[b] == 0 && isfinite(relres) && !(relres <= tol);
         active[b] = act;
-        if (act) iters[b] += 1;
+        if (act) {
+            iters[b] += 1;
+            if (any) *any = 1;
+        }
         return;
     }
     // partial final pass: only instances corrected since their last check were
@@ -176,10 +181,11 @@ __global__ void k_finalize(int batch, const unsigned long long* norms, const uns
 }
 
 void rt_finalize(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active, int* iters,
-                 const int* status, const int* where, double tol, int mode, int refine, mhe_info* info, void* s)
+                 const int* status, const int* where, double tol, int mode, int refine, mhe_info* info, int* any,
+                 void* s)
 {
     k_finalize<<<(batch + 127) / 128, 128, 0, (cudaStream_t)s>>>(batch, norms, kinf, active, iters, status, where,
-                                                                 tol, mode, refine, info);
+                                                                 tol, mode, refine, info, any);
 }
 
 // FP64 -> FP32 copy (round to nearest)
@@ -517,7 +523,8 @@ long long mhe_launch_count(mhe_ctx* ctx)
 // then branching, then top_len (including the serial plan, top_len >= max N),
 // each candidate timed as the best of `reps` fused factor+solve calls after one
 // warm-up, with CUDA events on the caller's stream.  Candidates whose context
-// cannot be created (memory) are skipped.
+// cannot be created (memory), or whose warm-up leaves any instance with a
+// non-zero status (a failed pivot, no convergence), are skipped.
 int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* rhs, void* stream, int reps,
                  mhe_dims* best, double* best_ms)
 {
@@ -539,6 +546,13 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
         cudaGetLastError();
         return fail(MHE_E_NOMEM, "autotune output buffers");
     }
+    mhe_info* inf_d = nullptr;
+    if (cudaMalloc(&inf_d, sizeof(mhe_info) * dims->batch) != cudaSuccess) {
+        cudaFree(x); cudaFree(w); cudaFree(lam);
+        cudaGetLastError();
+        return fail(MHE_E_NOMEM, "autotune output buffers");
+    }
+    std::vector<mhe_info> inf_h(dims->batch);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -550,7 +564,12 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
         mhe_ctx* c = nullptr;
         if (mhe_create(&d, stream, &c) != MHE_OK) return -1.0;
         double bestt = -1.0;
-        if (mhe_factor_solve(c, mats, rhs, x, w, lam, nullptr) == MHE_OK) {
+        bool ok = mhe_factor_solve(c, mats, rhs, x, w, lam, inf_d) == MHE_OK &&
+                  cudaMemcpyAsync(inf_h.data(), inf_d, sizeof(mhe_info) * dims->batch, cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream) == cudaSuccess &&
+                  cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess;
+        for (int b = 0; ok && b < dims->batch; ++b) ok = inf_h[b].status == MHE_OK;
+        if (ok) {
             for (int r = 0; r < reps; ++r) {
                 cudaEventRecord(e0, (cudaStream_t)stream);
                 mhe_factor_solve(c, mats, rhs, x, w, lam, nullptr);
@@ -582,13 +601,13 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(x); cudaFree(w); cudaFree(lam);
+    cudaFree(x); cudaFree(w); cudaFree(lam); cudaFree(inf_d);
     *best = *dims;
     best->leaf_len = bl;
     best->branching = bb;
     best->top_len = bt;
     if (best_ms) *best_ms = bms;
-    if (bms < 0) return fail(MHE_E_NOMEM, "no candidate plan could run");
+    if (bms < 0) return fail(MHE_E_NO_CONVERGE, "no candidate plan ran with every instance solved");
     return MHE_OK;
 }
 

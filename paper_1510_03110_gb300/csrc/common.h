@@ -68,6 +68,7 @@ struct LevelArgs {
     double *zx, *zw, *zl;                  // level 0: FP64 accumulate targets (nullptr: none)
 
     const int* active;     // per instance; nullptr = all active
+    const int* any_active; // non-null: the pass is skipped when *any_active == 0 (no instance refining)
     int* status;           // per instance error code
     int* where;            // per instance (level, chunk, stage) of the first error
     double piv_rel;        // relative pivot threshold of the Cholesky factorisations
@@ -91,6 +92,7 @@ struct ResidArgs {
     const long long* out_off;     // rl, ra of stage t >= 1 at out_off[b] + t - 1 (compact layout)
     unsigned long long* norms;    // per instance [r_inf, z_inf, b_inf] as bit patterns of |.|
     const int* active;
+    const int* any_active;        // non-null: nothing to do when *any_active == 0
     // MHE form (Eq. org_mhe): when C is set, Q of stage t >= 1 is applied in its
     // factors [[C^T V C, -C^T S^T], [-S C, W]] from C (ny x n) and
     // R = [[W, S], [S^T, V]] at the input offsets, and Q is not read

@@ -90,6 +90,7 @@ size_t Engine::layout(char* base)
     c.take(norms, (size_t)batch * 3);
     c.take(kinf, (size_t)batch);
     c.take(active, (size_t)batch);
+    c.take(any_act, (size_t)1);
     c.take(status, (size_t)batch);
     c.take(where, (size_t)batch * 3);
     c.take(iters, (size_t)batch);
@@ -104,6 +105,10 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     stream = s;
     prec = d.prec;
     if (prec != MHE_FP64 && prec != MHE_FP32_IR) { err = "unknown precision"; return MHE_E_ARG; }
+    if (prec == MHE_FP64 && !ops->reduce64) {
+        err = "this shape's FP64 workspace exceeds the shared memory of an SM: use MHE_FP32_IR";
+        return MHE_E_ARG;
+    }
     tol = d.refine_tol > 0 ? d.refine_tol : 1e-12;
     max_refine = d.max_refine >= 0 ? d.max_refine : (prec == MHE_FP64 ? 2 : 8);
     int maxN = 1;
@@ -302,6 +307,7 @@ void Engine::pass_rhs(const T* l, const T* a, const T* l0, const T* a0, const T*
         g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
         g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
         g.active = active_mask;
+        g.any_active = any_mask;
         mark(PH_RHS, k, 1);
         launches += g.nchunks > 0;
         launch<T>(ops->rhs64, ops->rhs32, g, k >= 1, stream);
@@ -324,6 +330,7 @@ void Engine::pass_down(const T* l, const T* a, const T* l0, const T* a0, const T
         g.x0 = x0;
         g.lN = lN;
         g.active = act;
+        g.any_active = act ? any_mask : nullptr;
         if (k == 0) {
             g.xd = x; g.wd = w; g.ld = lam;
             g.zx = zx; g.zw = zw; g.zl = zl;
@@ -353,6 +360,7 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
     r.ra0 = static_cast<T*>(ra0); r.rlN = static_cast<T*>(rlN); r.rx0 = static_cast<T*>(rx0);
     r.norms = norms;
     r.active = act;
+    r.any_active = act ? any_mask : nullptr;
     r.C = mheC;
     r.R = mheR;
     rt->memset0(norms, sizeof(unsigned long long) * 3 * plan.batch, stream);
@@ -405,10 +413,13 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
     const T* crlN = static_cast<const T*>(rlN);
     const T* crx0 = static_cast<const T*>(rx0);
     for (int it = 0; it < max_refine; ++it) {
+        any_mask = it == 0 ? nullptr : any_act;
         residual<T>(rhs, x, w, lam, it == 0 ? nullptr : active);
+        rt->memset0(any_act, sizeof(int), stream);
         rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
-                     stream);
+                     any_act, stream);
         ++launches;
+        any_mask = any_act;
         // correction problem K dz = r in UFTOC form (compact layout), then z += dz
         active_mask = active;
         rhs_compact = true;
@@ -420,9 +431,11 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
     }
     // final check: after a refinement loop only the instances corrected since
     // their last residual (still active) need one
+    any_mask = max_refine > 0 ? any_act : nullptr;
     residual<T>(rhs, x, w, lam, max_refine > 0 ? active : nullptr);
+    any_mask = nullptr;
     rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, 2, max_refine > 0 ? 3 : 0, info_dev,
-                 stream);
+                 nullptr, stream);
     ++launches;
     if (info) rt->copy(info, info_dev, sizeof(mhe_info) * plan.batch, stream);
     if (rt->error() != 0) { err = "CUDA error during the solve"; return MHE_E_CUDA; }

@@ -45,9 +45,10 @@ struct Runtime {
     // mode 2 fills mhe_info.  refine: bit 0 = refinement ran (a residual above
     // tol is NO_CONVERGE), bit 1 = the final residual covered only the instances
     // still active (the others keep the relres recorded by modes 0/1)
+    // modes 0/1 set *any = 1 when some instance takes another correction (any may be NULL)
     void (*finalize)(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
                      int* iters, const int* status, const int* where, double tol, int mode, int refine,
-                     mhe_info* info, void* stream);
+                     mhe_info* info, int* any, void* stream);
     // FP64 -> FP32 copy of count elements (FP32 mode keeps FP32 copies of the problem)
     void (*convert)(float* dst, const double* src, long long count, void* stream);
     int (*sync)(void* stream);
@@ -98,6 +99,8 @@ public:
     unsigned long long* norms = nullptr;   // per instance |r|, |z|, |b| maxima (bit patterns)
     unsigned int* kinf = nullptr;          // per instance ||K||_inf (float bit pattern)
     int *active = nullptr, *status = nullptr, *where = nullptr, *iters = nullptr;
+    int* any_act = nullptr;             // some instance still refining (set by finalize)
+    const int* any_mask = nullptr;      // passed to the refinement passes (nullptr outside refinement)
     mhe_info* info_dev = nullptr;
     void* arena = nullptr;
     size_t arena_bytes = 0;

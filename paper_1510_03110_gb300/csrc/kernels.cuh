@@ -20,15 +20,25 @@ constexpr int op_count()
     return OP == OP_REDUCE ? Ws<T, NX>::count : (OP == OP_RHS ? Ws<T, NX>::count_rhs : Ws<T, NX>::count_vec);
 }
 
-// warps per CTA: as many per-warp workspaces as fit in 200 KB, at most 8
+// teams per CTA of at most 256 threads: at most 256 / MHE_TEAM
+constexpr int kMaxTeams = 256 / MHE_TEAM;
+
+// teams per CTA: as many per-team workspaces as fit in 200 KB, at most kMaxTeams
 template <typename T, int NX, int OP>
 constexpr int level_warps()
 {
-    return (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) >= 8
-               ? 8
+    return (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) >= kMaxTeams
+               ? kMaxTeams
                : ((200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) < 1
                       ? 1
                       : (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)));
+}
+
+// a workspace the shared memory of one SM can hold (227 KB per CTA)
+template <typename T, int NX, int OP>
+constexpr bool level_fits()
+{
+    return (long long)op_count<T, NX, OP>() * (long long)sizeof(T) <= 227LL * 1024;
 }
 
 // CTAs of 256 threads per SM the register allocation is sized for: the small
@@ -47,10 +57,11 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = level_warps<T, NX, OP>();
-    const int warp = threadIdx.x >> 5;
-    const int ci = blockIdx.x * W + warp;
-    if (ci >= a.nchunks) return;
-    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * op_count<T, NX, OP>();
+    const int team = team_id();
+    const int ci = blockIdx.x * W + team;
+    if (ci >= a.nchunks) return;   // the whole team leaves together
+    if (a.any_active && *a.any_active == 0) return;   // a refinement pass with every instance converged
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)team * op_count<T, NX, OP>();
     if (OP == OP_REDUCE) reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     else if (OP == OP_RHS) rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     else down_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
@@ -68,7 +79,7 @@ void launch_level_v(const LevelArgs<T>& a, void* stream)
         attr = true;
     }
     const int grid = (a.nchunks + W - 1) / W;
-    k_level<T, NX, NW, UPPER, OP><<<grid, 32 * W, smem, (cudaStream_t)stream>>>(a);
+    k_level<T, NX, NW, UPPER, OP><<<grid, MHE_TEAM * W, smem, (cudaStream_t)stream>>>(a);
 }
 
 template <typename T, int NX, int NW, int OP>
@@ -82,11 +93,12 @@ void launch_level(const LevelArgs<T>& a, int upper, void* stream)
 template <int NX, int NW, typename TR, int NY>
 __global__ void __launch_bounds__(256) k_resid(ResidArgs<TR> r)
 {
-    __shared__ unsigned long long sm[8][ResidSmem<NX, NW, NY>::count];
-    const int warp = threadIdx.x >> 5;
-    const long long g = (long long)blockIdx.x * 8 + warp;
+    __shared__ unsigned long long sm[kMaxTeams][ResidSmem<NX, NW, NY>::count];
+    const int team = team_id();
+    const long long g = (long long)blockIdx.x * kMaxTeams + team;
     if (g >= r.nstages) return;
-    resid_stage<NX, NW, TR, NY>(r, g, sm[warp]);
+    if (r.any_active && *r.any_active == 0) return;
+    resid_stage<NX, NW, TR, NY>(r, g, sm[team]);
 }
 
 // NY = 0: Q form; NY > 0: MHE form (C, R)
@@ -94,16 +106,17 @@ template <int NX, int NW, typename TR, int NY = 0>
 void launch_resid(const ResidArgs<TR>& r, void* stream)
 {
     if (r.nstages <= 0) return;
-    const long long grid = (r.nstages + 7) / 8;
+    const long long grid = (r.nstages + kMaxTeams - 1) / kMaxTeams;
     k_resid<NX, NW, TR, NY><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
 }
 
-// warps per block of the one-pass MHE preparation: static shared memory <= 40 KB
+// teams per block of the one-pass MHE preparation: <= 40 KB of shared memory
+// per CTA (several CTAs per SM), at least one team
 template <int NX, int NW, int NY>
 constexpr int prep_warps()
 {
-    return (40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8) >= 8
-               ? 8
+    return (40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8) >= kMaxTeams
+               ? kMaxTeams
                : ((40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8) < 1
                       ? 1
                       : (40 * 1024) / (int)(PrepSmem<NX, NW, NY>::count * 8));
@@ -112,12 +125,12 @@ constexpr int prep_warps()
 template <int NX, int NW, int NY>
 __global__ void __launch_bounds__(256) k_prep(PrepArgs p)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = prep_warps<NX, NW, NY>();
-    __shared__ double sm[W][PrepSmem<NX, NW, NY>::count];
-    const int warp = threadIdx.x >> 5;
-    const long long g = (long long)blockIdx.x * W + warp;
+    const int team = team_id();
+    const long long g = (long long)blockIdx.x * W + team;
     if (g >= p.nstages) return;
-    prep_stage<NX, NW, NY>(p, g, sm[warp]);
+    prep_stage<NX, NW, NY>(p, g, reinterpret_cast<double*>(smem_raw) + (size_t)team * PrepSmem<NX, NW, NY>::count);
 }
 
 template <int NX, int NW, int NY>
@@ -125,33 +138,39 @@ void launch_prep(const PrepArgs& p, void* stream)
 {
     if (p.nstages <= 0) return;
     constexpr int W = prep_warps<NX, NW, NY>();
+    const size_t smem = (size_t)W * PrepSmem<NX, NW, NY>::count * 8;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_prep<NX, NW, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
     const long long grid = (p.nstages + W - 1) / W;
-    k_prep<NX, NW, NY><<<(unsigned)grid, 32 * W, 0, (cudaStream_t)stream>>>(p);
+    k_prep<NX, NW, NY><<<(unsigned)grid, MHE_TEAM * W, smem, (cudaStream_t)stream>>>(p);
 }
 
 template <int NX, int NW>
 __global__ void __launch_bounds__(256) k_knorm(KnormArgs r)
 {
-    __shared__ float sm[8][2 * NX + NW + 4];
-    const int warp = threadIdx.x >> 5;
-    const long long g = (long long)blockIdx.x * 8 + warp;
+    __shared__ float sm[kMaxTeams][2 * NX + NW + 4];
+    const int team = team_id();
+    const long long g = (long long)blockIdx.x * kMaxTeams + team;
     if (g >= r.nstages) return;
-    knorm_stage<NX, NW>(r, g, sm[warp]);
+    knorm_stage<NX, NW>(r, g, sm[team]);
 }
 
 template <int NX, int NW>
 void launch_knorm(const KnormArgs& r, void* stream)
 {
     if (r.nstages <= 0) return;
-    const long long grid = (r.nstages + 7) / 8;
+    const long long grid = (r.nstages + kMaxTeams - 1) / kMaxTeams;
     k_knorm<NX, NW><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
 }
 
 template <int NX, int NW, int NY>
 constexpr int asm_warps()
 {
-    return (40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8) >= 8
-               ? 8
+    return (40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8) >= kMaxTeams
+               ? kMaxTeams
                : ((40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8) < 1
                       ? 1
                       : (40 * 1024) / (int)(AsmSmem<NX, NW, NY>::count * 8));
@@ -162,14 +181,15 @@ __global__ void __launch_bounds__(256) k_assemble(long long S, const double* C, 
                                                    const double* yt, const double* wt, double* Q, double* l,
                                                    double* c)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = asm_warps<NX, NW, NY>();
-    __shared__ double sm[W][AsmSmem<NX, NW, NY>::count];
-    const int warp = threadIdx.x >> 5;
-    const long long s = (long long)blockIdx.x * W + warp;
+    const int team = team_id();
+    const long long s = (long long)blockIdx.x * W + team;
     if (s >= S) return;
     constexpr int NR = NW + NY, NQ = NX + NW;
     assemble_stage<NX, NW, NY>(C + s * NY * NX, R + s * NR * NR, yt + s * NY, wt + s * NW, Q + s * NQ * NQ,
-                               l + s * NQ, c ? c + s : nullptr, sm[warp]);
+                               l + s * NQ, c ? c + s : nullptr,
+                               reinterpret_cast<double*>(smem_raw) + (size_t)team * AsmSmem<NX, NW, NY>::count);
 }
 
 template <int NX, int NW, int NY>
@@ -178,8 +198,14 @@ void launch_assemble(long long S, const double* C, const double* R, const double
 {
     if (S <= 0) return;
     constexpr int W = asm_warps<NX, NW, NY>();
+    const size_t smem = (size_t)W * AsmSmem<NX, NW, NY>::count * 8;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_assemble<NX, NW, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
     const long long grid = (S + W - 1) / W;
-    k_assemble<NX, NW, NY><<<(unsigned)grid, 32 * W, 0, (cudaStream_t)stream>>>(S, C, R, yt, wt, Q, l, c);
+    k_assemble<NX, NW, NY><<<(unsigned)grid, MHE_TEAM * W, smem, (cudaStream_t)stream>>>(S, C, R, yt, wt, Q, l, c);
 }
 
 // Everything one compiled shape provides.
@@ -196,9 +222,15 @@ ShapeEntry make_shape()
     ShapeEntry e;
     e.ops.nx = NX;
     e.ops.nw = NW;
-    e.ops.reduce64 = &launch_level<double, NX, NW, OP_REDUCE>;
-    e.ops.rhs64 = &launch_level<double, NX, NW, OP_RHS>;
-    e.ops.down64 = &launch_level<double, NX, NW, OP_DOWN>;
+    if constexpr (level_fits<double, NX, OP_REDUCE>()) {
+        e.ops.reduce64 = &launch_level<double, NX, NW, OP_REDUCE>;
+        e.ops.rhs64 = &launch_level<double, NX, NW, OP_RHS>;
+        e.ops.down64 = &launch_level<double, NX, NW, OP_DOWN>;
+    } else {   // the FP64 workspace of one subproblem exceeds an SM's shared memory: FP32_IR only
+        e.ops.reduce64 = nullptr;
+        e.ops.rhs64 = nullptr;
+        e.ops.down64 = nullptr;
+    }
     e.ops.reduce32 = &launch_level<float, NX, NW, OP_REDUCE>;
     e.ops.rhs32 = &launch_level<float, NX, NW, OP_RHS>;
     e.ops.down32 = &launch_level<float, NX, NW, OP_DOWN>;

@@ -491,7 +491,7 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
     // every input block of the stage in one batched load: [C | R | A | B | y~ | w~ | a]
     constexpr int O1 = NY * NX, O2 = O1 + NR * NR, O3 = O2 + NX * NX, O4 = O3 + NX * NW, O5 = O4 + NY + NW;
     constexpr int TOT = O5 + NX;
-    constexpr int PER = (TOT + 31) / 32;
+    constexpr int PER = (TOT + MHE_TEAM - 1) / MHE_TEAM;
     wcopy<TOT, (PER + 1) / 2>(
         [&](int i) {
             if (i < O1) return C[i];

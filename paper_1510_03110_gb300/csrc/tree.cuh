@@ -179,7 +179,7 @@ MHE_DEV T pivot_div(T acc, T gjj)
 template <typename T, int NX, int M, bool INV = false>
 MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
 {
-    static_assert(M <= 32 && M <= NX, "one lane per row");
+    static_assert(M <= MHE_TEAM && M <= NX, "one lane per row");
     constexpr int ld = Ws<T, NX>::ld;
     wone([&](int) {
         T mx = 0;

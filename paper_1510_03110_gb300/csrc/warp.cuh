@@ -1,10 +1,15 @@
-// warp.cuh -- the warp-cooperative execution layer every tree kernel is written on.
+// warp.cuh -- the team-cooperative execution layer every tree kernel is written on.
 //
-// A kernel body is a sequence of `wfor(count, f)` steps: the 32 lanes of one warp
-// share the indices 0..count-1 round-robin, and the step ends with __syncwarp(),
-// so shared-memory results of one step are visible to every lane in the next.
+// A team is MHE_TEAM consecutive threads of a CTA (one warp by default; a
+// translation unit may set MHE_TEAM to 64, 128 or 256 before including this
+// header, for shapes whose per-subproblem work and workspace want more threads).
+// A kernel body is a sequence of `wfor(count, f)` steps: the team's lanes share
+// the indices 0..count-1 round-robin, and the step ends with the team's
+// barrier (__syncwarp for one warp, a named barrier per team otherwise), so
+// shared-memory results of one step are visible to every lane in the next.
 // Scalars and small vectors that one lane computes are written to shared memory
-// and read after the step's barrier.
+// and read after the step's barrier.  Every lane of a team calls the same
+// sequence of steps: no step is called from inside another step's body.
 #ifndef MHE_WARP_CUH
 #define MHE_WARP_CUH
 #include <cuda_runtime.h>
@@ -12,15 +17,32 @@
 
 #define MHE_DEV __device__ __forceinline__
 
+#ifndef MHE_TEAM
+#define MHE_TEAM 32
+#endif
+static_assert(MHE_TEAM == 32 || MHE_TEAM == 64 || MHE_TEAM == 128 || MHE_TEAM == 256, "team of 1, 2, 4 or 8 warps");
+
 namespace mhe {
 
-MHE_DEV int lane_id() { return threadIdx.x & 31; }
+MHE_DEV int lane_id() { return threadIdx.x & (MHE_TEAM - 1); }
+// index of the team within its CTA
+MHE_DEV int team_id() { return threadIdx.x / MHE_TEAM; }
+
+// Barrier of the team's lanes (named barrier team_id + 1 when a team is several warps).
+MHE_DEV void wsync()
+{
+#if MHE_TEAM == 32
+    __syncwarp();
+#else
+    asm volatile("bar.sync %0, %1;" ::"r"(team_id() + 1), "r"(MHE_TEAM) : "memory");
+#endif
+}
 
 template <class F>
 MHE_DEV void wfor(int count, F&& f)
 {
-    for (int i = lane_id(); i < count; i += 32) f(i);
-    __syncwarp();
+    for (int i = lane_id(); i < count; i += MHE_TEAM) f(i);
+    wsync();
 }
 
 // store(i, load(i)) for i < COUNT, lanes round-robin.  Each lane issues up to
@@ -29,7 +51,7 @@ MHE_DEV void wfor(int count, F&& f)
 template <int COUNT, int MAXCH = 16, class L, class S>
 MHE_DEV void wcopy(L&& load, S&& store)
 {
-    constexpr int PER = (COUNT + 31) / 32;
+    constexpr int PER = (COUNT + MHE_TEAM - 1) / MHE_TEAM;
     constexpr int CH = PER < MAXCH ? PER : MAXCH;
     using V = decltype(load(0));
 #pragma unroll
@@ -37,27 +59,24 @@ MHE_DEV void wcopy(L&& load, S&& store)
         V v[CH];
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
-            const int i = lane_id() + 32 * (k0 + k);
+            const int i = lane_id() + MHE_TEAM * (k0 + k);
             if (k0 + k < PER && i < COUNT) v[k] = load(i);
         }
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
-            const int i = lane_id() + 32 * (k0 + k);
+            const int i = lane_id() + MHE_TEAM * (k0 + k);
             if (k0 + k < PER && i < COUNT) store(i, v[k]);
         }
     }
-    __syncwarp();
+    wsync();
 }
-
-// Barrier of the warp's lanes.
-MHE_DEV void wsync() { __syncwarp(); }
 
 // Every lane runs f(lane); barrier afterwards.
 template <class F>
 MHE_DEV void wlanes(F&& f)
 {
     f(lane_id());
-    __syncwarp();
+    wsync();
 }
 
 // One lane runs f (index 0); barrier afterwards.
@@ -65,15 +84,16 @@ template <class F>
 MHE_DEV void wone(F&& f)
 {
     if (lane_id() == 0) f(0);
-    __syncwarp();
+    wsync();
 }
 
 // Ask L2 to fetch `bytes` starting at p (one prefetch per 128-byte line, the
-// lines shared round-robin by the lanes); no registers or shared memory used.
+// lines shared round-robin by the lanes); no registers or shared memory used,
+// no barrier.
 MHE_DEV void prefetch_l2(const void* p, int bytes)
 {
     const char* c = static_cast<const char*>(p);
-    for (int off = lane_id() * 128; off < bytes; off += 32 * 128)
+    for (int off = lane_id() * 128; off < bytes; off += MHE_TEAM * 128)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
 }
 

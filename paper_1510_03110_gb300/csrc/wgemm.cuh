@@ -4,17 +4,17 @@
 
 namespace mhe {
 
-// Lane tile of a warp product with M x N outputs: the smallest TM x TN whose
-// ceil(M/TM) ceil(N/TN) tiles fit in the 32 lanes (ties: fewest operand loads
-// TM + TN).  A lane keeps its TM x TN accumulators in registers and loads
+// Lane tile of a team product with M x N outputs: the smallest TM x TN whose
+// ceil(M/TM) ceil(N/TN) tiles fit in the team's lanes (ties: fewest operand
+// loads TM + TN).  A lane keeps its TM x TN accumulators in registers and loads
 // TM + TN operands per step of the inner dimension, so a 24 x 24 product costs
 // 9 shared-memory loads per 18 FMAs instead of two loads per FMA.
-constexpr int tile_pick(int M, int N)
+constexpr int tile_pick(int M, int N, int lanes)
 {
     int best = 0, cost = 1 << 30;
     for (int tm = 1; tm <= M; ++tm)
         for (int tn = 1; tn <= N; ++tn) {
-            if (((M + tm - 1) / tm) * ((N + tn - 1) / tn) > 32) continue;
+            if (((M + tm - 1) / tm) * ((N + tn - 1) / tn) > lanes) continue;
             const int c = tm * tn * 256 + tm + tn;
             if (c < cost) { cost = c; best = tm * 1024 + tn; }
         }
@@ -23,8 +23,8 @@ constexpr int tile_pick(int M, int N)
 
 template <int M, int N>
 struct Tile {
-    static constexpr int TM = tile_pick(M, N) / 1024;
-    static constexpr int TN = tile_pick(M, N) % 1024;
+    static constexpr int TM = tile_pick(M, N, MHE_TEAM) / 1024;
+    static constexpr int TN = tile_pick(M, N, MHE_TEAM) % 1024;
     static constexpr int GM = (M + TM - 1) / TM;
     static constexpr int GN = (N + TN - 1) / TN;
 };

@@ -144,3 +144,31 @@ def test_estimate_host_equals_device(prec, pieces):
     assert torch.equal(x1.cpu(), x2)
     s1.close()
     s2.close()
+
+
+def test_nx64_team_of_four_warps_matches_oracle():
+    """nx=64, nw=ny=32 (128-thread teams per subproblem, FP32 tree + FP64
+    refinement): uneven horizons incl. N = 1, 2, 3 against the FP64 oracle."""
+    import torch
+    n, m = 64, 32
+    Ns = [1, 2, 3, 17, 64, 130]
+    insts = [synth.mhe_instance(600 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP32_IR, refine_tol=1e-13, max_refine=24)
+    x, w, lam = _estimate(d, s)
+    torch.cuda.synchronize()
+    info = s.infos()
+    sols = split(x, w, lam, d["N"], n, m)
+    ref = _oracle(insts)
+    for b in range(len(Ns)):
+        assert info["status"][b] == 0, (b, info[b])
+        assert info["relres"][b] <= 1e-13
+        assert rel_err(sols[b], ref[b]) <= 1e-8, (b, rel_err(sols[b], ref[b]))
+    s.close()
+
+
+def test_nx64_fp64_is_refused():
+    """The FP64 workspace of an nx=64 subproblem exceeds an SM's shared memory."""
+    with pytest.raises(mhe.MheError) as e:
+        mhe.Solver(64, 32, [40], prec=mhe.MHE_FP64)
+    assert e.value.code == -1
