@@ -109,15 +109,16 @@ def make_workload(name):
                     seed=5, l2="inputs larger than L2 (a few GB)")
         b = w["buckets"][24]
         return desc, [dict(n=24, m=12, q=12, N=b["N"], pool=b["pool"], idx=b["idx"], x0=b["x0"])], 1
-    if name == "xl":
+    if name in ("xl", "xl_profile"):
         # 256 instances of nx = 64, nw = ny = 32, N = 1024 (262,144 stages); stages drawn from a seeded pool of
-        # 2048 independent stages (the eigenvalue scaling of 64 x 64 draws dominates generation time)
+        # 2048 independent stages (the eigenvalue scaling of 64 x 64 draws dominates generation time).
+        # xl_profile: 32 instances of N = 256, the ncu case of the same kernels
         rng = np.random.default_rng(5)
-        count, N, n, m = 256, 1024, 64, 32
+        count, N, n, m = (256, 1024, 64, 32) if name == "xl" else (32, 256, 64, 32)
         pool = synth.stage_pool(np.random.default_rng([5, n]), n, m, m, 2048)
         idx = rng.integers(0, 2048, size=count * (N - 1))
         x0 = rng.standard_normal((count, n))
-        desc = dict(workload="256 MHE instances of nx=64, nw=ny=32, N=1024", instances=count, nx=n, nw_ny=m,
+        desc = dict(workload=f"{count} MHE instances of nx=64, nw=ny=32, N={N}", instances=count, nx=n, nw_ny=m,
                     N=N, precision="FP32 tree (128-thread teams) + FP64 refinement", seed=5,
                     l2="inputs larger than L2 (26 GB resident)")
         return desc, [dict(n=n, m=m, q=m, N=np.full(count, N, dtype=np.int64), pool=pool, idx=idx, x0=x0)], 1
@@ -251,7 +252,10 @@ def run_gpu(args):
     t_tune = time.time()
     for bk in buckets:
         plan = dict(leaf_len=16 if prec == 0 else 8, branching=8 if prec == 0 else 4, top_len=4)
-        if args.autotune:
+        if args.plan:
+            lf, br, tp = (int(v) for v in args.plan.split(","))
+            plan = dict(leaf_len=lf, branching=br, top_len=tp)
+        elif args.autotune:
             # the library's autotuner on the first instances of the bucket (a contiguous prefix)
             d = bk["dev"]
             # a prefix of the bucket; nx = 64 tunes on the whole batch (its instances fill the SMs, which
@@ -642,7 +646,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile", "serve", "xl"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile", "serve", "xl", "xl_profile"])
+    ap.add_argument("--plan", default=None, help="leaf_len,branching,top_len used instead of the autotuner")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
     ap.add_argument("--estimators", type=int, default=1024, help="serving: estimator pool")
