@@ -69,7 +69,7 @@ typedef struct {
     int branching;       /* chunk length at levels >= 1 (0: automatic); >= 2 */
     int top_len;         /* a level with horizon <= top_len is solved as one chunk (0: automatic).
                             top_len >= max N gives the plain serial Riccati recursion */
-    double refine_tol;   /* target relative KKT residual (0: 1e-12) */
+    double refine_tol;   /* target relative KKT residual (0: 1e-14 for FP64, 1e-12 for FP32_IR) */
     int max_refine;      /* refinement iterations after the first solve (-1: 2 for FP64, 8 for FP32_IR) */
 } mhe_dims;
 

@@ -109,7 +109,9 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
         err = "this shape's FP64 workspace exceeds the shared memory of an SM: use MHE_FP32_IR";
         return MHE_E_ARG;
     }
-    tol = d.refine_tol > 0 ? d.refine_tol : 1e-12;
+    // FP64: the tree's backward error (~1e-13 on hard instances) can leave a forward
+    // error near 1e-10, so the default asks one FP64 correction of such instances
+    tol = d.refine_tol > 0 ? d.refine_tol : (prec == MHE_FP64 ? 1e-14 : 1e-12);
     max_refine = d.max_refine >= 0 ? d.max_refine : (prec == MHE_FP64 ? 2 : 8);
     int maxN = 1;
     for (int b = 0; b < d.batch; ++b) maxN = d.N[b] > maxN ? d.N[b] : maxN;

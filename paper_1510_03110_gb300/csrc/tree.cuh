@@ -25,6 +25,8 @@
 //   resid_stage   KKT residual rows of one stage (FP64).
 //   assemble_stage  MHE weights -> UFTOC Q_t, l_t, c_t (Section II).
 #pragma once
+#include <type_traits>
+
 #include "common.h"
 #include "warp.cuh"
 #include "wgemm.cuh"
@@ -217,26 +219,82 @@ MHE_DEV bool chol_G(Ws<T, NX>& s, double piv_rel)
     return chol_inplace<T, NX, MT, true>(s, s.G, piv_rel);
 }
 
-// y := (L L^T)^{-1} y with L = lower(s.G), y in registers.
-template <typename T, int NX, int MT>
-MHE_DEV void chol_solve_reg(const Ws<T, NX>& s, T (&y)[MT])
+// ---- blocked triangular solves with the Cholesky factor in s.G ---------------
+// Diagonal blocks of SB rows (the largest divisor of M up to 8): a column's
+// solve within a block is a short chain in registers; the coupling between
+// blocks is a team product (wgemm), so every lane works and no register array
+// grows with M.
+constexpr int solve_block(int M)
 {
-    constexpr int ld = Ws<T, NX>::ld;
-#pragma unroll
-    for (int j = 0; j < MT; ++j) {
-        T acc = y[j];
-#pragma unroll
-        for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * y[p];
-        y[j] = pivot_div(acc, s.G[j + j * ld]);
-    }
-#pragma unroll
-    for (int j = MT - 1; j >= 0; --j) {
-        T acc = y[j];
-#pragma unroll
-        for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * y[p];
-        y[j] = pivot_div(acc, s.G[j + j * ld]);
+    int b = 1;
+    for (int d = 1; d <= 8 && d <= M; ++d)
+        if (M % d == 0) b = d;
+    return b;
+}
+
+template <int I, int N, class F>
+MHE_DEV void static_for(F&& f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>());
+        static_for<I + 1, N>(f);
     }
 }
+
+// X = L^{-1} R (M rows, NC columns): rhs(i, c) gives R, put/get store and read X.
+template <typename T, int NX, int M, int NC, class FR, class FG, class FP>
+MHE_DEV void lower_solve(const Ws<T, NX>& s, FR&& rhs, FG&& get, FP&& put)
+{
+    constexpr int ld = Ws<T, NX>::ld, SB = solve_block(M), NB = M / SB;
+    static_for<0, NB>([&](auto jb) {
+        constexpr int J = decltype(jb)::value, R0 = J * SB;
+        if constexpr (J > 0)   // rows R0.. of R minus L[R0.., 0..R0) X[0..R0)
+            wgemm<T, SB, NC, R0>([&](int i, int c) { return rhs(R0 + i, c); },
+                                 [&](int i, int p) { return -s.G[R0 + i + p * ld]; },
+                                 [&](int p, int c) { return get(p, c); },
+                                 [&](int i, int c, T v) { put(R0 + i, c, v); });
+        wfor(NC, [&](int c) {
+            T y[SB];
+#pragma unroll
+            for (int i = 0; i < SB; ++i) {
+                T acc = (J > 0) ? get(R0 + i, c) : rhs(R0 + i, c);
+#pragma unroll
+                for (int p = 0; p < i; ++p) acc -= s.G[R0 + i + (R0 + p) * ld] * y[p];
+                y[i] = pivot_div(acc, s.G[R0 + i + (R0 + i) * ld]);
+            }
+#pragma unroll
+            for (int i = 0; i < SB; ++i) put(R0 + i, c, y[i]);
+        });
+    });
+}
+
+// X = L^{-T} R: rhs(i, c) gives R, put/get store and read X.
+template <typename T, int NX, int M, int NC, class FR, class FG, class FP>
+MHE_DEV void upper_solve(const Ws<T, NX>& s, FR&& rhs, FG&& get, FP&& put)
+{
+    constexpr int ld = Ws<T, NX>::ld, SB = solve_block(M), NB = M / SB;
+    static_for<0, NB>([&](auto kb) {
+        constexpr int J = NB - 1 - decltype(kb)::value, R0 = J * SB, R1 = R0 + SB;
+        if constexpr (J < NB - 1)   // rows R0.. of R minus L[R1.., R0..]^T X[R1..)
+            wgemm<T, SB, NC, M - R1>([&](int i, int c) { return rhs(R0 + i, c); },
+                                     [&](int i, int p) { return -s.G[R1 + p + (R0 + i) * ld]; },
+                                     [&](int p, int c) { return get(R1 + p, c); },
+                                     [&](int i, int c, T v) { put(R0 + i, c, v); });
+        wfor(NC, [&](int c) {
+            T y[SB];
+#pragma unroll
+            for (int i = SB - 1; i >= 0; --i) {
+                T acc = (J < NB - 1) ? get(R0 + i, c) : rhs(R0 + i, c);
+#pragma unroll
+                for (int p = i + 1; p < SB; ++p) acc -= s.G[R0 + p + (R0 + i) * ld] * y[p];
+                y[i] = pivot_div(acc, s.G[R0 + i + (R0 + i) * ld]);
+            }
+#pragma unroll
+            for (int i = 0; i < SB; ++i) put(R0 + i, c, y[i]);
+        });
+    });
+}
+
 
 // One backward stage of Algorithm 4 (or Algorithms 1-2 when want_v is false).
 // On entry s.P = P_{t+1}, s.Psi = Psi_{t+1}, s.V = V_{t+1}, s.v = v_{t+1},
@@ -280,42 +338,30 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
     wgemm<T, NX, 1, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.A[p + i * ld]; },
                         [&](int p, int) { return s.u[p]; }, [&](int i, int, T v) { s.tv[i] = v; });
     const bool bad = chol_G<T, NX, MT>(s, piv_rel);
-    // per column c: y = Lg^{-1} H^T e_c -> Y (in PB), K e_c = -Lg^{-T} y;  lane NX: k = G^{-1} g
-    wfor(NX + 1, [&](int c) {
-        T y[MT];
-        if (c < NX) {
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                T acc = s.H[c + j * ld];
-#pragma unroll
-                for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * y[p];
-                y[j] = pivot_div(acc, s.G[j + j * ld]);
-            }
-#pragma unroll
-            for (int j = 0; j < MT; ++j) s.PB[j + c * ld] = y[j];
-#pragma unroll
-            for (int j = MT - 1; j >= 0; --j) {
-                T acc = y[j];
-#pragma unroll
-                for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * y[p];
-                y[j] = pivot_div(acc, s.G[j + j * ld]);
-            }
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                s.K[j + c * ld] = -y[j];
-                if (Kout) Kout[j + c * MT] = -y[j];
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < MT; ++j) y[j] = s.g[j];
-            chol_solve_reg<T, NX, MT>(s, y);
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                s.k[j] = y[j];
-                if (kout) kout[j] = y[j];
-            }
-        }
-    });
+    // [Y | y] = Lg^{-1} [H^T | g] (Y in PB, y in tmp);  K = -Lg^{-T} Y (s.K),  k = Lg^{-T} y = G^{-1} g (s.k)
+    {
+        auto rhsY = [&](int i, int c) -> T { return c < NX ? s.H[c + i * ld] : s.g[i]; };
+        auto getY = [&](int i, int c) -> T { return c < NX ? s.PB[i + c * ld] : s.tmp[i]; };
+        auto putY = [&](int i, int c, T v) {
+            if (c < NX) s.PB[i + c * ld] = v;
+            else s.tmp[i] = v;
+        };
+        lower_solve<T, NX, MT, NX + 1>(s, rhsY, getY, putY);
+        auto getX = [&](int i, int c) -> T { return c < NX ? -s.K[i + c * ld] : s.k[i]; };
+        auto putX = [&](int i, int c, T v) {
+            if (c < NX) s.K[i + c * ld] = -v;
+            else s.k[i] = v;
+        };
+        upper_solve<T, NX, MT, NX + 1>(s, getY, getX, putX);
+        if (Kout || kout)
+            wfor(MT * NX + MT, [&](int r) {
+                if (r < MT * NX) {
+                    if (Kout) Kout[r] = s.K[r % MT + (r / MT) * ld];
+                } else if (kout) {
+                    kout[r - MT * NX] = s.k[r - MT * NX];
+                }
+            });
+    }
     // P -= Y^T Y (symmetric),  Psi = A^T u - l_x + K^T g,  store chol(G)
     wgemm<T, NX, NX, MT, true>([&](int i, int j) { return s.P[i + j * ld]; },
                                [&](int i, int q) { return -s.PB[q + i * ld]; },
@@ -339,34 +385,19 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
     wgemm<T, MT, NX, NX>([&](int, int) { return (T)0; }, [&](int j, int p) { return s.B[p + j * ld]; },
                          [&](int p, int c) { return s.V[p + c * ld]; },
                          [&](int j, int c, T v) { s.H[j + c * ld] = v; });
-    // per column c: Z = Lg^{-1} BV e_c (in PB), L e_c = -Lg^{-T} Z
-    wfor(NX, [&](int c) {
-        {
-            T z[MT];
-#pragma unroll
-            for (int j = 0; j < MT; ++j) z[j] = s.H[j + c * ld];
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                T acc = z[j];
-#pragma unroll
-                for (int p = 0; p < j; ++p) acc -= s.G[j + p * ld] * z[p];
-                z[j] = pivot_div(acc, s.G[j + j * ld]);
-            }
-#pragma unroll
-            for (int j = 0; j < MT; ++j) s.PB[j + c * ld] = z[j];
-#pragma unroll
-            for (int j = MT - 1; j >= 0; --j) {
-                T acc = z[j];
-#pragma unroll
-                for (int p = j + 1; p < MT; ++p) acc -= s.G[p + j * ld] * z[p];
-                z[j] = pivot_div(acc, s.G[j + j * ld]);
-            }
-            if (Lout) {
-#pragma unroll
-                for (int j = 0; j < MT; ++j) Lout[j + c * MT] = -z[j];
-            }
+    // Z = Lg^{-1} BV (in PB),  L = -Lg^{-T} Z (formed in Tt, stored)
+    {
+        auto rhsZ = [&](int i, int c) -> T { return s.H[i + c * ld]; };
+        auto getZ = [&](int i, int c) -> T { return s.PB[i + c * ld]; };
+        auto putZ = [&](int i, int c, T v) { s.PB[i + c * ld] = v; };
+        lower_solve<T, NX, MT, NX>(s, rhsZ, getZ, putZ);
+        if (Lout) {
+            auto getL = [&](int i, int c) -> T { return s.Tt[i + c * ld]; };
+            auto putL = [&](int i, int c, T v) { s.Tt[i + c * ld] = v; };
+            upper_solve<T, NX, MT, NX>(s, getZ, getL, putL);
+            wfor(MT * NX, [&](int r) { Lout[r] = -s.Tt[r % MT + (r / MT) * ld]; });
         }
-    });
+    }
     // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z (symmetric)
     wgemm<T, NX, NX, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.A[p + i * ld]; },
                          [&](int p, int j) { return s.V[p + j * ld]; },
@@ -548,17 +579,17 @@ MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Pin, const T
             s.tv[i] = acc;
         }
     });
-    wone([&](int) {
-        T y[MT];
-#pragma unroll
-        for (int j = 0; j < MT; ++j) y[j] = s.g[j];
-        chol_solve_reg<T, NX, MT>(s, y);
-#pragma unroll
-        for (int j = 0; j < MT; ++j) {
-            s.k[j] = y[j];
-            kout[j] = y[j];
-        }
-    });
+    // k = G^{-1} g with the stored factor: Lg y = g (y in tmp), Lg^T k = y
+    {
+        auto rhsg = [&](int i, int) -> T { return s.g[i]; };
+        auto gety = [&](int i, int) -> T { return s.tmp[i]; };
+        auto puty = [&](int i, int, T v) { s.tmp[i] = v; };
+        lower_solve<T, NX, MT, 1>(s, rhsg, gety, puty);
+        auto getk = [&](int i, int) -> T { return s.k[i]; };
+        auto putk = [&](int i, int, T v) { s.k[i] = v; };
+        upper_solve<T, NX, MT, 1>(s, gety, getk, putk);
+        wfor(MT, [&](int j) { kout[j] = s.k[j]; });
+    }
     wfor(NX, [&](int i) {
         T acc = s.tv[i] - X::lx(st, i);
 #pragma unroll 8
