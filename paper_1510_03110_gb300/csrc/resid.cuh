@@ -261,6 +261,100 @@ MHE_DEV void resid_mhe(const ResidArgs<TR>& r, int b, int t, int N, unsigned lon
     });
 }
 
+// Stage t >= 1 with the assembled Q: the same rows as resid_rows, as dot
+// products of length n or nw dealt round-robin to the lanes (each Q row is
+// split into its x and w halves) and one predicated FMA loop, then the rows
+//   Q_x x + Q_xw w + A^T lam_{t+1} - lam_t + l_x,  Q_xw^T x + Q_w w + B^T lam_{t+1} + l_w,
+//   A x + B w + a - x_{t+1}  (and the terminal rows at t = N - 1).
+template <int NX, int NW, typename TR>
+MHE_DEV void resid_q(const ResidArgs<TR>& r, int b, int t, int N, unsigned long long* sm)
+{
+    constexpr int NQ = NX + NW;
+    const long long gx = r.gs0[b] + b;
+    const double* xt = r.x + (gx + t) * NX;
+    const double* xn = xt + NX;
+    const double* lt = r.lam + (gx + t) * NX;
+    const double* ln = lt + NX;
+    const double* wt = r.w + r.w_off[b] + NX + (long long)(t - 1) * NW;
+    const long long s = r.in_off[b] + t - 1;
+    const double* A = r.A + s * NX * NX;
+    const double* B = r.B + s * NX * NW;
+    const double* Q = r.Q + s * NQ * NQ;
+    const double* l = r.l ? r.l + s * NQ : nullptr;
+    const double* a = r.a ? r.a + s * NX : nullptr;
+    const long long so = r.out_off[b] + t - 1;
+    TR* rl = r.rl + so * NQ;
+    TR* ra = r.ra + so * NX;
+    const bool lastst = (t == N - 1);
+    double* qx = reinterpret_cast<double*>(sm);   // Q[:, 0:n] x      (NQ)
+    double* qw = qx + NQ;                         // Q[:, n:n+nw] w   (NQ)
+    double* atl = qw + NQ;                        // A^T lam_{t+1}    (NX)
+    double* btl = atl + NX;                       // B^T lam_{t+1}    (NW)
+    double* dA = btl + NW;                        // A x              (NX)
+    double* dB = dA + NX;                         // B w              (NX)
+    double* zero = dB + NX;
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(zero + 1);
+    wone([&](int) {
+        zero[0] = 0.0;
+        mx[0] = mx[1] = mx[2] = 0ULL;
+    });
+    constexpr int T1 = NQ + NX + NW + NX;   // length-n tasks, then length-nw tasks
+    wfor(T1 + NQ + NX, [&](int k) {
+        const double* m;
+        const double* v;
+        double* o;
+        int st, len = NX;
+        if (k < NQ) { m = Q + k; st = NQ; v = xt; o = qx + k; }
+        else if (k < NQ + NX) { m = A + (k - NQ) * NX; st = 1; v = ln; o = atl + (k - NQ); }
+        else if (k < NQ + NX + NW) { m = B + (k - NQ - NX) * NX; st = 1; v = ln; o = btl + (k - NQ - NX); }
+        else if (k < T1) { m = A + (k - NQ - NX - NW); st = NX; v = xt; o = dA + (k - NQ - NX - NW); }
+        else if (k < T1 + NQ) { m = Q + (k - T1) + NX * NQ; st = NQ; v = wt; o = qw + (k - T1); len = NW; }
+        else { m = B + (k - T1 - NQ); st = NX; v = wt; o = dB + (k - T1 - NQ); len = NW; }
+        *o = dot_pred<(NX > NW ? NX : NW)>(m, st, v, len, 0.0);
+    });
+    unsigned long long m0 = 0, m1 = 0, m2 = 0;
+    const int nrow = NQ + NX + (lastst ? NX : 0);
+    const double* xN = r.x + (gx + N) * NX;
+    const double* lamN = r.lam + (gx + N) * NX;
+    wfor(nrow, [&](int i) {
+        const double *p1, *p2, *p3, *p4, *p5, *z1, *z2;
+        TR* dst;
+        if (i < NX) {
+            p1 = qx + i; p2 = qw + i; p3 = atl + i; p4 = lt + i; p5 = l ? l + i : zero;
+            z1 = xt + i; z2 = lt + i; dst = rl + i;
+        } else if (i < NQ) {
+            p1 = qx + i; p2 = qw + i; p3 = btl + (i - NX); p4 = zero; p5 = l ? l + i : zero;
+            z1 = wt + (i - NX); z2 = zero; dst = rl + i;
+        } else if (i < NQ + NX) {
+            const int ii = i - NQ;
+            p1 = dA + ii; p2 = dB + ii; p3 = zero; p4 = xn + ii; p5 = a ? a + ii : zero;
+            z1 = zero; z2 = zero; dst = ra + ii;
+        } else {
+            // terminal rows with Q_{x,N} = 0, l_N = 0: r = lambda_N
+            const int ii = i - NQ - NX;
+            p1 = zero; p2 = zero; p3 = zero; p4 = lamN + ii; p5 = zero;
+            z1 = xN + ii; z2 = lamN + ii; dst = r.rlN + (long long)b * NX + ii;
+        }
+        const double sum = *p5 + (((*p1 + *p2) + *p3) - *p4);   // r = -(l + K z)
+        *dst = (TR)sum;
+        const unsigned long long rr = abs_bits(sum), bb = abs_bits(*p5);
+        const unsigned long long za = abs_bits(*z1), zb = abs_bits(*z2);
+        const unsigned long long zz = za > zb ? za : zb;
+        m0 = rr > m0 ? rr : m0;
+        m1 = zz > m1 ? zz : m1;
+        m2 = bb > m2 ? bb : m2;
+    });
+    atomic_max_u64(mx + 0, m0);
+    atomic_max_u64(mx + 1, m1);
+    atomic_max_u64(mx + 2, m2);
+    wsync();
+    wone([&](int) {
+        atomic_max_u64(r.norms + 3LL * b + 0, mx[0]);
+        atomic_max_u64(r.norms + 3LL * b + 1, mx[1]);
+        atomic_max_u64(r.norms + 3LL * b + 2, mx[2]);
+    });
+}
+
 MHE_DEV int stage_instance(const long long* gs0, int batch, long long gstage)
 {
     int lo = 0, hi = batch;
@@ -282,7 +376,7 @@ MHE_DEV void resid_stage(const ResidArgs<TR>& r, long long gstage, unsigned long
         resid_rows<NX, NW, 1, TR>(r, b, t, N, sm);
     } else {
         if constexpr (NY > 0) resid_mhe<NX, NW, NY, TR>(r, b, t, N, sm);
-        else resid_rows<NX, NW, 0, TR>(r, b, t, N, sm);
+        else resid_q<NX, NW, TR>(r, b, t, N, sm);
     }
 }
 
