@@ -471,6 +471,15 @@ MHE_DEV void prefetch_leaf(const LevelArgs<T>& a, int b, int t)
     if (a.a) prefetch_l2(a.a + (a.rhs_off[b] + t - 1) * NX, (int)(sizeof(T) * NX));
 }
 
+// the stored factors K, k, L of level-0 stage g (down pass), into L2
+template <typename T, int NX, int NW>
+MHE_DEV void prefetch_factors(const LevelArgs<T>& a, long long g)
+{
+    prefetch_l2(a.Kst + g * NW * NX, (int)(sizeof(T) * NW * NX));
+    prefetch_l2(a.Lst + g * NW * NX, (int)(sizeof(T) * NW * NX));
+    prefetch_l2(a.kst + g * NW, (int)(sizeof(T) * NW));
+}
+
 // ---- Algorithm 4 over one chunk ----------------------------------------------
 
 template <typename T, int NX, int NW, bool UPPER>
@@ -783,6 +792,10 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     for (int tt = 0; tt < cd.len; ++tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
+        if (!UPPER && tt + 1 < cd.len) {   // the next stage's data and factors, into L2
+            prefetch_leaf<T, NX, NW>(a, b, t + 1);
+            prefetch_factors<T, NX, NW>(a, g + 1);
+        }
         if (UPPER)
             down_fwd_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), a.Kst + g * NX * NX,
                                                  a.kst + g * NX, a.Lst + g * NX * NX, !last, xo(t), wo(t));
@@ -818,6 +831,7 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     for (int tt = cd.len - 1; tt >= 0; --tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
+        if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1);
         if (UPPER)
             down_bwd_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), xo(t), wo(t), lo(t),
                                                  zxo(t), zwo(t), zlo(t));
