@@ -23,15 +23,18 @@ constexpr int op_count()
 // teams per CTA of at most 256 threads: at most 256 / MHE_TEAM
 constexpr int kMaxTeams = 256 / MHE_TEAM;
 
-// teams per CTA: as many per-team workspaces as fit in 200 KB, at most kMaxTeams
+// shared memory the level kernels give their teams' workspaces per CTA
+constexpr int kLevelSmem = 224 * 1024;
+
+// teams per CTA: as many per-team workspaces as fit in kLevelSmem, at most kMaxTeams
 template <typename T, int NX, int OP>
 constexpr int level_warps()
 {
-    return (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) >= kMaxTeams
+    return (kLevelSmem) / (int)(op_count<T, NX, OP>() * sizeof(T)) >= kMaxTeams
                ? kMaxTeams
-               : ((200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)) < 1
+               : ((kLevelSmem) / (int)(op_count<T, NX, OP>() * sizeof(T)) < 1
                       ? 1
-                      : (200 * 1024) / (int)(op_count<T, NX, OP>() * sizeof(T)));
+                      : (kLevelSmem) / (int)(op_count<T, NX, OP>() * sizeof(T)));
 }
 
 // a workspace the shared memory of one SM can hold (227 KB per CTA)

@@ -35,13 +35,27 @@ namespace mhe {
 
 enum { KIND_LEAF = 0, KIND_ARRIVAL = 1, KIND_UPPER = 2 };
 
-// Shared-memory workspace of one warp (every matrix slot holds up to NX x NX
-// with an odd leading dimension to spread the banks).
+// Leading dimension of the workspace matrices: a multiple of the 16-byte
+// vector (V elements) so every column starts 16-byte aligned, with an odd
+// number of vectors per column so neighbouring columns start in different
+// bank groups.
+constexpr int pick_ld(int n, int v)
+{
+    int l = n;
+    while (l % v != 0 || (l / v) % 2 == 0) ++l;
+    return l;
+}
+
+// Shared-memory workspace of one team (every matrix slot holds up to NX x NX;
+// columns and vectors 16-byte aligned for the vector loads of wgemm_tn).
 template <typename T, int NX>
 struct Ws {
-    static constexpr int ld = NX | 1;
+    static constexpr int VEC = 16 / (int)sizeof(T);
+    static constexpr int ld = pick_ld(NX, VEC);
     static constexpr int slot = NX * ld;
-    static constexpr int count = ((10 * slot + 8 * NX + 8) + 3) / 4 * 4;
+    static constexpr int nv = (NX + VEC - 1) / VEC * VEC;   // a vector's length, rounded to the 16-byte unit
+    static constexpr int count = (10 * slot + 8 * nv + 8 + VEC - 1) / VEC * VEC;
+    static_assert(ld % VEC == 0 && slot % VEC == 0 && nv % VEC == 0, "16-byte aligned columns and vectors");
     T *P, *V, *Qw, *A, *Tt, *B, *PB, *H, *K, *G;
     T *Psi, *v, *u, *e, *tv, *g, *k, *tmp;
     T* sc;
@@ -51,29 +65,29 @@ struct Ws {
         P = p; p += slot; V = p; p += slot; Qw = p; p += slot; A = p; p += slot;
         Tt = p; p += slot; B = p; p += slot; PB = p; p += slot; H = p; p += slot;
         K = p; p += slot; G = p; p += slot;
-        Psi = p; p += NX; v = p; p += NX; u = p; p += NX; e = p; p += NX;
-        tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
+        Psi = p; p += nv; v = p; p += nv; u = p; p += nv; e = p; p += nv;
+        tv = p; p += nv; g = p; p += nv; k = p; p += nv; tmp = p; p += nv;
         sc = p;
     }
     // right-hand-side pass: only A, B, K, G and the vectors
-    static constexpr int count_rhs = ((4 * slot + 8 * NX + 8) + 3) / 4 * 4;
+    static constexpr int count_rhs = (4 * slot + 8 * nv + 8 + VEC - 1) / VEC * VEC;
     MHE_DEV void carve_rhs(T* base)
     {
         T* p = base;
         P = V = Qw = Tt = PB = H = nullptr;
         A = p; p += slot; B = p; p += slot; K = p; p += slot; G = p; p += slot;
-        Psi = p; p += NX; v = p; p += NX; u = p; p += NX; e = p; p += NX;
-        tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
+        Psi = p; p += nv; v = p; p += nv; u = p; p += nv; e = p; p += nv;
+        tv = p; p += nv; g = p; p += nv; k = p; p += nv; tmp = p; p += nv;
         sc = p;
     }
     // down pass: the vectors only
-    static constexpr int count_vec = ((8 * NX + 8) + 3) / 4 * 4;
+    static constexpr int count_vec = (8 * nv + 8 + VEC - 1) / VEC * VEC;
     MHE_DEV void carve_vectors(T* base)
     {
         T* p = base;
         P = V = Qw = A = Tt = B = PB = H = K = G = nullptr;
-        Psi = p; p += NX; v = p; p += NX; u = p; p += NX; e = p; p += NX;
-        tv = p; p += NX; g = p; p += NX; k = p; p += NX; tmp = p; p += NX;
+        Psi = p; p += nv; v = p; p += nv; u = p; p += nv; e = p; p += nv;
+        tv = p; p += nv; g = p; p += nv; k = p; p += nv; tmp = p; p += nv;
         sc = p;
     }
 };
@@ -311,32 +325,25 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
     load_AB<T, NX, MT, KIND>(s, st);
     // P A -> Tt,  P B -> PB,  u = Psi - P a
-    wgemm<T, NX, NX, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.P[i + p * ld]; },
-                         [&](int p, int j) { return s.A[p + j * ld]; },
-                         [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
-    wgemm<T, NX, MT, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.P[i + p * ld]; },
-                         [&](int p, int j) { return s.B[p + j * ld]; },
-                         [&](int i, int j, T v) { s.PB[i + j * ld] = v; });
-    wgemm<T, NX, 1, NX>([&](int i, int) { return s.Psi[i]; }, [&](int i, int p) { return -s.P[i + p * ld]; },
-                        [&](int p, int) { return s.e[p]; }, [&](int i, int, T v) { s.u[i] = v; });
+    // (P is symmetric: row i of P is column i, read along the inner dimension)
+    wgemm_tn<T, NX, NX, NX, ld, ld>([&](int, int) { return (T)0; }, s.P, s.A, (T)1,
+                                    [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+    wgemm_tn<T, NX, MT, NX, ld, ld>([&](int, int) { return (T)0; }, s.P, s.B, (T)1,
+                                    [&](int i, int j, T v) { s.PB[i + j * ld] = v; });
+    wgemm_tn<T, NX, 1, NX, ld, 0>([&](int i, int) { return s.Psi[i]; }, s.P, s.e, (T)-1,
+                                  [&](int i, int, T v) { s.u[i] = v; });
     // F = Q_x + A^T P A -> P (symmetric),  G = Q_w + B^T P B (symmetric),  H = Q_xw + A^T P B,
     // g = B^T u - l_w,  tv = A^T u
-    wgemm<T, NX, NX, NX, true>([&](int i, int j) { return X::qx(st, i, j); },
-                               [&](int i, int p) { return s.A[p + i * ld]; },
-                               [&](int p, int j) { return s.Tt[p + j * ld]; },
-                               [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
-    wgemm<T, MT, MT, NX, true>([&](int i, int j) { return X::qw(st, i, j); },
-                               [&](int i, int p) { return s.B[p + i * ld]; },
-                               [&](int p, int j) { return s.PB[p + j * ld]; },
-                               [&](int i, int j, T v) { s.G[i + j * ld] = v; s.G[j + i * ld] = v; });
-    wgemm<T, NX, MT, NX>([&](int i, int j) { return X::qxw(st, i, j); },
-                         [&](int i, int p) { return s.A[p + i * ld]; },
-                         [&](int p, int j) { return s.PB[p + j * ld]; },
-                         [&](int i, int j, T v) { s.H[i + j * ld] = v; });
-    wgemm<T, MT, 1, NX>([&](int j, int) { return -X::lw(st, j); }, [&](int j, int p) { return s.B[p + j * ld]; },
-                        [&](int p, int) { return s.u[p]; }, [&](int j, int, T v) { s.g[j] = v; });
-    wgemm<T, NX, 1, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.A[p + i * ld]; },
-                        [&](int p, int) { return s.u[p]; }, [&](int i, int, T v) { s.tv[i] = v; });
+    wgemm_tn<T, NX, NX, NX, ld, ld, true>([&](int i, int j) { return X::qx(st, i, j); }, s.A, s.Tt, (T)1,
+                                          [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
+    wgemm_tn<T, MT, MT, NX, ld, ld, true>([&](int i, int j) { return X::qw(st, i, j); }, s.B, s.PB, (T)1,
+                                          [&](int i, int j, T v) { s.G[i + j * ld] = v; s.G[j + i * ld] = v; });
+    wgemm_tn<T, NX, MT, NX, ld, ld>([&](int i, int j) { return X::qxw(st, i, j); }, s.A, s.PB, (T)1,
+                                    [&](int i, int j, T v) { s.H[i + j * ld] = v; });
+    wgemm_tn<T, MT, 1, NX, ld, 0>([&](int j, int) { return -X::lw(st, j); }, s.B, s.u, (T)1,
+                                  [&](int j, int, T v) { s.g[j] = v; });
+    wgemm_tn<T, NX, 1, NX, ld, 0>([&](int, int) { return (T)0; }, s.A, s.u, (T)1,
+                                  [&](int i, int, T v) { s.tv[i] = v; });
     const bool bad = chol_G<T, NX, MT>(s, piv_rel);
     // [Y | y] = Lg^{-1} [H^T | g] (Y in PB, y in tmp);  K = -Lg^{-T} Y (s.K),  k = Lg^{-T} y = G^{-1} g (s.k)
     {
@@ -363,13 +370,10 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
             });
     }
     // P -= Y^T Y (symmetric),  Psi = A^T u - l_x + K^T g,  store chol(G)
-    wgemm<T, NX, NX, MT, true>([&](int i, int j) { return s.P[i + j * ld]; },
-                               [&](int i, int q) { return -s.PB[q + i * ld]; },
-                               [&](int q, int j) { return s.PB[q + j * ld]; },
-                               [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
-    wgemm<T, NX, 1, MT>([&](int i, int) { return s.tv[i] - X::lx(st, i); },
-                        [&](int i, int q) { return s.K[q + i * ld]; }, [&](int q, int) { return s.g[q]; },
-                        [&](int i, int, T v) { s.Psi[i] = v; });
+    wgemm_tn<T, NX, NX, MT, ld, ld, true>([&](int i, int j) { return s.P[i + j * ld]; }, s.PB, s.PB, (T)-1,
+                                          [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
+    wgemm_tn<T, NX, 1, MT, ld, 0>([&](int i, int) { return s.tv[i] - X::lx(st, i); }, s.K, s.g, (T)1,
+                                  [&](int i, int, T v) { s.Psi[i] = v; });
     if (Lgout)
         wfor(MT * MT, [&](int r) {
             const int i = r % MT, j = r / MT;
@@ -380,11 +384,10 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
     wgemm<T, NX, 1, MT>([&](int i, int) { return s.e[i]; }, [&](int i, int j) { return s.B[i + j * ld]; },
                         [&](int j, int) { return s.k[j]; }, [&](int i, int, T v) { s.tv[i] = v; });
     // v += V^T e;  BV = B^T V (in H)
-    wgemm<T, NX, 1, NX>([&](int i, int) { return s.v[i]; }, [&](int i, int p) { return s.V[p + i * ld]; },
-                        [&](int p, int) { return s.tv[p]; }, [&](int i, int, T v) { s.v[i] = v; });
-    wgemm<T, MT, NX, NX>([&](int, int) { return (T)0; }, [&](int j, int p) { return s.B[p + j * ld]; },
-                         [&](int p, int c) { return s.V[p + c * ld]; },
-                         [&](int j, int c, T v) { s.H[j + c * ld] = v; });
+    wgemm_tn<T, NX, 1, NX, ld, 0>([&](int i, int) { return s.v[i]; }, s.V, s.tv, (T)1,
+                                  [&](int i, int, T v) { s.v[i] = v; });
+    wgemm_tn<T, MT, NX, NX, ld, ld>([&](int, int) { return (T)0; }, s.B, s.V, (T)1,
+                                    [&](int j, int c, T v) { s.H[j + c * ld] = v; });
     // Z = Lg^{-1} BV (in PB),  L = -Lg^{-T} Z (formed in Tt, stored)
     {
         auto rhsZ = [&](int i, int c) -> T { return s.H[i + c * ld]; };
@@ -399,17 +402,12 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         }
     }
     // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z (symmetric)
-    wgemm<T, NX, NX, NX>([&](int, int) { return (T)0; }, [&](int i, int p) { return s.A[p + i * ld]; },
-                         [&](int p, int j) { return s.V[p + j * ld]; },
-                         [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
-    wgemm<T, NX, NX, MT>([&](int i, int j) { return s.Tt[i + j * ld]; },
-                         [&](int i, int q) { return s.K[q + i * ld]; },
-                         [&](int q, int j) { return s.H[q + j * ld]; },
-                         [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
-    wgemm<T, NX, NX, MT, true>([&](int i, int j) { return s.Qw[i + j * ld]; },
-                               [&](int i, int q) { return s.PB[q + i * ld]; },
-                               [&](int q, int j) { return s.PB[q + j * ld]; },
-                               [&](int i, int j, T v) { s.Qw[i + j * ld] = v; s.Qw[j + i * ld] = v; });
+    wgemm_tn<T, NX, NX, NX, ld, ld>([&](int, int) { return (T)0; }, s.A, s.V, (T)1,
+                                    [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+    wgemm_tn<T, NX, NX, MT, ld, ld>([&](int i, int j) { return s.Tt[i + j * ld]; }, s.K, s.H, (T)1,
+                                    [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+    wgemm_tn<T, NX, NX, MT, ld, ld, true>([&](int i, int j) { return s.Qw[i + j * ld]; }, s.PB, s.PB, (T)1,
+                                          [&](int i, int j, T v) { s.Qw[i + j * ld] = v; s.Qw[j + i * ld] = v; });
     T* tmp = s.V;
     s.V = s.Tt;
     s.Tt = tmp;

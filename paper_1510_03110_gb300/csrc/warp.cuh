@@ -97,6 +97,18 @@ MHE_DEV void prefetch_l2(const void* p, int bytes)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
 }
 
+// One 16-byte shared-memory load: 4 floats or 2 doubles (p 16-byte aligned).
+MHE_DEV void ld16(const float* p, float (&v)[4])
+{
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+MHE_DEV void ld16(const double* p, double (&v)[2])
+{
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+}
+
 MHE_DEV double msqrt(double v) { return sqrt(v); }
 MHE_DEV float msqrt(float v) { return sqrtf(v); }
 MHE_DEV double mabs(double v) { return fabs(v); }

@@ -72,4 +72,63 @@ MHE_DEV void wgemm(FI&& init, FA&& a, FB&& b, FO&& out)
     });
 }
 
+// out(i, j, init(i, j) + sgn * sum_{p<K} Ab[p + i LDA] Bb[p + j LDB]) for i < M,
+// j < N: both operands are read along the inner dimension (a transposed left
+// operand, the right operand by columns), 16 bytes per shared-memory load.
+// Ab, Bb 16-byte aligned; LDA, LDB multiples of the vector (LDB unused for
+// N = 1).  SYM as in wgemm.
+template <typename T, int M, int N, int K, int LDA, int LDB, bool SYM = false, class FI, class FO>
+MHE_DEV void wgemm_tn(FI&& init, const T* Ab, const T* Bb, T sgn, FO&& out)
+{
+    constexpr int V = 16 / (int)sizeof(T), KV = K / V * V;
+    static_assert(LDA % V == 0 && (N == 1 || LDB % V == 0), "aligned columns");
+    using TL = Tile<M, N>;
+    constexpr int TM = TL::TM, TN = TL::TN, GM = TL::GM, GN = TL::GN;
+    // a lane's rows and columns are interleaved (row g + GM r, column h + GN c): the
+    // lanes of a quarter-warp then read columns one leading dimension apart, an odd
+    // number of 16-byte vectors, so their vector loads fall in distinct bank groups
+    wlanes([&](int lane) {
+        if (lane >= GM * GN) return;
+        const int g = lane % GM, h = lane / GM;
+        const T* ap[TM];
+        const T* bp[TN];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) ap[r] = Ab + (g + GM * r < M ? g + GM * r : M - 1) * LDA;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) bp[c] = Bb + (h + GN * c < N ? h + GN * c : N - 1) * LDB;
+        T acc[TM][TN];
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) acc[r][c] = (T)0;
+#pragma unroll 2
+        for (int p = 0; p < KV; p += V) {
+            T av[TM][V], bv[TN][V];
+#pragma unroll
+            for (int r = 0; r < TM; ++r) ld16(ap[r] + p, av[r]);
+#pragma unroll
+            for (int c = 0; c < TN; ++c) ld16(bp[c] + p, bv[c]);
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c)
+#pragma unroll
+                    for (int q = 0; q < V; ++q) acc[r][c] += av[r][q] * bv[c][q];
+        }
+#pragma unroll
+        for (int p = KV; p < K; ++p)
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[r][c] += ap[r][p] * bp[c][p];
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) {
+                const int i = g + GM * r, j = h + GN * c;
+                if (i < M && j < N && (!SYM || i <= j)) out(i, j, init(i, j) + sgn * acc[r][c]);
+            }
+    });
+}
+
 }  // namespace mhe
