@@ -22,7 +22,9 @@ template <int NX, int NW, int NY = 0>
 struct ResidSmem {
     static constexpr int rows = 5 * NX + NW;
     static constexpr int q_form = 3 * rows + 4;                      // resid_rows
-    static constexpr int mhe_form = 4 * NX + 3 * NW + 3 * NY + 5;    // resid_mhe
+    // pieces of a length-n product in resid_mhe (only when the pieces stay >= 8 long)
+    static constexpr int sp = (NX % NW == 0 && NW >= 8) ? NX / NW : 1;
+    static constexpr int mhe_form = 4 * NX + 3 * NW + 3 * NY + 5 + sp * (2 * NX + NY + NW);   // resid_mhe
     static constexpr int count = q_form > mhe_form ? q_form : mhe_form;   // 8-byte entries
 };
 
@@ -193,20 +195,44 @@ MHE_DEV void resid_mhe(const ResidArgs<TR>& r, int b, int t, int N, unsigned lon
         mx[0] = mx[1] = mx[2] = 0ULL;
     });
     // V(p,q) = R[NW+p + (NW+q) NR], S(k,p) = R[k + (NW+p) NR], W(k,j) = R[k + j NR]
-    constexpr int T1 = NX + NY + NX + NW;   // length-n tasks, then length-nw tasks
-    wfor(T1 + NX + NW + NY, [&](int k) {
+    // The length-n dot products (A x, C x, A^T lam, B^T lam) are cut into SP pieces of
+    // length n / SP = nw when nw divides n and nw >= 8, so every task of the phase has
+    // one length (shorter pieces cost more in tasks than they save in idle lanes).
+    constexpr int T1 = NX + NY + NX + NW;                  // length-n dot products
+    constexpr int SP = ResidSmem<NX, NW, NY>::sp;          // pieces per length-n product
+    constexpr int LP = NX / SP;                            // piece length
+    constexpr int KM = LP > NW ? LP : NW;
+    double* part = zero + 4;                               // SP x T1 partial sums (past mx[3])
+    wfor(T1 * SP + NX + NW + NY, [&](int k) {
         const double* m;
         const double* v;
         double* o;
-        int st, len = NX;
-        if (k < NX) { m = A + k; st = NX; v = xt; o = dA + k; }
-        else if (k < NX + NY) { m = C + (k - NX); st = NY; v = xt; o = u + (k - NX); }
-        else if (k < 2 * NX + NY) { m = A + (k - NX - NY) * NX; st = 1; v = ln; o = atl + (k - NX - NY); }
-        else if (k < T1) { m = B + (k - 2 * NX - NY) * NX; st = 1; v = ln; o = btl + (k - 2 * NX - NY); }
-        else if (k < T1 + NX) { m = B + (k - T1); st = NX; v = wt; o = dB + (k - T1); len = NW; }
-        else if (k < T1 + NX + NW) { m = R + (k - T1 - NX); st = NR; v = wt; o = ww + (k - T1 - NX); len = NW; }
-        else { m = R + (NW + k - T1 - NX - NW) * NR; st = 1; v = wt; o = sw + (k - T1 - NX - NW); len = NW; }
-        *o = dot_pred<(NX > NW ? NX : NW)>(m, st, v, len, 0.0);
+        int st, len = LP;
+        if (k < T1 * SP) {
+            const int r = k % T1, c = k / T1, j0 = c * LP;
+            o = part + c * T1 + r;
+            if (r < NX) { m = A + r + j0 * NX; st = NX; v = xt + j0; }
+            else if (r < NX + NY) { m = C + (r - NX) + j0 * NY; st = NY; v = xt + j0; }
+            else if (r < 2 * NX + NY) { m = A + (r - NX - NY) * NX + j0; st = 1; v = ln + j0; }
+            else { m = B + (r - 2 * NX - NY) * NX + j0; st = 1; v = ln + j0; }
+        } else {
+            const int q = k - T1 * SP;
+            len = NW;
+            if (q < NX) { m = B + q; st = NX; v = wt; o = dB + q; }
+            else if (q < NX + NW) { m = R + (q - NX); st = NR; v = wt; o = ww + (q - NX); }
+            else { m = R + (NW + q - NX - NW) * NR; st = 1; v = wt; o = sw + (q - NX - NW); }
+        }
+        *o = dot_pred<KM>(m, st, v, len, 0.0);
+    });
+    // the length-n products from their pieces
+    wfor(T1, [&](int r) {
+        double s = part[r];
+#pragma unroll
+        for (int c = 1; c < SP; ++c) s += part[c * T1 + r];
+        if (r < NX) dA[r] = s;
+        else if (r < NX + NY) u[r - NX] = s;
+        else if (r < 2 * NX + NY) atl[r - NX - NY] = s;
+        else btl[r - 2 * NX - NY] = s;
     });
     wfor(NY + NW, [&](int k) {
         const double* m;
