@@ -18,6 +18,7 @@ int shapes_mid(ShapeEntry* out, int cap);
 int shapes_big(ShapeEntry* out, int cap);
 int shapes_sq(ShapeEntry* out, int cap);
 int shapes_xl(ShapeEntry* out, int cap);
+int shapes_n12(ShapeEntry* out, int cap);
 }  // namespace mhe
 
 // CUDA events around each level pass, recorded on the context's stream.
@@ -98,6 +99,7 @@ std::vector<mhe::ShapeEntry>& registry()
         int k = 0;
         k += mhe::shapes_small(buf + k, 32 - k);
         k += mhe::shapes_mid(buf + k, 32 - k);
+        k += mhe::shapes_n12(buf + k, 32 - k);
         k += mhe::shapes_big(buf + k, 32 - k);
         k += mhe::shapes_sq(buf + k, 32 - k);
         k += mhe::shapes_xl(buf + k, 32 - k);

@@ -1,8 +1,9 @@
 // warp.cuh -- the team-cooperative execution layer every tree kernel is written on.
 //
 // A team is MHE_TEAM consecutive threads of a CTA (one warp by default; a
-// translation unit may set MHE_TEAM to 64, 128 or 256 before including this
-// header, for shapes whose per-subproblem work and workspace want more threads).
+// translation unit may set MHE_TEAM before including this header: 8 or 16 for
+// shapes too small to keep a warp busy, several teams then sharing a warp; 64,
+// 128 or 256 for shapes whose per-subproblem work and workspace want more).
 // A kernel body is a sequence of `wfor(count, f)` steps: the team's lanes share
 // the indices 0..count-1 round-robin, and the step ends with the team's
 // barrier (__syncwarp for one warp, a named barrier per team otherwise), so
@@ -20,7 +21,9 @@
 #ifndef MHE_TEAM
 #define MHE_TEAM 32
 #endif
-static_assert(MHE_TEAM == 32 || MHE_TEAM == 64 || MHE_TEAM == 128 || MHE_TEAM == 256, "team of 1, 2, 4 or 8 warps");
+static_assert(MHE_TEAM == 8 || MHE_TEAM == 16 || MHE_TEAM == 32 || MHE_TEAM == 64 || MHE_TEAM == 128 ||
+                  MHE_TEAM == 256,
+              "a team is 8 or 16 lanes of a warp, or 1, 2, 4 or 8 warps");
 
 namespace mhe {
 
@@ -28,11 +31,14 @@ MHE_DEV int lane_id() { return threadIdx.x & (MHE_TEAM - 1); }
 // index of the team within its CTA
 MHE_DEV int team_id() { return threadIdx.x / MHE_TEAM; }
 
-// Barrier of the team's lanes (named barrier team_id + 1 when a team is several warps).
+// Barrier of the team's lanes: __syncwarp over the team's lanes within a warp,
+// a named barrier (team_id + 1) when a team is several warps.
 MHE_DEV void wsync()
 {
 #if MHE_TEAM == 32
     __syncwarp();
+#elif MHE_TEAM < 32
+    __syncwarp(((1u << MHE_TEAM) - 1u) << ((threadIdx.x & 31) & ~(MHE_TEAM - 1)));
 #else
     asm volatile("bar.sync %0, %1;" ::"r"(team_id() + 1), "r"(MHE_TEAM) : "memory");
 #endif
