@@ -108,12 +108,13 @@ MHE_DEV void wgemm_tn(FI&& init, const T* Ab, const T* Bb, T sgn, FO&& out)
             for (int r = 0; r < TM; ++r) ld16(ap[r] + p, av[r]);
 #pragma unroll
             for (int c = 0; c < TN; ++c) ld16(bp[c] + p, bv[c]);
+            // the vector element outermost: consecutive FMAs update different accumulators
 #pragma unroll
-            for (int r = 0; r < TM; ++r)
+            for (int q = 0; q < V; ++q)
 #pragma unroll
-                for (int c = 0; c < TN; ++c)
+                for (int r = 0; r < TM; ++r)
 #pragma unroll
-                    for (int q = 0; q < V; ++q) acc[r][c] += av[r][q] * bv[c][q];
+                    for (int c = 0; c < TN; ++c) acc[r][c] += av[r][q] * bv[c][q];
         }
 #pragma unroll
         for (int p = KV; p < K; ++p)

@@ -52,3 +52,21 @@ def rel_err(sol, ref) -> float:
         den = np.abs(b).max()
         e = max(e, float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max()))
     return e
+
+
+def device_from_pool(n, m, q, pool, idx, x0, device="cuda"):
+    """Stages drawn from a seeded pool (synth.batch_uneven / stage_pool) -> device
+    arrays in the library's layout, expanded on the device by an index gather."""
+    import torch
+    ix = torch.from_numpy(np.asarray(idx, dtype=np.int64)).to(device)
+    d = {}
+    for k in ("A", "B", "C", "R"):
+        p = torch.from_numpy(synth.colmajor(pool[k]).reshape(len(pool[k]), -1)).to(device)
+        d[k] = p.index_select(0, ix).contiguous().reshape(-1)
+    for k in ("a", "yt", "wt"):
+        p = torch.from_numpy(np.ascontiguousarray(pool[k])).to(device)
+        d[k] = p.index_select(0, ix).contiguous().reshape(-1)
+    x0 = np.asarray(x0, dtype=np.float64).reshape(-1, n)
+    d["x0"] = torch.from_numpy(np.ascontiguousarray(x0).reshape(-1)).to(device)
+    d["P0inv"] = torch.eye(n, dtype=torch.float64, device=device).reshape(1, -1).repeat(len(x0), 1).reshape(-1)
+    return d
