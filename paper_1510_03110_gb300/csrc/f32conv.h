@@ -5,17 +5,26 @@
 // issue at a small fraction of the FP32 rate; a conversion done on the integer
 // pipes costs a dozen integer operations instead.  Values whose float result is
 // a normal number take the integer path; zeros, subnormal results, overflow,
-// infinities and NaNs take the hardware conversion.  Host and device code.
+// infinities and NaNs take the hardware conversion, in a function kept out of
+// line so that the compiler branches around it instead of evaluating both sides
+// and selecting.  The widening float -> double is exact and done the same way.
+// Host and device code.
 #pragma once
 #include <string.h>
 
 #ifdef __CUDACC__
 #define MHE_HD __host__ __device__ __forceinline__
+#define MHE_HD_OUTLINE static __host__ __device__ __noinline__
 #else
 #define MHE_HD inline
+#define MHE_HD_OUTLINE static __attribute__((noinline, unused))
 #endif
 
 namespace mhe {
+
+// the rare cases of both conversions, by the hardware
+MHE_HD_OUTLINE float f32_rn_rare(double d) { return (float)d; }
+MHE_HD_OUTLINE double f64_rare(float f) { return (double)f; }
 
 MHE_HD float f32_rn(double d)
 {
@@ -35,7 +44,29 @@ MHE_HD float f32_rn(double d)
         memcpy(&r, &f, sizeof(r));
         return r;
     }
-    return (float)d;
+    return f32_rn_rare(d);
 }
+
+// float -> double, exact: a normal float keeps its sign and fraction and has its
+// exponent rebiased (127 -> 1023); a zero keeps its sign.  Subnormals,
+// infinities and NaNs take the hardware conversion.
+MHE_HD double f64_of(float f)
+{
+    unsigned b;
+    memcpy(&b, &f, sizeof(b));
+    const unsigned ab = b & 0x7FFFFFFFu;
+    if (ab - 0x00800000u < 0x7F000000u || ab == 0u) {
+        // high word: sign | exponent + 896 | top 20 fraction bits; low word: the other 3
+        const unsigned hi = (ab ? (ab >> 3) + 0x38000000u : 0u) | (b & 0x80000000u);
+        const unsigned long long u = ((unsigned long long)hi << 32) | (unsigned long long)(b << 29);
+        double d;
+        memcpy(&d, &u, sizeof(d));
+        return d;
+    }
+    return f64_rare(f);
+}
+
+// widening of a tree value to FP64 (the identity for FP64 trees)
+MHE_HD double f64_of(double d) { return d; }
 
 }  // namespace mhe

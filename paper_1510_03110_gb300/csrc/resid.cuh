@@ -18,6 +18,14 @@
 
 namespace mhe {
 
+// a residual entry in the precision of the correction solve
+template <typename TR>
+MHE_DEV TR to_tr(double v)
+{
+    if constexpr (sizeof(TR) == 4) return f32_rn(v);
+    else return v;
+}
+
 template <int NX, int NW, int NY = 0>
 struct ResidSmem {
     static constexpr int rows = 5 * NX + NW;
@@ -86,7 +94,7 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
             }
             const double li = l ? l[i] : 0.0;
             res = -li - acc;
-            rl[i] = (TR)(li + acc);
+            rl[i] = to_tr<TR>(li + acc);
             zz = (i < NX) ? (abs_bits(xt[i]) > abs_bits(lt[i]) ? abs_bits(xt[i]) : abs_bits(lt[i]))
                           : abs_bits(wt[i - NX]);
             bb = abs_bits(li);
@@ -101,13 +109,13 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
             }
             const double ai = a ? a[ii] : 0.0;
             res = -ai - acc;
-            ra[ii] = (TR)(ai + acc);
+            ra[ii] = to_tr<TR>(ai + acc);
             bb = abs_bits(ai);
         } else if (first && i < NQ + 2 * NX) {
             const int ii = i - NQ - NX;
             const double x0i = r.x0[(long long)b * NX + ii];
             res = x0i - xt[ii];
-            r.rx0[(long long)b * NX + ii] = (TR)res;
+            r.rx0[(long long)b * NX + ii] = to_tr<TR>(res);
             bb = abs_bits(x0i);
         } else {
             // terminal rows with Q_{x,N} = 0, l_N = 0:  -(0 - lambda_N)
@@ -115,7 +123,7 @@ MHE_DEV void resid_rows(const ResidArgs<TR>& r, int b, int t, int N, unsigned lo
             const double* xN = r.x + (gx + N) * NX;
             const double* lamN = r.lam + (gx + N) * NX;
             res = lamN[ii];
-            r.rlN[(long long)b * NX + ii] = (TR)(-res);
+            r.rlN[(long long)b * NX + ii] = to_tr<TR>(-res);
             zz = abs_bits(xN[ii]) > abs_bits(lamN[ii]) ? abs_bits(xN[ii]) : abs_bits(lamN[ii]);
         }
         sr[i] = abs_bits(res);
@@ -268,7 +276,7 @@ MHE_DEV void resid_mhe(const ResidArgs<TR>& r, int b, int t, int N, unsigned lon
             z1 = xN + ii; z2 = lamN + ii; dst = r.rlN + (long long)b * NX + ii;
         }
         const double sum = *p4 + ((*p1 + *p2) - *p3);   // r = -(l + K z) for the stationarity and dynamics rows
-        *dst = (TR)sum;
+        *dst = to_tr<TR>(sum);
         const unsigned long long rr = abs_bits(sum), bb = abs_bits(*p4);
         const unsigned long long za = abs_bits(*z1), zb = abs_bits(*z2);
         const unsigned long long zz = za > zb ? za : zb;
@@ -362,7 +370,7 @@ MHE_DEV void resid_q(const ResidArgs<TR>& r, int b, int t, int N, unsigned long 
             z1 = xN + ii; z2 = lamN + ii; dst = r.rlN + (long long)b * NX + ii;
         }
         const double sum = *p5 + (((*p1 + *p2) + *p3) - *p4);   // r = -(l + K z)
-        *dst = (TR)sum;
+        *dst = to_tr<TR>(sum);
         const unsigned long long rr = abs_bits(sum), bb = abs_bits(*p5);
         const unsigned long long za = abs_bits(*z1), zb = abs_bits(*z2);
         const unsigned long long zz = za > zb ? za : zb;
@@ -554,8 +562,9 @@ template <int NX, int NW, int NY>
 struct PrepSmem {
     static constexpr int NR = NW + NY;
     static constexpr int nd = NY + NW + NY;   // doubles: y~, w~, t = S^T w~ - V y~
-    // floats: C, R, V C, S C, Q_x, A, B, row sums
-    static constexpr int nf = NY * NX + NR * NR + NY * NX + NW * NX + NX * NX + NX * NX + NX * NW + 2 * NX + NW + 1;
+    // floats: C, R, A (later Q_x), B (later V C), S C, row sums
+    static constexpr int nb = NX * NW > NY * NX ? NX * NW : NY * NX;
+    static constexpr int nf = NY * NX + NR * NR + NX * NX + nb + NW * NX + 2 * NX + NW + 1;
     static constexpr int count = nd + (nf + 1) / 2;   // 8-byte words
 };
 
@@ -568,14 +577,16 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
     double* dy = sm;
     double* dw = dy + NY;
     double* dt = dw + NW;
+    // A and B are only read for the row sums of ||K||_inf, taken right after the
+    // load; Q_x and V C then reuse their space (fewer bytes per team, more teams per SM)
     float* fC = reinterpret_cast<float*>(sm + PrepSmem<NX, NW, NY>::nd);
     float* fR = fC + NY * NX;
-    float* fVC = fR + NR * NR;
-    float* fSC = fVC + NY * NX;
-    float* fQx = fSC + NW * NX;
-    float* fA = fQx + NX * NX;
+    float* fA = fR + NR * NR;
+    float* fQx = fA;
     float* fB = fA + NX * NX;
-    float* rsum = fB + NX * NW;
+    float* fVC = fB;
+    float* fSC = fB + PrepSmem<NX, NW, NY>::nb;
+    float* rsum = fSC + NW * NX;
     if (t == 0) {
         // arrival stage: x rows 1 + 1, w rows |P~0^{-1} row| + 1, dynamics rows 3, initial row 1
         const double* P0 = p.P0inv + (long long)b * NX * NX;
@@ -631,6 +642,24 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
             else if (i < O5) dy[i - O4] = v;   // y~ then w~ (contiguous)
             else a32[i - O5] = f;
         });
+    // rows of ||K||_inf, the A and B parts: stationarity rows (a column of A or
+    // B, and -lambda_t) and dynamics rows (a row of A and of B, and -x_{t+1})
+    wfor(NQ + NX, [&](int i) {
+        float rs;
+        if (i < NX) {
+            rs = 1.f;
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[j + i * NX]);
+        } else if (i < NQ) {
+            rs = 0.f;
+            for (int j = 0; j < NX; ++j) rs += mabs(fB[j + (i - NX) * NX]);
+        } else {
+            const int ii = i - NQ;
+            rs = 1.f;
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[ii + j * NX]);
+            for (int j = 0; j < NW; ++j) rs += mabs(fB[ii + j * NX]);
+        }
+        rsum[i] = rs;
+    });
     // FP32: V C and S C;  V(p,q) = R[NW+p + (NW+q) NR], S(k,q) = R[k + (NW+q) NR], W(k,j) = R[k + j NR]
     wgemm<float, NY, NX, NY>([&](int, int) { return 0.f; }, [&](int i, int q) { return fR[NW + i + (NW + q) * NR]; },
                              [&](int q, int j) { return fC[q + j * NY]; },
@@ -675,20 +704,10 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
         return fR[(i - NX) + (j - NX) * NR];
     };
     wfor(NQ * NQ, [&](int idx) { Qo[idx] = qf(idx % NQ, idx / NQ); });
-    // rows of ||K||_inf: stationarity (Q row, A or B column, -lambda_t) and dynamics
-    wfor(NQ + NX, [&](int i) {
-        float rs;
-        if (i < NQ) {
-            rs = (i < NX) ? 1.f : 0.f;
-            for (int j = 0; j < NQ; ++j) rs += mabs(qf(i, j));
-            if (i < NX) for (int j = 0; j < NX; ++j) rs += mabs(fA[j + i * NX]);
-            else for (int j = 0; j < NX; ++j) rs += mabs(fB[j + (i - NX) * NX]);
-        } else {
-            const int ii = i - NQ;
-            rs = 1.f;
-            for (int j = 0; j < NX; ++j) rs += mabs(fA[ii + j * NX]);
-            for (int j = 0; j < NW; ++j) rs += mabs(fB[ii + j * NX]);
-        }
+    // rows of ||K||_inf: the Q part of the stationarity rows
+    wfor(NQ, [&](int i) {
+        float rs = rsum[i];
+        for (int j = 0; j < NQ; ++j) rs += mabs(qf(i, j));
         rsum[i] = rs;
     });
     wone([&](int) {

@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "common.h"
+#include "f32conv.h"
 #include "warp.cuh"
 #include "wgemm.cuh"
 
@@ -739,11 +740,11 @@ MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* xt, con
         if (idx < NX) {
             s.Psi[idx] = s.u[idx];
             lo[idx] = s.u[idx];
-            if (zl) zl[idx] += (double)s.u[idx];
+            if (zl) zl[idx] += f64_of(s.u[idx]);
         } else if (idx < 2 * NX) {
-            zx[idx - NX] += (double)xt[idx - NX];
+            zx[idx - NX] += f64_of(xt[idx - NX]);
         } else {
-            zw[idx - 2 * NX] += (double)wt[idx - 2 * NX];
+            zw[idx - 2 * NX] += f64_of(wt[idx - 2 * NX]);
         }
     });
 }
@@ -821,8 +822,8 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
             xo(t1)[i] = s.e[i];
             lo(t1)[i] = acc;
             if (a.zx) {
-                zxo(t1)[i] += (double)s.e[i];
-                zlo(t1)[i] += (double)acc;
+                zxo(t1)[i] += f64_of(s.e[i]);
+                zlo(t1)[i] += f64_of(acc);
             }
         });
     }

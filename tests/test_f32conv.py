@@ -1,5 +1,6 @@
 """The integer FP64 -> FP32 conversion (csrc/f32conv.h) against IEEE 754
-round-to-nearest-even as numpy implements it, bit for bit.  The header is host
+round-to-nearest-even as numpy implements it, bit for bit, and the exact
+FP32 -> FP64 widening beside it.  The header is host
 and device code; here it is compiled for the host with the system C++ compiler."""
 import ctypes
 import os
@@ -19,6 +20,10 @@ extern "C" void conv(const double* x, float* y, long n)
 {
     for (long i = 0; i < n; ++i) y[i] = mhe::f32_rn(x[i]);
 }
+extern "C" void widen(const float* x, double* y, long n)
+{
+    for (long i = 0; i < n; ++i) y[i] = mhe::f64_of(x[i]);
+}
 '''
 
 
@@ -34,12 +39,20 @@ def conv():
     subprocess.run([cxx, "-O2", "-shared", "-fPIC", "-I", CSRC, src, "-o", so], check=True)
     L = ctypes.CDLL(so)
     L.conv.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long]
+    L.widen.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long]
 
     def f(x):
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.empty(x.size, dtype=np.float32)
         L.conv(x.ctypes.data, y.ctypes.data, x.size)
         return y
+
+    def g(x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.empty(x.size, dtype=np.float64)
+        L.widen(x.ctypes.data, y.ctypes.data, x.size)
+        return y
+    f.widen = g
     yield f
     shutil.rmtree(d, ignore_errors=True)
 
@@ -76,3 +89,17 @@ def test_ties_and_boundaries(conv):
     x = np.array(x, dtype=np.float64)
     with np.errstate(over="ignore"):
         assert _same_bits(conv(x), x.astype(np.float32))
+
+
+def test_widening_is_exact(conv):
+    rng = np.random.default_rng(2)
+    bits = rng.integers(0, 2**32, size=200000, dtype=np.uint64).astype(np.uint32)
+    x = np.concatenate([bits.view(np.float32),
+                        np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan], dtype=np.float32),
+                        np.array([2.0 ** -149, -(2.0 ** -126), 2.0 ** -126 * (1 - 2.0 ** -23)], dtype=np.float32),
+                        np.finfo(np.float32).max.reshape(1)])
+    y = conv.widen(x)
+    with np.errstate(invalid="ignore"):
+        ref = x.astype(np.float64)
+    a, b = y.view(np.uint64), ref.view(np.uint64)
+    assert np.all((a == b) | (np.isnan(y) & np.isnan(ref)))
