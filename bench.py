@@ -517,6 +517,23 @@ def run_serve(args):
                 **out)
 
 
+def pinned_h2d_gbs(nbytes=1 << 31, reps=3):
+    """Host-to-device bandwidth of one pinned 2 GiB copy on this machine (the floor of
+    the end-to-end number: the host link is shared with the machine's other GPUs)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    gbs = nbytes * reps / (time.perf_counter() - t) / 1e9
+    del h, d
+    return round(gbs, 1)
+
+
 def run_e2e(args, buckets, solvers, step, stream, instances):
     """The same step through mhe_estimate_host: the FP64 problem in pinned host
     memory, the solution (x, w, lambda, info) back in pinned host memory, every
@@ -554,16 +571,22 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
 
     e2e_step()
     torch.cuda.synchronize()
+    each = []
     t0 = time.perf_counter()
     for _ in range(k):
+        t1 = time.perf_counter()
         e2e_step()
+        each.append((time.perf_counter() - t1) * 1e3)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / k
     pool.shutdown()
+    gbs = pinned_h2d_gbs()
     infos = np.concatenate([info.numpy().view(mhe.INFO_DTYPE) for _, info in outs])
     del mhe
     return dict(value=round(instances / (ms * 1e-3), 3), unit="KKT solves/s", h2d_bytes_per_step=int(h2d),
                 d2h_bytes_per_step=int(d2h), ms_per_step=round(ms, 3), steps=k, pieces=args.e2e_pieces,
+                ms_each=[round(v, 2) for v in each], h2d_gbs_pinned=gbs,
+                h2d_floor_ms=round(h2d / (gbs * 1e6), 1),
                 relres_max=float(np.max(infos["relres"])), all_ok=bool(np.all(infos["status"] == 0)),
                 api="mhe_estimate_host (pinned host buffers), one caller thread per shape bucket",
                 timer="host wall clock around the synchronous calls")

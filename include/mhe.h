@@ -173,13 +173,13 @@ int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, do
 
 /* mhe_estimate with the problem and the outputs in HOST memory (page-locked
  * memory lets the copies run asynchronously).  The batch is cut into `pieces`
- * runs of consecutive instances with about equal stage counts; two engines on
- * two streams of their own take the pieces in turn, so the host-to-device copy
- * of one piece, the solve of another and the device-to-host copy of a third
- * overlap.  Inputs: an mhe_problem of host pointers, the same layout; outputs
+ * runs of consecutive instances with about equal stage counts; three engines
+ * on three streams of their own take the pieces in turn, so the host-to-device
+ * copies of the next two pieces overlap the solve of one and the device-to-host
+ * copy of the one before.  Inputs: an mhe_problem of host pointers, the same layout; outputs
  * x, w, lam as mhe_solve (host); info [batch] host or NULL.  Synchronous: returns
  * when every output has arrived.  The pipeline's engines and device buffers
- * (about 2/pieces of the whole batch's) are kept by the context for the next
+ * (about 3/pieces of the whole batch's) are kept by the context for the next
  * call and freed by mhe_destroy.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_CUDA. */
 int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info,
                       int pieces);

@@ -45,24 +45,26 @@ struct PassTiming {
     }
 };
 
-// Host-buffer pipeline of mhe_estimate_host: two engines on two streams take
+// Host-buffer pipeline of mhe_estimate_host: three engines on three streams take
 // the pieces of the batch in turn; each has its device copies of a piece's
 // inputs and outputs.
 struct HostPipe {
+    // pieces in flight: the copies of piece k + 1 and k + 2 run while piece k solves
+    static constexpr int NE = 3;
     struct Buf {
         void* p = nullptr;
         size_t bytes = 0;
     };
-    mhe::Engine eng[2];
-    cudaStream_t st[2] = {nullptr, nullptr};
-    cudaEvent_t done[2] = {nullptr, nullptr};
-    bool inited[2] = {false, false};
-    bool used[2] = {false, false};
-    Buf in[2][9];    // A B C R a y~ w~ x~0 P~0^{-1}
-    Buf out[2][3];   // x w lambda
+    mhe::Engine eng[NE];
+    cudaStream_t st[NE] = {};
+    cudaEvent_t done[NE] = {};
+    bool inited[NE] = {};
+    bool used[NE] = {};
+    Buf in[NE][9];    // A B C R a y~ w~ x~0 P~0^{-1}
+    Buf out[NE][3];   // x w lambda
     ~HostPipe()
     {
-        for (int e = 0; e < 2; ++e) {
+        for (int e = 0; e < NE; ++e) {
             if (st[e]) cudaStreamSynchronize(st[e]);
             if (inited[e]) eng[e].release();
             for (auto& b : in[e]) if (b.p) cudaFree(b.p);
@@ -347,7 +349,7 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
     if (!ctx->pipe) {
         HostPipe* hp = new (std::nothrow) HostPipe;
         if (!hp) return fail(MHE_E_NOMEM, "host allocation failed");
-        for (int e = 0; e < 2; ++e)
+        for (int e = 0; e < HostPipe::NE; ++e)
             if (cudaStreamCreateWithFlags(&hp->st[e], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&hp->done[e], cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
@@ -369,7 +371,7 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
     const int R = (m + q) * (m + q);
     int rc = MHE_OK;
     for (size_t k = 0; k + 1 < cut.size() && rc == MHE_OK; ++k) {
-        const int e = (int)(k & 1);
+        const int e = (int)(k % HostPipe::NE);
         const int b0 = cut[k], b1 = cut[k + 1], cnt = b1 - b0;
         if (hp.used[e] && cudaEventSynchronize(hp.done[e]) != cudaSuccess) { rc = MHE_E_CUDA; break; }
         const long long s0 = P.in_off[b0], x0s = P.gs0[b0] + b0, w0 = P.w_off[b0];
@@ -423,7 +425,7 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
         cudaEventRecord(hp.done[e], hp.st[e]);
         hp.used[e] = true;
     }
-    for (int e = 0; e < 2; ++e)
+    for (int e = 0; e < HostPipe::NE; ++e)
         if (cudaStreamSynchronize(hp.st[e]) != cudaSuccess && rc == MHE_OK) rc = MHE_E_CUDA;
     if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
     if (rc == MHE_E_CUDA && g_err.empty()) g_err = "CUDA error in the host-buffer pipeline";
@@ -516,7 +518,7 @@ long long mhe_launch_count(mhe_ctx* ctx)
     if (!ctx) return -1;
     long long l = ctx->eng.launches;
     if (ctx->pipe)
-        for (int e = 0; e < 2; ++e) l += ctx->pipe->inited[e] ? ctx->pipe->eng[e].launches : 0;
+        for (int e = 0; e < HostPipe::NE; ++e) l += ctx->pipe->inited[e] ? ctx->pipe->eng[e].launches : 0;
     return l;
 }
 
