@@ -218,7 +218,8 @@ def peaks():
                 src="measured" if p else "fallback",
                 # ALU peaks from unit counts x clock: 152 SMs x 128 FP32 lanes x 2 flop x clock;
                 # FP64: the part's nominal 1.25 TFLOP/s
-                fp32_tflops=152 * 128 * 2 * sm_max * 1e6 / 1e12, fp64_tflops=1.25)
+                fp32_tflops=152 * 128 * 2 * sm_max * 1e6 / 1e12, fp64_tflops=1.25,
+                bf16_tflops=float(p.get("bf16_tflops", 1900.0)))
 
 
 def read_traffic():
@@ -242,6 +243,13 @@ def run_gpu(args):
     build.build()
     torch.cuda.set_device(0)
     desc, buckets, prec = make_workload(args.workload)
+    # the Solver's precision: MHE_TF32_IR puts the reductions' stage products on the tensor cores
+    sprec = prec
+    if prec == 1 and (args.prec == "tf32" or (args.prec == "auto" and args.workload in ("xl", "xl_profile"))):
+        sprec = mhe.MHE_TF32_IR
+        desc["precision"] = ("FP32 tree (128-thread teams), stage products F, G, H on the tensor cores "
+                             "(tcgen05 kind::tf32, operands split hi + lo, 3 MMAs per product, FP32 accumulation) "
+                             "+ FP64 refinement")
     t0 = time.time()
     for bk in buckets:
         bk["dev"] = to_device(bk)
@@ -263,7 +271,7 @@ def run_gpu(args):
             k = min(len(bk["N"]), args.tune_instances if bk["n"] < 48 else len(bk["N"]))
             S = int(np.sum(bk["N"][:k] - 1))
             n, m = bk["n"], bk["m"]
-            dims, _keep = mhe.make_dims(n, m, bk["N"][:k], prec, 0, 0, 0, refine_tol, max_refine)
+            dims, _keep = mhe.make_dims(n, m, bk["N"][:k], sprec, 0, 0, 0, refine_tol, max_refine)
             Qp = torch.empty(max(S, 1), (n + m) ** 2, dtype=torch.float64, device="cuda")
             lp = torch.empty(max(S, 1), n + m, dtype=torch.float64, device="cuda")
             if S > 0:
@@ -275,7 +283,7 @@ def run_gpu(args):
             del Qp, lp
             plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"])
         plans.append(dict(nx=bk["n"], **plan))
-        s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=prec, refine_tol=refine_tol,
+        s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=sprec, refine_tol=refine_tol,
                        max_refine=max_refine, **plan)
         s.out = s.outputs()
         solvers.append(s)
@@ -328,7 +336,8 @@ def run_gpu(args):
         mhe.mhe_timing_enable(s.ctx, False)
     pk = peaks()
     traffic = read_traffic()
-    kern = {"reduce": "k_level<{t},{n},{m},0,REDUCE>", "rhs": "k_level<{t},{n},{m},0,RHS>",
+    kern = {"reduce": "k_level<{t},{n},{m},0,%s>" % ("REDUCE_TC" if sprec == 2 else "REDUCE"),
+            "rhs": "k_level<{t},{n},{m},0,RHS>",
             "down": "k_level<{t},{n},{m},0,DOWN>", "resid": "k_resid<{n},{m},{t},{y}>",
             "prep": "k_prep<{n},{m},{q}>" if prec == 1 else "k_assemble<{n},{m},{q}>"}
 
@@ -352,10 +361,19 @@ def run_gpu(args):
         tr = traffic.get(tkey)
         name = kern[r["phase"]].format(t="float" if prec == 1 else "double", n=n, m=m, q=q,
                                        y=(q if prec == 1 else 0))
-        return dict(bound=bound, kernel=name, achieved=round(achieved, 3), peak=round(peak, 2), unit=unit,
-                    frac=round(achieved / peak, 4), traffic=(tr * int(np.sum(bk["N"])) if tr else None),
-                    peak_src=src, work_per_launch=work, ms_per_launch=round(full_ms, 4),
-                    launches_per_step=r["calls"], ms_per_step=round(r["ms"], 4))
+        out = dict(bound=bound, kernel=name, achieved=round(achieved, 3), peak=round(peak, 2), unit=unit,
+                   frac=round(achieved / peak, 4), traffic=(tr * int(np.sum(bk["N"])) if tr else None),
+                   peak_src=src, work_per_launch=work, ms_per_launch=round(full_ms, 4),
+                   launches_per_step=r["calls"], ms_per_step=round(r["ms"], 4))
+        if r["phase"] == "reduce" and sprec == 2 and n == 64:
+            # the tensor pipe's view: MMA flops issued per stage (M = 128 rows, three MMAs per
+            # product for the hi/lo split) against TF32 = the measured BF16 peak x 1.1 / 2.25
+            mma = 3 * 2 * 128 * n * (n + (n + m)) * int(np.sum(bk["N"]))
+            tf = pk["bf16_tflops"] * 1.1 / 2.25
+            out["tensor"] = dict(mma_tflop_per_launch=mma / 1e12, achieved=round(mma / 1e12 / (full_ms * 1e-3), 2),
+                                 peak=round(tf, 1), unit="TFLOP/s", frac=round(mma / 1e12 / (full_ms * 1e-3) / tf, 4),
+                                 peak_src="TF32 dense = measured BF16 burst x 1.1 / 2.25 (nominal ratio)")
+        return out
 
     ranked = sorted(passes, key=lambda r: -r["ms"])
     kernels = [x for x in (roof(r) for r in ranked[:6]) if x]
@@ -363,13 +381,15 @@ def run_gpu(args):
 
     # plain serial Riccati on the same GPU: one chunk per instance (top_len >= N)
     base = {}
-    arms = [] if args.no_baseline else [("serial_same_precision", prec, max_refine if prec == 1 else 0)] + \
-        ([("serial_fp64", 0, 0)] if (prec == 1 and args.serial_fp64) else [])
-    for name, bprec, mref in arms:
+    arms = [] if args.no_baseline else [("serial_same_precision", sprec, max_refine if prec == 1 else 0, None)] + \
+        ([("serial_fp64", 0, 0, None)] if (prec == 1 and args.serial_fp64) else []) + \
+        ([("fp32_simt_products_same_plan", 1, max_refine, plans)] if sprec == 2 else [])
+    for name, bprec, mref, bplans in arms:
         ss = []
-        for bk in buckets:
-            s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
-                           top_len=int(np.max(bk["N"])) + 1)
+        for i, bk in enumerate(buckets):
+            bpl = dict(top_len=int(np.max(bk["N"])) + 1) if bplans is None else \
+                {k: v for k, v in bplans[i].items() if k != "nx"}
+            s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref, **bpl)
             s.out = s.outputs()
             ss.append(s)
         step(ss)
@@ -411,7 +431,8 @@ def run_gpu(args):
     p99 = step_sorted[min(len(step_sorted) - 1, int(np.ceil(0.99 * len(step_sorted))) - 1)]
     line = dict(metric=METRIC, value=round(value, 3), unit="KKT solves/s", n_gpus=1, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(ms, 4), higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f32+f64" if prec == 1 else "f64", data="synthetic",
+                vs_baseline=None, dtype=("tf32+f32+f64" if sprec == 2 else "f32+f64") if prec == 1 else "f64",
+                data="synthetic",
                 config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, generation_s=round(gen_s, 1),
                             plans=plans, autotune_s=round(tune_s, 1)),
                 latency_ms=dict(p50=round(statistics.median(step_ms), 4), p99=round(p99, 4),
@@ -685,6 +706,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--tune-instances", type=int, default=256)
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tf32"],
+                    help="tree precision of the FP32 workloads: tf32 = stage products on the tensor cores "
+                         "(MHE_TF32_IR; auto: tf32 for the nx = 64 workloads, fp32 otherwise)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

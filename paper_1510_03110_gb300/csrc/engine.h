@@ -21,6 +21,8 @@ struct ShapeOps {
     void (*rhs64)(const LevelArgs<double>&, int upper, void* stream);
     void (*down64)(const LevelArgs<double>&, int upper, void* stream);
     void (*reduce32)(const LevelArgs<float>&, int upper, void* stream);
+    // the reduction with its stage products on the tensor cores (MHE_TF32_IR), or nullptr
+    void (*reduce32tc)(const LevelArgs<float>&, int upper, void* stream);
     void (*rhs32)(const LevelArgs<float>&, int upper, void* stream);
     void (*down32)(const LevelArgs<float>&, int upper, void* stream);
     void (*resid64)(const ResidArgs<double>&, void* stream);

@@ -11,13 +11,20 @@
 
 namespace mhe {
 
-enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2 };
+// OP_REDUCE_TC: the reduction with the stage products on the tensor cores
+enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2, OP_REDUCE_TC = 3 };
+
+// floats past the workspace of a tensor-core reduction: a 32 KB operand tile,
+// the mbarrier and the TMEM address
+constexpr int kTcExtra = 8192 + 4;
 
 // shared-memory workspace (elements of T) one warp of a pass needs
 template <typename T, int NX, int OP>
 constexpr int op_count()
 {
-    return OP == OP_REDUCE ? Ws<T, NX>::count : (OP == OP_RHS ? Ws<T, NX>::count_rhs : Ws<T, NX>::count_vec);
+    return OP == OP_REDUCE ? Ws<T, NX>::count
+                           : (OP == OP_RHS ? Ws<T, NX>::count_rhs
+                                           : (OP == OP_DOWN ? Ws<T, NX>::count_vec : Ws<T, NX>::count + kTcExtra));
 }
 
 // teams per CTA of at most 256 threads: at most 256 / MHE_TEAM
@@ -51,8 +58,19 @@ constexpr bool level_fits()
 template <typename T, int NX, int OP>
 constexpr int level_min_blocks()
 {
-    return sizeof(T) == 4 ? (NX <= 8 ? 4 : (NX <= 12 ? 3 : (OP == OP_REDUCE ? 1 : 2)))
+    return sizeof(T) == 4 ? (NX <= 8 ? 4 : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP == OP_REDUCE_TC) ? 1 : 2)))
                           : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2));
+}
+
+// shapes whose stage products run on the tensor cores: a team of four warps,
+// one team per CTA, M = 128 >= n + m and 2n rows, K = n a multiple of 16,
+// a 128-row operand tile of at most 32 KB
+template <int NX, int NW>
+constexpr bool tc_shape()
+{
+    return MHE_TEAM == 128 && NX % 16 == 0 && NW % 16 == 0 && NX + NW <= 128 && 2 * NX <= 128 &&
+           128 * NX * 4 <= 32 * 1024 && level_warps<float, NX, OP_REDUCE_TC>() == 1 &&
+           (long long)op_count<float, NX, OP_REDUCE_TC>() * 4 <= 227LL * 1024;
 }
 
 template <typename T, int NX, int NW, int UPPER, int OP>
@@ -65,9 +83,32 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
     if (ci >= a.nchunks) return;   // the whole team leaves together
     if (a.any_active && *a.any_active == 0) return;   // a refinement pass with every instance converged
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)team * op_count<T, NX, OP>();
-    if (OP == OP_REDUCE) reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
-    else if (OP == OP_RHS) rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
-    else down_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    if constexpr (OP == OP_REDUCE_TC) {
+        // one team per CTA: TMEM (all 512 columns; one CTA fits an SM) and the mbarrier are the CTA's
+        static_assert(W == 1 && sizeof(T) == 4, "one FP32 tensor-core team per CTA");
+        float* xbuf = reinterpret_cast<float*>(smem_raw) + Ws<float, NX>::count;
+        uint64_t* mbar = reinterpret_cast<uint64_t*>(xbuf + 8192);
+        uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
+        if (threadIdx.x < 32) tc::tmem_alloc(slot, 512);
+        if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        TcState tcs{*slot, mbar, xbuf, 0u, 1};
+        reduce_chunk<T, NX, NW, UPPER != 0, true>(a, ci, sm, &tcs);
+        // a wait that ran out: give the MMAs of that phase another bounded wait before freeing TMEM
+        if (!tcs.ok) tc::mbar_wait(mbar, tcs.phase, tc::kWaitLimit);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (threadIdx.x < 32) tc::tmem_dealloc(tcs.tbase, 512);
+    } else if (OP == OP_REDUCE) {
+        reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    } else if (OP == OP_RHS) {
+        rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    } else {
+        down_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    }
 }
 
 template <typename T, int NX, int NW, int UPPER, int OP>
@@ -235,6 +276,8 @@ ShapeEntry make_shape()
         e.ops.down64 = nullptr;
     }
     e.ops.reduce32 = &launch_level<float, NX, NW, OP_REDUCE>;
+    if constexpr (tc_shape<NX, NW>()) e.ops.reduce32tc = &launch_level<float, NX, NW, OP_REDUCE_TC>;
+    else e.ops.reduce32tc = nullptr;
     e.ops.rhs32 = &launch_level<float, NX, NW, OP_RHS>;
     e.ops.down32 = &launch_level<float, NX, NW, OP_DOWN>;
     e.ops.resid64 = &launch_resid<NX, NW, double>;

@@ -29,6 +29,7 @@
 
 #include "common.h"
 #include "f32conv.h"
+#include "tc.cuh"
 #include "warp.cuh"
 #include "wgemm.cuh"
 
@@ -156,6 +157,14 @@ struct Acc {
         if (KIND == KIND_UPPER) return (T)(i == j ? 1 : 0);   // square-root master stage
         return s.Qw0[i + j * NX];
     }
+    // entry (i, j) of the stage Hessian [[Q_x, Q_xw], [Q_xw^T, Q_w]], i, j < n + m
+    static MHE_DEV T q(const StageRef<T>& s, int i, int j)
+    {
+        if (KIND == KIND_LEAF) return s.Q[i + j * (NX + MT)];
+        if (i < NX && j < NX) return qx(s, i, j);
+        if (i >= NX && j >= NX) return qw(s, i - NX, j - NX);
+        return (T)0;   // Q_xw = 0 at the arrival and master stages
+    }
     static MHE_DEV T lx(const StageRef<T>& s, int i) { return s.l ? s.l[i] : (T)0; }
     static MHE_DEV T lw(const StageRef<T>& s, int j)
     {
@@ -198,6 +207,11 @@ MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
 {
     static_assert(M <= MHE_TEAM && M <= NX, "one lane per row");
     constexpr int ld = Ws<T, NX>::ld;
+    if constexpr (M <= 32) {
+        // rows in the registers of one warp, columns passed by shuffles
+        team_chol<T, M, INV && sizeof(T) == 4>(Gm, ld, piv_rel, s.sc + 1);
+        return s.sc[1] != 0;
+    }
     wone([&](int) {
         T mx = 0;
         for (int i = 0; i < M; ++i) mx = mmax(mx, mabs(Gm[i + i * ld]));
@@ -311,36 +325,225 @@ MHE_DEV void upper_solve(const Ws<T, NX>& s, FR&& rhs, FG&& get, FP&& put)
 }
 
 
+// ---- the stage products on the tensor cores (tcgen05, kind::tf32) -------------
+//
+// Tensor state of a team whose stage products run on the tensor cores: TMEM
+// base address, the mbarrier the MMAs complete on and the parity of its next
+// phase, a 32 KB shared-memory tile outside the workspace, and whether every
+// wait so far completed within its limit.
+struct TcState {
+    uint32_t tbase;
+    uint64_t* mbar;
+    float* xbuf;
+    uint32_t phase;
+    int ok;
+};
+
+// the team's wait for the MMAs it committed last; a wait that runs out marks the
+// state failed, and no further MMA is issued
+MHE_DEV void tc_team_wait(TcState& t)
+{
+    if (!t.ok) return;
+    if (tc::team_wait(t.mbar, t.phase)) t.phase ^= 1u;
+    else t.ok = 0;
+}
+
+// Both products of Algorithm 1's stage update, with [A | B] the n x (n + m)
+// stage matrix and P = P_{t+1} (symmetric):
+//   X^T = [A | B]^T P                 (M = 128 >= n + m rows, K = n)
+//   [A | B]^T X = [[A^T P A, A^T P B], [B^T P A, B^T P B]]   (M = 128, K = n)
+// then F = Q_x + A^T P A -> s.P, H = Q_xw + A^T P B -> s.H, G = Q_w + B^T P B
+// -> s.G (full blocks, each entry from its own row of the product).  Every operand
+// is split into TF32 hi + lo (lo = x - hi rounded to TF32 again).  The B
+// operands are stored [hi; lo] (hi rows, then lo rows), so one MMA of twice the
+// N gives hi*hi and hi*lo side by side, and a second adds lo*hi to the hi*lo
+// half: hi*hi and the cross terms stay in separate FP32 accumulators, summed
+// when read (the small terms in the large accumulator lose bits to its
+// alignment, in their own they do not: a one-CTA measurement on GB300 gave a
+// max relative error of 2.0e-7 of sum |a b| for K = 64, an FP32 FMA chain
+// 1.8e-7, all three products in one accumulator 5.1e-7).  TMEM columns:
+// [0, 2n) the two halves of X^T, [2n, 2n + 2(n+m)) those of the second product.
+// Operand tiles, canonical K-major (rows of 4 x 16 B core matrices along K = n):
+// [A|B]^T hi in the V and Qw slots, lo in the extra tile; [P hi; P lo] in the PB
+// and H slots; [X^T hi; X^T lo] in PB..G once the first product is done.  The
+// workspace slots used as tiles are free in a stage without V (the serial plan
+// and the last chunk of each level).
+template <int NX, int MT, int KIND>
+MHE_DEV void tc_stage_products(Ws<float, NX>& s, const StageRef<float>& st, TcState& tcs)
+{
+    using X = Acc<float, KIND, NX, MT>;
+    using W = Ws<float, NX>;
+    constexpr int ld = W::ld;
+    constexpr int NAB = NX + MT;
+    constexpr int LBO = 128, SBO = (NX / 4) * 128;
+    constexpr int TILE = 128 * NX * 4;   // bytes of a 128-row operand tile
+    constexpr int C2 = 2 * NX;            // TMEM column of the second product
+    static_assert(MHE_TEAM == 128 && NX > 0, "a tensor-core team is the four warps of one CTA");
+    static_assert(NX % 16 == 0 && NAB % 16 == 0 && NAB <= 128, "MMA shapes M = 128, N = 2n and 2(n + m)");
+    static_assert(2 * W::slot * 4 >= TILE && TILE <= 32 * 1024, "[A|B]^T tiles fit the V, Qw slots and the extra tile");
+    static_assert(4 * W::slot * 4 >= 2 * NAB * NX * 4, "[X^T hi; X^T lo] fits the PB, H, K, G slots");
+    static_assert(C2 + 2 * NAB <= 512, "accumulators within the 512 TMEM columns");
+    char* ABh = reinterpret_cast<char*>(s.V);
+    char* ABl = reinterpret_cast<char*>(tcs.xbuf);
+    char* Ph = reinterpret_cast<char*>(s.PB);
+    char* Pl = Ph + (NX / 8) * SBO;   // row n of the stacked tile
+    char* Xh = reinterpret_cast<char*>(s.PB);
+    char* Xl = Xh + (NAB / 8) * SBO;  // row n + m of the stacked tile
+    auto split_store = [&](char* hi, char* lo, int off, const float (&x)[4]) {
+        float h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            h[i] = tc::tf32_hi(x[i]);
+            l[i] = tc::tf32_hi(x[i] - h[i]);
+        }
+        st16(reinterpret_cast<float*>(hi + off), h);
+        st16(reinterpret_cast<float*>(lo + off), l);
+    };
+    // operands: row r of [A|B]^T is column r of A or B, row r of P is its column r;
+    // each lane loads four 16-byte pieces, then splits and stores them
+    constexpr int UAB = NAB * (NX / 4), UP = NX * (NX / 4);
+    static_assert(UAB % (4 * MHE_TEAM) == 0 && UP % (4 * MHE_TEAM) == 0, "whole batches of four pieces per lane");
+    tc::lanes_publish([&](int lane) {
+#pragma unroll 1
+        for (int u0 = 0; u0 < UAB + UP; u0 += 4 * MHE_TEAM) {
+            float x[4][4];
+            int off[4];
+            const bool ab = u0 < UAB;   // the same for every lane of the batch
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int u = u0 + lane + q * MHE_TEAM;
+                if (ab) {
+                    const int r = u % NAB, kc = u / NAB;
+                    ld16((r < NX ? s.A + r * ld : s.B + (r - NX) * ld) + 4 * kc, x[q]);
+                    off[q] = tc::kmaj_off(r, 4 * kc, LBO, SBO);
+                } else {
+                    const int v = u - UAB, r = v % NX, kc = v / NX;
+                    ld16(s.P + r * ld + 4 * kc, x[q]);
+                    off[q] = tc::kmaj_off(r, 4 * kc, LBO, SBO);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split_store(ab ? ABh : Ph, ab ? ABl : Pl, off[q], x[q]);
+        }
+    });
+    wone([&](int) {
+        if (!tcs.ok) return;
+        tc::fence_after();
+        constexpr uint32_t id2 = tc::idesc_tf32(128, 2 * NX), id1 = tc::idesc_tf32(128, NX);
+#pragma unroll 1
+        for (int k = 0; k < NX / 8; ++k) {
+            const uint64_t ah = tc::sdesc(ABh + 256 * k, LBO, SBO), al = tc::sdesc(ABl + 256 * k, LBO, SBO);
+            const uint64_t b = tc::sdesc(Ph + 256 * k, LBO, SBO);
+            tc::mma_tf32(tcs.tbase, ah, b, id2, k > 0);     // [hi*hi | hi*lo]
+            tc::mma_tf32(tcs.tbase + NX, al, b, id1, true); // + lo*hi
+        }
+        tc::commit(tcs.mbar);
+    });
+    tc_team_wait(tcs);
+    // X^T (TMEM lane r = row r) -> its hi / lo rows
+    tc::lanes_publish([&](int r) {
+#pragma unroll 1
+        for (int c = 0; c < NX; c += 16) {
+            float v[16], w[16];
+            tc::tmem_ld16x2(tcs.tbase, r, c, NX + c, v, w);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += w[i];
+            if (r < NAB) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float x[4] = {v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]};
+                    split_store(Xh, Xl, tc::kmaj_off(r, c + 4 * q, LBO, SBO), x);
+                }
+            }
+        }
+    });
+    wone([&](int) {
+        if (!tcs.ok) return;
+        tc::fence_after();
+        constexpr uint32_t id2 = tc::idesc_tf32(128, 2 * NAB), id1 = tc::idesc_tf32(128, NAB);
+#pragma unroll 1
+        for (int k = 0; k < NX / 8; ++k) {
+            const uint64_t ah = tc::sdesc(ABh + 256 * k, LBO, SBO), al = tc::sdesc(ABl + 256 * k, LBO, SBO);
+            const uint64_t b = tc::sdesc(Xh + 256 * k, LBO, SBO);
+            tc::mma_tf32(tcs.tbase + C2, ah, b, id2, k > 0);
+            tc::mma_tf32(tcs.tbase + C2 + NAB, al, b, id1, true);
+        }
+        tc::commit(tcs.mbar);
+    });
+    tc_team_wait(tcs);
+    // row r of the second product: F and H rows (r < n), G rows (n <= r < n + m),
+    // whole rows; the stage Hessian's entries of the next 16 columns are
+    // requested before this block's accumulator loads and stores.  F is written
+    // in full (the update P = F - Y^T Y that follows reads one triangle and
+    // writes P symmetric), G in full (its Cholesky reads the lower triangle).
+    wlanes([&](int r) {
+        const bool row = r < NAB;   // whole warps
+        float qv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) qv[i] = row ? X::q(st, r, i) : 0.f;
+#pragma unroll 1
+        for (int c = 0; c < NAB; c += 16) {
+            float v[16], w[16];
+            tc::tmem_ld16x2(tcs.tbase, r, C2 + c, C2 + NAB + c, v, w);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = qv[i] + (v[i] + w[i]);
+            if (c + 16 < NAB) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) qv[i] = row ? X::q(st, r, c + 16 + i) : 0.f;
+            }
+            // c is a multiple of 16 and n, n + m are too: a block lies in one of P, H or G
+            if (r < NX) {
+                float* dst = c < NX ? s.P + r + c * ld : s.H + r + (c - NX) * ld;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dst[i * ld] = v[i];
+            } else if (row && c >= NX) {
+                float* dst = s.G + (r - NX) + (c - NX) * ld;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dst[i * ld] = v[i];
+            }
+        }
+        tc::fence_before();
+    });
+}
+
 // One backward stage of Algorithm 4 (or Algorithms 1-2 when want_v is false).
 // On entry s.P = P_{t+1}, s.Psi = Psi_{t+1}, s.V = V_{t+1}, s.v = v_{t+1},
 // s.Qw = partial Q^_w.  Stores P_{t+1}, chol(G_{t+1}), K_{t+1}, k_{t+1},
 // L_{t+1} (nullptr skips a store).  Returns true on a failed pivot.
-template <typename T, int NX, int MT, int KIND>
+template <typename T, int NX, int MT, int KIND, bool TC = false>
 MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout, T* Kout,
-                         T* kout, T* Lout, bool want_v, double piv_rel)
+                         T* kout, T* Lout, bool want_v, double piv_rel, TcState* tcs = nullptr)
 {
     constexpr int ld = Ws<T, NX>::ld;
-    constexpr int NT = NX * (NX + 1) / 2, MTT = MT * (MT + 1) / 2;
     using X = Acc<T, KIND, NX, MT>;
     if (Pout)
         wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
     load_AB<T, NX, MT, KIND>(s, st);
-    // P A -> Tt,  P B -> PB,  u = Psi - P a
-    // (P is symmetric: row i of P is column i, read along the inner dimension)
-    wgemm_tn<T, NX, NX, NX, ld, ld>([&](int, int) { return (T)0; }, s.P, s.A, (T)1,
-                                    [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
-    wgemm_tn<T, NX, MT, NX, ld, ld>([&](int, int) { return (T)0; }, s.P, s.B, (T)1,
-                                    [&](int i, int j, T v) { s.PB[i + j * ld] = v; });
-    wgemm_tn<T, NX, 1, NX, ld, 0>([&](int i, int) { return s.Psi[i]; }, s.P, s.e, (T)-1,
-                                  [&](int i, int, T v) { s.u[i] = v; });
-    // F = Q_x + A^T P A -> P (symmetric),  G = Q_w + B^T P B (symmetric),  H = Q_xw + A^T P B,
+    bool on_tc = false;
+    if constexpr (TC) on_tc = !want_v;
+    if (on_tc) {
+        // u = Psi - P a, then F, G, H on the tensor cores (P is overwritten by F)
+        wgemm_tn<T, NX, 1, NX, ld, 0>([&](int i, int) { return s.Psi[i]; }, s.P, s.e, (T)-1,
+                                      [&](int i, int, T v) { s.u[i] = v; });
+        if constexpr (TC) tc_stage_products<NX, MT, KIND>(s, st, *tcs);
+    } else {
+        // P A -> Tt,  P B -> PB,  u = Psi - P a
+        // (P is symmetric: row i of P is column i, read along the inner dimension)
+        wgemm_tn<T, NX, NX, NX, ld, ld>([&](int, int) { return (T)0; }, s.P, s.A, (T)1,
+                                        [&](int i, int j, T v) { s.Tt[i + j * ld] = v; });
+        wgemm_tn<T, NX, MT, NX, ld, ld>([&](int, int) { return (T)0; }, s.P, s.B, (T)1,
+                                        [&](int i, int j, T v) { s.PB[i + j * ld] = v; });
+        wgemm_tn<T, NX, 1, NX, ld, 0>([&](int i, int) { return s.Psi[i]; }, s.P, s.e, (T)-1,
+                                      [&](int i, int, T v) { s.u[i] = v; });
+        // F = Q_x + A^T P A -> P (symmetric),  G = Q_w + B^T P B (symmetric),  H = Q_xw + A^T P B
+        wgemm_tn<T, NX, NX, NX, ld, ld, true>([&](int i, int j) { return X::qx(st, i, j); }, s.A, s.Tt, (T)1,
+                                              [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
+        wgemm_tn<T, MT, MT, NX, ld, ld, true>([&](int i, int j) { return X::qw(st, i, j); }, s.B, s.PB, (T)1,
+                                              [&](int i, int j, T v) { s.G[i + j * ld] = v; s.G[j + i * ld] = v; });
+        wgemm_tn<T, NX, MT, NX, ld, ld>([&](int i, int j) { return X::qxw(st, i, j); }, s.A, s.PB, (T)1,
+                                        [&](int i, int j, T v) { s.H[i + j * ld] = v; });
+    }
     // g = B^T u - l_w,  tv = A^T u
-    wgemm_tn<T, NX, NX, NX, ld, ld, true>([&](int i, int j) { return X::qx(st, i, j); }, s.A, s.Tt, (T)1,
-                                          [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
-    wgemm_tn<T, MT, MT, NX, ld, ld, true>([&](int i, int j) { return X::qw(st, i, j); }, s.B, s.PB, (T)1,
-                                          [&](int i, int j, T v) { s.G[i + j * ld] = v; s.G[j + i * ld] = v; });
-    wgemm_tn<T, NX, MT, NX, ld, ld>([&](int i, int j) { return X::qxw(st, i, j); }, s.A, s.PB, (T)1,
-                                    [&](int i, int j, T v) { s.H[i + j * ld] = v; });
     wgemm_tn<T, MT, 1, NX, ld, 0>([&](int j, int) { return -X::lw(st, j); }, s.B, s.u, (T)1,
                                   [&](int j, int, T v) { s.g[j] = v; });
     wgemm_tn<T, NX, 1, NX, ld, 0>([&](int, int) { return (T)0; }, s.A, s.u, (T)1,
@@ -481,8 +684,8 @@ MHE_DEV void prefetch_factors(const LevelArgs<T>& a, long long g)
 
 // ---- Algorithm 4 over one chunk ----------------------------------------------
 
-template <typename T, int NX, int NW, bool UPPER>
-MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
+template <typename T, int NX, int NW, bool UPPER, bool TC = false>
+MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem, TcState* tcs = nullptr)
 {
     constexpr int ld = Ws<T, NX>::ld;
     const ChunkDesc cd = a.chunks[ci];
@@ -512,20 +715,20 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
         if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1);   // the next stage of the sweep
         bool bad;
         if (UPPER) {
-            bad = reduce_step<T, NX, NX, KIND_UPPER>(
+            bad = reduce_step<T, NX, NX, KIND_UPPER, TC>(
                 s, Addr<T, NX, NW>::upper(a, g), a.store_P ? a.Pst + g * NX * NX : nullptr,
                 a.Lgst + g * NX * NX, a.Kst + g * NX * NX, a.kst + g * NX,
-                last ? nullptr : a.Lst + g * NX * NX, !last, a.piv_rel);
+                last ? nullptr : a.Lst + g * NX * NX, !last, a.piv_rel, tcs);
         } else if (t == 0) {
-            bad = reduce_step<T, NX, NX, KIND_ARRIVAL>(
+            bad = reduce_step<T, NX, NX, KIND_ARRIVAL, TC>(
                 s, Addr<T, NX, NW>::arrival(a, b), a.store_P ? a.Pst0 + (long long)b * NX * NX : nullptr,
                 a.Lgst0 + (long long)b * NX * NX, a.Kst0 + (long long)b * NX * NX, a.kst0 + (long long)b * NX,
-                last ? nullptr : a.Lst0 + (long long)b * NX * NX, !last, a.piv_rel);
+                last ? nullptr : a.Lst0 + (long long)b * NX * NX, !last, a.piv_rel, tcs);
         } else {
-            bad = reduce_step<T, NX, NW, KIND_LEAF>(
+            bad = reduce_step<T, NX, NW, KIND_LEAF, TC>(
                 s, Addr<T, NX, NW>::leaf(a, b, t), a.store_P ? a.Pst + g * NX * NX : nullptr,
                 a.Lgst + g * NW * NW, a.Kst + g * NW * NX, a.kst + g * NW,
-                last ? nullptr : a.Lst + g * NW * NX, !last, a.piv_rel);
+                last ? nullptr : a.Lst + g * NW * NX, !last, a.piv_rel, tcs);
         }
         if (bad && bad_t < 0) bad_t = t;
     }
@@ -552,6 +755,10 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem)
             a.QN_up[(long long)b * NX * NX + idx] = s.P[idx % NX + (idx / NX) * ld];
             if (idx < NX) a.lN_up[(long long)b * NX + idx] = -s.Psi[idx];
         });
+    }
+    if constexpr (TC) {
+        // a tensor-core wait that ran out: the products after it are not valid
+        if (!tcs->ok) wone([&](int) { record_error(a.status, a.where, b, -7, a.level, ci, cd.t0); });
     }
     if (bad_t >= 0) wone([&](int) { record_error(a.status, a.where, b, -3, a.level, ci, bad_t); });
 }

@@ -115,6 +115,11 @@ MHE_DEV void ld16(const double* p, double (&v)[2])
     v[0] = q.x; v[1] = q.y;
 }
 
+// One 16-byte shared-memory store of 4 floats (p 16-byte aligned).
+MHE_DEV void st16(float* p, const float (&v)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
 MHE_DEV double msqrt(double v) { return sqrt(v); }
 MHE_DEV float msqrt(float v) { return sqrtf(v); }
 MHE_DEV double mabs(double v) { return fabs(v); }
@@ -163,6 +168,66 @@ MHE_DEV void atomic_max_nonneg(double* addr, double v)
     if (!(v >= 0.0)) v = __longlong_as_double(0x7ff8000000000000LL);   // NaN: keep it visible
     atomicMax(reinterpret_cast<unsigned long long*>(addr),
               static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// In-place Cholesky G = L L^T of the M x M matrix at Gm (lower triangle read
+// and written, leading dimension ld), M <= 32: one row per lane of the team's
+// first warp (or of the team, when it is narrower), the row held in registers,
+// and the entries of the current column passed between lanes by shuffles, so
+// a column costs no barrier.  Column j: the pivot d = G_jj (row j's register
+// j), L_jj = sqrt(d); L_ij = G_ij / L_jj for the rows below; then every row i
+// subtracts L_ij L_cj from its entries c = j+1..i.  A pivot that is not above
+// piv_rel * max_i |G_ii| is replaced by 1 and reported: *flag = 1 (else 0),
+// written by lane 0 before the closing team barrier.  INV stores 1 / L_jj on
+// the diagonal and multiplies by it (FP32); otherwise L_jj is stored and the
+// column divided (FP64).
+template <typename T, int M, bool INV>
+MHE_DEV void team_chol(T* Gm, int ld, double piv_rel, T* flag)
+{
+    constexpr int CW = MHE_TEAM < 32 ? MHE_TEAM : 32;
+    static_assert(M >= 1 && M <= CW, "one row per lane of one warp");
+    const int i = lane_id();
+    if (i < CW) {
+        const unsigned mask =
+            CW == 32 ? 0xffffffffu : (((1u << CW) - 1u) << ((threadIdx.x & 31) & ~(CW - 1)));
+        T g[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) g[c] = (i < M && c <= i) ? Gm[i + c * ld] : (T)0;
+        T mx = i < M ? mabs(Gm[i + i * ld]) : (T)0;
+#pragma unroll
+        for (int o = CW / 2; o > 0; o >>= 1) mx = mmax(mx, __shfl_xor_sync(mask, mx, o, CW));
+        const T thr = (T)(piv_rel * (double)mx);
+        int bad = 0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            T d = __shfl_sync(mask, g[j], j, CW);
+            if (!(d > thr)) {
+                bad = 1;
+                d = (T)1;
+            }
+            const T l = msqrt(d);
+            T lij;
+            if constexpr (INV) {
+                const T inv = (T)1 / l;
+                lij = g[j] * inv;
+                if (i == j) g[j] = inv;
+            } else {
+                lij = g[j] / l;
+                if (i == j) g[j] = l;
+            }
+            const T lv = i > j ? lij : (T)0;
+            if (i > j) g[j] = lij;
+#pragma unroll
+            for (int c = j + 1; c < M; ++c) g[c] -= lv * __shfl_sync(mask, lv, c, CW);
+        }
+        if (i < M) {
+#pragma unroll
+            for (int c = 0; c < M; ++c)
+                if (c <= i) Gm[i + c * ld] = g[c];
+        }
+        if (i == 0) *flag = (T)bad;
+    }
+    wsync();
 }
 
 }  // namespace mhe

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (mhe_estimate with the same plans; FP32 tree + FP64 refinement for the
-batched and nx=64 workloads, FP64 for the long horizon).  With the bench's
+batched and nx=64 workloads, the nx=64 stage products also on the tensor
+cores, FP64 for the long horizon).  With the bench's
 refinement tolerance (relres <= 1e-9): every instance's status and relative
 KKT residual, a property that holds at any size.  Sampled instances are
 compared with the FP64 oracle solved one by one after refining to relres <=
@@ -64,8 +65,11 @@ def test_long_horizon_nx20_N131072_full_size():
     _check_sample(sols, info, 0, p, 1e-10)
 
 
-def test_nx64_256_instances_full_size():
-    """256 instances of nx=64, nw=ny=32, N=1024 (the serial plan the autotuner picks)."""
+@pytest.mark.parametrize("prec", [mhe.MHE_TF32_IR, mhe.MHE_FP32_IR])
+def test_nx64_256_instances_full_size(prec):
+    """256 instances of nx=64, nw=ny=32, N=1024 (the serial plan the autotuner
+    picks), with the stage products on the tensor cores (the bench's default for
+    this workload) and in FP32 on the CUDA cores."""
     rng = np.random.default_rng(5)
     count, N, n, m = 256, 1024, 64, 32
     pool = synth.stage_pool(np.random.default_rng([5, n]), n, m, m, 2048)
@@ -73,10 +77,10 @@ def test_nx64_256_instances_full_size():
     x0 = rng.standard_normal((count, n))
     d = device_from_pool(n, m, m, pool, idx, x0)
     plan = dict(leaf_len=64, branching=4, top_len=N + 1)
-    sols, info = _estimate(n, m, m, [N] * count, d, mhe.MHE_FP32_IR, 1e-9, 16, plan)
+    sols, info = _estimate(n, m, m, [N] * count, d, prec, 1e-9, 16, plan)
     assert np.all(info["status"] == 0)
     assert np.max(info["relres"]) <= 1e-9
-    sols, info = _estimate(n, m, m, [N] * count, d, mhe.MHE_FP32_IR, 1e-12, 24, plan)
+    sols, info = _estimate(n, m, m, [N] * count, d, prec, 1e-12, 24, plan)
     assert np.all(info["status"] == 0)
     assert np.max(info["relres"]) <= 1e-12
     for j in (0, 137):
