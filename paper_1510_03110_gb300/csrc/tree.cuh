@@ -660,17 +660,28 @@ struct Addr {
     }
 };
 
-// L2 prefetch of the blocks of level-0 stage t of instance b (t >= 1)
+// L2 prefetch of the blocks of level-0 stage t of instance b (t >= 1) a pass
+// reads: PF_A, PF_B, PF_Q, PF_L (l) and PF_AV (a) select them
+enum { PF_A = 1, PF_B = 2, PF_Q = 4, PF_L = 8, PF_AV = 16, PF_ALL = 31 };
 template <typename T, int NX, int NW>
-MHE_DEV void prefetch_leaf(const LevelArgs<T>& a, int b, int t)
+MHE_DEV void prefetch_leaf(const LevelArgs<T>& a, int b, int t, int what = PF_ALL)
 {
     if (t < 1) return;
     const long long s = a.in_off[b] + t - 1;
-    prefetch_l2(a.A + s * NX * NX, (int)(sizeof(T) * NX * NX));
-    prefetch_l2(a.B + s * NX * NW, (int)(sizeof(T) * NX * NW));
-    prefetch_l2(a.Q + s * (NX + NW) * (NX + NW), (int)(sizeof(T) * (NX + NW) * (NX + NW)));
-    if (a.l) prefetch_l2(a.l + (a.rhs_off[b] + t - 1) * (NX + NW), (int)(sizeof(T) * (NX + NW)));
-    if (a.a) prefetch_l2(a.a + (a.rhs_off[b] + t - 1) * NX, (int)(sizeof(T) * NX));
+    if (what & PF_A) prefetch_l2(a.A + s * NX * NX, (int)(sizeof(T) * NX * NX));
+    if (what & PF_B) prefetch_l2(a.B + s * NX * NW, (int)(sizeof(T) * NX * NW));
+    if (what & PF_Q) prefetch_l2(a.Q + s * (NX + NW) * (NX + NW), (int)(sizeof(T) * (NX + NW) * (NX + NW)));
+    if ((what & PF_L) && a.l) prefetch_l2(a.l + (a.rhs_off[b] + t - 1) * (NX + NW), (int)(sizeof(T) * (NX + NW)));
+    if ((what & PF_AV) && a.a) prefetch_l2(a.a + (a.rhs_off[b] + t - 1) * NX, (int)(sizeof(T) * NX));
+}
+
+// the stored factors P, chol(G), K of level-0 stage g (right-hand-side pass), into L2
+template <typename T, int NX, int NW>
+MHE_DEV void prefetch_rhs_factors(const LevelArgs<T>& a, long long g)
+{
+    prefetch_l2(a.Pst + g * NX * NX, (int)(sizeof(T) * NX * NX));
+    prefetch_l2(a.Lgst + g * NW * NW, (int)(sizeof(T) * NW * NW));
+    prefetch_l2(a.Kst + g * NW * NX, (int)(sizeof(T) * NW * NX));
 }
 
 // the stored factors K, k, L of level-0 stage g (down pass), into L2
@@ -848,11 +859,18 @@ MHE_DEV void rhs_chunk(const LevelArgs<T>& a, int ci, T* smem)
     const T* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr)
                         : (a.lN ? a.lN + (long long)b * NX : nullptr);
     wfor(NX, [&](int i) { s.Psi[i] = (last && lN) ? -lN[i] : (T)0; });
-    if (!UPPER) prefetch_leaf<T, NX, NW>(a, b, cd.t0 + cd.len - 1);
+    if (!UPPER && cd.t0 + cd.len - 1 >= 1) {
+        prefetch_leaf<T, NX, NW>(a, b, cd.t0 + cd.len - 1, PF_A | PF_B | PF_L | PF_AV);
+        prefetch_rhs_factors<T, NX, NW>(a, cd.g0 + cd.len - 1);
+    }
     for (int tt = cd.len - 1; tt >= 0; --tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
-        if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1);
+        if (!UPPER && t - 1 >= 1 && tt > 0) {
+            // the next stage of the sweep: its blocks and stored factors
+            prefetch_leaf<T, NX, NW>(a, b, t - 1, PF_A | PF_B | PF_L | PF_AV);
+            prefetch_rhs_factors<T, NX, NW>(a, g - 1);
+        }
         if (UPPER) {
             rhs_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), a.Pst + g * NX * NX,
                                             a.Lgst + g * NX * NX, a.Kst + g * NX * NX, a.kst + g * NX);
@@ -999,7 +1017,7 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
         if (!UPPER && tt + 1 < cd.len) {   // the next stage's data and factors, into L2
-            prefetch_leaf<T, NX, NW>(a, b, t + 1);
+            prefetch_leaf<T, NX, NW>(a, b, t + 1, PF_A | PF_B | PF_AV);
             prefetch_factors<T, NX, NW>(a, g + 1);
         }
         if (UPPER)
@@ -1037,7 +1055,7 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     for (int tt = cd.len - 1; tt >= 0; --tt) {
         const int t = cd.t0 + tt;
         const long long g = cd.g0 + tt;
-        if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1);
+        if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1, PF_A | PF_Q | PF_L);
         if (UPPER)
             down_bwd_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), xo(t), wo(t), lo(t),
                                                  zxo(t), zwo(t), zlo(t));

@@ -121,6 +121,8 @@ MHE_DEV void st16(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 MHE_DEV double msqrt(double v) { return sqrt(v); }
+MHE_DEV float mrsqrt(float v) { return rsqrtf(v); }
+MHE_DEV double mrsqrt(double v) { return 1.0 / sqrt(v); }
 MHE_DEV float msqrt(float v) { return sqrtf(v); }
 MHE_DEV double mabs(double v) { return fabs(v); }
 MHE_DEV float mabs(float v) { return fabsf(v); }
@@ -179,8 +181,8 @@ MHE_DEV void atomic_max_nonneg(double* addr, double v)
 // subtracts L_ij L_cj from its entries c = j+1..i.  A pivot that is not above
 // piv_rel * max_i |G_ii| is replaced by 1 and reported: *flag = 1 (else 0),
 // written by lane 0 before the closing team barrier.  INV stores 1 / L_jj on
-// the diagonal and multiplies by it (FP32); otherwise L_jj is stored and the
-// column divided (FP64).
+// the diagonal and multiplies by it, 1 / L_jj from the reciprocal square root
+// of the pivot (FP32); otherwise L_jj is stored and the column divided (FP64).
 template <typename T, int M, bool INV>
 MHE_DEV void team_chol(T* Gm, int ld, double piv_rel, T* flag)
 {
@@ -205,13 +207,13 @@ MHE_DEV void team_chol(T* Gm, int ld, double piv_rel, T* flag)
                 bad = 1;
                 d = (T)1;
             }
-            const T l = msqrt(d);
             T lij;
             if constexpr (INV) {
-                const T inv = (T)1 / l;
+                const T inv = mrsqrt(d);   // 1 / L_jj in one step (the refinement absorbs its rounding)
                 lij = g[j] * inv;
                 if (i == j) g[j] = inv;
             } else {
+                const T l = msqrt(d);
                 lij = g[j] / l;
                 if (i == j) g[j] = l;
             }
