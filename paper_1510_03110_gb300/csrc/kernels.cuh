@@ -54,12 +54,15 @@ constexpr bool level_fits()
 // CTAs of 256 threads per SM the register allocation is sized for: the small
 // shapes' workspaces are small, so their occupancy is set by registers (64 or
 // 80 per thread keep 32 or 24 warps per SM); the n = 24 reduction keeps its
-// 255 registers (shared memory allows one CTA anyway), its vector passes 128.
+// 255 registers (shared memory allows one CTA anyway), its vector passes 128;
+// the n = 64 passes (one four-warp team per subproblem, a few hundred teams)
+// all take 255.
 template <typename T, int NX, int OP>
 constexpr int level_min_blocks()
 {
-    return sizeof(T) == 4 ? (NX <= 8 ? 4 : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP == OP_REDUCE_TC) ? 1 : 2)))
-                          : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2));
+    return NX >= 48 ? 1   // four-warp teams, a few per SM: every pass may take 255 registers
+                    : (sizeof(T) == 4 ? (NX <= 8 ? 4 : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP == OP_REDUCE_TC) ? 1 : 2)))
+                                      : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2)));
 }
 
 // shapes whose stage products run on the tensor cores: a team of four warps,

@@ -775,6 +775,10 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem, TcState* tcs =
 }
 
 // ---- the vector part of Algorithm 4 with stored factors -----------------------
+//
+// The dot products of this pass and of the down pass read their matrix from
+// global memory (L2 after the prefetch); their loops are unrolled in full so a
+// lane has all its loads in flight at once instead of a round trip per eight.
 
 template <typename T, int NX, int MT, int KIND>
 MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Pin, const T* Lgin,
@@ -787,7 +791,7 @@ MHE_DEV void rhs_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Pin, const T
     wcopy<MT * NX>([&](int idx) { return Kin[idx]; }, [&](int idx, T v) { s.K[idx % MT + (idx / MT) * ld] = v; });
     wfor(NX, [&](int i) {
         T acc = s.Psi[i];
-#pragma unroll 8
+#pragma unroll
         for (int p = 0; p < NX; ++p) acc -= Pin[i + p * NX] * s.e[p];
         s.u[i] = acc;
     });
@@ -831,15 +835,15 @@ MHE_DEV void closed_loop_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin,
     using X = Acc<T, KIND, NX, MT>;
     wfor(MT, [&](int j) {
         T acc = kin[j];
-#pragma unroll 8
+#pragma unroll
         for (int i = 0; i < NX; ++i) acc += Kin[j + i * MT] * s.e[i];
         s.tmp[j] = acc;
     });
     wfor(NX, [&](int i) {
         T acc = X::a(st, i);
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < NX; ++j) acc += X::A(st, i, j) * s.e[j];
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < MT; ++j) acc += X::B(st, i, j) * s.tmp[j];
         s.u[i] = acc;
     });
@@ -921,10 +925,10 @@ MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin, co
         if (idx < MT) {
             const int j = idx;
             T acc = kin[j];
-#pragma unroll 8
+#pragma unroll
             for (int i = 0; i < NX; ++i) acc += Kin[j + i * MT] * s.e[i];
             if (use_wh) {
-#pragma unroll 8
+#pragma unroll
                 for (int i = 0; i < NX; ++i) acc -= Lin[j + i * MT] * s.v[i];
             }
             s.tmp[j] = acc;
@@ -935,9 +939,9 @@ MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin, co
     });
     wfor(NX, [&](int i) {
         T acc = X::a(st, i);
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < NX; ++j) acc += X::A(st, i, j) * s.e[j];
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < MT; ++j) acc += X::B(st, i, j) * s.tmp[j];
         s.u[i] = acc;
     });
@@ -953,11 +957,11 @@ MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* xt, con
     using X = Acc<T, KIND, NX, MT>;
     wfor(NX, [&](int i) {
         T acc = X::lx(st, i);
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < NX; ++j) acc += X::qx(st, i, j) * xt[j];
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < MT; ++j) acc += X::qxw(st, i, j) * wt[j];
-#pragma unroll 8
+#pragma unroll
         for (int j = 0; j < NX; ++j) acc += X::A(st, j, i) * s.Psi[j];
         s.u[i] = acc;
     });
@@ -1040,7 +1044,7 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
         wfor(NX, [&](int i) {
             T acc = lN ? lN[i] : (T)0;
             if (QN) {
-#pragma unroll 8
+#pragma unroll
                 for (int j = 0; j < NX; ++j) acc += QN[i + j * NX] * s.e[j];
             }
             s.Psi[i] = acc;
