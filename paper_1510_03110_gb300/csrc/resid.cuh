@@ -561,41 +561,53 @@ MHE_DEV void assemble_stage(const double* C, const double* R, const double* yt, 
 template <int NX, int NW, int NY>
 struct PrepSmem {
     static constexpr int NR = NW + NY;
+    // odd leading dimensions: the lanes of a product tile or a row sum read
+    // down a column or along a row of these blocks without bank conflicts
+    static constexpr int odd(int n) { return n | 1; }
+    static constexpr int LC = odd(NY), LR = odd(NR), LA = odd(NX), LS = odd(NW);
     static constexpr int nd = NY + NW + NY;   // doubles: y~, w~, t = S^T w~ - V y~
     // floats: C, R, A (later Q_x), B (later V C), S C, row sums
-    static constexpr int nb = NX * NW > NY * NX ? NX * NW : NY * NX;
-    static constexpr int nf = NY * NX + NR * NR + NX * NX + nb + NW * NX + 2 * NX + NW + 1;
+    static constexpr int nb = LA * NW > LC * NX ? LA * NW : LC * NX;
+    static constexpr int nf = LC * NX + LR * NR + LA * NX + nb + LS * NX + 2 * NX + NW + 1;
     static constexpr int count = nd + (nf + 1) / 2;   // 8-byte words
 };
 
 template <int NX, int NW, int NY>
 MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
 {
+    using PS = PrepSmem<NX, NW, NY>;
     constexpr int NR = NW + NY, NQ = NX + NW;
+    constexpr int LC = PS::LC, LR = PS::LR, LA = PS::LA, LS = PS::LS;
     const int b = stage_instance(p.gs0, p.batch, gstage);
     const int t = (int)(gstage - p.gs0[b]);
     double* dy = sm;
     double* dw = dy + NY;
     double* dt = dw + NW;
     // A and B are only read for the row sums of ||K||_inf, taken right after the
-    // load; Q_x and V C then reuse their space (fewer bytes per team, more teams per SM)
-    float* fC = reinterpret_cast<float*>(sm + PrepSmem<NX, NW, NY>::nd);
-    float* fR = fC + NY * NX;
-    float* fA = fR + NR * NR;
+    // load; Q_x and V C then reuse their space (fewer bytes per team, more teams per SM).
+    // Blocks column-major with the padded leading dimensions LC (C, V C), LR (R),
+    // LA (A, Q_x, B), LS (S C).
+    float* fC = reinterpret_cast<float*>(sm + PS::nd);
+    float* fR = fC + LC * NX;
+    float* fA = fR + LR * NR;
     float* fQx = fA;
-    float* fB = fA + NX * NX;
+    float* fB = fA + LA * NX;
     float* fVC = fB;
-    float* fSC = fB + PrepSmem<NX, NW, NY>::nb;
-    float* rsum = fSC + NW * NX;
+    float* fSC = fB + PS::nb;
+    float* rsum = fSC + LS * NX;
     if (t == 0) {
         // arrival stage: x rows 1 + 1, w rows |P~0^{-1} row| + 1, dynamics rows 3, initial row 1
         const double* P0 = p.P0inv + (long long)b * NX * NX;
         float* P0f = p.P0_32 + (long long)b * NX * NX;
-        wcopy<NX * NX>([&](int i) { return P0[i]; }, [&](int i, double v) { P0f[i] = f32_rn(v); fA[i] = f32_rn(v); });
+        wcopy<NX * NX>([&](int i) { return P0[i]; }, [&](int i, double v) {
+            const float f = f32_rn(v);
+            P0f[i] = f;
+            fA[i % NX + (i / NX) * LA] = f;
+        });
         wfor(NX, [&](int i) {
             p.x0_32[(long long)b * NX + i] = f32_rn(p.x0[(long long)b * NX + i]);
             float rs = 1.f;
-            for (int j = 0; j < NX; ++j) rs += mabs(fA[i + j * NX]);
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[i + j * LA]);
             rsum[i] = rs > 3.f ? rs : 3.f;
         });
         wone([&](int) {
@@ -635,12 +647,24 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
         },
         [&](int i, double v) {
             const float f = f32_rn(v);
-            if (i < O1) fC[i] = f;
-            else if (i < O2) fR[i - O1] = f;
-            else if (i < O3) { A32[i - O2] = f; fA[i - O2] = f; }
-            else if (i < O4) { B32[i - O3] = f; fB[i - O3] = f; }
-            else if (i < O5) dy[i - O4] = v;   // y~ then w~ (contiguous)
-            else a32[i - O5] = f;
+            if (i < O1) {
+                fC[i % NY + (i / NY) * LC] = f;
+            } else if (i < O2) {
+                const int k = i - O1;
+                fR[k % NR + (k / NR) * LR] = f;
+            } else if (i < O3) {
+                const int k = i - O2;
+                A32[k] = f;
+                fA[k % NX + (k / NX) * LA] = f;
+            } else if (i < O4) {
+                const int k = i - O3;
+                B32[k] = f;
+                fB[k % NX + (k / NX) * LA] = f;
+            } else if (i < O5) {
+                dy[i - O4] = v;   // y~ then w~ (contiguous)
+            } else {
+                a32[i - O5] = f;
+            }
         });
     // rows of ||K||_inf, the A and B parts: stationarity rows (a column of A or
     // B, and -lambda_t) and dynamics rows (a row of A and of B, and -x_{t+1})
@@ -648,25 +672,25 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
         float rs;
         if (i < NX) {
             rs = 1.f;
-            for (int j = 0; j < NX; ++j) rs += mabs(fA[j + i * NX]);
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[j + i * LA]);
         } else if (i < NQ) {
             rs = 0.f;
-            for (int j = 0; j < NX; ++j) rs += mabs(fB[j + (i - NX) * NX]);
+            for (int j = 0; j < NX; ++j) rs += mabs(fB[j + (i - NX) * LA]);
         } else {
             const int ii = i - NQ;
             rs = 1.f;
-            for (int j = 0; j < NX; ++j) rs += mabs(fA[ii + j * NX]);
-            for (int j = 0; j < NW; ++j) rs += mabs(fB[ii + j * NX]);
+            for (int j = 0; j < NX; ++j) rs += mabs(fA[ii + j * LA]);
+            for (int j = 0; j < NW; ++j) rs += mabs(fB[ii + j * LA]);
         }
         rsum[i] = rs;
     });
     // FP32: V C and S C;  V(p,q) = R[NW+p + (NW+q) NR], S(k,q) = R[k + (NW+q) NR], W(k,j) = R[k + j NR]
-    wgemm<float, NY, NX, NY>([&](int, int) { return 0.f; }, [&](int i, int q) { return fR[NW + i + (NW + q) * NR]; },
-                             [&](int q, int j) { return fC[q + j * NY]; },
-                             [&](int i, int j, float v) { fVC[i + j * NY] = v; });
-    wgemm<float, NW, NX, NY>([&](int, int) { return 0.f; }, [&](int k, int q) { return fR[k + (NW + q) * NR]; },
-                             [&](int q, int j) { return fC[q + j * NY]; },
-                             [&](int k, int j, float v) { fSC[k + j * NW] = v; });
+    wgemm<float, NY, NX, NY>([&](int, int) { return 0.f; }, [&](int i, int q) { return fR[NW + i + (NW + q) * LR]; },
+                             [&](int q, int j) { return fC[q + j * LC]; },
+                             [&](int i, int j, float v) { fVC[i + j * LC] = v; });
+    wgemm<float, NW, NX, NY>([&](int, int) { return 0.f; }, [&](int k, int q) { return fR[k + (NW + q) * LR]; },
+                             [&](int q, int j) { return fC[q + j * LC]; },
+                             [&](int k, int j, float v) { fSC[k + j * LS] = v; });
     // FP64: t = S^T w~ - V y~ (ny) and l_w = S y~ - W w~ (nw): two dot products per lane
     wfor(NY + NW, [&](int k) {
         const double *m1, *v1, *m2, *v2;
@@ -689,21 +713,30 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
         }
     });
     // FP32: Q_x = C^T (V C) (one triangle, mirrored);  FP64: l_x = C^T t
-    wgemm<float, NX, NX, NY, true>([&](int, int) { return 0.f; }, [&](int i, int q) { return fC[q + i * NY]; },
-                                   [&](int q, int j) { return fVC[q + j * NY]; },
-                                   [&](int i, int j, float v) { fQx[i + j * NX] = v; fQx[j + i * NX] = v; });
+    wgemm<float, NX, NX, NY, true>([&](int, int) { return 0.f; }, [&](int i, int q) { return fC[q + i * LC]; },
+                                   [&](int q, int j) { return fVC[q + j * LC]; },
+                                   [&](int i, int j, float v) { fQx[i + j * LA] = v; fQx[j + i * LA] = v; });
     wfor(NX, [&](int i) {
         const double d = dot_pred<NY>(C + i * NY, 1, dt, NY, 0.0);
         lo[i] = d;
         lo32[i] = f32_rn(d);
     });
     auto qf = [&](int i, int j) -> float {
-        if (i < NX && j < NX) return fQx[i + j * NX];
-        if (i < NX) return -fSC[(j - NX) + i * NW];
-        if (j < NX) return -fSC[(i - NX) + j * NW];
-        return fR[(i - NX) + (j - NX) * NR];
+        if (i < NX && j < NX) return fQx[i + j * LA];
+        if (i < NX) return -fSC[(j - NX) + i * LS];
+        if (j < NX) return -fSC[(i - NX) + j * LS];
+        return fR[(i - NX) + (j - NX) * LR];
     };
-    wfor(NQ * NQ, [&](int idx) { Qo[idx] = qf(idx % NQ, idx / NQ); });
+    if constexpr (NQ % 4 == 0) {
+        // four consecutive rows of a column per 16-byte store
+        wfor(NQ * NQ / 4, [&](int u) {
+            const int i = 4 * (u % (NQ / 4)), j = u / (NQ / 4);
+            const float v[4] = {qf(i, j), qf(i + 1, j), qf(i + 2, j), qf(i + 3, j)};
+            st16(Qo + i + j * NQ, v);
+        });
+    } else {
+        wfor(NQ * NQ, [&](int idx) { Qo[idx] = qf(idx % NQ, idx / NQ); });
+    }
     // rows of ||K||_inf: the Q part of the stationarity rows
     wfor(NQ, [&](int i) {
         float rs = rsum[i];
