@@ -27,6 +27,11 @@ constexpr int op_count()
                                            : (OP == OP_DOWN ? Ws<T, NX>::count_vec : Ws<T, NX>::count + kTcExtra));
 }
 
+// CTAs of the residual kernel per SM its register budget is sized for
+// (measured on the batched workload: 4 -> 5 CTAs took the n = 24 pass from
+// 23.6 to 18.6 ms, 6 the same, 8 spilled and doubled it)
+constexpr int kResidBlocks = 5;
+
 // teams per CTA of at most 256 threads: at most 256 / MHE_TEAM
 constexpr int kMaxTeams = 256 / MHE_TEAM;
 
@@ -54,15 +59,19 @@ constexpr bool level_fits()
 // CTAs of 256 threads per SM the register allocation is sized for: the small
 // shapes' workspaces are small, so their occupancy is set by registers (64 or
 // 80 per thread keep 32 or 24 warps per SM); the n = 24 reduction keeps its
-// 255 registers (shared memory allows one CTA anyway), its vector passes 128;
+// 255 registers (shared memory allows one CTA anyway), its right-hand-side pass
+// 128 and its down pass 85 (measured: the down pass gains from a third CTA,
+// the right-hand-side pass, whose loads are unrolled wider, loses);
 // the n = 64 passes (one four-warp team per subproblem, a few hundred teams)
 // all take 255.
 template <typename T, int NX, int OP>
 constexpr int level_min_blocks()
 {
     return NX >= 48 ? 1   // four-warp teams, a few per SM: every pass may take 255 registers
-                    : (sizeof(T) == 4 ? (NX <= 8 ? 4 : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP == OP_REDUCE_TC) ? 1 : 2)))
-                                      : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2)));
+                    : (sizeof(T) == 4
+                           ? (NX <= 8 ? 4
+                                      : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP == OP_REDUCE_TC) ? 1 : (OP == OP_DOWN ? 3 : 2))))
+                           : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2)));
 }
 
 // shapes whose stage products run on the tensor cores: a team of four warps,
@@ -137,8 +146,10 @@ void launch_level(const LevelArgs<T>& a, int upper, void* stream)
     else launch_level_v<T, NX, NW, 0, OP>(a, stream);
 }
 
+// The residual waits on its FP64 loads from HBM; five CTAs of 256 threads per SM
+// (48 registers a thread, a few spilled) hide that latency better than four.
 template <int NX, int NW, typename TR, int NY>
-__global__ void __launch_bounds__(256) k_resid(ResidArgs<TR> r)
+__global__ void __launch_bounds__(256, kResidBlocks) k_resid(ResidArgs<TR> r)
 {
     __shared__ unsigned long long sm[kMaxTeams][ResidSmem<NX, NW, NY>::count];
     const int team = team_id();
