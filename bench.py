@@ -257,6 +257,8 @@ def run_gpu(args):
     refine_tol = 1e-9
     max_refine = 16 if prec == 1 else 2
     solvers, plans = [], []
+    stream = torch.cuda.current_stream()
+    bstreams = [torch.cuda.Stream() for _ in buckets]
     t_tune = time.time()
     for bk in buckets:
         plan = dict(leaf_len=16 if prec == 0 else 8, branching=8 if prec == 0 else 4, top_len=4)
@@ -284,18 +286,24 @@ def run_gpu(args):
             plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"])
         plans.append(dict(nx=bk["n"], **plan))
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=sprec, refine_tol=refine_tol,
-                       max_refine=max_refine, **plan)
+                       max_refine=max_refine, stream=bstreams[len(solvers)], **plan)
         s.out = s.outputs()
         solvers.append(s)
     tune_s = time.time() - t_tune
-    stream = torch.cuda.current_stream()
 
     def step(ss, timing=False):
-        for bk, s in zip(buckets, ss):
+        # one stream per shape bucket, forked from and joined back into the timed stream:
+        # the buckets' kernels overlap (one bucket's tails and small upper levels leave SMs idle)
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for bk, s, st in zip(buckets, ss, bstreams):
             d = bk["dev"]
+            st.wait_event(fork)
             # steps a0..a7 from the MHE data (stage assembly inside the library)
             s.estimate(bk["q"], d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"],
                        out=s.out)
+        for st in bstreams:
+            stream.wait_stream(st)
 
     for _ in range(args.warmup):
         step(solvers)
@@ -389,7 +397,8 @@ def run_gpu(args):
         for i, bk in enumerate(buckets):
             bpl = dict(top_len=int(np.max(bk["N"])) + 1) if bplans is None else \
                 {k: v for k, v in bplans[i].items() if k != "nx"}
-            s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref, **bpl)
+            s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
+                           stream=bstreams[i], **bpl)
             s.out = s.outputs()
             ss.append(s)
         step(ss)
