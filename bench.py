@@ -262,7 +262,9 @@ def run_gpu(args):
     t_tune = time.time()
     for bk in buckets:
         plan = dict(leaf_len=16 if prec == 0 else 8, branching=8 if prec == 0 else 4, top_len=4)
-        if args.plan:
+        if bk["n"] in args.serial_nx:
+            plan = dict(leaf_len=plan["leaf_len"], branching=plan["branching"], top_len=int(np.max(bk["N"])) + 1)
+        elif args.plan:
             lf, br, tp = (int(v) for v in args.plan.split(","))
             plan = dict(leaf_len=lf, branching=br, top_len=tp)
         elif args.autotune:
@@ -716,6 +718,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--tune-instances", type=int, default=256)
+    ap.add_argument("--serial-nx", type=lambda v: [int(x) for x in v.split(",") if x], default=[],
+                    help="shape buckets (nx list) that take the serial plan instead of the autotuner's")
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tf32"],
                     help="tree precision of the FP32 workloads: tf32 = stage products on the tensor cores "
                          "(MHE_TF32_IR; auto: tf32 for the nx = 64 workloads, fp32 otherwise)")
