@@ -56,12 +56,15 @@ typedef enum {
 typedef enum {
     MHE_FP64 = 0,     /* every product and factorisation in FP64 */
     MHE_FP32_IR = 1,  /* FP32 tree + iterative refinement against the FP64 KKT residual */
-    MHE_TF32_IR = 2   /* MHE_FP32_IR with the stage products F = Q_x + A^T P A, H, G of the
+    MHE_TF32_IR = 2,  /* MHE_FP32_IR with the stage products F = Q_x + A^T P A, H, G of the
                          reductions on the tensor cores (tcgen05 kind::tf32, each operand split
-                         into TF32 hi + lo, three MMAs per product, FP32 accumulation in TMEM)
+                         into TF32 hi + lo, hi*hi and hi*lo + lo*hi in separate FP32 TMEM
+                         accumulators)
                          for shapes compiled with a tensor-core reduction (nx = 64, nw = 32);
                          a stage that also forms V (the non-last chunks of a tree plan) and
                          every other shape compute as MHE_FP32_IR */
+    MHE_BF16_IR = 3   /* BF16 tensor-core products: not built; mhe_create and mhe_workspace_bytes
+                         refuse it (MHE_E_ARG, 0 bytes) */
 } mhe_precision;
 
 /* Problem shape and solver options (mhe_create copies it). */

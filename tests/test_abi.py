@@ -64,3 +64,21 @@ def test_product_path_has_no_fallback(tmp_path, monkeypatch):
     monkeypatch.setattr(mhe, "_lib", None)
     with pytest.raises(RuntimeError):
         mhe.lib()
+
+
+def test_precision_enum_matches_the_binding():
+    """The mhe_precision values of include/mhe.h and the binding's constants agree."""
+    txt = open(os.path.join(ROOT, "include", "mhe.h")).read()
+    body = txt[txt.index("typedef enum {\n    MHE_FP64"):]
+    body = body[:body.index("} mhe_precision;")]
+    vals = dict((k, int(v)) for k, v in re.findall(r"\b(MHE_[A-Z0-9_]+)\s*=\s*(\d+)", body))
+    assert vals == {"MHE_FP64": mhe.MHE_FP64, "MHE_FP32_IR": mhe.MHE_FP32_IR,
+                    "MHE_TF32_IR": mhe.MHE_TF32_IR, "MHE_BF16_IR": mhe.MHE_BF16_IR}
+
+
+def test_unbuilt_precision_rejected_on_host(L):
+    d32, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_FP32_IR)
+    dtf, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_TF32_IR)
+    dbf, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_BF16_IR)
+    assert mhe.mhe_workspace_bytes(dtf) == mhe.mhe_workspace_bytes(d32) > 0
+    assert mhe.mhe_workspace_bytes(dbf) == 0

@@ -218,6 +218,13 @@ def test_tf32_on_a_shape_without_tensor_products_is_fp32():
     assert torch.equal(out[0], out[1])
 
 
+def test_bf16_is_refused():
+    """MHE_BF16_IR is declared by the C-ABI but not built: mhe_create refuses it."""
+    with pytest.raises(mhe.MheError) as e:
+        mhe.Solver(64, 32, [40], prec=mhe.MHE_BF16_IR)
+    assert e.value.code == -1
+
+
 def test_nx64_fp64_is_refused():
     """The FP64 workspace of an nx=64 subproblem exceeds an SM's shared memory."""
     with pytest.raises(mhe.MheError) as e:
