@@ -248,7 +248,11 @@ def run_gpu(args):
     if prec == 1 and (args.prec == "tf32" or (args.prec == "auto" and args.workload in ("xl", "xl_profile"))):
         sprec = mhe.MHE_TF32_IR
         desc["precision"] = ("FP32 tree (128-thread teams), stage products F, G, H on the tensor cores "
-                             "(tcgen05 kind::tf32, operands split hi + lo, 3 MMAs per product, FP32 accumulation) "
+                             "(tcgen05 kind::tf32, operands split hi + lo, FP32 accumulation) + FP64 refinement")
+    elif prec == 1 and args.prec == "bf16":
+        sprec = mhe.MHE_BF16_IR
+        desc["precision"] = ("FP32 tree (128-thread teams), stage products F, G, H on the tensor cores "
+                             "(tcgen05 kind::f16, BF16 operands split hi + mid + lo, FP32 accumulation) "
                              "+ FP64 refinement")
     t0 = time.time()
     for bk in buckets:
@@ -346,7 +350,7 @@ def run_gpu(args):
         mhe.mhe_timing_enable(s.ctx, False)
     pk = peaks()
     traffic = read_traffic()
-    kern = {"reduce": "k_level<{t},{n},{m},0,%s>" % ("REDUCE_TC" if sprec == 2 else "REDUCE"),
+    kern = {"reduce": "k_level<{t},{n},{m},0,%s>" % {2: "REDUCE_TC", 3: "REDUCE_BF"}.get(sprec, "REDUCE"),
             "rhs": "k_level<{t},{n},{m},0,RHS>",
             "down": "k_level<{t},{n},{m},0,DOWN>", "resid": "k_resid<{n},{m},{t},{y}>",
             "prep": "k_prep<{n},{m},{q}>" if prec == 1 else "k_assemble<{n},{m},{q}>"}
@@ -375,14 +379,16 @@ def run_gpu(args):
                    frac=round(achieved / peak, 4), traffic=(tr * int(np.sum(bk["N"])) if tr else None),
                    peak_src=src, work_per_launch=work, ms_per_launch=round(full_ms, 4),
                    launches_per_step=r["calls"], ms_per_step=round(r["ms"], 4))
-        if r["phase"] == "reduce" and sprec == 2 and n == 64:
-            # the tensor pipe's view: MMA flops issued per stage (M = 128 rows, three MMAs per
-            # product for the hi/lo split) against TF32 = the measured BF16 peak x 1.1 / 2.25
-            mma = 3 * 2 * 128 * n * (n + (n + m)) * int(np.sum(bk["N"]))
-            tf = pk["bf16_tflops"] * 1.1 / 2.25
+        if r["phase"] == "reduce" and sprec in (2, 3) and n == 64:
+            # the tensor pipe's view: MMA flops issued per stage (M = 128 rows; TF32: N = 2k + k per
+            # product for the hi/lo split, against TF32 = the measured BF16 peak x 1.1 / 2.25; BF16:
+            # N = 2k + k + 2k + k for the three-way split, against the measured BF16 peak)
+            mma = (3 if sprec == 2 else 6) * 2 * 128 * n * (n + (n + m)) * int(np.sum(bk["N"]))
+            tf = pk["bf16_tflops"] * (1.1 / 2.25 if sprec == 2 else 1.0)
             out["tensor"] = dict(mma_tflop_per_launch=mma / 1e12, achieved=round(mma / 1e12 / (full_ms * 1e-3), 2),
                                  peak=round(tf, 1), unit="TFLOP/s", frac=round(mma / 1e12 / (full_ms * 1e-3) / tf, 4),
-                                 peak_src="TF32 dense = measured BF16 burst x 1.1 / 2.25 (nominal ratio)")
+                                 peak_src=("TF32 dense = measured BF16 burst x 1.1 / 2.25 (nominal ratio)"
+                                           if sprec == 2 else "BF16 dense, measured burst"))
         return out
 
     ranked = sorted(passes, key=lambda r: -r["ms"])
@@ -393,7 +399,7 @@ def run_gpu(args):
     base = {}
     arms = [] if args.no_baseline else [("serial_same_precision", sprec, max_refine if prec == 1 else 0, None)] + \
         ([("serial_fp64", 0, 0, None)] if (prec == 1 and args.serial_fp64) else []) + \
-        ([("fp32_simt_products_same_plan", 1, max_refine, plans)] if sprec == 2 else [])
+        ([("fp32_simt_products_same_plan", 1, max_refine, plans)] if sprec in (2, 3) else [])
     for name, bprec, mref, bplans in arms:
         ss = []
         for i, bk in enumerate(buckets):
@@ -442,7 +448,7 @@ def run_gpu(args):
     p99 = step_sorted[min(len(step_sorted) - 1, int(np.ceil(0.99 * len(step_sorted))) - 1)]
     line = dict(metric=METRIC, value=round(value, 3), unit="KKT solves/s", n_gpus=1, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(ms, 4), higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype=("tf32+f32+f64" if sprec == 2 else "f32+f64") if prec == 1 else "f64",
+                vs_baseline=None, dtype={2: "tf32+f32+f64", 3: "bf16+f32+f64"}.get(sprec, "f32+f64") if prec == 1 else "f64",
                 data="synthetic",
                 config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, generation_s=round(gen_s, 1),
                             plans=plans, autotune_s=round(tune_s, 1)),
@@ -720,9 +726,9 @@ def main():
     ap.add_argument("--tune-instances", type=int, default=256)
     ap.add_argument("--serial-nx", type=lambda v: [int(x) for x in v.split(",") if x], default=[],
                     help="shape buckets (nx list) that take the serial plan instead of the autotuner's")
-    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tf32"],
-                    help="tree precision of the FP32 workloads: tf32 = stage products on the tensor cores "
-                         "(MHE_TF32_IR; auto: tf32 for the nx = 64 workloads, fp32 otherwise)")
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "tf32", "bf16"],
+                    help="tree precision of the FP32 workloads: tf32 / bf16 = stage products on the tensor "
+                         "cores (MHE_TF32_IR / MHE_BF16_IR; auto: tf32 for the nx = 64 workloads, fp32 otherwise)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -63,8 +63,9 @@ typedef enum {
                          for shapes compiled with a tensor-core reduction (nx = 64, nw = 32);
                          a stage that also forms V (the non-last chunks of a tree plan) and
                          every other shape compute as MHE_FP32_IR */
-    MHE_BF16_IR = 3   /* BF16 tensor-core products: not built; mhe_create and mhe_workspace_bytes
-                         refuse it (MHE_E_ARG, 0 bytes) */
+    MHE_BF16_IR = 3   /* as MHE_TF32_IR with BF16 operands (tcgen05 kind::f16): each operand split
+                         three ways (hi + mid + lo), the six terms down to 2^-16 relative summed in
+                         three FP32 TMEM accumulators by magnitude */
 } mhe_precision;
 
 /* Problem shape and solver options (mhe_create copies it). */

@@ -231,8 +231,8 @@ int check_dims(const mhe_dims* d)
 {
     if (!d) return fail(MHE_E_ARG, "dims is NULL");
     if (d->nx < 1 || d->nw < 1 || d->batch < 1 || !d->N) return fail(MHE_E_ARG, "nx, nw, batch >= 1 and N required");
-    if (d->prec != MHE_FP64 && d->prec != MHE_FP32_IR && d->prec != MHE_TF32_IR)
-        return fail(MHE_E_ARG, "unknown or unbuilt precision (MHE_BF16_IR is not built)");
+    if (d->prec != MHE_FP64 && d->prec != MHE_FP32_IR && d->prec != MHE_TF32_IR && d->prec != MHE_BF16_IR)
+        return fail(MHE_E_ARG, "unknown precision");
     if (!find_shape(d->nx, d->nw))
         return fail(MHE_E_ARG, "shape (nx=" + std::to_string(d->nx) + ", nw=" + std::to_string(d->nw) +
                                    ") is not compiled into this library");

@@ -104,7 +104,10 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     rt = r;
     stream = s;
     prec = d.prec;
-    if (prec != MHE_FP64 && prec != MHE_FP32_IR && prec != MHE_TF32_IR) { err = "unknown precision"; return MHE_E_ARG; }
+    if (prec != MHE_FP64 && prec != MHE_FP32_IR && prec != MHE_TF32_IR && prec != MHE_BF16_IR) {
+        err = "unknown precision";
+        return MHE_E_ARG;
+    }
     if (prec == MHE_FP64 && !ops->reduce64) {
         err = "this shape's FP64 workspace exceeds the shared memory of an SM: use MHE_FP32_IR";
         return MHE_E_ARG;
@@ -293,8 +296,10 @@ void Engine::pass_reduce(const T* A_, const T* B_, const T* Q_, const T* P0_, co
         if (k >= 1 && !l) { g.lxh = nullptr; g.ah = nullptr; g.lNk = nullptr; }
         mark(PH_REDUCE, k, 1);
         launches += g.nchunks > 0;
-        launch<T>(ops->reduce64, (prec == MHE_TF32_IR && ops->reduce32tc) ? ops->reduce32tc : ops->reduce32, g,
-                  k >= 1, stream);
+        auto r32 = ops->reduce32;
+        if (prec == MHE_TF32_IR && ops->reduce32tc) r32 = ops->reduce32tc;
+        if (prec == MHE_BF16_IR && ops->reduce32bf) r32 = ops->reduce32bf;
+        launch<T>(ops->reduce64, r32, g, k >= 1, stream);
         mark(PH_REDUCE, k, 0);
     }
 }

@@ -23,6 +23,7 @@ struct ShapeOps {
     void (*reduce32)(const LevelArgs<float>&, int upper, void* stream);
     // the reduction with its stage products on the tensor cores (MHE_TF32_IR), or nullptr
     void (*reduce32tc)(const LevelArgs<float>&, int upper, void* stream);
+    void (*reduce32bf)(const LevelArgs<float>&, int upper, void* stream);   // the same with BF16 operands (MHE_BF16_IR)
     void (*rhs32)(const LevelArgs<float>&, int upper, void* stream);
     void (*down32)(const LevelArgs<float>&, int upper, void* stream);
     void (*resid64)(const ResidArgs<double>&, void* stream);

@@ -11,8 +11,9 @@
 
 namespace mhe {
 
-// OP_REDUCE_TC: the reduction with the stage products on the tensor cores
-enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2, OP_REDUCE_TC = 3 };
+// OP_REDUCE_TC / OP_REDUCE_BF: the reduction with the stage products on the
+// tensor cores, TF32 or BF16 operands
+enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2, OP_REDUCE_TC = 3, OP_REDUCE_BF = 4 };
 
 // floats past the workspace of a tensor-core reduction: a 32 KB operand tile,
 // the mbarrier and the TMEM address
@@ -24,7 +25,7 @@ constexpr int op_count()
 {
     return OP == OP_REDUCE ? Ws<T, NX>::count
                            : (OP == OP_RHS ? Ws<T, NX>::count_rhs
-                                           : (OP == OP_DOWN ? Ws<T, NX>::count_vec : Ws<T, NX>::count + kTcExtra));
+                                           : (OP == OP_DOWN ? Ws<T, NX>::count_vec : Ws<T, NX>::count + kTcExtra));   // both tensor-core reductions
 }
 
 // CTAs of the residual kernel per SM its register budget is sized for
@@ -70,7 +71,7 @@ constexpr int level_min_blocks()
     return NX >= 48 ? 1   // four-warp teams, a few per SM: every pass may take 255 registers
                     : (sizeof(T) == 4
                            ? (NX <= 8 ? 4
-                                      : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP == OP_REDUCE_TC) ? 1 : (OP == OP_DOWN ? 3 : 2))))
+                                      : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP >= OP_REDUCE_TC) ? 1 : (OP == OP_DOWN ? 3 : 2))))
                            : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2)));
 }
 
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
     if (ci >= a.nchunks) return;   // the whole team leaves together
     if (a.any_active && *a.any_active == 0) return;   // a refinement pass with every instance converged
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)team * op_count<T, NX, OP>();
-    if constexpr (OP == OP_REDUCE_TC) {
+    if constexpr (OP == OP_REDUCE_TC || OP == OP_REDUCE_BF) {
         // one team per CTA: TMEM (all 512 columns; one CTA fits an SM) and the mbarrier are the CTA's
         static_assert(W == 1 && sizeof(T) == 4, "one FP32 tensor-core team per CTA");
         float* xbuf = reinterpret_cast<float*>(smem_raw) + Ws<float, NX>::count;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
         __syncthreads();
         tc::fence_after();
         TcState tcs{*slot, mbar, xbuf, 0u, 1};
-        reduce_chunk<T, NX, NW, UPPER != 0, true>(a, ci, sm, &tcs);
+        reduce_chunk<T, NX, NW, UPPER != 0, OP == OP_REDUCE_TC ? 1 : 2>(a, ci, sm, &tcs);
         // a wait that ran out: give the MMAs of that phase another bounded wait before freeing TMEM
         if (!tcs.ok) tc::mbar_wait(mbar, tcs.phase, tc::kWaitLimit);
         tc::fence_before();
@@ -290,8 +291,13 @@ ShapeEntry make_shape()
         e.ops.down64 = nullptr;
     }
     e.ops.reduce32 = &launch_level<float, NX, NW, OP_REDUCE>;
-    if constexpr (tc_shape<NX, NW>()) e.ops.reduce32tc = &launch_level<float, NX, NW, OP_REDUCE_TC>;
-    else e.ops.reduce32tc = nullptr;
+    if constexpr (tc_shape<NX, NW>()) {
+        e.ops.reduce32tc = &launch_level<float, NX, NW, OP_REDUCE_TC>;
+        e.ops.reduce32bf = &launch_level<float, NX, NW, OP_REDUCE_BF>;
+    } else {
+        e.ops.reduce32tc = nullptr;
+        e.ops.reduce32bf = nullptr;
+    }
     e.ops.rhs32 = &launch_level<float, NX, NW, OP_RHS>;
     e.ops.down32 = &launch_level<float, NX, NW, OP_DOWN>;
     e.ops.resid64 = &launch_resid<NX, NW, double>;

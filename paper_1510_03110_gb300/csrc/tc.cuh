@@ -44,10 +44,32 @@ MHE_DEV float tf32_hi(float x)
     return __uint_as_float((b + 0x1000u) & 0xFFFFE000u);
 }
 
-// byte offset of element (r, k) in a canonical K-major tile
+// byte offset of element (r, k) in a canonical K-major tile of 32-bit elements
 MHE_TC_HD constexpr int kmaj_off(int r, int k, int lbo, int sbo)
 {
     return (r / 8) * sbo + (k / 4) * lbo + (r % 8) * 16 + (k % 4) * 4;
+}
+
+// the same for 16-bit elements (a core matrix row holds 8 of them)
+MHE_TC_HD constexpr int kmaj_off16(int r, int k, int lbo, int sbo)
+{
+    return (r / 8) * sbo + (k / 8) * lbo + (r % 8) * 16 + (k % 8) * 2;
+}
+
+// x rounded to the nearest BF16 value (ties to even), as its 16 bits and as a
+// float; integer arithmetic on the bit pattern (finite x)
+MHE_DEV unsigned short bf16_bits(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    return (unsigned short)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);
+}
+MHE_DEV float bf16_val(unsigned short h) { return __uint_as_float((unsigned)h << 16); }
+
+// instruction descriptor: kind::f16 with BF16 A and B (format 1), FP32 accumulator,
+// both K-major, N / 8 in bits 17-22, M / 16 in bits 24-28
+MHE_TC_HD constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // instruction descriptor: kind::tf32, dense, FP32 accumulator (D format 1),
@@ -96,6 +118,16 @@ MHE_DEV void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t 
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+        : "memory");
+}
+
+// D (+)= A B^T with BF16 operands, one instruction of K = 16
+MHE_DEV void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
         : "memory");
 }

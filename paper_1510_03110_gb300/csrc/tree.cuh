@@ -506,11 +506,169 @@ MHE_DEV void tc_stage_products(Ws<float, NX>& s, const StageRef<float>& st, TcSt
     });
 }
 
+// The same two products with BF16 operands (kind::f16, K = 16 per instruction).
+// A BF16 value keeps 7 fraction bits, so each operand is split three ways,
+// x = hi + mid + lo (each the BF16 rounding of what the previous pieces leave),
+// and each product sums the six terms down to 2^-16 relative in three FP32
+// accumulators by magnitude: hi*hi; hi*mid + mid*hi; hi*lo + mid*mid + lo*hi.
+// The B operands are stored [hi; mid; lo]: per K step, A_hi x [B_hi; B_mid]
+// (N = 2k) gives hi*hi | hi*mid, A_hi x B_lo gives hi*lo, A_mid x [B_hi; B_mid]
+// adds mid*hi | mid*mid, A_lo x B_hi adds lo*hi.  TMEM columns [0, 3n) hold the
+// three parts of X^T, then (after they are read) [0, 3(n+m)) those of the second
+// product.  Tiles (16-bit, canonical K-major): [A|B]^T hi and mid in the V, Qw
+// slots, lo in the extra tile; [P hi; mid; lo] in PB and H; [X^T hi; mid; lo]
+// in PB..G.
+template <int NX, int MT, int KIND>
+MHE_DEV void tc_stage_products_bf16(Ws<float, NX>& s, const StageRef<float>& st, TcState& tcs)
+{
+    using X = Acc<float, KIND, NX, MT>;
+    using W = Ws<float, NX>;
+    constexpr int ld = W::ld;
+    constexpr int NAB = NX + MT;
+    constexpr int LBO = 128, SBO = (NX / 8) * 128;
+    constexpr int TILE = 128 * NX * 2;   // bytes of a 128-row 16-bit operand tile
+    static_assert(MHE_TEAM == 128 && NX > 0, "a tensor-core team is the four warps of one CTA");
+    static_assert(NX % 16 == 0 && NAB % 16 == 0 && 2 * NAB <= 256, "MMA shapes M = 128, N <= 256");
+    static_assert(2 * W::slot * 4 >= 2 * TILE && TILE <= 32 * 1024, "[A|B]^T tiles fit the V, Qw slots and the extra tile");
+    static_assert(2 * W::slot * 4 >= 3 * NX * NX * 2 && 4 * W::slot * 4 >= 3 * NAB * NX * 2, "stacked B tiles fit");
+    static_assert(3 * NAB <= 512, "accumulators within the 512 TMEM columns");
+    char* Ah = reinterpret_cast<char*>(s.V);
+    char* Am = Ah + TILE;
+    char* Al = reinterpret_cast<char*>(tcs.xbuf);
+    char* Pt = reinterpret_cast<char*>(s.PB);   // [P hi; P mid; P lo], NX rows each
+    char* Xt = reinterpret_cast<char*>(s.PB);   // [X^T hi; mid; lo], NAB rows each
+    // 8 values of one row along K -> three 16-byte rows of core matrices
+    auto split_store8 = [&](char* h, char* m, char* l, const float (&x)[8]) {
+        unsigned short ph[8], pm[8], pl[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            ph[i] = tc::bf16_bits(x[i]);
+            const float r1 = x[i] - tc::bf16_val(ph[i]);
+            pm[i] = tc::bf16_bits(r1);
+            pl[i] = tc::bf16_bits(r1 - tc::bf16_val(pm[i]));
+        }
+        auto store = [](char* dst, const unsigned short (&v)[8]) {
+            const unsigned w[4] = {v[0] | (unsigned)v[1] << 16, v[2] | (unsigned)v[3] << 16,
+                                   v[4] | (unsigned)v[5] << 16, v[6] | (unsigned)v[7] << 16};
+            st16u(dst, w);
+        };
+        store(h, ph);
+        store(m, pm);
+        store(l, pl);
+    };
+    constexpr int UAB = NAB * (NX / 8), UP = NX * (NX / 8);   // 8-value pieces
+    tc::lanes_publish([&](int lane) {
+#pragma unroll 1
+        for (int u = lane; u < UAB + UP; u += MHE_TEAM) {
+            float x[8];
+            if (u < UAB) {
+                const int r = u % NAB, kc = u / NAB;
+                const float* src = (r < NX ? s.A + r * ld : s.B + (r - NX) * ld) + 8 * kc;
+                float a[4], b[4];
+                ld16(src, a);
+                ld16(src + 4, b);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { x[i] = a[i]; x[4 + i] = b[i]; }
+                const int off = tc::kmaj_off16(r, 8 * kc, LBO, SBO);
+                split_store8(Ah + off, Am + off, Al + off, x);
+            } else {
+                const int v = u - UAB, r = v % NX, kc = v / NX;
+                float a[4], b[4];
+                ld16(s.P + r * ld + 8 * kc, a);
+                ld16(s.P + r * ld + 8 * kc + 4, b);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { x[i] = a[i]; x[4 + i] = b[i]; }
+                split_store8(Pt + tc::kmaj_off16(r, 8 * kc, LBO, SBO), Pt + tc::kmaj_off16(NX + r, 8 * kc, LBO, SBO),
+                             Pt + tc::kmaj_off16(2 * NX + r, 8 * kc, LBO, SBO), x);
+            }
+        }
+    });
+    // issue the four MMAs per K step of one product: A [128 x K] against the stacked
+    // B rows [0, 2N) (hi, mid) and [2N, 3N) (lo), into TMEM columns [0, 3N)
+    auto issue = [&](const char* Bt, int N, uint32_t idN, uint32_t id2N) {
+#pragma unroll 1
+        for (int k = 0; k < NX / 16; ++k) {
+            const uint64_t ah = tc::sdesc(Ah + 256 * k, LBO, SBO), am = tc::sdesc(Am + 256 * k, LBO, SBO),
+                           al = tc::sdesc(Al + 256 * k, LBO, SBO);
+            const uint64_t bhm = tc::sdesc(Bt + 256 * k, LBO, SBO);
+            const uint64_t blo = tc::sdesc(Bt + (2 * N / 8) * SBO + 256 * k, LBO, SBO);
+            tc::mma_bf16(tcs.tbase, ah, bhm, id2N, k > 0);          // hi*hi | hi*mid
+            tc::mma_bf16(tcs.tbase + 2 * N, ah, blo, idN, k > 0);   // hi*lo
+            tc::mma_bf16(tcs.tbase + N, am, bhm, id2N, true);       // + mid*hi | mid*mid
+            tc::mma_bf16(tcs.tbase + 2 * N, al, bhm, idN, true);    // + lo*hi
+        }
+        tc::commit(tcs.mbar);
+    };
+    wone([&](int) {
+        if (!tcs.ok) return;
+        tc::fence_after();
+        issue(Pt, NX, tc::idesc_bf16(128, NX), tc::idesc_bf16(128, 2 * NX));
+    });
+    tc_team_wait(tcs);
+    // X^T (TMEM lane r = row r) -> its three stacked rows
+    tc::lanes_publish([&](int r) {
+#pragma unroll 1
+        for (int c = 0; c < NX; c += 16) {
+            float v[16], w[16], z[16];
+            tc::tmem_ld16x2(tcs.tbase, r, c, NX + c, v, w);
+            tc::tmem_ld16(tcs.tbase, r, 2 * NX + c, z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += w[i] + z[i];
+            if (r < NAB) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    float x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = v[8 * q + i];
+                    split_store8(Xt + tc::kmaj_off16(r, c + 8 * q, LBO, SBO),
+                                 Xt + tc::kmaj_off16(NAB + r, c + 8 * q, LBO, SBO),
+                                 Xt + tc::kmaj_off16(2 * NAB + r, c + 8 * q, LBO, SBO), x);
+                }
+            }
+        }
+    });
+    wone([&](int) {
+        if (!tcs.ok) return;
+        tc::fence_after();
+        issue(Xt, NAB, tc::idesc_bf16(128, NAB), tc::idesc_bf16(128, 2 * NAB));
+    });
+    tc_team_wait(tcs);
+    // row r of the second product (see tc_stage_products)
+    wlanes([&](int r) {
+        const bool row = r < NAB;   // whole warps
+        float qv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) qv[i] = row ? X::q(st, r, i) : 0.f;
+#pragma unroll 1
+        for (int c = 0; c < NAB; c += 16) {
+            float v[16], w[16], z[16];
+            tc::tmem_ld16x2(tcs.tbase, r, c, NAB + c, v, w);
+            tc::tmem_ld16(tcs.tbase, r, 2 * NAB + c, z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = qv[i] + (v[i] + (w[i] + z[i]));
+            if (c + 16 < NAB) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) qv[i] = row ? X::q(st, r, c + 16 + i) : 0.f;
+            }
+            if (r < NX) {
+                float* dst = c < NX ? s.P + r + c * ld : s.H + r + (c - NX) * ld;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dst[i * ld] = v[i];
+            } else if (row && c >= NX) {
+                float* dst = s.G + (r - NX) + (c - NX) * ld;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dst[i * ld] = v[i];
+            }
+        }
+        tc::fence_before();
+    });
+}
+
 // One backward stage of Algorithm 4 (or Algorithms 1-2 when want_v is false).
 // On entry s.P = P_{t+1}, s.Psi = Psi_{t+1}, s.V = V_{t+1}, s.v = v_{t+1},
 // s.Qw = partial Q^_w.  Stores P_{t+1}, chol(G_{t+1}), K_{t+1}, k_{t+1},
 // L_{t+1} (nullptr skips a store).  Returns true on a failed pivot.
-template <typename T, int NX, int MT, int KIND, bool TC = false>
+template <typename T, int NX, int MT, int KIND, int TC = 0>
 MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout, T* Kout,
                          T* kout, T* Lout, bool want_v, double piv_rel, TcState* tcs = nullptr)
 {
@@ -520,12 +678,13 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
     load_AB<T, NX, MT, KIND>(s, st);
     bool on_tc = false;
-    if constexpr (TC) on_tc = !want_v;
+    if constexpr (TC != 0) on_tc = !want_v;
     if (on_tc) {
         // u = Psi - P a, then F, G, H on the tensor cores (P is overwritten by F)
         wgemm_tn<T, NX, 1, NX, ld, 0>([&](int i, int) { return s.Psi[i]; }, s.P, s.e, (T)-1,
                                       [&](int i, int, T v) { s.u[i] = v; });
-        if constexpr (TC) tc_stage_products<NX, MT, KIND>(s, st, *tcs);
+        if constexpr (TC == 1) tc_stage_products<NX, MT, KIND>(s, st, *tcs);
+        if constexpr (TC == 2) tc_stage_products_bf16<NX, MT, KIND>(s, st, *tcs);
     } else {
         // P A -> Tt,  P B -> PB,  u = Psi - P a
         // (P is symmetric: row i of P is column i, read along the inner dimension)
@@ -695,7 +854,7 @@ MHE_DEV void prefetch_factors(const LevelArgs<T>& a, long long g)
 
 // ---- Algorithm 4 over one chunk ----------------------------------------------
 
-template <typename T, int NX, int NW, bool UPPER, bool TC = false>
+template <typename T, int NX, int NW, bool UPPER, int TC = 0>
 MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem, TcState* tcs = nullptr)
 {
     constexpr int ld = Ws<T, NX>::ld;
@@ -767,7 +926,7 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem, TcState* tcs =
             if (idx < NX) a.lN_up[(long long)b * NX + idx] = -s.Psi[idx];
         });
     }
-    if constexpr (TC) {
+    if constexpr (TC != 0) {
         // a tensor-core wait that ran out: the products after it are not valid
         if (!tcs->ok) wone([&](int) { record_error(a.status, a.where, b, -7, a.level, ci, cd.t0); });
     }

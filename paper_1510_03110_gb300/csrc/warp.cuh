@@ -115,6 +115,11 @@ MHE_DEV void ld16(const double* p, double (&v)[2])
     v[0] = q.x; v[1] = q.y;
 }
 
+// One 16-byte shared-memory store of 4 words (p 16-byte aligned).
+MHE_DEV void st16u(void* p, const unsigned (&w)[4])
+{
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
 // One 16-byte shared-memory store of 4 floats (p 16-byte aligned).
 MHE_DEV void st16(float* p, const float (&v)[4])
 {

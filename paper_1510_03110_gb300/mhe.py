@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmhe.so")
 MHE_FP64 = 0
 MHE_FP32_IR = 1
 MHE_TF32_IR = 2
-MHE_BF16_IR = 3   # declared by the C-ABI, not built: mhe_create refuses it
+MHE_BF16_IR = 3
 
 STATUS = {0: "MHE_OK", 1: "MHE_PENDING", -1: "MHE_E_ARG", -2: "MHE_E_NOMEM", -3: "MHE_E_NOT_PD",
           -4: "MHE_E_NONFINITE", -5: "MHE_E_NOT_FACTORED", -6: "MHE_E_NO_CONVERGE",

@@ -76,9 +76,13 @@ def test_precision_enum_matches_the_binding():
                     "MHE_TF32_IR": mhe.MHE_TF32_IR, "MHE_BF16_IR": mhe.MHE_BF16_IR}
 
 
-def test_unbuilt_precision_rejected_on_host(L):
+def test_tensor_core_precisions_share_the_fp32_workspace(L):
+    """The tensor-core precisions change only the products of the reductions:
+    the same workspace as MHE_FP32_IR; an unknown precision is refused."""
     d32, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_FP32_IR)
     dtf, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_TF32_IR)
     dbf, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_BF16_IR)
+    dno, _ = mhe.make_dims(64, 32, [100, 7], prec=7)
     assert mhe.mhe_workspace_bytes(dtf) == mhe.mhe_workspace_bytes(d32) > 0
-    assert mhe.mhe_workspace_bytes(dbf) == 0
+    assert mhe.mhe_workspace_bytes(dbf) == mhe.mhe_workspace_bytes(d32)
+    assert mhe.mhe_workspace_bytes(dno) == 0

@@ -171,14 +171,15 @@ def test_nx64_team_of_four_warps_matches_oracle(plan):
     s.close()
 
 
+@pytest.mark.parametrize("tc_prec", [mhe.MHE_TF32_IR, mhe.MHE_BF16_IR])
 @pytest.mark.parametrize("plan", [dict(top_len=1000), dict()])
-def test_nx64_tf32_tensor_core_products_match_oracle(plan):
-    """MHE_TF32_IR at nx=64, nw=ny=32: the stage products F, G, H of the
-    reductions on the tensor cores (tcgen05 kind::tf32, operands split into TF32
-    hi + lo), with the serial plan (every stage) and the default tree plan (the
-    last chunk of each level; the others in FP32).  Same bar as MHE_FP32_IR
-    against the FP64 oracle; the solution differs bitwise from the FP32 run's
-    (another product path ran)."""
+def test_nx64_tensor_core_products_match_oracle(plan, tc_prec):
+    """MHE_TF32_IR and MHE_BF16_IR at nx=64, nw=ny=32: the stage products F, G, H
+    of the reductions on the tensor cores (tcgen05 kind::tf32 with operands split
+    into TF32 hi + lo, or kind::f16 with BF16 operands split three ways), with the
+    serial plan (every stage) and the default tree plan (the last chunk of each
+    level; the others in FP32).  Same bar as MHE_FP32_IR against the FP64 oracle;
+    the solution differs bitwise from the FP32 run's (another product path ran)."""
     import torch
     n, m = 64, 32
     Ns = [1, 2, 3, 17, 64, 130]
@@ -186,7 +187,7 @@ def test_nx64_tf32_tensor_core_products_match_oracle(plan):
     d = device_inputs(insts)
     ref = _oracle(insts)
     xs = {}
-    for prec in (mhe.MHE_TF32_IR, mhe.MHE_FP32_IR):
+    for prec in (tc_prec, mhe.MHE_FP32_IR):
         s = mhe.Solver(n, m, d["N"], prec=prec, refine_tol=1e-13, max_refine=60, **plan)
         x, w, lam = _estimate(d, s)
         torch.cuda.synchronize()
@@ -198,31 +199,24 @@ def test_nx64_tf32_tensor_core_products_match_oracle(plan):
             assert rel_err(sols[b], ref[b]) <= 1e-8, (prec, b, rel_err(sols[b], ref[b]))
         xs[prec] = x.clone()
         s.close()
-    assert not torch.equal(xs[mhe.MHE_TF32_IR], xs[mhe.MHE_FP32_IR])
+    assert not torch.equal(xs[tc_prec], xs[mhe.MHE_FP32_IR])
 
 
-def test_tf32_on_a_shape_without_tensor_products_is_fp32():
-    """MHE_TF32_IR on a shape compiled without a tensor-core reduction computes
-    exactly as MHE_FP32_IR."""
+def test_tensor_precisions_on_a_shape_without_tensor_products_are_fp32():
+    """MHE_TF32_IR and MHE_BF16_IR on a shape compiled without a tensor-core
+    reduction compute exactly as MHE_FP32_IR."""
     import torch
     n, m = 24, 12
     insts = [synth.mhe_instance(700 + i, n, m, m, N) for i, N in enumerate([5, 40, 99])]
     d = device_inputs(insts)
     out = []
-    for prec in (mhe.MHE_TF32_IR, mhe.MHE_FP32_IR):
+    for prec in (mhe.MHE_TF32_IR, mhe.MHE_BF16_IR, mhe.MHE_FP32_IR):
         s = mhe.Solver(n, m, d["N"], prec=prec, refine_tol=1e-12)
         x, w, lam = _estimate(d, s)
         torch.cuda.synchronize()
         out.append(x.clone())
         s.close()
-    assert torch.equal(out[0], out[1])
-
-
-def test_bf16_is_refused():
-    """MHE_BF16_IR is declared by the C-ABI but not built: mhe_create refuses it."""
-    with pytest.raises(mhe.MheError) as e:
-        mhe.Solver(64, 32, [40], prec=mhe.MHE_BF16_IR)
-    assert e.value.code == -1
+    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
 
 
 def test_nx64_fp64_is_refused():

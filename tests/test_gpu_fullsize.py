@@ -65,7 +65,7 @@ def test_long_horizon_nx20_N131072_full_size():
     _check_sample(sols, info, 0, p, 1e-10)
 
 
-@pytest.mark.parametrize("prec", [mhe.MHE_TF32_IR, mhe.MHE_FP32_IR])
+@pytest.mark.parametrize("prec", [mhe.MHE_TF32_IR, mhe.MHE_BF16_IR, mhe.MHE_FP32_IR])
 def test_nx64_256_instances_full_size(prec):
     """256 instances of nx=64, nw=ny=32, N=1024 (the serial plan the autotuner
     picks), with the stage products on the tensor cores (the bench's default for
