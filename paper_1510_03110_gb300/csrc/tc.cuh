@@ -1,27 +1,30 @@
 // tc.cuh -- the pieces of the sm_103a fifth-generation tensor core (tcgen05)
 // the stage products of the large shapes use: tensor-memory (TMEM)
 // allocation, shared-memory matrix descriptors, instruction descriptors of
-// kind::tf32 with an FP32 accumulator in TMEM, completion through an mbarrier,
-// and TMEM -> register loads.  Written from the PTX ISA's tcgen05 chapter:
+// kind::tf32 and kind::f16 (BF16 operands) with an FP32 accumulator in TMEM,
+// completion through an mbarrier, and TMEM -> register loads.  Written from the
+// PTX ISA's tcgen05 chapter:
 //
 //  * Operands live in shared memory in the canonical K-major layout without
-//    swizzling: "core matrices" of 8 rows x 16 bytes (8 x 4 TF32 values, 128
-//    contiguous bytes); the descriptor gives the byte distance between core
-//    matrices adjacent along K (leading byte offset) and between 8-row groups
-//    (stride byte offset).  Element (r, k) of a tile with those strides sits at
+//    swizzling: "core matrices" of 8 rows x 16 bytes (8 x 4 TF32 or 8 x 8 BF16
+//    values, 128 contiguous bytes); the descriptor gives the byte distance
+//    between core matrices adjacent along K (leading byte offset) and between
+//    8-row groups (stride byte offset).  Element (r, k) of a 32-bit tile sits at
 //    (r / 8) * sbo + (k / 4) * lbo + (r % 8) * 16 + (k % 4) * 4 bytes.
 //  * D[m][n] = sum_k A[m][k] B[n][k]: both operands K-major, M = 128 rows of A,
-//    N rows of B (a multiple of 16, at most 256), K = 8 per instruction.
+//    N rows of B (a multiple of 16, at most 256), K = 8 (TF32) or 16 (BF16) per
+//    instruction.
 //  * The accumulator of an M = 128 MMA holds row m in TMEM lane m, column n in
 //    TMEM column (base + n); warp w of a four-warp team reads lanes 32w..32w+31
 //    (32x32b shape: thread t of the warp gets lane 32w + t).
 //  * One thread issues the MMAs and commits them to an mbarrier; every thread
 //    waits on the mbarrier's phase, with an iteration limit.
 //
-// Accuracy: a TF32 operand keeps 10 fraction bits.  The products that need
-// FP32 accuracy split each operand x = hi + lo (hi = x rounded to TF32, lo =
-// x - hi exactly) and sum hi*hi + hi*lo + lo*hi in the FP32 accumulator; the
-// dropped lo*lo term and the TF32 rounding of lo are ~2^-22 relative.
+// Accuracy: a TF32 operand keeps 10 fraction bits, a BF16 operand 7.  The
+// products that need FP32 accuracy split each operand into TF32 hi + lo or
+// BF16 hi + mid + lo and keep the terms of each magnitude in an accumulator of
+// their own (small terms added into a large accumulator lose bits to its
+// alignment); tree.cuh: tc_stage_products and tc_stage_products_bf16.
 #pragma once
 #include <stdint.h>
 
