@@ -186,6 +186,41 @@ MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef<T>& st)
     wcopy<NX>([&](int i) { return X::a(st, i); }, [&](int i, T v) { s.e[i] = v; });
 }
 
+// Store the R x C column-major block at src (shared memory, leading dimension
+// LD) to dst (global, leading dimension R), times sgn, keeping only i >= j when
+// LOWER; then tail(k) for k < ntail in the same step.  FP32 blocks of a multiple
+// of four rows go in 16-byte pieces (every column of dst then starts 16-byte
+// aligned, as dst does: the stored blocks are laid out back to back in a 256-byte
+// aligned arena), others element by element.
+template <typename T, int R, int C, int LD, bool LOWER = false, class TF>
+MHE_DEV void store_block(T* dst, const T* src, T sgn, int ntail, TF&& tail)
+{
+    if constexpr (sizeof(T) == 4 && R % 4 == 0 && LD % 4 == 0) {
+        constexpr int NV = R * C / 4;
+        wfor(NV + ntail, [&](int u) {
+            if (u >= NV) {
+                tail(u - NV);
+                return;
+            }
+            const int i = 4 * (u % (R / 4)), j = u / (R / 4);
+            float v[4];
+            ld16(src + i + j * LD, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = (LOWER && i + q < j) ? 0.f : sgn * v[q];
+            st16(dst + i + j * R, v);
+        });
+    } else {
+        wfor(R * C + ntail, [&](int r) {
+            if (r >= R * C) {
+                tail(r - R * C);
+                return;
+            }
+            const int i = r % R, j = r / R;
+            dst[r] = (LOWER && i < j) ? (T)0 : sgn * src[i + j * LD];
+        });
+    }
+}
+
 // In-place lower Cholesky of the M x M matrix Gm (leading dimension ld of the
 // workspace).  Returns true when a pivot fell below piv_rel * max diag (the
 // pivot is then replaced by 1 to stay finite).  Lane i owns row i of the lower
@@ -674,8 +709,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
 {
     constexpr int ld = Ws<T, NX>::ld;
     using X = Acc<T, KIND, NX, MT>;
-    if (Pout)
-        wfor(NX * NX, [&](int idx) { Pout[idx] = s.P[idx % NX + (idx / NX) * ld]; });
+    if (Pout) store_block<T, NX, NX, ld>(Pout, s.P, (T)1, 0, [](int) {});
     load_AB<T, NX, MT, KIND>(s, st);
     bool on_tc = false;
     if constexpr (TC != 0) on_tc = !want_v;
@@ -723,25 +757,17 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
             else s.k[i] = v;
         };
         upper_solve<T, NX, MT, NX + 1>(s, getY, getX, putX);
-        if (Kout || kout)
-            wfor(MT * NX + MT, [&](int r) {
-                if (r < MT * NX) {
-                    if (Kout) Kout[r] = s.K[r % MT + (r / MT) * ld];
-                } else if (kout) {
-                    kout[r - MT * NX] = s.k[r - MT * NX];
-                }
-            });
+        if (Kout)
+            store_block<T, MT, NX, ld>(Kout, s.K, (T)1, kout ? MT : 0, [&](int j) { kout[j] = s.k[j]; });
+        else if (kout)
+            wfor(MT, [&](int j) { kout[j] = s.k[j]; });
     }
     // P -= Y^T Y (symmetric),  Psi = A^T u - l_x + K^T g,  store chol(G)
     wgemm_tn<T, NX, NX, MT, ld, ld, true>([&](int i, int j) { return s.P[i + j * ld]; }, s.PB, s.PB, (T)-1,
                                           [&](int i, int j, T v) { s.P[i + j * ld] = v; s.P[j + i * ld] = v; });
     wgemm_tn<T, NX, 1, MT, ld, 0>([&](int i, int) { return s.tv[i] - X::lx(st, i); }, s.K, s.g, (T)1,
                                   [&](int i, int, T v) { s.Psi[i] = v; });
-    if (Lgout)
-        wfor(MT * MT, [&](int r) {
-            const int i = r % MT, j = r / MT;
-            Lgout[r] = i >= j ? s.G[i + j * ld] : (T)0;
-        });
+    if (Lgout) store_block<T, MT, MT, ld, true>(Lgout, s.G, (T)1, 0, [](int) {});
     if (!want_v) return bad;
     // e = a + B k
     wgemm<T, NX, 1, MT>([&](int i, int) { return s.e[i]; }, [&](int i, int j) { return s.B[i + j * ld]; },
@@ -761,7 +787,7 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
             auto getL = [&](int i, int c) -> T { return s.Tt[i + c * ld]; };
             auto putL = [&](int i, int c, T v) { s.Tt[i + c * ld] = v; };
             upper_solve<T, NX, MT, NX>(s, getZ, getL, putL);
-            wfor(MT * NX, [&](int r) { Lout[r] = -s.Tt[r % MT + (r / MT) * ld]; });
+            store_block<T, MT, NX, ld>(Lout, s.Tt, (T)-1, 0, [](int) {});
         }
     }
     // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z (symmetric)
