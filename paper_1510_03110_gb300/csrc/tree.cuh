@@ -173,16 +173,29 @@ struct Acc {
     static MHE_DEV T a(const StageRef<T>& s, int i) { return s.a ? s.a[i] : (T)0; }
 };
 
-// A -> s.A, B -> s.B, a -> s.e
+// A -> s.A, B -> s.B, a -> s.e.  FP32 blocks stored in memory (leaf and master
+// stages) move in 16-byte pieces when n is a multiple of four: a column of A or
+// B is n contiguous floats, 16-byte aligned (the blocks lie back to back in a
+// 256-byte aligned arena).
 template <typename T, int NX, int MT, int KIND>
 MHE_DEV void load_AB(Ws<T, NX>& s, const StageRef<T>& st)
 {
     constexpr int ld = Ws<T, NX>::ld;
     using X = Acc<T, KIND, NX, MT>;
-    wcopy<NX * NX>([&](int idx) { return X::A(st, idx % NX, idx / NX); },
-                   [&](int idx, T v) { s.A[idx % NX + (idx / NX) * ld] = v; });
-    wcopy<NX * MT>([&](int idx) { return X::B(st, idx % NX, idx / NX); },
-                   [&](int idx, T v) { s.B[idx % NX + (idx / NX) * ld] = v; });
+    if constexpr (sizeof(T) == 4 && NX % 4 == 0 && ld % 4 == 0 && KIND != KIND_ARRIVAL) {
+        constexpr int CA = NX * NX / 4, CB = NX * MT / 4;
+        wcopy<CA + CB>(
+            [&](int u) { return u < CA ? ld16g(st.A + 4 * u) : ld16g(st.B + 4 * (u - CA)); },
+            [&](int u, const F4& v) {
+                const int k = 4 * (u < CA ? u : u - CA);
+                st16((u < CA ? s.A : s.B) + k % NX + (k / NX) * ld, v);
+            });
+    } else {
+        wcopy<NX * NX>([&](int idx) { return X::A(st, idx % NX, idx / NX); },
+                       [&](int idx, T v) { s.A[idx % NX + (idx / NX) * ld] = v; });
+        wcopy<NX * MT>([&](int idx) { return X::B(st, idx % NX, idx / NX); },
+                       [&](int idx, T v) { s.B[idx % NX + (idx / NX) * ld] = v; });
+    }
     wcopy<NX>([&](int i) { return X::a(st, i); }, [&](int i, T v) { s.e[i] = v; });
 }
 

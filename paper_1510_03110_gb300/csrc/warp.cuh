@@ -115,6 +115,19 @@ MHE_DEV void ld16(const double* p, double (&v)[2])
     v[0] = q.x; v[1] = q.y;
 }
 
+// Four floats moved as one 16-byte piece (global or shared memory, 16-byte aligned).
+struct F4 {
+    float v[4];
+};
+MHE_DEV F4 ld16g(const float* p)
+{
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    return F4{{q.x, q.y, q.z, q.w}};
+}
+MHE_DEV void st16(float* p, const F4& x)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+}
 // One 16-byte shared-memory store of 4 words (p 16-byte aligned).
 MHE_DEV void st16u(void* p, const unsigned (&w)[4])
 {
