@@ -1,7 +1,9 @@
 // kernels.cuh -- __global__ wrappers and launchers of the level passes.
 //
-// Launch shape: one warp per chunk, W warps per CTA where W is the number of
-// per-warp shared-memory workspaces that fit in 200 KB (at most 8).
+// Launch shape: one team (MHE_TEAM lanes) per chunk, W teams per CTA where W is
+// the number of per-team shared-memory workspaces that fit in kLevelSmem (at
+// most 256 threads per CTA); the tensor-core reductions take one four-warp team
+// per CTA.
 #pragma once
 #include <cuda_runtime.h>
 

@@ -229,15 +229,6 @@ MHE_DEV bool team_wait(uint64_t* m, uint32_t parity)
     return all;
 }
 
-// shared-memory tiles written by the team (and accumulator reads done) before
-// one thread issues the next MMAs: proxy fence, tensor fence, team barrier
-MHE_DEV void team_publish()
-{
-    fence_smem_to_async();
-    fence_before();
-    wsync();
-}
-
 // every lane runs f (its index in the team), then the tiles it wrote are
 // published to the tensor core: proxy fence, tensor fence, one team barrier
 template <class F>
