@@ -30,8 +30,9 @@ template <int NX, int NW, int NY = 0>
 struct ResidSmem {
     static constexpr int rows = 5 * NX + NW;
     static constexpr int q_form = 3 * rows + 4;                      // resid_rows
-    // pieces of a length-n product in resid_mhe (only when the pieces stay >= 8 long)
-    static constexpr int sp = (NX % NW == 0 && NW >= 8) ? NX / NW : 1;
+    // pieces of a length-n product in resid_mhe: length-nw pieces when nw divides
+    // n and nw >= 3 (every task of the first phase then has one length)
+    static constexpr int sp = (NX % NW == 0 && NW >= 3) ? NX / NW : 1;
     static constexpr int mhe_form = 4 * NX + 3 * NW + 3 * NY + 5 + sp * (2 * NX + NY + NW);   // resid_mhe
     static constexpr int count = q_form > mhe_form ? q_form : mhe_form;   // 8-byte entries
 };
@@ -204,8 +205,9 @@ MHE_DEV void resid_mhe(const ResidArgs<TR>& r, int b, int t, int N, unsigned lon
     });
     // V(p,q) = R[NW+p + (NW+q) NR], S(k,p) = R[k + (NW+p) NR], W(k,j) = R[k + j NR]
     // The length-n dot products (A x, C x, A^T lam, B^T lam) are cut into SP pieces of
-    // length n / SP = nw when nw divides n and nw >= 8, so every task of the phase has
-    // one length (shorter pieces cost more in tasks than they save in idle lanes).
+    // length n / SP = nw when nw divides n and nw >= 3, so every task of the phase has
+    // one length (measured on the batched workload: the step 83.5 -> 82.1 ms when the
+    // nx = 6 and 12 shapes split too).
     constexpr int T1 = NX + NY + NX + NW;                  // length-n dot products
     constexpr int SP = ResidSmem<NX, NW, NY>::sp;          // pieces per length-n product
     constexpr int LP = NX / SP;                            // piece length
