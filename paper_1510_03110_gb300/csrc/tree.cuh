@@ -373,6 +373,39 @@ MHE_DEV void upper_solve(const Ws<T, NX>& s, FR&& rhs, FG&& get, FP&& put)
 }
 
 
+// Y = L^{-1} R and (when upper) X = L^{-T} Y for pivots blocks of at most 16
+// rows: one right-hand-side column per lane, held in registers through both
+// substitutions (the factor read by broadcast from shared memory), so the two
+// solves take one team step instead of a barrier per diagonal block.
+// rhs(i, c) gives R; putY / putX store Y and X.
+template <typename T, int NX, int M, int NC, class FR, class FY, class FX>
+MHE_DEV void col_solves(const Ws<T, NX>& s, bool upper, FR&& rhs, FY&& putY, FX&& putX)
+{
+    static_assert(M <= 16, "a right-hand-side column of at most 16 rows per lane");
+    constexpr int ld = Ws<T, NX>::ld;
+    wfor(NC, [&](int c) {
+        T y[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            T acc = rhs(i, c);
+#pragma unroll
+            for (int p = 0; p < i; ++p) acc -= s.G[i + p * ld] * y[p];
+            y[i] = pivot_div(acc, s.G[i + i * ld]);
+            putY(i, c, y[i]);
+        }
+        if (upper) {
+#pragma unroll
+            for (int i = M - 1; i >= 0; --i) {
+                T acc = y[i];
+#pragma unroll
+                for (int p = i + 1; p < M; ++p) acc -= s.G[p + i * ld] * y[p];
+                y[i] = pivot_div(acc, s.G[i + i * ld]);
+                putX(i, c, y[i]);
+            }
+        }
+    });
+}
+
 // ---- the stage products on the tensor cores (tcgen05, kind::tf32) -------------
 //
 // Tensor state of a team whose stage products run on the tensor cores: TMEM
@@ -763,13 +796,17 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
             if (c < NX) s.PB[i + c * ld] = v;
             else s.tmp[i] = v;
         };
-        lower_solve<T, NX, MT, NX + 1>(s, rhsY, getY, putY);
         auto getX = [&](int i, int c) -> T { return c < NX ? -s.K[i + c * ld] : s.k[i]; };
         auto putX = [&](int i, int c, T v) {
             if (c < NX) s.K[i + c * ld] = -v;
             else s.k[i] = v;
         };
-        upper_solve<T, NX, MT, NX + 1>(s, getY, getX, putX);
+        if constexpr (MT <= 16) {
+            col_solves<T, NX, MT, NX + 1>(s, true, rhsY, putY, putX);
+        } else {
+            lower_solve<T, NX, MT, NX + 1>(s, rhsY, getY, putY);
+            upper_solve<T, NX, MT, NX + 1>(s, getY, getX, putX);
+        }
         if (Kout)
             store_block<T, MT, NX, ld>(Kout, s.K, (T)1, kout ? MT : 0, [&](int j) { kout[j] = s.k[j]; });
         else if (kout)
@@ -795,13 +832,15 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
         auto rhsZ = [&](int i, int c) -> T { return s.H[i + c * ld]; };
         auto getZ = [&](int i, int c) -> T { return s.PB[i + c * ld]; };
         auto putZ = [&](int i, int c, T v) { s.PB[i + c * ld] = v; };
-        lower_solve<T, NX, MT, NX>(s, rhsZ, getZ, putZ);
-        if (Lout) {
-            auto getL = [&](int i, int c) -> T { return s.Tt[i + c * ld]; };
-            auto putL = [&](int i, int c, T v) { s.Tt[i + c * ld] = v; };
-            upper_solve<T, NX, MT, NX>(s, getZ, getL, putL);
-            store_block<T, MT, NX, ld>(Lout, s.Tt, (T)-1, 0, [](int) {});
+        auto getL = [&](int i, int c) -> T { return s.Tt[i + c * ld]; };
+        auto putL = [&](int i, int c, T v) { s.Tt[i + c * ld] = v; };
+        if constexpr (MT <= 16) {
+            col_solves<T, NX, MT, NX>(s, Lout != nullptr, rhsZ, putZ, putL);
+        } else {
+            lower_solve<T, NX, MT, NX>(s, rhsZ, getZ, putZ);
+            if (Lout) upper_solve<T, NX, MT, NX>(s, getZ, getL, putL);
         }
+        if (Lout) store_block<T, MT, NX, ld>(Lout, s.Tt, (T)-1, 0, [](int) {});
     }
     // V_new = A^T V + K^T BV -> Tt;  Q^_w += Z^T Z (symmetric)
     wgemm_tn<T, NX, NX, NX, ld, ld>([&](int, int) { return (T)0; }, s.A, s.V, (T)1,
