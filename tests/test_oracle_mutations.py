@@ -15,6 +15,7 @@ import oracle
 from oracle import core, dense
 from paper_1510_03110_gb300 import synth
 
+from test_golden import as_float, load  # noqa: E402
 from test_oracle import _mhe_cost, random_uftoc, rel  # noqa: E402
 
 SRC = open(core._SRC).read()
@@ -59,6 +60,24 @@ def _mutant(tmpdir, name):
         f.write(SRC.replace(old, new))
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", path_so, path_c, "-lm"])
     return core.load(path_so)
+
+
+# the mistakes that change the Newton step itself (the rest touch only the
+# objective's constant, the residual routine or rounding)
+STEP_CHANGING = ["drop_Qx_in_F", "transpose_A_in_F", "wrong_operand_in_H", "sign_lx_in_Psi",
+                 "sign_Psi_in_lambda", "sign_Qxw_assembly", "sign_lw_assembly"]
+
+
+def _golden_fails(lib_mut) -> bool:
+    """The exact golden step (n = 2, nw = ny = 1, N = 6) against a library."""
+    saved = core._lib
+    core._lib = lib_mut
+    try:
+        pf, sol = as_float(load("mhe_2x1x1_N6_exact"))
+        r = oracle.riccati(oracle.mhe_to_uftoc(pf))
+        return r["status"] != 0 or any(rel(r[k], sol[k]) > 1e-12 for k in ("x", "w", "lam"))
+    finally:
+        core._lib = saved
 
 
 def _pins_fail(lib_mut) -> list:
@@ -106,6 +125,8 @@ def _pins_fail(lib_mut) -> list:
             failed.append("long_horizon")
     finally:
         core._lib = saved
+    if _golden_fails(lib_mut):
+        failed.append("golden")
     return failed
 
 
@@ -116,3 +137,8 @@ def test_unmutated_oracle_passes_all_pins():
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(tmpdir_mod, name):
     assert _pins_fail(_mutant(tmpdir_mod, name)) != []
+
+
+@pytest.mark.parametrize("name", STEP_CHANGING)
+def test_exact_golden_step_alone_catches_step_changing_mistakes(tmpdir_mod, name):
+    assert _golden_fails(_mutant(tmpdir_mod, name))
