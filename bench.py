@@ -746,7 +746,7 @@ def main():
                                   p99=round(ser["p99_ms"] / max(tree["p99_ms"], 1e-9), 3)))))
         return
     if args.gpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
-        # replicas only: every rank solves its own copy of the workload
+        # one GPU does the work: rank 0 runs the workload, the other ranks exit without work
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:
             return
