@@ -732,6 +732,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if int(os.environ.get("RANK", "0")) != 0:
+        # one GPU does the work: rank 0 runs the workload, the other ranks exit without work
+        return
     if args.workload == "serve":
         res = run_serve(args)
         tree, ser = res["tree"], res["serial"]
@@ -745,11 +748,6 @@ def main():
                                   solves_per_s=round(tree["solves_per_s"] / max(ser["solves_per_s"], 1e-9), 3),
                                   p99=round(ser["p99_ms"] / max(tree["p99_ms"], 1e-9), 3)))))
         return
-    if args.gpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
-        # one GPU does the work: rank 0 runs the workload, the other ranks exit without work
-        rank = int(os.environ.get("RANK", "0"))
-        if rank != 0:
-            return
     run_gpu(args)
 
 
