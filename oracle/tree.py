@@ -15,6 +15,14 @@ TEST INFRASTRUCTURE ONLY.  Each step follows the paper in order and notation:
                    wbar_t = -L_{t+1} w^_i (Eq. control_signal_def with the
                    T-form of Eq. parric:Qh_Bh_alternative_def), followed by the
                    costate sweep of the KKT rows.
+Two forms of the reduced input (Theorem 1):
+  'T'   the T-form of Eq. parric:Qh_Bh_alternative_def, Q^_w = B^ = S Qbar^{-1} S^T
+        (input width n; singular G^ when S^T is rank deficient, the remark after it);
+  'U1'  the form of Eq. Bh_def, with U_1 an orthonormal basis of range(S^T):
+        Q^_w = U_1^T Qbar^{-1} U_1, B^ = S Qbar^{-1} U_1 (input width n_uo = rank S^T <= n),
+        and the chunk's inputs wbar = Qbar^{-1} U_1 w^ (the parametrisation of Kbar
+        and kbar that precedes Eq. reducedGK_S).  It stays well posed for chunks with
+        N_s nw < nx, where S^T has fewer than nx independent columns.
 Chunking (the paper leaves batch lengths to the user, Section VI remark):
 all chunks of a level have length L except the last, which takes the
 remainder (1..L stages).
@@ -76,6 +84,43 @@ def reduce_chunk(prob: Uftoc, t0: int, t1: int) -> dict:
                 K=K_l, k=k_l, L=L_l, G=G_l)
 
 
+def s_hat(prob: Uftoc, t0: int, t1: int, red: dict) -> np.ndarray:
+    """S of Eq. B for stages t0..t1-1: column block tau is
+    (A_{t1-1} + B_{t1-1} K_{0,t1}) ... (A_{tau+1} + B_{tau+1} K_{0,tau+2}) B_tau."""
+    n = prob.n
+    blocks = []
+    Phi = np.eye(n)                      # product of the closed-loop matrices after tau
+    for t in range(t1 - 1, t0 - 1, -1):
+        blocks.append(Phi @ prob.B[t])
+        Phi = Phi @ (prob.A[t] + prob.B[t] @ red["K"][t - t0])
+    return np.hstack(blocks[::-1])
+
+
+def qbar_inv(red: dict) -> np.ndarray:
+    """Qbar^{-1}, Qbar = blkdiag(G_{0,t+1}) over the chunk's stages (Eq. QuA)."""
+    Gs = red["G"]
+    dims = [G.shape[0] for G in Gs]
+    Qi = np.zeros((sum(dims), sum(dims)))
+    o = 0
+    for G, d in zip(Gs, dims):
+        Qi[o:o + d, o:o + d] = np.linalg.inv(G)
+        o += d
+    return Qi
+
+
+def reduce_u1(prob: Uftoc, t0: int, t1: int, red: dict) -> dict:
+    """The U_1 form of Theorem 1 (Eq. Bh_def): U_1 = orthonormal basis of range(S^T)
+    from the SVD of S^T (numerical rank with the usual threshold
+    sigma_max * max(shape) * eps), Q^_w = U_1^T Qbar^{-1} U_1, B^ = S Qbar^{-1} U_1."""
+    S = s_hat(prob, t0, t1, red)
+    U, sig, _ = np.linalg.svd(S.T, full_matrices=False)
+    tol = (sig[0] if sig.size else 0.0) * max(S.shape) * np.finfo(float).eps
+    U1 = U[:, :int(np.sum(sig > tol))]
+    Qi = qbar_inv(red)
+    Qw = U1.T @ Qi @ U1
+    return dict(S=S, U1=U1, Qbar_inv=Qi, Qw=0.5 * (Qw + Qw.T), Bhat=S @ Qi @ U1)
+
+
 def sub_problem(prob: Uftoc, t0: int, t1: int, QN=None, lN=None, cN=0.0, x0=None) -> Uftoc:
     """Stages t0..t1-1 of prob as a UFTOC problem (Eq. sub_problem_dscr)."""
     n = prob.n
@@ -94,20 +139,24 @@ def reduce_last(prob: Uftoc, t0: int) -> dict:
     return dict(Qxhat=r["P0"], lxhat=-r["Psi0"], chat=r["cbar0"])
 
 
-def master_problem(prob: Uftoc, reds: list, last: dict) -> Uftoc:
-    """Eq. red_mpc_problem: stage i has A^_i, B^_i, a^_i, Q^_i = blkdiag(Q^_x,i, Q^_w,i)
-    with Q^_w,i = B^_i, l = (l^_x,i, 0), c^_i; terminal (Q^_x,p, l^_x,p, c^_p)."""
+def master_problem(prob: Uftoc, reds: list, last: dict, u1s: list = None) -> Uftoc:
+    """Eq. red_mpc_problem: stage i has A^_i, B^_i, a^_i, Q^_i = blkdiag(Q^_x,i, Q^_w,i),
+    l = (l^_x,i, 0), c^_i; terminal (Q^_x,p, l^_x,p, c^_p).  T-form: Q^_w,i = B^_i
+    (n x n); with u1s (reduce_u1 per chunk): B^_i = S Qbar^{-1} U_1 (n x n_uo,i) and
+    Q^_w,i = U_1^T Qbar^{-1} U_1."""
     n = prob.n
     A, B, a, Q, l, c = [], [], [], [], [], []
-    for r in reds:
+    for i, r in enumerate(reds):
+        Bi, Qw = (r["Bhat"], r["Bhat"]) if u1s is None else (u1s[i]["Bhat"], u1s[i]["Qw"])
+        mi = Bi.shape[1]
         A.append(r["Ahat"])
-        B.append(r["Bhat"])
+        B.append(Bi)
         a.append(r["ahat"])
-        Qi = np.zeros((2 * n, 2 * n))
+        Qi = np.zeros((n + mi, n + mi))
         Qi[:n, :n] = r["Qxhat"]
-        Qi[n:, n:] = r["Bhat"]
+        Qi[n:, n:] = Qw
         Q.append(Qi)
-        l.append(np.concatenate([r["lxhat"], np.zeros(n)]))
+        l.append(np.concatenate([r["lxhat"], np.zeros(mi)]))
         c.append(r["chat"])
     return Uftoc(n, A, B, a, Q, l, c, last["Qxhat"], last["lxhat"], last["chat"],
                  np.asarray(prob.x0, float).copy())
@@ -123,9 +172,10 @@ def chunk_bounds(N: int, L: int) -> list:
 
 
 def tree_solve(prob: Uftoc, leaf_len: int = 4, branching: int = 2, top_len: int = 4,
-               down: str = "backsub", _level: int = 0, _trace=None) -> dict:
+               down: str = "backsub", _level: int = 0, _trace=None, form: str = "T") -> dict:
     """Algorithms 5 + 6.  Returns x (N+1, n), w (list per stage), lam (N+1, n)
-    and, for down='alg6', P and Psi at every stage (from the bottom subproblems)."""
+    and, for down='alg6', P and Psi at every stage (from the bottom subproblems).
+    form: 'T' or 'U1', the reduced input of every master stage (module docstring)."""
     n, N = prob.n, prob.N
     if N <= top_len or N < 2:
         r = riccati(prob, want_all=True)
@@ -142,10 +192,11 @@ def tree_solve(prob: Uftoc, leaf_len: int = 4, branching: int = 2, top_len: int 
     p = len(bnd) - 2                      # chunks 0..p, chunk p is the last one
     reds = [reduce_chunk(prob, bnd[i], bnd[i + 1]) for i in range(p)]
     last = reduce_last(prob, bnd[p])
-    master = master_problem(prob, reds, last)
+    u1s = [reduce_u1(prob, bnd[i], bnd[i + 1], reds[i]) for i in range(p)] if form == "U1" else None
+    master = master_problem(prob, reds, last, u1s)
     if _trace is not None:
         _trace.append(("level", _level, N, bnd))
-    top = tree_solve(master, leaf_len, branching, top_len, down, _level + 1, _trace)
+    top = tree_solve(master, leaf_len, branching, top_len, down, _level + 1, _trace, form)
     xh, wh, lh = top["x"], top["w"], top["lam"]
     x = np.zeros((N + 1, n))
     lam = np.zeros((N + 1, n))
@@ -177,11 +228,18 @@ def tree_solve(prob: Uftoc, leaf_len: int = 4, branching: int = 2, top_len: int 
             # back-substitution with the stored preliminary feedback
             xt = np.asarray(xh[i], float).copy()
             x[t0] = xt
+            if i < p and u1s is not None:
+                # U_1 form: the chunk's inputs wbar = Qbar^{-1} U_1 w^_i, split per stage
+                wbar = u1s[i]["Qbar_inv"] @ (u1s[i]["U1"] @ wh[i])
+                wofs = np.concatenate([[0], np.cumsum([prob.B[t].shape[1] for t in range(t0, t1)])])
             for t in range(t0, t1):
                 A, B, a = prob.A[t], prob.B[t], prob.a[t]
                 if i < p:
                     j = t - t0
-                    wt = reds[i]["k"][j] + reds[i]["K"][j] @ xt - reds[i]["L"][j] @ wh[i]
+                    if u1s is None:
+                        wt = reds[i]["k"][j] + reds[i]["K"][j] @ xt - reds[i]["L"][j] @ wh[i]
+                    else:
+                        wt = reds[i]["k"][j] + reds[i]["K"][j] @ xt + wbar[wofs[j]:wofs[j + 1]]
                 else:
                     wt = None
                 if wt is None:

@@ -9,7 +9,8 @@ tests/golden/make_golden.py, which uses neither the oracle nor the CUDA path).
   e = [w - w~; y~ - C x], by exact central differences; the stored cost is
   the MHE cost at the stored point.
 * The oracle (stage assembly + Algorithms 1-3, the dense LU solve, and the
-  tree of Algorithms 4-6 over several plans) reproduces it to rounding.
+  tree of Algorithms 4-6 over several plans, in the T-form and, with leaf
+  chunks shorter than nx / nw, in the U_1 form) reproduces it to rounding.
 * On the GPU, the CUDA path through the C-ABI reproduces it.
 """
 import importlib.util
@@ -140,12 +141,13 @@ def test_oracle_reproduces_the_exact_step(name):
     d = dense.solve(u)
     for k in ("x", "w", "lam"):
         assert _rel(d[k], sol[k]) <= 1e-13, k
-    for leaf, br, top in [(2, 2, 1), (3, 2, 2), (4, 3, 2)]:
+    plans = [(max(2, p["n"]), 2, 1, "T"), (3, 2, 2, "T"), (4, 3, 2, "T"), (1, 2, 1, "U1"), (2, 3, 1, "U1")]
+    for leaf, br, top, form in plans:      # leaf_len 1 with nw = 1 < nx: only the U_1 form
         for down in ("backsub", "alg6"):
-            t = tree.tree_solve(u, leaf_len=max(leaf, p["n"]), branching=br, top_len=top, down=down)
-            assert _rel(t["x"], sol["x"]) <= 1e-12, (leaf, br, top, down)
-            assert _rel(np.concatenate(t["w"]), sol["w"]) <= 1e-12, (leaf, br, top, down)
-            assert _rel(t["lam"], sol["lam"]) <= 1e-12, (leaf, br, top, down)
+            t = tree.tree_solve(u, leaf_len=leaf, branching=br, top_len=top, down=down, form=form)
+            assert _rel(t["x"], sol["x"]) <= 1e-12, (leaf, br, top, down, form)
+            assert _rel(np.concatenate(t["w"]), sol["w"]) <= 1e-12, (leaf, br, top, down, form)
+            assert _rel(t["lam"], sol["lam"]) <= 1e-12, (leaf, br, top, down, form)
 
 
 @pytest.mark.gpu

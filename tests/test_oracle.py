@@ -237,6 +237,9 @@ def test_alg4_matches_closed_forms(n, m, L):
     for t in range(L):
         assert rel(red["K"][t], K0[t]) < 1e-8
         assert rel(red["k"][t], k0[t]) < 1e-8
+    # the U_1 form's building blocks: S of Eq. B and Qbar^{-1} from Algorithm 4's stored factors
+    assert rel(tree.s_hat(p, 0, L, red), S) < 1e-10
+    assert rel(tree.qbar_inv(red), np.linalg.inv(Qbar)) < 1e-10
 
 
 @pytest.mark.parametrize("n,m,L", [(4, 2, 2), (4, 2, 5), (3, 3, 3), (5, 1, 6)])
@@ -265,6 +268,51 @@ def test_theorem1_reduced_problem_is_equivalent(n, m, L):
         assert rel(rr["x"][1], full["x"][L]) < 1e-9
         # and the multiplier of the boundary state is the same
         assert rel(rr["lam"][1], full["lam"][L]) < 1e-8
+
+
+@pytest.mark.parametrize("n,m,L", [(4, 2, 3), (6, 1, 2), (5, 1, 1), (3, 3, 2), (6, 2, 2)])
+def test_theorem1_u1_form(n, m, L):
+    """Theorem 1 in the form of Eq. Bh_def: U_1 is an orthonormal basis of range(S^T)
+    with n_uo = rank S^T = min(n, L m) columns; the reduced problem (horizon 1,
+    input w^ in R^{n_uo}, Q^_w = U_1^T Qbar^{-1} U_1, B^ = S Qbar^{-1} U_1) has, for
+    any terminal cost, the chunk's optimal value, final state and boundary
+    multiplier, and wbar = Qbar^{-1} U_1 w^ in w_t = k_{0,t+1} + K_{0,t+1} x_t + wbar_t
+    (Eq. control_signal_def) gives back the chunk's inputs.  With L m < n the
+    T-form's Q^_w = S Qbar^{-1} S^T has rank L m < n (the remark after Eq.
+    Qh_Bh_alternative_def: its G^ is singular) while the U_1 form stays well posed."""
+    p = random_uftoc(51 + n * L + m, n, L, [m], terminal=False)
+    red = tree.reduce_chunk(p, 0, L)
+    u1 = tree.reduce_u1(p, 0, L, red)
+    U1, S, r = u1["U1"], u1["S"], min(n, L * m)
+    assert U1.shape == (L * m, r)
+    assert np.abs(U1.T @ U1 - np.eye(r)).max() < 1e-12
+    assert rel(U1 @ (U1.T @ S.T), S.T) < 1e-12
+    assert np.linalg.matrix_rank(red["Bhat"]) == r
+    assert np.linalg.eigvalsh(u1["Qw"]).min() > 0
+    rng = np.random.default_rng(n + 7 * L + m)
+    for _ in range(3):
+        M = rng.standard_normal((n, n))
+        Ph, Psih, ch = M @ M.T, rng.standard_normal(n), -0.2
+        x0 = rng.standard_normal(n)
+        sp = tree.sub_problem(p, 0, L, Ph, -Psih, ch, x0)
+        full = oracle.riccati(sp)
+        Qr = np.zeros((n + r, n + r))
+        Qr[:n, :n] = red["Qxhat"]
+        Qr[n:, n:] = u1["Qw"]
+        rp = Uftoc(n, [red["Ahat"]], [u1["Bhat"]], [red["ahat"]], [Qr],
+                   [np.concatenate([red["lxhat"], np.zeros(r)])], [red["chat"]], Ph, -Psih, ch, x0)
+        rr = oracle.riccati(rp)
+        assert rr["status"] == 0
+        vf = oracle.objective(sp, full["x"], full["w"])
+        assert oracle.objective(rp, rr["x"], rr["w"]) == pytest.approx(vf, rel=1e-9)
+        assert rel(rr["x"][1], full["x"][L]) < 1e-9
+        assert rel(rr["lam"][1], full["lam"][L]) < 1e-8
+        wbar = u1["Qbar_inv"] @ (U1 @ rr["w"])
+        xt = x0.copy()
+        for t in range(L):
+            wt = red["k"][t] + red["K"][t] @ xt + wbar[t * m:(t + 1) * m]
+            assert rel(wt, full["w"][t * m:(t + 1) * m]) < 1e-8, t
+            xt = p.A[t] @ xt + p.B[t] @ wt + p.a[t]
 
 
 def test_master_problem_boundary_states_by_lu():
@@ -311,6 +359,25 @@ def test_tree_invariance_generic_terminal(N):
         assert rel(t["x"], r["x"]) < 1e-9
         assert rel(np.concatenate(t["w"]), r["w"]) < 1e-9
         assert rel(t["lam"], r["lam"]) < 1e-9
+
+
+U1_TREES = [(6, 1, 2, 2, 2), (6, 1, 3, 2, 1), (5, 1, 1, 2, 1), (3, 1, 1, 3, 1), (4, 2, 4, 3, 2), (6, 3, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("n,m,leaf,br,top", U1_TREES)
+@pytest.mark.parametrize("down", ["backsub", "alg6"])
+def test_tree_u1_form_solves_short_chunks(n, m, leaf, br, top, down):
+    """Algorithms 5-6 with every master stage in the U_1 form equal the serial
+    solution, including plans whose leaf chunks are too short for the T-form
+    (leaf_len * nw < nx: S^T rank deficient, G^ singular)."""
+    p = synth.mhe_instance(7, n, m, m, 40)
+    u = oracle.mhe_to_uftoc(p)
+    r = oracle.riccati(u)
+    t = tree.tree_solve(u, leaf, br, top, down, form="U1")
+    assert t["levels"] >= 1
+    assert rel(t["x"], r["x"]) < 1e-9
+    assert rel(np.concatenate(t["w"]), r["w"]) < 1e-9
+    assert rel(t["lam"], r["lam"]) < 1e-9
 
 
 def test_backsubstitution_equals_literal_alg6():

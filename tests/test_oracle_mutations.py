@@ -142,3 +142,37 @@ def test_planted_mistake_is_caught(tmpdir_mod, name):
 @pytest.mark.parametrize("name", STEP_CHANGING)
 def test_exact_golden_step_alone_catches_step_changing_mistakes(tmpdir_mod, name):
     assert _golden_fails(_mutant(tmpdir_mod, name))
+
+
+# Planted mistakes in the U_1 form of the reduction (Eq. Bh_def), made in a
+# wrapper around the oracle's reduce_u1: each must fail the U_1 tree pin.
+U1_MUTATIONS = {
+    # B^ = S U_1 (Qbar^{-1} dropped)
+    "u1_drop_qbar_in_Bhat": lambda d: dict(d, Bhat=d["S"] @ d["U1"]),
+    # Q^_w = I (U_1 taken as Qbar^{-1}-orthonormal)
+    "u1_Qw_identity": lambda d: dict(d, Qw=np.eye(d["Qw"].shape[0])),
+    # wbar = U_1 w^ (Qbar^{-1} dropped in the chunk's inputs)
+    "u1_wbar_without_qbar": lambda d: dict(d, Qbar_inv=np.eye(d["Qbar_inv"].shape[0])),
+    # Q^_w = 2 U_1^T Qbar^{-1} U_1 (the reduced input's cost scaled, e.g. a dropped 1/2)
+    "u1_Qw_scaled": lambda d: dict(d, Qw=2.0 * d["Qw"]),
+}
+
+
+def _u1_pins_fail():
+    from oracle import tree
+    u = oracle.mhe_to_uftoc(synth.mhe_instance(7, 6, 1, 1, 40))
+    r = oracle.riccati(u)
+    t = tree.tree_solve(u, 2, 2, 2, "backsub", form="U1")
+    return rel(t["x"], r["x"]) > 1e-9 or rel(np.concatenate(t["w"]), r["w"]) > 1e-9 or rel(t["lam"], r["lam"]) > 1e-9
+
+
+def test_unmutated_u1_form_passes():
+    assert not _u1_pins_fail()
+
+
+@pytest.mark.parametrize("name", sorted(U1_MUTATIONS))
+def test_planted_u1_mistake_is_caught(monkeypatch, name):
+    from oracle import tree
+    good = tree.reduce_u1
+    monkeypatch.setattr(tree, "reduce_u1", lambda *a: U1_MUTATIONS[name](good(*a)))
+    assert _u1_pins_fail()
