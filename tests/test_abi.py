@@ -28,6 +28,21 @@ def test_header_symbols_are_exported(L):
         assert hasattr(L, n), n
 
 
+def test_binding_declares_every_signature(L):
+    """Every function of the header has argtypes (as many as the declaration has
+    parameters) and a restype in the binding, so no 64-bit pointer or size is
+    passed through ctypes' default int conversion."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mhe.h")).read(), flags=re.S)
+    decls = re.findall(r"\b(mhe_[a-z_0-9]+)\s*\(([^()]*)\)\s*;", txt)
+    assert len(decls) == len(declared())
+    for name, params in decls:
+        params = params.strip()
+        count = 0 if params in ("", "void") else params.count(",") + 1
+        fn = getattr(L, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == count, (name, count, fn.argtypes)
+        assert fn.restype is not None, name
+
+
 def test_shapes_listed(L):
     s = mhe.shapes()
     for need in [(4, 2), (6, 3), (12, 6), (20, 10), (24, 12)]:
