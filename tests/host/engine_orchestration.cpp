@@ -10,7 +10,11 @@
 //   refinement -- each correction is a residual, a right-hand-side pass up and
 //     a down pass down on the compact correction layout with the active mask,
 //     and a final residual closes the solve;
-// plus the host-side argument and state errors, and the launch counter.
+// the MHE-form entry (one preparation pass, or the FP64 assembly, then the
+// reduction with the right-hand side inside and residuals in the MHE form), a
+// serving context re-planned for a new batch (uploaded tree and offsets, grown
+// workspace, resident problem), the host-side argument and state errors, and
+// the launch counter.
 // Prints "OK" and exits 0, or prints the first failed check and exits 1.
 #include <stdio.h>
 #include <stdlib.h>
@@ -121,6 +125,26 @@ void rhs32(const LevelArgs<float>& g, int u, void*) { rec_level("rhs", g, u); }
 void down32(const LevelArgs<float>& g, int u, void*) { rec_level("down", g, u); }
 void resid64(const ResidArgs<double>& a, void*) { rec_resid(a); }
 void resid32(const ResidArgs<float>& a, void*) { rec_resid(a); }
+void resid_mhe32(const ResidArgs<float>& a, void*)
+{
+    rec_resid(a);
+    g_log.back().op = a.C ? "resid_mhe" : "resid_mhe_without_C";
+}
+void prep32(const PrepArgs& pa, void*)
+{
+    Rec r;
+    r.op = "prep";
+    r.l = pa.l32; r.A = pa.A32; r.Q = pa.Q32;
+    g_log.push_back(r);
+}
+void assemble(long long, const double*, const double*, const double*, const double*, double* Q, double* l, double*,
+              void*)
+{
+    Rec r;
+    r.op = "assemble";
+    r.Q = Q; r.l = l;
+    g_log.push_back(r);
+}
 void knorm(const KnormArgs&, void*)
 {
     Rec r;
@@ -136,7 +160,8 @@ ShapeOps make_ops(int nx, int nw, bool tc)
     o.reduce64 = red64; o.rhs64 = rhs64; o.down64 = down64;
     o.reduce32 = red32; o.reduce32tc = tc ? red32tc : nullptr; o.reduce32bf = nullptr;
     o.rhs32 = rhs32; o.down32 = down32;
-    o.resid64 = resid64; o.resid32 = resid32; o.resid_mhe32 = resid32; o.knorm = knorm;
+    o.resid64 = resid64; o.resid32 = resid32; o.resid_mhe32 = resid_mhe32; o.knorm = knorm;
+    o.prep32 = prep32; o.assemble = assemble;
     return o;
 }
 
@@ -233,7 +258,7 @@ long long counted_launches()
     long long c = 0;
     for (const Rec& r : g_log) {
         if (r.op == "reduce" || r.op == "reduce_tc" || r.op == "rhs" || r.op == "down") c += r.nchunks > 0;
-        else c += 1;   // knorm, convert, resid, finalize
+        else c += 1;   // knorm, convert, resid, finalize, prep, assemble
     }
     return c;
 }
@@ -401,6 +426,98 @@ void scenario_errors()
     CHECK(e3.init(d, &ops, &kFakeRuntime, nullptr) == MHE_E_ARG, "a leaf too short for the T-form reduction");
 }
 
+// Steps a0..a7 from MHE data: FP32 -- one preparation pass, the reduction with the
+// right-hand side inside, the fused solve, every residual in the MHE form; FP64 --
+// the assembly into the internal Q, l, then factor and fused solve on them
+void scenario_estimate()
+{
+    Problem p(4, 2, {30, 65});
+    std::vector<double> C(2 * 4 * 93 + 1), Rm(16 * 93 + 1), yt(2 * 93 + 1), wt(2 * 93 + 1);
+    mhe_problem mp;
+    mp.ny = 2; mp.A = p.A.data(); mp.B = p.B.data(); mp.C = C.data(); mp.R = Rm.data(); mp.a = p.a.data();
+    mp.yt = yt.data(); mp.wt = wt.data(); mp.x0 = p.x0.data(); mp.P0inv = p.P0.data();
+    ShapeOps ops = make_ops(4, 2, false);
+    {
+        Engine e;
+        mhe_dims d = dims_of(p, MHE_FP32_IR, 4, 2, 2, 2);
+        CHECK(e.init(d, &ops, &kFakeRuntime, nullptr) == MHE_OK, "init: %s", e.err.c_str());
+        g_log.clear();
+        g_converge_after = 1;
+        CHECK(e.estimate(mp, p.x.data(), p.w.data(), p.lam.data(), p.info.data()) == MHE_OK, "estimate: %s",
+              e.err.c_str());
+        CHECK(g_log[0].op == "prep" && of("prep").size() == 1, "one preparation pass first");
+        CHECK(of("convert").empty() && of("knorm").empty(), "the preparation pass replaces the copies and ||K||");
+        check_reduce_chain(e, of("reduce"), true);
+        if (g_fail) return;
+        CHECK(of("reduce")[0].A == (const void*)e.A32 && of("reduce")[0].l == (const void*)e.l32,
+              "the reduction reads the prepared FP32 copies");
+        const size_t first_resid = find_from("resid_mhe", 0);
+        CHECK(of("rhs", 0, first_resid).empty(), "the first solve is fused into the reduction");
+        check_down_chain(e, of("down", 0, first_resid), e.dx, p.x.data(), nullptr, e.in_off);
+        CHECK(of("resid").empty() && of("resid_mhe_without_C").empty() && of("resid_mhe").size() == 3,
+              "every residual of the estimate is in the MHE form (2 corrections + the final one)");
+        CHECK(e.launches == counted_launches(), "launch counter");
+        e.release();
+    }
+    {
+        Engine e;
+        mhe_dims d = dims_of(p, MHE_FP64, 4, 2, 2, 0);
+        CHECK(e.init(d, &ops, &kFakeRuntime, nullptr) == MHE_OK, "init: %s", e.err.c_str());
+        g_log.clear();
+        CHECK(e.estimate(mp, p.x.data(), p.w.data(), p.lam.data(), p.info.data()) == MHE_OK, "estimate: %s",
+              e.err.c_str());
+        CHECK(g_log[0].op == "assemble" && g_log[0].Q == (const void*)e.Q64 && g_log[0].l == (const void*)e.l64,
+              "FP64: the stage assembly into the internal Q and l first");
+        check_reduce_chain(e, of("reduce"), true);
+        if (g_fail) return;
+        CHECK(of("reduce")[0].Q == (const void*)e.Q64 && of("reduce")[0].l == (const void*)e.l64,
+              "the FP64 reduction reads the assembled Q and l");
+        check_down_chain(e, of("down"), p.x.data(), nullptr, nullptr, e.in_off);
+        CHECK(e.launches == counted_launches(), "launch counter");
+        mp.ny = 3;
+        CHECK(e.estimate(mp, p.x.data(), p.w.data(), p.lam.data(), p.info.data()) == MHE_E_ARG, "ny not compiled");
+        e.release();
+    }
+}
+
+// Serving: a context re-planned for a new batch uploads the new tree, grows
+// its workspace when needed, and factors and solves a resident problem
+void scenario_replan()
+{
+    Problem p(4, 2, {10, 20});
+    ShapeOps ops = make_ops(4, 2, false);
+    Engine e;
+    mhe_dims d = dims_of(p, MHE_FP32_IR, 4, 2, 2, 1);
+    CHECK(e.init(d, &ops, &kFakeRuntime, nullptr) == MHE_OK, "init");
+    const size_t before = e.arena_bytes;
+    Problem q(4, 2, {50, 7, 90});
+    std::vector<long long> offs = {5, 0, 300};   // any offsets into the resident arrays
+    CHECK(e.replan(q.N.data(), q.batch, offs.data()) == MHE_OK, "replan: %s", e.err.c_str());
+    CHECK(e.arena_bytes > before, "the workspace grew for the larger batch");
+    CHECK(!e.factored, "a re-planned context must be factored again");
+    std::vector<long long> got(3);
+    memcpy(got.data(), e.in_off, sizeof(long long) * 3);
+    CHECK(got == offs, "the custom stage offsets are uploaded");
+    Resident r;
+    memset(&r, 0, sizeof(r));
+    r.A = q.A.data(); r.B = q.B.data(); r.Q = q.Q.data(); r.P0inv = q.P0.data(); r.l = q.l.data();
+    r.a = q.a.data(); r.x0 = q.x0.data();
+    std::vector<float> At(q.A.size()), Bt(q.B.size()), Qt(q.Q.size()), P0t(q.P0.size()), lt(q.l.size()),
+        at(q.a.size()), x0t(q.x0.size());
+    r.At = At.data(); r.Bt = Bt.data(); r.Qt = Qt.data(); r.P0t = P0t.data(); r.lt = lt.data(); r.at = at.data();
+    r.x0t = x0t.data();
+    g_log.clear();
+    CHECK(e.solve_resident(r, q.x.data(), q.w.data(), q.lam.data(), q.info.data()) == MHE_OK, "solve_resident");
+    CHECK(g_log[0].op == "knorm", "||K|| of the resident problem first");
+    check_reduce_chain(e, of("reduce"), true);
+    if (g_fail) return;
+    CHECK(of("reduce")[0].A == (const void*)At.data() && of("reduce")[0].l == (const void*)lt.data(),
+          "the resident FP32 copies feed the reduction");
+    const size_t first_resid = find_from("resid", 0);
+    check_down_chain(e, of("down", 0, first_resid), e.dx, q.x.data(), nullptr, e.in_off);
+    e.release();
+}
+
 }  // namespace
 
 int main()
@@ -409,6 +526,8 @@ int main()
     if (!g_fail) scenario_fp64_fused();
     if (!g_fail) scenario_tensor_precision();
     if (!g_fail) scenario_errors();
+    if (!g_fail) scenario_estimate();
+    if (!g_fail) scenario_replan();
     if (g_fail) return 1;
     printf("OK\n");
     return 0;

@@ -4,8 +4,8 @@ table of host memory and a kernel table that records launches.  It checks the
 order and data flow of Algorithm 5 (reduce level 0 up, each level reading the
 master data the level below wrote), Algorithm 6 (down pass top level first,
 each level reading the solution of the level above) and of the refinement
-loop, plus the host-side errors.  Planted mistakes in a copy of engine.cpp
-must each make it fail."""
+loop, the MHE-form entry and a re-planned serving context, plus the host-side
+errors.  Planted mistakes in a copy of engine.cpp must each make it fail."""
 import os
 import shutil
 import subprocess
@@ -40,6 +40,10 @@ MUTATIONS = {
     # corrections read in the caller's layout instead of the compact one
     "corrections_in_input_layout": ("        rhs_compact = true;\n        pass_rhs<T>(crl, cra, crl0, cra0, crlN);",
                                     "        rhs_compact = false;\n        pass_rhs<T>(crl, cra, crl0, cra0, crlN);"),
+    # the MHE-form estimate's residual loses its factors C, R (would read the unformed Q)
+    "estimate_residual_without_C": ("    mheC = p.C; mheR = p.R;", "    mheC = nullptr; mheR = p.R;"),
+    # a re-planned serving batch ignores the resident stage offsets
+    "replan_drops_offsets": ("    if (in_off_custom) p.in_off.assign(in_off_custom, in_off_custom + batch);\n", ""),
     # the corrections lose the active mask
     "refinement_without_mask": ("        active_mask = active;\n        rhs_compact = true;",
                                 "        active_mask = nullptr;\n        rhs_compact = true;"),
