@@ -139,6 +139,37 @@ def test_scalar_closed_form():
     assert r["lam"][0, 0] == pytest.approx(lam0, rel=1e-13)
 
 
+@pytest.mark.parametrize("n,N", [(1, 1), (3, 5), (4, 40)])
+def test_integrator_special_case(n, N):
+    """A_t = B_t = I, Q_xw = 0, Q_x = q_x I, Q_w = q_w I, Q_x,N = q_N I, no linear
+    terms: every P_t of Algorithm 1 is p_t I with the scalar recursion
+    p_t = q_x + q_w p_{t+1} / (q_w + p_{t+1}), p_N = q_N (eliminating w_t by hand),
+    and the closed-loop state is x_{t+1} = q_w / (q_w + p_{t+1}) x_t.  The tree
+    reproduces it."""
+    qx, qw, qN = 0.7, 1.9, 2.5
+    I = np.eye(n)
+    Q = np.block([[qx * I, np.zeros((n, n))], [np.zeros((n, n)), qw * I]])
+    x0 = np.linspace(1.0, -1.0, n)
+    p = Uftoc(n, [I] * N, [I] * N, [np.zeros(n)] * N, [Q] * N, [np.zeros(2 * n)] * N, [0.0] * N,
+              qN * I, np.zeros(n), 0.0, x0)
+    r = oracle.riccati(p, want_all=True)
+    assert r["status"] == 0
+    pt = [0.0] * (N + 1)
+    pt[N] = qN
+    for t in range(N - 1, -1, -1):
+        pt[t] = qx + qw * pt[t + 1] / (qw + pt[t + 1])
+    for t in range(N + 1):
+        assert np.abs(r["P"][t] - pt[t] * I).max() <= 1e-14 * pt[t]
+    x = x0.copy()
+    for t in range(N):
+        assert rel(r["x"][t], x) < 1e-13
+        x = qw / (qw + pt[t + 1]) * x
+    assert rel(r["x"][N], x) < 1e-13
+    if N >= 4:
+        t = tree.tree_solve(p, 2, 2, 2, "backsub")
+        assert rel(t["x"], r["x"]) < 1e-12 and rel(t["lam"], r["lam"]) < 1e-12
+
+
 def _mhe_cost(p, xm, wm):
     """Eq. org_mhe evaluated directly: arrival cost plus the weighted process and
     sensor noise, with v_k eliminated through y~_k = C_k x_k + (v_k - v~_k)."""
