@@ -411,6 +411,83 @@ def test_tree_u1_form_solves_short_chunks(n, m, leaf, br, top, down):
     assert rel(t["lam"], r["lam"]) < 1e-9
 
 
+def _pivoted_cholesky(M, rtol=1e-10):
+    """M = Pi R^T R Pi^T with R = [R11 R12] (r x n, R11 upper triangular), r the
+    number of pivots above rtol * max diag; returns (perm, R)."""
+    M = np.array(M, float)
+    n = M.shape[0]
+    perm = np.arange(n)
+    R = np.zeros((n, n))
+    thr = rtol * max(np.max(np.diag(M)), 1e-300)
+    r = 0
+    for j in range(n):
+        i = j + int(np.argmax(np.diag(M)[j:]))
+        if M[i, i] <= thr:
+            break
+        M[[j, i], :] = M[[i, j], :]
+        M[:, [j, i]] = M[:, [i, j]]
+        R[:, [j, i]] = R[:, [i, j]]
+        perm[[j, i]] = perm[[i, j]]
+        R[j, j] = np.sqrt(M[j, j])
+        R[j, j + 1:] = M[j, j + 1:] / R[j, j]
+        M[j + 1:, j + 1:] -= np.outer(R[j, j + 1:], R[j, j + 1:])
+        r += 1
+    return perm, R[:r]
+
+
+@pytest.mark.parametrize("n,m,L", [(6, 1, 2), (5, 1, 3), (4, 2, 2), (6, 2, 2)])
+def test_pivoted_square_root_basis_gives_the_same_step(n, m, L):
+    """Theorem 1 holds for any basis of range(S^T), not only an orthonormal one:
+    with the T-form's Q^_w = S Qbar^{-1} S^T factored by a pivoted Cholesky,
+    Pi^T Q^_w Pi = R^T R, R = [R11 R12] of rank r = min(n, L nw), the master stage
+    B = Pi R^T (n x r), Q_w = I_r and, in the down pass, w^ = Pi [R11^{-1} w^'; 0]
+    before wbar_t = -L_{t+1} w^ give the serial solution -- also for
+    L nw < n, where the T-form's master G is singular.  (The square-root master
+    stage of the CUDA path is the full-rank case, Pi = I.)"""
+    q = synth.mhe_instance(11 + n + L, n, m, m, 7 * L + 3)
+    u = oracle.mhe_to_uftoc(q)
+    ref = oracle.riccati(u)
+    bnd = tree.chunk_bounds(u.N, L)
+    p = len(bnd) - 2
+    reds = [tree.reduce_chunk(u, bnd[i], bnd[i + 1]) for i in range(p)]
+    last = tree.reduce_last(u, bnd[p])
+    A, B, a, Q, lv, c, facs = [], [], [], [], [], [], []
+    for i, r in enumerate(reds):
+        perm, R = _pivoted_cholesky(r["Bhat"])
+        rank = R.shape[0]
+        assert rank == (n if i == 0 else min(n, (bnd[i + 1] - bnd[i]) * m))   # chunk 0 holds the arrival stage
+        Pi = np.eye(n)[:, perm]
+        assert np.abs(Pi @ R.T @ R @ Pi.T - r["Bhat"]).max() <= 1e-10 * np.abs(r["Bhat"]).max()
+        facs.append((Pi, R))
+        A.append(r["Ahat"])
+        B.append(Pi @ R.T)
+        a.append(r["ahat"])
+        Qi = np.zeros((n + rank, n + rank))
+        Qi[:n, :n] = r["Qxhat"]
+        Qi[n:, n:] = np.eye(rank)
+        Q.append(Qi)
+        lv.append(np.concatenate([r["lxhat"], np.zeros(rank)]))
+        c.append(0.0)
+    master = Uftoc(n, A, B, a, Q, lv, c, last["Qxhat"], last["lxhat"], 0.0, u.x0)
+    mr = oracle.riccati(master)
+    assert mr["status"] == 0
+    wo = np.concatenate([[0], np.cumsum(master.m)])
+    for i in range(p):
+        Pi, R = facs[i]
+        rank = R.shape[0]
+        wp = mr["w"][wo[i]:wo[i + 1]]
+        wT = Pi @ np.concatenate([np.linalg.solve(R[:, :rank], wp), np.zeros(n - rank)])
+        xt = mr["x"][i].copy()
+        assert rel(xt, ref["x"][bnd[i]]) < 1e-9
+        for t in range(bnd[i], bnd[i + 1]):
+            j = t - bnd[i]
+            wt = reds[i]["k"][j] + reds[i]["K"][j] @ xt - reds[i]["L"][j] @ wT
+            woff = int(np.sum([u.m[s] for s in range(t)]))
+            assert rel(wt, ref["w"][woff:woff + u.m[t]]) < 1e-8, (i, t)
+            xt = u.A[t] @ xt + u.B[t] @ wt + u.a[t]
+        assert rel(xt, ref["x"][bnd[i + 1]]) < 1e-9
+
+
 def test_backsubstitution_equals_literal_alg6():
     p = synth.mhe_instance(4, 3, 2, 2, 50)
     u = oracle.mhe_to_uftoc(p)
