@@ -147,8 +147,9 @@ def _ptr(t):
     if t is None:
         return None
     import torch
-    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), \
-        "expected a contiguous float64 CUDA tensor"
+    # checked always (not by assert): a host pointer handed to the kernels would fault the GPU
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -215,10 +216,12 @@ def _hptr(t):
     if t is None:
         return None
     if isinstance(t, np.ndarray):
-        assert t.dtype == np.float64 and t.flags["C_CONTIGUOUS"], "expected a contiguous float64 array"
+        if not (t.dtype == np.float64 and t.flags["C_CONTIGUOUS"]):
+            raise TypeError("expected a contiguous float64 array")
         return ctypes.c_void_p(t.ctypes.data)
-    assert (not t.is_cuda) and str(t.dtype) == "torch.float64" and t.is_contiguous(), \
-        "expected a contiguous float64 CPU tensor"
+    import torch
+    if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CPU tensor or numpy array")
     return ctypes.c_void_p(t.data_ptr())
 
 

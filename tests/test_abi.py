@@ -101,3 +101,23 @@ def test_tensor_core_precisions_share_the_fp32_workspace(L):
     assert mhe.mhe_workspace_bytes(dtf) == mhe.mhe_workspace_bytes(d32) > 0
     assert mhe.mhe_workspace_bytes(dbf) == mhe.mhe_workspace_bytes(d32)
     assert mhe.mhe_workspace_bytes(dno) == 0
+
+
+def test_pointer_checks_raise_without_asserts():
+    """The binding's pointer checks are real checks (they survive python -O): a
+    host tensor where a device pointer is expected, or the wrong dtype or
+    layout, raises TypeError before anything reaches the library."""
+    import numpy as np
+    import torch
+    with pytest.raises(TypeError):
+        mhe._ptr(torch.zeros(4, dtype=torch.float64))          # host memory
+    with pytest.raises(TypeError):
+        mhe._ptr(np.zeros(4))
+    with pytest.raises(TypeError):
+        mhe._hptr(np.zeros(4, dtype=np.float32))
+    with pytest.raises(TypeError):
+        mhe._hptr(np.zeros((4, 4))[:, 1])                      # not contiguous
+    with pytest.raises(TypeError):
+        mhe._hptr(torch.zeros(4, dtype=torch.float32))
+    assert mhe._hptr(np.zeros(4)) is not None and mhe._hptr(torch.zeros(4, dtype=torch.float64)) is not None
+    assert mhe._ptr(None) is None and mhe._hptr(None) is None
