@@ -308,6 +308,40 @@ def info_array(t):
     return t.cpu().numpy().view(INFO_DTYPE)
 
 
+class SizeError(MheError, ValueError):
+    """An argument array shorter than the problem's layout needs (MHE_E_ARG,
+    raised by the binding before the call)."""
+
+    def __init__(self, msg):
+        RuntimeError.__init__(self, f"MHE_E_ARG: {msg}")
+        self.code = -1
+
+
+def _need(t, count, name):
+    """Raise SizeError unless tensor/array t holds at least `count` elements (the
+    library takes raw pointers and cannot check: a short buffer would be read or
+    written past its end on the GPU).  None is left to the library, which reports
+    a NULL pointer as MHE_E_ARG."""
+    if t is None:
+        return
+    have = int(t.numel()) if hasattr(t, "numel") else int(np.asarray(t).size)
+    if have < count:
+        raise SizeError(f"{name} holds {have} elements; this problem needs {count}")
+
+
+def check_sizes(nx, nw, S, batch, X, W, ny=None, **arrays):
+    """Element counts of the batch's arrays against the layout of include/mhe.h:
+    S caller stages, batch instances, X states (sum of N_b + 1), W inputs
+    (sum of nx + (N_b - 1) nw); ny for the MHE-form arrays C, R, yt, wt."""
+    nq = nx + nw
+    need = dict(A=S * nx * nx, B=S * nx * nw, Q=S * nq * nq, P0inv=batch * nx * nx, l=S * nq, a=S * nx,
+                x0=batch * nx, x=X * nx, w=W, lam=X * nx)
+    if ny is not None:
+        need.update(C=S * ny * nx, R=S * (nw + ny) ** 2, yt=S * ny, wt=S * nw)
+    for name, t in arrays.items():
+        _need(t, need[name], name)
+
+
 class Solver:
     """One context: dims fixed at construction, tensors passed per call.
 
@@ -336,22 +370,29 @@ class Solver:
         lam = torch.empty(self.X, self.nx, dtype=torch.float64, device="cuda")
         return x, w, lam
 
+    def _sizes(self, ny=None, **arrays):
+        check_sizes(self.nx, self.nw, self.S, self.batch, self.X, self.W, ny, **arrays)
+
     def factor(self, A, B, Q, P0inv):
+        self._sizes(A=A, B=B, Q=Q, P0inv=P0inv)
         mhe_factor(self.ctx, A, B, Q, P0inv)
 
     def solve(self, l, a, x0, out=None):
         x, w, lam = out if out is not None else self.outputs()
+        self._sizes(l=l, a=a, x0=x0, x=x, w=w, lam=lam)
         mhe_solve(self.ctx, l, a, x0, x, w, lam, self.info)
         return x, w, lam
 
     def factor_solve(self, A, B, Q, P0inv, l, a, x0, out=None):
         x, w, lam = out if out is not None else self.outputs()
+        self._sizes(A=A, B=B, Q=Q, P0inv=P0inv, l=l, a=a, x0=x0, x=x, w=w, lam=lam)
         mhe_factor_solve(self.ctx, A, B, Q, P0inv, l, a, x0, x, w, lam, self.info)
         return x, w, lam
 
     def estimate(self, ny, A, B, C, R, a, yt, wt, x0, P0inv, out=None):
         """Steps a0..a7 from MHE data (mhe_estimate)."""
         x, w, lam = out if out is not None else self.outputs()
+        self._sizes(ny, A=A, B=B, C=C, R=R, a=a, yt=yt, wt=wt, x0=x0, P0inv=P0inv, x=x, w=w, lam=lam)
         mhe_estimate(self.ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, self.info)
         return x, w, lam
 

@@ -121,3 +121,29 @@ def test_pointer_checks_raise_without_asserts():
         mhe._hptr(torch.zeros(4, dtype=torch.float32))
     assert mhe._hptr(np.zeros(4)) is not None and mhe._hptr(torch.zeros(4, dtype=torch.float64)) is not None
     assert mhe._ptr(None) is None and mhe._hptr(None) is None
+
+
+def test_size_checks_of_the_binding():
+    """Arrays shorter than the problem's layout are refused with MHE_E_ARG before
+    the library sees their pointers; None is left to the library (NULL check)."""
+    import numpy as np
+    import torch
+    nx, nw, ny, N = 4, 2, 2, [5, 9]
+    S, batch, X, W = sum(v - 1 for v in N), len(N), sum(v + 1 for v in N), sum(nx + (v - 1) * nw for v in N)
+    ok = dict(A=torch.zeros(S * nx * nx), B=torch.zeros(S * nx * nw), C=torch.zeros(S * ny * nx),
+              R=torch.zeros(S * (nw + ny) ** 2), a=torch.zeros(S * nx), yt=torch.zeros(S * ny),
+              wt=torch.zeros(S * nw), x0=torch.zeros(batch * nx), P0inv=torch.zeros(batch * nx * nx),
+              Q=torch.zeros(S * (nx + nw) ** 2), l=torch.zeros(S * (nx + nw)), x=torch.zeros(X * nx),
+              w=torch.zeros(W), lam=torch.zeros(X * nx))
+    mhe.check_sizes(nx, nw, S, batch, X, W, ny, **ok)
+    mhe.check_sizes(nx, nw, S, batch, X, W, ny, **dict(ok, C=None))
+    for name in ok:
+        short = dict(ok)
+        short[name] = torch.zeros(ok[name].numel() - 1)
+        with pytest.raises(mhe.MheError) as e:
+            mhe.check_sizes(nx, nw, S, batch, X, W, ny, **short)
+        assert e.value.code == -1 and isinstance(e.value, ValueError) and name in str(e.value)
+    # a wrong ny makes the MHE-form arrays too short: refused the same way
+    with pytest.raises(mhe.MheError):
+        mhe.check_sizes(nx, nw, S, batch, X, W, ny + 1, C=ok["C"])
+    mhe.check_sizes(nx, nw, 0, 2, 4, 2 * nx, ny, A=np.zeros(0), x0=np.zeros(2 * nx))   # N = 1: no stages
