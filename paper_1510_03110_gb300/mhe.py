@@ -428,6 +428,7 @@ class Server:
         _check(lib().mhe_server_create(int(device_bytes), int(prec), float(refine_tol), int(max_refine),
                                        ctypes.byref(self.s)), "mhe_server_create")
         self.nx = {}
+        self.stage_len = {}   # doubles of one packed stage, per estimator
 
     def open(self, p):
         """Admit an estimator whose initial window is the N-1 stages of p (mhe_instance format)."""
@@ -435,14 +436,23 @@ class Server:
         arrs = [cm(p["A"]), cm(p["B"]), cm(p["C"]), cm(p["R"]), np.ascontiguousarray(p["a"], np.float64),
                 np.ascontiguousarray(p["yt"], np.float64), np.ascontiguousarray(p["wt"], np.float64),
                 np.ascontiguousarray(p["x0"], np.float64), cm(p["P0inv"])]
+        n, m, q, S = int(p["n"]), int(p["m"]), int(p["q"]), int(p["N"]) - 1
+        for arr, name, count in zip(arrs, ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv"),
+                                    (S * n * n, S * n * m, S * q * n, S * (m + q) ** 2, S * n, S * q, S * m,
+                                     n, n * n)):
+            _need(arr, count, name)
         ptrs = [a.ctypes.data_as(c_void_p) for a in arrs]
         eid = c_int()
-        _check(lib().mhe_estimator_open(self.s, int(p["n"]), int(p["m"]), int(p["q"]), int(p["N"]), *ptrs,
+        _check(lib().mhe_estimator_open(self.s, n, m, q, int(p["N"]), *ptrs,
                                         ctypes.byref(eid)), "mhe_estimator_open")
-        self.nx[eid.value] = int(p["n"])
+        self.nx[eid.value] = n
+        self.stage_len[eid.value] = n * n + n * m + q * n + (m + q) ** 2 + n + q + m
         return eid.value
 
     def submit(self, est, packed):
+        if int(est) in self.stage_len:
+            packed = np.ascontiguousarray(packed, dtype=np.float64)
+            _need(packed, self.stage_len[int(est)], "packed stage")
         t = ctypes.c_ulonglong()
         _check(lib().mhe_submit(self.s, int(est), packed.ctypes.data_as(c_void_p), ctypes.byref(t)), "mhe_submit")
         return t.value

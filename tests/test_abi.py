@@ -147,3 +147,26 @@ def test_size_checks_of_the_binding():
     with pytest.raises(mhe.MheError):
         mhe.check_sizes(nx, nw, S, batch, X, W, ny + 1, C=ok["C"])
     mhe.check_sizes(nx, nw, 0, 2, 4, 2 * nx, ny, A=np.zeros(0), x0=np.zeros(2 * nx))   # N = 1: no stages
+
+
+def test_server_size_checks_of_the_binding():
+    """The serving binding refuses a window or a packed stage shorter than the
+    estimator's shape needs, before the library reads the host arrays."""
+    import numpy as np
+    from paper_1510_03110_gb300 import synth
+    srv = mhe.Server.__new__(mhe.Server)      # the checks run before any library call
+    srv.s, srv.nx, srv.stage_len = None, {}, {}
+    n, m, q = 4, 2, 2
+    st = synth.plant_stream(1, n, m, q, 30)
+    win = synth.window_of(st, 0, 20, np.zeros(n), n, m, q)
+    short = dict(win, C=win["C"][:-1])
+    with pytest.raises(mhe.MheError) as e:
+        srv.open(short)
+    assert e.value.code == -1 and "C" in str(e.value)
+    with pytest.raises(mhe.MheError):
+        srv.open(dict(win, N=25))             # more stages claimed than given
+    srv.stage_len[7] = n * n + n * m + q * n + (m + q) ** 2 + n + q + m
+    packed = mhe.pack_stage(*(st[f][0] for f in ("A", "B", "C", "R", "a", "yt", "wt")))
+    assert packed.size == srv.stage_len[7]
+    with pytest.raises(mhe.MheError):
+        srv.submit(7, packed[:-1])
