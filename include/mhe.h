@@ -22,7 +22,10 @@
  *     is block s = sum_{b' < b} S_b' + (t - 1).  Every matrix block is
  *     column-major with its natural leading dimension.
  *   - Pointers named "device" must be CUDA device (or managed) memory of the
- *     current device.  The library never frees caller memory.
+ *     current device.  The library never frees caller memory.  It receives
+ *     plain pointers and cannot check their extents: every array must hold the
+ *     element count its documentation states for the batch (a shorter one is
+ *     read or written past its end).
  *   - Calls are asynchronous and ordered on the stream given to mhe_create;
  *     argument and allocation errors are returned synchronously, errors found
  *     on the device (a non-positive-definite pivot, non-convergence) are
