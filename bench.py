@@ -205,6 +205,21 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(rows))
 
 
+def clocks_verdict(clk):
+    """The timing rule on clocks: a run that saw a hardware or thermal slowdown, or
+    SM clocks well below their maximum with no reason given (a leftover clock
+    lock), is not a valid measurement; the power cap is kept and noted."""
+    if not clk or not clk.get("samples"):
+        return "no clock samples"
+    bad = [r for r in clk["reasons"] if r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")]
+    if bad:
+        return "rejected: " + ", ".join(bad)
+    sm, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    if sm and mx and sm < 0.9 * mx and not clk["reasons"]:
+        return "rejected: SM clock %.0f of %.0f MHz with no reason active" % (sm, mx)
+    return "ok (sw_power_cap active, noted)" if "sw_power_cap" in clk["reasons"] else "ok"
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def peaks():
@@ -333,6 +348,8 @@ def run_gpu(args):
     torch.cuda.nvtx.range_pop()
     wall = time.time() - t_host
     clk = clocks.stop()
+    if clk:
+        clk["verdict"] = clocks_verdict(clk)
     launches = sum(mhe.mhe_launch_count(s.ctx) for s in solvers) + mhe.mhe_assemble_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)

@@ -43,3 +43,40 @@ def test_ranks_other_than_zero_exit_without_work():
         r = _bench(["--impl", arm, "--gpus", "2", "--steps", "1", "--warmup", "3"], env, timeout=120)
         assert r.returncode == 0, (arm, r.stderr[-2000:])
         assert r.stdout.strip() == "", (arm, r.stdout)
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_clock_samples_and_verdict():
+    """The clock record of the timed region: nvidia-smi rows parsed into the median
+    SM clock, the maximum and the active reasons, and the timing rule applied
+    (slowdowns and unexplained low clocks reject the run; the power cap is noted)."""
+    b = _bench_module()
+    c = b.Clocks()
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+    rows = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1100.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"]
+    c.f.write("\n".join(rows) + "\n")
+    c.p = Done()
+    clk = c.stop()
+    assert clk["samples"] == 3 and clk["sm_mhz"] == 2070.0 and clk["sm_max_mhz"] == 2070.0
+    assert clk["reasons"] == ["sw_power_cap"]
+    assert b.clocks_verdict(clk).startswith("ok")
+    assert b.clocks_verdict(dict(clk, reasons=["hw_slowdown"])).startswith("rejected")
+    assert b.clocks_verdict(dict(clk, reasons=["sw_thermal_slowdown", "sw_power_cap"])).startswith("rejected")
+    assert b.clocks_verdict(dict(clk, reasons=[], sm_mhz=1200.0)).startswith("rejected")
+    assert b.clocks_verdict(dict(clk, reasons=["sw_power_cap"], sm_mhz=1700.0)).startswith("ok")
+    assert b.clocks_verdict(None) == "no clock samples"
