@@ -78,10 +78,11 @@ typedef struct {
     int batch;           /* number of independent instances */
     const int* N;        /* host array [batch]: UFTOC horizon of each instance, >= 1 */
     int prec;            /* mhe_precision */
-    int leaf_len;        /* level-0 chunk length (0: automatic); leaf_len * nw >= nx */
-    int branching;       /* chunk length at levels >= 1 (0: automatic); >= 2 */
-    int top_len;         /* a level with horizon <= top_len is solved as one chunk (0: automatic).
-                            top_len >= max N gives the plain serial Riccati recursion */
+    int leaf_len;        /* level-0 chunk length (0: max(8, ceil(nx / nw))); leaf_len * nw >= nx */
+    int branching;       /* chunk length at levels >= 1 (0: 4); >= 2 */
+    int top_len;         /* a level with horizon <= top_len is solved as one chunk (0: 4).
+                            top_len >= max N gives the plain serial Riccati recursion.
+                            mhe_autotune measures candidate plans and returns the fastest */
     double refine_tol;   /* target relative KKT residual (0: 1e-14 for FP64, 1e-12 for FP32_IR) */
     int max_refine;      /* refinement iterations after the first solve (-1: 2 for FP64, 8 for FP32_IR) */
 } mhe_dims;
