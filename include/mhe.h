@@ -246,9 +246,9 @@ int mhe_submit(mhe_server* s, int est, const double* stage, unsigned long long* 
  * releases the ticket and returns the request's status. */
 int mhe_poll(mhe_server* s, unsigned long long ticket, double* x_est, mhe_info* info, double* latency_s);
 
-/* Plan of every round (as mhe_dims.leaf_len, branching, top_len; 0 =
- * automatic; top_len above every N = the serial recursion).  Before the first
- * request only. */
+/* Plan of every round (as mhe_dims.leaf_len, branching, top_len; 0 = the
+ * defaults listed there; top_len above every N = the serial recursion).
+ * Before the first request only. */
 int mhe_server_set_plan(mhe_server* s, int leaf_len, int branching, int top_len);
 
 /* Device bytes the server holds. */

@@ -176,7 +176,7 @@ struct Bucket {
 
 struct mhe_server {
     int prec = MHE_FP32_IR;
-    int leaf_len = 0, branching = 0, top_len = 0;   // plan of every round (0: automatic)
+    int leaf_len = 0, branching = 0, top_len = 0;   // plan of every round (0: the default plan)
     size_t budget = 0, used = 0;
     double refine_tol = 1e-9;
     int max_refine = 8;
