@@ -64,6 +64,16 @@ def test_workspace_bytes_host_only(L):
     assert b32 < 4 * 131072 * per_stage * 4 + 2 * copies
 
 
+def test_zero_plan_fields_are_the_documented_defaults(L):
+    """leaf_len = branching = top_len = 0 select max(8, ceil(nx / nw)), 4 and 4
+    (the sizes of the workspace agree with the explicit plan)."""
+    for nx, nw, N in [(24, 12, [100, 2000, 37]), (6, 3, [5000]), (64, 32, [1024] * 4), (1, 1, [3, 4])]:
+        d0, _ = mhe.make_dims(nx, nw, N, prec=mhe.MHE_FP32_IR)
+        de, _ = mhe.make_dims(nx, nw, N, prec=mhe.MHE_FP32_IR, leaf_len=max(8, -(-nx // nw)), branching=4,
+                              top_len=4)
+        assert mhe.mhe_workspace_bytes(d0) == mhe.mhe_workspace_bytes(de) > 0
+
+
 def test_bad_dims_rejected_on_host(L):
     d, _ = mhe.make_dims(5, 4, [10])        # shape not compiled
     assert mhe.mhe_workspace_bytes(d) == 0
