@@ -205,7 +205,7 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(rows))
 
 
-def clocks_verdict(clk):
+def clocks_check(clk):
     """The timing rule on clocks: a run that saw a hardware or thermal slowdown, or
     SM clocks well below their maximum with no reason given (a leftover clock
     lock), is not a valid measurement; the power cap is kept and noted."""
@@ -349,7 +349,7 @@ def run_gpu(args):
     wall = time.time() - t_host
     clk = clocks.stop()
     if clk:
-        clk["verdict"] = clocks_verdict(clk)
+        clk["rule"] = clocks_check(clk)
     launches = sum(mhe.mhe_launch_count(s.ctx) for s in solvers) + mhe.mhe_assemble_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)

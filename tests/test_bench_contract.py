@@ -53,7 +53,7 @@ def _bench_module():
     return mod
 
 
-def test_clock_samples_and_verdict():
+def test_clock_samples_and_rule():
     """The clock record of the timed region: nvidia-smi rows parsed into the median
     SM clock, the maximum and the active reasons, and the timing rule applied
     (slowdowns and unexplained low clocks reject the run; the power cap is noted)."""
@@ -74,9 +74,9 @@ def test_clock_samples_and_verdict():
     clk = c.stop()
     assert clk["samples"] == 3 and clk["sm_mhz"] == 2070.0 and clk["sm_max_mhz"] == 2070.0
     assert clk["reasons"] == ["sw_power_cap"]
-    assert b.clocks_verdict(clk).startswith("ok")
-    assert b.clocks_verdict(dict(clk, reasons=["hw_slowdown"])).startswith("rejected")
-    assert b.clocks_verdict(dict(clk, reasons=["sw_thermal_slowdown", "sw_power_cap"])).startswith("rejected")
-    assert b.clocks_verdict(dict(clk, reasons=[], sm_mhz=1200.0)).startswith("rejected")
-    assert b.clocks_verdict(dict(clk, reasons=["sw_power_cap"], sm_mhz=1700.0)).startswith("ok")
-    assert b.clocks_verdict(None) == "no clock samples"
+    assert b.clocks_check(clk).startswith("ok")
+    assert b.clocks_check(dict(clk, reasons=["hw_slowdown"])).startswith("rejected")
+    assert b.clocks_check(dict(clk, reasons=["sw_thermal_slowdown", "sw_power_cap"])).startswith("rejected")
+    assert b.clocks_check(dict(clk, reasons=[], sm_mhz=1200.0)).startswith("rejected")
+    assert b.clocks_check(dict(clk, reasons=["sw_power_cap"], sm_mhz=1700.0)).startswith("ok")
+    assert b.clocks_check(None) == "no clock samples"
