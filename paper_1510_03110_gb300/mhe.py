@@ -291,7 +291,7 @@ def mhe_assemble_count():
 
 def mhe_plan_info(ctx):
     """[(level, chunks, stages)] of the planned tree."""
-    buf = (c_ll * 3 * 256)()
+    buf = (c_ll * (3 * 256))()     # 3 long longs per level, up to 256 levels
     k = lib().mhe_plan_info(ctx, buf, 256)
     return [(int(buf[3 * i]), int(buf[3 * i + 1]), int(buf[3 * i + 2])) for i in range(min(k, 256))]
 

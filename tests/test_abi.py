@@ -180,3 +180,15 @@ def test_server_size_checks_of_the_binding():
     assert packed.size == srv.stage_len[7]
     with pytest.raises(mhe.MheError):
         srv.submit(7, packed[:-1])
+
+
+def test_plan_info_unpacks_the_levels(monkeypatch):
+    """mhe_plan_info's buffer: 3 long longs per level, read back as (level, chunks, stages)."""
+    class Fake:
+        def mhe_plan_info(self, ctx, buf, cap):
+            assert cap == 256
+            for k, v in enumerate([0, 40, 1000, 1, 9, 39, 2, 1, 8]):
+                buf[k] = v
+            return 3
+    monkeypatch.setattr(mhe, "lib", lambda: Fake())
+    assert mhe.mhe_plan_info(None) == [(0, 40, 1000), (1, 9, 39), (2, 1, 8)]
