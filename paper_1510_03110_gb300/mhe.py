@@ -297,7 +297,15 @@ def mhe_plan_info(ctx):
 
 
 def mhe_assemble(nx, nw, ny, C, R, yt, wt, Q, l, c=None, stream=None):
+    """Step a0 for S stages; C is (S, ny * nx) (one column-major block per row),
+    which fixes S."""
+    if C is not None and (C.dim() != 2 or C.shape[1] != ny * nx):
+        raise SizeError(f"C must be (S, ny * nx) = (S, {ny * nx}), got {tuple(C.shape)}")
     S = C.shape[0] if C is not None else 0
+    nq = nx + nw
+    for t, count, name in ((R, S * (nw + ny) ** 2, "R"), (yt, S * ny, "yt"), (wt, S * nw, "wt"),
+                           (Q, S * nq * nq, "Q"), (l, S * nq, "l"), (c, S if c is not None else 0, "c")):
+        _need(t, count, name)
     return _check(lib().mhe_assemble(int(nx), int(nw), int(ny), int(S), _ptr(C), _ptr(R), _ptr(yt),
                                      _ptr(wt), _ptr(Q), _ptr(l), _ptr(c), _stream(stream)),
                   "mhe_assemble")
