@@ -102,6 +102,35 @@ def problem_1x1x1():
                 wt=[[F(-1, 4) * k] for k in range(K)])
 
 
+def problem_4x2x2():
+    """n = 4, nw = ny = 2, four measured stages (UFTOC horizon N = 5); the
+    cross-weight S of R = [[W, S], [S^T, V]] is a non-symmetric 2 x 2 block, so
+    S and S^T cannot be confused without changing the answer."""
+    K = 4
+    A, B, C, R, a, yt, wt = [], [], [], [], [], [], []
+    for k in range(K):
+        A.append([[F(4, 5), F(1, 3), F(0), F(k, 10)],
+                  [F(-1, 4), F(7, 10), F(1, 5), F(0)],
+                  [F(0), F(1, 6), F(9, 10), F(-1, 3)],
+                  [F(1, 8), F(0), F(1, 4), F(3, 5) + F(k, 20)]])
+        B.append([[F(1, 2), F(0)], [F(1), F(1, 3)], [F(0), F(1, 2)], [F(-1, 4), F(1)]])
+        C.append([[F(1), F(0), F(1, 2), F(0)], [F(0), F(1), F(0), F(-1, 3) * (k + 1)]])
+        # R = M M^T + I with M lower triangular and rational: symmetric positive definite
+        M = [[F(1), F(0), F(0), F(0)],
+             [F(1, 2), F(1), F(0), F(0)],
+             [F(-1, 3), F(1, 4) * (k + 1), F(1), F(0)],
+             [F(1, 5), F(-1, 2), F(1, 3), F(1)]]
+        R.append([[sum((M[i][t] * M[j][t] for t in range(4)), F(0)) + (F(1) if i == j else F(0))
+                   for j in range(4)] for i in range(4)])
+        a.append([F(k, 7), F(-1, 9), F(1, 11), F(0)])
+        yt.append([F(1, 2) - F(k, 5), F((-1) ** k, 4)])
+        wt.append([F(1, 10) * k, F(-1, 6)])
+    return dict(n=4, m=2, q=2, N=K + 1, x0=[F(1, 2), F(-1), F(0), F(2)],
+                P0inv=[[F(3), F(1, 2), F(0), F(0)], [F(1, 2), F(2), F(1, 4), F(0)],
+                       [F(0), F(1, 4), F(1), F(0)], [F(0), F(0), F(0), F(3, 2)]],
+                A=A, B=B, C=C, R=R, a=a, yt=yt, wt=wt)
+
+
 def states(p, X0, ws):
     """X_0 .. X_K from the dynamics of Eq. org_mhe."""
     X = [X0]
@@ -209,7 +238,8 @@ def fixture_text(name, p):
     return "\n".join(out) + "\n"
 
 
-FIXTURES = {"mhe_2x1x1_N6_exact.txt": problem_2x1x1, "mhe_1x1x1_N4_exact.txt": problem_1x1x1}
+FIXTURES = {"mhe_2x1x1_N6_exact.txt": problem_2x1x1, "mhe_1x1x1_N4_exact.txt": problem_1x1x1,
+            "mhe_4x2x2_N5_exact.txt": problem_4x2x2}
 
 
 def main():

@@ -24,7 +24,7 @@ import oracle
 from oracle import dense, tree
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-NAMES = ["mhe_2x1x1_N6_exact", "mhe_1x1x1_N4_exact"]
+NAMES = ["mhe_2x1x1_N6_exact", "mhe_1x1x1_N4_exact", "mhe_4x2x2_N5_exact"]
 
 
 def load(name):

@@ -40,6 +40,9 @@ MUTATIONS = {
     # Alg 1: P_t = F - K^T G K stored as computed, not its symmetric part
     "drop_symmetrisation_of_P": ("0.5 * ((AT(F, i, j, n) - AT(KGK, i, j, n)) +\n                                         (AT(F, j, i, n) - AT(KGK, j, i, n)));",
                                  "(AT(F, i, j, n) - AT(KGK, i, j, n));"),
+    # Section II: l_w = S^T y~ (S and S^T confused; type-checks when nw = ny)
+    "transpose_S_in_lw": ("/* l_w = S y~ - W w~ */\n    mv(m, q, S, m, 0, yt, t1);",
+                          "/* l_w = S y~ - W w~ */\n    mv(m, q, S, m, 1, yt, t1);"),
     # residual: the -lambda_t term of the x-stationarity row is dropped
     "drop_lambda_in_residual": ("if (i < n) { s -= ltt[i]; rs += 1.0; }", "if (i < n) { rs += 1.0; }"),
 }
@@ -65,17 +68,21 @@ def _mutant(tmpdir, name):
 # the mistakes that change the Newton step itself (the rest touch only the
 # objective's constant, the residual routine or rounding)
 STEP_CHANGING = ["drop_Qx_in_F", "transpose_A_in_F", "wrong_operand_in_H", "sign_lx_in_Psi",
-                 "sign_Psi_in_lambda", "sign_Qxw_assembly", "sign_lw_assembly"]
+                 "sign_Psi_in_lambda", "sign_Qxw_assembly", "sign_lw_assembly", "transpose_S_in_lw"]
 
 
 def _golden_fails(lib_mut) -> bool:
-    """The exact golden step (n = 2, nw = ny = 1, N = 6) against a library."""
+    """The exact golden steps (n = 2, nw = ny = 1, N = 6 and n = 4, nw = ny = 2, N = 5
+    with a non-symmetric S) against a library."""
     saved = core._lib
     core._lib = lib_mut
     try:
-        pf, sol = as_float(load("mhe_2x1x1_N6_exact"))
-        r = oracle.riccati(oracle.mhe_to_uftoc(pf))
-        return r["status"] != 0 or any(rel(r[k], sol[k]) > 1e-12 for k in ("x", "w", "lam"))
+        for name in ("mhe_2x1x1_N6_exact", "mhe_4x2x2_N5_exact"):
+            pf, sol = as_float(load(name))
+            r = oracle.riccati(oracle.mhe_to_uftoc(pf))
+            if r["status"] != 0 or any(rel(r[k], sol[k]) > 1e-12 for k in ("x", "w", "lam")):
+                return True
+        return False
     finally:
         core._lib = saved
 
