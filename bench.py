@@ -237,6 +237,74 @@ def peaks():
                 bf16_tflops=float(p.get("bf16_tflops", 1900.0)))
 
 
+# FP64 and FP32 FMA throughput of the GPU (the ALU roofline denominators next to the
+# measured HBM and BF16 peaks): every thread runs eight independent FMA chains, 8 CTAs
+# of 256 threads per SM, best of two timed runs after a warm-up (CUDA events).
+ALU_PROBE = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+template <typename T>
+__global__ void k_fma(T* out, int iters, T a, T b)
+{
+    T x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+        x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+template <typename T>
+static double tflops(int blocks, int threads, int iters)
+{
+    T* out = nullptr;
+    if (cudaMalloc(&out, sizeof(T) * blocks * threads) != cudaSuccess) return -1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0);
+        k_fma<T><<<blocks, threads>>>(out, iters, (T)0.999999, (T)1e-7);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaFree(out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+}
+int main()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256;
+    const double f64 = tflops<double>(blocks, threads, 20000);
+    const double f32 = tflops<float>(blocks, threads, 160000);
+    const cudaError_t err = cudaGetLastError();
+    printf("{\"fp64_tflops\": %.4f, \"fp32_tflops\": %.4f, \"sm_count\": %d, \"status\": \"%s\"}\n", f64, f32,
+           sms, cudaGetErrorString(err));
+    return err == cudaSuccess ? 0 : 1;
+}
+"""
+
+
+def run_alu_peaks():
+    """Compile and run the FMA probe (one GPU); prints its JSON line."""
+    from paper_1510_03110_gb300.build import ARCH, nvcc
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "alu_peaks.cu"), os.path.join(d, "alu_peaks")
+        open(src, "w").write(ALU_PROBE)
+        subprocess.run([nvcc(), "-O3", *ARCH, "-o", exe, src], check=True)
+        r = subprocess.run([exe], capture_output=True, text=True)
+        sys.stdout.write(r.stdout)
+        sys.stderr.write(r.stderr)
+        return r.returncode
+
+
 def read_traffic():
     """DRAM bytes per stage of the leaf reduction from the committed ncu summary (or None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -725,7 +793,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "long", "profile", "serve", "xl", "xl_profile"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks"])
     ap.add_argument("--plan", default=None, help="leaf_len,branching,top_len used instead of the autotuner")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
@@ -752,6 +821,8 @@ def main():
     if int(os.environ.get("RANK", "0")) != 0:
         # one GPU does the work: rank 0 runs the workload, the other ranks exit without work
         return
+    if args.workload == "alu_peaks":
+        raise SystemExit(run_alu_peaks())
     if args.workload == "serve":
         res = run_serve(args)
         tree, ser = res["tree"], res["serial"]

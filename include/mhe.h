@@ -279,20 +279,24 @@ int mhe_plan_info(mhe_ctx* ctx, long long* out, int cap);
  * the whole device and take an unbounded time at a sample instant, or a host
  * application that owns the device-memory budget and forbids allocations by
  * libraries -- this solves ONE instance (layout as above, batch = 1) in FP64
- * with the serial plan (the whole horizon as one chunk: Algorithms 1-3) in a
- * single kernel launch on `stream`, without allocating anything.  The stored
- * factors live in a fixed scratch array of 2^20 doubles (8 MiB) that the
- * library reserves on every GPU that loads it, until the process exits.
+ * with the whole horizon as one chunk, in a single kernel launch on `stream`,
+ * without allocating anything.  The stored factors live in a fixed scratch
+ * array of 2^20 doubles (8 MiB) that the library reserves on every GPU that
+ * loads its device code, until the process exits.
  * Limits: (nx, nw) compiled in (mhe_shapes) and
  *   N * (nw*nw + nw*nx + nw) + 2*nx*nx + nx <= 2^20;
  * larger N is rejected with MHE_E_ARG before anything runs.  Outputs (device):
  * x, w, lam as for mhe_solve; status (device, 1 int, may be NULL) receives
- * MHE_OK or MHE_E_NOT_PD.  The first call on a device looks up the scratch
- * array's device address and sets the kernels' shared-memory limits, so make
- * that first call before any stream capture.  Every call shares the one
- * scratch array: calls whose kernels overlap on the GPU (other streams, other
- * host threads) race on it; order them on one stream.  Errors: MHE_E_ARG,
- * MHE_E_CUDA. */
+ * MHE_OK or MHE_E_NOT_PD (a Cholesky pivot below the threshold).
+ * The first call on each device is a warm-up: it looks up the scratch array's
+ * device address and sets the kernels' shared-memory limits, and under lazy
+ * module loading (the CUDA default) it is the call that loads the library's
+ * device code, which reserves the scratch array -- so it may allocate and
+ * synchronise.  Make it once, outside the time-critical loop and before any
+ * stream capture; later calls on that device allocate nothing.  Every call
+ * shares the one scratch array, which keeps the last call's contents: calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race
+ * on it; order them on one stream.  Errors: MHE_E_ARG, MHE_E_CUDA. */
 int mhe_solve_serial_noalloc(int nx, int nw, int N, const double* A, const double* B, const double* Q,
                              const double* P0inv, const double* l, const double* a, const double* x0,
                              double* x, double* w, double* lam, int* status, void* stream);

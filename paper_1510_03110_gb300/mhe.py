@@ -260,11 +260,34 @@ def mhe_timing_read(ctx):
              float(buf[5 * i + 4])) for i in range(min(k, 1024))]
 
 
+def _iptr(t):
+    """A device int32 buffer of at least one element (a status word) -> pointer;
+    None passes as NULL.  Checked always: the kernel writes through it, so a host
+    pointer or a tensor of another type would fault the GPU."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
+            and t.numel() >= 1):
+        raise TypeError("status must be None or a contiguous int32 CUDA tensor of at least one element")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def mhe_solve_serial_noalloc(nx, nw, N, A, B, Q, P0inv, l, a, x0, x, w, lam, status=None,
                              stream=None):
-    """One instance, serial plan, FP64, no device allocation (fixed library scratch)."""
-    sp = ctypes.c_void_p(status.data_ptr()) if status is not None else None
-    return _check(lib().mhe_solve_serial_noalloc(int(nx), int(nw), int(N), _ptr(A), _ptr(B), _ptr(Q),
+    """One instance, serial plan, FP64, no device allocation (fixed library scratch).
+
+    Every array is checked against the layout of include/mhe.h for batch = 1
+    (S = N - 1 caller stages) before the call: the library takes raw pointers
+    and cannot check their extents."""
+    nx, nw, N = int(nx), int(nw), int(N)
+    S, nq = max(N - 1, 0), nx + nw
+    for t, count, name in ((A, S * nx * nx, "A"), (B, S * nx * nw, "B"), (Q, S * nq * nq, "Q"),
+                           (l, S * nq, "l"), (a, S * nx, "a"), (P0inv, nx * nx, "P0inv"), (x0, nx, "x0"),
+                           (x, (N + 1) * nx, "x"), (w, nx + S * nw, "w"), (lam, (N + 1) * nx, "lam")):
+        _need(t, count, name)
+    sp = _iptr(status)
+    return _check(lib().mhe_solve_serial_noalloc(nx, nw, N, _ptr(A), _ptr(B), _ptr(Q),
                                                  _ptr(P0inv), _ptr(l), _ptr(a), _ptr(x0), _ptr(x), _ptr(w),
                                                  _ptr(lam), sp, _stream(stream)),
                   "mhe_solve_serial_noalloc")

@@ -144,8 +144,40 @@ def test_timing_autotune_assemble(fake):
         mhe.mhe_assemble(nx, nw, ny, C.reshape(-1), R, v, v, Q, v)
     with pytest.raises(mhe.MheError):
         mhe.mhe_assemble(nx, nw, ny, C, R[:-1], v, v, Q, v)
-    mhe.mhe_solve_serial_noalloc(4, 2, 10, *([z] * 10))
+    arrs = _noalloc_arrays(4, 2, 10)
+    mhe.mhe_solve_serial_noalloc(4, 2, 10, *arrs)
     assert fake.calls["mhe_solve_serial_noalloc"][:3] == (4, 2, 10)
+    assert fake.calls["mhe_solve_serial_noalloc"][13] is None    # no status word: NULL
+
+
+def _noalloc_arrays(n, m, N):
+    """Arrays of exactly the batch = 1 layout: A B Q P0inv l a x0 x w lam."""
+    S, nq = N - 1, n + m
+    z = lambda k: torch.zeros(k, dtype=torch.float64)  # noqa: E731
+    return [z(S * n * n), z(S * n * m), z(S * nq * nq), z(n * n), z(S * nq), z(S * n), z(n),
+            z((N + 1) * n), z(n + S * m), z((N + 1) * n)]
+
+
+@pytest.mark.parametrize("short", range(10))
+def test_noalloc_refuses_short_arrays(fake, short):
+    """Every array of mhe_solve_serial_noalloc is checked against the batch = 1 layout before the
+    call: one element short is refused (SizeError, MHE_E_ARG) and the library is not called."""
+    arrs = _noalloc_arrays(6, 3, 12)
+    arrs[short] = arrs[short][:-1]
+    with pytest.raises(mhe.SizeError):
+        mhe.mhe_solve_serial_noalloc(6, 3, 12, *arrs)
+    assert "mhe_solve_serial_noalloc" not in fake.calls
+
+
+@pytest.mark.parametrize("status", [torch.zeros(1, dtype=torch.int32),          # host memory
+                                    torch.zeros(1, dtype=torch.int64),          # wrong type
+                                    torch.zeros(0, dtype=torch.int32),          # empty
+                                    np.zeros(1, dtype=np.int32)])               # not a tensor
+def test_noalloc_refuses_a_bad_status_buffer(fake, status):
+    """The status word must be None or a contiguous int32 CUDA tensor (the kernel writes it)."""
+    with pytest.raises(TypeError):
+        mhe.mhe_solve_serial_noalloc(4, 2, 10, *_noalloc_arrays(4, 2, 10), status=status)
+    assert "mhe_solve_serial_noalloc" not in fake.calls
 
 
 def test_info_records():

@@ -151,7 +151,7 @@ def test_oracle_reproduces_the_exact_step(name):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("name", ["mhe_2x1x1_N6_exact", "mhe_1x1x1_N4_exact"])
+@pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("plan", [dict(leaf_len=4, branching=3, top_len=2), dict(top_len=1000)])
 def test_cuda_path_reproduces_the_exact_step(name, plan):
     import torch
@@ -170,3 +170,30 @@ def test_cuda_path_reproduces_the_exact_step(name, plan):
     assert info["status"][0] == 0
     for k in ("x", "w", "lam"):
         assert _rel(got[k], sol[k]) <= 1e-10, k
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("prec,bound", [(0, 1e-10), (1, 1e-8)])
+@pytest.mark.parametrize("plan", [dict(leaf_len=4, branching=3, top_len=2), dict(top_len=1000)])
+def test_mhe_form_entry_reproduces_the_exact_step(name, prec, bound, plan):
+    """mhe_estimate from the MHE weights (C, R, y~, w~): in MHE_FP32_IR the FP32 preparation pass
+    (Q from FP32 products of C and R) and the FP64 residual that applies Q in its factors, which
+    the bench times; in MHE_FP64 the FP64 assembly.  Both reproduce the exact rational step."""
+    import torch
+
+    from gpu_util import device_inputs, split
+    from paper_1510_03110_gb300 import mhe
+
+    pf, sol = as_float(load(name))
+    d = device_inputs([pf])
+    s = mhe.Solver(d["n"], d["m"], d["N"], prec=prec, **plan)
+    x, w, lam = s.estimate(d["q"], d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"], d["x0"],
+                           d["P0inv"])
+    torch.cuda.synchronize()
+    got = split(x, w, lam, d["N"], d["n"], d["m"])[0]
+    info = s.infos()
+    s.close()
+    assert info["status"][0] == 0
+    for k in ("x", "w", "lam"):
+        assert _rel(got[k], sol[k]) <= bound, k

@@ -66,7 +66,7 @@ def test_result_is_the_same_alone_and_in_the_mix():
     x0 = np.zeros(n)
     alone = _run_alone(mhe.MHE_FP32_IR, st, N, x0, K, n, m, q, tol)
 
-    srv = mhe.Server(2 << 30, prec=mhe.MHE_FP32_IR, refine_tol=tol)
+    srv = mhe.Server(2 << 30, prec=mhe.MHE_FP32_IR, refine_tol=tol, max_refine=16)
     others = []
     for i, (nn, NN) in enumerate([(6, 50), (12, 200), (6, 120), (24, 90), (12, 60)] * 4):
         ss = synth.plant_stream(100 + i, nn, nn // 2, nn // 2, NN - 1 + K)
@@ -80,7 +80,7 @@ def test_result_is_the_same_alone_and_in_the_mix():
     mixed = [srv.wait(t, n) for t in tickets_e]
     for t, nn in tickets_o:
         r = srv.wait(t, nn)
-        assert r["status"] in (0, -6) and r["relres"] <= 1e-8
+        assert r["status"] == 0 and r["relres"] <= tol
     srv.close()
     for j in range(K):
         err = np.abs(mixed[j]["x"] - alone[j]["x"]).max() / np.abs(alone[j]["x"]).max()
