@@ -85,6 +85,12 @@ typedef struct {
                             mhe_autotune measures candidate plans and returns the fastest */
     double refine_tol;   /* target relative KKT residual (0: 1e-14 for FP64, 1e-12 for FP32_IR) */
     int max_refine;      /* refinement iterations after the first solve (-1: 2 for FP64, 8 for FP32_IR) */
+    int fp64_masters;    /* MHE_FP32_IR / TF32_IR / BF16_IR: 1 = the master problems of the tree's levels
+                            k >= 1 (Eq. red_mpc_problem, Algorithm 5) are reduced, factored and solved in
+                            FP64 -- the Cholesky factorisations of the reduced problems in FP64 -- while
+                            level 0 stays in the tree's precision; their data are widened after level 0
+                            and level 1's solution is narrowed for level 0's down pass.  0 = every level
+                            in the tree's precision.  Ignored by MHE_FP64 */
 } mhe_dims;
 
 /* Matrix data of the problem, FP64, device memory, read while the stream

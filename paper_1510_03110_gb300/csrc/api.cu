@@ -208,6 +208,22 @@ void rt_convert(float* dst, const double* src, long long count, void* s)
     k_convert<<<(unsigned)blocks, 256, 0, (cudaStream_t)s>>>(dst, src, count);
 }
 
+// FP32 -> FP64 copy (exact)
+__global__ void k_widen(double* dst, const float* src, long long count)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        dst[i] = (double)src[i];
+}
+
+void rt_widen(double* dst, const float* src, long long count, void* s)
+{
+    if (count <= 0) return;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_widen<<<(unsigned)blocks, 256, 0, (cudaStream_t)s>>>(dst, src, count);
+}
+
 void rt_mark(void* user, int phase, int level, int begin, void* s)
 {
     PassTiming* t = static_cast<PassTiming*>(user);
@@ -225,7 +241,7 @@ void rt_mark(void* user, int phase, int level, int begin, void* s)
 }
 
 const mhe::Runtime kRuntime = {rt_alloc, rt_release, rt_memset0, rt_copy, rt_finalize, rt_convert, rt_sync,
-                               rt_error, rt_mark};
+                               rt_error, rt_mark, rt_widen};
 
 int check_dims(const mhe_dims* d)
 {
@@ -273,6 +289,8 @@ size_t mhe_workspace_bytes(const mhe_dims* dims)
     if (check_dims(dims) != MHE_OK) return 0;
     mhe::Engine e;
     e.prec = dims->prec;
+    e.ops = &find_shape(dims->nx, dims->nw)->ops;
+    e.m64 = dims->fp64_masters != 0 && dims->prec != MHE_FP64;
     const int min_leaf = (dims->nx + dims->nw - 1) / dims->nw;
     const char* err = nullptr;
     if (mhe::make_plan(dims->nx, dims->nw, dims->N, dims->batch,
@@ -389,6 +407,7 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             d.nx = n; d.nw = m; d.batch = cnt; d.N = P.N.data() + b0; d.prec = E.prec;
             d.leaf_len = E.leaf; d.branching = E.br; d.top_len = E.topl;
             d.refine_tol = E.tol; d.max_refine = E.max_refine;
+            d.fp64_masters = E.m64 ? 1 : 0;
             rc = hp.eng[e].init(d, E.ops, &kRuntime, hp.st[e]);
             if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
             hp.inited[e] = true;

@@ -73,6 +73,11 @@ struct LevelArgs {
     int* where;            // per instance (level, chunk, stage) of the first error
     double piv_rel;        // relative pivot threshold of the Cholesky factorisations
     int store_P;           // keep P_{t+1} per stage (needed by right-hand-side-only passes)
+    // shapes whose per-subproblem workspace exceeds an SM's shared memory (FP64 at
+    // nx = 64): gws_teams slots of the workspace in global memory (L2-resident),
+    // one per CTA of a launch of at most gws_teams CTAs
+    T* gws;
+    int gws_teams;
 };
 
 // Residual kernel arguments (level 0).  Reads the caller's FP64 problem and

@@ -42,24 +42,40 @@ size_t Engine::layout(char* base)
         c.take(B_.li, (size_t)batch);
         const size_t ns = (size_t)L.nstages, nx_ = (size_t)L.nstates;
         const size_t mk = (k == 0) ? (size_t)m : (size_t)n;
-        c.take_raw(B_.Pst, ns * n2 * ts);
-        c.take_raw(B_.Lgst, ns * mk * mk * ts);
-        c.take_raw(B_.Kst, ns * mk * n * ts);
-        c.take_raw(B_.kst, ns * mk * ts);
-        c.take_raw(B_.Lst, ns * mk * n * ts);
+        const size_t tk = (m64 && k >= 1) ? sizeof(double) : ts;   // the level's compute type
+        c.take_raw(B_.Pst, ns * n2 * tk);
+        c.take_raw(B_.Lgst, ns * mk * mk * tk);
+        c.take_raw(B_.Kst, ns * mk * n * tk);
+        c.take_raw(B_.kst, ns * mk * tk);
+        c.take_raw(B_.Lst, ns * mk * n * tk);
         if (k >= 1) {
-            c.take_raw(B_.Ah, ns * n2 * ts);
-            c.take_raw(B_.Bh, ns * n2 * ts);
-            c.take_raw(B_.Qxh, ns * n2 * ts);
-            c.take_raw(B_.ah, ns * n * ts);
-            c.take_raw(B_.lxh, ns * n * ts);
-            c.take_raw(B_.QN, (size_t)batch * n2 * ts);
-            c.take_raw(B_.lN, (size_t)batch * n * ts);
-            c.take_raw(B_.xd, nx_ * n * ts);
-            c.take_raw(B_.wd, ns * n * ts);
-            c.take_raw(B_.ld, nx_ * n * ts);
+            c.take_raw(B_.Ah, ns * n2 * tk);
+            c.take_raw(B_.Bh, ns * n2 * tk);
+            c.take_raw(B_.Qxh, ns * n2 * tk);
+            c.take_raw(B_.ah, ns * n * tk);
+            c.take_raw(B_.lxh, ns * n * tk);
+            c.take_raw(B_.QN, (size_t)batch * n2 * tk);
+            c.take_raw(B_.lN, (size_t)batch * n * tk);
+            c.take_raw(B_.xd, nx_ * n * tk);
+            c.take_raw(B_.wd, ns * n * tk);
+            c.take_raw(B_.ld, nx_ * n * tk);
+        }
+        if (m64 && k == 1) {   // the FP32 side of the level-0 / level-1 hand-off
+            c.take_raw(B_.Ah32, ns * n2 * sizeof(float));
+            c.take_raw(B_.Bh32, ns * n2 * sizeof(float));
+            c.take_raw(B_.Qxh32, ns * n2 * sizeof(float));
+            c.take_raw(B_.ah32, ns * n * sizeof(float));
+            c.take_raw(B_.lxh32, ns * n * sizeof(float));
+            c.take_raw(B_.QN32, (size_t)batch * n2 * sizeof(float));
+            c.take_raw(B_.lN32, (size_t)batch * n * sizeof(float));
+            c.take_raw(B_.xd32, nx_ * n * sizeof(float));
+            c.take_raw(B_.wd32, ns * n * sizeof(float));
+            c.take_raw(B_.ld32, nx_ * n * sizeof(float));
         }
     }
+    if (ops && ops->gws64 > 0 && ops->gws_teams > 0 && (prec == MHE_FP64 || m64))
+        c.take_raw(gws, (size_t)ops->gws_teams * (size_t)ops->gws64 * sizeof(double));
+    if (m64) c.take(rx0_64, (size_t)batch * n);
     c.take_raw(Pst0, (size_t)batch * n2 * ts);
     c.take_raw(Lgst0, (size_t)batch * n2 * ts);
     c.take_raw(Kst0, (size_t)batch * n2 * ts);
@@ -109,7 +125,12 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
         return MHE_E_ARG;
     }
     if (prec == MHE_FP64 && !ops->reduce64) {
-        err = "this shape's FP64 workspace exceeds the shared memory of an SM: use MHE_FP32_IR";
+        err = "this shape has no FP64 passes compiled: use MHE_FP32_IR";
+        return MHE_E_ARG;
+    }
+    m64 = d.fp64_masters != 0 && prec != MHE_FP64;
+    if (m64 && (!ops->reduce64 || !rt->widen)) {
+        err = "FP64 master levels need the shape's FP64 passes";
         return MHE_E_ARG;
     }
     // FP64: the tree's backward error (~1e-13 on hard instances) can leave a forward
@@ -238,11 +259,15 @@ LevelArgs<T> Engine::args(int k) const
     }
     if (k + 1 < (int)lv.size()) {
         const LevelBuf& U = lv[k + 1];
-        a.Ah_up = static_cast<T*>(U.Ah); a.Bh_up = static_cast<T*>(U.Bh); a.ah_up = static_cast<T*>(U.ah);
-        a.Qxh_up = static_cast<T*>(U.Qxh); a.lxh_up = static_cast<T*>(U.lxh);
-        a.QN_up = static_cast<T*>(U.QN); a.lN_up = static_cast<T*>(U.lN);
-        a.xd_up = static_cast<const T*>(U.xd); a.wd_up = static_cast<const T*>(U.wd);
-        a.ld_up = static_cast<const T*>(U.ld);
+        // with FP64 master levels the FP32 level 0 writes the FP32 side of level 1's
+        // master data and reads the FP32 copy of level 1's solution
+        const bool st = m64 && k == 0;
+        a.Ah_up = static_cast<T*>(st ? U.Ah32 : U.Ah); a.Bh_up = static_cast<T*>(st ? U.Bh32 : U.Bh);
+        a.ah_up = static_cast<T*>(st ? U.ah32 : U.ah);
+        a.Qxh_up = static_cast<T*>(st ? U.Qxh32 : U.Qxh); a.lxh_up = static_cast<T*>(st ? U.lxh32 : U.lxh);
+        a.QN_up = static_cast<T*>(st ? U.QN32 : U.QN); a.lN_up = static_cast<T*>(st ? U.lN32 : U.lN);
+        a.xd_up = static_cast<const T*>(st ? U.xd32 : U.xd); a.wd_up = static_cast<const T*>(st ? U.wd32 : U.wd);
+        a.ld_up = static_cast<const T*>(st ? U.ld32 : U.ld);
     }
     a.Pst = static_cast<T*>(L.Pst);
     a.Lgst = static_cast<T*>(L.Lgst);
@@ -261,6 +286,8 @@ LevelArgs<T> Engine::args(int k) const
     a.where = where;
     a.piv_rel = (sizeof(T) == 8) ? 1e-14 : 1e-7;
     a.store_P = 1;
+    a.gws = sizeof(T) == 8 ? static_cast<T*>(gws) : nullptr;
+    a.gws_teams = ops ? ops->gws_teams : 0;
     return a;
 }
 
@@ -284,24 +311,37 @@ void launch<float>(void (*)(const LevelArgs<double>&, int, void*),
 }
 
 // Algorithm 5: reduce level 0, 1, ... (tops included at their level).  With
-// l/a given the vector part of Algorithm 4 runs in the same pass.
+// l/a given the vector part of Algorithm 4 runs in the same pass.  With FP64
+// master levels the levels k >= 1 run in FP64 on the widened master data.
 template <typename T>
 void Engine::pass_reduce(const T* A_, const T* B_, const T* Q_, const T* P0_, const T* l, const T* a)
 {
     for (int k = 0; k < (int)lv.size(); ++k) {
-        LevelArgs<T> g = args<T>(k);
-        g.A = A_; g.B = B_; g.Q = Q_; g.P0inv = P0_;
-        g.l = l;
-        g.a = a;
-        if (k >= 1 && !l) { g.lxh = nullptr; g.ah = nullptr; g.lNk = nullptr; }
-        mark(PH_REDUCE, k, 1);
-        launches += g.nchunks > 0;
-        auto r32 = ops->reduce32;
-        if (prec == MHE_TF32_IR && ops->reduce32tc) r32 = ops->reduce32tc;
-        if (prec == MHE_BF16_IR && ops->reduce32bf) r32 = ops->reduce32bf;
-        launch<T>(ops->reduce64, r32, g, k >= 1, stream);
-        mark(PH_REDUCE, k, 0);
+        if (m64 && k >= 1) {
+            if (k == 1) widen_master(true, l != nullptr);
+            reduce_level<double>(k, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, l != nullptr);
+        } else {
+            reduce_level<T>(k, A_, B_, Q_, P0_, l, a, l != nullptr);
+        }
     }
+}
+
+template <typename T>
+void Engine::reduce_level(int k, const T* A_, const T* B_, const T* Q_, const T* P0_, const T* l, const T* a,
+                          bool with_rhs)
+{
+    LevelArgs<T> g = args<T>(k);
+    g.A = A_; g.B = B_; g.Q = Q_; g.P0inv = P0_;
+    g.l = l;
+    g.a = a;
+    if (k >= 1 && !with_rhs) { g.lxh = nullptr; g.ah = nullptr; g.lNk = nullptr; }
+    mark(PH_REDUCE, k, 1);
+    launches += g.nchunks > 0;
+    auto r32 = ops->reduce32;
+    if (prec == MHE_TF32_IR && ops->reduce32tc) r32 = ops->reduce32tc;
+    if (prec == MHE_BF16_IR && ops->reduce32bf) r32 = ops->reduce32bf;
+    launch<T>(ops->reduce64, r32, g, k >= 1, stream);
+    mark(PH_REDUCE, k, 0);
 }
 
 // The vector part of Algorithm 4 alone, level by level, with stored factors.
@@ -309,45 +349,106 @@ template <typename T>
 void Engine::pass_rhs(const T* l, const T* a, const T* l0, const T* a0, const T* lN)
 {
     for (int k = 0; k < (int)lv.size(); ++k) {
-        LevelArgs<T> g = args<T>(k);
-        g.rhs_off = rhs_compact ? cmp_off : in_off;
-        g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
-        g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
-        g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
-        g.active = active_mask;
-        g.any_active = any_mask;
-        mark(PH_RHS, k, 1);
-        launches += g.nchunks > 0;
-        launch<T>(ops->rhs64, ops->rhs32, g, k >= 1, stream);
-        mark(PH_RHS, k, 0);
+        if (m64 && k >= 1) {
+            if (k == 1) widen_master(false, true);
+            rhs_level<double>(k, nullptr, nullptr, nullptr, nullptr, nullptr);
+        } else {
+            rhs_level<T>(k, l, a, l0, a0, lN);
+        }
     }
 }
 
+template <typename T>
+void Engine::rhs_level(int k, const T* l, const T* a, const T* l0, const T* a0, const T* lN)
+{
+    LevelArgs<T> g = args<T>(k);
+    g.rhs_off = rhs_compact ? cmp_off : in_off;
+    if (k == 0 || !m64) {   // the level-0 problem in the compute type (read at level 0 only)
+        g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
+        g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
+    }
+    g.l = l; g.a = a; g.l0 = l0; g.a0 = a0; g.lN = lN;
+    g.active = active_mask;
+    g.any_active = any_mask;
+    mark(PH_RHS, k, 1);
+    launches += g.nchunks > 0;
+    launch<T>(ops->rhs64, ops->rhs32, g, k >= 1, stream);
+    mark(PH_RHS, k, 0);
+}
+
 // Algorithm 6 as back-substitution, top level first.  With FP64 targets z
-// given, the level-0 solution (x, w, lam of type T) is added into them.
+// given, the level-0 solution (x, w, lam of type T) is added into them.  With
+// FP64 master levels the levels k >= 1 run in FP64 (their top chunks read the
+// FP64 x~0 in x0_hi) and level 1's solution is narrowed for level 0.
 template <typename T>
 void Engine::pass_down(const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x, T* w,
                        T* lam, double* zx, double* zw, double* zl, const int* act)
 {
     for (int k = (int)lv.size() - 1; k >= 0; --k) {
-        LevelArgs<T> g = args<T>(k);
-        g.rhs_off = rhs_compact ? cmp_off : in_off;
+        if (m64 && k >= 1) {
+            down_level<double>(k, nullptr, nullptr, nullptr, nullptr, x0_hi, nullptr, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, nullptr, act);
+            if (k == 1) narrow_solution();
+        } else {
+            down_level<T>(k, l, a, l0, a0, x0, lN, x, w, lam, zx, zw, zl, act);
+        }
+    }
+}
+
+template <typename T>
+void Engine::down_level(int k, const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x,
+                        T* w, T* lam, double* zx, double* zw, double* zl, const int* act)
+{
+    LevelArgs<T> g = args<T>(k);
+    g.rhs_off = rhs_compact ? cmp_off : in_off;
+    if (k == 0 || !m64) {
         g.A = static_cast<const T*>(mA); g.B = static_cast<const T*>(mB);
         g.Q = static_cast<const T*>(mQ); g.P0inv = static_cast<const T*>(mP0);
-        g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;
-        g.x0 = x0;
-        g.lN = lN;
-        g.active = act;
-        g.any_active = act ? any_mask : nullptr;
-        if (k == 0) {
-            g.xd = x; g.wd = w; g.ld = lam;
-            g.zx = zx; g.zw = zw; g.zl = zl;
-        }
-        mark(PH_DOWN, k, 1);
-        launches += g.nchunks > 0;
-        launch<T>(ops->down64, ops->down32, g, k >= 1, stream);
-        mark(PH_DOWN, k, 0);
     }
+    g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;
+    g.x0 = x0;
+    g.lN = lN;
+    g.active = act;
+    g.any_active = act ? any_mask : nullptr;
+    if (k == 0) {
+        g.xd = x; g.wd = w; g.ld = lam;
+        g.zx = zx; g.zw = zw; g.zl = zl;
+    }
+    mark(PH_DOWN, k, 1);
+    launches += g.nchunks > 0;
+    launch<T>(ops->down64, ops->down32, g, k >= 1, stream);
+    mark(PH_DOWN, k, 0);
+}
+
+void Engine::widen_master(bool mats, bool vecs)
+{
+    const LevelBuf& U = lv[1];
+    const long long ns = plan.levels[1].nstages, n = plan.n, nb = plan.batch;
+    auto wid = [&](void* dst, void* src, long long count) {
+        rt->widen(static_cast<double*>(dst), static_cast<const float*>(src), count, stream);
+        ++launches;
+    };
+    if (mats) {
+        wid(U.Ah, U.Ah32, ns * n * n);
+        wid(U.Bh, U.Bh32, ns * n * n);
+        wid(U.Qxh, U.Qxh32, ns * n * n);
+        wid(U.QN, U.QN32, nb * n * n);
+    }
+    if (vecs) {
+        wid(U.ah, U.ah32, ns * n);
+        wid(U.lxh, U.lxh32, ns * n);
+        wid(U.lN, U.lN32, nb * n);
+    }
+}
+
+void Engine::narrow_solution()
+{
+    const LevelBuf& U = lv[1];
+    const long long ns = plan.levels[1].nstages, nx_ = plan.levels[1].nstates, n = plan.n;
+    rt->convert(static_cast<float*>(U.xd32), static_cast<const double*>(U.xd), nx_ * n, stream);
+    rt->convert(static_cast<float*>(U.wd32), static_cast<const double*>(U.wd), ns * n, stream);
+    rt->convert(static_cast<float*>(U.ld32), static_cast<const double*>(U.ld), nx_ * n, stream);
+    launches += 3;
 }
 
 template <typename T>
@@ -401,6 +502,7 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
 {
     const bool fp64 = sizeof(T) == 8;
     active_mask = nullptr;
+    x0_hi = rhs->x0;   // FP64 master levels: the top chunks above level 0 read x~0 in FP64
     if (!fused) pass_rhs<T>(l, a, nullptr, nullptr, nullptr);
     if (fp64) {
         pass_down<T>(l, a, nullptr, nullptr, x0, nullptr, reinterpret_cast<T*>(x), reinterpret_cast<T*>(w),
@@ -428,6 +530,11 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
                      any_act, stream);
         ++launches;
         any_mask = any_act;
+        if (m64) {   // the correction's x~0 for the FP64 master levels
+            rt->widen(rx0_64, static_cast<const float*>(rx0), (long long)plan.batch * plan.n, stream);
+            ++launches;
+            x0_hi = rx0_64;
+        }
         // correction problem K dz = r in UFTOC form (compact layout), then z += dz
         active_mask = active;
         rhs_compact = true;

@@ -35,6 +35,10 @@ struct ShapeOps {
                      double* Q, double* l, double* c, void* stream);
     void (*prep32)(const PrepArgs&, void* stream);
     void (*resid_mhe32)(const ResidArgs<float>&, void* stream);
+    // FP64 reductions whose workspace lives in global memory: elements of one
+    // team's workspace and the number of team slots a context provides (0: none)
+    long long gws64;
+    int gws_teams;
 };
 
 // Memory and small shape-independent steps.
@@ -58,11 +62,13 @@ struct Runtime {
     int (*error)();   // sticky error of the launches so far (0 = none)
     // optional per-pass timing marks (begin = 1 before a launch, 0 after)
     void (*mark)(void* user, int phase, int level, int begin, void* stream);
+    // FP32 -> FP64 copy of count elements (master data of FP64 master levels)
+    void (*widen)(double* dst, const float* src, long long count, void* stream);
 };
 
 enum { PH_REDUCE = 0, PH_RHS = 1, PH_DOWN = 2, PH_RESID = 3, PH_PREP = 4, PH_COUNT = 5 };
 
-struct LevelBuf {   // every array of the compute type T
+struct LevelBuf {   // every array of the level's compute type (FP64 at k >= 1 with FP64 master levels)
     ChunkDesc* chunks = nullptr;
     LevelInst* li = nullptr;
     int nchunks = 0;
@@ -70,6 +76,10 @@ struct LevelBuf {   // every array of the compute type T
     void *Ah = nullptr, *Bh = nullptr, *ah = nullptr, *Qxh = nullptr, *lxh = nullptr;
     void *QN = nullptr, *lN = nullptr;   // terminal of this level (k >= 1)
     void *xd = nullptr, *wd = nullptr, *ld = nullptr;
+    // level 1 with FP64 master levels: the FP32 master data level 0 writes (widened
+    // to the arrays above) and the FP32 copy of this level's solution level 0 reads
+    void *Ah32 = nullptr, *Bh32 = nullptr, *ah32 = nullptr, *Qxh32 = nullptr, *lxh32 = nullptr;
+    void *QN32 = nullptr, *lN32 = nullptr, *xd32 = nullptr, *wd32 = nullptr, *ld32 = nullptr;
 };
 
 // A problem already resident on the device: FP64 arrays (the residual, and
@@ -87,6 +97,7 @@ public:
     const Runtime* rt = nullptr;
     void* stream = nullptr;
     int prec = MHE_FP64;
+    bool m64 = false;                   // FP32 / TF32 / BF16 tree whose master levels k >= 1 run in FP64
     double tol = 1e-10;
     int max_refine = 0;
 
@@ -99,6 +110,9 @@ public:
     void *rl = nullptr, *ra = nullptr, *rl0 = nullptr, *ra0 = nullptr, *rlN = nullptr, *rx0 = nullptr;   // T
     float *A32 = nullptr, *B32 = nullptr, *Q32 = nullptr, *P0_32 = nullptr;   // FP32 mode: problem copies
     float *l32 = nullptr, *a32 = nullptr, *x0_32 = nullptr;
+    void* gws = nullptr;                // global-memory workspace of FP64 reductions too large for shared memory
+    double* rx0_64 = nullptr;           // FP64 master levels: the correction's x~0 in FP64
+    const double* x0_hi = nullptr;      // FP64 master levels: the x~0 their top chunks read
     unsigned long long* norms = nullptr;   // per instance |r|, |z|, |b| maxima (bit patterns)
     unsigned int* kinf = nullptr;          // per instance ||K||_inf (float bit pattern)
     int *active = nullptr, *status = nullptr, *where = nullptr, *iters = nullptr;
@@ -145,6 +159,18 @@ private:
     template <typename T>
     void pass_down(const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x, T* w,
                    T* lam, double* zx, double* zw, double* zl, const int* act);
+    template <typename T>
+    void reduce_level(int k, const T* A_, const T* B_, const T* Q_, const T* P0_, const T* l, const T* a,
+                      bool with_rhs);
+    template <typename T>
+    void rhs_level(int k, const T* l, const T* a, const T* l0, const T* a0, const T* lN);
+    template <typename T>
+    void down_level(int k, const T* l, const T* a, const T* l0, const T* a0, const T* x0, const T* lN, T* x, T* w,
+                    T* lam, double* zx, double* zw, double* zl, const int* act);
+    // FP64 master levels: level 1's FP32 master data -> FP64 (matrices and/or
+    // vectors), and level 1's FP64 solution -> the FP32 copy level 0 reads
+    void widen_master(bool mats, bool vecs);
+    void narrow_solution();
     template <typename T>
     int run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, double* x, double* w, double* lam,
                   mhe_info* info, bool skip_first_rhs);

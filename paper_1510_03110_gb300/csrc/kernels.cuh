@@ -88,11 +88,32 @@ constexpr bool tc_shape()
            (long long)op_count<float, NX, OP_REDUCE_TC>() * 4 <= 227LL * 1024;
 }
 
+// Team slots of a global-memory workspace a context provides: two CTAs of one
+// team per SM of a 152-SM GB300 (the register budget of a 128-thread team at 255
+// registers a thread allows two per SM).  A launch takes at most this many CTAs
+// and each CTA walks the chunks blockIdx.x, blockIdx.x + gridDim.x, ...
+constexpr int kGwsTeams = 2 * 152;
+
 template <typename T, int NX, int NW, int UPPER, int OP>
 __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(LevelArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int W = level_warps<T, NX, OP>();
+    if constexpr (!level_fits<T, NX, OP>()) {
+        // the workspace of one subproblem exceeds an SM's shared memory (FP64 at
+        // nx = 64): one team per CTA, its workspace in the CTA's slot of the
+        // context's global workspace (L2-resident; the FP64 pipe, at about two
+        // DFMAs per clock per SM, hides the L2 latency of the products)
+        static_assert(W == 1 && (OP == OP_REDUCE || OP == OP_RHS || OP == OP_DOWN), "one CUDA-core team per CTA");
+        if (a.any_active && *a.any_active == 0) return;
+        T* ws = a.gws + (size_t)blockIdx.x * op_count<T, NX, OP>();
+        for (int ci = blockIdx.x; ci < a.nchunks; ci += gridDim.x) {
+            if constexpr (OP == OP_REDUCE) reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, ws);
+            else if constexpr (OP == OP_RHS) rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, ws);
+            else down_chunk<T, NX, NW, UPPER != 0>(a, ci, ws);
+        }
+        return;
+    }
     const int team = team_id();
     const int ci = blockIdx.x * W + team;
     if (ci >= a.nchunks) return;   // the whole team leaves together
@@ -130,6 +151,13 @@ template <typename T, int NX, int NW, int UPPER, int OP>
 void launch_level_v(const LevelArgs<T>& a, void* stream)
 {
     constexpr int W = level_warps<T, NX, OP>();
+    if constexpr (!level_fits<T, NX, OP>()) {
+        // global-memory workspace: at most gws_teams CTAs of one team, no dynamic shared memory
+        if (!a.gws || a.gws_teams < 1) return;   // the context holds no workspace slots: nothing is launched
+        const int grid = a.nchunks < a.gws_teams ? a.nchunks : a.gws_teams;
+        k_level<T, NX, NW, UPPER, OP><<<grid, MHE_TEAM, 0, (cudaStream_t)stream>>>(a);
+        return;
+    }
     const size_t smem = (size_t)W * op_count<T, NX, OP>() * sizeof(T);
     static bool attr = false;
     if (!attr) {
@@ -287,7 +315,8 @@ ShapeEntry make_shape()
         e.ops.reduce64 = &launch_level<double, NX, NW, OP_REDUCE>;
         e.ops.rhs64 = &launch_level<double, NX, NW, OP_RHS>;
         e.ops.down64 = &launch_level<double, NX, NW, OP_DOWN>;
-    } else {   // the FP64 workspace of one subproblem exceeds an SM's shared memory: FP32_IR only
+    } else {   // the FP64 workspace of one subproblem exceeds an SM's shared memory: a translation
+               // unit of its own adds the global-memory variant (set_fp64_global_ops)
         e.ops.reduce64 = nullptr;
         e.ops.rhs64 = nullptr;
         e.ops.down64 = nullptr;
@@ -309,9 +338,25 @@ ShapeEntry make_shape()
     e.ops.assemble = &launch_assemble<NX, NW, NY>;
     e.ops.prep32 = &launch_prep<NX, NW, NY>;
     e.ops.resid_mhe32 = &launch_resid<NX, NW, float, NY>;
+    e.ops.gws64 = 0;
+    e.ops.gws_teams = 0;
     e.ny = NY;
     e.assemble = &launch_assemble<NX, NW, NY>;
     return e;
+}
+
+// The FP64 passes of a shape whose FP64 reduction workspace exceeds an SM's
+// shared memory: the reduction keeps it in global memory (k_level's global
+// variant); the right-hand-side and down passes need less and stay in shared memory.
+template <int NX, int NW>
+void set_fp64_global_ops(ShapeOps& o)
+{
+    static_assert(!level_fits<double, NX, OP_REDUCE>(), "shapes whose FP64 workspace fits use make_shape");
+    o.reduce64 = &launch_level<double, NX, NW, OP_REDUCE>;
+    o.rhs64 = &launch_level<double, NX, NW, OP_RHS>;
+    o.down64 = &launch_level<double, NX, NW, OP_DOWN>;
+    o.gws64 = op_count<double, NX, OP_REDUCE>();
+    o.gws_teams = kGwsTeams;
 }
 
 }  // namespace mhe

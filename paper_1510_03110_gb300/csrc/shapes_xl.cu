@@ -2,16 +2,23 @@
 // four warps (128 threads): 64,32,32.  A subproblem's FP32 workspace is
 // ~168 KB of shared memory (one per SM), so one warp per subproblem would leave
 // the SM nearly idle; the team shares each stage's products four times wider.
-// Their FP64 workspace does not fit an SM: these shapes run in MHE_FP32_IR.
+// Their FP64 reduction workspace does not fit an SM: its FP64 passes, with the
+// workspace in global memory, come from shapes_xl64.cu.
 #define MHE_TEAM 128
 #include "kernels.cuh"
 
 namespace mhe {
 
+void shapes_xl_fp64(ShapeOps& o);   // shapes_xl64.cu
+
 int shapes_xl(ShapeEntry* out, int cap)
 {
     int k = 0;
-    if (k < cap) out[k++] = make_shape<64, 32, 32>();
+    if (k < cap) {
+        out[k] = make_shape<64, 32, 32>();
+        shapes_xl_fp64(out[k].ops);
+        ++k;
+    }
     return k;
 }
 

@@ -32,7 +32,7 @@ c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 class mhe_dims(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nw", c_int), ("batch", c_int), ("N", ctypes.POINTER(c_int)),
                 ("prec", c_int), ("leaf_len", c_int), ("branching", c_int), ("top_len", c_int),
-                ("refine_tol", c_double), ("max_refine", c_int)]
+                ("refine_tol", c_double), ("max_refine", c_int), ("fp64_masters", c_int)]
 
 
 class mhe_matrices(ctypes.Structure):
@@ -168,10 +168,11 @@ def shapes():
 
 
 def make_dims(nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0, refine_tol=0.0,
-              max_refine=-1):
+              max_refine=-1, fp64_masters=False):
     N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).reshape(-1))
     d = mhe_dims(int(nx), int(nw), int(N.size), N.ctypes.data_as(ctypes.POINTER(c_int)), int(prec),
-                 int(leaf_len), int(branching), int(top_len), float(refine_tol), int(max_refine))
+                 int(leaf_len), int(branching), int(top_len), float(refine_tol), int(max_refine),
+                 int(bool(fp64_masters)))
     return d, N
 
 
@@ -380,13 +381,13 @@ class Solver:
     """
 
     def __init__(self, nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0,
-                 refine_tol=0.0, max_refine=-1, stream=None):
+                 refine_tol=0.0, max_refine=-1, stream=None, fp64_masters=False):
         import torch
         self.nx, self.nw = int(nx), int(nw)
         self.N = np.asarray(N, dtype=np.int64).reshape(-1)
         self.batch = int(self.N.size)
         self.dims, self._N32 = make_dims(nx, nw, self.N, prec, leaf_len, branching, top_len,
-                                         refine_tol, max_refine)
+                                         refine_tol, max_refine, fp64_masters)
         self.stream = stream
         self.ctx = mhe_create(self.dims, stream)
         self.X = int(np.sum(self.N + 1))

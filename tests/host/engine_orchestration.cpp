@@ -41,7 +41,9 @@ struct Rec {
     const void *l = nullptr, *a = nullptr, *x0 = nullptr, *l0 = nullptr, *a0 = nullptr, *lN = nullptr;
     const void *rhs_off = nullptr, *active = nullptr, *any_active = nullptr, *chunks = nullptr, *li = nullptr;
     const void *A = nullptr, *Q = nullptr;
+    const void *dst = nullptr, *src = nullptr;   // convert / widen
     int mode = -1;
+    int ts = 0;   // element size of a level pass's compute type
 };
 
 std::vector<Rec> g_log;
@@ -70,8 +72,19 @@ void f_convert(float* d, const double* s, long long count, void*)
 {
     Rec r;
     r.op = "convert";
+    r.dst = d;
+    r.src = s;
     g_log.push_back(r);
     for (long long i = 0; i < count; ++i) d[i] = (float)s[i];
+}
+void f_widen(double* d, const float* s, long long count, void*)
+{
+    Rec r;
+    r.op = "widen";
+    r.dst = d;
+    r.src = s;
+    g_log.push_back(r);
+    for (long long i = 0; i < count; ++i) d[i] = (double)s[i];
 }
 int g_pass = 0;
 void f_finalize(int batch, const unsigned long long*, const unsigned int*, int* active, int*, const int*, const int*,
@@ -89,7 +102,8 @@ void f_finalize(int batch, const unsigned long long*, const unsigned int*, int* 
         ++g_pass;
     }
 }
-const Runtime kFakeRuntime = {f_alloc, f_release, f_memset0, f_copy, f_finalize, f_convert, f_sync, f_error, nullptr};
+const Runtime kFakeRuntime = {f_alloc, f_release, f_memset0, f_copy, f_finalize, f_convert, f_sync, f_error, nullptr,
+                              f_widen};
 
 template <typename T>
 void rec_level(const char* op, const LevelArgs<T>& g, int upper)
@@ -105,6 +119,7 @@ void rec_level(const char* op, const LevelArgs<T>& g, int upper)
     r.l = g.l; r.a = g.a; r.x0 = g.x0; r.l0 = g.l0; r.a0 = g.a0; r.lN = g.lN;
     r.rhs_off = g.rhs_off; r.active = g.active; r.any_active = g.any_active; r.chunks = g.chunks; r.li = g.li;
     r.A = g.A; r.Q = g.Q;
+    r.ts = (int)sizeof(T);
     g_log.push_back(r);
 }
 template <typename T>
@@ -258,7 +273,7 @@ long long counted_launches()
     long long c = 0;
     for (const Rec& r : g_log) {
         if (r.op == "reduce" || r.op == "reduce_tc" || r.op == "rhs" || r.op == "down") c += r.nchunks > 0;
-        else c += 1;   // knorm, convert, resid, finalize, prep, assemble
+        else c += 1;   // knorm, convert, widen, resid, finalize, prep, assemble
     }
     return c;
 }
@@ -518,6 +533,90 @@ void scenario_replan()
     e.release();
 }
 
+// FP64 master levels: level 0 in FP32, levels k >= 1 in FP64.  After level 0's
+// reduction its FP32 master data are widened into level 1's FP64 arrays, which
+// level 1 reads; after level 1's down pass its solution is narrowed into the FP32
+// copy level 0 reads; the top chunks above level 0 read x~0 in FP64 (the caller's
+// for the first solve, the widened correction x~0 for each correction).
+void scenario_fp64_masters()
+{
+    Problem p(4, 2, {7, 40, 100, 2});
+    ShapeOps ops = make_ops(4, 2, false);
+    Engine e;
+    const int R = 2;
+    mhe_dims d = dims_of(p, MHE_FP32_IR, 4, 2, 2, R);
+    d.fp64_masters = 1;
+    CHECK(e.init(d, &ops, &kFakeRuntime, nullptr) == MHE_OK, "init: %s", e.err.c_str());
+    CHECK(e.m64 && e.plan.levels.size() >= 3, "FP64 master levels over several levels");
+    g_log.clear();
+    g_converge_after = 2;
+    mhe_matrices mt = p.mats();
+    CHECK(e.factor(mt, nullptr, nullptr, nullptr, nullptr) == MHE_OK, "factor: %s", e.err.c_str());
+    const std::vector<Rec> red = of("reduce");
+    const int L = (int)e.plan.levels.size();
+    CHECK((int)red.size() == L, "one reduction per level");
+    for (int k = 0; k < L; ++k) CHECK(red[k].ts == (k == 0 ? 4 : 8), "level %d compute type %d bytes", k, red[k].ts);
+    {
+        const std::vector<Rec> wid = of("widen");
+        CHECK(wid.size() == 4, "the factor widens A^, B^, Q^_x and the terminal (%d)", (int)wid.size());
+        CHECK(wid[0].src == red[0].Ah_up && wid[0].dst == red[1].Ah, "A^ widened from level 0 to level 1");
+        CHECK(wid[1].src == red[0].Bh_up && wid[1].dst == red[1].Bh, "B^ widened");
+        CHECK(wid[2].src == red[0].Qxh_up && wid[2].dst == red[1].Qxh, "Q^_x widened");
+        CHECK(wid[3].src == red[0].QN_up && wid[3].dst == red[1].QNk, "terminal widened");
+        CHECK(find_from("widen", 0) > find_from("reduce", 0), "widening after level 0's reduction");
+        for (int k = 2; k < L; ++k)
+            CHECK(red[k].Ah == red[k - 1].Ah_up && red[k].QNk == red[k - 1].QN_up, "FP64 level %d chained", k);
+    }
+    const size_t f_end = g_log.size();
+    mhe_rhs rh = p.rhs();
+    CHECK(e.solve(&rh, p.x.data(), p.w.data(), p.lam.data(), p.info.data(), false) == MHE_OK, "solve: %s",
+          e.err.c_str());
+    const size_t first_resid = find_from("resid", f_end);
+    {
+        const std::vector<Rec> rhs = of("rhs", f_end, first_resid);
+        CHECK((int)rhs.size() == L && rhs[0].ts == 4 && rhs[1].ts == 8, "right-hand-side pass types");
+        const std::vector<Rec> wid = of("widen", f_end, first_resid);
+        CHECK(wid.size() == 3 && wid[0].src == rhs[0].ah_up && wid[0].dst == rhs[1].ah &&
+                  wid[1].src == rhs[0].lxh_up && wid[1].dst == rhs[1].lxh && wid[2].src == rhs[0].lN_up &&
+                  wid[2].dst == rhs[1].lNk,
+              "the right-hand-side pass widens a^, l^_x and the terminal vector");
+        const std::vector<Rec> down = of("down", f_end, first_resid);
+        CHECK((int)down.size() == L && down[L - 1].level == 0 && down[L - 1].ts == 4 && down[L - 2].ts == 8,
+              "down pass: FP64 levels first, level 0 last in FP32");
+        for (int i = 0; i + 1 < L; ++i)
+            CHECK(down[i].x0 == (const void*)p.x0.data(), "the first solve's FP64 levels read the caller's x~0");
+        const std::vector<Rec> nar = of("convert", find_from("down", f_end), first_resid);
+        const Rec& d1 = down[L - 2];
+        const Rec& d0 = down[L - 1];
+        CHECK(nar.size() == 3 && nar[0].src == d1.xd && nar[0].dst == d0.xd_up && nar[1].src == d1.wd &&
+                  nar[1].dst == d0.wd_up && nar[2].src == d1.ld && nar[2].dst == d0.ld_up,
+              "level 1's solution narrowed into the FP32 copy level 0 reads");
+        size_t lvl0 = f_end, conv = f_end;   // positions of level 0's down pass and of the last narrowing
+        for (size_t i = f_end; i < first_resid; ++i) {
+            if (g_log[i].op == "down" && g_log[i].level == 0) lvl0 = i;
+            if (g_log[i].op == "convert") conv = i;
+        }
+        CHECK(conv < lvl0, "narrowing before level 0's down pass");
+    }
+    // each correction: the correction's x~0 widened, and the FP64 levels' top chunks read it
+    size_t pos = first_resid;
+    for (int it = 0; it < R; ++it) {
+        const size_t fin = find_from("finalize", pos);
+        const size_t next = find_from("resid", fin);
+        const std::vector<Rec> wid = of("widen", fin, next);
+        CHECK(!wid.empty() && wid[0].dst == (const void*)e.rx0_64 && wid[0].src == e.rx0,
+              "correction %d widens its x~0", it);
+        const std::vector<Rec> down = of("down", fin, next);
+        CHECK((int)down.size() == L, "correction %d down pass", it);
+        for (int i = 0; i + 1 < L; ++i)
+            CHECK(down[i].x0 == (const void*)e.rx0_64, "correction %d: FP64 level reads the widened x~0", it);
+        CHECK(down[L - 1].x0 == e.rx0, "correction %d: level 0 reads the FP32 x~0", it);
+        pos = next;
+    }
+    CHECK(e.launches == counted_launches(), "launch counter %lld, launches seen %lld", e.launches, counted_launches());
+    e.release();
+}
+
 }  // namespace
 
 int main()
@@ -528,6 +627,7 @@ int main()
     if (!g_fail) scenario_errors();
     if (!g_fail) scenario_estimate();
     if (!g_fail) scenario_replan();
+    if (!g_fail) scenario_fp64_masters();
     if (g_fail) return 1;
     printf("OK\n");
     return 0;

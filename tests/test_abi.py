@@ -192,3 +192,27 @@ def test_plan_info_unpacks_the_levels(monkeypatch):
             return 3
     monkeypatch.setattr(mhe, "lib", lambda: Fake())
     assert mhe.mhe_plan_info(None) == [(0, 40, 1000), (1, 9, 39), (2, 1, 8)]
+
+
+def test_fp64_workspace_at_nx64_and_fp64_master_levels(L):
+    """FP64 at nx = 64 is accepted: its workspace includes the reduction's global-memory
+    team slots (two 128-thread teams per SM of 152, ~342 KB each).  FP64 master levels
+    enlarge the FP32 workspace by the FP64 copies of the upper levels' arrays."""
+    d64, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_FP64)
+    d32, _ = mhe.make_dims(64, 32, [100, 7], prec=mhe.MHE_FP32_IR)
+    assert mhe.mhe_workspace_bytes(d64) > 304 * 342 * 1024 > mhe.mhe_workspace_bytes(d32) > 0
+    for nx, nw in [(24, 12), (64, 32), (6, 3)]:
+        plain, _ = mhe.make_dims(nx, nw, [2000, 300], prec=mhe.MHE_FP32_IR, leaf_len=8, branching=4, top_len=4)
+        mixed, _ = mhe.make_dims(nx, nw, [2000, 300], prec=mhe.MHE_FP32_IR, leaf_len=8, branching=4, top_len=4,
+                                 fp64_masters=True)
+        assert mhe.mhe_workspace_bytes(mixed) > mhe.mhe_workspace_bytes(plain) > 0
+    assert ctypes_sizeof_dims_matches_header()
+
+
+def ctypes_sizeof_dims_matches_header():
+    """The binding's mhe_dims has every field of the header's struct, in order."""
+    txt = open(os.path.join(ROOT, "include", "mhe.h")).read()
+    body = txt[txt.index("typedef struct {\n    int nx;"):]
+    body = body[:body.index("} mhe_dims;")]
+    names = re.findall(r"^\s+(?:const\s+)?(?:int|double)\*?\s+(\w+);", body, re.M)
+    return names == [f[0] for f in mhe.mhe_dims._fields_]

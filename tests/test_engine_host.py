@@ -20,20 +20,21 @@ ENGINE = open(os.path.join(CSRC, "engine.cpp")).read()
 
 MUTATIONS = {
     # Algorithm 6 run bottom-up instead of top level first
-    "down_pass_bottom_up": ("for (int k = (int)lv.size() - 1; k >= 0; --k) {\n        LevelArgs<T> g = args<T>(k);\n"
-                            "        g.rhs_off = rhs_compact ? cmp_off : in_off;\n        g.A = static_cast<const T*>(mA); "
-                            "g.B = static_cast<const T*>(mB);\n        g.Q = static_cast<const T*>(mQ); "
-                            "g.P0inv = static_cast<const T*>(mP0);\n        g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;\n"
-                            "        g.x0 = x0;",
-                            "for (int k = 0; k < (int)lv.size(); ++k) {\n        LevelArgs<T> g = args<T>(k);\n"
-                            "        g.rhs_off = rhs_compact ? cmp_off : in_off;\n        g.A = static_cast<const T*>(mA); "
-                            "g.B = static_cast<const T*>(mB);\n        g.Q = static_cast<const T*>(mQ); "
-                            "g.P0inv = static_cast<const T*>(mP0);\n        g.l = l; g.a = a; g.l0 = l0; g.a0 = a0;\n"
-                            "        g.x0 = x0;"),
+    "down_pass_bottom_up": ("for (int k = (int)lv.size() - 1; k >= 0; --k) {\n        if (m64 && k >= 1) {\n"
+                            "            down_level",
+                            "for (int k = 0; k < (int)lv.size(); ++k) {\n        if (m64 && k >= 1) {\n"
+                            "            down_level"),
     # a level reads the wrong part of its parent's solution
-    "parent_w_for_x": ("a.xd_up = static_cast<const T*>(U.xd);", "a.xd_up = static_cast<const T*>(U.wd);"),
+    "parent_w_for_x": ("a.xd_up = static_cast<const T*>(st ? U.xd32 : U.xd);",
+                       "a.xd_up = static_cast<const T*>(st ? U.xd32 : U.wd);"),
     # a level reads its own master data instead of the data the level below wrote
-    "master_data_not_chained": ("a.Ah_up = static_cast<T*>(U.Ah);", "a.Ah_up = static_cast<T*>(L.Pst);"),
+    "master_data_not_chained": ("a.Ah_up = static_cast<T*>(st ? U.Ah32 : U.Ah);", "a.Ah_up = static_cast<T*>(L.Pst);"),
+    # FP64 master levels: level 1 reads its FP32 master data without the widening
+    "fp64_masters_not_widened": ("        wid(U.Bh, U.Bh32, ns * n * n);\n", ""),
+    # FP64 master levels: level 0's down pass reads a stale FP32 copy of level 1's solution
+    "fp64_masters_not_narrowed": ("            if (k == 1) narrow_solution();\n", ""),
+    # FP64 master levels: the corrections' top chunks read the first solve's x~0
+    "fp64_masters_correction_x0": ("            x0_hi = rx0_64;\n", ""),
     # the master-problem variant not selected at level 1
     "upper_from_level_2": ("launch<T>(ops->reduce64, r32, g, k >= 1, stream);",
                            "launch<T>(ops->reduce64, r32, g, k >= 2, stream);"),

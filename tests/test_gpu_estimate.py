@@ -217,10 +217,3 @@ def test_tensor_precisions_on_a_shape_without_tensor_products_are_fp32():
         out.append(x.clone())
         s.close()
     assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
-
-
-def test_nx64_fp64_is_refused():
-    """The FP64 workspace of an nx=64 subproblem exceeds an SM's shared memory."""
-    with pytest.raises(mhe.MheError) as e:
-        mhe.Solver(64, 32, [40], prec=mhe.MHE_FP64)
-    assert e.value.code == -1
