@@ -35,6 +35,7 @@ from paper_1510_03110_gb300 import synth  # noqa: E402
 
 METRIC = "KKT solves/s and p99 latency vs plain batched serial Riccati, same GPU, rel-res<=1e-8"
 RELRES_BAR = 1e-8
+LONG_N = 131072   # horizon of the long workload (--N)
 
 
 def flops_leaf_stage(n, m):
@@ -123,12 +124,14 @@ def make_workload(name):
                     l2="inputs larger than L2 (26 GB resident)")
         return desc, [dict(n=n, m=m, q=m, N=np.full(count, N, dtype=np.int64), pool=pool, idx=idx, x0=x0)], 1
     if name == "long":
-        p = synth.mhe_instance(1, 20, 10, 10, 131072)
+        N = LONG_N
+        p = synth.mhe_instance(1, 20, 10, 10, N)
         pool = {k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")}
         desc = dict(workload="long-horizon single MHE instance", instances=1, nx=20, nw=10, ny=10,
-                    N=131072, precision="FP64", seed=1, l2="inputs larger than L2")
-        return desc, [dict(n=20, m=10, q=10, N=np.array([131072]), pool=pool,
-                           idx=np.arange(131071), x0=p["x0"][None, :])], 0
+                    N=N, precision="FP64", seed=1,
+                    l2="inputs larger than L2" if N * 8400 > 129e6 else "inputs smaller than L2 (L2 not flushed)")
+        return desc, [dict(n=20, m=10, q=10, N=np.array([N]), pool=pool,
+                           idx=np.arange(N - 1), x0=p["x0"][None, :])], 0
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -394,6 +397,19 @@ def run_gpu(args):
         for st in bstreams:
             stream.wait_stream(st)
 
+    def step_serial(ss):
+        # the same step with the buckets one after another
+        prev = torch.cuda.Event()
+        prev.record(stream)
+        for bk, s, st in zip(buckets, ss, bstreams):
+            d = bk["dev"]
+            st.wait_event(prev)
+            s.estimate(bk["q"], d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"], d["x0"], d["P0inv"],
+                       out=s.out)
+            prev = torch.cuda.Event()
+            prev.record(st)
+        stream.wait_event(prev)
+
     for _ in range(args.warmup):
         step(solvers)
     torch.cuda.synchronize()
@@ -480,18 +496,52 @@ def run_gpu(args):
     kernels = [x for x in (roof(r) for r in ranked[:6]) if x]
     roofline = kernels[0] if kernels else None
 
+    # every pass once more with the buckets one after another (no stream overlap): the
+    # per-kernel roofline fractions of kernels[] (the timed step overlaps the buckets, so
+    # there a kernel's pass time includes the SMs the other buckets hold)
+    kernels_serial = []
+    if len(buckets) > 1:
+        for s in solvers:
+            mhe.mhe_timing_read(s.ctx)
+            mhe.mhe_timing_enable(s.ctx, True)
+        step_serial(solvers)
+        torch.cuda.synchronize()
+        spasses = []
+        for bk, s in zip(buckets, solvers):
+            for (ph, lvl, calls, tms, tmax) in mhe.mhe_timing_read(s.ctx):
+                spasses.append(dict(nx=bk["n"], phase=ph, level=lvl, calls=calls, ms=tms, ms_max=tmax))
+            mhe.mhe_timing_enable(s.ctx, False)
+        kernels_serial = [x for x in (roof(r) for r in sorted(spasses, key=lambda r: -r["ms"])[:8]) if x]
+    else:
+        kernels_serial = kernels
+
+    # error against the FP64 oracle on sampled instances (the oracle solves each one on the
+    # host) and the library's own per-instance estimate (the last correction's size) for all
+    err_oracle = sample_errors(buckets, solvers, per_bucket=args.err_samples)
+    est = np.asarray(infos["est_relerr"], dtype=np.float64)
+    est_summary = dict(max=float(est.max()), p50=float(np.median(est)), p99=float(np.quantile(est, 0.99)),
+                       instances=int(est.size),
+                       note="mhe_info.est_relerr = ||dz_last||_inf / ||z||_inf of the last correction, per instance")
+
     # plain serial Riccati on the same GPU: one chunk per instance (top_len >= N)
     base = {}
-    arms = [] if args.no_baseline else [("serial_same_precision", sprec, max_refine if prec == 1 else 0, None)] + \
-        ([("serial_fp64", 0, 0, None)] if (prec == 1 and args.serial_fp64) else []) + \
-        ([("fp32_simt_products_same_plan", 1, max_refine, plans)] if sprec in (2, 3) else [])
-    for name, bprec, mref, bplans in arms:
+    xl = args.workload in ("xl", "xl_profile")
+    tree_plans = [dict(nx=b["n"], leaf_len=16, branching=4, top_len=4) for b in buckets]
+    short_plans = [dict(nx=b["n"], leaf_len=8, branching=4, top_len=4) for b in buckets]
+    # (name, precision, corrections, plans (None: serial), FP64 master levels)
+    arms = [] if args.no_baseline else [("serial_same_precision", sprec, max_refine if prec == 1 else 0, None, 0)] + \
+        ([("serial_fp64", 0, 2, None, 0)] if (prec == 1 and (args.serial_fp64 or xl)) else []) + \
+        ([("tree_fp64", 0, 2, tree_plans, 0)] if (prec == 1 and xl) else []) + \
+        ([("tree_short_leaves_fp64_masters", sprec, max_refine, short_plans, 1),
+          ("tree_short_leaves_fp32_masters", sprec, max_refine, short_plans, 0)] if (prec == 1 and xl) else []) + \
+        ([("fp32_simt_products_same_plan", 1, max_refine, plans, 0)] if sprec in (2, 3) else [])
+    for name, bprec, mref, bplans, m64 in arms:
         ss = []
         for i, bk in enumerate(buckets):
             bpl = dict(top_len=int(np.max(bk["N"])) + 1) if bplans is None else \
                 {k: v for k, v in bplans[i].items() if k != "nx"}
             s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
-                           stream=bstreams[i], **bpl)
+                           stream=bstreams[i], fp64_masters=bool(m64), **bpl)
             s.out = s.outputs()
             ss.append(s)
         step(ss)
@@ -506,7 +556,12 @@ def run_gpu(args):
         bms = e0.elapsed_time(e1) / k
         binf = np.concatenate([s.infos() for s in ss])
         base[name] = dict(value=round(instances / (bms * 1e-3), 3), ms_per_step=round(bms, 3),
-                          relres_max=float(np.max(binf["relres"])), steps=k)
+                          relres_max=float(np.max(binf["relres"])), steps=k,
+                          all_ok=bool(np.all(binf["status"] == 0)),
+                          refine_iters_max=int(np.max(binf["refine_iters"])),
+                          precision={0: "FP64", 1: "FP32+IR", 2: "TF32+IR", 3: "BF16+IR"}[bprec] +
+                          (" + FP64 master levels" if m64 else ""),
+                          plan="serial" if bplans is None else {k: v for k, v in bplans[0].items() if k != "nx"})
         for s in ss:
             s.close()
 
@@ -549,12 +604,202 @@ def run_gpu(args):
                                            serving_p99=round(serving["serial"]["p99_ms"] /
                                                              max(serving["tree"]["p99_ms"], 1e-9), 2)))),
                 serving=serving,
-                roofline=roofline, kernels=kernels[1:], passes=sorted(passes, key=lambda r: -r["ms"])[:8],
+                err_vs_oracle=err_oracle, est_relerr=est_summary,
+                roofline=roofline, kernels=kernels_serial, kernels_overlapped=kernels[1:],
+                passes=sorted(passes, key=lambda r: -r["ms"])[:8],
                 cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clk,
                 wall_s=round(wall, 3))
     print(json.dumps(line))
     for s in solvers:
         s.close()
+
+
+def sample_errors(buckets, solvers, per_bucket=2, seed=13):
+    """max over sampled instances of ||z - z_oracle||_inf / ||z_oracle||_inf per block (x, w,
+    lambda): the GPU solution of each sampled instance against the FP64 oracle (plain C)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    rows = []
+    for bk, s in zip(buckets, solvers):
+        n, m, q = bk["n"], bk["m"], bk["q"]
+        Nb = np.asarray(bk["N"])
+        offs = np.concatenate([[0], np.cumsum(Nb - 1)])
+        xo = np.concatenate([[0], np.cumsum(Nb + 1)])
+        wo = np.concatenate([[0], np.cumsum(n + (Nb - 1) * m)])
+        x, w, lam = s.out
+        for j in rng.choice(len(Nb), size=min(per_bucket, len(Nb)), replace=False):
+            p = synth.instance_from_pool(bk["pool"], bk["idx"][offs[j]:offs[j + 1]], bk["x0"][j], n, m, q)
+            ref = oracle.riccati(oracle.mhe_to_uftoc(p))
+            got = dict(x=x[xo[j]:xo[j + 1]].cpu().numpy(), lam=lam[xo[j]:xo[j + 1]].cpu().numpy(),
+                       w=w[wo[j]:wo[j + 1]].cpu().numpy())
+            e = 0.0
+            for k in ("x", "w", "lam"):
+                a, b = np.asarray(got[k]).ravel(), np.asarray(ref[k]).ravel()
+                e = max(e, float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
+            rows.append(dict(nx=n, instance=int(j), N=int(Nb[j]), rel_err=e))
+    return dict(max=max(r["rel_err"] for r in rows) if rows else None, samples=rows,
+                definition="max over x, w, lambda of ||z - z_oracle||_inf / ||z_oracle||_inf")
+
+
+def run_long_sweep(args):
+    """Depth scaling of the tree on one long horizon (nx = 20, nw = ny = 10, FP64): N in
+    {1024, 16384, 131072} (prefixes of one seeded instance) x leaf_len in {8, 16, 32, 64} x
+    branching in {2, 4, 8, 16} (top_len 4), and the serial recursion (top_len > N) at each N.
+    Per plan: levels, ms per solve (CUDA events, best of the timed repetitions), relres, the
+    level-0 reduction's FP64-pipe fraction; per N the error of the fastest plan against the
+    FP64 oracle."""
+    import torch
+
+    import oracle
+    from paper_1510_03110_gb300 import build, mhe
+    build.build()
+    torch.cuda.set_device(0)
+    Ns = [int(v) for v in args.sweep_N.split(",")]
+    leaves = [int(v) for v in args.sweep_leaf.split(",")]
+    brs = [int(v) for v in args.sweep_branching.split(",")]
+    n, m, q = 20, 10, 10
+    t0 = time.time()
+    full = synth.mhe_instance(1, n, m, q, max(Ns))
+    gen_s = time.time() - t0
+    pk = peaks()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N in Ns:
+        p = dict(full, N=N, **{k: full[k][:N - 1] for k in ("A", "B", "C", "R", "a", "yt", "wt")})
+        bk = dict(n=n, m=m, q=q, N=np.array([N]), pool={k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")},
+                  idx=np.arange(N - 1), x0=p["x0"][None, :])
+        d = to_device(bk)
+        S = N - 1
+        Q = torch.empty(S, (n + m) ** 2, dtype=torch.float64, device="cuda")
+        l = torch.empty(S, n + m, dtype=torch.float64, device="cuda")
+        mhe.mhe_assemble(n, m, q, d["C"], d["R"], d["yt"], d["wt"], Q, l)
+        plans = [(lf, br, 4) for lf in leaves for br in brs] + [(16, 4, N + 1)]
+        best = None
+        for (lf, br, top) in plans:
+            s = mhe.Solver(n, m, [N], prec=mhe.MHE_FP64, leaf_len=lf, branching=br, top_len=top)
+            out = s.outputs()
+            reps = 1 if (top > N and N > 20000) else args.sweep_reps
+            s.factor_solve(d["A"], d["B"], Q, d["P0inv"], l, d["a"], d["x0"], out=out)   # warm-up
+            torch.cuda.synchronize()
+            mhe.mhe_timing_read(s.ctx)
+            mhe.mhe_timing_enable(s.ctx, True)
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.factor_solve(d["A"], d["B"], Q, d["P0inv"], l, d["a"], d["x0"], out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            tim = mhe.mhe_timing_read(s.ctx)
+            red0 = [r for r in tim if r[0] == "reduce" and r[1] == 0]
+            ms_red0 = red0[0][3] / max(red0[0][2], 1) if red0 else None
+            f = (flops_serial_stage if top > N else flops_leaf_stage)(n, m) * N
+            info = s.infos()
+            levels = len(mhe.mhe_plan_info(s.ctx))
+            row = dict(N=N, plan="serial" if top > N else dict(leaf_len=lf, branching=br, top_len=top),
+                       levels=levels, ms=round(min(times), 4), relres=float(info["relres"][0]),
+                       status=int(info["status"][0]),
+                       level0_reduce_ms=round(ms_red0, 4) if ms_red0 else None,
+                       level0_reduce_fp64_frac=round(f / (ms_red0 * 1e-3) / 1e12 / pk["fp64_tflops"], 4)
+                       if ms_red0 else None)
+            rows.append(row)
+            if top <= N and (best is None or row["ms"] < best[0]["ms"]):
+                best = (row, [v.clone() for v in out])
+            s.close()
+        # the fastest plan's solution against the FP64 oracle
+        ref = oracle.riccati(oracle.mhe_to_uftoc(p))
+        x, w, lam = best[1]
+        e = 0.0
+        for k, a in (("x", x), ("w", w), ("lam", lam)):
+            a = a.cpu().numpy().ravel()
+            b = np.asarray(ref[k]).ravel()
+            e = max(e, float(np.abs(a - b).max() / np.abs(b).max()))
+        best[0]["rel_err_vs_oracle"] = e
+        del d, Q, l
+        torch.cuda.empty_cache()
+    out = dict(workload="long-horizon depth sweep, nx=20, nw=ny=10, FP64", seed=1, generation_s=round(gen_s, 1),
+               fp64_peak_tflops=pk["fp64_tflops"], rows=rows)
+    summary = []
+    for N in Ns:
+        r = [x for x in rows if x["N"] == N]
+        tree = min((x for x in r if x["plan"] != "serial"), key=lambda x: x["ms"])
+        ser = [x for x in r if x["plan"] == "serial"][0]
+        summary.append(dict(N=N, best_tree_ms=tree["ms"], best_plan=tree["plan"], levels=tree["levels"],
+                            serial_ms=ser["ms"], speedup=round(ser["ms"] / tree["ms"], 2),
+                            rel_err_vs_oracle=tree.get("rel_err_vs_oracle")))
+    out["summary"] = summary
+    return out
+
+
+def run_small(args):
+    """Config 1: one instance nx = 4, nw = ny = 2, N = 64, FP64, seed 0: the latency of one
+    Newton step through the C-ABI (inputs resident on the device; each solve timed with CUDA
+    events and synchronised), for the tree plan, the serial plan and the allocation-free
+    single-kernel entry; error against the FP64 oracle."""
+    import torch
+
+    import oracle
+    from paper_1510_03110_gb300 import build, mhe
+    build.build()
+    torch.cuda.set_device(0)
+    n, m, q, N = 4, 2, 2, 64
+    p = synth.mhe_instance(0, n, m, q, N)
+    ref = oracle.riccati(oracle.mhe_to_uftoc(p))
+    bk = dict(n=n, m=m, q=q, N=np.array([N]), pool={k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")},
+              idx=np.arange(N - 1), x0=p["x0"][None, :])
+    d = to_device(bk)
+    Q = torch.empty(N - 1, (n + m) ** 2, dtype=torch.float64, device="cuda")
+    l = torch.empty(N - 1, n + m, dtype=torch.float64, device="cuda")
+    mhe.mhe_assemble(n, m, q, d["C"], d["R"], d["yt"], d["wt"], Q, l)
+    stream = torch.cuda.current_stream()
+    K = max(args.steps, 50)
+    out = {}
+
+    def lat(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(K):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts = np.array(ts)
+        return dict(p50_ms=round(float(np.median(ts)), 4), p99_ms=round(float(np.quantile(ts, 0.99)), 4),
+                    mean_ms=round(float(ts.mean()), 4))
+
+    def err(x, w, lam):
+        e = 0.0
+        for k, a in (("x", x), ("w", w), ("lam", lam)):
+            a = a.cpu().numpy().ravel()
+            b = np.asarray(ref[k]).ravel()
+            e = max(e, float(np.abs(a - b).max() / np.abs(b).max()))
+        return e
+
+    for name, plan in [("tree", dict(leaf_len=4, branching=2, top_len=2)), ("serial", dict(top_len=N + 1))]:
+        s = mhe.Solver(n, m, [N], prec=mhe.MHE_FP64, max_refine=0, **plan)
+        o = s.outputs()
+        r = lat(lambda: s.factor_solve(d["A"], d["B"], Q, d["P0inv"], l, d["a"], d["x0"], out=o))
+        r["rel_err_vs_oracle"] = err(*o)
+        r["relres"] = float(s.infos()["relres"][0])
+        r["levels"] = len(mhe.mhe_plan_info(s.ctx))
+        r["launches_per_solve"] = mhe.mhe_launch_count(s.ctx) // (K + max(args.warmup, 3))
+        out[name] = r
+        s.close()
+    x = torch.empty((N + 1) * n, dtype=torch.float64, device="cuda")
+    w = torch.empty(n + (N - 1) * m, dtype=torch.float64, device="cuda")
+    lam = torch.empty((N + 1) * n, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    r = lat(lambda: mhe.mhe_solve_serial_noalloc(n, m, N, d["A"], d["B"], Q.reshape(-1), d["P0inv"], l.reshape(-1),
+                                                 d["a"], d["x0"], x, w, lam, st))
+    r["rel_err_vs_oracle"] = err(x, w, lam)
+    r["launches_per_solve"] = 1
+    out["single_kernel_serial"] = r
+    return out
 
 
 def run_serve(args):
@@ -794,13 +1039,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks"])
+                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks", "small"])
+    ap.add_argument("--N", type=int, default=131072, help="long workload: the horizon")
+    ap.add_argument("--sweep", action="store_true", help="long workload: the depth sweep over N, leaf, branching")
+    ap.add_argument("--sweep-N", default="1024,16384,131072")
+    ap.add_argument("--sweep-leaf", default="8,16,32,64")
+    ap.add_argument("--sweep-branching", default="2,4,8,16")
+    ap.add_argument("--sweep-reps", type=int, default=3)
+    ap.add_argument("--err-samples", type=int, default=2, help="instances per bucket checked against the oracle")
     ap.add_argument("--plan", default=None, help="leaf_len,branching,top_len used instead of the autotuner")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
     ap.add_argument("--estimators", type=int, default=1024, help="serving: estimator pool")
     ap.add_argument("--serve-bytes", type=int, default=96 << 30, help="serving: device-memory budget")
-    ap.add_argument("--serve-duration", type=float, default=2.0,
+    ap.add_argument("--serve-duration", type=float, default=10.0,
                     help="batch workload: seconds of a serving run appended to the line (0: none)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the serial-plan GPU baseline")
     ap.add_argument("--baseline-steps", type=int, default=2)
@@ -823,6 +1075,28 @@ def main():
         return
     if args.workload == "alu_peaks":
         raise SystemExit(run_alu_peaks())
+    global LONG_N
+    LONG_N = args.N
+    if args.workload == "long" and args.sweep:
+        res = run_long_sweep(args)
+        big = res["summary"][-1]
+        print(json.dumps(dict(metric=METRIC, value=round(1e3 / big["best_tree_ms"], 3), unit="KKT solves/s",
+                              n_gpus=1, steps=args.sweep_reps, warmup=1, ms_per_step=big["best_tree_ms"],
+                              higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                              data="synthetic", config=dict(workload=res["workload"], N=big["N"]),
+                              sweep=res)))
+        return
+    if args.workload == "small":
+        res = run_small(args)
+        t = res["tree"]
+        print(json.dumps(dict(metric=METRIC, value=round(1e3 / t["mean_ms"], 3), unit="KKT solves/s", n_gpus=1,
+                              steps=max(args.steps, 50), warmup=max(args.warmup, 3), ms_per_step=t["mean_ms"],
+                              higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                              data="synthetic",
+                              config=dict(workload="single MHE instance nx=4, nw=ny=2, N=64, FP64, seed 0",
+                                          l2="inputs smaller than L2 (latency case; not flushed)"),
+                              latency_ms=dict(p50=t["p50_ms"], p99=t["p99_ms"]), arms=res)))
+        return
     if args.workload == "serve":
         res = run_serve(args)
         tree, ser = res["tree"], res["serial"]

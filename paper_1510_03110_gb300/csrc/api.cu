@@ -140,10 +140,13 @@ int rt_copy(void* dst, const void* src, size_t bytes, void* s)
 int rt_sync(void* s) { return cudaStreamSynchronize((cudaStream_t)s) == cudaSuccess ? 0 : -1; }
 int rt_error() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
 
-// relres = ||r|| / (||K|| ||z|| + ||b||) per instance
+// relres = ||r|| / (||K|| ||z|| + ||b||) per instance.  dz[b] (float bits) is the
+// largest |entry| of the corrections the down passes have added since it was last
+// cleared: cleared here before every correction, so when an instance stops
+// refining it holds its last correction, and est_relerr = ||dz_last|| / ||z||.
 __global__ void k_finalize(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
                            int* iters, const int* status, const int* where, double tol, int mode, int refine,
-                           mhe_info* info, int* any)
+                           mhe_info* info, int* any, unsigned int* dz)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
@@ -153,6 +156,7 @@ __global__ void k_finalize(int batch, const unsigned long long* norms, const uns
     const double K = (double)__uint_as_float(kinf[b]);
     const double den = K * z + bb;
     double relres = den > 0 ? r / den : r;
+    const double dzv = (double)__uint_as_float(dz[b]);
     if (mode < 2) {
         const int was = (mode == 0) ? 1 : active[b];
         if (!was) return;
@@ -160,15 +164,20 @@ __global__ void k_finalize(int batch, const unsigned long long* norms, const uns
         info[b].relres = relres;
         const int act = status[b] == 0 && isfinite(relres) && !(relres <= tol);
         active[b] = act;
+        // the last correction of an instance that stops here (none at the first check)
+        info[b].est_relerr = (mode == 0 || !(z > 0)) ? 0.0 : dzv / z;
         if (act) {
             iters[b] += 1;
+            dz[b] = 0u;   // the correction that follows is measured afresh
             if (any) *any = 1;
         }
         return;
     }
     // partial final pass: only instances corrected since their last check were
     // re-evaluated; the others keep the residual recorded at that check
-    if ((refine & 2) && !active[b]) relres = info[b].relres;
+    const bool kept = (refine & 2) && !active[b];
+    if (kept) relres = info[b].relres;
+    const double est = kept ? info[b].est_relerr : (((refine & 1) && iters[b] > 0 && z > 0) ? dzv / z : 0.0);
     mhe_info o;
     memset(&o, 0, sizeof(o));
     int st = status[b];
@@ -180,16 +189,16 @@ __global__ void k_finalize(int batch, const unsigned long long* norms, const uns
     o.stage = where[3 * b + 2];
     o.refine_iters = iters[b];
     o.relres = relres;
-    o.est_relerr = 0.0;
+    o.est_relerr = est;
     info[b] = o;
 }
 
 void rt_finalize(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active, int* iters,
                  const int* status, const int* where, double tol, int mode, int refine, mhe_info* info, int* any,
-                 void* s)
+                 unsigned int* dz, void* s)
 {
     k_finalize<<<(batch + 127) / 128, 128, 0, (cudaStream_t)s>>>(batch, norms, kinf, active, iters, status, where,
-                                                                 tol, mode, refine, info, any);
+                                                                 tol, mode, refine, info, any, dz);
 }
 
 // FP64 -> FP32 copy (round to nearest)

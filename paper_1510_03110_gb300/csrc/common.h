@@ -66,6 +66,7 @@ struct LevelArgs {
     const T *xd_up, *wd_up, *ld_up;        // solution of the level above
     T *xd, *wd, *ld;                       // this level's solution
     double *zx, *zw, *zl;                  // level 0: FP64 accumulate targets (nullptr: none)
+    unsigned int* dznorm;                  // with z: per instance max |added value| (float bits), or nullptr
 
     const int* active;     // per instance; nullptr = all active
     const int* any_active; // non-null: the pass is skipped when *any_active == 0 (no instance refining)

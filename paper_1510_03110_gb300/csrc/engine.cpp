@@ -105,6 +105,7 @@ size_t Engine::layout(char* base)
     }
     c.take(norms, (size_t)batch * 3);
     c.take(kinf, (size_t)batch);
+    c.take(dznorm, (size_t)batch);
     c.take(active, (size_t)batch);
     c.take(any_act, (size_t)1);
     c.take(status, (size_t)batch);
@@ -413,6 +414,7 @@ void Engine::down_level(int k, const T* l, const T* a, const T* l0, const T* a0,
     if (k == 0) {
         g.xd = x; g.wd = w; g.ld = lam;
         g.zx = zx; g.zw = zw; g.zl = zl;
+        g.dznorm = zx ? dznorm : nullptr;
     }
     mark(PH_DOWN, k, 1);
     launches += g.nchunks > 0;
@@ -527,7 +529,7 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
         residual<T>(rhs, x, w, lam, it == 0 ? nullptr : active);
         rt->memset0(any_act, sizeof(int), stream);
         rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, it == 0 ? 0 : 1, 1, info_dev,
-                     any_act, stream);
+                     any_act, dznorm, stream);
         ++launches;
         any_mask = any_act;
         if (m64) {   // the correction's x~0 for the FP64 master levels
@@ -550,7 +552,7 @@ int Engine::run_solve(const mhe_rhs* rhs, const T* l, const T* a, const T* x0, d
     residual<T>(rhs, x, w, lam, max_refine > 0 ? active : nullptr);
     any_mask = nullptr;
     rt->finalize(plan.batch, norms, kinf, active, iters, status, where, tol, 2, max_refine > 0 ? 3 : 0, info_dev,
-                 nullptr, stream);
+                 nullptr, dznorm, stream);
     ++launches;
     if (info) rt->copy(info, info_dev, sizeof(mhe_info) * plan.batch, stream);
     if (rt->error() != 0) { err = "CUDA error during the solve"; return MHE_E_CUDA; }

@@ -52,10 +52,13 @@ struct Runtime {
     // mode 2 fills mhe_info.  refine: bit 0 = refinement ran (a residual above
     // tol is NO_CONVERGE), bit 1 = the final residual covered only the instances
     // still active (the others keep the relres recorded by modes 0/1)
-    // modes 0/1 set *any = 1 when some instance takes another correction (any may be NULL)
+    // modes 0/1 set *any = 1 when some instance takes another correction (any may be NULL);
+    // dz: per instance the largest |entry| of the corrections added since its last
+    // clearing (float bits), cleared for each instance that takes another correction,
+    // giving mhe_info.est_relerr
     void (*finalize)(int batch, const unsigned long long* norms, const unsigned int* kinf, int* active,
                      int* iters, const int* status, const int* where, double tol, int mode, int refine,
-                     mhe_info* info, int* any, void* stream);
+                     mhe_info* info, int* any, unsigned int* dz, void* stream);
     // FP64 -> FP32 copy of count elements (FP32 mode keeps FP32 copies of the problem)
     void (*convert)(float* dst, const double* src, long long count, void* stream);
     int (*sync)(void* stream);
@@ -115,6 +118,7 @@ public:
     const double* x0_hi = nullptr;      // FP64 master levels: the x~0 their top chunks read
     unsigned long long* norms = nullptr;   // per instance |r|, |z|, |b| maxima (bit patterns)
     unsigned int* kinf = nullptr;          // per instance ||K||_inf (float bit pattern)
+    unsigned int* dznorm = nullptr;        // per instance ||dz||_inf of the current correction (float bits)
     int *active = nullptr, *status = nullptr, *where = nullptr, *iters = nullptr;
     int* any_act = nullptr;             // some instance still refining (set by finalize)
     const int* any_mask = nullptr;      // passed to the refinement passes (nullptr outside refinement)

@@ -1185,11 +1185,15 @@ MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin, co
     wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
 }
 
+// |v| as a float (the size of a correction; float is ample for a norm)
+MHE_DEV float absf_of(float v) { return fabsf(v); }
+MHE_DEV float absf_of(double v) { return abs_to_float(v); }
+
 // lambda_t = Q_x x_t + Q_xw w_t + l_x + A^T lambda_{t+1}  (lambda_{t+1} in s.Psi -> result in s.Psi);
-// with FP64 targets z given, z += (x_t, w_t, lambda_t)
+// with FP64 targets z given, z += (x_t, w_t, lambda_t) and dzm keeps the lane's largest |added value|
 template <typename T, int NX, int MT, int KIND>
 MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* xt, const T* wt, T* lo,
-                           double* zx, double* zw, double* zl)
+                           double* zx, double* zw, double* zl, float& dzm)
 {
     using X = Acc<T, KIND, NX, MT>;
     wfor(NX, [&](int i) {
@@ -1206,11 +1210,16 @@ MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* xt, con
         if (idx < NX) {
             s.Psi[idx] = s.u[idx];
             lo[idx] = s.u[idx];
-            if (zl) zl[idx] += f64_of(s.u[idx]);
+            if (zl) {
+                zl[idx] += f64_of(s.u[idx]);
+                dzm = fmaxf(dzm, absf_of(s.u[idx]));
+            }
         } else if (idx < 2 * NX) {
             zx[idx - NX] += f64_of(xt[idx - NX]);
+            dzm = fmaxf(dzm, absf_of(xt[idx - NX]));
         } else {
             zw[idx - 2 * NX] += f64_of(wt[idx - 2 * NX]);
+            dzm = fmaxf(dzm, absf_of(wt[idx - 2 * NX]));
         }
     });
 }
@@ -1273,6 +1282,7 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
                                                 a.kst + g * NW, a.Lst + g * NW * NX, !last, xo(t), wo(t));
     }
     const int t1 = cd.t0 + cd.len;
+    float dzm = 0.f;   // this lane's largest |value| added into z (the size of a correction)
     if (last) {
         // lambda_N = Q_{x,N} x_N + l_N (Q_{x,N} = 0 at level 0)
         const T* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;
@@ -1290,6 +1300,7 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
             if (a.zx) {
                 zxo(t1)[i] += f64_of(s.e[i]);
                 zlo(t1)[i] += f64_of(acc);
+                dzm = fmaxf(dzm, fmaxf(absf_of(s.e[i]), absf_of(acc)));
             }
         });
     }
@@ -1299,14 +1310,18 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
         if (!UPPER && tt > 0) prefetch_leaf<T, NX, NW>(a, b, t - 1, PF_A | PF_Q | PF_L);
         if (UPPER)
             down_bwd_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), xo(t), wo(t), lo(t),
-                                                 zxo(t), zwo(t), zlo(t));
+                                                 zxo(t), zwo(t), zlo(t), dzm);
         else if (t == 0)
             down_bwd_step<T, NX, NX, KIND_ARRIVAL>(s, Addr<T, NX, NW>::arrival(a, b), xo(t), wo(t), lo(t),
-                                                   zxo(t), zwo(t), zlo(t));
+                                                   zxo(t), zwo(t), zlo(t), dzm);
         else
             down_bwd_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), xo(t), wo(t), lo(t),
-                                                zxo(t), zwo(t), zlo(t));
+                                                zxo(t), zwo(t), zlo(t), dzm);
     }
+    // the instance's largest |correction entry| (non-negative floats order like their bit patterns)
+    if (a.zx && a.dznorm) wlanes([&](int) {
+        if (dzm > 0.f) atomicMax(a.dznorm + b, __float_as_uint(dzm));
+    });
 }
 
 }  // namespace mhe

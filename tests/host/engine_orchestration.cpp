@@ -88,7 +88,7 @@ void f_widen(double* d, const float* s, long long count, void*)
 }
 int g_pass = 0;
 void f_finalize(int batch, const unsigned long long*, const unsigned int*, int* active, int*, const int*, const int*,
-                double, int mode, int, mhe_info*, int* any, void*)
+                double, int mode, int, mhe_info*, int* any, unsigned int*, void*)
 {
     Rec r;
     r.op = "finalize";

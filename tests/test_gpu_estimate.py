@@ -217,3 +217,38 @@ def test_tensor_precisions_on_a_shape_without_tensor_products_are_fp32():
         out.append(x.clone())
         s.close()
     assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
+
+
+@pytest.mark.parametrize("prec", [mhe.MHE_FP32_IR, mhe.MHE_FP64])
+def test_error_estimate_per_instance(prec):
+    """mhe_info.est_relerr = ||dz_last||_inf / ||z||_inf of the last correction applied to the
+    instance: zero for an instance that took no correction, positive otherwise, and at least
+    the remaining error against the FP64 oracle (a correction that contracts the error shrinks
+    it below the size of that correction)."""
+    import torch
+    n, m = 24, 12
+    Ns = [1, 5, 40, 99, 300, 1000, 2045]
+    insts = [synth.mhe_instance(1100 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    ref = _oracle(insts)
+    s = mhe.Solver(n, m, d["N"], prec=prec, refine_tol=1e-12 if prec == mhe.MHE_FP32_IR else 1e-15,
+                   max_refine=8 if prec == mhe.MHE_FP32_IR else 2, leaf_len=8, branching=4, top_len=4)
+    x, w, lam = _estimate(d, s)
+    torch.cuda.synchronize()
+    info = s.infos()
+    sols = split(x, w, lam, d["N"], n, m)
+    s.close()
+    refined = 0
+    for b in range(len(Ns)):
+        est, it = float(info["est_relerr"][b]), int(info["refine_iters"][b])
+        assert np.isfinite(est) and est >= 0
+        if it == 0:
+            assert est == 0.0
+            continue
+        refined += 1
+        assert est > 0
+        z = np.concatenate([np.ravel(sols[b][k]) for k in ("x", "w", "lam")])
+        zr = np.concatenate([np.ravel(ref[b][k]) for k in ("x", "w", "lam")])
+        assert np.abs(z - zr).max() / np.abs(zr).max() <= est, (b, est)
+    if prec == mhe.MHE_FP32_IR:
+        assert refined == len(Ns)
