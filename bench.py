@@ -344,7 +344,7 @@ def run_gpu(args):
     for bk in buckets:
         bk["dev"] = to_device(bk)
     gen_s = time.time() - t0
-    refine_tol = 1e-9
+    refine_tol = args.refine_tol
     max_refine = 16 if prec == 1 else 2
     solvers, plans = [], []
     stream = torch.cuda.current_stream()
@@ -378,7 +378,8 @@ def run_gpu(args):
             plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"])
         plans.append(dict(nx=bk["n"], **plan))
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=sprec, refine_tol=refine_tol,
-                       max_refine=max_refine, stream=bstreams[len(solvers)], **plan)
+                       max_refine=max_refine, stream=bstreams[len(solvers)],
+                       fp64_masters=args.fp64_masters and prec == 1, **plan)
         s.out = s.outputs()
         solvers.append(s)
     tune_s = time.time() - t_tune
@@ -590,7 +591,8 @@ def run_gpu(args):
                 warmup=args.warmup, ms_per_step=round(ms, 4), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype={2: "tf32+f32+f64", 3: "bf16+f32+f64"}.get(sprec, "f32+f64") if prec == 1 else "f64",
                 data="synthetic",
-                config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, generation_s=round(gen_s, 1),
+                config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, fp64_master_levels=bool(args.fp64_masters),
+                            generation_s=round(gen_s, 1),
                             plans=plans, autotune_s=round(tune_s, 1)),
                 latency_ms=dict(p50=round(statistics.median(step_ms), 4), p99=round(p99, 4),
                                 note="one step solves every instance; latency = step time"),
@@ -599,10 +601,10 @@ def run_gpu(args):
                 serial_gpu=base,
                 speedup_vs_serial=dict({k: round(value / v["value"], 2) for k, v in base.items()},
                                        **({} if serving is None else dict(
-                                           serving_solves_per_s=round(serving["tree"]["solves_per_s"] /
+                                           serving_solves_per_s=round(serving["tree_reuse"]["solves_per_s"] /
                                                                       max(serving["serial"]["solves_per_s"], 1e-9), 2),
                                            serving_p99=round(serving["serial"]["p99_ms"] /
-                                                             max(serving["tree"]["p99_ms"], 1e-9), 2)))),
+                                                             max(serving["tree_reuse"]["p99_ms"], 1e-9), 2)))),
                 serving=serving,
                 err_vs_oracle=err_oracle, est_relerr=est_summary,
                 roofline=roofline, kernels=kernels_serial, kernels_overlapped=kernels[1:],
@@ -802,39 +804,47 @@ def run_small(args):
     return out
 
 
-def run_serve(args):
-    """Receding-horizon serving: Poisson arrivals at args.rate requests/s for args.duration s over a pool
-    of estimators (nx ~ U{6,12,24}, nw = ny = nx/2, N ~ U{50,200,1000}); every request shifts one
-    estimator's window by one new stage of its simulated plant (y ~ N(C x, 0.01 I), R = blkdiag(W, 100 I)).
-    Run once with the tree plan and once with the serial plan (top_len above every N)."""
-    import torch
-    from paper_1510_03110_gb300 import build, mhe
-    build.build()
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(4)
+def serve_setup(args, rates, T, seed=4):
+    """The serving workload: a pool of estimators (nx ~ U{6,12,24}, nw = ny = nx/2, N ~ U{50,200,1000}),
+    for each offered rate a seeded Poisson arrival sequence over T seconds (who and when), and every
+    estimator's simulated plant stream long enough for the busiest sequence (y ~ N(C x, 0.01 I),
+    R = blkdiag(W, 100 I))."""
+    rng = np.random.default_rng(seed)
     E = args.estimators
     nxs = rng.choice(np.array([6, 12, 24]), size=E)
     Ns = rng.choice(np.array([50, 200, 1000]), size=E)
-    T = args.duration
-    count = int(args.rate * T * 1.05) + 16
-    gaps = rng.exponential(1.0 / args.rate, size=count)
-    t_arr = np.cumsum(gaps)
-    count = int(np.searchsorted(t_arr, T))
-    t_arr = t_arr[:count]
-    who = rng.integers(0, E, size=count)
-    per = np.bincount(who, minlength=E)
+    seqs = {}
+    per_max = np.zeros(E, dtype=np.int64)
+    for rate in rates:
+        r2 = np.random.default_rng([seed, int(rate)])
+        count = int(rate * T * 1.05) + 16
+        t_arr = np.cumsum(r2.exponential(1.0 / rate, size=count))
+        count = int(np.searchsorted(t_arr, T))
+        who = r2.integers(0, E, size=count)
+        seqs[rate] = (t_arr[:count], who)
+        per_max = np.maximum(per_max, np.bincount(who, minlength=E))
     t0 = time.time()
     streams = {}
     for n in (6, 12, 24):
         ids = np.nonzero(nxs == n)[0]
         if len(ids) == 0:
             continue
-        L = int(np.max(Ns[ids] - 1 + per[ids])) + 1
+        L = int(np.max(Ns[ids] - 1 + per_max[ids])) + 2
         ps = synth.plant_streams([5, n], n, n // 2, n // 2, len(ids), L)
         for j, e in enumerate(ids):
             streams[int(e)] = synth.stream_of(ps, j)
-    # pre-packed requests in arrival order
-    nxt = np.zeros(E, dtype=np.int64)
+    return dict(E=E, nxs=nxs, Ns=Ns, seqs=seqs, streams=streams, T=T, gen_s=round(time.time() - t0, 1))
+
+
+def serve_once(args, ws, rate, plan, reuse=True):
+    """One serving run: admit every estimator, warm up with one request each, then submit the
+    rate's arrival sequence at its times from this thread and wait for every result; latency is
+    submission to completion as the server records it."""
+    from paper_1510_03110_gb300 import mhe
+    E, nxs, Ns, streams = ws["E"], ws["nxs"], ws["Ns"], ws["streams"]
+    t_arr, who = ws["seqs"][rate]
+    count = len(t_arr)
+    nxt = np.ones(E, dtype=np.int64)   # request 0 of each estimator is the warm-up
     packed = []
     for i in range(count):
         e = int(who[i])
@@ -843,46 +853,96 @@ def run_serve(args):
         nxt[e] += 1
         packed.append(mhe.pack_stage(st["A"][k], st["B"][k], st["C"][k], st["R"][k], st["a"][k], st["yt"][k],
                                      st["wt"][k]))
-    gen_s = time.time() - t0
+    srv = mhe.Server(args.serve_bytes, prec=mhe.MHE_FP32_IR, refine_tol=args.serve_tol)
+    srv.set_plan(**plan)
+    srv.set_reuse(reuse)
+    ids = []
+    for e in range(E):
+        n = int(nxs[e])
+        ids.append(srv.open(synth.window_of(streams[e], 0, int(Ns[e]), np.zeros(n), n, n // 2, n // 2)))
+    warm = []
+    for e in range(E):
+        st = streams[e]
+        k = int(Ns[e] - 1)
+        warm.append(srv.submit(ids[e], mhe.pack_stage(*(np.asarray(st[f][k]) for f in
+                                                       ("A", "B", "C", "R", "a", "yt", "wt")))))
+    for e, tk in enumerate(warm):
+        srv.wait(tk, int(nxs[e]), timeout=300)
+    s0 = srv.stats()
+    tickets = []
+    tstart = time.perf_counter()
+    for i in range(count):
+        target = tstart + t_arr[i]
+        while time.perf_counter() < target:
+            pass
+        tickets.append(srv.submit(ids[int(who[i])], packed[i]))
+    t_sub_end = time.perf_counter()
+    lat, bad, relres = [], 0, 0.0
+    for i, tk in enumerate(tickets):
+        r = srv.wait(tk, int(nxs[int(who[i])]), timeout=600)
+        lat.append(r["latency"])
+        bad += r["status"] != 0
+        relres = max(relres, r["relres"])
+    t_end = time.perf_counter()
+    s1 = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    span = max(t_end - tstart, 1e-9)
+    req = max(s1["requests"] - s0["requests"], 1)
+    return dict(offered_per_s=round(count / max(t_arr[-1], 1e-9), 1), submitted_per_s=round(count / (t_sub_end - tstart), 1),
+                solves_per_s=round(count / span, 1), p50_ms=round(1e3 * float(np.median(lat)), 3),
+                p99_ms=round(1e3 * float(np.quantile(lat, 0.99)), 3), mean_ms=round(1e3 * float(lat.mean()), 3),
+                requests=count, failed=int(bad), relres_max=relres, submit_s=round(t_sub_end - tstart, 3),
+                span_s=round(span, 3), rounds=s1["rounds"] - s0["rounds"],
+                stages_reduced_per_request=round((s1["stages_reduced"] - s0["stages_reduced"]) / req, 1),
+                stages_per_request=round((s1["stages_solved"] - s0["stages_solved"]) / req, 1))
+
+
+SERVE_PLANS = [("tree_reuse", dict(leaf_len=0, branching=0, top_len=0), True),
+               ("serial", dict(leaf_len=0, branching=0, top_len=1 << 20), True)]
+
+
+def run_serve(args):
+    """Receding-horizon serving at args.rate requests/s for args.duration s: the tree plan with
+    factorisation reuse across shifts, and the plain serial recursion (top_len above every N,
+    its one chunk re-reduced at every shift)."""
+    import torch
+    from paper_1510_03110_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    ws = serve_setup(args, [args.rate], args.duration)
     out = {}
-    for plan_name, plan in [("tree", dict(leaf_len=0, branching=0, top_len=0)),
-                            ("serial", dict(leaf_len=0, branching=0, top_len=1 << 20))]:
-        srv = mhe.Server(args.serve_bytes, prec=mhe.MHE_FP32_IR, refine_tol=1e-9)
-        srv.set_plan(**plan)
-        ids = []
-        for e in range(E):
-            n = int(nxs[e])
-            ids.append(srv.open(synth.window_of(streams[e], 0, int(Ns[e]), np.zeros(n), n, n // 2, n // 2)))
-        # warm-up: one request per estimator (engines, workspaces, first rounds)
-        warm = [srv.submit(ids[e], mhe.pack_stage(*(np.asarray(streams[e][f][0]) for f in
-                                                   ("A", "B", "C", "R", "a", "yt", "wt")))) for e in range(E)]
-        for e, tk in enumerate(warm):
-            srv.wait(tk, int(nxs[e]), timeout=120)
-        tickets = []
-        tstart = time.perf_counter()
-        for i in range(count):
-            target = tstart + t_arr[i]
-            while time.perf_counter() < target:
-                pass
-            tickets.append(srv.submit(ids[int(who[i])], packed[i]))
-        t_sub_end = time.perf_counter()
-        lat, bad, relres = [], 0, 0.0
-        for i, tk in enumerate(tickets):
-            r = srv.wait(tk, int(nxs[int(who[i])]), timeout=300)
-            lat.append(r["latency"])
-            bad += r["status"] != 0
-            relres = max(relres, r["relres"])
-        t_end = time.perf_counter()
-        srv.close()
-        lat = np.array(lat)
-        span = max(t_end - tstart, 1e-9)
-        out[plan_name] = dict(solves_per_s=round(count / span, 1), p50_ms=round(1e3 * float(np.median(lat)), 3),
-                              p99_ms=round(1e3 * float(np.quantile(lat, 0.99)), 3),
-                              mean_ms=round(1e3 * float(lat.mean()), 3), requests=count, failed=int(bad),
-                              relres_max=relres, submit_s=round(t_sub_end - tstart, 3), span_s=round(span, 3))
-    return dict(estimators=E, rate=args.rate, duration_s=T, generation_s=round(gen_s, 1),
-                nx="U{6,12,24}", N="U{50,200,1000}", precision="FP32 tree + FP64 refinement, relres<=1e-9",
-                **out)
+    for name, plan, reuse in SERVE_PLANS:
+        out[name] = serve_once(args, ws, args.rate, plan, reuse)
+    return dict(estimators=ws["E"], rate=args.rate, duration_s=args.duration, generation_s=ws["gen_s"],
+                nx="U{6,12,24}", N="U{50,200,1000}",
+                precision="FP32 tree + FP64 refinement, relres<=%g" % args.serve_tol, **out)
+
+
+def run_serve_sweep(args):
+    """The offered rate raised until the server saturates, per plan: solves/s, p50/p99 at each
+    rate; the highest rate whose throughput keeps up (>= 95% of the offered rate) with p99 below
+    args.p99_bound_ms."""
+    import torch
+    from paper_1510_03110_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    rates = [float(v) for v in args.rates.split(",")]
+    ws = serve_setup(args, rates, args.duration)
+    res = {name: [] for name, _, _ in SERVE_PLANS}
+    for rate in rates:
+        for name, plan, reuse in SERVE_PLANS:
+            r = serve_once(args, ws, rate, plan, reuse)
+            r["rate"] = rate
+            res[name].append(r)
+    sat = {}
+    for name, rows in res.items():
+        ok = [r for r in rows if r["solves_per_s"] >= 0.95 * r["offered_per_s"] and r["p99_ms"] <= args.p99_bound_ms]
+        sat[name] = dict(max_sustained_rate=max((r["rate"] for r in ok), default=None),
+                         max_solves_per_s=max(r["solves_per_s"] for r in rows))
+    return dict(estimators=ws["E"], duration_s=args.duration, generation_s=ws["gen_s"], rates=rates,
+                p99_bound_ms=args.p99_bound_ms, nx="U{6,12,24}", N="U{50,200,1000}",
+                precision="FP32 tree + FP64 refinement, relres<=%g" % args.serve_tol, runs=res, saturation=sat)
 
 
 def pinned_h2d_gbs(nbytes=1 << 31, reps=3):
@@ -1047,10 +1107,15 @@ def main():
     ap.add_argument("--sweep-branching", default="2,4,8,16")
     ap.add_argument("--sweep-reps", type=int, default=3)
     ap.add_argument("--err-samples", type=int, default=2, help="instances per bucket checked against the oracle")
+    ap.add_argument("--refine-tol", type=float, default=1e-9, help="relative KKT residual the refinement reaches")
+    ap.add_argument("--fp64-masters", action="store_true", help="master levels k >= 1 in FP64 (mixed precisions)")
     ap.add_argument("--plan", default=None, help="leaf_len,branching,top_len used instead of the autotuner")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")
     ap.add_argument("--estimators", type=int, default=1024, help="serving: estimator pool")
+    ap.add_argument("--rates", default="", help="serving: comma-separated offered rates for a saturation sweep")
+    ap.add_argument("--p99-bound-ms", type=float, default=50.0, help="serving sweep: p99 a sustained rate keeps")
+    ap.add_argument("--serve-tol", type=float, default=1e-9, help="serving: relres the refinement reaches")
     ap.add_argument("--serve-bytes", type=int, default=96 << 30, help="serving: device-memory budget")
     ap.add_argument("--serve-duration", type=float, default=10.0,
                     help="batch workload: seconds of a serving run appended to the line (0: none)")
@@ -1097,9 +1162,19 @@ def main():
                                           l2="inputs smaller than L2 (latency case; not flushed)"),
                               latency_ms=dict(p50=t["p50_ms"], p99=t["p99_ms"]), arms=res)))
         return
+    if args.workload == "serve" and args.rates:
+        res = run_serve_sweep(args)
+        print(json.dumps(dict(metric=METRIC, value=res["saturation"]["tree_reuse"]["max_solves_per_s"],
+                              unit="KKT solves/s", n_gpus=1, steps=len(res["rates"]), warmup=1,
+                              ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
+                              dtype="f32+f64", data="synthetic",
+                              config=dict(workload="receding-horizon serving, Poisson arrivals, rate sweep",
+                                          estimators=res["estimators"], duration_s=res["duration_s"]),
+                              serve_sweep=res)))
+        return
     if args.workload == "serve":
         res = run_serve(args)
-        tree, ser = res["tree"], res["serial"]
+        tree, ser = res["tree_reuse"], res["serial"]
         print(json.dumps(dict(metric=METRIC, value=tree["solves_per_s"], unit="KKT solves/s", n_gpus=1,
                               steps=tree["requests"], warmup=1, ms_per_step=tree["mean_ms"], higher_is_better=True,
                               scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic",

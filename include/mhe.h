@@ -78,7 +78,11 @@ typedef struct {
     int batch;           /* number of independent instances */
     const int* N;        /* host array [batch]: UFTOC horizon of each instance, >= 1 */
     int prec;            /* mhe_precision */
-    int leaf_len;        /* level-0 chunk length (0: max(8, ceil(nx / nw))); leaf_len * nw >= nx */
+    int leaf_len;        /* level-0 chunk length (0: max(8, ceil(nx / nw))).  leaf_len * nw < nx
+                            makes a leaf chunk's reduced input rank deficient (Section IV-B, the
+                            remark on a singular G^): the master stages are then factored with a
+                            pivoted Cholesky that stops at the numerical rank (the U_1 basis of
+                            Eq. Bh_def), at every level */
     int branching;       /* chunk length at levels >= 1 (0: 4); >= 2 */
     int top_len;         /* a level with horizon <= top_len is solved as one chunk (0: 4).
                             top_len >= max N gives the plain serial Riccati recursion.
@@ -254,11 +258,30 @@ int mhe_poll(mhe_server* s, unsigned long long ticket, double* x_est, mhe_info* 
 
 /* Plan of every round (as mhe_dims.leaf_len, branching, top_len; 0 = the
  * defaults listed there; top_len above every N = the serial recursion).
- * Before the first request only. */
+ * Before the first mhe_estimator_open only (the estimators' rings are sized for
+ * the plan): MHE_E_ARG afterwards. */
 int mhe_server_set_plan(mhe_server* s, int leaf_len, int branching, int top_len);
 
 /* Device bytes the server holds. */
 size_t mhe_server_used_bytes(mhe_server* s);
+
+/* Factorisation reuse across the shifts of a receding horizon (on by
+ * default).  The tree's chunk boundaries are fixed in absolute sample time,
+ * so a shift by one sample changes only each level's first chunk (it loses
+ * its oldest stage), its last chunk (the new stage) and the chunk that stops
+ * being last; the server keeps every other chunk's Algorithm 4 output (its
+ * stored factors and its master stage, Eq. red_mpc_problem) across rounds and
+ * reduces only those, then runs the vector part, the down pass (Algorithm 6)
+ * and the refinement over the whole window.  on = 0 reduces every chunk of
+ * every round (the results agree within the refinement tolerance).  With the
+ * serial plan (top_len above N) the one chunk changes at every shift. */
+int mhe_server_set_reuse(mhe_server* s, int on);
+
+/* Counters since mhe_server_create: out[0] rounds, out[1] requests served,
+ * out[2] stages reduced again (the matrix part of Algorithm 4 or Algorithms
+ * 1-2), out[3] stages of the solved windows (sum of N); returns 4 (writes at
+ * most cap values). */
+int mhe_server_stats(mhe_server* s, long long* out, int cap);
 
 /* Finish the rounds in flight, stop the worker, free everything. */
 int mhe_server_destroy(mhe_server* s);
@@ -306,6 +329,27 @@ int mhe_plan_info(mhe_ctx* ctx, long long* out, int cap);
 int mhe_solve_serial_noalloc(int nx, int nw, int N, const double* A, const double* B, const double* Q,
                              const double* P0inv, const double* l, const double* a, const double* x0,
                              double* x, double* w, double* lam, int* status, void* stream);
+
+/* No counterpart in the paper; for testing the failure path of the tensor-core
+ * reductions (MHE_TF32_IR, MHE_BF16_IR).  Sets, for every later launch on the
+ * current device, the number of tries each wait for a stage's products on the
+ * tensor cores makes before it gives up; tries < 0 restores the default
+ * (2^20).  A wait that gives up marks its instance MHE_E_TIMEOUT (with level,
+ * chunk and stage in mhe_info), the team issues no further products, and one
+ * more wait with the default limit lets the products in flight finish before
+ * the tensor memory is freed, so the context stays usable.  Not thread-safe
+ * against launches in flight.  Errors: MHE_E_CUDA. */
+int mhe_debug_set_tc_wait_limit(int tries);
+
+/* The FP64 KKT residual of mhe_estimate in the mixed precisions: on = 1 (the
+ * default) evaluates the stage products in double-float arithmetic on the FP32
+ * pipes -- every FP64 input carried as a float pair hi + lo (48 bits), products
+ * and sums with their rounding errors recovered -- which on GB300 is several
+ * times faster than the FP64 pipe and accurate to about 1e-14 of the products'
+ * magnitude; on = 0 evaluates it with FP64 instructions.  Both give the same
+ * solution within the refinement tolerance.  No counterpart in the paper (it
+ * leaves the precision of the products open).  Errors: MHE_E_ARG. */
+int mhe_set_double_float_residual(mhe_ctx* ctx, int on);
 
 /* Kernels launched so far by this context (all passes, residuals included),
  * and by mhe_assemble in this process. */

@@ -19,6 +19,7 @@ int shapes_big(ShapeEntry* out, int cap);
 int shapes_sq(ShapeEntry* out, int cap);
 int shapes_xl(ShapeEntry* out, int cap);
 int shapes_n12(ShapeEntry* out, int cap);
+int set_tc_wait_limit(int tries);   // shapes_xl.cu
 }  // namespace mhe
 
 // CUDA events around each level pass, recorded on the context's stream.
@@ -302,10 +303,10 @@ size_t mhe_workspace_bytes(const mhe_dims* dims)
     e.m64 = dims->fp64_masters != 0 && dims->prec != MHE_FP64;
     const int min_leaf = (dims->nx + dims->nw - 1) / dims->nw;
     const char* err = nullptr;
-    if (mhe::make_plan(dims->nx, dims->nw, dims->N, dims->batch,
-                       dims->leaf_len > 0 ? dims->leaf_len : (min_leaf > 8 ? min_leaf : 8),
-                       dims->branching > 0 ? dims->branching : 4, dims->top_len > 0 ? dims->top_len : 4, e.plan,
-                       &err) != 0)
+    const int leaf = dims->leaf_len > 0 ? dims->leaf_len : (min_leaf > 8 ? min_leaf : 8);
+    e.pivot = mhe::needs_rank_revealing(dims->nx, dims->nw, leaf);
+    if (mhe::make_plan(dims->nx, dims->nw, dims->N, dims->batch, leaf, dims->branching > 0 ? dims->branching : 4,
+                       dims->top_len > 0 ? dims->top_len : 4, e.plan, &err, e.pivot) != 0)
         return 0;
     return e.layout(nullptr);
 }
@@ -662,6 +663,22 @@ int mhe_plan_info(mhe_ctx* ctx, long long* out, int cap)
 }
 
 long long mhe_assemble_count(void) { return g_assemble_launches; }
+
+int mhe_set_double_float_residual(mhe_ctx* ctx, int on)
+{
+    if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
+    ctx->eng.df_resid = on != 0;
+    return MHE_OK;
+}
+
+int mhe_debug_set_tc_wait_limit(int tries)
+{
+    if (mhe::set_tc_wait_limit(tries) != 0) {
+        cudaGetLastError();
+        return fail(MHE_E_CUDA, "setting the tensor-core wait limit failed");
+    }
+    return MHE_OK;
+}
 
 const char* mhe_last_error(void) { return g_err.c_str(); }
 

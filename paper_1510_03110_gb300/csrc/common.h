@@ -17,9 +17,13 @@ struct ChunkDesc {
     int t0;
     int len;
     int flags;
-    long long g0;       // global stage index of t0 within this level's stage arrays
+    long long g0;       // global stage index of t0 within this level's stage arrays (stored factors, master data)
     long long parent;   // non-last: global stage index of the master stage it becomes at level k+1
     long long px;       // parent's state index holding x^_i (non-top); -1 for the top
+    long long pw;       // non-last: index of w^_i in the level above's solution (= parent, except when the
+                        // stored data live in serving rings and the solution in per-round arrays)
+    long long parent2;  // non-last: a second index the master stage's data are also written to (the
+                        // mirrored tail of a serving ring), or -1
 };
 
 // Per (level, instance) bookkeeping.
@@ -73,6 +77,11 @@ struct LevelArgs {
     int* status;           // per instance error code
     int* where;            // per instance (level, chunk, stage) of the first error
     double piv_rel;        // relative pivot threshold of the Cholesky factorisations
+    // rank-revealing master stages (leaf chunks with leaf_len * nw < nx): per master
+    // stage of level k+1, the pivot order of its factored Q^_w (nx entries) and its rank;
+    // nullptr: every master stage has full rank (plain Cholesky)
+    int* piv_up;
+    double piv_rank;       // a pivot at or below piv_rank * max diag ends the factorisation (the rank)
     int store_P;           // keep P_{t+1} per stage (needed by right-hand-side-only passes)
     // shapes whose per-subproblem workspace exceeds an SM's shared memory (FP64 at
     // nx = 64): gws_teams slots of the workspace in global memory (L2-resident),
@@ -103,6 +112,11 @@ struct ResidArgs {
     // factors [[C^T V C, -C^T S^T], [-S C, W]] from C (ny x n) and
     // R = [[W, S], [S^T, V]] at the input offsets, and Q is not read
     const double *C, *R;
+    // MHE form, FP32 correction solves: the stage matrices A, B, C, R as float pairs
+    // (value = hi + lo to 48 bits, written by the preparation pass, same layouts);
+    // when set the residual's stage products run in double-float arithmetic on the
+    // FP32 pipes, and only the vectors are read in FP64
+    const float *Ahi, *Alo, *Bhi, *Blo, *Chi, *Clo, *Rhi, *Rlo;
 };
 
 // MHE data (Eq. org_mhe, Section II) -> the FP32 working copies of the UFTOC
@@ -116,6 +130,9 @@ struct PrepArgs {
     float *A32, *B32, *Q32, *l32, *a32, *x0_32, *P0_32;
     double* l;                    // FP64 l = [C^T (S^T w~ - V y~); S y~ - W w~]
     unsigned int* kinf;           // per instance, bit pattern of a non-negative float
+    // optional (nullptr: not written): the low parts of A and B (their high parts are
+    // A32, B32) and both parts of C and R, for the double-float residual
+    float *A_lo, *B_lo, *C_hi, *C_lo, *R_hi, *R_lo;
 };
 
 // ||K||_inf per instance (max absolute row sum of the KKT matrix), once per

@@ -43,22 +43,37 @@ size_t Engine::layout(char* base)
         const size_t ns = (size_t)L.nstages, nx_ = (size_t)L.nstates;
         const size_t mk = (k == 0) ? (size_t)m : (size_t)n;
         const size_t tk = (m64 && k >= 1) ? sizeof(double) : ts;   // the level's compute type
-        c.take_raw(B_.Pst, ns * n2 * tk);
-        c.take_raw(B_.Lgst, ns * mk * mk * tk);
-        c.take_raw(B_.Kst, ns * mk * n * tk);
-        c.take_raw(B_.kst, ns * mk * tk);
-        c.take_raw(B_.Lst, ns * mk * n * tk);
+        if (use_ext && k < ext.levels()) {   // the server's stores (serving with reuse)
+            B_.Pst = ext.Pst[k]; B_.Lgst = ext.Lgst[k]; B_.Kst = ext.Kst[k]; B_.kst = ext.kst[k];
+            B_.Lst = ext.Lst[k];
+            B_.Ah = ext.Ah[k]; B_.Bh = ext.Bh[k]; B_.Qxh = ext.Qxh[k]; B_.ah = ext.ah[k]; B_.lxh = ext.lxh[k];
+            const size_t nr = k < rlist.size() ? rlist[k].size() : 0;
+            c.take(B_.rchunks, nr);
+            B_.nrchunks = (int)nr;
+        } else {
+            B_.rchunks = nullptr;
+            B_.nrchunks = 0;
+            c.take_raw(B_.Pst, ns * n2 * tk);
+            c.take_raw(B_.Lgst, ns * mk * mk * tk);
+            c.take_raw(B_.Kst, ns * mk * n * tk);
+            c.take_raw(B_.kst, ns * mk * tk);
+            c.take_raw(B_.Lst, ns * mk * n * tk);
+        }
         if (k >= 1) {
-            c.take_raw(B_.Ah, ns * n2 * tk);
-            c.take_raw(B_.Bh, ns * n2 * tk);
-            c.take_raw(B_.Qxh, ns * n2 * tk);
-            c.take_raw(B_.ah, ns * n * tk);
-            c.take_raw(B_.lxh, ns * n * tk);
+            if (!(use_ext && k < ext.levels())) {
+                c.take_raw(B_.Ah, ns * n2 * tk);
+                c.take_raw(B_.Bh, ns * n2 * tk);
+                c.take_raw(B_.Qxh, ns * n2 * tk);
+                c.take_raw(B_.ah, ns * n * tk);
+                c.take_raw(B_.lxh, ns * n * tk);
+            }
             c.take_raw(B_.QN, (size_t)batch * n2 * tk);
             c.take_raw(B_.lN, (size_t)batch * n * tk);
             c.take_raw(B_.xd, nx_ * n * tk);
             c.take_raw(B_.wd, ns * n * tk);
             c.take_raw(B_.ld, nx_ * n * tk);
+            if (pivot) c.take(B_.piv, ns * (size_t)(n + 1));
+            else B_.piv = nullptr;
         }
         if (m64 && k == 1) {   // the FP32 side of the level-0 / level-1 hand-off
             c.take_raw(B_.Ah32, ns * n2 * sizeof(float));
@@ -145,7 +160,8 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     int br = d.branching > 0 ? d.branching : 4;
     int top = d.top_len > 0 ? d.top_len : 4;
     const char* e = nullptr;
-    int rc = make_plan(d.nx, d.nw, d.N, d.batch, leaf, br, top, plan, &e);
+    pivot = needs_rank_revealing(d.nx, d.nw, leaf);
+    int rc = make_plan(d.nx, d.nw, d.N, d.batch, leaf, br, top, plan, &e, pivot);
     if (rc != 0) { err = e; return MHE_E_ARG; }
     this->leaf = leaf;
     this->br = br;
@@ -177,9 +193,11 @@ int Engine::replan(const int* N, int batch, const long long* in_off_custom)
 {
     const char* e = nullptr;
     Plan p;
-    if (make_plan(plan.n, plan.m, N, batch, leaf, br, topl, p, &e) != 0) { err = e; return MHE_E_ARG; }
+    if (make_plan(plan.n, plan.m, N, batch, leaf, br, topl, p, &e, pivot) != 0) { err = e; return MHE_E_ARG; }
     if (in_off_custom) p.in_off.assign(in_off_custom, in_off_custom + batch);
     plan = p;
+    use_ext = false;
+    rlist.clear();
     factored = false;
     const size_t need = layout(nullptr);
     if (need > arena_bytes) {
@@ -191,6 +209,64 @@ int Engine::replan(const int* N, int batch, const long long* in_off_custom)
     }
     layout(static_cast<char*>(arena));
     return upload_plan();
+}
+
+int Engine::replan_serve(const std::vector<ServeWindow>& w, const ExtStores& st, long long* reduced)
+{
+    const char* e = nullptr;
+    Plan p;
+    std::vector<std::vector<ChunkDesc>> dirty;
+    if (make_serve_plan(plan.n, plan.m, w, leaf, br, topl, p, dirty, reduced, &e) != 0) { err = e; return MHE_E_ARG; }
+    if (p.levels.size() > st.levels()) { err = "the round's tree is deeper than the server's stores"; return MHE_E_ARG; }
+    if (m64) { err = "serving with reuse keeps every level in the context's precision"; return MHE_E_ARG; }
+    plan = p;
+    rlist = dirty;
+    ext = st;
+    use_ext = true;
+    factored = false;
+    const size_t need = layout(nullptr);
+    if (need > arena_bytes) {
+        rt->sync(stream);
+        rt->release(arena);
+        arena = rt->alloc(need + need / 4);
+        if (!arena) { arena_bytes = 0; err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
+        arena_bytes = need + need / 4;
+    }
+    layout(static_cast<char*>(arena));
+    for (size_t k = 0; k < rlist.size() && k < lv.size(); ++k)
+        if (!rlist[k].empty()) rt->copy(lv[k].rchunks, rlist[k].data(), rlist[k].size() * sizeof(ChunkDesc), stream);
+    return upload_plan();
+}
+
+int Engine::solve_resident_reuse(const Resident& r, double* x, double* w, double* lam, mhe_info* info)
+{
+    A = r.A; B = r.B; Q = r.Q; P0inv = r.P0inv;
+    mheC = mheR = nullptr;
+    mA = r.At; mB = r.Bt; mQ = r.Qt; mP0 = r.P0t;
+    rt->memset0(status, sizeof(int) * plan.batch, stream);
+    rt->memset0(where, sizeof(int) * 3 * plan.batch, stream);
+    KnormArgs kn;
+    kn.batch = plan.batch;
+    kn.nstages = plan.gs0[plan.batch];
+    kn.gs0 = gs0;
+    kn.in_off = in_off;
+    kn.A = A; kn.B = B; kn.Q = Q; kn.P0inv = P0inv;
+    kn.kinf = kinf;
+    rt->memset0(kinf, sizeof(unsigned int) * plan.batch, stream);
+    launches += 1;
+    ops->knorm(kn, stream);
+    mhe_rhs rh;
+    rh.l = r.l; rh.a = r.a; rh.x0 = r.x0;
+    factored = true;
+    // the matrix part on the changed chunks only; the vector part of every chunk follows in run_solve
+    if (prec == MHE_FP64) {
+        pass_reduce<double>(r.A, r.B, r.Q, r.P0inv, nullptr, nullptr);
+        return run_solve<double>(&rh, r.l, r.a, r.x0, x, w, lam, info, false);
+    }
+    pass_reduce<float>(static_cast<const float*>(r.At), static_cast<const float*>(r.Bt),
+                       static_cast<const float*>(r.Qt), static_cast<const float*>(r.P0t), nullptr, nullptr);
+    return run_solve<float>(&rh, static_cast<const float*>(r.lt), static_cast<const float*>(r.at),
+                            static_cast<const float*>(r.x0t), x, w, lam, info, false);
 }
 
 int Engine::solve_resident(const Resident& r, double* x, double* w, double* lam, mhe_info* info)
@@ -235,8 +311,9 @@ void Engine::release()
     arena = nullptr;
     if (l64) rt->release(l64);
     if (Q64) rt->release(Q64);
-    l64 = Q64 = nullptr;
-    l64_bytes = Q64_bytes = 0;
+    if (dfp) rt->release(dfp);
+    l64 = Q64 = dfp = nullptr;
+    l64_bytes = Q64_bytes = dfp_bytes = 0;
 }
 
 template <typename T>
@@ -289,6 +366,10 @@ LevelArgs<T> Engine::args(int k) const
     a.store_P = 1;
     a.gws = sizeof(T) == 8 ? static_cast<T*>(gws) : nullptr;
     a.gws_teams = ops ? ops->gws_teams : 0;
+    a.piv_up = (pivot && k + 1 < (int)lv.size()) ? lv[k + 1].piv : nullptr;
+    // the numerical rank of a master stage's Q^_w: pivots above this fraction of its
+    // largest diagonal (the FP32 accumulation leaves its null directions near 1e-7 of it)
+    a.piv_rank = (sizeof(T) == 8) ? 1e-10 : 1e-5;
     return a;
 }
 
@@ -332,6 +413,10 @@ void Engine::reduce_level(int k, const T* A_, const T* B_, const T* Q_, const T*
                           bool with_rhs)
 {
     LevelArgs<T> g = args<T>(k);
+    if (lv[k].rchunks) {   // serving with reuse: only the chunks whose data changed
+        g.chunks = lv[k].rchunks;
+        g.nchunks = lv[k].nrchunks;
+    }
     g.A = A_; g.B = B_; g.Q = Q_; g.P0inv = P0_;
     g.l = l;
     g.a = a;
@@ -474,6 +559,9 @@ void Engine::residual(const mhe_rhs* rhs, const double* x, const double* w, cons
     r.any_active = act ? any_mask : nullptr;
     r.C = mheC;
     r.R = mheR;
+    if (mheC && sizeof(T) == 4 && rAh) {   // the double-float residual of the MHE form
+        r.Ahi = rAh; r.Alo = rAl; r.Bhi = rBh; r.Blo = rBl; r.Chi = rCh; r.Clo = rCl; r.Rhi = rRh; r.Rlo = rRl;
+    }
     rt->memset0(norms, sizeof(unsigned long long) * 3 * plan.batch, stream);
     mark(PH_RESID, 0, 1);
     launches += r.nstages > 0;
@@ -675,6 +763,24 @@ int Engine::estimate(const mhe_problem& p, double* x, double* w, double* lam, mh
     pa.A32 = A32; pa.B32 = B32; pa.Q32 = Q32; pa.l32 = l32; pa.a32 = a32; pa.x0_32 = x0_32; pa.P0_32 = P0_32;
     pa.l = l64;
     pa.kinf = kinf;
+    rAh = rAl = rBh = rBl = rCh = rCl = rRh = rRl = nullptr;
+    if (df_resid) {
+        const int q = p.ny;
+        const size_t per = (size_t)n * n + (size_t)n * m + 2 * (size_t)q * n + 2 * (size_t)(m + q) * (m + q);
+        if (!reserve(rt, stream, dfp, dfp_bytes, sizeof(float) * (size_t)S * per + 64)) {
+            err = "device allocation of the residual's float pairs failed";
+            return MHE_E_NOMEM;
+        }
+        float* f = reinterpret_cast<float*>(dfp);
+        pa.A_lo = f; f += (size_t)S * n * n;
+        pa.B_lo = f; f += (size_t)S * n * m;
+        pa.C_hi = f; f += (size_t)S * q * n;
+        pa.C_lo = f; f += (size_t)S * q * n;
+        pa.R_hi = f; f += (size_t)S * (m + q) * (m + q);
+        pa.R_lo = f;
+        rAh = A32; rAl = pa.A_lo; rBh = B32; rBl = pa.B_lo;
+        rCh = pa.C_hi; rCl = pa.C_lo; rRh = pa.R_hi; rRl = pa.R_lo;
+    }
     mark(PH_PREP, 0, 1);
     ops->prep32(pa, stream);
     mark(PH_PREP, 0, 0);

@@ -75,14 +75,27 @@ struct LevelBuf {   // every array of the level's compute type (FP64 at k >= 1 w
     ChunkDesc* chunks = nullptr;
     LevelInst* li = nullptr;
     int nchunks = 0;
+    // serving with reuse: the chunks the reduction pass runs on (nullptr: all of chunks)
+    ChunkDesc* rchunks = nullptr;
+    int nrchunks = 0;
     void *Pst = nullptr, *Lgst = nullptr, *Kst = nullptr, *kst = nullptr, *Lst = nullptr;
     void *Ah = nullptr, *Bh = nullptr, *ah = nullptr, *Qxh = nullptr, *lxh = nullptr;
     void *QN = nullptr, *lN = nullptr;   // terminal of this level (k >= 1)
     void *xd = nullptr, *wd = nullptr, *ld = nullptr;
+    int* piv = nullptr;   // k >= 1, rank-revealing plans: pivot order and rank of each master stage
     // level 1 with FP64 master levels: the FP32 master data level 0 writes (widened
     // to the arrays above) and the FP32 copy of this level's solution level 0 reads
     void *Ah32 = nullptr, *Bh32 = nullptr, *ah32 = nullptr, *Qxh32 = nullptr, *lxh32 = nullptr;
     void *QN32 = nullptr, *lN32 = nullptr, *xd32 = nullptr, *wd32 = nullptr, *ld32 = nullptr;
+};
+
+// Serving with reuse: the stored factors of every level and the master-stage data
+// of the levels k >= 1 live in stores the server keeps across rounds (one ring
+// per estimator and level, addressed through the chunk descriptors), not in a
+// context's workspace.  Per level: P, chol(G), K, k, L; A^, R^T, Q^_x, a^, l^_x.
+struct ExtStores {
+    std::vector<void*> Pst, Lgst, Kst, kst, Lst, Ah, Bh, Qxh, ah, lxh;
+    size_t levels() const { return Pst.size(); }
 };
 
 // A problem already resident on the device: FP64 arrays (the residual, and
@@ -101,6 +114,7 @@ public:
     void* stream = nullptr;
     int prec = MHE_FP64;
     bool m64 = false;                   // FP32 / TF32 / BF16 tree whose master levels k >= 1 run in FP64
+    bool pivot = false;                 // rank-revealing master stages (leaf_len * nw < nx)
     double tol = 1e-10;
     int max_refine = 0;
 
@@ -130,6 +144,13 @@ public:
     const double *mheC = nullptr, *mheR = nullptr;   // set: the residual applies Q in its MHE factors
     double *l64 = nullptr, *Q64 = nullptr;           // mhe_estimate's FP64 l (and Q in FP64 mode)
     size_t l64_bytes = 0, Q64_bytes = 0;
+    // mhe_estimate in the mixed precisions: A, B, C, R as float pairs for the double-float
+    // residual (lo of A and B, hi and lo of C and R; the hi of A and B are A32, B32)
+    double* dfp = nullptr;
+    size_t dfp_bytes = 0;
+    const float *rAh = nullptr, *rAl = nullptr, *rBh = nullptr, *rBl = nullptr;
+    const float *rCh = nullptr, *rCl = nullptr, *rRh = nullptr, *rRl = nullptr;
+    bool df_resid = false;              // the MHE-form FP32 residual in double-float arithmetic
     const void *mA = nullptr, *mB = nullptr, *mQ = nullptr, *mP0 = nullptr;    // the problem in the compute type
     const int* active_mask = nullptr;   // instances still refining (nullptr: all)
     void* mark_user = nullptr;          // non-null: record per-pass timing marks
@@ -150,6 +171,15 @@ public:
     int replan(const int* N, int batch, const long long* in_off_custom);
     // serving: factor + solve + refinement of a resident problem
     int solve_resident(const Resident& r, double* x, double* w, double* lam, mhe_info* info);
+    // serving with reuse: plan the round's windows (make_serve_plan) on the server's
+    // stores; the reduction then runs only on the chunks whose data changed
+    int replan_serve(const std::vector<ServeWindow>& w, const ExtStores& st, long long* reduced);
+    // serving with reuse: the reduction of the changed chunks (matrix part), then the
+    // whole solve (vector part up, down pass, refinement) on the resident problem
+    int solve_resident_reuse(const Resident& r, double* x, double* w, double* lam, mhe_info* info);
+    bool use_ext = false;               // level arrays from ext (serving with reuse)
+    ExtStores ext;
+    std::vector<std::vector<ChunkDesc>> rlist;   // per level: the reduction's chunks (serving with reuse)
     int leaf = 0, br = 0, topl = 0;
     void mark(int phase, int level, int begin);
 

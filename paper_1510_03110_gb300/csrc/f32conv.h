@@ -69,4 +69,39 @@ MHE_HD double f64_of(float f)
 // widening of a tree value to FP64 (the identity for FP64 trees)
 MHE_HD double f64_of(double d) { return d; }
 
+// The low part of a double-float pair: lo = RN(d - hi) with hi = f32_rn(d), so
+// that hi + lo holds d to 48 bits.  The remainder d - hi is exact in binary64:
+// the 29 fraction bits f32_rn dropped, minus 2^29 when it rounded up, in units
+// of 2^(e - 1075) for d's biased exponent e; that integer is rounded to float
+// and scaled by the power of two (exact for normal results).  Zeros and values
+// whose remainder would leave the float normal range take the hardware path.
+MHE_HD_OUTLINE float f32_lo_rare(double d, float hi) { return (float)(d - (double)hi); }
+
+MHE_HD float f32_lo(double d, float hi)
+{
+    unsigned long long u;
+    memcpy(&u, &d, sizeof(u));
+    const unsigned uh = (unsigned)(u >> 32), ul = (unsigned)u;
+    const unsigned e = (uh >> 20) & 0x7FFu;
+    // normal float hi and a normal scale 2^(e - 1075): e in 949 .. 1150
+    if (e - 949u <= 201u) {
+        const unsigned rem = ul & 0x1FFFFFFFu;
+        const unsigned top = ((uh & 0xFFFFFu) << 3) | (ul >> 29);
+        const bool up = rem > 0x10000000u || (rem == 0x10000000u && (top & 1u));
+        const int r = up ? (int)rem - (int)0x20000000 : (int)rem;   // |r| <= 2^28
+#ifdef __CUDA_ARCH__
+        const float fr = __int2float_rn(r);
+#else
+        const float fr = (float)r;
+#endif
+        const unsigned sb = ((e - 948u) << 23);                       // 2^(e - 1075) as a float
+        float scale;
+        memcpy(&scale, &sb, sizeof(scale));
+        const float lo = fr * scale;
+        return (uh & 0x80000000u) ? -lo : lo;
+    }
+    (void)hi;
+    return f32_lo_rare(d, hi);
+}
+
 }  // namespace mhe

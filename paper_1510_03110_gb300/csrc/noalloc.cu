@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(32) k_serial_noalloc(int N, const double* A, c
     if (threadIdx.x == 0) {
         cd.inst = 0; cd.t0 = 0; cd.len = N;
         cd.flags = mhe::CH_LAST | mhe::CH_TOP | mhe::CH_ARRIVAL;
-        cd.g0 = 0; cd.parent = -1; cd.px = -1;
+        cd.g0 = 0; cd.parent = -1; cd.px = -1; cd.pw = -1; cd.parent2 = -1;
         li.gs = 0; li.gx = 0; li.N = N; li.top = 1;
         off[0] = 0; off[1] = 0;
         st[0] = st[1] = st[2] = st[3] = 0;   // the status of this call starts at zero

@@ -34,7 +34,9 @@ struct ResidSmem {
     // n and nw >= 3 (every task of the first phase then has one length)
     static constexpr int sp = (NX % NW == 0 && NW >= 3) ? NX / NW : 1;
     static constexpr int mhe_form = 4 * NX + 3 * NW + 3 * NY + 5 + sp * (2 * NX + NY + NW);   // resid_mhe
-    static constexpr int count = q_form > mhe_form ? q_form : mhe_form;   // 8-byte entries
+    static constexpr int mhe_df = mhe_form + 2 * NX + NW;   // resid_mhe_df: + the split x_t, w_t, lambda_{t+1}
+    static constexpr int qm = q_form > mhe_form ? q_form : mhe_form;
+    static constexpr int count = qm > mhe_df ? qm : mhe_df;   // 8-byte entries
 };
 
 // One stage t of instance b: rows of stationarity in x_t and w_t, dynamics
@@ -297,6 +299,222 @@ MHE_DEV void resid_mhe(const ResidArgs<TR>& r, int b, int t, int N, unsigned lon
     });
 }
 
+// ---- the MHE-form residual in double-float arithmetic ------------------------
+//
+// The residual r = b - K z needs about FP64 accuracy (the refinement drives it to
+// 1e-12 of ||K|| ||z||), but GB300 issues FP64 at a small fraction of its FP32
+// rate.  Every FP64 input is carried as a float pair hi + lo (48 bits): the stage
+// matrices as the pairs the preparation pass wrote, the vectors split here in
+// integer arithmetic (f32_rn, f32_lo).  A product of two pairs keeps ah bh exactly
+// (its rounding error by an FMA) and the cross terms ah bl + al bh in float; a dot
+// product sums the exact ah bh in float with each addition's error recovered
+// (two-sum) into a float compensation, which also takes the product errors and
+// cross terms (compensated dot product in the manner of Ogita, Rump and Oishi's
+// Dot2, extended to pair inputs).  The result is about as accurate as if computed
+// with 48-bit significands, ample for relres 1e-12 at the refinement's ~1e-13
+// floor of FP64 summation order differences.  Only the FP32 pipes are used.
+
+// s + c += (ah + al)(bh + bl)
+MHE_DEV void df_acc(float& s, float& c, float ah, float al, float bh, float bl)
+{
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);          // ah bh - p, exactly
+    const float t = s + p;
+    const float z = t - s;
+    const float se = (s - (t - z)) + (p - z);   // s + p - t, exactly
+    s = t;
+    c += se + (pe + fmaf(ah, bl, al * bh));
+}
+
+// (s, c) += (s2, c2)
+MHE_DEV void df_add(float& s, float& c, float s2, float c2)
+{
+    const float t = s + s2;
+    const float z = t - s;
+    const float se = (s - (t - z)) + (s2 - z);
+    s = t;
+    c += se + c2;
+}
+
+// the pair (s, c) as a normalised pair (hi, lo), |lo| <= ulp(hi) / 2
+MHE_DEV float2 df_norm(float s, float c)
+{
+    const float h = s + c;
+    return make_float2(h, c - (h - s));
+}
+
+MHE_DEV float2 df_split(double v)
+{
+    const float h = f32_rn(v);
+    return make_float2(h, f32_lo(v, h));
+}
+
+// sum_{j < k} (mh + ml)[j sm] * v[j] into (s, c): one predicated loop, as dot_pred
+template <int KMAX>
+MHE_DEV void dot_df(const float* mh, const float* ml, int sm, const float2* v, int k, float& s, float& c)
+{
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j < k) df_acc(s, c, mh[j * sm], ml[j * sm], v[j].x, v[j].y);
+}
+
+// Stage t >= 1 in the MHE form with FP32 correction solves: the tasks of
+// resid_mhe, each a double-float dot product.
+template <int NX, int NW, int NY>
+MHE_DEV void resid_mhe_df(const ResidArgs<float>& r, int b, int t, int N, unsigned long long* sm)
+{
+    constexpr int NR = NW + NY, NQ = NX + NW;
+    const long long gx = r.gs0[b] + b;
+    const double* xt = r.x + (gx + t) * NX;
+    const double* xn = xt + NX;
+    const double* lt = r.lam + (gx + t) * NX;
+    const double* ln = lt + NX;
+    const double* wt = r.w + r.w_off[b] + NX + (long long)(t - 1) * NW;
+    const long long s = r.in_off[b] + t - 1;
+    const float *Ah = r.Ahi + s * NX * NX, *Al = r.Alo + s * NX * NX;
+    const float *Bh = r.Bhi + s * NX * NW, *Bl = r.Blo + s * NX * NW;
+    const float *Ch = r.Chi + s * NY * NX, *Cl = r.Clo + s * NY * NX;
+    const float *Rh = r.Rhi + s * NR * NR, *Rl = r.Rlo + s * NR * NR;
+    const double* l = r.l ? r.l + s * NQ : nullptr;
+    const double* a = r.a ? r.a + s * NX : nullptr;
+    const long long so = r.out_off[b] + t - 1;
+    float* rl = r.rl + so * NQ;
+    float* ra = r.ra + so * NX;
+    const bool lastst = (t == N - 1);
+    float2* dA = reinterpret_cast<float2*>(sm);   // A x
+    float2* dB = dA + NX;                         // B w
+    float2* atl = dB + NX;                        // A^T lam_{t+1}
+    float2* cte = atl + NX;                       // C^T e
+    float2* u = cte + NX;                         // C x
+    float2* sw = u + NY;                          // S^T w
+    float2* e = sw + NY;                          // V u - S^T w
+    float2* btl = e + NY;                         // B^T lam_{t+1}
+    float2* ww = btl + NW;                        // W w
+    float2* su = ww + NW;                         // S u
+    float2* vx = su + NW;                         // x_t, w_t, lam_{t+1} as pairs
+    float2* vw = vx + NX;
+    float2* vl = vw + NW;
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(vl + NX);
+    constexpr int T1 = NX + NY + NX + NW;
+    constexpr int SP = ResidSmem<NX, NW, NY>::sp;
+    constexpr int LP = NX / SP;
+    constexpr int KM = LP > NW ? LP : NW;
+    float2* part = reinterpret_cast<float2*>(mx + 4);   // SP x T1 partial sums
+    wfor(2 * NX + NW, [&](int k) {
+        if (k < NX) vx[k] = df_split(xt[k]);
+        else if (k < NX + NW) vw[k - NX] = df_split(wt[k - NX]);
+        else vl[k - NX - NW] = df_split(ln[k - NX - NW]);
+        if (k == 0) mx[0] = mx[1] = mx[2] = 0ULL;
+    });
+    wfor(T1 * SP + NX + NW + NY, [&](int k) {
+        const float *mh, *ml;
+        const float2* v;
+        float2* o;
+        int st, len = LP;
+        if (k < T1 * SP) {
+            const int q = k % T1, c = k / T1, j0 = c * LP;
+            o = part + c * T1 + q;
+            if (q < NX) { mh = Ah + q + j0 * NX; ml = Al + q + j0 * NX; st = NX; v = vx + j0; }
+            else if (q < NX + NY) { mh = Ch + (q - NX) + j0 * NY; ml = Cl + (q - NX) + j0 * NY; st = NY; v = vx + j0; }
+            else if (q < 2 * NX + NY) {
+                mh = Ah + (q - NX - NY) * NX + j0; ml = Al + (q - NX - NY) * NX + j0; st = 1; v = vl + j0;
+            } else {
+                mh = Bh + (q - 2 * NX - NY) * NX + j0; ml = Bl + (q - 2 * NX - NY) * NX + j0; st = 1; v = vl + j0;
+            }
+        } else {
+            const int q = k - T1 * SP;
+            len = NW;
+            if (q < NX) { mh = Bh + q; ml = Bl + q; st = NX; v = vw; o = dB + q; }
+            else if (q < NX + NW) { mh = Rh + (q - NX); ml = Rl + (q - NX); st = NR; v = vw; o = ww + (q - NX); }
+            else {
+                mh = Rh + (NW + q - NX - NW) * NR; ml = Rl + (NW + q - NX - NW) * NR; st = 1; v = vw;
+                o = sw + (q - NX - NW);
+            }
+        }
+        float ds = 0.f, dc = 0.f;
+        dot_df<KM>(mh, ml, st, v, len, ds, dc);
+        *o = make_float2(ds, dc);
+    });
+    // the length-n products from their pieces; C x normalised (it is the next phase's vector)
+    wfor(T1, [&](int q) {
+        float ds = part[q].x, dc = part[q].y;
+#pragma unroll
+        for (int c = 1; c < SP; ++c) df_add(ds, dc, part[c * T1 + q].x, part[c * T1 + q].y);
+        if (q < NX) dA[q] = make_float2(ds, dc);
+        else if (q < NX + NY) u[q - NX] = df_norm(ds, dc);
+        else if (q < 2 * NX + NY) atl[q - NX - NY] = make_float2(ds, dc);
+        else btl[q - 2 * NX - NY] = make_float2(ds, dc);
+    });
+    // e = V u - S^T w (normalised: the next phase's vector), S u
+    wfor(NY + NW, [&](int k) {
+        const float *mh, *ml;
+        float ds, dc;
+        if (k < NY) { mh = Rh + NW + k + NW * NR; ml = Rl + NW + k + NW * NR; ds = -sw[k].x; dc = -sw[k].y; }
+        else { mh = Rh + (k - NY) + NW * NR; ml = Rl + (k - NY) + NW * NR; ds = 0.f; dc = 0.f; }
+        dot_df<NY>(mh, ml, NR, u, NY, ds, dc);
+        if (k < NY) e[k] = df_norm(ds, dc);
+        else su[k - NY] = make_float2(ds, dc);
+    });
+    wfor(NX, [&](int i) {
+        float ds = 0.f, dc = 0.f;
+        dot_df<NY>(Ch + i * NY, Cl + i * NY, 1, e, NY, ds, dc);
+        cte[i] = make_float2(ds, dc);
+    });
+    unsigned long long m0 = 0, m1 = 0, m2 = 0;
+    const int nrow = NQ + NX + (lastst ? NX : 0);
+    const double* xN = r.x + (gx + N) * NX;
+    const double* lamN = r.lam + (gx + N) * NX;
+    const float2 zero2 = make_float2(0.f, 0.f);
+    wfor(nrow, [&](int i) {
+        float2 p1, p2;
+        const double *p3, *p4, *z1, *z2;
+        const double zd = 0.0;
+        float* dst;
+        if (i < NX) {
+            p1 = cte[i]; p2 = atl[i]; p3 = lt + i; p4 = l ? l + i : &zd;
+            z1 = xt + i; z2 = lt + i; dst = rl + i;
+        } else if (i < NQ) {
+            const int q = i - NX;
+            p1 = ww[q]; p2 = btl[q]; p4 = l ? l + i : &zd;
+            p3 = &zd;
+            z1 = wt + q; z2 = &zd; dst = rl + i;
+        } else if (i < NQ + NX) {
+            const int ii = i - NQ;
+            p1 = dA[ii]; p2 = dB[ii]; p3 = xn + ii; p4 = a ? a + ii : &zd;
+            z1 = &zd; z2 = &zd; dst = ra + ii;
+        } else {
+            // terminal rows with Q_{x,N} = 0, l_N = 0: r = lambda_N
+            const int ii = i - NQ - NX;
+            p1 = zero2; p2 = zero2; p3 = lamN + ii; p4 = &zd;
+            z1 = xN + ii; z2 = lamN + ii; dst = r.rlN + (long long)b * NX + ii;
+        }
+        // r = -(l + K z): p4 + (p1 + p2 - p3), with the S u term of the w rows subtracted
+        const float2 v3 = df_split(*p3), v4 = df_split(*p4);
+        float ds = v4.x, dc = v4.y;
+        df_add(ds, dc, p1.x, p1.y);
+        df_add(ds, dc, p2.x, p2.y);
+        df_add(ds, dc, -v3.x, -v3.y);
+        if (i >= NX && i < NQ) df_add(ds, dc, -su[i - NX].x, -su[i - NX].y);
+        const float sum = ds + dc;
+        *dst = sum;
+        const unsigned long long rr = abs_bits(f64_of(sum)), bb = abs_bits(*p4);
+        const unsigned long long za = abs_bits(*z1), zb = abs_bits(*z2);
+        const unsigned long long zz = za > zb ? za : zb;
+        m0 = rr > m0 ? rr : m0;
+        m1 = zz > m1 ? zz : m1;
+        m2 = bb > m2 ? bb : m2;
+    });
+    atomic_max_u64(mx + 0, m0);
+    atomic_max_u64(mx + 1, m1);
+    atomic_max_u64(mx + 2, m2);
+    wsync();
+    wone([&](int) {
+        atomic_max_u64(r.norms + 3LL * b + 0, mx[0]);
+        atomic_max_u64(r.norms + 3LL * b + 1, mx[1]);
+        atomic_max_u64(r.norms + 3LL * b + 2, mx[2]);
+    });
+}
+
 // Stage t >= 1 with the assembled Q: the same rows as resid_rows, as dot
 // products of length n or nw dealt round-robin to the lanes (each Q row is
 // split into its x and w halves) and one predicated FMA loop, then the rows
@@ -411,8 +629,17 @@ MHE_DEV void resid_stage(const ResidArgs<TR>& r, long long gstage, unsigned long
     if (t == 0) {
         resid_rows<NX, NW, 1, TR>(r, b, t, N, sm);
     } else {
-        if constexpr (NY > 0) resid_mhe<NX, NW, NY, TR>(r, b, t, N, sm);
-        else resid_q<NX, NW, TR>(r, b, t, N, sm);
+        if constexpr (NY > 0) {
+            if constexpr (sizeof(TR) == 4) {
+                if (r.Ahi) {
+                    resid_mhe_df<NX, NW, NY>(r, b, t, N, sm);
+                    return;
+                }
+            }
+            resid_mhe<NX, NW, NY, TR>(r, b, t, N, sm);
+        } else {
+            resid_q<NX, NW, TR>(r, b, t, N, sm);
+        }
     }
 }
 
@@ -629,6 +856,14 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
     const double* av = p.a + s * NX;
     float* A32 = p.A32 + s * NX * NX;
     float* B32 = p.B32 + s * NX * NW;
+    // the double-float pairs of the residual (when asked for): hi = the FP32 rounding, lo = the rest
+    const bool pairs = p.A_lo != nullptr;
+    float* Alo = pairs ? p.A_lo + s * NX * NX : nullptr;
+    float* Blo = pairs ? p.B_lo + s * NX * NW : nullptr;
+    float* Chi = pairs ? p.C_hi + s * NY * NX : nullptr;
+    float* Clo = pairs ? p.C_lo + s * NY * NX : nullptr;
+    float* Rhi = pairs ? p.R_hi + s * NR * NR : nullptr;
+    float* Rlo = pairs ? p.R_lo + s * NR * NR : nullptr;
     float* a32 = p.a32 + s * NX;
     float* Qo = p.Q32 + s * NQ * NQ;
     double* lo = p.l + s * NQ;
@@ -651,17 +886,21 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
             const float f = f32_rn(v);
             if (i < O1) {
                 fC[i % NY + (i / NY) * LC] = f;
+                if (pairs) { Chi[i] = f; Clo[i] = f32_lo(v, f); }
             } else if (i < O2) {
                 const int k = i - O1;
                 fR[k % NR + (k / NR) * LR] = f;
+                if (pairs) { Rhi[k] = f; Rlo[k] = f32_lo(v, f); }
             } else if (i < O3) {
                 const int k = i - O2;
                 A32[k] = f;
                 fA[k % NX + (k / NX) * LA] = f;
+                if (pairs) Alo[k] = f32_lo(v, f);
             } else if (i < O4) {
                 const int k = i - O3;
                 B32[k] = f;
                 fB[k % NX + (k / NX) * LA] = f;
+                if (pairs) Blo[k] = f32_lo(v, f);
             } else if (i < O5) {
                 dy[i - O4] = v;   // y~ then w~ (contiguous)
             } else {

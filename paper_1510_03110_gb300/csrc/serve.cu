@@ -13,6 +13,13 @@
 // tree (factor + solve + refinement) on the device while the host prepares the
 // next one.  The result of a request is the estimate of the newest measured
 // state, UFTOC x_{N-1}.
+//
+// Factorisation reuse: the tree's chunk boundaries are fixed in absolute sample
+// time (make_serve_plan), and every estimator keeps, per level, a ring of the
+// stored factors and master stages of its chunks.  A shift changes only each
+// level's first and last chunk (and the chunk that stops being last); a round
+// re-reduces those, keeps every other chunk's Algorithm 4 output, and runs the
+// vector part, the down pass and the refinement over the whole window.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -130,6 +137,11 @@ struct Estimator {
     int slot;              // index into the bucket's per-estimator arrays
     bool in_flight = false;
     std::deque<Request> pending;
+    long long k0 = 0;      // absolute index of the window's first measured sample
+    // per level of the tree: first slot and capacity of this estimator's ring in the
+    // bucket's stores, and the chunk ranges of its previous round
+    std::vector<long long> sbase, scap;
+    std::vector<mhe::ServeLevelHist> hist;
 };
 
 struct Round;
@@ -145,6 +157,10 @@ struct Bucket {
     int cap_est = 0, used_est = 0;
     double *x0_all = nullptr, *P0_all = nullptr;
     std::vector<int> members;   // estimator ids
+    // stores of the tree's stored factors and master stages, one per level
+    // (elements of the server's compute type), in slots of every estimator's rings
+    mhe::ExtStores st;
+    std::vector<long long> st_cap, st_used;   // slots allocated and used, per level
     struct Slot {
         mhe::Engine eng;
         cudaStream_t stream = nullptr;
@@ -177,6 +193,8 @@ struct Bucket {
 struct mhe_server {
     int prec = MHE_FP32_IR;
     int leaf_len = 0, branching = 0, top_len = 0;   // plan of every round (0: the default plan)
+    int reuse = 1;                                  // keep unchanged chunks' reductions across rounds
+    long long n_rounds = 0, n_requests = 0, n_reduced = 0, n_stages = 0;   // counters (mhe_server_stats)
     size_t budget = 0, used = 0;
     double refine_tol = 1e-9;
     int max_refine = 8;
@@ -268,6 +286,65 @@ bool grow_bucket(mhe_server* s, Bucket& b, long long need_slots, int need_est)
     return true;
 }
 
+// the plan rounds use for shape (nx, nw): the server's, 0 = the defaults of mhe_dims
+void eff_plan(const mhe_server* s, int nx, int nw, int* leaf, int* br, int* top)
+{
+    const int min_leaf = (nx + nw - 1) / nw;
+    *leaf = s->leaf_len > 0 ? s->leaf_len : (min_leaf > 8 ? min_leaf : 8);
+    *br = s->branching > 0 ? s->branching : 4;
+    *top = s->top_len > 0 ? s->top_len : 4;
+}
+
+// elements of one store slot at level k: P, chol(G), K, k, L (and at k >= 1 the
+// master stage A^, R^T, Q^_x, a^, l^_x)
+size_t slot_elems(int k, int n, int m)
+{
+    const size_t mk = k == 0 ? (size_t)m : (size_t)n, n2 = (size_t)n * n;
+    return n2 + mk * mk + 2 * mk * n + mk + (k >= 1 ? 3 * n2 + 2 * (size_t)n : 0);
+}
+
+// grow the bucket's stores to at least need[k] slots per level (the server's
+// streams are idle); the used part of each array is kept
+bool grow_stores(mhe_server* s, Bucket& b, const std::vector<long long>& need)
+{
+    const int n = b.nx, m = b.nw;
+    const size_t ts = s->prec == MHE_FP64 ? sizeof(double) : sizeof(float);
+    if (b.st_cap.size() < need.size()) {
+        b.st_cap.resize(need.size(), 0);
+        b.st_used.resize(need.size(), 0);
+        for (auto* v : {&b.st.Pst, &b.st.Lgst, &b.st.Kst, &b.st.kst, &b.st.Lst, &b.st.Ah, &b.st.Bh, &b.st.Qxh,
+                        &b.st.ah, &b.st.lxh})
+            v->resize(need.size(), nullptr);
+    }
+    for (size_t k = 0; k < need.size(); ++k) {
+        if (need[k] <= b.st_cap[k]) continue;
+        long long cap = b.st_cap[k] ? b.st_cap[k] : 1024;
+        while (cap < need[k]) cap *= 2;
+        const size_t mk = k == 0 ? (size_t)m : (size_t)n, n2 = (size_t)n * n;
+        const size_t per[10] = {n2, mk * mk, mk * n, mk, mk * n, n2, n2, n2, (size_t)n, (size_t)n};
+        void** arr[10] = {&b.st.Pst[k], &b.st.Lgst[k], &b.st.Kst[k], &b.st.kst[k], &b.st.Lst[k],
+                          &b.st.Ah[k], &b.st.Bh[k], &b.st.Qxh[k], &b.st.ah[k], &b.st.lxh[k]};
+        const int narr = k == 0 ? 5 : 10;
+        const size_t add = (size_t)(cap - b.st_cap[k]) * slot_elems((int)k, n, m) * ts;
+        if (s->used + add > s->budget) return false;
+        for (int i = 0; i < narr; ++i) {
+            void* p = nullptr;
+            if (cudaMalloc(&p, (size_t)cap * per[i] * ts) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            if (*arr[i]) {
+                cudaMemcpy(p, *arr[i], (size_t)b.st_used[k] * per[i] * ts, cudaMemcpyDeviceToDevice);
+                cudaFree(*arr[i]);
+            }
+            *arr[i] = p;
+        }
+        s->used += add;
+        b.st_cap[k] = cap;
+    }
+    return true;
+}
+
 // round buffers of one engine slot for `batch` members, S new stages, X states, W inputs
 bool ensure_slot(mhe_server* s, Bucket& bk, Bucket::Slot& sl, size_t batch, size_t X, size_t W)
 {
@@ -354,8 +431,32 @@ int launch_round(mhe_server* s, Bucket& bk, Bucket::Slot& sl)
         if (rc != MHE_OK) return rc;
         sl.ready = true;
     }
-    int rc = sl.eng.replan(Nv.data(), batch, in_off.data());
+    // the round's tree on the estimators' rings (make_serve_plan): only the chunks whose
+    // data changed since an estimator's previous round are reduced again
+    std::vector<mhe::ServeWindow> win(batch);
+    long long reduced = 0, stages = 0;
+    for (int b = 0; b < batch; ++b) {
+        Estimator& e = s->est[sl.ests[b]];
+        e.k0 += 1;   // the shift: samples k0 .. k0 + N - 2
+        if (!s->reuse) e.hist.clear();   // nothing kept: every chunk reduced again
+        win[b].N = e.N;
+        win[b].k0 = e.k0;
+        win[b].in_off = in_off[b];
+        win[b].base = e.sbase.data();
+        win[b].cap = e.scap.data();
+        win[b].nlev = (int)e.sbase.size();
+        win[b].hist = &e.hist;
+        stages += e.N;
+    }
+    int rc = sl.eng.replan_serve(win, bk.st, &reduced);
     if (rc != MHE_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->n_rounds += 1;
+        s->n_requests += batch;
+        s->n_reduced += reduced;
+        s->n_stages += stages;
+    }
     const size_t sd = stage_doubles(n, m, q);
     for (int b = 0; b < batch; ++b) memcpy(sl.h_stage + (size_t)b * sd, sl.reqs[b].stage.data(), sizeof(double) * sd);
     cudaStream_t st = sl.stream;
@@ -396,7 +497,7 @@ int launch_round(mhe_server* s, Bucket& bk, Bucket::Slot& sl)
     } else {
         r.At = bk.A; r.Bt = bk.B; r.Qt = bk.Q; r.P0t = sl.P0; r.lt = bk.l; r.at = bk.a; r.x0t = sl.x0;
     }
-    rc = sl.eng.solve_resident(r, sl.x, sl.w, sl.lam, sl.d_info);
+    rc = sl.eng.solve_resident_reuse(r, sl.x, sl.w, sl.lam, sl.d_info);
     k_extract<<<batch, 64, 0, st>>>(batch, n, sl.est_slot, sl.gxd, sl.Nd, sl.x, sl.res, bk.x0_all);
     cudaMemcpyAsync(sl.h_res, sl.res, sizeof(double) * batch * n, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(sl.h_info, sl.d_info, sizeof(mhe_info) * batch, cudaMemcpyDeviceToHost, st);
@@ -532,8 +633,20 @@ int mhe_estimator_open(mhe_server* s, int nx, int nw, int ny, int N, const doubl
         }
     }
     const int cap = N - 1;
-    // admission by device memory: ring slots (mirrored) and per-estimator arrays
-    if (!grow_bucket(s, *bk, bk->used_slots + 2LL * cap, bk->used_est + 1)) {
+    // the tree's rings of this estimator (per level: capacity and tail)
+    int leaf, br, top;
+    eff_plan(s, nx, nw, &leaf, &br, &top);
+    std::vector<long long> rcap;
+    long long tail = 0;
+    if (mhe::serve_caps(N, leaf, br, top, rcap, &tail) < 1) {
+        mhe::set_last_error("bad plan for the estimator's horizon");
+        return MHE_E_ARG;
+    }
+    // admission by device memory: ring slots (mirrored), per-estimator arrays and the tree's stores
+    std::vector<long long> need(rcap.size());
+    for (size_t k = 0; k < rcap.size(); ++k)
+        need[k] = (k < bk->st_used.size() ? bk->st_used[k] : 0) + rcap[k] + tail;
+    if (!grow_bucket(s, *bk, bk->used_slots + 2LL * cap, bk->used_est + 1) || !grow_stores(s, *bk, need)) {
         s->err = "admission refused: the device-memory budget is exhausted";
         mhe::set_last_error(s->err);
         return MHE_E_ADMISSION;
@@ -548,6 +661,13 @@ int mhe_estimator_open(mhe_server* s, int nx, int nw, int ny, int N, const doubl
     e.slot = bk->used_est;
     bk->used_slots += 2LL * cap;
     bk->used_est += 1;
+    e.k0 = 0;
+    e.scap = rcap;
+    e.sbase.resize(rcap.size());
+    for (size_t k = 0; k < rcap.size(); ++k) {
+        e.sbase[k] = bk->st_used[k];
+        bk->st_used[k] += rcap[k] + tail;
+    }
     // the initial window: assemble on the device (Section II), write both mirrors
     const int n = nx, m = nw, q = ny;
     size_t u = 0;
@@ -654,16 +774,37 @@ int mhe_server_set_plan(mhe_server* s, int leaf_len, int branching, int top_len)
         return MHE_E_ARG;
     }
     std::lock_guard<std::mutex> lock(s->mu);
-    for (auto& b : s->buckets)
-        for (auto& sl : b->slot)
-            if (sl.ready || sl.busy) {
-                mhe::set_last_error("mhe_server_set_plan must precede the first request");
-                return MHE_E_ARG;
-            }
+    if (!s->est.empty()) {   // the estimators' rings are sized for the plan
+        mhe::set_last_error("mhe_server_set_plan must precede the first mhe_estimator_open");
+        return MHE_E_ARG;
+    }
     s->leaf_len = leaf_len;
     s->branching = branching;
     s->top_len = top_len;
     return MHE_OK;
+}
+
+int mhe_server_set_reuse(mhe_server* s, int on)
+{
+    if (!s) {
+        mhe::set_last_error("bad arguments to mhe_server_set_reuse");
+        return MHE_E_ARG;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->reuse = on ? 1 : 0;
+    return MHE_OK;
+}
+
+int mhe_server_stats(mhe_server* s, long long* out, int cap)
+{
+    if (!s || (!out && cap > 0)) {
+        mhe::set_last_error("bad arguments to mhe_server_stats");
+        return MHE_E_ARG;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    const long long v[4] = {s->n_rounds, s->n_requests, s->n_reduced, s->n_stages};
+    for (int i = 0; i < 4 && i < cap; ++i) out[i] = v[i];
+    return 4;
 }
 
 int mhe_server_destroy(mhe_server* s)
@@ -680,6 +821,9 @@ int mhe_server_destroy(mhe_server* s)
         cudaFree(b->A); cudaFree(b->B); cudaFree(b->Q); cudaFree(b->l); cudaFree(b->a);
         cudaFree(b->Af); cudaFree(b->Bf); cudaFree(b->Qf); cudaFree(b->lf); cudaFree(b->af);
         cudaFree(b->x0_all); cudaFree(b->P0_all);
+        for (auto* v : {&b->st.Pst, &b->st.Lgst, &b->st.Kst, &b->st.kst, &b->st.Lst, &b->st.Ah, &b->st.Bh,
+                        &b->st.Qxh, &b->st.ah, &b->st.lxh})
+            for (void* p : *v) cudaFree(p);
         for (auto& sl : b->slot) {
             if (sl.ready) sl.eng.release();
             cudaFree(sl.x); cudaFree(sl.w); cudaFree(sl.lam); cudaFree(sl.x0); cudaFree(sl.P0); cudaFree(sl.res);

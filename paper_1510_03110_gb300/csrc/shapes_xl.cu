@@ -11,6 +11,13 @@ namespace mhe {
 
 void shapes_xl_fp64(ShapeOps& o);   // shapes_xl64.cu
 
+// the tries of the tensor-core product waits of this unit's kernels (< 0: the default)
+int set_tc_wait_limit(int tries)
+{
+    const int v = tries < 0 ? -1 : tries;
+    return cudaMemcpyToSymbol(tc::g_wait_override, &v, sizeof(int)) == cudaSuccess ? 0 : -1;
+}
+
 int shapes_xl(ShapeEntry* out, int cap)
 {
     int k = 0;

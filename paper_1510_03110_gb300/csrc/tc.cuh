@@ -219,11 +219,17 @@ MHE_DEV void tmem_ld16x2(uint32_t tbase, int /*lane*/, int col_a, int col_b, flo
 // bounded time; the MMAs of one stage take microseconds)
 constexpr int kWaitLimit = 1 << 20;
 
+// Tries of the product waits when >= 0 (a test setting, default -1: kWaitLimit);
+// the wait that frees TMEM after a failed one always takes kWaitLimit.  One copy
+// per translation unit: the tensor-core kernels' unit sets its own.
+static __device__ int g_wait_override = -1;
+
 // every thread of the team (= the CTA) waits for the phase; true when all saw
 // it complete.  Accumulator reads may follow.
 MHE_DEV bool team_wait(uint64_t* m, uint32_t parity)
 {
-    const bool ok = mbar_wait(m, parity, kWaitLimit);
+    const int lim = g_wait_override >= 0 ? g_wait_override : kWaitLimit;
+    const bool ok = mbar_wait(m, parity, lim);
     const bool all = __syncthreads_and(ok) != 0;
     fence_after();
     return all;

@@ -290,6 +290,73 @@ MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
     return s.sc[1] != 0;
 }
 
+// Rank-revealing (pivoted) Cholesky of the symmetric NX x NX matrix Gm (both
+// triangles held): at step j the largest remaining diagonal is brought to (j, j)
+// by a symmetric row and column swap; the factorisation stops at the first step
+// whose largest remaining diagonal is at or below rank_rel * max diag, and that
+// step is the numerical rank r.  On return Pi^T Gm_in Pi = L L^T restricted to
+// r columns: L (lower trapezoidal, NX x r) in Gm's lower part, the pivot order
+// Pi in permv (as values of T), and r is returned.
+template <typename T, int NX>
+MHE_DEV int chol_pivoted(Ws<T, NX>& s, T* Gm, double rank_rel, T* permv)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    wone([&](int) {
+        T mx = 0;
+        for (int i = 0; i < NX; ++i) {
+            mx = mmax(mx, mabs(Gm[i + i * ld]));
+            permv[i] = (T)i;
+        }
+        s.sc[0] = (T)(rank_rel * (double)mx);
+        s.sc[3] = (T)NX;
+    });
+    for (int j = 0; j < NX; ++j) {
+        wone([&](int) {
+            int p = j;
+            T best = Gm[j + j * ld];
+            for (int i = j + 1; i < NX; ++i)
+                if (Gm[i + i * ld] > best) { best = Gm[i + i * ld]; p = i; }
+            s.sc[4] = (T)p;
+            if (!(best > s.sc[0])) s.sc[3] = (T)j;   // the rank: nothing above the threshold remains
+        });
+        if ((int)s.sc[3] == j) break;   // the same value for every lane (read after the barrier)
+        const int p = (int)s.sc[4];
+        if (p != j) {
+            wfor(NX, [&](int q) {
+                const T t = Gm[j + q * ld];
+                Gm[j + q * ld] = Gm[p + q * ld];
+                Gm[p + q * ld] = t;
+            });
+            wfor(NX, [&](int q) {
+                const T t = Gm[q + j * ld];
+                Gm[q + j * ld] = Gm[q + p * ld];
+                Gm[q + p * ld] = t;
+            });
+            wone([&](int) {
+                const T t = permv[j];
+                permv[j] = permv[p];
+                permv[p] = t;
+            });
+        }
+        wone([&](int) {
+            const T l = msqrt(Gm[j + j * ld]);
+            Gm[j + j * ld] = l;
+            s.sc[2] = l;
+        });
+        const T ljj = s.sc[2];
+        wfor(NX, [&](int i) {
+            if (i > j) Gm[i + j * ld] /= ljj;
+        });
+        // the trailing block, both triangles (the next pivot search and swaps read them)
+        const int rem = NX - j - 1;
+        wfor(rem * rem, [&](int u) {
+            const int i = j + 1 + u % rem, c = j + 1 + u / rem;
+            Gm[i + c * ld] -= Gm[i + j * ld] * Gm[c + j * ld];
+        });
+    }
+    return (int)s.sc[3];
+}
+
 template <typename T, int NX, int MT>
 MHE_DEV bool chol_G(Ws<T, NX>& s, double piv_rel)
 {
@@ -420,6 +487,28 @@ struct TcState {
     int ok;
 };
 
+// Accumulator rows from TMEM; after a wait that ran out (the products may still be in
+// flight) nothing is read and zeros stand in (the instance already reports the timeout).
+// The condition is the same for every thread of the team, as the loads require.
+MHE_DEV void tmem_pair(const TcState& t, int row, int c0, int c1, float (&v)[16], float (&w)[16])
+{
+    if (t.ok) {
+        tc::tmem_ld16x2(t.tbase, row, c0, c1, v, w);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = w[i] = 0.f;
+    }
+}
+MHE_DEV void tmem_one(const TcState& t, int row, int c0, float (&v)[16])
+{
+    if (t.ok) {
+        tc::tmem_ld16(t.tbase, row, c0, v);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+    }
+}
+
 // the team's wait for the MMAs it committed last; a wait that runs out marks the
 // state failed, and no further MMA is issued
 MHE_DEV void tc_team_wait(TcState& t)
@@ -526,7 +615,7 @@ MHE_DEV void tc_stage_products(Ws<float, NX>& s, const StageRef<float>& st, TcSt
 #pragma unroll 1
         for (int c = 0; c < NX; c += 16) {
             float v[16], w[16];
-            tc::tmem_ld16x2(tcs.tbase, r, c, NX + c, v, w);
+            tmem_pair(tcs, r, c, NX + c, v, w);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] += w[i];
             if (r < NAB) {
@@ -565,7 +654,7 @@ MHE_DEV void tc_stage_products(Ws<float, NX>& s, const StageRef<float>& st, TcSt
 #pragma unroll 1
         for (int c = 0; c < NAB; c += 16) {
             float v[16], w[16];
-            tc::tmem_ld16x2(tcs.tbase, r, C2 + c, C2 + NAB + c, v, w);
+            tmem_pair(tcs, r, C2 + c, C2 + NAB + c, v, w);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = qv[i] + (v[i] + w[i]);
             if (c + 16 < NAB) {
@@ -691,8 +780,8 @@ MHE_DEV void tc_stage_products_bf16(Ws<float, NX>& s, const StageRef<float>& st,
 #pragma unroll 1
         for (int c = 0; c < NX; c += 16) {
             float v[16], w[16], z[16];
-            tc::tmem_ld16x2(tcs.tbase, r, c, NX + c, v, w);
-            tc::tmem_ld16(tcs.tbase, r, 2 * NX + c, z);
+            tmem_pair(tcs, r, c, NX + c, v, w);
+            tmem_one(tcs, r, 2 * NX + c, z);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] += w[i] + z[i];
             if (r < NAB) {
@@ -723,8 +812,8 @@ MHE_DEV void tc_stage_products_bf16(Ws<float, NX>& s, const StageRef<float>& st,
 #pragma unroll 1
         for (int c = 0; c < NAB; c += 16) {
             float v[16], w[16], z[16];
-            tc::tmem_ld16x2(tcs.tbase, r, c, NAB + c, v, w);
-            tc::tmem_ld16(tcs.tbase, r, 2 * NAB + c, z);
+            tmem_pair(tcs, r, c, NAB + c, v, w);
+            tmem_one(tcs, r, 2 * NAB + c, z);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = qv[i] + (v[i] + (w[i] + z[i]));
             if (c + 16 < NAB) {
@@ -986,12 +1075,34 @@ MHE_DEV void reduce_chunk(const LevelArgs<T>& a, int ci, T* smem, TcState* tcs =
         // Q^_w = S Qbar^{-1} S^T accumulated above.  Same master problem with
         // w^' = R w^; its G = I + R P R^T is far better conditioned than
         // B^ + B^ P B^.
-        if (chol_inplace<T, NX, NX>(s, s.Qw, a.piv_rel) && bad_t < 0) bad_t = cd.t0;
-        const long long gp = cd.parent;
-        wfor(NX * NX, [&](int idx) {
+        // With leaf chunks too short for a full-rank Q^_w (leaf_len * nw < nx: S^T rank
+        // deficient, Section IV-B's remark on a singular G^), the factorisation pivots and
+        // stops at the numerical rank r, Pi^T Q^_w Pi = L L^T with L n x r, and the
+        // master stage is B = Pi L padded with zero columns to width n, Q_w = I: a
+        // basis U_1 = S^T Pi [L_11^{-T}; 0] of range(S^T) in Theorem 1; the down pass
+        // recovers w^ = Pi [L_11^{-T} w^'_{1..r}; 0].
+        int rank = NX;
+        if (a.piv_up) {
+            rank = chol_pivoted<T, NX>(s, s.Qw, a.piv_rank, s.u);
+            if (rank == 0 && bad_t < 0) bad_t = cd.t0;
+        } else if (chol_inplace<T, NX, NX>(s, s.Qw, a.piv_rel) && bad_t < 0) {
+            bad_t = cd.t0;
+        }
+        // the master stage's data at cd.parent (and at its mirror cd.parent2, when given)
+        const int copies = cd.parent2 >= 0 ? 2 : 1;
+        wfor(copies * NX * NX, [&](int u) {
+            const long long gp = u < NX * NX ? cd.parent : cd.parent2;
+            const int idx = u % (NX * NX);
             int i = idx % NX, j = idx / NX;
             a.Ah_up[gp * NX * NX + idx] = s.V[j + i * ld];
-            a.Bh_up[gp * NX * NX + idx] = i >= j ? s.Qw[i + j * ld] : (T)0;
+            if (a.piv_up) {   // row Pi(i) of B is row i of L (columns j >= r are zero)
+                const int pi = (int)s.u[i];
+                a.Bh_up[gp * NX * NX + pi + j * NX] = (i >= j && j < rank) ? s.Qw[i + j * ld] : (T)0;
+                if (j == 0) a.piv_up[gp * (NX + 1) + i] = pi;
+                if (idx == 0) a.piv_up[gp * (NX + 1) + NX] = rank;
+            } else {
+                a.Bh_up[gp * NX * NX + idx] = i >= j ? s.Qw[i + j * ld] : (T)0;
+            }
             a.Qxh_up[gp * NX * NX + idx] = s.P[i + j * ld];
             if (idx < NX) {
                 a.ah_up[gp * NX + idx] = s.v[idx];
@@ -1140,8 +1251,10 @@ MHE_DEV void rhs_chunk(const LevelArgs<T>& a, int ci, T* smem)
                 closed_loop_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), a.Kst + g * NW * NX,
                                                        a.kst + g * NW);
         }
-        const long long gp = cd.parent;
-        wfor(NX, [&](int i) {
+        const int copies = cd.parent2 >= 0 ? 2 : 1;
+        wfor(copies * NX, [&](int u) {
+            const long long gp = u < NX ? cd.parent : cd.parent2;
+            const int i = u % NX;
             a.ah_up[gp * NX + i] = s.e[i];
             a.lxh_up[gp * NX + i] = -s.Psi[i];
         });
@@ -1238,10 +1351,25 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     // x^_i -> s.e, w^_i -> s.v, lambda^_{i+1} -> s.Psi
     wfor(NX, [&](int i) {
         s.e[i] = top ? a.x0[(long long)b * NX + i] : a.xd_up[cd.px * NX + i];
-        s.v[i] = last ? (T)0 : a.wd_up[cd.parent * NX + i];
+        s.v[i] = last ? (T)0 : a.wd_up[cd.pw * NX + i];
         s.Psi[i] = last ? (T)0 : a.ld_up[(cd.px + 1) * NX + i];
     });
-    if (!last) {
+    if (!last && a.piv_up) {
+        // rank-revealing master stage B = Pi L (n x r, zero-padded): the parent solved for
+        // w^'; w^ = Pi [L_11^{-T} w^'_{1..r}; 0], with L(i, j) = B(Pi(i), j)
+        const int* pv = a.piv_up + cd.parent * (NX + 1);
+        const T* Bq = a.Bh_up + cd.parent * NX * NX;
+        wone([&](int) {
+            const int r = pv[NX];
+            for (int i = r - 1; i >= 0; --i) {
+                T acc = s.v[i];
+                for (int p = i + 1; p < r; ++p) acc -= Bq[pv[p] + i * NX] * s.v[p];
+                s.v[i] = acc / Bq[pv[i] + i * NX];
+            }
+            for (int i = 0; i < NX; ++i) s.tmp[i] = s.v[i];
+            for (int i = 0; i < NX; ++i) s.v[pv[i]] = i < r ? s.tmp[i] : (T)0;
+        });
+    } else if (!last) {
         // the parent solved for w^' = R w^ (square-root master stage): w^ = R^{-1} w^'
         const T* Lq = a.Bh_up + cd.parent * NX * NX;   // R^T, lower triangular
         wone([&](int) {

@@ -95,6 +95,10 @@ def _declare(L):
     L.mhe_launch_count.restype = c_ll
     L.mhe_assemble_count.argtypes = []
     L.mhe_assemble_count.restype = c_ll
+    L.mhe_set_double_float_residual.argtypes = [c_void_p, c_int]
+    L.mhe_set_double_float_residual.restype = c_int
+    L.mhe_debug_set_tc_wait_limit.argtypes = [c_int]
+    L.mhe_debug_set_tc_wait_limit.restype = c_int
     L.mhe_solve_serial_noalloc.argtypes = [c_int, c_int, c_int] + [c_void_p] * 12
     L.mhe_solve_serial_noalloc.restype = c_int
     L.mhe_autotune.argtypes = [P(mhe_dims), P(mhe_matrices), P(mhe_rhs), c_void_p, c_int, P(mhe_dims),
@@ -112,6 +116,10 @@ def _declare(L):
     L.mhe_server_set_plan.restype = c_int
     L.mhe_server_used_bytes.argtypes = [c_void_p]
     L.mhe_server_used_bytes.restype = ctypes.c_size_t
+    L.mhe_server_set_reuse.argtypes = [c_void_p, c_int]
+    L.mhe_server_set_reuse.restype = c_int
+    L.mhe_server_stats.argtypes = [c_void_p, ctypes.POINTER(c_ll), c_int]
+    L.mhe_server_stats.restype = c_int
     L.mhe_server_destroy.argtypes = [c_void_p]
     L.mhe_server_destroy.restype = c_int
     L.mhe_last_error.argtypes = []
@@ -311,6 +319,16 @@ def mhe_launch_count(ctx):
 
 def mhe_assemble_count():
     return int(lib().mhe_assemble_count())
+
+
+def mhe_set_double_float_residual(ctx, on=True):
+    """The mixed-precision MHE-form residual in double-float (True, default) or FP64 arithmetic."""
+    return _check(lib().mhe_set_double_float_residual(ctx, int(bool(on))), "mhe_set_double_float_residual")
+
+
+def mhe_debug_set_tc_wait_limit(tries):
+    """Tries of the tensor-core product waits (< 0: the default); a test of the timeout path."""
+    return _check(lib().mhe_debug_set_tc_wait_limit(int(tries)), "mhe_debug_set_tc_wait_limit")
 
 
 def mhe_plan_info(ctx):
@@ -517,6 +535,18 @@ class Server:
 
     def used_bytes(self):
         return int(lib().mhe_server_used_bytes(self.s))
+
+    def set_reuse(self, on=True):
+        _check(lib().mhe_server_set_reuse(self.s, int(bool(on))), "mhe_server_set_reuse")
+
+    def stats(self):
+        """{rounds, requests, stages_reduced, stages_solved} since the server was created."""
+        buf = (c_ll * 4)()
+        k = lib().mhe_server_stats(self.s, buf, 4)
+        if k < 0:
+            raise MheError(k, "mhe_server_stats")
+        return dict(rounds=int(buf[0]), requests=int(buf[1]), stages_reduced=int(buf[2]),
+                    stages_solved=int(buf[3]))
 
     def close(self):
         if self.s:

@@ -437,8 +437,13 @@ void scenario_errors()
     d.prec = (mhe_precision)7;
     CHECK(e2.init(d, &ops, &kFakeRuntime, nullptr) == MHE_E_ARG, "unknown precision");
     Engine e3;
-    d = dims_of(p, MHE_FP32_IR, 1, 2, 2, 1);   // leaf_len * nw < nx
-    CHECK(e3.init(d, &ops, &kFakeRuntime, nullptr) == MHE_E_ARG, "a leaf too short for the T-form reduction");
+    d = dims_of(p, MHE_FP32_IR, 1, 2, 2, 1);   // leaf_len * nw < nx: rank-revealing master stages
+    CHECK(e3.init(d, &ops, &kFakeRuntime, nullptr) == MHE_OK && e3.pivot, "a short leaf selects pivoting");
+    CHECK(e3.lv.size() >= 2 && e3.lv[1].piv != nullptr, "pivot records per master stage");
+    e3.release();
+    Engine e4;
+    d = dims_of(p, MHE_FP32_IR, 4, 1, 2, 1);   // branching < 2
+    CHECK(e4.init(d, &ops, &kFakeRuntime, nullptr) == MHE_E_ARG, "branching below 2 is refused");
 }
 
 // Steps a0..a7 from MHE data: FP32 -- one preparation pass, the reduction with the

@@ -77,7 +77,11 @@ def test_zero_plan_fields_are_the_documented_defaults(L):
 def test_bad_dims_rejected_on_host(L):
     d, _ = mhe.make_dims(5, 4, [10])        # shape not compiled
     assert mhe.mhe_workspace_bytes(d) == 0
-    d, _ = mhe.make_dims(4, 2, [10], leaf_len=1)   # leaf_len * nw < nx
+    d, _ = mhe.make_dims(4, 2, [10], leaf_len=1)   # leaf_len * nw < nx: rank-revealing master stages
+    assert mhe.mhe_workspace_bytes(d) > 0
+    d, _ = mhe.make_dims(4, 2, [10], leaf_len=-1)
+    assert mhe.mhe_workspace_bytes(d) > 0            # negative = the default plan
+    d, _ = mhe.make_dims(4, 2, [10], branching=1)    # branching must be >= 2
     assert mhe.mhe_workspace_bytes(d) == 0
     d, _ = mhe.make_dims(4, 2, [0])         # horizon must be >= 1
     assert mhe.mhe_workspace_bytes(d) == 0

@@ -252,3 +252,35 @@ def test_error_estimate_per_instance(prec):
         assert np.abs(z - zr).max() / np.abs(zr).max() <= est, (b, est)
     if prec == mhe.MHE_FP32_IR:
         assert refined == len(Ns)
+
+
+def test_tensor_core_wait_that_runs_out_is_reported_and_the_context_recovers():
+    """The failure path of the tensor-core reductions: with the product waits limited to
+    0 tries the first wait of every team runs out; the instance reports MHE_E_TIMEOUT
+    with the place (level 0, its chunk, the chunk's first stage), the team issues no
+    further products and waits once more (default limit) before freeing its tensor
+    memory.  After the default limit is restored the same context solves correctly."""
+    import torch
+    n, m = 64, 32
+    insts = [synth.mhe_instance(1500 + i, n, m, m, N) for i, N in enumerate([9, 20])]
+    d = device_inputs(insts)
+    ref = _oracle(insts)
+    s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_TF32_IR, top_len=1000, refine_tol=1e-12, max_refine=8)
+    try:
+        mhe.mhe_debug_set_tc_wait_limit(0)
+        _estimate(d, s)
+        torch.cuda.synchronize()
+        info = s.infos()
+    finally:
+        mhe.mhe_debug_set_tc_wait_limit(-1)
+    for b in range(2):
+        assert info["status"][b] == -7, info[b]
+        assert info["level"][b] == 0 and info["chunk"][b] == b and info["stage"][b] == 0, info[b]
+    x, w, lam = _estimate(d, s)
+    torch.cuda.synchronize()
+    info = s.infos()
+    sols = split(x, w, lam, d["N"], n, m)
+    s.close()
+    for b in range(2):
+        assert info["status"][b] == 0, info[b]
+        assert rel_err(sols[b], ref[b]) <= 1e-8

@@ -32,28 +32,72 @@ def _oracle_sequence(stream, N, x0, requests, n, m, q):
     return out
 
 
-def _run_alone(prec, stream, N, x0, requests, n, m, q, tol):
+def _run_alone(prec, stream, N, x0, requests, n, m, q, tol, plan=None, reuse=True, stats=None):
     srv = mhe.Server(1 << 30, prec=prec, refine_tol=tol)
+    if plan:
+        srv.set_plan(**plan)
+    srv.set_reuse(reuse)
     e = srv.open(synth.window_of(stream, 0, N, x0, n, m, q))
     res = []
     for j in range(requests):
         t = srv.submit(e, _stage(stream, N - 1 + j))
         res.append(srv.wait(t, n))
+    if stats is not None:
+        stats.update(srv.stats())
     srv.close()
     return res
 
 
-@pytest.mark.parametrize("prec,tol,bound", [(mhe.MHE_FP64, 1e-12, 1e-10), (mhe.MHE_FP32_IR, 1e-11, 1e-8)])
-def test_served_estimates_match_oracle(prec, tol, bound):
-    n, m, q, N, K = 4, 2, 2, 40, 6
+PLANS = [dict(leaf_len=8, branching=4, top_len=4), dict(leaf_len=4, branching=2, top_len=2),
+         dict(leaf_len=0, branching=0, top_len=1 << 20)]
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=["tree", "short_leaves", "serial"])
+@pytest.mark.parametrize("prec,tol,bound", [(mhe.MHE_FP64, 1e-12, 1e-10), (mhe.MHE_FP32_IR, 1e-12, 1e-8)])
+def test_served_estimates_match_oracle(prec, tol, bound, plan):
+    """K = 70 consecutive shifts of one estimator (N = 40): the windows cross many chunk
+    boundaries and wrap the level rings, so most rounds reuse the reductions of chunks
+    kept from earlier rounds.  Every result equals the oracle's from-scratch solve of
+    that window.  FP32_IR refines to relres 1e-12, the residual at which the forward
+    error of the worst-conditioned windows meets 1e-8 (relres 1e-11 left 1.02e-8 on one
+    of these 70)."""
+    n, m, q, N, K = 4, 2, 2, 40, 70
     st = synth.plant_stream(1, n, m, q, N - 1 + K)
     x0 = np.zeros(n)
-    got = _run_alone(prec, st, N, x0, K, n, m, q, tol)
+    got = _run_alone(prec, st, N, x0, K, n, m, q, tol, plan=plan)
     ref = _oracle_sequence(st, N, x0, K, n, m, q)
     for j in range(K):
         assert got[j]["status"] == 0
         err = np.abs(got[j]["x"] - ref[j]).max() / np.abs(ref[j]).max()
         assert err <= bound, (j, err)
+
+
+@pytest.mark.parametrize("prec", [mhe.MHE_FP64, mhe.MHE_FP32_IR])
+def test_reuse_equals_full_refactorisation_and_reduces_little(prec):
+    """The same request sequence served with factorisation reuse and with every chunk
+    reduced again gives the same estimates (the kept reductions are exactly what a fresh
+    reduction computes); with reuse the stages reduced per request are a few chunks per
+    level, O(leaf_len * levels), against N per request without it."""
+    n, m, q, N, K = 12, 6, 6, 1000, 30
+    st = synth.plant_stream(21, n, m, q, N - 1 + K)
+    x0 = np.zeros(n)
+    plan = dict(leaf_len=8, branching=4, top_len=4)
+    s_on, s_off = {}, {}
+    on = _run_alone(prec, st, N, x0, K, n, m, q, 1e-11, plan=plan, reuse=True, stats=s_on)
+    off = _run_alone(prec, st, N, x0, K, n, m, q, 1e-11, plan=plan, reuse=False, stats=s_off)
+    for j in range(K):
+        assert on[j]["status"] == 0 and off[j]["status"] == 0
+        err = np.abs(on[j]["x"] - off[j]["x"]).max() / np.abs(off[j]["x"]).max()
+        assert err <= 1e-13, (j, err)
+    assert s_on["requests"] == s_off["requests"] == K
+    assert s_on["stages_solved"] == s_off["stages_solved"] == K * N
+    # without reuse every stage of every level is reduced in every round (level 0's N and the
+    # master stages above); with it, after the first round, a few chunks per level
+    assert s_off["stages_reduced"] >= K * N
+    first = s_off["stages_reduced"] / K
+    per = (s_on["stages_reduced"] - first) / (K - 1)
+    assert per <= 3 * (8 + 1) + 3 * 4 * 6, per
+    assert per < N / 10
 
 
 def test_result_is_the_same_alone_and_in_the_mix():
