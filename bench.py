@@ -380,6 +380,7 @@ def run_gpu(args):
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=sprec, refine_tol=refine_tol,
                        max_refine=max_refine, stream=bstreams[len(solvers)],
                        fp64_masters=args.fp64_masters and prec == 1, **plan)
+        mhe.mhe_set_double_float_residual(s.ctx, not args.fp64_residual)
         s.out = s.outputs()
         solvers.append(s)
     tune_s = time.time() - t_tune
@@ -543,6 +544,7 @@ def run_gpu(args):
                 {k: v for k, v in bplans[i].items() if k != "nx"}
             s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
                            stream=bstreams[i], fp64_masters=bool(m64), **bpl)
+            mhe.mhe_set_double_float_residual(s.ctx, not args.fp64_residual)
             s.out = s.outputs()
             ss.append(s)
         step(ss)
@@ -592,6 +594,8 @@ def run_gpu(args):
                 vs_baseline=None, dtype={2: "tf32+f32+f64", 3: "bf16+f32+f64"}.get(sprec, "f32+f64") if prec == 1 else "f64",
                 data="synthetic",
                 config=dict(desc, refine_tol=refine_tol, relres_bar=RELRES_BAR, fp64_master_levels=bool(args.fp64_masters),
+                            residual="FP64 instructions" if (args.fp64_residual or prec == 0) else
+                            "double-float (float pairs on the FP32 pipes)",
                             generation_s=round(gen_s, 1),
                             plans=plans, autotune_s=round(tune_s, 1)),
                 latency_ms=dict(p50=round(statistics.median(step_ms), 4), p99=round(p99, 4),
@@ -1109,6 +1113,8 @@ def main():
     ap.add_argument("--err-samples", type=int, default=2, help="instances per bucket checked against the oracle")
     ap.add_argument("--refine-tol", type=float, default=1e-9, help="relative KKT residual the refinement reaches")
     ap.add_argument("--fp64-masters", action="store_true", help="master levels k >= 1 in FP64 (mixed precisions)")
+    ap.add_argument("--fp64-residual", action="store_true",
+                    help="mixed precisions: the MHE-form residual with FP64 instructions (default: double-float)")
     ap.add_argument("--plan", default=None, help="leaf_len,branching,top_len used instead of the autotuner")
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: seconds of arrivals")

@@ -150,7 +150,7 @@ public:
     size_t dfp_bytes = 0;
     const float *rAh = nullptr, *rAl = nullptr, *rBh = nullptr, *rBl = nullptr;
     const float *rCh = nullptr, *rCl = nullptr, *rRh = nullptr, *rRl = nullptr;
-    bool df_resid = false;              // the MHE-form FP32 residual in double-float arithmetic
+    bool df_resid = true;               // the MHE-form FP32 residual in double-float arithmetic
     const void *mA = nullptr, *mB = nullptr, *mQ = nullptr, *mP0 = nullptr;    // the problem in the compute type
     const int* active_mask = nullptr;   // instances still refining (nullptr: all)
     void* mark_user = nullptr;          // non-null: record per-pass timing marks

@@ -190,12 +190,34 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid(ResidArgs<TR> r)
     resid_stage<NX, NW, TR, NY>(r, g, sm[team]);
 }
 
+// The double-float residual (MHE form, FP32 correction solves): the FP32 pipes do
+// about twice the instructions of the FP64 form, and the pairs need more registers;
+// four CTAs per SM give 64 registers a thread
+constexpr int kResidBlocksDF = 4;
+
+template <int NX, int NW, int NY>
+__global__ void __launch_bounds__(256, kResidBlocksDF) k_resid_df(ResidArgs<float> r)
+{
+    __shared__ unsigned long long sm[kMaxTeams][ResidSmem<NX, NW, NY>::count];
+    const int team = team_id();
+    const long long g = (long long)blockIdx.x * kMaxTeams + team;
+    if (g >= r.nstages) return;
+    if (r.any_active && *r.any_active == 0) return;
+    resid_stage<NX, NW, float, NY>(r, g, sm[team]);
+}
+
 // NY = 0: Q form; NY > 0: MHE form (C, R)
 template <int NX, int NW, typename TR, int NY = 0>
 void launch_resid(const ResidArgs<TR>& r, void* stream)
 {
     if (r.nstages <= 0) return;
     const long long grid = (r.nstages + kMaxTeams - 1) / kMaxTeams;
+    if constexpr (NY > 0 && sizeof(TR) == 4) {
+        if (r.Ahi) {
+            k_resid_df<NX, NW, NY><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
+            return;
+        }
+    }
     k_resid<NX, NW, TR, NY><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(r);
 }
 

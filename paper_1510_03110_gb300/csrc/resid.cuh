@@ -400,6 +400,19 @@ MHE_DEV void resid_mhe_df(const ResidArgs<float>& r, int b, int t, int N, unsign
     constexpr int LP = NX / SP;
     constexpr int KM = LP > NW ? LP : NW;
     float2* part = reinterpret_cast<float2*>(mx + 4);   // SP x T1 partial sums
+    // the stage's matrix pairs and right-hand side into L2 now, so that the loads of the
+    // product phases below wait on L2 rather than on HBM (one warp per stage, its phases
+    // separated by barriers: the kernel is bound by memory latency, not bandwidth)
+    prefetch_l2(Ah, (int)sizeof(float) * NX * NX);
+    prefetch_l2(Al, (int)sizeof(float) * NX * NX);
+    prefetch_l2(Bh, (int)sizeof(float) * NX * NW);
+    prefetch_l2(Bl, (int)sizeof(float) * NX * NW);
+    prefetch_l2(Ch, (int)sizeof(float) * NY * NX);
+    prefetch_l2(Cl, (int)sizeof(float) * NY * NX);
+    prefetch_l2(Rh, (int)sizeof(float) * NR * NR);
+    prefetch_l2(Rl, (int)sizeof(float) * NR * NR);
+    if (l) prefetch_l2(l, (int)sizeof(double) * NQ);
+    if (a) prefetch_l2(a, (int)sizeof(double) * NX);
     wfor(2 * NX + NW, [&](int k) {
         if (k < NX) vx[k] = df_split(xt[k]);
         else if (k < NX + NW) vw[k - NX] = df_split(wt[k - NX]);

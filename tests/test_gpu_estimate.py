@@ -284,3 +284,39 @@ def test_tensor_core_wait_that_runs_out_is_reported_and_the_context_recovers():
     for b in range(2):
         assert info["status"][b] == 0, info[b]
         assert rel_err(sols[b], ref[b]) <= 1e-8
+
+
+@pytest.mark.parametrize("n,m", [(6, 3), (12, 6), (24, 12), (20, 10), (64, 32)])
+def test_double_float_residual_equals_fp64_residual(n, m):
+    """The MHE-form residual of the mixed precisions in double-float arithmetic against the
+    same residual with FP64 instructions: on the same iterate (the first solve, no correction)
+    both report the same relres to 1e-13 absolute (the pairs carry 48 bits), and with
+    refinement both reach relres <= 1e-12 and the oracle's solution within 1e-8."""
+    import torch
+    Ns = [1, 2, 5, 40, 300]
+    insts = [synth.mhe_instance(1600 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    ref = _oracle(insts)
+    rel = {}
+    for df in (True, False):
+        s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP32_IR, max_refine=0)
+        mhe.mhe_set_double_float_residual(s.ctx, df)
+        _estimate(d, s)
+        torch.cuda.synchronize()
+        rel[df] = np.array(s.infos()["relres"])
+        s.close()
+    assert np.all(rel[True] > 0)
+    assert np.all(np.abs(rel[True] - rel[False]) <= 1e-13 + 1e-6 * rel[False]), (rel[True], rel[False])
+    # nx = 64: the serial plan (its FP32 tree plans contract by only ~0.5 per correction)
+    plan = dict(top_len=1000) if n == 64 else dict()
+    for df in (True, False):
+        s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP32_IR, refine_tol=1e-12, max_refine=30, **plan)
+        mhe.mhe_set_double_float_residual(s.ctx, df)
+        x, w, lam = _estimate(d, s)
+        torch.cuda.synchronize()
+        info = s.infos()
+        sols = split(x, w, lam, d["N"], n, m)
+        s.close()
+        for b in range(len(Ns)):
+            assert info["status"][b] == 0 and info["relres"][b] <= 1e-12, (df, b, info[b])
+            assert rel_err(sols[b], ref[b]) <= 1e-8, (df, b, rel_err(sols[b], ref[b]))
