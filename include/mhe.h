@@ -95,6 +95,12 @@ typedef struct {
                             level 0 stays in the tree's precision; their data are widened after level 0
                             and level 1's solution is narrowed for level 0's down pass.  0 = every level
                             in the tree's precision.  Ignored by MHE_FP64 */
+    int down_pass;       /* 0: Algorithm 6 as back-substitution with the stored factors (w_t = k_0 + K_0 x_t
+                            - L_{t+1} w^), the default; 1: Algorithm 6 as printed -- every subproblem
+                            solved again with Algorithms 1-3 from its parent's P^, Psi^ and x^ (a second
+                            factorisation per stage; same result).  1 is refused (MHE_E_ARG) with
+                            fp64_masters and for shapes without it compiled (nx > 32).  mhe_autotune
+                            times both and returns the faster */
 } mhe_dims;
 
 /* Matrix data of the problem, FP64, device memory, read while the stream
@@ -216,8 +222,10 @@ int mhe_shapes(int* nx_out, int* nw_out, int cap);
  * remark on batch lengths): times candidate plans (leaf_len, branching,
  * top_len; the serial plan top_len > max N included) of mhe_factor_solve on
  * the given problem -- leaf_len first, then branching, then top_len, each
- * the best of `reps` runs after a warm-up, CUDA events on `stream` -- and
- * writes dims with the fastest plan into *best (time in *best_ms).  A plan
+ * the best of `reps` runs after a warm-up, CUDA events on `stream`; then
+ * the down pass of the chosen plan, back-substitution or Algorithm 6 as
+ * printed (down_pass) -- and writes dims with the fastest into *best (time
+ * in *best_ms).  A plan
  * whose warm-up leaves any instance with a non-zero status (a failed pivot,
  * no convergence) is not a candidate.  Allocates one context per candidate in
  * turn.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_NO_CONVERGE (no plan solved

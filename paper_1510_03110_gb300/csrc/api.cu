@@ -301,6 +301,7 @@ size_t mhe_workspace_bytes(const mhe_dims* dims)
     e.prec = dims->prec;
     e.ops = &find_shape(dims->nx, dims->nw)->ops;
     e.m64 = dims->fp64_masters != 0 && dims->prec != MHE_FP64;
+    e.literal = dims->down_pass == 1;
     const int min_leaf = (dims->nx + dims->nw - 1) / dims->nw;
     const char* err = nullptr;
     const int leaf = dims->leaf_len > 0 ? dims->leaf_len : (min_leaf > 8 ? min_leaf : 8);
@@ -418,6 +419,7 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             d.leaf_len = E.leaf; d.branching = E.br; d.top_len = E.topl;
             d.refine_tol = E.tol; d.max_refine = E.max_refine;
             d.fp64_masters = E.m64 ? 1 : 0;
+            d.down_pass = E.literal ? 1 : 0;
             rc = hp.eng[e].init(d, E.ops, &kRuntime, hp.st[e]);
             if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
             hp.inited[e] = true;
@@ -591,11 +593,12 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    auto time_plan = [&](int leaf, int br, int top) -> double {
+    auto time_plan = [&](int leaf, int br, int top, int down) -> double {
         mhe_dims d = *dims;
         d.leaf_len = leaf;
         d.branching = br;
         d.top_len = top;
+        d.down_pass = down;
         mhe_ctx* c = nullptr;
         if (mhe_create(&d, stream, &c) != MHE_OK) return -1.0;
         double bestt = -1.0;
@@ -618,21 +621,26 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
         mhe_destroy(c);
         return bestt;
     };
-    int bl = min_leaf > 8 ? min_leaf : 8, bb = 4, bt = 4;
-    double bms = time_plan(bl, bb, bt);
+    const int down0 = dims->down_pass;
+    int bl = min_leaf > 8 ? min_leaf : 8, bb = 4, bt = 4, bd = down0;
+    double bms = time_plan(bl, bb, bt, down0);
     for (int leaf : {4, 8, 16, 32, 64}) {
         if (leaf < min_leaf || leaf == bl) continue;
-        double t = time_plan(leaf, bb, bt);
+        double t = time_plan(leaf, bb, bt, down0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bl = leaf; }
     }
     for (int br : {2, 8, 16}) {
-        double t = time_plan(bl, br, bt);
+        double t = time_plan(bl, br, bt, down0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bb = br; }
     }
     for (int top : {1, 16, 64, 256, maxN + 1}) {
         if (top == bt) continue;
-        double t = time_plan(bl, bb, top);
+        double t = time_plan(bl, bb, top, down0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bt = top; }
+    }
+    {   // the other down pass (a context that cannot have it is simply not a candidate)
+        double t = time_plan(bl, bb, bt, 1 - down0);
+        if (t > 0 && (bms < 0 || t < bms)) { bms = t; bd = 1 - down0; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -641,6 +649,7 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
     best->leaf_len = bl;
     best->branching = bb;
     best->top_len = bt;
+    best->down_pass = bd;
     if (best_ms) *best_ms = bms;
     if (bms < 0) return fail(MHE_E_NO_CONVERGE, "no candidate plan ran with every instance solved");
     return MHE_OK;

@@ -72,6 +72,13 @@ struct LevelArgs {
     double *zx, *zw, *zl;                  // level 0: FP64 accumulate targets (nullptr: none)
     unsigned int* dznorm;                  // with z: per instance max |added value| (float bits), or nullptr
 
+    // the literal Algorithm 6 down pass: per state of this level the true cost-to-go
+    // P_t, Psi_t its re-solve computes (written), those of the level above (read), and the
+    // re-solved feedback K_t, k_t per stage (scratch; the arrival stage's per instance)
+    T *Pd, *Psid;
+    const T *Pd_up, *Psid_up;
+    T *Kalt, *kalt, *Kalt0, *kalt0;
+
     const int* active;     // per instance; nullptr = all active
     const int* any_active; // non-null: the pass is skipped when *any_active == 0 (no instance refining)
     int* status;           // per instance error code

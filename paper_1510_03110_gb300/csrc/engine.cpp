@@ -75,6 +75,14 @@ size_t Engine::layout(char* base)
             if (pivot) c.take(B_.piv, ns * (size_t)(n + 1));
             else B_.piv = nullptr;
         }
+        if (literal) {
+            c.take_raw(B_.Pd, nx_ * n2 * tk);
+            c.take_raw(B_.Psid, nx_ * n * tk);
+            c.take_raw(B_.Kalt, ns * mk * n * tk);
+            c.take_raw(B_.kalt, ns * mk * tk);
+        } else {
+            B_.Pd = B_.Psid = B_.Kalt = B_.kalt = nullptr;
+        }
         if (m64 && k == 1) {   // the FP32 side of the level-0 / level-1 hand-off
             c.take_raw(B_.Ah32, ns * n2 * sizeof(float));
             c.take_raw(B_.Bh32, ns * n2 * sizeof(float));
@@ -96,6 +104,10 @@ size_t Engine::layout(char* base)
     c.take_raw(Kst0, (size_t)batch * n2 * ts);
     c.take_raw(kst0, (size_t)batch * n * ts);
     c.take_raw(Lst0, (size_t)batch * n2 * ts);
+    if (literal) {
+        c.take_raw(Kalt0, (size_t)batch * n2 * ts);
+        c.take_raw(kalt0, (size_t)batch * n * ts);
+    }
     c.take(in_off, (size_t)batch);
     c.take(cmp_off, (size_t)batch);
     c.take(w_off, (size_t)batch);
@@ -147,6 +159,12 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     m64 = d.fp64_masters != 0 && prec != MHE_FP64;
     if (m64 && (!ops->reduce64 || !rt->widen)) {
         err = "FP64 master levels need the shape's FP64 passes";
+        return MHE_E_ARG;
+    }
+    if (d.down_pass != 0 && d.down_pass != 1) { err = "down_pass must be 0 or 1"; return MHE_E_ARG; }
+    literal = d.down_pass == 1;
+    if (literal && (m64 || !ops->down64lit || !ops->down32lit)) {
+        err = "the literal Algorithm 6 down pass is not compiled for this shape or precision option";
         return MHE_E_ARG;
     }
     // FP64: the tree's backward error (~1e-13 on hard instances) can leave a forward
@@ -364,6 +382,18 @@ LevelArgs<T> Engine::args(int k) const
     a.where = where;
     a.piv_rel = (sizeof(T) == 8) ? 1e-14 : 1e-7;
     a.store_P = 1;
+    a.Pd = static_cast<T*>(L.Pd);
+    a.Psid = static_cast<T*>(L.Psid);
+    a.Kalt = static_cast<T*>(L.Kalt);
+    a.kalt = static_cast<T*>(L.kalt);
+    if (k + 1 < (int)lv.size()) {
+        a.Pd_up = static_cast<const T*>(lv[k + 1].Pd);
+        a.Psid_up = static_cast<const T*>(lv[k + 1].Psid);
+    }
+    if (k == 0) {
+        a.Kalt0 = static_cast<T*>(Kalt0);
+        a.kalt0 = static_cast<T*>(kalt0);
+    }
     a.gws = sizeof(T) == 8 ? static_cast<T*>(gws) : nullptr;
     a.gws_teams = ops ? ops->gws_teams : 0;
     a.piv_up = (pivot && k + 1 < (int)lv.size()) ? lv[k + 1].piv : nullptr;
@@ -503,7 +533,8 @@ void Engine::down_level(int k, const T* l, const T* a, const T* l0, const T* a0,
     }
     mark(PH_DOWN, k, 1);
     launches += g.nchunks > 0;
-    launch<T>(ops->down64, ops->down32, g, k >= 1, stream);
+    if (literal) launch<T>(ops->down64lit, ops->down32lit, g, k >= 1, stream);
+    else launch<T>(ops->down64, ops->down32, g, k >= 1, stream);
     mark(PH_DOWN, k, 0);
 }
 

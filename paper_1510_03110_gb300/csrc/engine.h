@@ -26,6 +26,9 @@ struct ShapeOps {
     void (*reduce32bf)(const LevelArgs<float>&, int upper, void* stream);   // the same with BF16 operands (MHE_BF16_IR)
     void (*rhs32)(const LevelArgs<float>&, int upper, void* stream);
     void (*down32)(const LevelArgs<float>&, int upper, void* stream);
+    // the literal Algorithm 6 down pass (every subproblem solved again), or nullptr
+    void (*down64lit)(const LevelArgs<double>&, int upper, void* stream);
+    void (*down32lit)(const LevelArgs<float>&, int upper, void* stream);
     void (*resid64)(const ResidArgs<double>&, void* stream);
     void (*resid32)(const ResidArgs<float>&, void* stream);
     void (*knorm)(const KnormArgs&, void* stream);
@@ -83,6 +86,8 @@ struct LevelBuf {   // every array of the level's compute type (FP64 at k >= 1 w
     void *QN = nullptr, *lN = nullptr;   // terminal of this level (k >= 1)
     void *xd = nullptr, *wd = nullptr, *ld = nullptr;
     int* piv = nullptr;   // k >= 1, rank-revealing plans: pivot order and rank of each master stage
+    // the literal Algorithm 6 down pass: P_t, Psi_t per state; the re-solved K_t, k_t per stage
+    void *Pd = nullptr, *Psid = nullptr, *Kalt = nullptr, *kalt = nullptr;
     // level 1 with FP64 master levels: the FP32 master data level 0 writes (widened
     // to the arrays above) and the FP32 copy of this level's solution level 0 reads
     void *Ah32 = nullptr, *Bh32 = nullptr, *ah32 = nullptr, *Qxh32 = nullptr, *lxh32 = nullptr;
@@ -115,6 +120,8 @@ public:
     int prec = MHE_FP64;
     bool m64 = false;                   // FP32 / TF32 / BF16 tree whose master levels k >= 1 run in FP64
     bool pivot = false;                 // rank-revealing master stages (leaf_len * nw < nx)
+    bool literal = false;               // the down pass as Algorithm 6 prints it (every subproblem solved again)
+    void *Kalt0 = nullptr, *kalt0 = nullptr;   // literal down pass: the arrival stage's re-solved K, k
     double tol = 1e-10;
     int max_refine = 0;
 

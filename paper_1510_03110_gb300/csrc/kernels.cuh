@@ -15,7 +15,8 @@ namespace mhe {
 
 // OP_REDUCE_TC / OP_REDUCE_BF: the reduction with the stage products on the
 // tensor cores, TF32 or BF16 operands
-enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2, OP_REDUCE_TC = 3, OP_REDUCE_BF = 4 };
+// OP_DOWN_LIT: Algorithm 6 as printed (every subproblem solved again), the reduction's workspace
+enum { OP_REDUCE = 0, OP_RHS = 1, OP_DOWN = 2, OP_REDUCE_TC = 3, OP_REDUCE_BF = 4, OP_DOWN_LIT = 5 };
 
 // floats past the workspace of a tensor-core reduction: a 32 KB operand tile,
 // the mbarrier and the TMEM address
@@ -25,9 +26,10 @@ constexpr int kTcExtra = 8192 + 4;
 template <typename T, int NX, int OP>
 constexpr int op_count()
 {
-    return OP == OP_REDUCE ? Ws<T, NX>::count
-                           : (OP == OP_RHS ? Ws<T, NX>::count_rhs
-                                           : (OP == OP_DOWN ? Ws<T, NX>::count_vec : Ws<T, NX>::count + kTcExtra));   // both tensor-core reductions
+    return (OP == OP_REDUCE || OP == OP_DOWN_LIT)
+               ? Ws<T, NX>::count
+               : (OP == OP_RHS ? Ws<T, NX>::count_rhs
+                               : (OP == OP_DOWN ? Ws<T, NX>::count_vec : Ws<T, NX>::count + kTcExtra));   // both tensor-core reductions
 }
 
 // CTAs of the residual kernel per SM its register budget is sized for
@@ -74,7 +76,7 @@ constexpr int level_min_blocks()
                     : (sizeof(T) == 4
                            ? (NX <= 8 ? 4
                                       : (NX <= 12 ? 3 : ((OP == OP_REDUCE || OP >= OP_REDUCE_TC) ? 1 : (OP == OP_DOWN ? 3 : 2))))
-                           : (NX <= 12 ? 2 : (OP == OP_REDUCE ? 1 : 2)));
+                           : (NX <= 12 ? 2 : ((OP == OP_REDUCE || OP == OP_DOWN_LIT) ? 1 : 2)));
 }
 
 // shapes whose stage products run on the tensor cores: a team of four warps,
@@ -142,6 +144,8 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
         reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     } else if (OP == OP_RHS) {
         rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
+    } else if (OP == OP_DOWN_LIT) {
+        down_chunk_literal<T, NX, NW, UPPER != 0>(a, ci, sm);
     } else {
         down_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     }
@@ -353,6 +357,14 @@ ShapeEntry make_shape()
     }
     e.ops.rhs32 = &launch_level<float, NX, NW, OP_RHS>;
     e.ops.down32 = &launch_level<float, NX, NW, OP_DOWN>;
+    // the literal Algorithm 6 down pass, for the shapes whose reduction workspace fits an SM
+    if constexpr (level_fits<double, NX, OP_REDUCE>() && NX <= 32) {
+        e.ops.down64lit = &launch_level<double, NX, NW, OP_DOWN_LIT>;
+        e.ops.down32lit = &launch_level<float, NX, NW, OP_DOWN_LIT>;
+    } else {
+        e.ops.down64lit = nullptr;
+        e.ops.down32lit = nullptr;
+    }
     e.ops.resid64 = &launch_resid<NX, NW, double>;
     e.ops.resid32 = &launch_resid<NX, NW, float>;
     e.ops.knorm = &launch_knorm<NX, NW>;

@@ -1452,4 +1452,158 @@ MHE_DEV void down_chunk(const LevelArgs<T>& a, int ci, T* smem)
     });
 }
 
+// ---- Algorithm 6 as printed: every subproblem solved again --------------------
+//
+// Level by level from the top, subproblem i of level k is solved with
+// Algorithms 1-3 from its parent's data: the backward recursion (Algorithms 1-2,
+// no V) over its stages from the cost-to-go of the level above at its end state,
+// P^_{i+1} and Psi^_{i+1} (the last subproblem from the level's own terminal),
+// then the forward recursion (Algorithm 3) from x^_i: w_t = K_t x_t + k_t,
+// x_{t+1} = A_t x_t + B_t w_t + a_t, lambda_t = P_t x_t - Psi_t.  The re-solve
+// writes P_t, Psi_t at every state of the subproblem for the level below.  The
+// result equals the back-substitution of down_chunk; its cost is a second
+// factorisation per stage.  The feedback K_t, k_t goes to scratch arrays: the
+// reduction's stored factors stay as they are for later right-hand sides.
+template <typename T, int NX, int NW, bool UPPER>
+MHE_DEV void down_chunk_literal(const LevelArgs<T>& a, int ci, T* smem)
+{
+    constexpr int ld = Ws<T, NX>::ld;
+    const ChunkDesc cd = a.chunks[ci];
+    const int b = cd.inst;
+    if (a.active && !a.active[b]) return;
+    const bool last = (cd.flags & CH_LAST) != 0;
+    const bool top = (cd.flags & CH_TOP) != 0;
+    Ws<T, NX> s;
+    s.carve(smem);
+    const LevelInst li = a.li[b];
+    const int t1 = cd.t0 + cd.len;
+    // the terminal of the re-solve: the parent's cost-to-go at the chunk's end state, or
+    // the level's own terminal (Q_{x,N} = 0, l_N at level 0; the level's QN, lN above)
+    const T* QN = UPPER ? a.QNk + (long long)b * NX * NX : nullptr;
+    const T* lN = UPPER ? (a.lNk ? a.lNk + (long long)b * NX : nullptr) : (a.lN ? a.lN + (long long)b * NX : nullptr);
+    const T* Pt = last ? QN : a.Pd_up + (cd.px + 1) * NX * NX;
+    const T* Pst = last ? nullptr : a.Psid_up + (cd.px + 1) * NX;
+    // the end state's P, Psi are written here only for the level's last chunk; the end
+    // state of any other chunk is the next chunk's first, which writes them
+    T* Pd = a.Pd + (li.gx + t1) * NX * NX;
+    T* Psd = a.Psid + (li.gx + t1) * NX;
+    wfor(NX * NX, [&](int idx) {
+        const int i = idx % NX, j = idx / NX;
+        const T v = Pt ? Pt[idx] : (T)0;
+        s.P[i + j * ld] = v;
+        if (last) Pd[idx] = v;
+        if (idx < NX) {
+            const T ps = last ? (lN ? -lN[idx] : (T)0) : Pst[idx];
+            s.Psi[idx] = ps;
+            if (last) Psd[idx] = ps;
+        }
+    });
+    int bad_t = -1;
+    // backward: Algorithms 1-2 over the chunk; P_{t+1} of each stage to Pd at state t + 1
+    for (int tt = cd.len - 1; tt >= 0; --tt) {
+        const int t = cd.t0 + tt;
+        const long long g = cd.g0 + tt;
+        T* Po = a.Pd + (li.gx + t + 1) * NX * NX;
+        if (tt < cd.len - 1)
+            wfor(NX, [&](int i) { a.Psid[(li.gx + t + 1) * NX + i] = s.Psi[i]; });
+        bool bad;
+        if (UPPER) {
+            bad = reduce_step<T, NX, NX, KIND_UPPER>(s, Addr<T, NX, NW>::upper(a, g), tt < cd.len - 1 ? Po : nullptr,
+                                                     nullptr, a.Kalt + g * NX * NX, a.kalt + g * NX, nullptr, false,
+                                                     a.piv_rel);
+        } else if (t == 0) {
+            bad = reduce_step<T, NX, NX, KIND_ARRIVAL>(s, Addr<T, NX, NW>::arrival(a, b),
+                                                       tt < cd.len - 1 ? Po : nullptr, nullptr,
+                                                       a.Kalt0 + (long long)b * NX * NX, a.kalt0 + (long long)b * NX,
+                                                       nullptr, false, a.piv_rel);
+        } else {
+            bad = reduce_step<T, NX, NW, KIND_LEAF>(s, Addr<T, NX, NW>::leaf(a, b, t), tt < cd.len - 1 ? Po : nullptr,
+                                                    nullptr, a.Kalt + g * NW * NX, a.kalt + g * NW, nullptr, false,
+                                                    a.piv_rel);
+        }
+        if (bad && bad_t < 0) bad_t = t;
+    }
+    // P_0, Psi_0 of the chunk at its first state
+    wfor(NX * NX, [&](int idx) {
+        a.Pd[(li.gx + cd.t0) * NX * NX + idx] = s.P[idx % NX + (idx / NX) * ld];
+        if (idx < NX) a.Psid[(li.gx + cd.t0) * NX + idx] = s.Psi[idx];
+    });
+    if (bad_t >= 0) wone([&](int) { record_error(a.status, a.where, b, -3, a.level, ci, bad_t); });
+    // forward: Algorithm 3 from x^_i (the top: x~0)
+    auto xo = [&](int t) -> T* { return a.xd + (li.gx + t) * NX; };
+    auto lo = [&](int t) -> T* { return a.ld + (li.gx + t) * NX; };
+    auto wo = [&](int t) -> T* {
+        if (UPPER) return a.wd + (li.gs + t) * NX;
+        return a.wd + a.w_off[b] + (t == 0 ? 0 : NX + (long long)(t - 1) * NW);
+    };
+    auto zxo = [&](int t) -> double* { return a.zx ? a.zx + (li.gx + t) * NX : nullptr; };
+    auto zlo = [&](int t) -> double* { return a.zl ? a.zl + (li.gx + t) * NX : nullptr; };
+    auto zwo = [&](int t) -> double* {
+        return a.zw ? a.zw + a.w_off[b] + (t == 0 ? 0 : NX + (long long)(t - 1) * NW) : nullptr;
+    };
+    wfor(NX, [&](int i) { s.e[i] = top ? a.x0[(long long)b * NX + i] : a.xd_up[cd.px * NX + i]; });
+    float dzm = 0.f;
+    // lambda_t = P_t x_t - Psi_t (Algorithm 3), x_t and lambda_t written, z accumulated at level 0
+    auto state_out = [&](int t) {
+        const T* P = a.Pd + (li.gx + t) * NX * NX;
+        const T* Ps = a.Psid + (li.gx + t) * NX;
+        wfor(NX, [&](int i) {
+            T acc = -Ps[i];
+#pragma unroll
+            for (int j = 0; j < NX; ++j) acc += P[i + j * NX] * s.e[j];
+            xo(t)[i] = s.e[i];
+            lo(t)[i] = acc;
+            if (a.zx) {
+                zxo(t)[i] += f64_of(s.e[i]);
+                zlo(t)[i] += f64_of(acc);
+                dzm = fmaxf(dzm, fmaxf(absf_of(s.e[i]), absf_of(acc)));
+            }
+        });
+    };
+    for (int tt = 0; tt < cd.len; ++tt) {
+        const int t = cd.t0 + tt;
+        const long long g = cd.g0 + tt;
+        state_out(t);
+        T* w = wo(t);
+        double* zw = zwo(t);
+        auto fwd = [&](const StageRef<T>& st, const T* K, const T* k, auto kind_tag, auto mt_tag) {
+            constexpr int KIND = decltype(kind_tag)::value, MT = decltype(mt_tag)::value;
+            using X = Acc<T, KIND, NX, MT>;
+            wfor(MT, [&](int j) {
+                T acc = k[j];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) acc += K[j + i * MT] * s.e[i];
+                s.tmp[j] = acc;
+                w[j] = acc;
+                if (zw) {
+                    zw[j] += f64_of(acc);
+                    dzm = fmaxf(dzm, absf_of(acc));
+                }
+            });
+            wfor(NX, [&](int i) {
+                T acc = X::a(st, i);
+#pragma unroll
+                for (int j = 0; j < NX; ++j) acc += X::A(st, i, j) * s.e[j];
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc += X::B(st, i, j) * s.tmp[j];
+                s.u[i] = acc;
+            });
+            wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
+        };
+        if (UPPER)
+            fwd(Addr<T, NX, NW>::upper(a, g), a.Kalt + g * NX * NX, a.kalt + g * NX,
+                std::integral_constant<int, KIND_UPPER>(), std::integral_constant<int, NX>());
+        else if (t == 0)
+            fwd(Addr<T, NX, NW>::arrival(a, b), a.Kalt0 + (long long)b * NX * NX, a.kalt0 + (long long)b * NX,
+                std::integral_constant<int, KIND_ARRIVAL>(), std::integral_constant<int, NX>());
+        else
+            fwd(Addr<T, NX, NW>::leaf(a, b, t), a.Kalt + g * NW * NX, a.kalt + g * NW,
+                std::integral_constant<int, KIND_LEAF>(), std::integral_constant<int, NW>());
+    }
+    if (last) state_out(t1);   // the level's final state (the next chunk writes the others' end states)
+    if (a.zx && a.dznorm) wlanes([&](int) {
+        if (dzm > 0.f) atomicMax(a.dznorm + b, __float_as_uint(dzm));
+    });
+}
+
 }  // namespace mhe

@@ -32,7 +32,7 @@ c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 class mhe_dims(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nw", c_int), ("batch", c_int), ("N", ctypes.POINTER(c_int)),
                 ("prec", c_int), ("leaf_len", c_int), ("branching", c_int), ("top_len", c_int),
-                ("refine_tol", c_double), ("max_refine", c_int), ("fp64_masters", c_int)]
+                ("refine_tol", c_double), ("max_refine", c_int), ("fp64_masters", c_int), ("down_pass", c_int)]
 
 
 class mhe_matrices(ctypes.Structure):
@@ -176,11 +176,11 @@ def shapes():
 
 
 def make_dims(nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0, refine_tol=0.0,
-              max_refine=-1, fp64_masters=False):
+              max_refine=-1, fp64_masters=False, down_pass=0):
     N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).reshape(-1))
     d = mhe_dims(int(nx), int(nw), int(N.size), N.ctypes.data_as(ctypes.POINTER(c_int)), int(prec),
                  int(leaf_len), int(branching), int(top_len), float(refine_tol), int(max_refine),
-                 int(bool(fp64_masters)))
+                 int(bool(fp64_masters)), int(down_pass))
     return d, N
 
 
@@ -310,7 +310,8 @@ def mhe_autotune(dims, A, B, Q, P0inv, l, a, x0, reps=2, stream=None):
     ms = c_double()
     _check(lib().mhe_autotune(ctypes.byref(dims), ctypes.byref(m), ctypes.byref(r), _stream(stream), int(reps),
                               ctypes.byref(best), ctypes.byref(ms)), "mhe_autotune")
-    return dict(leaf_len=best.leaf_len, branching=best.branching, top_len=best.top_len, ms=ms.value)
+    return dict(leaf_len=best.leaf_len, branching=best.branching, top_len=best.top_len, down_pass=best.down_pass,
+                ms=ms.value)
 
 
 def mhe_launch_count(ctx):
@@ -399,13 +400,13 @@ class Solver:
     """
 
     def __init__(self, nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0,
-                 refine_tol=0.0, max_refine=-1, stream=None, fp64_masters=False):
+                 refine_tol=0.0, max_refine=-1, stream=None, fp64_masters=False, down_pass=0):
         import torch
         self.nx, self.nw = int(nx), int(nw)
         self.N = np.asarray(N, dtype=np.int64).reshape(-1)
         self.batch = int(self.N.size)
         self.dims, self._N32 = make_dims(nx, nw, self.N, prec, leaf_len, branching, top_len,
-                                         refine_tol, max_refine, fp64_masters)
+                                         refine_tol, max_refine, fp64_masters, down_pass)
         self.stream = stream
         self.ctx = mhe_create(self.dims, stream)
         self.X = int(np.sum(self.N + 1))

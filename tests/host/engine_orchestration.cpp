@@ -42,6 +42,7 @@ struct Rec {
     const void *rhs_off = nullptr, *active = nullptr, *any_active = nullptr, *chunks = nullptr, *li = nullptr;
     const void *A = nullptr, *Q = nullptr;
     const void *dst = nullptr, *src = nullptr;   // convert / widen
+    const void *Pd = nullptr, *Psid = nullptr, *Pd_up = nullptr, *Psid_up = nullptr, *Kalt = nullptr;
     int mode = -1;
     int ts = 0;   // element size of a level pass's compute type
 };
@@ -119,6 +120,7 @@ void rec_level(const char* op, const LevelArgs<T>& g, int upper)
     r.l = g.l; r.a = g.a; r.x0 = g.x0; r.l0 = g.l0; r.a0 = g.a0; r.lN = g.lN;
     r.rhs_off = g.rhs_off; r.active = g.active; r.any_active = g.any_active; r.chunks = g.chunks; r.li = g.li;
     r.A = g.A; r.Q = g.Q;
+    r.Pd = g.Pd; r.Psid = g.Psid; r.Pd_up = g.Pd_up; r.Psid_up = g.Psid_up; r.Kalt = g.Kalt;
     r.ts = (int)sizeof(T);
     g_log.push_back(r);
 }
@@ -138,6 +140,8 @@ void red32(const LevelArgs<float>& g, int u, void*) { rec_level("reduce", g, u);
 void red32tc(const LevelArgs<float>& g, int u, void*) { rec_level("reduce_tc", g, u); }
 void rhs32(const LevelArgs<float>& g, int u, void*) { rec_level("rhs", g, u); }
 void down32(const LevelArgs<float>& g, int u, void*) { rec_level("down", g, u); }
+void down64lit(const LevelArgs<double>& g, int u, void*) { rec_level("down_lit", g, u); }
+void down32lit(const LevelArgs<float>& g, int u, void*) { rec_level("down_lit", g, u); }
 void resid64(const ResidArgs<double>& a, void*) { rec_resid(a); }
 void resid32(const ResidArgs<float>& a, void*) { rec_resid(a); }
 void resid_mhe32(const ResidArgs<float>& a, void*)
@@ -175,6 +179,7 @@ ShapeOps make_ops(int nx, int nw, bool tc)
     o.reduce64 = red64; o.rhs64 = rhs64; o.down64 = down64;
     o.reduce32 = red32; o.reduce32tc = tc ? red32tc : nullptr; o.reduce32bf = nullptr;
     o.rhs32 = rhs32; o.down32 = down32;
+    o.down64lit = down64lit; o.down32lit = down32lit;
     o.resid64 = resid64; o.resid32 = resid32; o.resid_mhe32 = resid_mhe32; o.knorm = knorm;
     o.prep32 = prep32; o.assemble = assemble;
     return o;
@@ -272,7 +277,8 @@ long long counted_launches()
 {
     long long c = 0;
     for (const Rec& r : g_log) {
-        if (r.op == "reduce" || r.op == "reduce_tc" || r.op == "rhs" || r.op == "down") c += r.nchunks > 0;
+        if (r.op == "reduce" || r.op == "reduce_tc" || r.op == "rhs" || r.op == "down" || r.op == "down_lit")
+            c += r.nchunks > 0;
         else c += 1;   // knorm, convert, widen, resid, finalize, prep, assemble
     }
     return c;
@@ -622,6 +628,48 @@ void scenario_fp64_masters()
     e.release();
 }
 
+// Algorithm 6 as printed: every down pass runs the literal variant, top level first;
+// level k reads the cost-to-go (P, Psi per state) that level k+1's re-solve wrote,
+// and the re-solved feedback goes to scratch, not to the reduction's stored factors
+void scenario_literal_down()
+{
+    Problem p(4, 2, {7, 40, 100, 2});
+    ShapeOps ops = make_ops(4, 2, false);
+    Engine e;
+    mhe_dims d = dims_of(p, MHE_FP32_IR, 4, 2, 2, 1);
+    d.down_pass = 1;
+    CHECK(e.init(d, &ops, &kFakeRuntime, nullptr) == MHE_OK && e.literal, "init: %s", e.err.c_str());
+    g_log.clear();
+    g_converge_after = 1;
+    mhe_matrices mt = p.mats();
+    mhe_rhs rh = p.rhs();
+    CHECK(e.factor(mt, nullptr, nullptr, nullptr, nullptr) == MHE_OK, "factor");
+    const size_t f_end = g_log.size();
+    CHECK(e.solve(&rh, p.x.data(), p.w.data(), p.lam.data(), p.info.data(), false) == MHE_OK, "solve");
+    CHECK(of("down", f_end).empty(), "no back-substitution pass in literal mode");
+    const std::vector<Rec> dl = of("down_lit", f_end, find_from("resid", f_end));
+    const int L = (int)e.plan.levels.size();
+    CHECK((int)dl.size() == L, "one literal down pass per level");
+    for (int i = 0; i < L; ++i) {
+        const int k = L - 1 - i;
+        CHECK(dl[i].level == k, "literal down pass %d at level %d", i, dl[i].level);
+        CHECK(dl[i].Pd && dl[i].Psid && dl[i].Kalt, "level %d: cost-to-go and scratch arrays", k);
+        if (k + 1 < L) {
+            CHECK(dl[i].Pd_up == dl[i - 1].Pd && dl[i].Psid_up == dl[i - 1].Psid,
+                  "level %d reads the cost-to-go level %d wrote", k, k + 1);
+            CHECK(dl[i].xd_up == dl[i - 1].xd, "level %d reads the solution level %d wrote", k, k + 1);
+        }
+    }
+    const std::vector<Rec> red = of("reduce");
+    for (const Rec& r : dl)
+        for (const Rec& q : red) CHECK(r.Kalt != q.A, "scratch apart from the problem data");
+    CHECK(e.launches == counted_launches(), "launch counter");
+    e.release();
+    Engine e2;
+    d.fp64_masters = 1;
+    CHECK(e2.init(d, &ops, &kFakeRuntime, nullptr) == MHE_E_ARG, "literal with FP64 master levels is refused");
+}
+
 }  // namespace
 
 int main()
@@ -633,6 +681,7 @@ int main()
     if (!g_fail) scenario_estimate();
     if (!g_fail) scenario_replan();
     if (!g_fail) scenario_fp64_masters();
+    if (!g_fail) scenario_literal_down();
     if (g_fail) return 1;
     printf("OK\n");
     return 0;
