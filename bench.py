@@ -49,9 +49,12 @@ def pass_model(ph, lvl, n, m, q, prec, N, serial=False, df=False):
       reduce  Algorithm 4 per stage (flops_leaf_stage; the arrival stage has width n)
       resid   FP64 FMAs of the KKT rows per stage: dynamics A x + B w, costate
               A^T lam + B^T lam, and Q z in the MHE factors (FP32_IR: C x, V u, S^T w,
-              C^T e, W w, S u) or with the assembled Q (FP64)
-      prep    bytes: FP64 A, B, C, R, a, y~, w~ read; FP32 A, B, Q, a, l and FP64 l written
-              (FP64 mode: C, R, y~, w~ read, FP64 Q, l written)
+              C^T e, W w, S u) or with the assembled Q (FP64); the double-float form (default
+              in the mixed precisions) by its bytes instead: the stage matrices as pairs,
+              l, a and the iterate in FP64, the FP32 correction rows written
+      prep    bytes: FP64 A, B, C, R, a, y~, w~ read; FP32 A, B, Q, a, l and FP64 l written, and with
+              the double-float residual the float pairs of A, B, C, R (FP64 mode: C, R, y~, w~ read,
+              FP64 Q, l written)
       rhs     bytes: stored P, chol(G), K and FP32 A, B, a, l read per stage
       down    bytes: stored K, k, L and FP32 A, B, Q, a, l read; x, w, lam written (FP32)
               and accumulated into FP64 z"""
@@ -77,6 +80,8 @@ def pass_model(ph, lvl, n, m, q, prec, N, serial=False, df=False):
         if prec == 1:
             b = 8 * (n * n + n * m + q * n + (m + q) ** 2 + n + q + m) + 4 * (n * n + n * m + (n + m) ** 2 + 2 * n + m) \
                 + 8 * (n + m)
+            if df:   # the residual's float pairs: lo of A, B; hi and lo of C, R
+                b += 4 * (n * n + n * m + 2 * q * n + 2 * (m + q) ** 2)
         else:
             b = 8 * (q * n + (m + q) ** 2 + q + m) + 8 * ((n + m) ** 2 + n + m)
         return ("hbm", b * stages / 1e9, "GB/s")
@@ -865,7 +870,7 @@ def serve_once(args, ws, rate, plan, reuse=True):
         nxt[e] += 1
         packed.append(mhe.pack_stage(st["A"][k], st["B"][k], st["C"][k], st["R"][k], st["a"][k], st["yt"][k],
                                      st["wt"][k]))
-    srv = mhe.Server(args.serve_bytes, prec=mhe.MHE_FP32_IR, refine_tol=args.serve_tol)
+    srv = mhe.Server(args.serve_bytes, prec=mhe.MHE_FP32_IR, refine_tol=args.serve_tol, max_refine=args.serve_refine)
     srv.set_plan(**plan)
     srv.set_reuse(reuse)
     ids = []
@@ -889,22 +894,25 @@ def serve_once(args, ws, rate, plan, reuse=True):
             pass
         tickets.append(srv.submit(ids[int(who[i])], packed[i]))
     t_sub_end = time.perf_counter()
-    lat, bad, relres = [], 0, 0.0
+    lat, statuses, relres, iters = [], {}, 0.0, 0
     for i, tk in enumerate(tickets):
         r = srv.wait(tk, int(nxs[int(who[i])]), timeout=600)
         lat.append(r["latency"])
-        bad += r["status"] != 0
+        statuses[int(r["status"])] = statuses.get(int(r["status"]), 0) + 1
         relres = max(relres, r["relres"])
-    t_end = time.perf_counter()
+        iters = max(iters, r["iters"])
     s1 = srv.stats()
     srv.close()
     lat = np.array(lat)
-    span = max(t_end - tstart, 1e-9)
+    # the span from the first submission to the last completion (submission + the latency the server
+    # measured), not to the end of this thread's polling of the results
+    span = max(float(np.max(t_arr[:count] + lat)), 1e-9)
     req = max(s1["requests"] - s0["requests"], 1)
     return dict(offered_per_s=round(count / max(t_arr[-1], 1e-9), 1), submitted_per_s=round(count / (t_sub_end - tstart), 1),
                 solves_per_s=round(count / span, 1), p50_ms=round(1e3 * float(np.median(lat)), 3),
                 p99_ms=round(1e3 * float(np.quantile(lat, 0.99)), 3), mean_ms=round(1e3 * float(lat.mean()), 3),
-                requests=count, failed=int(bad), relres_max=relres, submit_s=round(t_sub_end - tstart, 3),
+                requests=count, failed=int(count - statuses.get(0, 0)), statuses=statuses, relres_max=relres,
+                refine_iters_max=iters, submit_s=round(t_sub_end - tstart, 3),
                 span_s=round(span, 3), rounds=s1["rounds"] - s0["rounds"],
                 stages_reduced_per_request=round((s1["stages_reduced"] - s0["stages_reduced"]) / req, 1),
                 stages_per_request=round((s1["stages_solved"] - s0["stages_solved"]) / req, 1))
@@ -912,6 +920,8 @@ def serve_once(args, ws, rate, plan, reuse=True):
 
 SERVE_PLANS = [("tree_reuse", dict(leaf_len=0, branching=0, top_len=0), True),
                ("serial", dict(leaf_len=0, branching=0, top_len=1 << 20), True)]
+# the tree without reuse (every chunk of every round reduced again), for the sweep
+SERVE_FULL = ("tree_no_reuse", dict(leaf_len=0, branching=0, top_len=0), False)
 
 
 def run_serve(args):
@@ -941,9 +951,10 @@ def run_serve_sweep(args):
     torch.cuda.set_device(0)
     rates = [float(v) for v in args.rates.split(",")]
     ws = serve_setup(args, rates, args.duration)
-    res = {name: [] for name, _, _ in SERVE_PLANS}
+    plans = SERVE_PLANS + [SERVE_FULL]
+    res = {name: [] for name, _, _ in plans}
     for rate in rates:
-        for name, plan, reuse in SERVE_PLANS:
+        for name, plan, reuse in plans:
             r = serve_once(args, ws, rate, plan, reuse)
             r["rate"] = rate
             res[name].append(r)
@@ -1133,6 +1144,7 @@ def main():
     ap.add_argument("--rates", default="", help="serving: comma-separated offered rates for a saturation sweep")
     ap.add_argument("--p99-bound-ms", type=float, default=50.0, help="serving sweep: p99 a sustained rate keeps")
     ap.add_argument("--serve-tol", type=float, default=1e-9, help="serving: relres the refinement reaches")
+    ap.add_argument("--serve-refine", type=int, default=8, help="serving: corrections allowed per request")
     ap.add_argument("--serve-bytes", type=int, default=96 << 30, help="serving: device-memory budget")
     ap.add_argument("--serve-duration", type=float, default=10.0,
                     help="batch workload: seconds of a serving run appended to the line (0: none)")
