@@ -1144,7 +1144,7 @@ def main():
     ap.add_argument("--rates", default="", help="serving: comma-separated offered rates for a saturation sweep")
     ap.add_argument("--p99-bound-ms", type=float, default=50.0, help="serving sweep: p99 a sustained rate keeps")
     ap.add_argument("--serve-tol", type=float, default=1e-9, help="serving: relres the refinement reaches")
-    ap.add_argument("--serve-refine", type=int, default=8, help="serving: corrections allowed per request")
+    ap.add_argument("--serve-refine", type=int, default=16, help="serving: corrections allowed per request")
     ap.add_argument("--serve-bytes", type=int, default=96 << 30, help="serving: device-memory budget")
     ap.add_argument("--serve-duration", type=float, default=10.0,
                     help="batch workload: seconds of a serving run appended to the line (0: none)")

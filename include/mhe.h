@@ -221,7 +221,9 @@ int mhe_shapes(int* nx_out, int* nw_out, int cap);
 /* Autotuner for the batch lengths the paper leaves to the user (Section VI,
  * remark on batch lengths): times candidate plans (leaf_len, branching,
  * top_len; the serial plan top_len > max N included) of mhe_factor_solve on
- * the given problem -- leaf_len first, then branching, then top_len, each
+ * the given problem -- leaf_len (4 .. 256) first, then branching (2 .. 16),
+ * then top_len (1 .. 1024 and above every N: instances no longer than top_len
+ * are solved as one chunk, longer ones by the tree), each
  * the best of `reps` runs after a warm-up, CUDA events on `stream`; then
  * the down pass of the chosen plan, back-substitution or Algorithm 6 as
  * printed (down_pass) -- and writes dims with the fastest into *best (time

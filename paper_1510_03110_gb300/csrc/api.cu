@@ -624,7 +624,7 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
     const int down0 = dims->down_pass;
     int bl = min_leaf > 8 ? min_leaf : 8, bb = 4, bt = 4, bd = down0;
     double bms = time_plan(bl, bb, bt, down0);
-    for (int leaf : {4, 8, 16, 32, 64}) {
+    for (int leaf : {4, 8, 16, 32, 64, 128, 256}) {
         if (leaf < min_leaf || leaf == bl) continue;
         double t = time_plan(leaf, bb, bt, down0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bl = leaf; }
@@ -633,7 +633,8 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
         double t = time_plan(bl, br, bt, down0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bb = br; }
     }
-    for (int top : {1, 16, 64, 256, maxN + 1}) {
+    for (int top : {1, 16, 64, 256, 512, 1024, maxN + 1}) {
+        if (top > maxN + 1) continue;
         if (top == bt) continue;
         double t = time_plan(bl, bb, top, down0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bt = top; }
