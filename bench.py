@@ -737,15 +737,41 @@ def run_long_sweep(args):
         best[0]["rel_err_vs_oracle"] = e
         del d, Q, l
         torch.cuda.empty_cache()
+    # the Kalman filter + RTS smoother on the GPU (the comparison of Section VI) on an instance of the same
+    # sizes with uncorrelated noises (S = 0, which the smoother needs), one warp walking the horizon
+    rts_rows = []
+    zs = synth.mhe_instance(2, n, m, q, max(Ns), s_zero=True)
+    for N in Ns:
+        p = dict(zs, N=N, **{k: zs[k][:N - 1] for k in ("A", "B", "C", "R", "a", "yt", "wt")})
+        bk = dict(n=n, m=m, q=q, N=np.array([N]), pool={k: p[k] for k in ("A", "B", "C", "R", "a", "yt", "wt")},
+                  idx=np.arange(N - 1), x0=p["x0"][None, :])
+        d = to_device(bk)
+        x = torch.empty((N + 1) * n, dtype=torch.float64, device="cuda")
+        w = torch.empty(n + (N - 1) * m, dtype=torch.float64, device="cuda")
+        work = torch.empty(int(mhe.lib().mhe_rts_workspace_bytes(n, m, q, 1, np.array([N], np.int32).ctypes.data_as(
+            __import__("ctypes").POINTER(__import__("ctypes").c_int)))), dtype=torch.uint8, device="cuda")
+        call = lambda: mhe.mhe_rts_smooth(n, m, q, [N], d["A"], d["B"], d["C"], d["R"], d["a"], d["yt"], d["wt"],  # noqa: E731
+                                          d["x0"], d["P0inv"], x, w, work=work)
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rts_rows.append(dict(N=N, rts_ms=round(e0.elapsed_time(e1), 4)))
+        del d, x, w, work
     out = dict(workload="long-horizon depth sweep, nx=20, nw=ny=10, FP64", seed=1, generation_s=round(gen_s, 1),
-               fp64_peak_tflops=pk["fp64_tflops"], rows=rows)
+               fp64_peak_tflops=pk["fp64_tflops"], rows=rows, rts=rts_rows)
     summary = []
     for N in Ns:
         r = [x for x in rows if x["N"] == N]
         tree = min((x for x in r if x["plan"] != "serial"), key=lambda x: x["ms"])
         ser = [x for x in r if x["plan"] == "serial"][0]
+        rt = [x for x in rts_rows if x["N"] == N][0]["rts_ms"]
         summary.append(dict(N=N, best_tree_ms=tree["ms"], best_plan=tree["plan"], levels=tree["levels"],
-                            serial_ms=ser["ms"], speedup=round(ser["ms"] / tree["ms"], 2),
+                            serial_ms=ser["ms"], speedup=round(ser["ms"] / tree["ms"], 2), rts_ms=rt,
+                            speedup_vs_rts=round(rt / tree["ms"], 2),
                             rel_err_vs_oracle=tree.get("rel_err_vs_oracle")))
     out["summary"] = summary
     return out

@@ -361,6 +361,51 @@ int mhe_debug_set_tc_wait_limit(int tries);
  * leaves the precision of the products open).  Errors: MHE_E_ARG. */
 int mhe_set_double_float_residual(mhe_ctx* ctx, int on);
 
+/* MHE with inequality constraints (Section II; the paper notes that an
+ * interior-point method spends its time in Newton steps of the UFTOC form the
+ * library solves).  The constraint sets are not in the paper; this outer loop
+ * takes box bounds on the process noise, w_lo <= w_t <= w_hi for the measured
+ * stages t = 1 .. N_b - 1 (w_0 and the states free), and runs a primal barrier
+ * method: each Newton step is one mhe_factor_solve on ctx of the problem with
+ * the barrier's Hessian added to Q_w and its gradient to l_w; the step keeps
+ * w at least 0.5% of its distance inside each bound, and a full short step
+ * divides the barrier parameter by 10, per instance.  Options: bounds [batch]
+ * [nw] (device, FP64, w_lo < w_hi); mu0 (0: 1), mu_final (0: 1e-9), max_newton
+ * (0: 200).  Outputs as mhe_solve (x, w the solution; lam and info those of the
+ * last Newton step's problem); newton_steps (host, may be NULL) the steps
+ * taken.  Allocates its work buffers per call; synchronises the context's
+ * stream once per Newton step.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_CUDA,
+ * MHE_E_NO_CONVERGE (max_newton reached), and those of mhe_factor_solve. */
+typedef struct {
+    const double* w_lo;   /* [batch][nw] lower bounds of w_t (device) */
+    const double* w_hi;   /* [batch][nw] upper bounds of w_t (device) */
+    double mu0;           /* initial barrier parameter (0: 1) */
+    double mu_final;      /* barrier parameter at which an instance stops (0: 1e-9) */
+    int max_newton;       /* Newton steps at most (0: 200) */
+} mhe_ip_opts;
+int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs, const mhe_ip_opts* ip, double* x,
+                 double* w, double* lam, mhe_info* info, int* newton_steps);
+
+/* The Kalman filter + Rauch-Tung-Striebel smoother for the MHE model, the
+ * classical method Section VI compares the parallel Riccati recursion with.
+ * For uncorrelated noises (the S block of every R_t zero; not checked) the
+ * smoothed means are the x and w of the Newton step of Eq. org_mhe (Section
+ * II).  One warp per instance runs the forward filter over its N-1 measured
+ * stages and the backward smoother, FP64, every inverse through a Cholesky
+ * factor.  Inputs: the mhe_problem fields (device, FP64, same layouts) for
+ * the compiled shapes (2,1,1), (4,2,2), (6,3,3), (12,6,6), (20,10,10),
+ * (24,12,12); N host array [batch], every N_b >= 2.  Outputs (device): x
+ * [sum (N_b+1)][nx] and w (nx + (N_b-1) nw per instance) as for mhe_solve;
+ * status [batch] (device, may be NULL) MHE_OK or MHE_E_NOT_PD.  work: device
+ * memory of at least mhe_rts_workspace_bytes (the filter's means and
+ * covariances of every step).  Stream-ordered; the host array N is read
+ * during the call.  Errors: MHE_E_ARG, MHE_E_CUDA. */
+size_t mhe_rts_workspace_bytes(int nx, int nw, int ny, int batch, const int* N);
+int mhe_rts_smooth(int nx, int nw, int ny, int batch, const int* N, const double* A, const double* B,
+                   const double* C, const double* R, const double* a, const double* yt, const double* wt,
+                   const double* x0, const double* P0inv, double* x, double* w, void* work, size_t work_bytes,
+                   int* status, void* stream);
+
 /* Kernels launched so far by this context (all passes, residuals included),
  * and by mhe_assemble in this process. */
 long long mhe_launch_count(mhe_ctx* ctx);

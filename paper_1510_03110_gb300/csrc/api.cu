@@ -269,6 +269,8 @@ int check_dims(const mhe_dims* d)
 
 namespace mhe {
 void set_last_error(const std::string& msg) { g_err = msg; }
+const Plan* ctx_plan(mhe_ctx* ctx) { return &ctx->eng.plan; }
+void* ctx_stream(mhe_ctx* ctx) { return ctx->eng.stream; }
 const ShapeEntry* shape_entry(int nx, int nw) { return find_shape(nx, nw); }
 const Runtime* cuda_runtime() { return &kRuntime; }
 }  // namespace mhe

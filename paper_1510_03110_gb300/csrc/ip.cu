@@ -1,0 +1,337 @@
+// ip.cu -- an interior-point outer loop for MHE with bounded process noise.
+//
+// Section II states MHE with inequality constraints and notes that an
+// interior-point method spends its time in Newton steps, each the solution of a
+// UFTOC problem of the form the library solves.  The paper does not give the
+// constraint sets; this loop takes box bounds lo <= w_t <= hi on the process
+// noise of every measured stage (t = 1 .. N-1; w_0 and the states are free) and
+// runs a primal barrier method:
+//   minimise  f(z) - mu sum log(w - lo) - mu sum log(hi - w)  subject to the dynamics,
+// one Newton step at a time.  The Newton step's quadratic model is the UFTOC
+// problem with Q_w + D and l_w + b - D w at every stage, where D = mu/(w-lo)^2 +
+// mu/(hi-w)^2 (diagonal) and b = -mu/(w-lo) + mu/(hi-w); its solution z' (through
+// mhe_factor_solve, the tree) is dynamically feasible, and so is every step
+// z + alpha (z' - z) from a feasible z.  alpha is the largest step up to 1 that
+// keeps w at least 0.5 % of the distance from each bound (fraction to the
+// boundary); when a step is full and short, mu shrinks by 10.  Every instance
+// has its own mu and stops on its own; the loop ends when all have mu below
+// the target and a short step, or after max_newton steps.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mhe.h"
+#include "engine.h"
+#include "f32conv.h"
+
+namespace mhe {
+void set_last_error(const std::string& msg);
+const Plan* ctx_plan(mhe_ctx* ctx);      // api.cu
+void* ctx_stream(mhe_ctx* ctx);
+}  // namespace mhe
+
+namespace {
+
+struct IpArgs {
+    int n, m, batch;
+    const long long *in_off, *xo, *wo;   // per instance: caller stage, state and input offsets
+    const int* N;
+    const double *A, *B, *Q, *l, *a, *x0, *lo, *hi;
+    double *Qb, *lb;                     // the Newton model's Q and l (caller stage layout)
+    double *x, *w;                       // the iterate
+    const double *xn, *wn;               // the model's solution
+    double* mu;                          // per instance
+    unsigned long long* amin;            // per instance: min step, as float bits of a positive value
+    unsigned long long* dmax;            // per instance: max |z' - z|, bits of a non-negative double
+    unsigned long long* zmax;            // per instance: max |z|
+    int* done;                           // per instance: converged
+    int* any;                            // some instance still iterating
+    double mu_final;
+};
+
+__device__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// the start: w_t = the middle of the box (t >= 1), w_0 = 0, x by the dynamics from x~0
+__global__ void k_ip_init(IpArgs r, double mu0)
+{
+    const int b = blockIdx.x;
+    if (b >= r.batch || threadIdx.x != 0) return;
+    const int n = r.n, m = r.m, N = r.N[b];
+    double* x = r.x + r.xo[b] * n;
+    double* w = r.w + r.wo[b];
+    const double* lo = r.lo + (long long)b * m;
+    const double* hi = r.hi + (long long)b * m;
+    for (int i = 0; i < n; ++i) {
+        x[i] = r.x0[(long long)b * n + i];
+        w[i] = 0.0;
+        x[n + i] = x[i];   // x_1 = x_0 + w_0
+    }
+    for (int t = 1; t < N; ++t) {
+        const long long s = r.in_off[b] + t - 1;
+        const double* A = r.A + s * n * n;
+        const double* B = r.B + s * n * m;
+        const double* a = r.a + s * n;
+        double* wt = w + n + (long long)(t - 1) * m;
+        for (int j = 0; j < m; ++j) wt[j] = 0.5 * (lo[j] + hi[j]);
+        const double* xt = x + (long long)t * n;
+        double* xn = x + (long long)(t + 1) * n;
+        for (int i = 0; i < n; ++i) {
+            double acc = a[i];
+            for (int j = 0; j < n; ++j) acc += A[i + j * n] * xt[j];
+            for (int j = 0; j < m; ++j) acc += B[i + j * n] * wt[j];
+            xn[i] = acc;
+        }
+    }
+    r.mu[b] = mu0;
+    r.done[b] = 0;
+}
+
+// the Newton model of every stage t >= 1: Q + D on the w block, l + b - D w
+__global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
+{
+    const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= S) return;
+    const int b = stage_inst[s], t = stage_t[s];
+    const int n = r.n, m = r.m, nq = n + m;
+    const double* Q = r.Q + s * nq * nq;
+    double* Qb = r.Qb + s * nq * nq;
+    const double* l = r.l + s * nq;
+    double* lb = r.lb + s * nq;
+    const double* w = r.w + r.wo[b] + n + (long long)(t - 1) * m;
+    const double mu = r.mu[b];
+    for (int idx = threadIdx.x; idx < nq * nq; idx += blockDim.x) {
+        const int i = idx % nq, j = idx / nq;
+        double v = Q[idx];
+        if (i == j && i >= n) {
+            const int q = i - n;
+            const double dl = w[q] - r.lo[(long long)b * m + q], dh = r.hi[(long long)b * m + q] - w[q];
+            v += mu / (dl * dl) + mu / (dh * dh);
+        }
+        Qb[idx] = v;
+    }
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+        double v = l[i];
+        if (i >= n) {
+            const int q = i - n;
+            const double dl = w[q] - r.lo[(long long)b * m + q], dh = r.hi[(long long)b * m + q] - w[q];
+            const double D = mu / (dl * dl) + mu / (dh * dh);
+            v += -mu / dl + mu / dh - D * w[q];
+        }
+        lb[i] = v;
+    }
+}
+
+// per instance: the largest step keeping every bounded w 0.5 % inside its box, and max |z' - z|, max |z|
+__global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
+{
+    const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= S) return;
+    const int b = stage_inst[s], t = stage_t[s];
+    if (r.done[b]) return;
+    const int n = r.n, m = r.m;
+    const long long woff = r.wo[b] + n + (long long)(t - 1) * m;
+    float amin = 1.0f;
+    double dmax = 0.0, zmax = 0.0;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const double wv = r.w[woff + q], d = r.wn[woff + q] - wv;
+        const double lo = r.lo[(long long)b * m + q], hi = r.hi[(long long)b * m + q];
+        double amax = 1.0;
+        if (d < 0) amax = 0.995 * (lo - wv) / d;
+        else if (d > 0) amax = 0.995 * (hi - wv) / d;
+        amin = fminf(amin, (float)fmin(amax, 1.0));
+        dmax = fmax(dmax, fabs(d));
+        zmax = fmax(zmax, fabs(wv));
+    }
+    const double* xt = r.x + (r.xo[b] + t) * n;
+    const double* xnt = r.xn + (r.xo[b] + t) * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        dmax = fmax(dmax, fabs(xnt[i] - xt[i]));
+        zmax = fmax(zmax, fabs(xt[i]));
+    }
+    if (amin < 1.0f) atomicMin(r.amin + b, (unsigned long long)__float_as_uint(fmaxf(amin, 0.f)));
+    if (dmax > 0.0) atomicMax(r.dmax + b, dbits(dmax));
+    if (zmax > 0.0) atomicMax(r.zmax + b, dbits(zmax));
+}
+
+// z += alpha (z' - z) for the instances still iterating (every state, every input)
+__global__ void k_ip_step(IpArgs r, long long X, long long Wn, const int* x_inst, const int* w_inst)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < X * r.n) {
+        const int b = x_inst[i / r.n];
+        if (!r.done[b]) {
+            const double al = (double)__uint_as_float((unsigned)r.amin[b]);
+            r.x[i] += al * (r.xn[i] - r.x[i]);
+        }
+    }
+    if (i < Wn) {
+        const int b = w_inst[i];
+        if (!r.done[b]) {
+            const double al = (double)__uint_as_float((unsigned)r.amin[b]);
+            r.w[i] += al * (r.wn[i] - r.w[i]);
+        }
+    }
+}
+
+// the per-instance reductions of a step: no step limit yet (1), no change, no size
+__global__ void k_ip_clear(IpArgs r)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= r.batch) return;
+    r.amin[b] = (unsigned long long)__float_as_uint(1.0f);
+    r.dmax[b] = 0ULL;
+    r.zmax[b] = 0ULL;
+}
+
+// per instance: a full, short step ends the current barrier subproblem (mu /= 10); convergence
+__global__ void k_ip_update(IpArgs r, double step_tol)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= r.batch) return;
+    if (!r.done[b]) {
+        const double al = (double)__uint_as_float((unsigned)r.amin[b]);
+        const double d = __longlong_as_double((long long)r.dmax[b]);
+        const double z = __longlong_as_double((long long)r.zmax[b]);
+        if (al >= 1.0 && d <= step_tol * (1.0 + z)) {
+            if (r.mu[b] <= r.mu_final) r.done[b] = 1;
+            else r.mu[b] = fmax(0.1 * r.mu[b], 0.5 * r.mu_final);
+        }
+    }
+    if (!r.done[b]) atomicOr(r.any, 1);
+    r.amin[b] = (unsigned long long)__float_as_uint(1.0f);
+    r.dmax[b] = 0ULL;
+    r.zmax[b] = 0ULL;
+}
+
+template <typename T>
+T* dev_alloc(size_t count, std::vector<void*>& pool)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, (count ? count : 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    pool.push_back(p);
+    return static_cast<T*>(p);
+}
+
+}  // namespace
+
+extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs, const mhe_ip_opts* ip,
+                            double* x, double* w, double* lam, mhe_info* info, int* newton_steps)
+{
+    if (!ctx || !mats || !rhs || !ip || !x || !w || !lam) {
+        mhe::set_last_error("NULL argument to mhe_ip_solve");
+        return MHE_E_ARG;
+    }
+    if (!ip->w_lo || !ip->w_hi) {
+        mhe::set_last_error("the bounds w_lo, w_hi are required");
+        return MHE_E_ARG;
+    }
+    const mhe::Plan& P = *mhe::ctx_plan(ctx);
+    cudaStream_t st = (cudaStream_t)mhe::ctx_stream(ctx);
+    const int n = P.n, m = P.m, batch = P.batch;
+    const long long S = P.S_in, X = P.X_total, Wn = P.W_total;
+    if (S > 0 && (!mats->A || !mats->B || !mats->Q || !rhs->l || !rhs->a)) {
+        mhe::set_last_error("incomplete problem");
+        return MHE_E_ARG;
+    }
+    const double mu0 = ip->mu0 > 0 ? ip->mu0 : 1.0;
+    const double mu_final = ip->mu_final > 0 ? ip->mu_final : 1e-9;
+    const int max_newton = ip->max_newton > 0 ? ip->max_newton : 200;
+    // host-side maps: stage -> (instance, t), state -> instance, input -> instance
+    std::vector<int> s_inst(S), s_t(S), x_inst(X), w_inst(Wn);
+    std::vector<long long> xo(batch), wo(batch);
+    {
+        long long s = 0, xi = 0, wi = 0;
+        for (int b = 0; b < batch; ++b) {
+            xo[b] = xi;
+            wo[b] = wi;
+            for (int t = 1; t < P.N[b]; ++t, ++s) { s_inst[s] = b; s_t[s] = t; }
+            for (int k = 0; k <= P.N[b]; ++k) x_inst[xi++] = b;
+            const long long nw_b = n + (long long)(P.N[b] - 1) * m;
+            for (long long k = 0; k < nw_b; ++k) w_inst[wi++] = b;
+        }
+    }
+    std::vector<void*> pool;
+    int* d_sinst = dev_alloc<int>(S, pool);
+    int* d_st = dev_alloc<int>(S, pool);
+    int* d_xinst = dev_alloc<int>(X, pool);
+    int* d_winst = dev_alloc<int>(Wn, pool);
+    long long* d_off = dev_alloc<long long>(3 * (size_t)batch, pool);
+    int* d_N = dev_alloc<int>(batch, pool);
+    double* Qb = dev_alloc<double>((size_t)S * (n + m) * (n + m), pool);
+    double* lb = dev_alloc<double>((size_t)S * (n + m), pool);
+    double* xn = dev_alloc<double>((size_t)X * n, pool);
+    double* wn = dev_alloc<double>((size_t)Wn, pool);
+    double* mu = dev_alloc<double>(batch, pool);
+    unsigned long long* red = dev_alloc<unsigned long long>(3 * (size_t)batch, pool);
+    int* done = dev_alloc<int>(batch, pool);
+    int* any = dev_alloc<int>(1, pool);
+    int* h_any = nullptr;
+    auto cleanup = [&]() {
+        for (void* p : pool) cudaFree(p);
+        if (h_any) cudaFreeHost(h_any);
+    };
+    if (!d_sinst || !d_st || !d_xinst || !d_winst || !d_off || !d_N || !Qb || !lb || !xn || !wn || !mu || !red ||
+        !done || !any || cudaHostAlloc(&h_any, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        mhe::set_last_error("device allocation for the interior-point loop failed");
+        return MHE_E_NOMEM;
+    }
+    std::vector<long long> off(3 * (size_t)batch);
+    for (int b = 0; b < batch; ++b) {
+        off[b] = P.in_off[b];
+        off[batch + b] = xo[b];
+        off[2 * batch + b] = wo[b];
+    }
+    cudaMemcpyAsync(d_sinst, s_inst.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_st, s_t.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_xinst, x_inst.data(), sizeof(int) * X, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_winst, w_inst.data(), sizeof(int) * Wn, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * 3 * batch, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_N, P.N.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, st);
+    IpArgs r;
+    memset(&r, 0, sizeof(r));
+    r.n = n; r.m = m; r.batch = batch;
+    r.in_off = d_off; r.xo = d_off + batch; r.wo = d_off + 2 * batch; r.N = d_N;
+    r.A = mats->A; r.B = mats->B; r.Q = mats->Q; r.l = rhs->l; r.a = rhs->a; r.x0 = rhs->x0;
+    r.lo = ip->w_lo; r.hi = ip->w_hi;
+    r.Qb = Qb; r.lb = lb; r.x = x; r.w = w; r.xn = xn; r.wn = wn;
+    r.mu = mu; r.amin = red; r.dmax = red + batch; r.zmax = red + 2 * batch;
+    r.done = done; r.any = any; r.mu_final = mu_final;
+    k_ip_init<<<batch, 32, 0, st>>>(r, mu0);
+    k_ip_clear<<<(batch + 127) / 128, 128, 0, st>>>(r);
+    const dim3 fb(32, 8);
+    const unsigned fgrid = (unsigned)((S + 7) / 8);
+    int steps = 0;
+    int rc = MHE_OK;
+    mhe_matrices mq = *mats;
+    mq.Q = Qb;
+    mhe_rhs rq = *rhs;
+    rq.l = lb;
+    for (; steps < max_newton; ++steps) {
+        if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
+        rc = mhe_factor_solve(ctx, &mq, &rq, xn, wn, lam, info);
+        if (rc != MHE_OK) break;
+        if (S > 0) k_ip_measure<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
+        const long long tot = X * n > Wn ? X * n : Wn;
+        k_ip_step<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, X, Wn, d_xinst, d_winst);
+        cudaMemsetAsync(any, 0, sizeof(int), st);
+        k_ip_update<<<(batch + 127) / 128, 128, 0, st>>>(r, 1e-6);
+        cudaMemcpyAsync(h_any, any, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MHE_E_CUDA; break; }
+        if (*h_any == 0) { ++steps; break; }
+    }
+    if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
+    if (rc == MHE_OK && *h_any != 0) {
+        mhe::set_last_error("the interior-point loop reached max_newton before every instance converged");
+        rc = MHE_E_NO_CONVERGE;
+    }
+    if (newton_steps) *newton_steps = steps;
+    cleanup();
+    return rc;
+}

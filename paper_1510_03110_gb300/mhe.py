@@ -48,6 +48,11 @@ class mhe_problem(ctypes.Structure):
                 ("a", c_void_p), ("yt", c_void_p), ("wt", c_void_p), ("x0", c_void_p), ("P0inv", c_void_p)]
 
 
+class mhe_ip_opts(ctypes.Structure):
+    _fields_ = [("w_lo", c_void_p), ("w_hi", c_void_p), ("mu0", c_double), ("mu_final", c_double),
+                ("max_newton", c_int)]
+
+
 class mhe_info(ctypes.Structure):
     _fields_ = [("status", c_int), ("level", c_int), ("chunk", c_int), ("stage", c_int),
                 ("refine_iters", c_int), ("pad", c_int), ("relres", c_double), ("est_relerr", c_double)]
@@ -95,6 +100,14 @@ def _declare(L):
     L.mhe_launch_count.restype = c_ll
     L.mhe_assemble_count.argtypes = []
     L.mhe_assemble_count.restype = c_ll
+    L.mhe_ip_solve.argtypes = [c_void_p, P(mhe_matrices), P(mhe_rhs), P(mhe_ip_opts), c_void_p, c_void_p, c_void_p,
+                               c_void_p, P(c_int)]
+    L.mhe_ip_solve.restype = c_int
+    L.mhe_rts_workspace_bytes.argtypes = [c_int, c_int, c_int, c_int, P(c_int)]
+    L.mhe_rts_workspace_bytes.restype = ctypes.c_size_t
+    L.mhe_rts_smooth.argtypes = [c_int, c_int, c_int, c_int, P(c_int)] + [c_void_p] * 12 + [ctypes.c_size_t,
+                                                                                            c_void_p, c_void_p]
+    L.mhe_rts_smooth.restype = c_int
     L.mhe_set_double_float_residual.argtypes = [c_void_p, c_int]
     L.mhe_set_double_float_residual.restype = c_int
     L.mhe_debug_set_tc_wait_limit.argtypes = [c_int]
@@ -322,6 +335,36 @@ def mhe_assemble_count():
     return int(lib().mhe_assemble_count())
 
 
+def mhe_rts_smooth(nx, nw, ny, N, A, B, C, R, a, yt, wt, x0, P0inv, x, w, work=None, status=None, stream=None):
+    """Kalman filter + RTS smoother on the GPU (S = 0 models): the x, w of the MHE Newton step.
+    Every array is checked against the batch layout; work (uint8 CUDA tensor) is allocated when None."""
+    import torch
+    N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).reshape(-1))
+    batch = int(N.size)
+    S = int(np.sum(N - 1))
+    X = int(np.sum(N + 1))
+    W = int(np.sum(nx + (N - 1) * nw))
+    for t, count, name in ((A, S * nx * nx, "A"), (B, S * nx * nw, "B"), (C, S * ny * nx, "C"),
+                           (R, S * (nw + ny) ** 2, "R"), (a, S * nx, "a"), (yt, S * ny, "yt"), (wt, S * nw, "wt"),
+                           (x0, batch * nx, "x0"), (P0inv, batch * nx * nx, "P0inv"), (x, X * nx, "x"), (w, W, "w")):
+        _need(t, count, name)
+    nbytes = int(lib().mhe_rts_workspace_bytes(int(nx), int(nw), int(ny), batch,
+                                               N.ctypes.data_as(ctypes.POINTER(c_int))))
+    if nbytes == 0:
+        raise SizeError("no RTS smoother for this shape, or a horizon below 2")
+    if work is None:
+        work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    if not (isinstance(work, torch.Tensor) and work.is_cuda and work.numel() * work.element_size() >= nbytes):
+        raise TypeError(f"work must be a CUDA tensor of at least {nbytes} bytes")
+    sp = _iptr(status) if status is not None else None
+    if status is not None:
+        _need(status, batch, "status")
+    return _check(lib().mhe_rts_smooth(int(nx), int(nw), int(ny), batch, N.ctypes.data_as(ctypes.POINTER(c_int)),
+                                       _ptr(A), _ptr(B), _ptr(C), _ptr(R), _ptr(a), _ptr(yt), _ptr(wt), _ptr(x0),
+                                       _ptr(P0inv), _ptr(x), _ptr(w), ctypes.c_void_p(work.data_ptr()),
+                                       ctypes.c_size_t(nbytes), sp, _stream(stream)), "mhe_rts_smooth")
+
+
 def mhe_set_double_float_residual(ctx, on=True):
     """The mixed-precision MHE-form residual in double-float (True, default) or FP64 arithmetic."""
     return _check(lib().mhe_set_double_float_residual(ctx, int(bool(on))), "mhe_set_double_float_residual")
@@ -446,6 +489,22 @@ class Solver:
         self._sizes(ny, A=A, B=B, C=C, R=R, a=a, yt=yt, wt=wt, x0=x0, P0inv=P0inv, x=x, w=w, lam=lam)
         mhe_estimate(self.ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, self.info)
         return x, w, lam
+
+    def ip_solve(self, A, B, Q, P0inv, l, a, x0, w_lo, w_hi, mu0=0.0, mu_final=0.0, max_newton=0, out=None):
+        """mhe_ip_solve: bounds w_lo <= w_t <= w_hi ([batch][nw] each) by a barrier interior-point loop whose
+        Newton steps are this context's factor + solve.  Returns (x, w, lam, newton steps)."""
+        x, w, lam = out if out is not None else self.outputs()
+        self._sizes(A=A, B=B, Q=Q, P0inv=P0inv, l=l, a=a, x0=x0, x=x, w=w, lam=lam)
+        _need(w_lo, self.batch * self.nw, "w_lo")
+        _need(w_hi, self.batch * self.nw, "w_hi")
+        m = mhe_matrices(_ptr(A), _ptr(B), _ptr(Q), _ptr(P0inv))
+        r = mhe_rhs(_ptr(l), _ptr(a), _ptr(x0))
+        o = mhe_ip_opts(_ptr(w_lo), _ptr(w_hi), float(mu0), float(mu_final), int(max_newton))
+        steps = c_int()
+        _check(lib().mhe_ip_solve(self.ctx, ctypes.byref(m), ctypes.byref(r), ctypes.byref(o), _ptr(x), _ptr(w),
+                                  _ptr(lam), ctypes.c_void_p(self.info.data_ptr()), ctypes.byref(steps)),
+               "mhe_ip_solve")
+        return x, w, lam, steps.value
 
     def infos(self):
         return info_array(self.info)
