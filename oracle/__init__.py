@@ -12,6 +12,8 @@ Modules
   dense  dense KKT assembly + LAPACK LU solve (the Newton step by definition).
   rts    Kalman filter + Rauch-Tung-Striebel smoother (textbook), used to pin
          the MHE -> UFTOC transform.
+  boxqp  MHE with box-bounded process noise (Section II's constrained MHE),
+         solved exactly by a primal active-set method on the dense KKT system.
   tree   the paper's parallel scheme executed serially: Algorithm 4 (chunk
          reduction), the master problem (Section IV-C), Algorithms 5 and 6.
 """
