@@ -386,7 +386,8 @@ def run_gpu(args):
                                  d["P0inv"][:k].contiguous(), lp, d["a"][:S].contiguous(),
                                  d["x0"][:k * n].contiguous())
             del Qp, lp
-            plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"])
+            plan = dict(leaf_len=r["leaf_len"], branching=r["branching"], top_len=r["top_len"],
+                        down_pass=r["down_pass"], team=r["team"])
         plans.append(dict(nx=bk["n"], **plan))
         s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=sprec, refine_tol=refine_tol,
                        max_refine=max_refine, stream=bstreams[len(solvers)],
@@ -550,7 +551,10 @@ def run_gpu(args):
         ([("tree_short_leaves_fp64_masters", sprec, max_refine, short_plans, 1),
           ("tree_short_leaves_fp32_masters", sprec, max_refine, short_plans, 0)] if (prec == 1 and xl) else []) + \
         ([("fp32_simt_products_same_plan", 1, max_refine, plans, 0)] if sprec in (2, 3) else [])
-    for name, bprec, mref, bplans, m64 in arms:
+    # the headline's own plans with each context's launch sequence replayed as a CUDA graph
+    arms = [a + (False,) for a in arms] + \
+        ([] if args.no_baseline else [("same_plans_cuda_graph", sprec, max_refine, plans, int(args.fp64_masters), True)])
+    for name, bprec, mref, bplans, m64, graph in arms:
         ss = []
         for i, bk in enumerate(buckets):
             bpl = dict(top_len=int(np.max(bk["N"])) + 1) if bplans is None else \
@@ -558,9 +562,12 @@ def run_gpu(args):
             s = mhe.Solver(bk["n"], bk["m"], bk["N"], prec=bprec, refine_tol=refine_tol, max_refine=mref,
                            stream=bstreams[i], fp64_masters=bool(m64), **bpl)
             mhe.mhe_set_double_float_residual(s.ctx, not args.fp64_residual)
+            if graph:
+                s.set_graph(True)
             s.out = s.outputs()
             ss.append(s)
-        step(ss)
+        for _ in range(2 if graph else 1):   # graphs: one eager call, then the capture
+            step(ss)
         torch.cuda.synchronize()
         k = max(1, min(args.steps, args.baseline_steps))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -577,7 +584,8 @@ def run_gpu(args):
                           refine_iters_max=int(np.max(binf["refine_iters"])),
                           precision={0: "FP64", 1: "FP32+IR", 2: "TF32+IR", 3: "BF16+IR"}[bprec] +
                           (" + FP64 master levels" if m64 else ""),
-                          plan="serial" if bplans is None else {k: v for k, v in bplans[0].items() if k != "nx"})
+                          plan="serial" if bplans is None else {k: v for k, v in bplans[0].items() if k != "nx"},
+                          cuda_graph=graph)
         for s in ss:
             s.close()
 
@@ -801,18 +809,20 @@ def run_small(args):
     K = max(args.steps, 50)
     out = {}
 
-    def lat(fn):
-        for _ in range(max(args.warmup, 3)):
-            fn()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(K):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
+    def lat(fn, st=None):
+        st = st if st is not None else stream
+        with torch.cuda.stream(st):
+            for _ in range(max(args.warmup, 3)):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(K):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
         ts = np.array(ts)
         return dict(p50_ms=round(float(np.median(ts)), 4), p99_ms=round(float(np.quantile(ts, 0.99)), 4),
                     mean_ms=round(float(ts.mean()), 4))
@@ -825,10 +835,16 @@ def run_small(args):
             e = max(e, float(np.abs(a - b).max() / np.abs(b).max()))
         return e
 
-    for name, plan in [("tree", dict(leaf_len=4, branching=2, top_len=2)), ("serial", dict(top_len=N + 1))]:
-        s = mhe.Solver(n, m, [N], prec=mhe.MHE_FP64, max_refine=0, **plan)
+    tree_plan, serial_plan = dict(leaf_len=4, branching=2, top_len=2), dict(top_len=N + 1)
+    # the "_graph" arms replay the launch sequence as a CUDA graph (mhe_set_graph) on a stream of their own
+    for name, plan, graph in [("tree", tree_plan, False), ("serial", serial_plan, False),
+                              ("tree_graph", tree_plan, True), ("serial_graph", serial_plan, True)]:
+        gst = torch.cuda.Stream() if graph else None
+        s = mhe.Solver(n, m, [N], prec=mhe.MHE_FP64, max_refine=0, stream=gst, **plan)
+        if graph:
+            s.set_graph(True)
         o = s.outputs()
-        r = lat(lambda: s.factor_solve(d["A"], d["B"], Q, d["P0inv"], l, d["a"], d["x0"], out=o))
+        r = lat(lambda: s.factor_solve(d["A"], d["B"], Q, d["P0inv"], l, d["a"], d["x0"], out=o), gst)
         r["rel_err_vs_oracle"] = err(*o)
         r["relres"] = float(s.infos()["relres"][0])
         r["levels"] = len(mhe.mhe_plan_info(s.ctx))

@@ -101,6 +101,10 @@ typedef struct {
                             factorisation per stage; same result).  1 is refused (MHE_E_ARG) with
                             fp64_masters and for shapes without it compiled (nx > 32).  mhe_autotune
                             times both and returns the faster */
+    int team;            /* lanes that work on one subproblem together (the kernels' team width): 0 =
+                            the shape's default; otherwise one of the widths compiled for the shape
+                            (mhe_shape_teams), else MHE_E_ARG.  mhe_autotune times every compiled
+                            width and returns the fastest */
 } mhe_dims;
 
 /* Matrix data of the problem, FP64, device memory, read while the stream
@@ -218,6 +222,11 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
  * nx_out / nw_out and returns the number available. */
 int mhe_shapes(int* nx_out, int* nw_out, int cap);
 
+/* Team widths compiled for the shape (nx, nw), the default first: writes up to
+ * cap of them into teams and returns the number available (0: shape not
+ * compiled). */
+int mhe_shape_teams(int nx, int nw, int* teams, int cap);
+
 /* Autotuner for the batch lengths the paper leaves to the user (Section VI,
  * remark on batch lengths): times candidate plans (leaf_len, branching,
  * top_len; the serial plan top_len > max N included) of mhe_factor_solve on
@@ -226,8 +235,8 @@ int mhe_shapes(int* nx_out, int* nw_out, int cap);
  * are solved as one chunk, longer ones by the tree), each
  * the best of `reps` runs after a warm-up, CUDA events on `stream`; then
  * the down pass of the chosen plan, back-substitution or Algorithm 6 as
- * printed (down_pass) -- and writes dims with the fastest into *best (time
- * in *best_ms).  A plan
+ * printed (down_pass), then every team width compiled for the shape (team)
+ * -- and writes dims with the fastest into *best (time in *best_ms).  A plan
  * whose warm-up leaves any instance with a non-zero status (a failed pivot,
  * no convergence) is not a candidate.  Allocates one context per candidate in
  * turn.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_NO_CONVERGE (no plan solved
@@ -361,6 +370,22 @@ int mhe_debug_set_tc_wait_limit(int tries);
  * leaves the precision of the products open).  Errors: MHE_E_ARG. */
 int mhe_set_double_float_residual(mhe_ctx* ctx, int on);
 
+/* CUDA-graph replay (no paper counterpart).  With graphs on, mhe_factor,
+ * mhe_solve, mhe_factor_solve and mhe_estimate keep, per entry point, the
+ * launch sequence of their last argument pointers: the first call with a set
+ * of pointers runs as usual (and makes every allocation the sequence needs),
+ * the second captures its launches on the context's stream into a CUDA graph
+ * and launches it, later calls with the same pointers launch the graph.  The
+ * sequence never depends on the data, so a replay reads the current contents of
+ * the same buffers.  Other pointers start over.  Calls stay eager on the legacy
+ * default stream (it cannot be captured), with timing enabled, while the caller
+ * is capturing the stream itself, and for a sequence that cannot be captured
+ * (a copy to pageable host memory); host-side argument errors are reported per
+ * call as before.  on = 0 drops the graphs (after synchronising the stream).
+ * Errors: MHE_E_ARG (ctx NULL); from the entry points, MHE_E_CUDA if a graph
+ * launch fails. */
+int mhe_set_graph(mhe_ctx* ctx, int on);
+
 /* MHE with inequality constraints (Section II; the paper notes that an
  * interior-point method spends its time in Newton steps of the UFTOC form the
  * library solves).  The constraint sets are not in the paper; this outer loop
@@ -371,11 +396,17 @@ int mhe_set_double_float_residual(mhe_ctx* ctx, int on);
  * w at least 0.5% of its distance inside each bound, and a full short step
  * divides the barrier parameter by 10, per instance.  Options: bounds [batch]
  * [nw] (device, FP64, w_lo < w_hi); mu0 (0: 1), mu_final (0: 1e-9), max_newton
- * (0: 200).  Outputs as mhe_solve (x, w the solution; lam and info those of the
- * last Newton step's problem); newton_steps (host, may be NULL) the steps
- * taken.  Allocates its work buffers per call; synchronises the context's
- * stream once per Newton step.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_CUDA,
- * MHE_E_NO_CONVERGE (max_newton reached), and those of mhe_factor_solve. */
+ * (0: 200).  Outputs as mhe_solve: x, w the solution, lam the multipliers of
+ * the last Newton step's problem, info [batch] (device or host, may be NULL)
+ * per instance the record of the last Newton step it took (a step whose
+ * status is not MHE_OK stops that instance; MHE_E_NO_CONVERGE for one still
+ * iterating at max_newton); newton_steps (host, may be NULL) the steps taken.
+ * Allocates its work buffers per call; synchronises the context's stream once
+ * per Newton step and before it returns.  Errors: MHE_E_ARG, MHE_E_NOMEM,
+ * MHE_E_CUDA, MHE_E_NO_CONVERGE (max_newton reached), and those of
+ * mhe_factor_solve.  Contexts in MHE_FP64 suit it best: the barrier's Hessian
+ * grows like 1/mu near an active bound, which the FP32 tree resolves only with
+ * more refinement. */
 typedef struct {
     const double* w_lo;   /* [batch][nw] lower bounds of w_t (device) */
     const double* w_hi;   /* [batch][nw] upper bounds of w_t (device) */

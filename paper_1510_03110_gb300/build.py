@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmhe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "engine.cpp", "plan.cpp", "shapes_small.cu", "shapes_mid.cu",
-           "shapes_big.cu", "shapes_sq.cu", "shapes_xl.cu", "shapes_xl64.cu", "shapes_n12.cu", "noalloc.cu", "serve.cu", "rts.cu", "ip.cu"]
+           "shapes_big.cu", "shapes_sq.cu", "shapes_xl.cu", "shapes_xl64.cu", "shapes_n12.cu", "noalloc.cu", "serve.cu", "rts.cu", "ip.cu", "shapes_t16.cu", "shapes_t32.cu"]
 
 
 def nvcc() -> str:

@@ -19,6 +19,8 @@ int shapes_big(ShapeEntry* out, int cap);
 int shapes_sq(ShapeEntry* out, int cap);
 int shapes_xl(ShapeEntry* out, int cap);
 int shapes_n12(ShapeEntry* out, int cap);
+int shapes_t16(ShapeEntry* out, int cap);
+int shapes_t32(ShapeEntry* out, int cap);
 int set_tc_wait_limit(int tries);   // shapes_xl.cu
 }  // namespace mhe
 
@@ -76,10 +78,36 @@ struct HostPipe {
     }
 };
 
+// CUDA-graph replay of an entry point's launch sequence (mhe_set_graph).  The
+// sequence depends only on the plan, the options and the argument pointers, never
+// on the data: the key holds the entry and its pointers.  A first call with a key
+// runs eagerly (making every allocation the sequence needs), the second captures
+// its launches into a graph, later ones launch the graph.
+struct GraphCache {
+    std::vector<uintptr_t> key;
+    long long gen = -1;               // the engine's allocation generation at capture
+    bool warm = false;                // one eager call with this key has run
+    bool refused = false;             // capture failed for this key: stay eager
+    long long launches = 0;           // kernels in the captured sequence
+    cudaGraphExec_t exec = nullptr;
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+        gen = -1;
+        warm = refused = false;
+        launches = 0;
+    }
+    ~GraphCache() { reset(); }
+};
+
 struct mhe_ctx {
     mhe::Engine eng;
     PassTiming timing;
     HostPipe* pipe = nullptr;
+    bool graph_on = false;
+    GraphCache graph[5];              // per entry point (index 1..4)
 };
 
 namespace {
@@ -106,15 +134,19 @@ std::vector<mhe::ShapeEntry>& registry()
         k += mhe::shapes_big(buf + k, 32 - k);
         k += mhe::shapes_sq(buf + k, 32 - k);
         k += mhe::shapes_xl(buf + k, 32 - k);
+        // team-width variants after every default
+        k += mhe::shapes_t16(buf + k, 32 - k);
+        k += mhe::shapes_t32(buf + k, 32 - k);
         reg.assign(buf, buf + k);
     });
     return reg;
 }
 
-const mhe::ShapeEntry* find_shape(int nx, int nw)
+// the shape's entry of the given team width (0: its default, the first registered)
+const mhe::ShapeEntry* find_shape(int nx, int nw, int team = 0)
 {
     for (auto& e : registry())
-        if (e.ops.nx == nx && e.ops.nw == nw) return &e;
+        if (e.ops.nx == nx && e.ops.nw == nw && (team == 0 || e.ops.team == team)) return &e;
     return nullptr;
 }
 
@@ -262,8 +294,73 @@ int check_dims(const mhe_dims* d)
     if (!find_shape(d->nx, d->nw))
         return fail(MHE_E_ARG, "shape (nx=" + std::to_string(d->nx) + ", nw=" + std::to_string(d->nw) +
                                    ") is not compiled into this library");
+    if (d->team != 0 && !find_shape(d->nx, d->nw, d->team))
+        return fail(MHE_E_ARG, "team width " + std::to_string(d->team) + " is not compiled for shape (nx=" +
+                                   std::to_string(d->nx) + ", nw=" + std::to_string(d->nw) + ")");
     return MHE_OK;
 }
+
+// run fn (an entry point's launch sequence on the context's stream), through the
+// context's graph cache when graphs are on
+template <class F>
+int run_graphed(mhe_ctx* ctx, std::vector<uintptr_t> key, F&& fn)
+{
+    mhe::Engine& e = ctx->eng;
+    cudaStream_t st = (cudaStream_t)e.stream;
+    // the legacy default stream cannot be captured; timing marks need eager events
+    if (!ctx->graph_on || st == nullptr || e.mark_user) return fn();
+    GraphCache& g = ctx->graph[key[0]];
+    key.push_back((uintptr_t)e.df_resid);
+    const bool same = g.key == key && g.gen == e.alloc_gen;
+    if (same && g.exec) {
+        if (cudaGraphLaunch(g.exec, st) != cudaSuccess) return fail(MHE_E_CUDA, "launch of the captured graph failed");
+        e.launches += g.launches;
+        return MHE_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!same || !g.warm || g.refused || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone) {
+        // first call with this key (or the caller is capturing the stream itself): eager
+        const bool keep_refused = same && g.refused;
+        if (!same) g.reset();
+        const int rc = fn();
+        if (rc == MHE_OK) {
+            g.key = key;
+            g.gen = e.alloc_gen;
+            g.warm = true;
+            g.refused = keep_refused;
+        }
+        return rc;
+    }
+    const long long gen0 = e.alloc_gen, l0 = e.launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        g.refused = true;
+        return fn();
+    }
+    const int rc = fn();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = rc == MHE_OK && ce == cudaSuccess && graph && e.alloc_gen == gen0 &&
+                    cudaGraphInstantiate(&exec, graph, 0ULL) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        // something in the sequence cannot be captured (a pageable host copy, an
+        // allocation): run it eagerly, now and for this key from now on
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        e.launches = l0;
+        g.refused = true;
+        return fn();
+    }
+    g.exec = exec;
+    g.launches = e.launches - l0;
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) return fail(MHE_E_CUDA, "launch of the captured graph failed");
+    return MHE_OK;
+}
+
+uintptr_t up(const void* p) { return (uintptr_t)p; }
 
 }  // namespace
 
@@ -285,7 +382,7 @@ int mhe_create(const mhe_dims* dims, void* stream, mhe_ctx** out)
     if (rc != MHE_OK) return rc;
     mhe_ctx* c = new (std::nothrow) mhe_ctx;
     if (!c) return fail(MHE_E_NOMEM, "host allocation failed");
-    rc = c->eng.init(*dims, &find_shape(dims->nx, dims->nw)->ops, &kRuntime, stream);
+    rc = c->eng.init(*dims, &find_shape(dims->nx, dims->nw, dims->team)->ops, &kRuntime, stream);
     if (rc != MHE_OK) {
         g_err = c->eng.err;
         c->eng.release();
@@ -301,7 +398,7 @@ size_t mhe_workspace_bytes(const mhe_dims* dims)
     if (check_dims(dims) != MHE_OK) return 0;
     mhe::Engine e;
     e.prec = dims->prec;
-    e.ops = &find_shape(dims->nx, dims->nw)->ops;
+    e.ops = &find_shape(dims->nx, dims->nw, dims->team)->ops;
     e.m64 = dims->fp64_masters != 0 && dims->prec != MHE_FP64;
     e.literal = dims->down_pass == 1;
     const int min_leaf = (dims->nx + dims->nw - 1) / dims->nw;
@@ -317,17 +414,30 @@ size_t mhe_workspace_bytes(const mhe_dims* dims)
 int mhe_factor(mhe_ctx* ctx, const mhe_matrices* mats)
 {
     if (!ctx || !mats) return fail(MHE_E_ARG, "ctx or mats is NULL");
-    int rc = ctx->eng.factor(*mats, nullptr, nullptr, nullptr, nullptr);
-    if (rc != MHE_OK) g_err = ctx->eng.err;
-    return rc;
+    mhe::Engine& e = ctx->eng;
+    return run_graphed(ctx, {1, up(mats->A), up(mats->B), up(mats->Q), up(mats->P0inv)}, [&] {
+        const int r = e.factor(*mats, nullptr, nullptr, nullptr, nullptr);
+        if (r != MHE_OK) g_err = e.err;
+        return r;
+    });
 }
 
 int mhe_solve(mhe_ctx* ctx, const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_info* info)
 {
     if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
-    int rc = ctx->eng.solve(rhs, x, w, lam, info, false);
-    if (rc != MHE_OK) g_err = ctx->eng.err;
-    return rc;
+    mhe::Engine& e = ctx->eng;
+    // host-side checks first: a replayed graph does not run them
+    if (!e.factored) return fail(MHE_E_NOT_FACTORED, "mhe_solve before mhe_factor");
+    // the problem the last factorisation left in the engine (the residual reads it) is part of the key
+    std::vector<uintptr_t> key = {2, up(x), up(w), up(lam), up(info), up(e.A), up(e.B), up(e.Q), up(e.P0inv),
+                                  up(e.mA), up(e.mB), up(e.mQ), up(e.mP0), up(e.mheC), up(e.mheR), up(e.rAh),
+                                  up(e.rBh), up(e.rCh), up(e.rRh)};
+    if (rhs) for (const void* p : {(const void*)rhs->l, (const void*)rhs->a, (const void*)rhs->x0}) key.push_back(up(p));
+    return run_graphed(ctx, key, [&] {
+        const int r = e.solve(rhs, x, w, lam, info, false);
+        if (r != MHE_OK) g_err = e.err;
+        return r;
+    });
 }
 
 int mhe_factor_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs, double* x, double* w,
@@ -335,18 +445,42 @@ int mhe_factor_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs,
 {
     if (!ctx || !mats || !rhs) return fail(MHE_E_ARG, "ctx, mats or rhs is NULL");
     if (!rhs->x0 || (ctx->eng.plan.S_in > 0 && (!rhs->l || !rhs->a))) return fail(MHE_E_ARG, "incomplete right-hand side");
-    int rc = ctx->eng.factor(*mats, rhs, x, w, lam);
-    if (rc == MHE_OK) rc = ctx->eng.solve(rhs, x, w, lam, info, true);
-    if (rc != MHE_OK) g_err = ctx->eng.err;
-    return rc;
+    mhe::Engine& e = ctx->eng;
+    return run_graphed(ctx,
+                       {3, up(mats->A), up(mats->B), up(mats->Q), up(mats->P0inv), up(rhs->l), up(rhs->a),
+                        up(rhs->x0), up(x), up(w), up(lam), up(info)},
+                       [&] {
+                           int r = e.factor(*mats, rhs, x, w, lam);
+                           if (r == MHE_OK) r = e.solve(rhs, x, w, lam, info, true);
+                           if (r != MHE_OK) g_err = e.err;
+                           return r;
+                       });
 }
 
 int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info)
 {
     if (!ctx || !prob) return fail(MHE_E_ARG, "ctx or prob is NULL");
-    const int rc = ctx->eng.estimate(*prob, x, w, lam, info);
-    if (rc != MHE_OK) g_err = ctx->eng.err;
-    return rc;
+    mhe::Engine& e = ctx->eng;
+    const mhe_problem& p = *prob;
+    return run_graphed(ctx,
+                       {4, (uintptr_t)p.ny, up(p.A), up(p.B), up(p.C), up(p.R), up(p.a), up(p.yt), up(p.wt),
+                        up(p.x0), up(p.P0inv), up(x), up(w), up(lam), up(info)},
+                       [&] {
+                           const int r = e.estimate(p, x, w, lam, info);
+                           if (r != MHE_OK) g_err = e.err;
+                           return r;
+                       });
+}
+
+int mhe_set_graph(mhe_ctx* ctx, int on)
+{
+    if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
+    if (!on) {
+        cudaStreamSynchronize((cudaStream_t)ctx->eng.stream);
+        for (auto& g : ctx->graph) g.reset();
+    }
+    ctx->graph_on = on != 0;
+    return MHE_OK;
 }
 
 namespace {
@@ -471,6 +605,7 @@ int mhe_destroy(mhe_ctx* ctx)
 {
     if (!ctx) return MHE_OK;
     cudaStreamSynchronize((cudaStream_t)ctx->eng.stream);
+    for (auto& g : ctx->graph) g.reset();
     delete ctx->pipe;
     ctx->pipe = nullptr;
     ctx->eng.release();
@@ -493,12 +628,27 @@ int mhe_assemble(int nx, int nw, int ny, long long S, const double* C, const dou
 
 int mhe_shapes(int* nx_out, int* nw_out, int cap)
 {
-    auto& r = registry();
-    for (int i = 0; i < (int)r.size() && i < cap; ++i) {
-        if (nx_out) nx_out[i] = r[i].ops.nx;
-        if (nw_out) nw_out[i] = r[i].ops.nw;
+    int k = 0;
+    for (auto& e : registry()) {
+        if (find_shape(e.ops.nx, e.ops.nw) != &e) continue;   // a team-width variant
+        if (k < cap) {
+            if (nx_out) nx_out[k] = e.ops.nx;
+            if (nw_out) nw_out[k] = e.ops.nw;
+        }
+        ++k;
     }
-    return (int)r.size();
+    return k;
+}
+
+int mhe_shape_teams(int nx, int nw, int* teams, int cap)
+{
+    int k = 0;
+    for (auto& e : registry()) {
+        if (e.ops.nx != nx || e.ops.nw != nw) continue;
+        if (k < cap && teams) teams[k] = e.ops.team;
+        ++k;
+    }
+    return k;
 }
 
 int mhe_timing_enable(mhe_ctx* ctx, int enable)
@@ -595,12 +745,13 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    auto time_plan = [&](int leaf, int br, int top, int down) -> double {
+    auto time_plan = [&](int leaf, int br, int top, int down, int team) -> double {
         mhe_dims d = *dims;
         d.leaf_len = leaf;
         d.branching = br;
         d.top_len = top;
         d.down_pass = down;
+        d.team = team;
         mhe_ctx* c = nullptr;
         if (mhe_create(&d, stream, &c) != MHE_OK) return -1.0;
         double bestt = -1.0;
@@ -624,26 +775,37 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
         return bestt;
     };
     const int down0 = dims->down_pass;
-    int bl = min_leaf > 8 ? min_leaf : 8, bb = 4, bt = 4, bd = down0;
-    double bms = time_plan(bl, bb, bt, down0);
+    const int team0 = dims->team;
+    int bl = min_leaf > 8 ? min_leaf : 8, bb = 4, bt = 4, bd = down0, bteam = team0;
+    double bms = time_plan(bl, bb, bt, down0, team0);
     for (int leaf : {4, 8, 16, 32, 64, 128, 256}) {
         if (leaf < min_leaf || leaf == bl) continue;
-        double t = time_plan(leaf, bb, bt, down0);
+        double t = time_plan(leaf, bb, bt, down0, team0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bl = leaf; }
     }
     for (int br : {2, 8, 16}) {
-        double t = time_plan(bl, br, bt, down0);
+        double t = time_plan(bl, br, bt, down0, team0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bb = br; }
     }
     for (int top : {1, 16, 64, 256, 512, 1024, maxN + 1}) {
         if (top > maxN + 1) continue;
         if (top == bt) continue;
-        double t = time_plan(bl, bb, top, down0);
+        double t = time_plan(bl, bb, top, down0, team0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bt = top; }
     }
     {   // the other down pass (a context that cannot have it is simply not a candidate)
-        double t = time_plan(bl, bb, bt, 1 - down0);
+        double t = time_plan(bl, bb, bt, 1 - down0, team0);
         if (t > 0 && (bms < 0 || t < bms)) { bms = t; bd = 1 - down0; }
+    }
+    {   // every team width compiled for the shape
+        const int def = find_shape(dims->nx, dims->nw)->ops.team;
+        for (auto& e : registry()) {
+            if (e.ops.nx != dims->nx || e.ops.nw != dims->nw) continue;
+            const int tw = e.ops.team;
+            if (tw == (team0 ? team0 : def)) continue;   // the width already timed
+            double t = time_plan(bl, bb, bt, bd, tw);
+            if (t > 0 && (bms < 0 || t < bms)) { bms = t; bteam = tw; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -653,6 +815,7 @@ int mhe_autotune(const mhe_dims* dims, const mhe_matrices* mats, const mhe_rhs* 
     best->branching = bb;
     best->top_len = bt;
     best->down_pass = bd;
+    best->team = bteam;
     if (best_ms) *best_ms = bms;
     if (bms < 0) return fail(MHE_E_NO_CONVERGE, "no candidate plan ran with every instance solved");
     return MHE_OK;

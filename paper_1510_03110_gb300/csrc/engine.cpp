@@ -186,6 +186,7 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
     this->topl = top;
     arena_bytes = layout(nullptr);
     arena = rt->alloc(arena_bytes);
+    ++alloc_gen;
     if (!arena) { err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
     layout(static_cast<char*>(arena));
     return upload_plan();
@@ -222,6 +223,7 @@ int Engine::replan(const int* N, int batch, const long long* in_off_custom)
         rt->sync(stream);
         rt->release(arena);
         arena = rt->alloc(need + need / 4);
+        ++alloc_gen;
         if (!arena) { arena_bytes = 0; err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
         arena_bytes = need + need / 4;
     }
@@ -247,6 +249,7 @@ int Engine::replan_serve(const std::vector<ServeWindow>& w, const ExtStores& st,
         rt->sync(stream);
         rt->release(arena);
         arena = rt->alloc(need + need / 4);
+        ++alloc_gen;
         if (!arena) { arena_bytes = 0; err = "device allocation of the workspace failed"; return MHE_E_NOMEM; }
         arena_bytes = need + need / 4;
     }
@@ -733,9 +736,10 @@ int Engine::solve(const mhe_rhs* rhs, double* x, double* w, double* lam, mhe_inf
 
 namespace {
 // (re)allocate an internal buffer to at least `need` bytes
-bool reserve(const Runtime* rt, void* stream, double*& p, size_t& have, size_t need)
+bool reserve(const Runtime* rt, void* stream, double*& p, size_t& have, size_t need, long long& gen)
 {
     if (need <= have && p) return true;
+    ++gen;
     if (p) {
         rt->sync(stream);
         rt->release(p);
@@ -757,14 +761,14 @@ int Engine::estimate(const mhe_problem& p, double* x, double* w, double* lam, mh
     if (!x || !w || !lam) { err = "output pointer is NULL"; return MHE_E_ARG; }
     const int n = plan.n, m = plan.m;
     const long long S = plan.S_in;
-    if (!reserve(rt, stream, l64, l64_bytes, sizeof(double) * (size_t)S * (n + m))) {
+    if (!reserve(rt, stream, l64, l64_bytes, sizeof(double) * (size_t)S * (n + m), alloc_gen)) {
         err = "device allocation of l failed";
         return MHE_E_NOMEM;
     }
     mhe_rhs rhs;
     rhs.l = l64; rhs.a = p.a; rhs.x0 = p.x0;
     if (prec == MHE_FP64) {
-        if (!reserve(rt, stream, Q64, Q64_bytes, sizeof(double) * (size_t)S * (n + m) * (n + m))) {
+        if (!reserve(rt, stream, Q64, Q64_bytes, sizeof(double) * (size_t)S * (n + m) * (n + m), alloc_gen)) {
             err = "device allocation of Q failed";
             return MHE_E_NOMEM;
         }
@@ -798,7 +802,7 @@ int Engine::estimate(const mhe_problem& p, double* x, double* w, double* lam, mh
     if (df_resid) {
         const int q = p.ny;
         const size_t per = (size_t)n * n + (size_t)n * m + 2 * (size_t)q * n + 2 * (size_t)(m + q) * (m + q);
-        if (!reserve(rt, stream, dfp, dfp_bytes, sizeof(float) * (size_t)S * per + 64)) {
+        if (!reserve(rt, stream, dfp, dfp_bytes, sizeof(float) * (size_t)S * per + 64, alloc_gen)) {
             err = "device allocation of the residual's float pairs failed";
             return MHE_E_NOMEM;
         }

@@ -42,6 +42,15 @@ struct ShapeOps {
     // team's workspace and the number of team slots a context provides (0: none)
     long long gws64;
     int gws_teams;
+    int team;   // lanes per subproblem team of these kernels
+};
+
+// Everything one compiled shape provides (one entry per shape and team width).
+struct ShapeEntry {
+    ShapeOps ops;
+    int ny;
+    void (*assemble)(long long, const double*, const double*, const double*, const double*, double*, double*,
+                     double*, void*);
 };
 
 // Memory and small shape-independent steps.
@@ -162,6 +171,7 @@ public:
     const int* active_mask = nullptr;   // instances still refining (nullptr: all)
     void* mark_user = nullptr;          // non-null: record per-pass timing marks
     long long launches = 0;             // kernels launched by this context so far
+    long long alloc_gen = 0;            // device allocations made so far (a captured graph holds their addresses)
     bool factored = false;
     std::string err;
 

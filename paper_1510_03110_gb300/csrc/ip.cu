@@ -5,17 +5,21 @@
 // UFTOC problem of the form the library solves.  The paper does not give the
 // constraint sets; this loop takes box bounds lo <= w_t <= hi on the process
 // noise of every measured stage (t = 1 .. N-1; w_0 and the states are free) and
-// runs a primal barrier method:
+// runs a primal-dual barrier method on
 //   minimise  f(z) - mu sum log(w - lo) - mu sum log(hi - w)  subject to the dynamics,
-// one Newton step at a time.  The Newton step's quadratic model is the UFTOC
-// problem with Q_w + D and l_w + b - D w at every stage, where D = mu/(w-lo)^2 +
-// mu/(hi-w)^2 (diagonal) and b = -mu/(w-lo) + mu/(hi-w); its solution z' (through
-// mhe_factor_solve, the tree) is dynamically feasible, and so is every step
-// z + alpha (z' - z) from a feasible z.  alpha is the largest step up to 1 that
-// keeps w at least 0.5 % of the distance from each bound (fraction to the
-// boundary); when a step is full and short, mu shrinks by 10.  Every instance
-// has its own mu and stops on its own; the loop ends when all have mu below
-// the target and a short step, or after max_newton steps.
+// with the bounds' multipliers zl, zh >= 0 carried alongside w (s_l = w - lo,
+// s_h = hi - w; the barrier's optimality asks s_l zl = s_h zh = mu).  One Newton
+// step on these conditions is the UFTOC problem with, at every stage,
+//   Q_w + Sigma  and  l_w - mu/s_l + mu/s_h - Sigma w,   Sigma = zl/s_l + zh/s_h (diagonal),
+// solved by mhe_factor_solve (the tree); its solution z' gives the primal step
+// z' - z (dynamically feasible from a feasible z) and the multipliers' steps
+//   dzl = mu/s_l - zl - (zl/s_l) dw,   dzh = mu/s_h - zh + (zh/s_h) dw.
+// The primal and the dual step lengths are each the largest up to 1 that keeps
+// s_l, s_h (resp. zl, zh) at least 0.5% of their current value from zero
+// (fraction to the boundary).  A full, short primal step ends the barrier
+// subproblem: mu becomes min(mu / 5, mu^1.5).  Every instance has its own mu and
+// stops on its own; the loop ends when all have mu at or below the target and a
+// short step, or after max_newton steps.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -24,7 +28,6 @@
 
 #include "../../include/mhe.h"
 #include "engine.h"
-#include "f32conv.h"
 
 namespace mhe {
 void set_last_error(const std::string& msg);
@@ -34,6 +37,8 @@ void* ctx_stream(mhe_ctx* ctx);
 
 namespace {
 
+constexpr double kTau = 0.995;          // fraction to the boundary
+
 struct IpArgs {
     int n, m, batch;
     const long long *in_off, *xo, *wo;   // per instance: caller stage, state and input offsets
@@ -41,19 +46,27 @@ struct IpArgs {
     const double *A, *B, *Q, *l, *a, *x0, *lo, *hi;
     double *Qb, *lb;                     // the Newton model's Q and l (caller stage layout)
     double *x, *w;                       // the iterate
+    double *zl, *zh;                     // the bounds' multipliers (the layout of w; bounded entries only)
+    double *dzl, *dzh;                   // their steps
     const double *xn, *wn;               // the model's solution
     double* mu;                          // per instance
-    unsigned long long* amin;            // per instance: min step, as float bits of a positive value
+    unsigned long long* ap;              // per instance: primal step length, float bits of a value in (0, 1]
+    unsigned long long* ad;              // per instance: dual step length
     unsigned long long* dmax;            // per instance: max |z' - z|, bits of a non-negative double
     unsigned long long* zmax;            // per instance: max |z|
-    int* done;                           // per instance: converged
+    int* done;                           // per instance: converged, or stopped by a failed Newton step
     int* any;                            // some instance still iterating
+    const mhe_info* info;                // the Newton step's per-instance records
+    mhe_info* final_info;                // per instance: the record of the last step it iterated
     double mu_final;
 };
 
 __device__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ unsigned long long fbits(double v) { return (unsigned long long)__float_as_uint((float)v); }
+__device__ double fval(unsigned long long b) { return (double)__uint_as_float((unsigned)b); }
 
-// the start: w_t = the middle of the box (t >= 1), w_0 = 0, x by the dynamics from x~0
+// the start: w_t = the middle of the box (t >= 1), w_0 = 0, x by the dynamics
+// from x~0; the multipliers on the central path of mu0 (s zl = s zh = mu0)
 __global__ void k_ip_init(IpArgs r, double mu0)
 {
     const int b = blockIdx.x;
@@ -73,8 +86,14 @@ __global__ void k_ip_init(IpArgs r, double mu0)
         const double* A = r.A + s * n * n;
         const double* B = r.B + s * n * m;
         const double* a = r.a + s * n;
-        double* wt = w + n + (long long)(t - 1) * m;
-        for (int j = 0; j < m; ++j) wt[j] = 0.5 * (lo[j] + hi[j]);
+        const long long wofs = r.wo[b] + n + (long long)(t - 1) * m;
+        double* wt = r.w + wofs;
+        for (int j = 0; j < m; ++j) {
+            wt[j] = 0.5 * (lo[j] + hi[j]);
+            const double half = 0.5 * (hi[j] - lo[j]);
+            r.zl[wofs + j] = mu0 / half;
+            r.zh[wofs + j] = mu0 / half;
+        }
         const double* xt = x + (long long)t * n;
         double* xn = x + (long long)(t + 1) * n;
         for (int i = 0; i < n; ++i) {
@@ -88,7 +107,7 @@ __global__ void k_ip_init(IpArgs r, double mu0)
     r.done[b] = 0;
 }
 
-// the Newton model of every stage t >= 1: Q + D on the w block, l + b - D w
+// the Newton model of every stage t >= 1: Q + Sigma on the w block, l - mu/s_l + mu/s_h - Sigma w
 __global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
 {
     const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
@@ -99,15 +118,16 @@ __global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const in
     double* Qb = r.Qb + s * nq * nq;
     const double* l = r.l + s * nq;
     double* lb = r.lb + s * nq;
-    const double* w = r.w + r.wo[b] + n + (long long)(t - 1) * m;
+    const long long wofs = r.wo[b] + n + (long long)(t - 1) * m;
+    const double* w = r.w + wofs;
     const double mu = r.mu[b];
     for (int idx = threadIdx.x; idx < nq * nq; idx += blockDim.x) {
         const int i = idx % nq, j = idx / nq;
         double v = Q[idx];
         if (i == j && i >= n) {
             const int q = i - n;
-            const double dl = w[q] - r.lo[(long long)b * m + q], dh = r.hi[(long long)b * m + q] - w[q];
-            v += mu / (dl * dl) + mu / (dh * dh);
+            const double sl = w[q] - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - w[q];
+            v += r.zl[wofs + q] / sl + r.zh[wofs + q] / sh;
         }
         Qb[idx] = v;
     }
@@ -115,15 +135,19 @@ __global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const in
         double v = l[i];
         if (i >= n) {
             const int q = i - n;
-            const double dl = w[q] - r.lo[(long long)b * m + q], dh = r.hi[(long long)b * m + q] - w[q];
-            const double D = mu / (dl * dl) + mu / (dh * dh);
-            v += -mu / dl + mu / dh - D * w[q];
+            const double sl = w[q] - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - w[q];
+            const double sig = r.zl[wofs + q] / sl + r.zh[wofs + q] / sh;
+            v += -mu / sl + mu / sh - sig * w[q];
         }
         lb[i] = v;
     }
 }
 
-// per instance: the largest step keeping every bounded w 0.5 % inside its box, and max |z' - z|, max |z|
+// the largest step in (0, 1] keeping v + a dv >= (1 - tau) v (v > 0)
+__device__ double max_step(double v, double dv) { return dv < 0 ? fmin(1.0, -kTau * v / dv) : 1.0; }
+
+// per stage: the multipliers' steps; per instance: the primal and dual step
+// lengths, max |z' - z| and max |z|
 __global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
 {
     const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
@@ -132,15 +156,18 @@ __global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const
     if (r.done[b]) return;
     const int n = r.n, m = r.m;
     const long long woff = r.wo[b] + n + (long long)(t - 1) * m;
-    float amin = 1.0f;
-    double dmax = 0.0, zmax = 0.0;
+    const double mu = r.mu[b];
+    double ap = 1.0, ad = 1.0, dmax = 0.0, zmax = 0.0;
     for (int q = threadIdx.x; q < m; q += blockDim.x) {
         const double wv = r.w[woff + q], d = r.wn[woff + q] - wv;
-        const double lo = r.lo[(long long)b * m + q], hi = r.hi[(long long)b * m + q];
-        double amax = 1.0;
-        if (d < 0) amax = 0.995 * (lo - wv) / d;
-        else if (d > 0) amax = 0.995 * (hi - wv) / d;
-        amin = fminf(amin, (float)fmin(amax, 1.0));
+        const double sl = wv - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - wv;
+        const double zl = r.zl[woff + q], zh = r.zh[woff + q];
+        const double dzl = mu / sl - zl - zl / sl * d;
+        const double dzh = mu / sh - zh + zh / sh * d;
+        r.dzl[woff + q] = dzl;
+        r.dzh[woff + q] = dzh;
+        ap = fmin(ap, fmin(max_step(sl, d), max_step(sh, -d)));
+        ad = fmin(ad, fmin(max_step(zl, dzl), max_step(zh, dzh)));
         dmax = fmax(dmax, fabs(d));
         zmax = fmax(zmax, fabs(wv));
     }
@@ -150,59 +177,79 @@ __global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const
         dmax = fmax(dmax, fabs(xnt[i] - xt[i]));
         zmax = fmax(zmax, fabs(xt[i]));
     }
-    if (amin < 1.0f) atomicMin(r.amin + b, (unsigned long long)__float_as_uint(fmaxf(amin, 0.f)));
+    // step lengths as float bits: truncating to float only shortens a positive step's
+    // representation by rounding, so it is taken down to the float below
+    if (ap < 1.0) atomicMin(r.ap + b, fbits(fmax(__double2float_rd(ap), 0.0f)));
+    if (ad < 1.0) atomicMin(r.ad + b, fbits(fmax(__double2float_rd(ad), 0.0f)));
     if (dmax > 0.0) atomicMax(r.dmax + b, dbits(dmax));
     if (zmax > 0.0) atomicMax(r.zmax + b, dbits(zmax));
 }
 
-// z += alpha (z' - z) for the instances still iterating (every state, every input)
-__global__ void k_ip_step(IpArgs r, long long X, long long Wn, const int* x_inst, const int* w_inst)
+// z += ap (z' - z), zl += ad dzl, zh += ad dzh for the instances still iterating
+__global__ void k_ip_step(IpArgs r, long long X, long long Wn, const int* x_inst, const int* w_inst,
+                          const unsigned char* bounded)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < X * r.n) {
         const int b = x_inst[i / r.n];
-        if (!r.done[b]) {
-            const double al = (double)__uint_as_float((unsigned)r.amin[b]);
-            r.x[i] += al * (r.xn[i] - r.x[i]);
-        }
+        if (!r.done[b]) r.x[i] += fval(r.ap[b]) * (r.xn[i] - r.x[i]);
     }
     if (i < Wn) {
         const int b = w_inst[i];
         if (!r.done[b]) {
-            const double al = (double)__uint_as_float((unsigned)r.amin[b]);
-            r.w[i] += al * (r.wn[i] - r.w[i]);
+            r.w[i] += fval(r.ap[b]) * (r.wn[i] - r.w[i]);
+            if (bounded[i]) {
+                const double ad = fval(r.ad[b]);
+                r.zl[i] += ad * r.dzl[i];
+                r.zh[i] += ad * r.dzh[i];
+            }
         }
     }
 }
 
-// the per-instance reductions of a step: no step limit yet (1), no change, no size
+// the per-instance reductions of a step: full steps (1), no change, no size
 __global__ void k_ip_clear(IpArgs r)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= r.batch) return;
-    r.amin[b] = (unsigned long long)__float_as_uint(1.0f);
+    r.ap[b] = fbits(1.0);
+    r.ad[b] = fbits(1.0);
     r.dmax[b] = 0ULL;
     r.zmax[b] = 0ULL;
 }
 
-// per instance: a full, short step ends the current barrier subproblem (mu /= 10); convergence
+// per instance: a failed Newton step stops it; a full, short primal step ends the
+// barrier subproblem (mu -> min(mu / 5, mu^1.5)), and at mu_final the instance
 __global__ void k_ip_update(IpArgs r, double step_tol)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= r.batch) return;
     if (!r.done[b]) {
-        const double al = (double)__uint_as_float((unsigned)r.amin[b]);
+        r.final_info[b] = r.info[b];
+        if (r.info[b].status != MHE_OK) r.done[b] = 1;
+    }
+    if (!r.done[b]) {
+        const double ap = fval(r.ap[b]);
         const double d = __longlong_as_double((long long)r.dmax[b]);
         const double z = __longlong_as_double((long long)r.zmax[b]);
-        if (al >= 1.0 && d <= step_tol * (1.0 + z)) {
-            if (r.mu[b] <= r.mu_final) r.done[b] = 1;
-            else r.mu[b] = fmax(0.1 * r.mu[b], 0.5 * r.mu_final);
+        if (ap >= 1.0 && d <= step_tol * (1.0 + z)) {
+            const double mu = r.mu[b];
+            if (mu <= r.mu_final) r.done[b] = 1;
+            else r.mu[b] = fmax(fmin(0.2 * mu, pow(mu, 1.5)), 0.5 * r.mu_final);
         }
     }
     if (!r.done[b]) atomicOr(r.any, 1);
-    r.amin[b] = (unsigned long long)__float_as_uint(1.0f);
+    r.ap[b] = fbits(1.0);
+    r.ad[b] = fbits(1.0);
     r.dmax[b] = 0ULL;
     r.zmax[b] = 0ULL;
+}
+
+// the instances still iterating when the step limit is reached
+__global__ void k_ip_unfinished(IpArgs r)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < r.batch && !r.done[b]) r.final_info[b].status = MHE_E_NO_CONVERGE;
 }
 
 template <typename T>
@@ -242,7 +289,9 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     const double mu_final = ip->mu_final > 0 ? ip->mu_final : 1e-9;
     const int max_newton = ip->max_newton > 0 ? ip->max_newton : 200;
     // host-side maps: stage -> (instance, t), state -> instance, input -> instance
+    // and which input entries are bounded (w_t, t >= 1)
     std::vector<int> s_inst(S), s_t(S), x_inst(X), w_inst(Wn);
+    std::vector<unsigned char> bnd(Wn, 0);
     std::vector<long long> xo(batch), wo(batch);
     {
         long long s = 0, xi = 0, wi = 0;
@@ -252,7 +301,10 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
             for (int t = 1; t < P.N[b]; ++t, ++s) { s_inst[s] = b; s_t[s] = t; }
             for (int k = 0; k <= P.N[b]; ++k) x_inst[xi++] = b;
             const long long nw_b = n + (long long)(P.N[b] - 1) * m;
-            for (long long k = 0; k < nw_b; ++k) w_inst[wi++] = b;
+            for (long long k = 0; k < nw_b; ++k) {
+                bnd[wi] = k >= n;
+                w_inst[wi++] = b;
+            }
         }
     }
     std::vector<void*> pool;
@@ -266,17 +318,24 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     double* lb = dev_alloc<double>((size_t)S * (n + m), pool);
     double* xn = dev_alloc<double>((size_t)X * n, pool);
     double* wn = dev_alloc<double>((size_t)Wn, pool);
+    double* zl = dev_alloc<double>((size_t)Wn, pool);
+    double* zh = dev_alloc<double>((size_t)Wn, pool);
+    double* dzl = dev_alloc<double>((size_t)Wn, pool);
+    double* dzh = dev_alloc<double>((size_t)Wn, pool);
+    unsigned char* d_bnd = dev_alloc<unsigned char>((size_t)Wn, pool);
     double* mu = dev_alloc<double>(batch, pool);
-    unsigned long long* red = dev_alloc<unsigned long long>(3 * (size_t)batch, pool);
+    unsigned long long* red = dev_alloc<unsigned long long>(4 * (size_t)batch, pool);
     int* done = dev_alloc<int>(batch, pool);
     int* any = dev_alloc<int>(1, pool);
+    mhe_info* step_info = dev_alloc<mhe_info>(batch, pool);
+    mhe_info* final_info = dev_alloc<mhe_info>(batch, pool);
     int* h_any = nullptr;
     auto cleanup = [&]() {
         for (void* p : pool) cudaFree(p);
         if (h_any) cudaFreeHost(h_any);
     };
-    if (!d_sinst || !d_st || !d_xinst || !d_winst || !d_off || !d_N || !Qb || !lb || !xn || !wn || !mu || !red ||
-        !done || !any || cudaHostAlloc(&h_any, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    if (!d_sinst || !d_st || !d_xinst || !d_winst || !d_off || !d_N || !Qb || !lb || !xn || !wn || !zl || !zh || !dzl || !dzh || !d_bnd || !mu || !red ||
+        !done || !any || !step_info || !final_info || cudaHostAlloc(&h_any, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         mhe::set_last_error("device allocation for the interior-point loop failed");
@@ -292,6 +351,9 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     cudaMemcpyAsync(d_st, s_t.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_xinst, x_inst.data(), sizeof(int) * X, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_winst, w_inst.data(), sizeof(int) * Wn, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_bnd, bnd.data(), (size_t)Wn, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(zl, 0, sizeof(double) * Wn, st);
+    cudaMemsetAsync(zh, 0, sizeof(double) * Wn, st);
     cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * 3 * batch, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_N, P.N.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, st);
     IpArgs r;
@@ -301,8 +363,10 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     r.A = mats->A; r.B = mats->B; r.Q = mats->Q; r.l = rhs->l; r.a = rhs->a; r.x0 = rhs->x0;
     r.lo = ip->w_lo; r.hi = ip->w_hi;
     r.Qb = Qb; r.lb = lb; r.x = x; r.w = w; r.xn = xn; r.wn = wn;
-    r.mu = mu; r.amin = red; r.dmax = red + batch; r.zmax = red + 2 * batch;
+    r.zl = zl; r.zh = zh; r.dzl = dzl; r.dzh = dzh;
+    r.mu = mu; r.ap = red; r.ad = red + batch; r.dmax = red + 2 * batch; r.zmax = red + 3 * batch;
     r.done = done; r.any = any; r.mu_final = mu_final;
+    r.info = step_info; r.final_info = final_info;
     k_ip_init<<<batch, 32, 0, st>>>(r, mu0);
     k_ip_clear<<<(batch + 127) / 128, 128, 0, st>>>(r);
     const dim3 fb(32, 8);
@@ -315,22 +379,25 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     rq.l = lb;
     for (; steps < max_newton; ++steps) {
         if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
-        rc = mhe_factor_solve(ctx, &mq, &rq, xn, wn, lam, info);
+        rc = mhe_factor_solve(ctx, &mq, &rq, xn, wn, lam, step_info);
         if (rc != MHE_OK) break;
         if (S > 0) k_ip_measure<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
         const long long tot = X * n > Wn ? X * n : Wn;
-        k_ip_step<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, X, Wn, d_xinst, d_winst);
+        k_ip_step<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, X, Wn, d_xinst, d_winst, d_bnd);
         cudaMemsetAsync(any, 0, sizeof(int), st);
         k_ip_update<<<(batch + 127) / 128, 128, 0, st>>>(r, 1e-6);
         cudaMemcpyAsync(h_any, any, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MHE_E_CUDA; break; }
         if (*h_any == 0) { ++steps; break; }
     }
-    if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
     if (rc == MHE_OK && *h_any != 0) {
+        k_ip_unfinished<<<(batch + 127) / 128, 128, 0, st>>>(r);
         mhe::set_last_error("the interior-point loop reached max_newton before every instance converged");
         rc = MHE_E_NO_CONVERGE;
     }
+    if ((rc == MHE_OK || rc == MHE_E_NO_CONVERGE) && info)
+        cudaMemcpyAsync(info, final_info, sizeof(mhe_info) * batch, cudaMemcpyDefault, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
     if (newton_steps) *newton_steps = steps;
     cleanup();
     return rc;

@@ -12,6 +12,7 @@
 #include "tree.cuh"
 
 namespace mhe {
+MHE_TEAM_NS_BEGIN
 
 // OP_REDUCE_TC / OP_REDUCE_BF: the reduction with the stage products on the
 // tensor cores, TF32 or BF16 operands
@@ -323,20 +324,13 @@ void launch_assemble(long long S, const double* C, const double* R, const double
     k_assemble<NX, NW, NY><<<(unsigned)grid, MHE_TEAM * W, smem, (cudaStream_t)stream>>>(S, C, R, yt, wt, Q, l, c);
 }
 
-// Everything one compiled shape provides.
-struct ShapeEntry {
-    ShapeOps ops;
-    int ny;
-    void (*assemble)(long long, const double*, const double*, const double*, const double*, double*, double*,
-                     double*, void*);
-};
-
 template <int NX, int NW, int NY>
 ShapeEntry make_shape()
 {
     ShapeEntry e;
     e.ops.nx = NX;
     e.ops.nw = NW;
+    e.ops.team = MHE_TEAM;
     if constexpr (level_fits<double, NX, OP_REDUCE>()) {
         e.ops.reduce64 = &launch_level<double, NX, NW, OP_REDUCE>;
         e.ops.rhs64 = &launch_level<double, NX, NW, OP_RHS>;
@@ -393,4 +387,5 @@ void set_fp64_global_ops(ShapeOps& o)
     o.gws_teams = kGwsTeams;
 }
 
+MHE_TEAM_NS_END
 }  // namespace mhe

@@ -17,6 +17,7 @@
 #include "wgemm.cuh"
 
 namespace mhe {
+MHE_TEAM_NS_BEGIN
 
 // a residual entry in the precision of the correction solve
 template <typename TR>
@@ -1004,4 +1005,5 @@ MHE_DEV void prep_stage(const PrepArgs& p, long long gstage, double* sm)
     });
 }
 
+MHE_TEAM_NS_END
 }  // namespace mhe

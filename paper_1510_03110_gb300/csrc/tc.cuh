@@ -37,6 +37,7 @@
 #endif
 
 namespace mhe {
+MHE_TEAM_NS_BEGIN
 namespace tc {
 
 // x rounded to the nearest TF32 value (ties away from zero) in integer
@@ -249,4 +250,5 @@ MHE_DEV void lanes_publish(F&& f)
 #endif  // MHE_TC_EMULATED
 
 }  // namespace tc
+MHE_TEAM_NS_END
 }  // namespace mhe

@@ -34,6 +34,7 @@
 #include "wgemm.cuh"
 
 namespace mhe {
+MHE_TEAM_NS_BEGIN
 
 enum { KIND_LEAF = 0, KIND_ARRIVAL = 1, KIND_UPPER = 2 };
 
@@ -235,8 +236,9 @@ MHE_DEV void store_block(T* dst, const T* src, T sgn, int ntail, TF&& tail)
 }
 
 // In-place lower Cholesky of the M x M matrix Gm (leading dimension ld of the
-// workspace).  Returns true when a pivot fell below piv_rel * max diag (the
-// pivot is then replaced by 1 to stay finite).  Lane i owns row i of the lower
+// workspace).  Returns true when a pivot fell below piv_rel * G_jj, its
+// column's diagonal before elimination (the pivot is then replaced by 1 to stay
+// finite).  Lane i owns row i of the lower
 // triangle: at column j lane j takes the square root, the lanes below scale
 // their entry of column j and update their own row, so no two lanes write the
 // same entry and a column costs two barriers.  INV (FP32 only) stores 1 / L_jj
@@ -260,16 +262,14 @@ MHE_DEV bool chol_inplace(Ws<T, NX>& s, T* Gm, double piv_rel)
         team_chol<T, M, INV && sizeof(T) == 4>(Gm, ld, piv_rel, s.sc + 1);
         return s.sc[1] != 0;
     }
-    wone([&](int) {
-        T mx = 0;
-        for (int i = 0; i < M; ++i) mx = mmax(mx, mabs(Gm[i + i * ld]));
-        s.sc[0] = (T)(piv_rel * (double)mx);
-        s.sc[1] = 0;
-    });
+    wone([&](int) { s.sc[1] = 0; });
     for (int j = 0; j < M; ++j) {
         wone([&](int) {
             T d = Gm[j + j * ld];
-            if (!(d > s.sc[0])) { s.sc[1] = 1; d = 1; }
+            // column j's diagonal before elimination: the pivot plus the squares of row j of L
+            T g0 = d;
+            for (int k = 0; k < j; ++k) g0 += Gm[j + k * ld] * Gm[j + k * ld];
+            if (!(d > (T)(piv_rel * (double)mabs(g0)))) { s.sc[1] = 1; d = 1; }
             const T l = msqrt(d);
             s.sc[2] = l;
             Gm[j + j * ld] = (INV && sizeof(T) == 4) ? (T)1 / l : l;
@@ -1606,4 +1606,5 @@ MHE_DEV void down_chunk_literal(const LevelArgs<T>& a, int ci, T* smem)
     });
 }
 
+MHE_TEAM_NS_END
 }  // namespace mhe

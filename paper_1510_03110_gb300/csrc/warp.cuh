@@ -25,7 +25,17 @@ static_assert(MHE_TEAM == 8 || MHE_TEAM == 16 || MHE_TEAM == 32 || MHE_TEAM == 6
                   MHE_TEAM == 256,
               "a team is 8 or 16 lanes of a warp, or 1, 2, 4 or 8 warps");
 
+// What the device headers define (kernels, their launchers, device helpers)
+// sits in an inline namespace named by the team width: a shape compiled at two
+// widths in two translation units then has two distinct sets of kernels and
+// host symbols, and code names them through mhe:: as before.
+#define MHE_TEAM_CAT2(a, b) a##b
+#define MHE_TEAM_CAT(a, b) MHE_TEAM_CAT2(a, b)
+#define MHE_TEAM_NS_BEGIN inline namespace MHE_TEAM_CAT(team, MHE_TEAM) {
+#define MHE_TEAM_NS_END }
+
 namespace mhe {
+MHE_TEAM_NS_BEGIN
 
 MHE_DEV int lane_id() { return threadIdx.x & (MHE_TEAM - 1); }
 // index of the team within its CTA
@@ -197,8 +207,9 @@ MHE_DEV void atomic_max_nonneg(double* addr, double v)
 // a column costs no barrier.  Column j: the pivot d = G_jj (row j's register
 // j), L_jj = sqrt(d); L_ij = G_ij / L_jj for the rows below; then every row i
 // subtracts L_ij L_cj from its entries c = j+1..i.  A pivot that is not above
-// piv_rel * max_i |G_ii| is replaced by 1 and reported: *flag = 1 (else 0),
-// written by lane 0 before the closing team barrier.  INV stores 1 / L_jj on
+// piv_rel * G_jj (column j's own diagonal before elimination: a test that a
+// diagonal scaling of G leaves unchanged) is replaced by 1 and reported:
+// *flag = 1 (else 0), written by lane 0 before the closing team barrier.  INV stores 1 / L_jj on
 // the diagonal and multiplies by it, 1 / L_jj from the reciprocal square root
 // of the pivot (FP32); otherwise L_jj is stored and the column divided (FP64).
 template <typename T, int M, bool INV>
@@ -213,14 +224,12 @@ MHE_DEV void team_chol(T* Gm, int ld, double piv_rel, T* flag)
         T g[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) g[c] = (i < M && c <= i) ? Gm[i + c * ld] : (T)0;
-        T mx = i < M ? mabs(Gm[i + i * ld]) : (T)0;
-#pragma unroll
-        for (int o = CW / 2; o > 0; o >>= 1) mx = mmax(mx, __shfl_xor_sync(mask, mx, o, CW));
-        const T thr = (T)(piv_rel * (double)mx);
+        const T thr_i = i < M ? (T)(piv_rel * (double)mabs(Gm[i + i * ld])) : (T)0;
         int bad = 0;
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             T d = __shfl_sync(mask, g[j], j, CW);
+            const T thr = __shfl_sync(mask, thr_i, j, CW);
             if (!(d > thr)) {
                 bad = 1;
                 d = (T)1;
@@ -250,6 +259,7 @@ MHE_DEV void team_chol(T* Gm, int ld, double piv_rel, T* flag)
     wsync();
 }
 
+MHE_TEAM_NS_END
 }  // namespace mhe
 
 #endif  // MHE_WARP_CUH

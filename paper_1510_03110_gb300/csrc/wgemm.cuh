@@ -3,6 +3,7 @@
 #include "warp.cuh"
 
 namespace mhe {
+MHE_TEAM_NS_BEGIN
 
 // Lane tile of a team product with M x N outputs: the smallest TM x TN whose
 // ceil(M/TM) ceil(N/TN) tiles fit in the team's lanes (ties: fewest operand
@@ -132,4 +133,5 @@ MHE_DEV void wgemm_tn(FI&& init, const T* Ab, const T* Bb, T sgn, FO&& out)
     });
 }
 
+MHE_TEAM_NS_END
 }  // namespace mhe

@@ -32,7 +32,8 @@ c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 class mhe_dims(ctypes.Structure):
     _fields_ = [("nx", c_int), ("nw", c_int), ("batch", c_int), ("N", ctypes.POINTER(c_int)),
                 ("prec", c_int), ("leaf_len", c_int), ("branching", c_int), ("top_len", c_int),
-                ("refine_tol", c_double), ("max_refine", c_int), ("fp64_masters", c_int), ("down_pass", c_int)]
+                ("refine_tol", c_double), ("max_refine", c_int), ("fp64_masters", c_int), ("down_pass", c_int),
+                ("team", c_int)]
 
 
 class mhe_matrices(ctypes.Structure):
@@ -90,6 +91,8 @@ def _declare(L):
     L.mhe_assemble.restype = c_int
     L.mhe_shapes.argtypes = [P(c_int), P(c_int), c_int]
     L.mhe_shapes.restype = c_int
+    L.mhe_shape_teams.argtypes = [c_int, c_int, P(c_int), c_int]
+    L.mhe_shape_teams.restype = c_int
     L.mhe_timing_enable.argtypes = [c_void_p, c_int]
     L.mhe_timing_enable.restype = c_int
     L.mhe_timing_read.argtypes = [c_void_p, ctypes.POINTER(c_double), c_int]
@@ -100,6 +103,8 @@ def _declare(L):
     L.mhe_launch_count.restype = c_ll
     L.mhe_assemble_count.argtypes = []
     L.mhe_assemble_count.restype = c_ll
+    L.mhe_set_graph.argtypes = [c_void_p, c_int]
+    L.mhe_set_graph.restype = c_int
     L.mhe_ip_solve.argtypes = [c_void_p, P(mhe_matrices), P(mhe_rhs), P(mhe_ip_opts), c_void_p, c_void_p, c_void_p,
                                c_void_p, P(c_int)]
     L.mhe_ip_solve.restype = c_int
@@ -188,12 +193,19 @@ def shapes():
     return [(nx[i], nw[i]) for i in range(k)]
 
 
+def shape_teams(nx, nw):
+    """Team widths compiled for (nx, nw), the default first (mhe_shape_teams)."""
+    t = (c_int * 16)()
+    k = lib().mhe_shape_teams(int(nx), int(nw), t, 16)
+    return [t[i] for i in range(min(k, 16))]
+
+
 def make_dims(nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0, refine_tol=0.0,
-              max_refine=-1, fp64_masters=False, down_pass=0):
+              max_refine=-1, fp64_masters=False, down_pass=0, team=0):
     N = np.ascontiguousarray(np.asarray(N, dtype=np.int32).reshape(-1))
     d = mhe_dims(int(nx), int(nw), int(N.size), N.ctypes.data_as(ctypes.POINTER(c_int)), int(prec),
                  int(leaf_len), int(branching), int(top_len), float(refine_tol), int(max_refine),
-                 int(bool(fp64_masters)), int(down_pass))
+                 int(bool(fp64_masters)), int(down_pass), int(team))
     return d, N
 
 
@@ -324,7 +336,7 @@ def mhe_autotune(dims, A, B, Q, P0inv, l, a, x0, reps=2, stream=None):
     _check(lib().mhe_autotune(ctypes.byref(dims), ctypes.byref(m), ctypes.byref(r), _stream(stream), int(reps),
                               ctypes.byref(best), ctypes.byref(ms)), "mhe_autotune")
     return dict(leaf_len=best.leaf_len, branching=best.branching, top_len=best.top_len, down_pass=best.down_pass,
-                ms=ms.value)
+                team=best.team, ms=ms.value)
 
 
 def mhe_launch_count(ctx):
@@ -443,13 +455,13 @@ class Solver:
     """
 
     def __init__(self, nx, nw, N, prec=MHE_FP64, leaf_len=0, branching=0, top_len=0,
-                 refine_tol=0.0, max_refine=-1, stream=None, fp64_masters=False, down_pass=0):
+                 refine_tol=0.0, max_refine=-1, stream=None, fp64_masters=False, down_pass=0, team=0):
         import torch
         self.nx, self.nw = int(nx), int(nw)
         self.N = np.asarray(N, dtype=np.int64).reshape(-1)
         self.batch = int(self.N.size)
         self.dims, self._N32 = make_dims(nx, nw, self.N, prec, leaf_len, branching, top_len,
-                                         refine_tol, max_refine, fp64_masters, down_pass)
+                                         refine_tol, max_refine, fp64_masters, down_pass, team)
         self.stream = stream
         self.ctx = mhe_create(self.dims, stream)
         self.X = int(np.sum(self.N + 1))
@@ -489,6 +501,10 @@ class Solver:
         self._sizes(ny, A=A, B=B, C=C, R=R, a=a, yt=yt, wt=wt, x0=x0, P0inv=P0inv, x=x, w=w, lam=lam)
         mhe_estimate(self.ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, self.info)
         return x, w, lam
+
+    def set_graph(self, on=True):
+        """mhe_set_graph: replay each entry point's launch sequence as a CUDA graph."""
+        _check(lib().mhe_set_graph(self.ctx, int(bool(on))), "mhe_set_graph")
 
     def ip_solve(self, A, B, Q, P0inv, l, a, x0, w_lo, w_hi, mu0=0.0, mu_final=0.0, max_newton=0, out=None):
         """mhe_ip_solve: bounds w_lo <= w_t <= w_hi ([batch][nw] each) by a barrier interior-point loop whose

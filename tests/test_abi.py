@@ -220,3 +220,23 @@ def ctypes_sizeof_dims_matches_header():
     body = body[:body.index("} mhe_dims;")]
     names = re.findall(r"^\s+(?:const\s+)?(?:int|double)\*?\s+(\w+);", body, re.M)
     return names == [f[0] for f in mhe.mhe_dims._fields_]
+
+
+def test_team_width_variants_listed_and_validated(L):
+    """Every compiled shape lists its team widths, the default first; a width that
+    is not compiled for the shape is refused on the host; the registry of shapes
+    lists each shape once."""
+    shapes = mhe.shapes()
+    assert len(set(shapes)) == len(shapes)
+    for nx, nw in shapes:
+        teams = mhe.shape_teams(nx, nw)
+        assert teams and len(set(teams)) == len(teams), (nx, nw)
+        for t in teams:
+            d, _keep = mhe.make_dims(nx, nw, [40, 7], mhe.MHE_FP32_IR, team=t)
+            assert mhe.mhe_workspace_bytes(d) > 0, (nx, nw, t)
+        for t in (1, 3, 4096):
+            d, _keep = mhe.make_dims(nx, nw, [40, 7], mhe.MHE_FP32_IR, team=t)
+            assert mhe.mhe_workspace_bytes(d) == 0, (nx, nw, t)
+    assert mhe.shape_teams(6, 3) == [8, 16, 32]
+    assert mhe.shape_teams(12, 6) == [16, 32]
+    assert mhe.shape_teams(5, 5) == []

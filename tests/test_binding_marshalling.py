@@ -47,6 +47,7 @@ class Fake:
     def mhe_autotune(self, dims, m, r, stream, reps, best, ms):
         self._rec("mhe_autotune", (dims, m, r, reps))
         best._obj.leaf_len, best._obj.branching, best._obj.top_len, best._obj.down_pass = 16, 4, 3, 1
+        best._obj.team = 16
         ms._obj.value = 1.5
         return 0
 
@@ -132,7 +133,7 @@ def test_timing_autotune_assemble(fake):
     d, _ = mhe.make_dims(4, 2, [10])
     z = torch.zeros(64, dtype=torch.float64)
     r = mhe.mhe_autotune(d, z, z, z, z, z, z, z, reps=3)
-    assert r == dict(leaf_len=16, branching=4, top_len=3, down_pass=1, ms=1.5) and fake.calls["mhe_autotune"][3] == 3
+    assert r == dict(leaf_len=16, branching=4, top_len=3, down_pass=1, team=16, ms=1.5) and fake.calls["mhe_autotune"][3] == 3
     S, nx, nw, ny = 5, 4, 2, 2
     C = torch.zeros(S, ny * nx, dtype=torch.float64)
     R = torch.zeros(S * (nw + ny) ** 2, dtype=torch.float64)
