@@ -53,7 +53,9 @@ typedef enum {
     MHE_E_NO_CONVERGE = -6,   /* refinement did not reach refine_tol */
     MHE_E_TIMEOUT = -7,       /* a bounded device wait ran out */
     MHE_E_CUDA = -8,          /* a CUDA runtime call failed */
-    MHE_E_ADMISSION = -9      /* serving: request cannot be admitted */
+    MHE_E_ADMISSION = -9,     /* serving: request cannot be admitted */
+    MHE_E_BOUNDS = -10        /* the bounds-checked build (libmhe_bounds.so) found an index outside
+                                 its array; the access was not made (where: level, chunk, index) */
 } mhe_status;
 
 typedef enum {

@@ -3,6 +3,9 @@
 Every translation unit under csrc/ is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a) and linked into
 paper_1510_03110_gb300/libmhe.so.  Objects go to paper_1510_03110_gb300/_build/.
+build(bounds_check=True) makes the bounds-checked debug library
+libmhe_bounds.so (-DMHE_BOUNDS_CHECK; objects in _build_bounds/), which the
+binding loads instead when MHE_BOUNDS_CHECK=1 is set in the environment.
 """
 from __future__ import annotations
 
@@ -16,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmhe.so")
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libmhe_bounds.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "engine.cpp", "plan.cpp", "shapes_small.cu", "shapes_mid.cu",
            "shapes_big.cu", "shapes_sq.cu", "shapes_xl.cu", "shapes_xl64.cu", "shapes_n12.cu", "noalloc.cu", "serve.cu", "rts.cu", "ip.cu", "shapes_t16.cu", "shapes_t32.cu"]
@@ -36,9 +41,9 @@ def _deps_mtime() -> float:
     return t
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+def _compile(src: str, verbose: bool, bdir: str = BUILD, defines: tuple = ()) -> str:
+    obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", *defines,
            "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr"]
@@ -52,21 +57,23 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, bounds_check: bool = False) -> str:
+    lib, bdir = (LIB_BOUNDS, BUILD_BOUNDS) if bounds_check else (LIB, BUILD)
+    defines = ("-DMHE_BOUNDS_CHECK",) if bounds_check else ()
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     jobs = jobs or min(len(SOURCES), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, bdir, defines), SOURCES))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds_check="--bounds-check" in sys.argv))

@@ -95,6 +95,10 @@ struct LevelArgs {
     // one per CTA of a launch of at most gws_teams CTAs
     T* gws;
     int gws_teams;
+    // array extents, read by the bounds-checked build (MHE_BOUNDS_CHECK) only: caller
+    // stages, instances, this level's stages and states, the level above's (-1: not checked)
+    long long ext_S_in, ext_S, ext_X, ext_S_up, ext_X_up;
+    int ext_batch;
 };
 
 // Residual kernel arguments (level 0).  Reads the caller's FP64 problem and

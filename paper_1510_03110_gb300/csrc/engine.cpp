@@ -397,6 +397,14 @@ LevelArgs<T> Engine::args(int k) const
         a.Kalt0 = static_cast<T*>(Kalt0);
         a.kalt0 = static_cast<T*>(kalt0);
     }
+    // extents for the bounds-checked build (serving rings: not checked)
+    a.ext_S_in = plan.S_in;
+    a.ext_batch = plan.batch;
+    a.ext_S = use_ext ? -1 : plan.levels[k].nstages;
+    a.ext_X = use_ext ? -1 : plan.levels[k].nstates;
+    const bool up = k + 1 < (int)plan.levels.size();
+    a.ext_S_up = (use_ext || !up) ? -1 : plan.levels[k + 1].nstages;
+    a.ext_X_up = (use_ext || !up) ? -1 : plan.levels[k + 1].nstates;
     a.gws = sizeof(T) == 8 ? static_cast<T*>(gws) : nullptr;
     a.gws_teams = ops ? ops->gws_teams : 0;
     a.piv_up = (pivot && k + 1 < (int)lv.size()) ? lv[k + 1].piv : nullptr;

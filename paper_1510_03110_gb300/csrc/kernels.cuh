@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
         if (a.any_active && *a.any_active == 0) return;
         T* ws = a.gws + (size_t)blockIdx.x * op_count<T, NX, OP>();
         for (int ci = blockIdx.x; ci < a.nchunks; ci += gridDim.x) {
+            if (!chunk_in_bounds(a, ci)) continue;
             if constexpr (OP == OP_REDUCE) reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, ws);
             else if constexpr (OP == OP_RHS) rhs_chunk<T, NX, NW, UPPER != 0>(a, ci, ws);
             else down_chunk<T, NX, NW, UPPER != 0>(a, ci, ws);
@@ -134,13 +135,15 @@ __global__ void __launch_bounds__(256, level_min_blocks<T, NX, OP>()) k_level(Le
         __syncthreads();
         tc::fence_after();
         TcState tcs{*slot, mbar, xbuf, 0u, 1};
-        reduce_chunk<T, NX, NW, UPPER != 0, OP == OP_REDUCE_TC ? 1 : 2>(a, ci, sm, &tcs);
+        if (chunk_in_bounds(a, ci)) reduce_chunk<T, NX, NW, UPPER != 0, OP == OP_REDUCE_TC ? 1 : 2>(a, ci, sm, &tcs);
         // a wait that ran out: give the MMAs of that phase another bounded wait before freeing TMEM
         if (!tcs.ok) tc::mbar_wait(mbar, tcs.phase, tc::kWaitLimit);
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
         if (threadIdx.x < 32) tc::tmem_dealloc(tcs.tbase, 512);
+    } else if (!chunk_in_bounds(a, ci)) {
+        return;
     } else if (OP == OP_REDUCE) {
         reduce_chunk<T, NX, NW, UPPER != 0>(a, ci, sm);
     } else if (OP == OP_RHS) {

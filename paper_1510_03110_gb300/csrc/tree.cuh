@@ -944,6 +944,59 @@ MHE_DEV bool reduce_step(Ws<T, NX>& s, const StageRef<T>& st, T* Pout, T* Lgout,
     return bad;
 }
 
+// ---- bounds-checked build -----------------------------------------------------
+// Compiled with MHE_BOUNDS_CHECK (libmhe_bounds.so), the tree passes check each
+// chunk descriptor against the extents of the level's arrays before the chunk is
+// processed, and each caller-stage index before it is used: an index outside its
+// array records MHE_E_BOUNDS for the instance with (level, chunk, index), and the
+// chunk is skipped or the index replaced by 0, so that no access leaves its
+// array.  Extents < 0 are not checked (serving rings).  The regular build
+// compiles none of it.
+constexpr int kBoundsCode = -10;   // MHE_E_BOUNDS
+
+MHE_DEV bool in_ext(long long i, long long ext) { return ext < 0 || (i >= 0 && i < ext); }
+
+template <typename T>
+MHE_DEV long long bounds_index(const LevelArgs<T>& a, int b, long long i, long long ext)
+{
+#ifdef MHE_BOUNDS_CHECK
+    if (!in_ext(i, ext)) {
+        if (b >= 0 && b < a.ext_batch) record_error(a.status, a.where, b, kBoundsCode, a.level, -1, (int)i);
+        return 0;
+    }
+#else
+    (void)a; (void)b; (void)ext;
+#endif
+    return i;
+}
+
+// the descriptor of chunk ci within the level's extents (always true in the regular build)
+template <typename T>
+MHE_DEV bool chunk_in_bounds(const LevelArgs<T>& a, int ci)
+{
+#ifdef MHE_BOUNDS_CHECK
+    const ChunkDesc cd = a.chunks[ci];
+    if (cd.inst < 0 || cd.inst >= a.ext_batch) return false;   // no instance to report to
+    const LevelInst li = a.li[cd.inst];
+    bool out = true;
+    long long bad = 0;   // the offending index, reported in the stage field of where
+    if (cd.t0 < 0 || cd.len < 1 || cd.t0 + cd.len > li.N) bad = cd.t0;
+    else if (!in_ext(cd.g0, a.ext_S) || !in_ext(cd.g0 + cd.len - 1, a.ext_S)) bad = cd.g0;
+    else if (!in_ext(li.gx, a.ext_X) || !in_ext(li.gx + li.N, a.ext_X)) bad = li.gx;
+    else if (cd.parent >= 0 && (!in_ext(cd.parent, a.ext_S_up) || !in_ext(cd.pw, a.ext_S_up))) bad = cd.parent;
+    else if (cd.parent2 >= 0 && !in_ext(cd.parent2, a.ext_S_up)) bad = cd.parent2;
+    else if (cd.px >= 0 && !in_ext(cd.px, a.ext_X_up)) bad = cd.px;
+    else out = false;
+    if (out) {
+        if (lane_id() == 0) record_error(a.status, a.where, cd.inst, kBoundsCode, a.level, ci, (int)bad);
+        return false;
+    }
+#else
+    (void)a; (void)ci;
+#endif
+    return true;
+}
+
 // ---- stage addressing -------------------------------------------------------
 
 template <typename T, int NX, int NW>
@@ -951,8 +1004,8 @@ struct Addr {
     // level-0 stage t >= 1 of instance b
     static MHE_DEV StageRef<T> leaf(const LevelArgs<T>& a, int b, int t)
     {
-        const long long s = a.in_off[b] + t - 1;
-        const long long sr = a.rhs_off[b] + t - 1;
+        const long long s = bounds_index(a, b, a.in_off[b] + t - 1, a.ext_S_in);
+        const long long sr = bounds_index(a, b, a.rhs_off[b] + t - 1, a.ext_S_in);
         StageRef<T> r;
         r.A = a.A + s * NX * NX;
         r.B = a.B + s * NX * NW;
@@ -993,6 +1046,9 @@ template <typename T, int NX, int NW>
 MHE_DEV void prefetch_leaf(const LevelArgs<T>& a, int b, int t, int what = PF_ALL)
 {
     if (t < 1) return;
+#ifdef MHE_BOUNDS_CHECK
+    if (!in_ext(a.in_off[b] + t - 1, a.ext_S_in) || !in_ext(a.rhs_off[b] + t - 1, a.ext_S_in)) return;
+#endif
     const long long s = a.in_off[b] + t - 1;
     if (what & PF_A) prefetch_l2(a.A + s * NX * NX, (int)(sizeof(T) * NX * NX));
     if (what & PF_B) prefetch_l2(a.B + s * NX * NW, (int)(sizeof(T) * NX * NW));

@@ -16,6 +16,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmhe.so")
+# MHE_BOUNDS_CHECK=1: the bounds-checked debug build (build.build(bounds_check=True))
+if os.environ.get("MHE_BOUNDS_CHECK") == "1":
+    LIB_PATH = os.path.join(HERE, "libmhe_bounds.so")
 
 MHE_FP64 = 0
 MHE_FP32_IR = 1
@@ -24,7 +27,7 @@ MHE_BF16_IR = 3
 
 STATUS = {0: "MHE_OK", 1: "MHE_PENDING", -1: "MHE_E_ARG", -2: "MHE_E_NOMEM", -3: "MHE_E_NOT_PD",
           -4: "MHE_E_NONFINITE", -5: "MHE_E_NOT_FACTORED", -6: "MHE_E_NO_CONVERGE",
-          -7: "MHE_E_TIMEOUT", -8: "MHE_E_CUDA", -9: "MHE_E_ADMISSION"}
+          -7: "MHE_E_TIMEOUT", -8: "MHE_E_CUDA", -9: "MHE_E_ADMISSION", -10: "MHE_E_BOUNDS"}
 
 c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
 
