@@ -1054,6 +1054,9 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
     import concurrent.futures as cf
     pool = cf.ThreadPoolExecutor(len(buckets))   # one caller thread per shape bucket (ctypes drops the GIL)
 
+    for s in solvers:
+        s.set_host_in_place(bool(args.e2e_in_place))
+
     def one(i):
         bk, s, hb, (hx, info) = buckets[i], solvers[i], host[i], outs[i]
         mhe.mhe_estimate_host(s.ctx, bk["q"], hb["A"], hb["B"], hb["C"], hb["R"], hb["a"], hb["yt"], hb["wt"],
@@ -1073,6 +1076,22 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
         each.append((time.perf_counter() - t1) * 1e3)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / k
+    timeline = None
+    if args.e2e_timeline:
+        # one more step with the pipelines' timelines recorded (outside the timed steps)
+        for s in solvers:
+            mhe.mhe_timing_enable(s.ctx, True)
+        t1 = time.perf_counter()
+        e2e_step()
+        wall_tl = (time.perf_counter() - t1) * 1e3
+        timeline = dict(step_ms=round(wall_tl, 2), columns=["engine", "b0", "b1", "host_issue_ms", "h2d_issued_ms",
+                                                             "inputs_arrived_ms", "solved_ms", "outputs_back_ms"],
+                        buckets=[dict(nx=bk["n"], pieces=[[round(v, 3) for v in row]
+                                                          for row in mhe.mhe_pipe_timeline(s.ctx)])
+                                 for bk, s in zip(buckets, solvers)])
+        for s in solvers:
+            mhe.mhe_timing_enable(s.ctx, False)
+            mhe.mhe_timing_read(s.ctx)
     pool.shutdown()
     gbs = pinned_h2d_gbs()
     infos = np.concatenate([info.numpy().view(mhe.INFO_DTYPE) for _, info in outs])
@@ -1082,8 +1101,9 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
                 ms_each=[round(v, 2) for v in each], h2d_gbs_pinned=gbs,
                 h2d_floor_ms=round(h2d / (gbs * 1e6), 1),
                 relres_max=float(np.max(infos["relres"])), all_ok=bool(np.all(infos["status"] == 0)),
-                api="mhe_estimate_host (pinned host buffers), one caller thread per shape bucket",
-                timer="host wall clock around the synchronous calls")
+                api="mhe_estimate_host (pinned host buffers), one caller thread per shape bucket" +
+                    (", inputs read in place (mhe_set_host_in_place)" if args.e2e_in_place else ""),
+                timer="host wall clock around the synchronous calls", timeline=timeline)
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -1195,6 +1215,8 @@ def main():
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-pieces", type=int, default=4, help="pieces of the host-buffer pipeline per bucket")
+    ap.add_argument("--e2e-in-place", action="store_true", help="end to end: the kernels read the pinned inputs in place")
+    ap.add_argument("--e2e-timeline", action="store_true", help="end to end: record one step's pipeline timeline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--tune-instances", type=int, default=256)

@@ -220,6 +220,24 @@ int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, do
 int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info,
                       int pieces);
 
+/* mhe_estimate_host reading its inputs in place (on = 1): no host-to-device
+ * copies; each piece's kernels read the stage data from pinned host memory
+ * over the host link (the preparation pass once, the residual passes a_t,
+ * x~0 and P~0^{-1} again), and only the outputs are copied back.  Every input
+ * must then be in pinned (page-locked, mapped) host memory, else
+ * mhe_estimate_host returns MHE_E_ARG.  on = 0 (default): the copy engines
+ * move each piece's inputs to device buffers.  Errors: MHE_E_ARG (ctx NULL). */
+int mhe_set_host_in_place(mhe_ctx* ctx, int on);
+
+/* The timeline of the last mhe_estimate_host call made with timing enabled
+ * (mhe_timing_enable): per piece 8 values -- engine, first and last + 1
+ * instance, the host's time of issue (ms after the call began), and the device
+ * times (ms after the call's start event) at which its input copies were
+ * issued, its inputs had arrived, its solve had finished, its outputs were
+ * back (-1 where not available).  Writes up to cap pieces into out [cap][8],
+ * returns the number of pieces.  A profiling aid. */
+int mhe_pipe_timeline(mhe_ctx* ctx, double* out, int cap);
+
 /* Shapes (nx, nw) compiled into this library: writes up to cap pairs into
  * nx_out / nw_out and returns the number available. */
 int mhe_shapes(int* nx_out, int* nw_out, int cap);

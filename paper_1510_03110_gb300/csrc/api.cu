@@ -5,6 +5,7 @@
 
 #include <mutex>
 #include <new>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -65,16 +66,40 @@ struct HostPipe {
     bool used[NE] = {};
     Buf in[NE][9];    // A B C R a y~ w~ x~0 P~0^{-1}
     Buf out[NE][3];   // x w lambda
+    void* stage[NE] = {};      // pinned staging of each engine's plan uploads
+    size_t stage_bytes[NE] = {};
+    // timeline of the last call (with timing enabled): per piece its engine, instances,
+    // host issue time and four events (inputs issued, inputs arrived, solved, outputs back)
+    struct Piece {
+        int e, b0, b1;
+        double host_ms;
+        cudaEvent_t ev[4];
+    };
+    std::vector<Piece> line;
+    cudaEvent_t t0 = nullptr;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    cudaEvent_t ev()
+    {
+        if (evused == evpool.size()) {
+            cudaEvent_t v;
+            cudaEventCreate(&v);
+            evpool.push_back(v);
+        }
+        return evpool[evused++];
+    }
     ~HostPipe()
     {
         for (int e = 0; e < NE; ++e) {
             if (st[e]) cudaStreamSynchronize(st[e]);
+            if (stage[e]) cudaFreeHost(stage[e]);
             if (inited[e]) eng[e].release();
             for (auto& b : in[e]) if (b.p) cudaFree(b.p);
             for (auto& b : out[e]) if (b.p) cudaFree(b.p);
             if (done[e]) cudaEventDestroy(done[e]);
             if (st[e]) cudaStreamDestroy(st[e]);
         }
+        for (auto v : evpool) cudaEventDestroy(v);
     }
 };
 
@@ -108,6 +133,7 @@ struct mhe_ctx {
     HostPipe* pipe = nullptr;
     bool graph_on = false;
     GraphCache graph[5];              // per entry point (index 1..4)
+    bool host_in_place = false;       // mhe_estimate_host: kernels read the pinned inputs in place
 };
 
 namespace {
@@ -472,6 +498,34 @@ int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, do
                        });
 }
 
+int mhe_pipe_timeline(mhe_ctx* ctx, double* out, int cap)
+{
+    if (!ctx || (!out && cap > 0)) return fail(MHE_E_ARG, "ctx or out is NULL");
+    if (!ctx->pipe) return 0;
+    HostPipe& hp = *ctx->pipe;
+    int k = 0;
+    for (auto& pc : hp.line) {
+        if (k < cap) {
+            double* o = out + 8 * k;
+            o[0] = pc.e; o[1] = pc.b0; o[2] = pc.b1; o[3] = pc.host_ms;
+            for (int i = 0; i < 4; ++i) {
+                float ms = -1.f;
+                if (cudaEventElapsedTime(&ms, hp.t0, pc.ev[i]) != cudaSuccess) { cudaGetLastError(); ms = -1.f; }
+                o[4 + i] = ms;
+            }
+        }
+        ++k;
+    }
+    return k;
+}
+
+int mhe_set_host_in_place(mhe_ctx* ctx, int on)
+{
+    if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
+    ctx->host_in_place = on != 0;
+    return MHE_OK;
+}
+
 int mhe_set_graph(mhe_ctx* ctx, int on)
 {
     if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
@@ -526,6 +580,29 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
         ctx->pipe = hp;
     }
     HostPipe& hp = *ctx->pipe;
+    // in-place reads: the device address of every input (pinned host memory, mapped)
+    const double* dsrc[9] = {prob->A, prob->B, prob->C, prob->R, prob->a, prob->yt, prob->wt, prob->x0, prob->P0inv};
+    if (ctx->host_in_place)
+        for (int i = 0; i < 9; ++i) {
+            if (!dsrc[i]) continue;
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, dsrc[i]) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+                !at.devicePointer) {
+                cudaGetLastError();
+                return fail(MHE_E_ARG, "in-place reads need every input in pinned host memory");
+            }
+            dsrc[i] = static_cast<const double*>(at.devicePointer);
+        }
+    // the timeline of this call (timing enabled): a start event on every engine's stream
+    const bool tl = ctx->eng.mark_user != nullptr;
+    const auto h0 = std::chrono::steady_clock::now();
+    hp.line.clear();
+    hp.evused = 0;
+    if (tl) {
+        hp.t0 = hp.ev();
+        cudaEventRecord(hp.t0, hp.st[0]);
+        for (int e = 1; e < HostPipe::NE; ++e) cudaStreamWaitEvent(hp.st[e], hp.t0, 0);
+    }
     // pieces of consecutive instances with about equal stage counts
     std::vector<int> cut(1, 0);
     const long long per = (P.S_in + P.batch) / pieces + 1;
@@ -549,6 +626,7 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             W += n + (long long)(P.N[b] - 1) * m;
         }
         if (!hp.inited[e]) {
+            hp.eng[e].upload_stage = nullptr;   // the first plan is uploaded synchronously
             mhe_dims d;
             memset(&d, 0, sizeof(d));
             d.nx = n; d.nw = m; d.batch = cnt; d.N = P.N.data() + b0; d.prec = E.prec;
@@ -563,6 +641,18 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             rc = hp.eng[e].replan(P.N.data() + b0, cnt, nullptr);
             if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
         }
+        // pinned staging for the next plan upload of this engine, grown to what this one wanted
+        // (engine e's stream has passed its previous uploads: done[e] was waited for above)
+        if (hp.eng[e].upload_need > hp.stage_bytes[e]) {
+            if (hp.stage[e]) cudaFreeHost(hp.stage[e]);
+            hp.stage[e] = nullptr;
+            hp.stage_bytes[e] = 0;
+            const size_t want = hp.eng[e].upload_need + hp.eng[e].upload_need / 4;
+            if (cudaHostAlloc(&hp.stage[e], want, cudaHostAllocDefault) == cudaSuccess) hp.stage_bytes[e] = want;
+            else { hp.stage[e] = nullptr; cudaGetLastError(); }
+            hp.eng[e].upload_stage = hp.stage[e];
+            hp.eng[e].upload_stage_bytes = hp.stage_bytes[e];
+        }
         const size_t sz_in[9] = {(size_t)S * n * n, (size_t)S * n * m, (size_t)S * q * n, (size_t)S * R,
                                  (size_t)S * n, (size_t)S * q, (size_t)S * m, (size_t)cnt * n,
                                  (size_t)cnt * n * n};
@@ -570,28 +660,49 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
                                 prob->a + s0 * n, prob->yt + s0 * q, prob->wt + s0 * m, prob->x0 + (long long)b0 * n,
                                 prob->P0inv + (long long)b0 * n * n};
         const size_t sz_out[3] = {(size_t)X * n, (size_t)W, (size_t)X * n};
-        for (int i = 0; i < 9 && rc == MHE_OK; ++i)
+        for (int i = 0; i < 9 && rc == MHE_OK && !ctx->host_in_place; ++i)
             if (reserve_buf(hp.in[e][i], sizeof(double) * sz_in[i]) != 0) rc = MHE_E_NOMEM;
         for (int i = 0; i < 3 && rc == MHE_OK; ++i)
             if (reserve_buf(hp.out[e][i], sizeof(double) * sz_out[i]) != 0) rc = MHE_E_NOMEM;
         if (rc != MHE_OK) { g_err = "device allocation of a pipeline buffer failed"; break; }
-        for (int i = 0; i < 9; ++i)
-            if (sz_in[i] > 0)
-                cudaMemcpyAsync(hp.in[e][i].p, src[i], sizeof(double) * sz_in[i], cudaMemcpyHostToDevice, hp.st[e]);
+        HostPipe::Piece pc{e, b0, b1, 0.0, {}};
+        if (tl) {
+            pc.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+            for (auto& v : pc.ev) v = hp.ev();
+            cudaEventRecord(pc.ev[0], hp.st[e]);
+        }
+        const double* in[9];
+        if (ctx->host_in_place) {
+            // the piece's inputs where they are: its kernels read host memory over the
+            // host link, and no copy is made
+            const long long off[9] = {s0 * n * n, s0 * n * m, s0 * q * n, s0 * R, s0 * n, s0 * q, s0 * m,
+                                      (long long)b0 * n, (long long)b0 * n * n};
+            for (int i = 0; i < 9; ++i) in[i] = dsrc[i] ? dsrc[i] + off[i] : nullptr;
+        } else {
+            for (int i = 0; i < 9; ++i) {
+                if (sz_in[i] > 0)
+                    cudaMemcpyAsync(hp.in[e][i].p, src[i], sizeof(double) * sz_in[i], cudaMemcpyHostToDevice,
+                                    hp.st[e]);
+                in[i] = (const double*)hp.in[e][i].p;
+            }
+        }
+        if (tl) cudaEventRecord(pc.ev[1], hp.st[e]);
         mhe_problem dp;
         dp.ny = q;
-        dp.A = (const double*)hp.in[e][0].p; dp.B = (const double*)hp.in[e][1].p;
-        dp.C = (const double*)hp.in[e][2].p; dp.R = (const double*)hp.in[e][3].p;
-        dp.a = (const double*)hp.in[e][4].p; dp.yt = (const double*)hp.in[e][5].p;
-        dp.wt = (const double*)hp.in[e][6].p; dp.x0 = (const double*)hp.in[e][7].p;
-        dp.P0inv = (const double*)hp.in[e][8].p;
+        dp.A = in[0]; dp.B = in[1]; dp.C = in[2]; dp.R = in[3]; dp.a = in[4]; dp.yt = in[5]; dp.wt = in[6];
+        dp.x0 = in[7]; dp.P0inv = in[8];
         rc = hp.eng[e].estimate(dp, (double*)hp.out[e][0].p, (double*)hp.out[e][1].p, (double*)hp.out[e][2].p,
                                 info ? info + b0 : nullptr);
         if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
+        if (tl) cudaEventRecord(pc.ev[2], hp.st[e]);
         cudaMemcpyAsync(x + x0s * n, hp.out[e][0].p, sizeof(double) * sz_out[0], cudaMemcpyDeviceToHost, hp.st[e]);
         cudaMemcpyAsync(w + w0, hp.out[e][1].p, sizeof(double) * sz_out[1], cudaMemcpyDeviceToHost, hp.st[e]);
         cudaMemcpyAsync(lam + x0s * n, hp.out[e][2].p, sizeof(double) * sz_out[2], cudaMemcpyDeviceToHost, hp.st[e]);
         cudaEventRecord(hp.done[e], hp.st[e]);
+        if (tl) {
+            cudaEventRecord(pc.ev[3], hp.st[e]);
+            hp.line.push_back(pc);
+        }
         hp.used[e] = true;
     }
     for (int e = 0; e < HostPipe::NE; ++e)

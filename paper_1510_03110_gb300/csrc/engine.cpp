@@ -194,16 +194,41 @@ int Engine::init(const mhe_dims& d, const ShapeOps* o, const Runtime* r, void* s
 
 int Engine::upload_plan()
 {
+    // every host array of the plan with its device destination
+    struct Piece {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    };
+    std::vector<Piece> pcs;
     for (size_t k = 0; k < plan.levels.size(); ++k) {
         const PlanLevel& L = plan.levels[k];
-        if (!L.chunks.empty())
-            rt->copy(lv[k].chunks, L.chunks.data(), L.chunks.size() * sizeof(ChunkDesc), stream);
-        rt->copy(lv[k].li, L.li.data(), L.li.size() * sizeof(LevelInst), stream);
+        if (!L.chunks.empty()) pcs.push_back({lv[k].chunks, L.chunks.data(), L.chunks.size() * sizeof(ChunkDesc)});
+        pcs.push_back({lv[k].li, L.li.data(), L.li.size() * sizeof(LevelInst)});
     }
-    rt->copy(in_off, plan.in_off.data(), plan.in_off.size() * sizeof(long long), stream);
-    rt->copy(cmp_off, plan.cmp_off.data(), plan.cmp_off.size() * sizeof(long long), stream);
-    rt->copy(w_off, plan.w_off.data(), plan.w_off.size() * sizeof(long long), stream);
-    rt->copy(gs0, plan.gs0.data(), plan.gs0.size() * sizeof(long long), stream);
+    pcs.push_back({in_off, plan.in_off.data(), plan.in_off.size() * sizeof(long long)});
+    pcs.push_back({cmp_off, plan.cmp_off.data(), plan.cmp_off.size() * sizeof(long long)});
+    pcs.push_back({w_off, plan.w_off.data(), plan.w_off.size() * sizeof(long long)});
+    pcs.push_back({gs0, plan.gs0.data(), plan.gs0.size() * sizeof(long long)});
+    if (use_ext)   // serving with reuse: the chunks each level reduces again
+        for (size_t k = 0; k < rlist.size() && k < lv.size(); ++k)
+            if (!rlist[k].empty()) pcs.push_back({lv[k].rchunks, rlist[k].data(), rlist[k].size() * sizeof(ChunkDesc)});
+    size_t need = 0;
+    for (const Piece& p : pcs) need += (p.bytes + 15) & ~(size_t)15;
+    upload_need = need;
+    if (upload_stage && need <= upload_stage_bytes) {
+        // through the caller's pinned staging buffer: the copies are asynchronous and
+        // queue on the stream without holding the host (a copy from pageable memory
+        // waits for every copy queued before it on the device, other streams' too)
+        char* st = static_cast<char*>(upload_stage);
+        for (const Piece& p : pcs) {
+            memcpy(st, p.src, p.bytes);
+            rt->copy(p.dst, st, p.bytes, stream);
+            st += (p.bytes + 15) & ~(size_t)15;
+        }
+        return MHE_OK;
+    }
+    for (const Piece& p : pcs) rt->copy(p.dst, p.src, p.bytes, stream);
     if (rt->sync(stream) != 0) { err = "CUDA error while uploading the plan"; return MHE_E_CUDA; }
     return MHE_OK;
 }
@@ -254,9 +279,7 @@ int Engine::replan_serve(const std::vector<ServeWindow>& w, const ExtStores& st,
         arena_bytes = need + need / 4;
     }
     layout(static_cast<char*>(arena));
-    for (size_t k = 0; k < rlist.size() && k < lv.size(); ++k)
-        if (!rlist[k].empty()) rt->copy(lv[k].rchunks, rlist[k].data(), rlist[k].size() * sizeof(ChunkDesc), stream);
-    return upload_plan();
+    return upload_plan();   // with the reduction's chunk lists (rlist)
 }
 
 int Engine::solve_resident_reuse(const Resident& r, double* x, double* w, double* lam, mhe_info* info)

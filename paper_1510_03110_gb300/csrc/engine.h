@@ -172,6 +172,12 @@ public:
     void* mark_user = nullptr;          // non-null: record per-pass timing marks
     long long launches = 0;             // kernels launched by this context so far
     long long alloc_gen = 0;            // device allocations made so far (a captured graph holds their addresses)
+    // optional pinned host buffer (caller-owned) through which the plan is uploaded
+    // asynchronously; the caller keeps it untouched until the stream has passed the
+    // uploads.  upload_need: the bytes the last upload wanted
+    void* upload_stage = nullptr;
+    size_t upload_stage_bytes = 0;
+    size_t upload_need = 0;
     bool factored = false;
     std::string err;
 

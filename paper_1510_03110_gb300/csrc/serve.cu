@@ -180,6 +180,9 @@ struct Bucket {
         int rc = 0;   // launch status of the round in flight
         long long *s1 = nullptr, *s2 = nullptr;
         double* h_stage = nullptr;       // pinned staging of the new stages
+        char* h_meta = nullptr;          // pinned staging of the round's index arrays
+        void* h_plan = nullptr;          // pinned staging of the round's plan upload
+        size_t h_plan_bytes = 0;
         double* h_res = nullptr;         // pinned results
         mhe_info* h_info = nullptr;
         mhe_info* d_info = nullptr;
@@ -345,6 +348,9 @@ bool grow_stores(mhe_server* s, Bucket& b, const std::vector<long long>& need)
     return true;
 }
 
+// pinned bytes of a round's index arrays (s1, s2, est_slot, gx, N) for `batch` members
+size_t meta_bytes(size_t batch) { return 3 * (sizeof(long long) * batch + 16) + 2 * (sizeof(int) * batch + 16); }
+
 // round buffers of one engine slot for `batch` members, S new stages, X states, W inputs
 bool ensure_slot(mhe_server* s, Bucket& bk, Bucket::Slot& sl, size_t batch, size_t X, size_t W)
 {
@@ -358,7 +364,7 @@ bool ensure_slot(mhe_server* s, Bucket& bk, Bucket::Slot& sl, size_t batch, size
     cudaFree(sl.stage_in); cudaFree(sl.Qn); cudaFree(sl.ln); cudaFree(sl.An); cudaFree(sl.Bn); cudaFree(sl.an);
     cudaFree(sl.Cn); cudaFree(sl.Rn); cudaFree(sl.yn); cudaFree(sl.wn);
     cudaFree(sl.s1); cudaFree(sl.s2); cudaFree(sl.d_info);
-    cudaFreeHost(sl.h_stage); cudaFreeHost(sl.h_res); cudaFreeHost(sl.h_info);
+    cudaFreeHost(sl.h_stage); cudaFreeHost(sl.h_res); cudaFreeHost(sl.h_info); cudaFreeHost(sl.h_meta);
     batch = batch * 2 + 16;
     X = X * 2 + 64;
     W = W * 2 + 64;
@@ -390,12 +396,13 @@ bool ensure_slot(mhe_server* s, Bucket& bk, Bucket::Slot& sl, size_t batch, size
     cudaHostAlloc(&sl.h_stage, sizeof(double) * batch * stage_doubles(n, m, q), cudaHostAllocDefault);
     cudaHostAlloc(&sl.h_res, sizeof(double) * batch * n, cudaHostAllocDefault);
     cudaHostAlloc(&sl.h_info, sizeof(mhe_info) * batch, cudaHostAllocDefault);
+    cudaHostAlloc(reinterpret_cast<void**>(&sl.h_meta), meta_bytes(batch), cudaHostAllocDefault);
     sl.cap_batch = batch;
     sl.cap_X = X;
     sl.cap_W = W;
     s->used += u;
     return sl.x && sl.w && sl.lam && sl.stage_in && sl.Cn && sl.Rn && sl.yn && sl.wn && sl.h_stage && sl.h_res &&
-           sl.h_info && sl.d_info;
+           sl.h_info && sl.d_info && sl.h_meta;
 }
 
 // launch one round of bucket bk on engine slot sl for the estimators in sl.ests
@@ -448,8 +455,19 @@ int launch_round(mhe_server* s, Bucket& bk, Bucket::Slot& sl)
         win[b].hist = &e.hist;
         stages += e.N;
     }
+    // the plan goes up through the slot's pinned staging (its previous round has completed)
+    sl.eng.upload_stage = sl.h_plan;
+    sl.eng.upload_stage_bytes = sl.h_plan_bytes;
     int rc = sl.eng.replan_serve(win, bk.st, &reduced);
     if (rc != MHE_OK) return rc;
+    if (sl.eng.upload_need > sl.h_plan_bytes) {   // uploaded synchronously this time: grow the staging
+        cudaFreeHost(sl.h_plan);
+        sl.h_plan = nullptr;
+        sl.h_plan_bytes = 0;
+        const size_t want = sl.eng.upload_need * 2 + 4096;
+        if (cudaHostAlloc(&sl.h_plan, want, cudaHostAllocDefault) == cudaSuccess) sl.h_plan_bytes = want;
+        else { sl.h_plan = nullptr; cudaGetLastError(); }
+    }
     {
         std::lock_guard<std::mutex> lock(s->mu);
         s->n_rounds += 1;
@@ -461,11 +479,19 @@ int launch_round(mhe_server* s, Bucket& bk, Bucket::Slot& sl)
     for (int b = 0; b < batch; ++b) memcpy(sl.h_stage + (size_t)b * sd, sl.reqs[b].stage.data(), sizeof(double) * sd);
     cudaStream_t st = sl.stream;
     cudaMemcpyAsync(sl.stage_in, sl.h_stage, sizeof(double) * sd * batch, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(sl.s1, s1.data(), sizeof(long long) * batch, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(sl.s2, s2.data(), sizeof(long long) * batch, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(sl.est_slot, eslot.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(sl.gxd, gx.data(), sizeof(long long) * batch, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(sl.Nd, Nv.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, st);
+    {   // the index arrays through pinned staging: asynchronous, no wait behind other streams' copies
+        char* hm = sl.h_meta;
+        auto up = [&](void* dst, const void* src, size_t bytes) {
+            memcpy(hm, src, bytes);
+            cudaMemcpyAsync(dst, hm, bytes, cudaMemcpyHostToDevice, st);
+            hm += (bytes + 15) & ~(size_t)15;
+        };
+        up(sl.s1, s1.data(), sizeof(long long) * batch);
+        up(sl.s2, s2.data(), sizeof(long long) * batch);
+        up(sl.est_slot, eslot.data(), sizeof(int) * batch);
+        up(sl.gxd, gx.data(), sizeof(long long) * batch);
+        up(sl.Nd, Nv.data(), sizeof(int) * batch);
+    }
     // split the packed MHE stages [A | B | C | R | a | y~ | w~] into per-field arrays
     const size_t oA = 0, oB = oA + n * n, oC = oB + n * m, oR = oC + q * n, oa = oR + (m + q) * (m + q),
                  oy = oa + n, ow = oy + q;
@@ -537,6 +563,8 @@ void worker_loop(mhe_server* s)
                 if (sl.busy) {
                     // a round in flight: complete it once its event has fired
                     if (cudaEventQuery(sl.done) == cudaSuccess || sl.rc != MHE_OK) {
+                        // a failed launch: nothing of it may still read the slot's staging
+                        if (sl.rc != MHE_OK) cudaStreamSynchronize(sl.stream);
                         complete_round(s, bk, sl, sl.rc);
                         progress = true;
                         s->cv.notify_all();
@@ -831,7 +859,8 @@ int mhe_server_destroy(mhe_server* s)
             cudaFree(sl.stage_in); cudaFree(sl.Qn); cudaFree(sl.ln); cudaFree(sl.An); cudaFree(sl.Bn);
             cudaFree(sl.an); cudaFree(sl.Cn); cudaFree(sl.Rn); cudaFree(sl.yn); cudaFree(sl.wn);
             cudaFree(sl.s1); cudaFree(sl.s2); cudaFree(sl.d_info);
-            cudaFreeHost(sl.h_stage); cudaFreeHost(sl.h_res); cudaFreeHost(sl.h_info);
+            cudaFreeHost(sl.h_stage); cudaFreeHost(sl.h_res); cudaFreeHost(sl.h_info); cudaFreeHost(sl.h_meta);
+            cudaFreeHost(sl.h_plan);
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
         }

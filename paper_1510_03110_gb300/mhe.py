@@ -106,6 +106,10 @@ def _declare(L):
     L.mhe_launch_count.restype = c_ll
     L.mhe_assemble_count.argtypes = []
     L.mhe_assemble_count.restype = c_ll
+    L.mhe_pipe_timeline.argtypes = [c_void_p, P(c_double), c_int]
+    L.mhe_pipe_timeline.restype = c_int
+    L.mhe_set_host_in_place.argtypes = [c_void_p, c_int]
+    L.mhe_set_host_in_place.restype = c_int
     L.mhe_set_graph.argtypes = [c_void_p, c_int]
     L.mhe_set_graph.restype = c_int
     L.mhe_ip_solve.argtypes = [c_void_p, P(mhe_matrices), P(mhe_rhs), P(mhe_ip_opts), c_void_p, c_void_p, c_void_p,
@@ -342,6 +346,16 @@ def mhe_autotune(dims, A, B, Q, P0inv, l, a, x0, reps=2, stream=None):
                 team=best.team, ms=ms.value)
 
 
+def mhe_pipe_timeline(ctx, cap=256):
+    """mhe_pipe_timeline: per piece (engine, b0, b1, host issue ms, inputs issued, inputs arrived, solved,
+    outputs back) of the last mhe_estimate_host call made with timing enabled."""
+    out = (c_double * (8 * cap))()
+    k = lib().mhe_pipe_timeline(ctx, out, cap)
+    if k < 0:
+        raise MheError(k, "mhe_pipe_timeline")
+    return [tuple(out[8 * i:8 * i + 8]) for i in range(min(k, cap))]
+
+
 def mhe_launch_count(ctx):
     return int(lib().mhe_launch_count(ctx))
 
@@ -504,6 +518,10 @@ class Solver:
         self._sizes(ny, A=A, B=B, C=C, R=R, a=a, yt=yt, wt=wt, x0=x0, P0inv=P0inv, x=x, w=w, lam=lam)
         mhe_estimate(self.ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, self.info)
         return x, w, lam
+
+    def set_host_in_place(self, on=True):
+        """mhe_set_host_in_place: mhe_estimate_host reads pinned host inputs in place (no copies)."""
+        _check(lib().mhe_set_host_in_place(self.ctx, int(bool(on))), "mhe_set_host_in_place")
 
     def set_graph(self, on=True):
         """mhe_set_graph: replay each entry point's launch sequence as a CUDA graph."""
