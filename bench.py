@@ -20,6 +20,11 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+# the host pipeline of the end-to-end arm runs a stream per piece and shape bucket (up to
+# ~30): give them as many hardware work queues as the device offers, so that streams do
+# not share a queue and wait on each other's unrelated work (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import statistics
 import subprocess
 import sys
@@ -1057,13 +1062,34 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
     for s in solvers:
         s.set_host_in_place(bool(args.e2e_in_place))
 
+    calls = {}   # per bucket: host times (s) at which its call began and returned
+
     def one(i):
         bk, s, hb, (hx, info) = buckets[i], solvers[i], host[i], outs[i]
+        t_in = time.perf_counter()
         mhe.mhe_estimate_host(s.ctx, bk["q"], hb["A"], hb["B"], hb["C"], hb["R"], hb["a"], hb["yt"], hb["wt"],
                               hb["x0"], hb["P0inv"], hx[0], hx[1], hx[2], info, pieces=args.e2e_pieces)
+        calls[i] = (t_in, time.perf_counter())
+
+    # one host thread: every bucket's pipeline issued (the largest first), then each waited on
+    order = sorted(range(len(buckets)), key=lambda i: -int(np.sum(buckets[i]["N"])) * buckets[i]["n"] ** 2)
+
+    def e2e_step_one_thread():
+        t_in = time.perf_counter()
+        for i in order:
+            bk, s, hb, (hx, info) = buckets[i], solvers[i], host[i], outs[i]
+            mhe.mhe_estimate_host_async(s.ctx, bk["q"], hb["A"], hb["B"], hb["C"], hb["R"], hb["a"], hb["yt"],
+                                        hb["wt"], hb["x0"], hb["P0inv"], hx[0], hx[1], hx[2], info,
+                                        pieces=args.e2e_pieces)
+        for i in order:
+            mhe.mhe_estimate_host_wait(solvers[i].ctx)
+            calls[i] = (t_in, time.perf_counter())
 
     def e2e_step():
-        list(pool.map(one, range(len(buckets))))
+        if args.e2e_threads == "one":
+            e2e_step_one_thread()
+        else:
+            list(pool.map(one, range(len(buckets))))
 
     for _ in range(2):   # warm-up: the pipeline's engines and device buffers, the pinned pages
         e2e_step()
@@ -1078,17 +1104,28 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
     ms = (time.perf_counter() - t0) * 1e3 / k
     timeline = None
     if args.e2e_timeline:
-        # one more step with the pipelines' timelines recorded (outside the timed steps)
+        # more steps with the pipelines' timelines recorded (outside the timed steps): per step the
+        # host window of each bucket's call and the device time its last output arrived; the
+        # pieces of the slowest step
         for s in solvers:
             mhe.mhe_timing_enable(s.ctx, True)
-        t1 = time.perf_counter()
-        e2e_step()
-        wall_tl = (time.perf_counter() - t1) * 1e3
-        timeline = dict(step_ms=round(wall_tl, 2), columns=["engine", "b0", "b1", "host_issue_ms", "h2d_issued_ms",
-                                                             "inputs_arrived_ms", "solved_ms", "outputs_back_ms"],
-                        buckets=[dict(nx=bk["n"], pieces=[[round(v, 3) for v in row]
-                                                          for row in mhe.mhe_pipe_timeline(s.ctx)])
-                                 for bk, s in zip(buckets, solvers)])
+        steps_tl, worst = [], None
+        for _ in range(k):
+            t1 = time.perf_counter()
+            e2e_step()
+            wall_tl = (time.perf_counter() - t1) * 1e3
+            host_calls = {buckets[i]["n"]: [round((a - t1) * 1e3, 2), round((b - t1) * 1e3, 2)]
+                          for i, (a, b) in calls.items()}
+            pieces = {bk["n"]: mhe.mhe_pipe_timeline(s.ctx) for bk, s in zip(buckets, solvers)}
+            steps_tl.append(dict(step_ms=round(wall_tl, 2), host_calls_ms=host_calls,
+                                 device_last_out_ms={n: round(max(r[7] for r in p), 2) for n, p in pieces.items() if p}))
+            if worst is None or wall_tl > worst[0]:
+                worst = (wall_tl, pieces)
+        timeline = dict(steps=steps_tl, columns=["engine", "b0", "b1", "host_issue_ms", "h2d_issued_ms",
+                                                 "inputs_arrived_ms", "solved_ms", "outputs_back_ms"],
+                        slowest=dict(step_ms=round(worst[0], 2),
+                                     buckets=[dict(nx=n, pieces=[[round(v, 3) for v in row] for row in p])
+                                              for n, p in worst[1].items()]))
         for s in solvers:
             mhe.mhe_timing_enable(s.ctx, False)
             mhe.mhe_timing_read(s.ctx)
@@ -1101,7 +1138,10 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
                 ms_each=[round(v, 2) for v in each], h2d_gbs_pinned=gbs,
                 h2d_floor_ms=round(h2d / (gbs * 1e6), 1),
                 relres_max=float(np.max(infos["relres"])), all_ok=bool(np.all(infos["status"] == 0)),
-                api="mhe_estimate_host (pinned host buffers), one caller thread per shape bucket" +
+                api=("mhe_estimate_host (pinned host buffers), one caller thread per shape bucket"
+                     if args.e2e_threads == "bucket" else
+                     "mhe_estimate_host_async for every shape bucket, then mhe_estimate_host_wait (pinned host "
+                     "buffers), one caller thread") +
                     (", inputs read in place (mhe_set_host_in_place)" if args.e2e_in_place else ""),
                 timer="host wall clock around the synchronous calls", timeline=timeline)
 
@@ -1215,6 +1255,8 @@ def main():
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-pieces", type=int, default=4, help="pieces of the host-buffer pipeline per bucket")
+    ap.add_argument("--e2e-threads", choices=["one", "bucket"], default="one",
+                    help="end to end: one host thread issuing every bucket's pipeline, or a thread per bucket")
     ap.add_argument("--e2e-in-place", action="store_true", help="end to end: the kernels read the pinned inputs in place")
     ap.add_argument("--e2e-timeline", action="store_true", help="end to end: record one step's pipeline timeline")
     ap.add_argument("--no-cpu", action="store_true")

@@ -209,16 +209,36 @@ int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, do
 
 /* mhe_estimate with the problem and the outputs in HOST memory (page-locked
  * memory lets the copies run asynchronously).  The batch is cut into `pieces`
- * runs of consecutive instances with about equal stage counts; three engines
- * on three streams of their own take the pieces in turn, so the host-to-device
- * copies of the next two pieces overlap the solve of one and the device-to-host
- * copy of the one before.  Inputs: an mhe_problem of host pointers, the same layout; outputs
- * x, w, lam as mhe_solve (host); info [batch] host or NULL.  Synchronous: returns
- * when every output has arrived.  The pipeline's engines and device buffers
- * (about 3/pieces of the whole batch's) are kept by the context for the next
- * call and freed by mhe_destroy.  Errors: MHE_E_ARG, MHE_E_NOMEM, MHE_E_CUDA. */
+ * runs of consecutive instances with about equal stage counts; up to sixteen
+ * engines on streams of their own take them (piece k on engine k mod 16): with
+ * at most sixteen pieces all are issued at once, so the host-to-device copies of
+ * the later pieces overlap the solves of the earlier ones and the
+ * device-to-host copies follow each solve.  Inputs: an mhe_problem of host
+ * pointers, the same layout; outputs x, w, lam as mhe_solve (host); info
+ * [batch] host or NULL.  Synchronous: returns when every output has arrived.
+ * The input copies of all pieces go through one stream in piece order (the
+ * copy engine then runs them back to back); each piece's solve and output copy
+ * run on its engine's stream.  Every stream takes one of the device's hardware
+ * work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 by default): a process that runs
+ * several pipelines at once should raise it (up to 32) to cover their 1 +
+ * min(pieces, 16) streams each, else streams share queues and wait on each
+ * other's work.  The pipeline's engines and device buffers (about
+ * min(pieces, 16)/pieces of the whole batch's) are kept by the context for the
+ * next call and freed by mhe_destroy.  Errors: MHE_E_ARG, MHE_E_NOMEM,
+ * MHE_E_CUDA. */
 int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info,
                       int pieces);
+
+/* mhe_estimate_host in two halves: _async issues every piece (copies, solves,
+ * output copies) and returns without waiting -- the host buffers must stay
+ * untouched until the wait; _wait blocks until the context's pipeline has
+ * finished and reports a CUDA error of it.  One host thread can so run the
+ * pipelines of several contexts at once (issue all, then wait on each).
+ * mhe_estimate_host = _async + _wait.  Errors as mhe_estimate_host; _async
+ * returns host-side errors at once. */
+int mhe_estimate_host_async(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam,
+                            mhe_info* info, int pieces);
+int mhe_estimate_host_wait(mhe_ctx* ctx);
 
 /* mhe_estimate_host reading its inputs in place (on = 1): no host-to-device
  * copies; each piece's kernels read the stage data from pinned host memory

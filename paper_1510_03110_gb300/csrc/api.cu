@@ -49,12 +49,13 @@ struct PassTiming {
     }
 };
 
-// Host-buffer pipeline of mhe_estimate_host: three engines on three streams take
-// the pieces of the batch in turn; each has its device copies of a piece's
-// inputs and outputs.
+// Host-buffer pipeline of mhe_estimate_host: up to NE engines on streams of their
+// own take the pieces of the batch (piece k on engine k mod NE); each has its
+// device copies of a piece's inputs and outputs.  With at most NE pieces every
+// piece is issued at once and no host thread waits between them: the copies of
+// piece k + 1 run while piece k solves, in the order the copy engine takes them.
 struct HostPipe {
-    // pieces in flight: the copies of piece k + 1 and k + 2 run while piece k solves
-    static constexpr int NE = 3;
+    static constexpr int NE = 16;
     struct Buf {
         void* p = nullptr;
         size_t bytes = 0;
@@ -62,8 +63,14 @@ struct HostPipe {
     mhe::Engine eng[NE];
     cudaStream_t st[NE] = {};
     cudaEvent_t done[NE] = {};
+    // the input copies of every piece on one stream, in piece order: the copy engine then
+    // streams them back to back at the full host-link rate (copies interleaved from many
+    // streams were measured to reach a fraction of it); each piece's solve waits on its own
+    cudaStream_t cst = nullptr;
+    cudaEvent_t arrived[NE] = {};
     bool inited[NE] = {};
     bool used[NE] = {};
+    int last_b0[NE] = {}, last_b1[NE] = {};   // the instances of the plan each engine holds
     Buf in[NE][9];    // A B C R a y~ w~ x~0 P~0^{-1}
     Buf out[NE][3];   // x w lambda
     void* stage[NE] = {};      // pinned staging of each engine's plan uploads
@@ -100,6 +107,12 @@ struct HostPipe {
             if (st[e]) cudaStreamDestroy(st[e]);
         }
         for (auto v : evpool) cudaEventDestroy(v);
+        if (cst) {
+            cudaStreamSynchronize(cst);
+            cudaStreamDestroy(cst);
+        }
+        for (auto v : arrived)
+            if (v) cudaEventDestroy(v);
     }
 };
 
@@ -556,6 +569,28 @@ int reserve_buf(HostPipe::Buf& b, size_t need)
 int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam, mhe_info* info,
                       int pieces)
 {
+    const int rc = mhe_estimate_host_async(ctx, prob, x, w, lam, info, pieces);
+    const int rw = ctx ? mhe_estimate_host_wait(ctx) : MHE_OK;
+    return rc != MHE_OK ? rc : rw;
+}
+
+int mhe_estimate_host_wait(mhe_ctx* ctx)
+{
+    if (!ctx) return fail(MHE_E_ARG, "ctx is NULL");
+    if (!ctx->pipe) return MHE_OK;
+    HostPipe& hp = *ctx->pipe;
+    int rc = MHE_OK;
+    if (cudaStreamSynchronize(hp.cst) != cudaSuccess) rc = MHE_E_CUDA;
+    for (int e = 0; e < HostPipe::NE; ++e)
+        if (hp.st[e] && cudaStreamSynchronize(hp.st[e]) != cudaSuccess) rc = MHE_E_CUDA;
+    if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
+    if (rc == MHE_E_CUDA) g_err = "CUDA error in the host-buffer pipeline";
+    return rc;
+}
+
+int mhe_estimate_host_async(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, double* lam,
+                            mhe_info* info, int pieces)
+{
     if (!ctx || !prob) return fail(MHE_E_ARG, "ctx or prob is NULL");
     if (!x || !w || !lam) return fail(MHE_E_ARG, "output pointer is NULL");
     mhe::Engine& E = ctx->eng;
@@ -570,16 +605,26 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
     if (!ctx->pipe) {
         HostPipe* hp = new (std::nothrow) HostPipe;
         if (!hp) return fail(MHE_E_NOMEM, "host allocation failed");
-        for (int e = 0; e < HostPipe::NE; ++e)
-            if (cudaStreamCreateWithFlags(&hp->st[e], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&hp->done[e], cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                delete hp;
-                return fail(MHE_E_CUDA, "stream or event creation failed");
-            }
+        if (cudaStreamCreateWithFlags(&hp->cst, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete hp;
+            return fail(MHE_E_CUDA, "stream creation failed");
+        }
         ctx->pipe = hp;
     }
     HostPipe& hp = *ctx->pipe;
+    // the engines' streams and events, created when first used: every stream takes one of
+    // the device's hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS of them, 8 by default,
+    // 32 at most), and streams beyond that share queues and wait on each other's work
+    for (int e = 0; e < HostPipe::NE && e < pieces; ++e) {
+        if (hp.st[e]) continue;
+        if (cudaStreamCreateWithFlags(&hp.st[e], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&hp.done[e], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&hp.arrived[e], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MHE_E_CUDA, "stream or event creation failed");
+        }
+    }
     // in-place reads: the device address of every input (pinned host memory, mapped)
     const double* dsrc[9] = {prob->A, prob->B, prob->C, prob->R, prob->a, prob->yt, prob->wt, prob->x0, prob->P0inv};
     if (ctx->host_in_place)
@@ -600,8 +645,9 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
     hp.evused = 0;
     if (tl) {
         hp.t0 = hp.ev();
-        cudaEventRecord(hp.t0, hp.st[0]);
-        for (int e = 1; e < HostPipe::NE; ++e) cudaStreamWaitEvent(hp.st[e], hp.t0, 0);
+        cudaEventRecord(hp.t0, hp.cst);
+        for (int e = 0; e < HostPipe::NE; ++e)
+            if (hp.st[e]) cudaStreamWaitEvent(hp.st[e], hp.t0, 0);
     }
     // pieces of consecutive instances with about equal stage counts
     std::vector<int> cut(1, 0);
@@ -637,10 +683,12 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             rc = hp.eng[e].init(d, E.ops, &kRuntime, hp.st[e]);
             if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
             hp.inited[e] = true;
-        } else {
+        } else if (hp.last_b0[e] != b0 || hp.last_b1[e] != b1) {
             rc = hp.eng[e].replan(P.N.data() + b0, cnt, nullptr);
             if (rc != MHE_OK) { g_err = hp.eng[e].err; break; }
         }
+        hp.last_b0[e] = b0;
+        hp.last_b1[e] = b1;
         // pinned staging for the next plan upload of this engine, grown to what this one wanted
         // (engine e's stream has passed its previous uploads: done[e] was waited for above)
         if (hp.eng[e].upload_need > hp.stage_bytes[e]) {
@@ -666,10 +714,12 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             if (reserve_buf(hp.out[e][i], sizeof(double) * sz_out[i]) != 0) rc = MHE_E_NOMEM;
         if (rc != MHE_OK) { g_err = "device allocation of a pipeline buffer failed"; break; }
         HostPipe::Piece pc{e, b0, b1, 0.0, {}};
+        // the copy stream must not overwrite engine e's input buffers while its previous piece reads them
+        if (!ctx->host_in_place) cudaStreamWaitEvent(hp.cst, hp.done[e], 0);
         if (tl) {
             pc.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
             for (auto& v : pc.ev) v = hp.ev();
-            cudaEventRecord(pc.ev[0], hp.st[e]);
+            cudaEventRecord(pc.ev[0], hp.cst);
         }
         const double* in[9];
         if (ctx->host_in_place) {
@@ -682,11 +732,16 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
             for (int i = 0; i < 9; ++i) {
                 if (sz_in[i] > 0)
                     cudaMemcpyAsync(hp.in[e][i].p, src[i], sizeof(double) * sz_in[i], cudaMemcpyHostToDevice,
-                                    hp.st[e]);
+                                    hp.cst);
                 in[i] = (const double*)hp.in[e][i].p;
             }
+            cudaEventRecord(hp.arrived[e], hp.cst);
+            cudaStreamWaitEvent(hp.st[e], hp.arrived[e], 0);
         }
-        if (tl) cudaEventRecord(pc.ev[1], hp.st[e]);
+        if (tl) {
+            cudaEventRecord(pc.ev[1], hp.cst);
+            cudaStreamWaitEvent(hp.st[e], pc.ev[1], 0);
+        }
         mhe_problem dp;
         dp.ny = q;
         dp.A = in[0]; dp.B = in[1]; dp.C = in[2]; dp.R = in[3]; dp.a = in[4]; dp.yt = in[5]; dp.wt = in[6];
@@ -705,8 +760,6 @@ int mhe_estimate_host(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* 
         }
         hp.used[e] = true;
     }
-    for (int e = 0; e < HostPipe::NE; ++e)
-        if (cudaStreamSynchronize(hp.st[e]) != cudaSuccess && rc == MHE_OK) rc = MHE_E_CUDA;
     if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
     if (rc == MHE_E_CUDA && g_err.empty()) g_err = "CUDA error in the host-buffer pipeline";
     return rc;

@@ -106,6 +106,10 @@ def _declare(L):
     L.mhe_launch_count.restype = c_ll
     L.mhe_assemble_count.argtypes = []
     L.mhe_assemble_count.restype = c_ll
+    L.mhe_estimate_host_async.argtypes = L.mhe_estimate_host.argtypes
+    L.mhe_estimate_host_async.restype = c_int
+    L.mhe_estimate_host_wait.argtypes = [c_void_p]
+    L.mhe_estimate_host_wait.restype = c_int
     L.mhe_pipe_timeline.argtypes = [c_void_p, P(c_double), c_int]
     L.mhe_pipe_timeline.restype = c_int
     L.mhe_set_host_in_place.argtypes = [c_void_p, c_int]
@@ -266,8 +270,7 @@ def _hptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def mhe_estimate_host(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info=None, pieces=8):
-    """mhe_estimate_host: problem and outputs in host memory (pinned for overlap)."""
+def _host_args(ny, A, B, C, R, a, yt, wt, x0, P0inv, info):
     p = mhe_problem(int(ny), _hptr(A), _hptr(B), _hptr(C), _hptr(R), _hptr(a), _hptr(yt), _hptr(wt), _hptr(x0),
                     _hptr(P0inv))
     if info is None:
@@ -276,8 +279,25 @@ def mhe_estimate_host(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info
         ip = ctypes.c_void_p(info.ctypes.data)
     else:
         ip = ctypes.c_void_p(info.data_ptr())
+    return p, ip
+
+
+def mhe_estimate_host(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info=None, pieces=8):
+    """mhe_estimate_host: problem and outputs in host memory (pinned for overlap)."""
+    p, ip = _host_args(ny, A, B, C, R, a, yt, wt, x0, P0inv, info)
     return _check(lib().mhe_estimate_host(ctx, ctypes.byref(p), _hptr(x), _hptr(w), _hptr(lam), ip, int(pieces)),
                   "mhe_estimate_host")
+
+
+def mhe_estimate_host_async(ctx, ny, A, B, C, R, a, yt, wt, x0, P0inv, x, w, lam, info=None, pieces=8):
+    """mhe_estimate_host_async: issue the host pipeline and return; mhe_estimate_host_wait completes it."""
+    p, ip = _host_args(ny, A, B, C, R, a, yt, wt, x0, P0inv, info)
+    return _check(lib().mhe_estimate_host_async(ctx, ctypes.byref(p), _hptr(x), _hptr(w), _hptr(lam), ip,
+                                                int(pieces)), "mhe_estimate_host_async")
+
+
+def mhe_estimate_host_wait(ctx):
+    return _check(lib().mhe_estimate_host_wait(ctx), "mhe_estimate_host_wait")
 
 
 def mhe_destroy(ctx):

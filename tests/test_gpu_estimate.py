@@ -138,12 +138,47 @@ def test_estimate_host_equals_device(prec, pieces):
     sols = split(x2, w2, l2, d["N"], n, m)
     for b in range(len(Ns)):
         assert rel_err(sols[b], ref[b]) <= (1e-10 if prec == mhe.MHE_FP64 else 1e-8)
-    # a second call reuses the pipeline's engines and buffers
+    # a second call reuses the pipeline's engines and buffers; other piece counts re-plan
+    # the engines whose instances change; inputs read in place give the same bits
+    for pc, in_place in ((pieces, False), (pieces + 2, False), (pieces, False), (pieces, True)):
+        s2.set_host_in_place(in_place)
+        x2.zero_()
+        mhe.mhe_estimate_host(s2.ctx, m, h["A"], h["B"], h["C"], h["R"], h["a"], h["yt"], h["wt"], h["x0"],
+                              h["P0inv"], x2, w2, l2, info2, pieces=pc)
+        assert torch.equal(x1.cpu(), x2), (pc, in_place)
+    # with timing enabled the call records its pipeline's timeline: every piece's events in order
+    mhe.mhe_timing_enable(s2.ctx, True)
+    s2.set_host_in_place(False)
     mhe.mhe_estimate_host(s2.ctx, m, h["A"], h["B"], h["C"], h["R"], h["a"], h["yt"], h["wt"], h["x0"], h["P0inv"],
                           x2, w2, l2, info2, pieces=pieces)
-    assert torch.equal(x1.cpu(), x2)
+    tl = mhe.mhe_pipe_timeline(s2.ctx)
+    assert 1 <= len(tl) <= min(pieces, len(Ns)) and tl[0][1] == 0 and tl[-1][2] == len(Ns)
+    for k, row in enumerate(tl):
+        assert 0 <= row[4] <= row[5] <= row[6] <= row[7]
+        if k + 1 < len(tl):
+            assert row[2] == tl[k + 1][1]   # the pieces tile the batch in order
+    mhe.mhe_timing_enable(s2.ctx, False)
+    mhe.mhe_timing_read(s2.ctx)
     s1.close()
     s2.close()
+
+
+def test_estimate_host_in_place_refuses_pageable_inputs():
+    import torch
+    n, m = 4, 2
+    insts = [synth.mhe_instance(590, n, m, m, 12)]
+    d = device_inputs(insts)
+    s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP32_IR)
+    s.set_host_in_place(True)
+    h = {k: d[k].cpu() for k in ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv")}   # pageable
+    x = torch.zeros((13 * n,), dtype=torch.float64)
+    w = torch.zeros((n + 11 * m,), dtype=torch.float64)
+    lam = torch.zeros((13 * n,), dtype=torch.float64)
+    with pytest.raises(mhe.MheError) as e:
+        mhe.mhe_estimate_host(s.ctx, m, h["A"], h["B"], h["C"], h["R"], h["a"], h["yt"], h["wt"], h["x0"],
+                              h["P0inv"], x, w, lam, None, pieces=2)
+    assert e.value.code == -1
+    s.close()
 
 
 @pytest.mark.parametrize("plan", [dict(), dict(top_len=1000)])
@@ -320,3 +355,31 @@ def test_double_float_residual_equals_fp64_residual(n, m):
         for b in range(len(Ns)):
             assert info["status"][b] == 0 and info["relres"][b] <= 1e-12, (df, b, info[b])
             assert rel_err(sols[b], ref[b]) <= 1e-8, (df, b, rel_err(sols[b], ref[b]))
+
+
+def test_estimate_host_async_two_contexts_from_one_thread():
+    """mhe_estimate_host_async on two contexts, then mhe_estimate_host_wait on each:
+    the results of the synchronous call, bit for bit."""
+    import torch
+    outs = []
+    for n, m, seed in ((6, 3, 600), (12, 6, 700)):
+        Ns = [5, 40, 200, 77, 1, 130]
+        insts = [synth.mhe_instance(seed + i, n, m, m, N) for i, N in enumerate(Ns)]
+        d = device_inputs(insts)
+        s = mhe.Solver(n, m, d["N"], prec=mhe.MHE_FP32_IR, refine_tol=1e-12)
+        h = {k: d[k].cpu().pin_memory() for k in ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv")}
+        X, W = int(sum(N + 1 for N in Ns)), int(sum(n + (N - 1) * m for N in Ns))
+        ref = [torch.zeros(X * n, dtype=torch.float64).pin_memory(), torch.zeros(W, dtype=torch.float64).pin_memory(),
+               torch.zeros(X * n, dtype=torch.float64).pin_memory()]
+        got = [torch.zeros_like(t).pin_memory() for t in ref]
+        mhe.mhe_estimate_host(s.ctx, m, *[h[k] for k in ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv")],
+                              *ref, None, pieces=3)
+        outs.append((s, h, m, ref, got))
+    for s, h, m, ref, got in outs:
+        mhe.mhe_estimate_host_async(s.ctx, m, *[h[k] for k in ("A", "B", "C", "R", "a", "yt", "wt", "x0", "P0inv")],
+                                    *got, None, pieces=3)
+    for s, h, m, ref, got in outs:
+        mhe.mhe_estimate_host_wait(s.ctx)
+        for a, b in zip(ref, got):
+            assert torch.equal(a, b)
+        s.close()
