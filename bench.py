@@ -1254,7 +1254,7 @@ def main():
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--serial-fp64", action="store_true", help="also time the serial plan in FP64")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--e2e-pieces", type=int, default=4, help="pieces of the host-buffer pipeline per bucket")
+    ap.add_argument("--e2e-pieces", type=int, default=8, help="pieces of the host-buffer pipeline per bucket")
     ap.add_argument("--e2e-threads", choices=["one", "bucket"], default="one",
                     help="end to end: one host thread issuing every bucket's pipeline, or a thread per bucket")
     ap.add_argument("--e2e-in-place", action="store_true", help="end to end: the kernels read the pinned inputs in place")

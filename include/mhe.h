@@ -216,9 +216,10 @@ int mhe_estimate(mhe_ctx* ctx, const mhe_problem* prob, double* x, double* w, do
  * device-to-host copies follow each solve.  Inputs: an mhe_problem of host
  * pointers, the same layout; outputs x, w, lam as mhe_solve (host); info
  * [batch] host or NULL.  Synchronous: returns when every output has arrived.
- * The input copies of all pieces go through one stream in piece order (the
- * copy engine then runs them back to back); each piece's solve and output copy
- * run on its engine's stream.  Every stream takes one of the device's hardware
+ * The input copies of all pieces go through one stream, shared by every
+ * pipeline of the process, in the order they are issued (the copy engine then
+ * runs them back to back at the host link's rate); each piece's solve and
+ * output copy run on its engine's stream.  Every stream takes one of the device's hardware
  * work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 by default): a process that runs
  * several pipelines at once should raise it (up to 32) to cover their 1 +
  * min(pieces, 16) streams each, else streams share queues and wait on each

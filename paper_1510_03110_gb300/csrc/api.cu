@@ -49,6 +49,29 @@ struct PassTiming {
     }
 };
 
+// One stream per device for the host-to-device copies of every host pipeline of the
+// process: the host link moves about 211 GB/s whatever the number of streams that share
+// it (measured on GB300), and copies queued on several streams were measured to leave
+// it partly idle in some steps and to finish one pipeline's inputs long after another's;
+// on one stream they run back to back in the order they were issued.  Created on first
+// use, kept for the life of the process.
+static cudaStream_t shared_copy_stream()
+{
+    static std::mutex mu;
+    static cudaStream_t st[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!st[dev] && cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        st[dev] = nullptr;
+    }
+    return st[dev];
+}
+
 // Host-buffer pipeline of mhe_estimate_host: up to NE engines on streams of their
 // own take the pieces of the batch (piece k on engine k mod NE); each has its
 // device copies of a piece's inputs and outputs.  With at most NE pieces every
@@ -63,9 +86,8 @@ struct HostPipe {
     mhe::Engine eng[NE];
     cudaStream_t st[NE] = {};
     cudaEvent_t done[NE] = {};
-    // the input copies of every piece on one stream, in piece order: the copy engine then
-    // streams them back to back at the full host-link rate (copies interleaved from many
-    // streams were measured to reach a fraction of it); each piece's solve waits on its own
+    // the stream of the input copies (shared by every pipeline of the process: see
+    // shared_copy_stream); each piece's solve waits on its own copies' event
     cudaStream_t cst = nullptr;
     cudaEvent_t arrived[NE] = {};
     bool inited[NE] = {};
@@ -107,10 +129,7 @@ struct HostPipe {
             if (st[e]) cudaStreamDestroy(st[e]);
         }
         for (auto v : evpool) cudaEventDestroy(v);
-        if (cst) {
-            cudaStreamSynchronize(cst);
-            cudaStreamDestroy(cst);
-        }
+        // the shared copy stream is not the pipeline's own: it is left to the process
         for (auto v : arrived)
             if (v) cudaEventDestroy(v);
     }
@@ -580,7 +599,6 @@ int mhe_estimate_host_wait(mhe_ctx* ctx)
     if (!ctx->pipe) return MHE_OK;
     HostPipe& hp = *ctx->pipe;
     int rc = MHE_OK;
-    if (cudaStreamSynchronize(hp.cst) != cudaSuccess) rc = MHE_E_CUDA;
     for (int e = 0; e < HostPipe::NE; ++e)
         if (hp.st[e] && cudaStreamSynchronize(hp.st[e]) != cudaSuccess) rc = MHE_E_CUDA;
     if (rc == MHE_OK && cudaGetLastError() != cudaSuccess) rc = MHE_E_CUDA;
@@ -605,8 +623,8 @@ int mhe_estimate_host_async(mhe_ctx* ctx, const mhe_problem* prob, double* x, do
     if (!ctx->pipe) {
         HostPipe* hp = new (std::nothrow) HostPipe;
         if (!hp) return fail(MHE_E_NOMEM, "host allocation failed");
-        if (cudaStreamCreateWithFlags(&hp->cst, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
+        hp->cst = shared_copy_stream();
+        if (!hp->cst) {
             delete hp;
             return fail(MHE_E_CUDA, "stream creation failed");
         }
