@@ -832,17 +832,21 @@ int Engine::estimate(const mhe_problem& p, double* x, double* w, double* lam, mh
     rAh = rAl = rBh = rBl = rCh = rCl = rRh = rRl = nullptr;
     if (df_resid) {
         const int q = p.ny;
-        const size_t per = (size_t)n * n + (size_t)n * m + 2 * (size_t)q * n + 2 * (size_t)(m + q) * (m + q);
-        if (!reserve(rt, stream, dfp, dfp_bytes, sizeof(float) * (size_t)S * per + 64, alloc_gen)) {
+        // six arrays, each starting on a 16-byte boundary (the residual loads rows of A and B
+        // in vectors of up to four floats)
+        auto r4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
+        const size_t nA = r4((size_t)S * n * n), nB = r4((size_t)S * n * m), nC = r4((size_t)S * q * n),
+                     nR = r4((size_t)S * (m + q) * (m + q));
+        if (!reserve(rt, stream, dfp, dfp_bytes, sizeof(float) * (nA + nB + 2 * nC + 2 * nR) + 64, alloc_gen)) {
             err = "device allocation of the residual's float pairs failed";
             return MHE_E_NOMEM;
         }
         float* f = reinterpret_cast<float*>(dfp);
-        pa.A_lo = f; f += (size_t)S * n * n;
-        pa.B_lo = f; f += (size_t)S * n * m;
-        pa.C_hi = f; f += (size_t)S * q * n;
-        pa.C_lo = f; f += (size_t)S * q * n;
-        pa.R_hi = f; f += (size_t)S * (m + q) * (m + q);
+        pa.A_lo = f; f += nA;
+        pa.B_lo = f; f += nB;
+        pa.C_hi = f; f += nC;
+        pa.C_lo = f; f += nC;
+        pa.R_hi = f; f += nR;
         pa.R_lo = f;
         rAh = A32; rAl = pa.A_lo; rBh = B32; rBl = pa.B_lo;
         rCh = pa.C_hi; rCl = pa.C_lo; rRh = pa.R_hi; rRl = pa.R_lo;

@@ -359,6 +359,41 @@ MHE_DEV void dot_df(const float* mh, const float* ml, int sm, const float2* v, i
         if (j < k) df_acc(s, c, mh[j * sm], ml[j * sm], v[j].x, v[j].y);
 }
 
+// sum_{j < L} (mh + ml)[j] * v[j] into (s, c) over a contiguous row segment, in
+// loads of VW floats (mh, ml aligned to VW floats)
+template <int L, int VW>
+MHE_DEV void dot_df_row(const float* mh, const float* ml, const float2* v, float& s, float& c)
+{
+    static_assert(L % VW == 0 && (VW == 1 || VW == 2 || VW == 4), "whole vectors");
+#pragma unroll
+    for (int j = 0; j < L; j += VW) {
+        if constexpr (VW == 4) {
+            const float4 h = *reinterpret_cast<const float4*>(mh + j);
+            const float4 l = *reinterpret_cast<const float4*>(ml + j);
+            df_acc(s, c, h.x, l.x, v[j].x, v[j].y);
+            df_acc(s, c, h.y, l.y, v[j + 1].x, v[j + 1].y);
+            df_acc(s, c, h.z, l.z, v[j + 2].x, v[j + 2].y);
+            df_acc(s, c, h.w, l.w, v[j + 3].x, v[j + 3].y);
+        } else if constexpr (VW == 2) {
+            const float2 h = *reinterpret_cast<const float2*>(mh + j);
+            const float2 l = *reinterpret_cast<const float2*>(ml + j);
+            df_acc(s, c, h.x, l.x, v[j].x, v[j].y);
+            df_acc(s, c, h.y, l.y, v[j + 1].x, v[j + 1].y);
+        } else {
+            df_acc(s, c, mh[j], ml[j], v[j].x, v[j].y);
+        }
+    }
+}
+
+// the widest load (4, 2 or 1 floats) that divides the row segment length LP, the
+// column length NX and the stage blocks NX x NX and NX x NW (so that every segment
+// of A and B starts aligned, given 16-byte aligned arrays)
+template <int NX, int NW, int LP>
+constexpr int df_row_width()
+{
+    return (LP % 4 == 0 && NX % 4 == 0 && (NX * NW) % 4 == 0) ? 4 : ((LP % 2 == 0 && NX % 2 == 0) ? 2 : 1);
+}
+
 // Stage t >= 1 in the MHE form with FP32 correction solves: the tasks of
 // resid_mhe, each a double-float dot product.
 template <int NX, int NW, int NY>
@@ -420,21 +455,30 @@ MHE_DEV void resid_mhe_df(const ResidArgs<float>& r, int b, int t, int N, unsign
         else vl[k - NX - NW] = df_split(ln[k - NX - NW]);
         if (k == 0) mx[0] = mx[1] = mx[2] = 0ULL;
     });
+    // the tasks: the column-strided pieces of A x and C x first, then the contiguous row
+    // pieces of A^T lam and B^T lam (vector loads), then the length-nw products: warps
+    // mostly run tasks of one kind
+    constexpr int TS = (NX + NY) * SP, TC = (NX + NW) * SP;
+    constexpr int VW = df_row_width<NX, NW, LP>();
     wfor(T1 * SP + NX + NW + NY, [&](int k) {
         const float *mh, *ml;
         const float2* v;
         float2* o;
         int st, len = LP;
-        if (k < T1 * SP) {
-            const int q = k % T1, c = k / T1, j0 = c * LP;
+        if (k < TS) {
+            const int q = k % (NX + NY), c = k / (NX + NY), j0 = c * LP;
             o = part + c * T1 + q;
             if (q < NX) { mh = Ah + q + j0 * NX; ml = Al + q + j0 * NX; st = NX; v = vx + j0; }
-            else if (q < NX + NY) { mh = Ch + (q - NX) + j0 * NY; ml = Cl + (q - NX) + j0 * NY; st = NY; v = vx + j0; }
-            else if (q < 2 * NX + NY) {
-                mh = Ah + (q - NX - NY) * NX + j0; ml = Al + (q - NX - NY) * NX + j0; st = 1; v = vl + j0;
-            } else {
-                mh = Bh + (q - 2 * NX - NY) * NX + j0; ml = Bl + (q - 2 * NX - NY) * NX + j0; st = 1; v = vl + j0;
-            }
+            else { mh = Ch + (q - NX) + j0 * NY; ml = Cl + (q - NX) + j0 * NY; st = NY; v = vx + j0; }
+        } else if (k < TS + TC) {
+            const int q = (k - TS) % (NX + NW), c = (k - TS) / (NX + NW), j0 = c * LP;
+            o = part + c * T1 + NX + NY + q;
+            if (q < NX) { mh = Ah + q * NX + j0; ml = Al + q * NX + j0; }
+            else { mh = Bh + (q - NX) * NX + j0; ml = Bl + (q - NX) * NX + j0; }
+            float ds = 0.f, dc = 0.f;
+            dot_df_row<LP, VW>(mh, ml, vl + j0, ds, dc);
+            *o = make_float2(ds, dc);
+            return;
         } else {
             const int q = k - T1 * SP;
             len = NW;
