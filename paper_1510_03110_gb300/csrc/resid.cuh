@@ -485,8 +485,12 @@ MHE_DEV void resid_mhe_df(const ResidArgs<float>& r, int b, int t, int N, unsign
             if (q < NX) { mh = Bh + q; ml = Bl + q; st = NX; v = vw; o = dB + q; }
             else if (q < NX + NW) { mh = Rh + (q - NX); ml = Rl + (q - NX); st = NR; v = vw; o = ww + (q - NX); }
             else {
-                mh = Rh + (NW + q - NX - NW) * NR; ml = Rl + (NW + q - NX - NW) * NR; st = 1; v = vw;
-                o = sw + (q - NX - NW);
+                // S^T w: the first nw entries of column nw + i of R, contiguous
+                const int i = q - NX - NW;
+                float ds = 0.f, dc = 0.f;
+                dot_df_row<NW, df_row_width<NR, NR, NW>()>(Rh + (NW + i) * NR, Rl + (NW + i) * NR, vw, ds, dc);
+                sw[i] = make_float2(ds, dc);
+                return;
             }
         }
         float ds = 0.f, dc = 0.f;
@@ -515,7 +519,7 @@ MHE_DEV void resid_mhe_df(const ResidArgs<float>& r, int b, int t, int N, unsign
     });
     wfor(NX, [&](int i) {
         float ds = 0.f, dc = 0.f;
-        dot_df<NY>(Ch + i * NY, Cl + i * NY, 1, e, NY, ds, dc);
+        dot_df_row<NY, df_row_width<NY, NX, NY>()>(Ch + i * NY, Cl + i * NY, e, ds, dc);   // column i of C
         cte[i] = make_float2(ds, dc);
     });
     unsigned long long m0 = 0, m1 = 0, m2 = 0;
