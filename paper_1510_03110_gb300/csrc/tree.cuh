@@ -25,6 +25,7 @@
 //   resid_stage   KKT residual rows of one stage (FP64).
 //   assemble_stage  MHE weights -> UFTOC Q_t, l_t, c_t (Section II).
 #pragma once
+#include <stdint.h>
 #include <type_traits>
 
 #include "common.h"
@@ -1354,6 +1355,37 @@ MHE_DEV void down_fwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* Kin, co
     wfor(NX, [&](int i) { s.e[i] = s.u[i]; });
 }
 
+// sum_j p[j] v[j] over a contiguous column of N entries (v in shared memory): in
+// 16-byte vector loads when p is aligned to them (the whole team takes the same
+// branch: its columns are N entries apart), else entry by entry.  The transposed
+// products (A^T lambda) read a column per lane this way instead of one strided
+// entry per lane and step.
+template <int N, typename T>
+MHE_DEV T col_dot(const T* p, const T* v)
+{
+    constexpr int VW = sizeof(T) == 4 ? (N % 4 == 0 ? 4 : (N % 2 == 0 ? 2 : 1)) : (N % 2 == 0 ? 2 : 1);
+    T acc = (T)0;
+    if (VW > 1 && (reinterpret_cast<uintptr_t>(p) % (VW * sizeof(T))) == 0) {
+#pragma unroll
+        for (int j = 0; j < N; j += VW) {
+            if constexpr (sizeof(T) == 4 && VW == 4) {
+                const float4 q = *reinterpret_cast<const float4*>(p + j);
+                acc += q.x * v[j] + q.y * v[j + 1] + q.z * v[j + 2] + q.w * v[j + 3];
+            } else if constexpr (sizeof(T) == 4 && VW == 2) {
+                const float2 q = *reinterpret_cast<const float2*>(p + j);
+                acc += q.x * v[j] + q.y * v[j + 1];
+            } else if constexpr (sizeof(T) == 8 && VW == 2) {
+                const double2 q = *reinterpret_cast<const double2*>(p + j);
+                acc += q.x * v[j] + q.y * v[j + 1];
+            }
+        }
+        return acc;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc += p[j] * v[j];
+    return acc;
+}
+
 // |v| as a float (the size of a correction; float is ample for a norm)
 MHE_DEV float absf_of(float v) { return fabsf(v); }
 MHE_DEV float absf_of(double v) { return abs_to_float(v); }
@@ -1371,8 +1403,9 @@ MHE_DEV void down_bwd_step(Ws<T, NX>& s, const StageRef<T>& st, const T* xt, con
         for (int j = 0; j < NX; ++j) acc += X::qx(st, i, j) * xt[j];
 #pragma unroll
         for (int j = 0; j < MT; ++j) acc += X::qxw(st, i, j) * wt[j];
-#pragma unroll
-        for (int j = 0; j < NX; ++j) acc += X::A(st, j, i) * s.Psi[j];
+        // (A^T lambda_{t+1})_i: column i of A (the arrival stage has A = I)
+        if constexpr (KIND == KIND_ARRIVAL) acc += s.Psi[i];
+        else acc += col_dot<NX>(st.A + i * NX, s.Psi);
         s.u[i] = acc;
     });
     wfor(NX + (zx ? NX + MT : 0), [&](int idx) {
