@@ -1112,12 +1112,14 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
         steps_tl, worst = [], None
         for _ in range(k):
             t1 = time.perf_counter()
+            c1 = time.process_time()
             e2e_step()
             wall_tl = (time.perf_counter() - t1) * 1e3
+            cpu_tl = (time.process_time() - c1) * 1e3
             host_calls = {buckets[i]["n"]: [round((a - t1) * 1e3, 2), round((b - t1) * 1e3, 2)]
                           for i, (a, b) in calls.items()}
             pieces = {bk["n"]: mhe.mhe_pipe_timeline(s.ctx) for bk, s in zip(buckets, solvers)}
-            steps_tl.append(dict(step_ms=round(wall_tl, 2), host_calls_ms=host_calls,
+            steps_tl.append(dict(step_ms=round(wall_tl, 2), host_cpu_ms=round(cpu_tl, 2), host_calls_ms=host_calls,
                                  device_last_out_ms={n: round(max(r[7] for r in p), 2) for n, p in pieces.items() if p}))
             if worst is None or wall_tl > worst[0]:
                 worst = (wall_tl, pieces)
