@@ -1136,7 +1136,8 @@ def run_e2e(args, buckets, solvers, step, stream, instances):
     infos = np.concatenate([info.numpy().view(mhe.INFO_DTYPE) for _, info in outs])
     del mhe
     return dict(value=round(instances / (ms * 1e-3), 3), unit="KKT solves/s", h2d_bytes_per_step=int(h2d),
-                d2h_bytes_per_step=int(d2h), ms_per_step=round(ms, 3), steps=k, pieces=args.e2e_pieces,
+                d2h_bytes_per_step=int(d2h), ms_per_step=round(ms, 3),
+                ms_median=round(float(np.median(each)), 3), steps=k, pieces=args.e2e_pieces,
                 ms_each=[round(v, 2) for v in each], h2d_gbs_pinned=gbs,
                 h2d_floor_ms=round(h2d / (gbs * 1e6), 1),
                 relres_max=float(np.max(infos["relres"])), all_ok=bool(np.all(infos["status"] == 0)),
