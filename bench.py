@@ -868,6 +868,94 @@ def run_small(args):
     return out
 
 
+def run_ip(args):
+    """MHE with box-bounded process noise (the interior-point loop, mhe_ip_solve): 256 instances of nx = 12,
+    nw = ny = 6, N ~ U[32,512] (seed 6), FP64; the box around zero at half the largest |w_t[j]| of the
+    unconstrained solution (the library's own solve), shifted by 10%.  Timed: whole mhe_ip_solve calls in both
+    methods (predictor-corrector: a factor and two solves of the tree per iteration; path following: a factor +
+    solve per iteration; one host synchronisation per iteration), against the unconstrained solve of the same
+    problems; checked: every input strictly inside its box, every instance converged."""
+    import torch
+    from paper_1510_03110_gb300 import build, mhe
+    build.build()
+    torch.cuda.set_device(0)
+    n, m, count = 12, 6, 256
+    rng = np.random.default_rng(6)
+    Ns = [int(v) for v in rng.integers(32, 513, size=count)]
+    insts = [synth.mhe_instance(6000 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    cat = lambda key, cm: np.concatenate([(synth.colmajor(p[key]) if cm else p[key]).reshape(-1)  # noqa: E731
+                                          for p in insts])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()  # noqa: E731
+    S = int(sum(N - 1 for N in Ns))
+    A, B, C, R = t(cat("A", True)), t(cat("B", True)), t(cat("C", True)), t(cat("R", True))
+    a, yt, wt = t(cat("a", False)), t(cat("yt", False)), t(cat("wt", False))
+    x0 = t(np.concatenate([p["x0"] for p in insts]))
+    P0 = t(np.concatenate([synth.colmajor(p["P0inv"]).reshape(-1) for p in insts]))
+    Q = torch.empty(S * (n + m) ** 2, dtype=torch.float64, device="cuda")
+    l = torch.empty(S * (n + m), dtype=torch.float64, device="cuda")
+    mhe.mhe_assemble(n, m, m, C.view(S, -1), R, yt, wt, Q, l)
+    stream = torch.cuda.Stream()
+    s = mhe.Solver(n, m, Ns, prec=mhe.MHE_FP64, stream=stream)
+    with torch.cuda.stream(stream):
+        x, w, lam = s.factor_solve(A, B, Q, P0, l, a, x0)
+    stream.synchronize()
+    wh = w.cpu().numpy()
+    lo, hi, off = [], [], 0
+    for N in Ns:
+        wb = wh[off + n:off + n + (N - 1) * m].reshape(N - 1, m)
+        c = 0.5 * np.maximum(np.abs(wb).max(axis=0), 1e-3)
+        sh = rng.uniform(-0.1, 0.1, m) * c
+        lo.append(-c + sh)
+        hi.append(c + sh)
+        off += n + (N - 1) * m
+    lo_t, hi_t = t(np.concatenate(lo)), t(np.concatenate(hi))
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), out
+
+    with torch.cuda.stream(stream):
+        s.factor_solve(A, B, Q, P0, l, a, x0)   # warm-up
+        ms_unc, _ = timed(lambda: s.factor_solve(A, B, Q, P0, l, a, x0), 5)
+    stream.synchronize()
+
+    def arm(method):
+        with torch.cuda.stream(stream):
+            s.ip_solve(A, B, Q, P0, l, a, x0, lo_t, hi_t, method=method)   # warm-up
+            ms, (xi, wi, li, steps) = timed(lambda: s.ip_solve(A, B, Q, P0, l, a, x0, lo_t, hi_t, method=method), 3)
+        stream.synchronize()
+        info = s.infos()
+        wi = wi.cpu().numpy()
+        inside, active, off = True, 0, 0
+        for b, N in enumerate(Ns):
+            wb = wi[off + n:off + n + (N - 1) * m].reshape(N - 1, m)
+            inside = inside and bool(np.all(wb > lo[b]) and np.all(wb < hi[b]))
+            active += int(np.sum((wb - lo[b] < 1e-6 * (hi[b] - lo[b])) | (hi[b] - wb < 1e-6 * (hi[b] - lo[b]))))
+            off += n + (N - 1) * m
+        return dict(ms_per_ip_solve=round(ms, 3), iterations=int(steps), ms_per_iteration=round(ms / max(int(steps), 1), 3),
+                    ip_solves_per_s=round(count / (ms * 1e-3), 3), all_inside_the_box=inside,
+                    bounds_within_1e6_of_the_box=active, all_ok=bool(np.all(info["status"] == 0))), wi
+
+    pc, w_pc = arm(mhe.MHE_IP_PREDICTOR_CORRECTOR)
+    pf, w_pf = arm(mhe.MHE_IP_PATH_FOLLOWING)
+    s.close()
+    pc.update(factorisations_per_iteration=1, solves_per_iteration=2)
+    pf.update(factorisations_per_iteration=1, solves_per_iteration=1)
+    return dict(workload="box-bounded MHE, interior-point loop: 256 instances nx=12, nw=ny=6, N ~ U[32,512], FP64",
+                instances=count, stages=S, bounded_inputs=int(S * m), ms_unconstrained_solve=round(ms_unc, 3),
+                predictor_corrector=pc, path_following=pf,
+                max_abs_w_difference_between_methods=float(np.abs(w_pc - w_pf).max()),
+                speedup_predictor_corrector=round(pf["ms_per_ip_solve"] / pc["ms_per_ip_solve"], 3),
+                ip_solves_per_s=pc["ip_solves_per_s"], ms_per_ip_solve=pc["ms_per_ip_solve"])
+
+
 def serve_setup(args, rates, T, seed=4):
     """The serving workload: a pool of estimators (nx ~ U{6,12,24}, nw = ny = nx/2, N ~ U{50,200,1000}),
     for each offered rate a seeded Poisson arrival sequence over T seconds (who and when), and every
@@ -1227,7 +1315,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks", "small"])
+                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks", "small", "ip"])
     ap.add_argument("--N", type=int, default=131072, help="long workload: the horizon")
     ap.add_argument("--sweep", action="store_true", help="long workload: the depth sweep over N, leaf, branching")
     ap.add_argument("--sweep-N", default="1024,16384,131072")
@@ -1299,6 +1387,13 @@ def main():
                               config=dict(workload="single MHE instance nx=4, nw=ny=2, N=64, FP64, seed 0",
                                           l2="inputs smaller than L2 (latency case; not flushed)"),
                               latency_ms=dict(p50=t["p50_ms"], p99=t["p99_ms"]), arms=res)))
+        return
+    if args.workload == "ip":
+        res = run_ip(args)
+        print(json.dumps(dict(metric=METRIC, value=res["ip_solves_per_s"], unit="box-bounded MHE solves/s", n_gpus=1,
+                              steps=3, warmup=1, ms_per_step=res["ms_per_ip_solve"], higher_is_better=True,
+                              scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                              config=dict(workload=res["workload"]), ip=res)))
         return
     if args.workload == "serve" and args.rates:
         res = run_serve_sweep(args)

@@ -431,29 +431,40 @@ int mhe_set_graph(mhe_ctx* ctx, int on);
  * interior-point method spends its time in Newton steps of the UFTOC form the
  * library solves).  The constraint sets are not in the paper; this outer loop
  * takes box bounds on the process noise, w_lo <= w_t <= w_hi for the measured
- * stages t = 1 .. N_b - 1 (w_0 and the states free), and runs a primal barrier
- * method: each Newton step is one mhe_factor_solve on ctx of the problem with
- * the barrier's Hessian added to Q_w and its gradient to l_w; the step keeps
- * w at least 0.5% of its distance inside each bound, and a full short step
- * divides the barrier parameter by 10, per instance.  Options: bounds [batch]
- * [nw] (device, FP64, w_lo < w_hi); mu0 (0: 1), mu_final (0: 1e-9), max_newton
- * (0: 200).  Outputs as mhe_solve: x, w the solution, lam the multipliers of
- * the last Newton step's problem, info [batch] (device or host, may be NULL)
- * per instance the record of the last Newton step it took (a step whose
- * status is not MHE_OK stops that instance; MHE_E_NO_CONVERGE for one still
- * iterating at max_newton); newton_steps (host, may be NULL) the steps taken.
- * Allocates its work buffers per call; synchronises the context's stream once
- * per Newton step and before it returns.  Errors: MHE_E_ARG, MHE_E_NOMEM,
- * MHE_E_CUDA, MHE_E_NO_CONVERGE (max_newton reached), and those of
- * mhe_factor_solve.  Contexts in MHE_FP64 suit it best: the barrier's Hessian
- * grows like 1/mu near an active bound, which the FP32 tree resolves only with
- * more refinement. */
+ * stages t = 1 .. N_b - 1 (w_0 and the states free), and runs a primal-dual
+ * interior-point method whose Newton steps are UFTOC problems on ctx: the
+ * bounds' Hessian term added to Q_w and their gradient term to l_w.
+ * method MHE_IP_PREDICTOR_CORRECTOR (0, the default): Mehrotra's
+ * predictor-corrector, one mhe_factor and two mhe_solve per iteration (the
+ * affine-scaling predictor, then the corrector with the centring target
+ * (mu_aff / mu)^3 mu and the predictor's second-order term); method
+ * MHE_IP_PATH_FOLLOWING (1): barrier path following, one mhe_factor_solve per
+ * iteration, the barrier parameter lowered to min(mu / 5, mu^1.5) after a full
+ * short step.  Steps keep every slack and multiplier at least 0.5% of its
+ * value from zero; targets stay at or above mu_final / 2; an instance stops
+ * when its target is at most mu_final and a step is full and short.
+ * Options: bounds [batch][nw] (device, FP64, w_lo < w_hi); mu0 (0: 1, the
+ * start's complementarity), mu_final (0: 1e-9), max_newton (0: 200
+ * iterations).  Outputs as mhe_solve: x, w the solution, lam the multipliers
+ * of the last Newton step's problem, info [batch] (device or host, may be
+ * NULL) per instance the record of the last step it took (a step whose status
+ * is not MHE_OK stops that instance; MHE_E_NO_CONVERGE for one still iterating
+ * at max_newton); newton_steps (host, may be NULL) the iterations taken (each
+ * one factorisation).  Allocates its work buffers per call; synchronises the
+ * context's stream once per iteration and before it returns.  Errors:
+ * MHE_E_ARG (NULL arguments, an unknown method), MHE_E_NOMEM, MHE_E_CUDA,
+ * MHE_E_NO_CONVERGE (max_newton reached), and those of the factor and solve
+ * entry points.  Contexts in MHE_FP64 suit it best: the Hessian term grows
+ * like 1/mu near an active bound, which the FP32 tree resolves only with more
+ * refinement. */
+enum { MHE_IP_PREDICTOR_CORRECTOR = 0, MHE_IP_PATH_FOLLOWING = 1 };
 typedef struct {
     const double* w_lo;   /* [batch][nw] lower bounds of w_t (device) */
     const double* w_hi;   /* [batch][nw] upper bounds of w_t (device) */
-    double mu0;           /* initial barrier parameter (0: 1) */
-    double mu_final;      /* barrier parameter at which an instance stops (0: 1e-9) */
-    int max_newton;       /* Newton steps at most (0: 200) */
+    double mu0;           /* complementarity of the starting point (0: 1) */
+    double mu_final;      /* target at which an instance stops (0: 1e-9) */
+    int max_newton;       /* iterations at most (0: 200) */
+    int method;           /* MHE_IP_PREDICTOR_CORRECTOR or MHE_IP_PATH_FOLLOWING */
 } mhe_ip_opts;
 int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rhs* rhs, const mhe_ip_opts* ip, double* x,
                  double* w, double* lam, mhe_info* info, int* newton_steps);

@@ -5,21 +5,33 @@
 // UFTOC problem of the form the library solves.  The paper does not give the
 // constraint sets; this loop takes box bounds lo <= w_t <= hi on the process
 // noise of every measured stage (t = 1 .. N-1; w_0 and the states are free) and
-// runs a primal-dual barrier method on
-//   minimise  f(z) - mu sum log(w - lo) - mu sum log(hi - w)  subject to the dynamics,
+// runs a primal-dual interior-point method on
+//   minimise  f(z)  subject to the dynamics and lo <= w <= hi,
 // with the bounds' multipliers zl, zh >= 0 carried alongside w (s_l = w - lo,
-// s_h = hi - w; the barrier's optimality asks s_l zl = s_h zh = mu).  One Newton
-// step on these conditions is the UFTOC problem with, at every stage,
-//   Q_w + Sigma  and  l_w - mu/s_l + mu/s_h - Sigma w,   Sigma = zl/s_l + zh/s_h (diagonal),
-// solved by mhe_factor_solve (the tree); its solution z' gives the primal step
-// z' - z (dynamically feasible from a feasible z) and the multipliers' steps
-//   dzl = mu/s_l - zl - (zl/s_l) dw,   dzh = mu/s_h - zh + (zh/s_h) dw.
-// The primal and the dual step lengths are each the largest up to 1 that keeps
-// s_l, s_h (resp. zl, zh) at least 0.5% of their current value from zero
-// (fraction to the boundary).  A full, short primal step ends the barrier
-// subproblem: mu becomes min(mu / 5, mu^1.5).  Every instance has its own mu and
-// stops on its own; the loop ends when all have mu at or below the target and a
-// short step, or after max_newton steps.
+// s_h = hi - w).  Newton's method on the optimality conditions with the
+// complementarity targets s_l zl = c_l, s_h zh = c_h (per bounded entry) is,
+// after eliminating the multipliers' steps, the UFTOC problem with, at every
+// stage,
+//   Q_w + Sigma  and  l_w - c_l/s_l + c_h/s_h - Sigma w,   Sigma = zl/s_l + zh/s_h (diagonal),
+// whose solution z' gives the primal step z' - z (dynamically feasible from a
+// feasible z) and the multipliers' steps
+//   dzl = c_l/s_l - zl - (zl/s_l) dw,   dzh = c_h/s_h - zh + (zh/s_h) dw.
+// Two ways of choosing the targets:
+//   * predictor-corrector (Mehrotra's; the default): factor once per iteration
+//     and solve twice.  The predictor (c = 0, the affine-scaling step) gives
+//     the step lengths to the boundary and the complementarity mu_aff those
+//     lengths would reach; with mu the current mean of s zl and s zh, the
+//     centring weight sigma = (mu_aff / mu)^3 and the corrector's targets
+//     c_l = sigma mu - dw_aff dzl_aff,  c_h = sigma mu + dw_aff dzh_aff
+//     (the second-order term of the affine step) give the step taken;
+//   * barrier path following: c_l = c_h = mu, one factor + solve per step,
+//     and mu is lowered to min(mu / 5, mu^1.5) when a step is full and short.
+// Steps are cut to keep s_l, s_h (resp. zl, zh) at least 0.5% of their
+// current value from zero (fraction to the boundary), primal and dual apart.
+// The targets never go below mu_final / 2; an instance stops when its target is
+// at most mu_final and a step is full and short.  Every instance has its own mu
+// and stops on its own; the loop ends when all have stopped, or after
+// max_newton iterations.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -54,6 +66,8 @@ struct IpArgs {
     unsigned long long* ad;              // per instance: dual step length
     unsigned long long* dmax;            // per instance: max |z' - z|, bits of a non-negative double
     unsigned long long* zmax;            // per instance: max |z|
+    double* csum;                        // per instance: sum of s_l zl + s_h zh (predictor-corrector)
+    double* caff;                        // per instance: the same after the predictor's step
     int* done;                           // per instance: converged, or stopped by a failed Newton step
     int* any;                            // some instance still iterating
     const mhe_info* info;                // the Newton step's per-instance records
@@ -107,12 +121,17 @@ __global__ void k_ip_init(IpArgs r, double mu0)
     r.done[b] = 0;
 }
 
-// the Newton model of every stage t >= 1: Q + Sigma on the w block, l - mu/s_l + mu/s_h - Sigma w
-__global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
+// the Newton model of every stage t >= 1 (rows as the header states):
+//   mode 0  Q + Sigma and l with the targets c_l = c_h = mu (barrier path following)
+//   mode 1  Q + Sigma and l with c_l = c_h = 0 (the predictor)
+//   mode 2  l only, with the corrector's targets, which it keeps in dzl, dzh for
+//           the step (the predictor's solution in xn, wn)
+__global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const int* stage_t, int mode)
 {
     const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
     if (s >= S) return;
     const int b = stage_inst[s], t = stage_t[s];
+    if (mode == 2 && r.done[b]) return;
     const int n = r.n, m = r.m, nq = n + m;
     const double* Q = r.Q + s * nq * nq;
     double* Qb = r.Qb + s * nq * nq;
@@ -121,34 +140,125 @@ __global__ void k_ip_form(IpArgs r, long long S, const int* stage_inst, const in
     const long long wofs = r.wo[b] + n + (long long)(t - 1) * m;
     const double* w = r.w + wofs;
     const double mu = r.mu[b];
-    for (int idx = threadIdx.x; idx < nq * nq; idx += blockDim.x) {
-        const int i = idx % nq, j = idx / nq;
-        double v = Q[idx];
-        if (i == j && i >= n) {
-            const int q = i - n;
-            const double sl = w[q] - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - w[q];
-            v += r.zl[wofs + q] / sl + r.zh[wofs + q] / sh;
+    if (mode != 2) {
+        for (int idx = threadIdx.x; idx < nq * nq; idx += blockDim.x) {
+            const int i = idx % nq, j = idx / nq;
+            double v = Q[idx];
+            if (i == j && i >= n) {
+                const int q = i - n;
+                const double sl = w[q] - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - w[q];
+                v += r.zl[wofs + q] / sl + r.zh[wofs + q] / sh;
+            }
+            Qb[idx] = v;
         }
-        Qb[idx] = v;
     }
     for (int i = threadIdx.x; i < nq; i += blockDim.x) {
         double v = l[i];
         if (i >= n) {
             const int q = i - n;
             const double sl = w[q] - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - w[q];
-            const double sig = r.zl[wofs + q] / sl + r.zh[wofs + q] / sh;
-            v += -mu / sl + mu / sh - sig * w[q];
+            const double zl = r.zl[wofs + q], zh = r.zh[wofs + q];
+            const double sig = zl / sl + zh / sh;
+            double cl = mode == 0 ? mu : 0.0, ch = cl;
+            if (mode == 2) {
+                const double d = r.wn[wofs + q] - w[q];
+                const double dzl = -zl - zl / sl * d, dzh = -zh + zh / sh * d;
+                cl = mu - d * dzl;
+                ch = mu + d * dzh;
+                r.dzl[wofs + q] = cl;
+                r.dzh[wofs + q] = ch;
+            }
+            v += -cl / sl + ch / sh - sig * w[q];
         }
         lb[i] = v;
     }
 }
 
+__device__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// the largest step in (0, 1] keeping v + a dv >= 0 (v > 0)
+__device__ double step_to_boundary(double v, double dv) { return dv < 0 ? fmin(1.0, -v / dv) : 1.0; }
+
+// the predictor: per instance its step lengths to the boundary and the current
+// sum of the complementarity products (one warp per stage, blockDim.x = 32)
+__global__ void k_ip_aff_len(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
+{
+    const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= S) return;
+    const int b = stage_inst[s], t = stage_t[s];
+    if (r.done[b]) return;
+    const int n = r.n, m = r.m;
+    const long long woff = r.wo[b] + n + (long long)(t - 1) * m;
+    double ap = 1.0, ad = 1.0, c = 0.0;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const double wv = r.w[woff + q], d = r.wn[woff + q] - wv;
+        const double sl = wv - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - wv;
+        const double zl = r.zl[woff + q], zh = r.zh[woff + q];
+        const double dzl = -zl - zl / sl * d, dzh = -zh + zh / sh * d;
+        ap = fmin(ap, fmin(step_to_boundary(sl, d), step_to_boundary(sh, -d)));
+        ad = fmin(ad, fmin(step_to_boundary(zl, dzl), step_to_boundary(zh, dzh)));
+        c += sl * zl + sh * zh;
+    }
+    if (ap < 1.0) atomicMin(r.ap + b, fbits(fmax(__double2float_rd(ap), 0.0f)));
+    if (ad < 1.0) atomicMin(r.ad + b, fbits(fmax(__double2float_rd(ad), 0.0f)));
+    c = warp_sum(c);
+    if (threadIdx.x == 0) atomicAdd(r.csum + b, c);
+}
+
+// the predictor: the sum of the complementarity products its step lengths reach
+__global__ void k_ip_aff_mu(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
+{
+    const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= S) return;
+    const int b = stage_inst[s], t = stage_t[s];
+    if (r.done[b]) return;
+    const int n = r.n, m = r.m;
+    const long long woff = r.wo[b] + n + (long long)(t - 1) * m;
+    const double ap = fval(r.ap[b]), ad = fval(r.ad[b]);
+    double c = 0.0;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const double wv = r.w[woff + q], d = r.wn[woff + q] - wv;
+        const double sl = wv - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - wv;
+        const double zl = r.zl[woff + q], zh = r.zh[woff + q];
+        const double dzl = -zl - zl / sl * d, dzh = -zh + zh / sh * d;
+        c += (sl + ap * d) * (zl + ad * dzl) + (sh - ap * d) * (zh + ad * dzh);
+    }
+    c = warp_sum(c);
+    if (threadIdx.x == 0) atomicAdd(r.caff + b, c);
+}
+
+// per instance: the corrector's centring target sigma mu (at least mu_final / 2)
+// into mu; the step lengths and sums cleared for the corrector
+__global__ void k_ip_sigma(IpArgs r)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= r.batch) return;
+    if (!r.done[b]) {
+        const double nb = 2.0 * (double)(r.N[b] - 1) * r.m;
+        double target = 0.0;
+        if (nb > 0 && r.csum[b] > 0.0) {
+            const double mu = r.csum[b] / nb, maff = fmax(r.caff[b], 0.0) / nb;
+            const double ratio = fmin(maff / mu, 1.0);
+            target = ratio * ratio * ratio * mu;
+        }
+        r.mu[b] = fmax(target, 0.5 * r.mu_final);
+    }
+    r.ap[b] = fbits(1.0);
+    r.ad[b] = fbits(1.0);
+    r.csum[b] = 0.0;
+    r.caff[b] = 0.0;
+}
+
 // the largest step in (0, 1] keeping v + a dv >= (1 - tau) v (v > 0)
 __device__ double max_step(double v, double dv) { return dv < 0 ? fmin(1.0, -kTau * v / dv) : 1.0; }
 
-// per stage: the multipliers' steps; per instance: the primal and dual step
+// per stage: the multipliers' steps (pc: the targets c_l, c_h from dzl, dzh, else mu); per instance: the primal and dual step
 // lengths, max |z' - z| and max |z|
-__global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
+__global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const int* stage_t, int pc)
 {
     const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
     if (s >= S) return;
@@ -162,8 +272,9 @@ __global__ void k_ip_measure(IpArgs r, long long S, const int* stage_inst, const
         const double wv = r.w[woff + q], d = r.wn[woff + q] - wv;
         const double sl = wv - r.lo[(long long)b * m + q], sh = r.hi[(long long)b * m + q] - wv;
         const double zl = r.zl[woff + q], zh = r.zh[woff + q];
-        const double dzl = mu / sl - zl - zl / sl * d;
-        const double dzh = mu / sh - zh + zh / sh * d;
+        const double cl = pc ? r.dzl[woff + q] : mu, ch = pc ? r.dzh[woff + q] : mu;
+        const double dzl = cl / sl - zl - zl / sl * d;
+        const double dzh = ch / sh - zh + zh / sh * d;
         r.dzl[woff + q] = dzl;
         r.dzh[woff + q] = dzh;
         ap = fmin(ap, fmin(max_step(sl, d), max_step(sh, -d)));
@@ -216,11 +327,14 @@ __global__ void k_ip_clear(IpArgs r)
     r.ad[b] = fbits(1.0);
     r.dmax[b] = 0ULL;
     r.zmax[b] = 0ULL;
+    r.csum[b] = 0.0;
+    r.caff[b] = 0.0;
 }
 
-// per instance: a failed Newton step stops it; a full, short primal step ends the
-// barrier subproblem (mu -> min(mu / 5, mu^1.5)), and at mu_final the instance
-__global__ void k_ip_update(IpArgs r, double step_tol)
+// per instance: a failed Newton step stops it; a full, short primal step with the
+// target at mu_final or below ends it; path following: such a step at a larger
+// mu ends the barrier subproblem (mu -> min(mu / 5, mu^1.5))
+__global__ void k_ip_update(IpArgs r, double step_tol, int pc)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= r.batch) return;
@@ -235,7 +349,7 @@ __global__ void k_ip_update(IpArgs r, double step_tol)
         if (ap >= 1.0 && d <= step_tol * (1.0 + z)) {
             const double mu = r.mu[b];
             if (mu <= r.mu_final) r.done[b] = 1;
-            else r.mu[b] = fmax(fmin(0.2 * mu, pow(mu, 1.5)), 0.5 * r.mu_final);
+            else if (!pc) r.mu[b] = fmax(fmin(0.2 * mu, pow(mu, 1.5)), 0.5 * r.mu_final);
         }
     }
     if (!r.done[b]) atomicOr(r.any, 1);
@@ -288,6 +402,11 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     const double mu0 = ip->mu0 > 0 ? ip->mu0 : 1.0;
     const double mu_final = ip->mu_final > 0 ? ip->mu_final : 1e-9;
     const int max_newton = ip->max_newton > 0 ? ip->max_newton : 200;
+    if (ip->method != MHE_IP_PREDICTOR_CORRECTOR && ip->method != MHE_IP_PATH_FOLLOWING) {
+        mhe::set_last_error("unknown interior-point method");
+        return MHE_E_ARG;
+    }
+    const int pc = ip->method == MHE_IP_PREDICTOR_CORRECTOR;
     // host-side maps: stage -> (instance, t), state -> instance, input -> instance
     // and which input entries are bounded (w_t, t >= 1)
     std::vector<int> s_inst(S), s_t(S), x_inst(X), w_inst(Wn);
@@ -323,7 +442,7 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     double* dzl = dev_alloc<double>((size_t)Wn, pool);
     double* dzh = dev_alloc<double>((size_t)Wn, pool);
     unsigned char* d_bnd = dev_alloc<unsigned char>((size_t)Wn, pool);
-    double* mu = dev_alloc<double>(batch, pool);
+    double* mu = dev_alloc<double>(3 * (size_t)batch, pool);
     unsigned long long* red = dev_alloc<unsigned long long>(4 * (size_t)batch, pool);
     int* done = dev_alloc<int>(batch, pool);
     int* any = dev_alloc<int>(1, pool);
@@ -364,7 +483,7 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     r.lo = ip->w_lo; r.hi = ip->w_hi;
     r.Qb = Qb; r.lb = lb; r.x = x; r.w = w; r.xn = xn; r.wn = wn;
     r.zl = zl; r.zh = zh; r.dzl = dzl; r.dzh = dzh;
-    r.mu = mu; r.ap = red; r.ad = red + batch; r.dmax = red + 2 * batch; r.zmax = red + 3 * batch;
+    r.mu = mu; r.csum = mu + batch; r.caff = mu + 2 * batch; r.ap = red; r.ad = red + batch; r.dmax = red + 2 * batch; r.zmax = red + 3 * batch;
     r.done = done; r.any = any; r.mu_final = mu_final;
     r.info = step_info; r.final_info = final_info;
     k_ip_init<<<batch, 32, 0, st>>>(r, mu0);
@@ -377,21 +496,38 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     mq.Q = Qb;
     mhe_rhs rq = *rhs;
     rq.l = lb;
+    const unsigned bgrid = (unsigned)((batch + 127) / 128);
     for (; steps < max_newton; ++steps) {
-        if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
-        rc = mhe_factor_solve(ctx, &mq, &rq, xn, wn, lam, step_info);
+        if (pc) {
+            // predictor: factor the model once, solve with c = 0
+            if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st, 1);
+            rc = mhe_factor(ctx, &mq);
+            if (rc == MHE_OK) rc = mhe_solve(ctx, &rq, xn, wn, lam, step_info);
+            if (rc != MHE_OK) break;
+            if (S > 0) {
+                k_ip_aff_len<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
+                k_ip_aff_mu<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
+            }
+            k_ip_sigma<<<bgrid, 128, 0, st>>>(r);
+            // corrector: the same factorisation, the right-hand side of the targets
+            if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st, 2);
+            rc = mhe_solve(ctx, &rq, xn, wn, lam, step_info);
+        } else {
+            if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st, 0);
+            rc = mhe_factor_solve(ctx, &mq, &rq, xn, wn, lam, step_info);
+        }
         if (rc != MHE_OK) break;
-        if (S > 0) k_ip_measure<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
+        if (S > 0) k_ip_measure<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st, pc);
         const long long tot = X * n > Wn ? X * n : Wn;
         k_ip_step<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, X, Wn, d_xinst, d_winst, d_bnd);
         cudaMemsetAsync(any, 0, sizeof(int), st);
-        k_ip_update<<<(batch + 127) / 128, 128, 0, st>>>(r, 1e-6);
+        k_ip_update<<<bgrid, 128, 0, st>>>(r, 1e-6, pc);
         cudaMemcpyAsync(h_any, any, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MHE_E_CUDA; break; }
         if (*h_any == 0) { ++steps; break; }
     }
     if (rc == MHE_OK && *h_any != 0) {
-        k_ip_unfinished<<<(batch + 127) / 128, 128, 0, st>>>(r);
+        k_ip_unfinished<<<bgrid, 128, 0, st>>>(r);
         mhe::set_last_error("the interior-point loop reached max_newton before every instance converged");
         rc = MHE_E_NO_CONVERGE;
     }

@@ -24,6 +24,8 @@ MHE_FP64 = 0
 MHE_FP32_IR = 1
 MHE_TF32_IR = 2
 MHE_BF16_IR = 3
+MHE_IP_PREDICTOR_CORRECTOR = 0
+MHE_IP_PATH_FOLLOWING = 1
 
 STATUS = {0: "MHE_OK", 1: "MHE_PENDING", -1: "MHE_E_ARG", -2: "MHE_E_NOMEM", -3: "MHE_E_NOT_PD",
           -4: "MHE_E_NONFINITE", -5: "MHE_E_NOT_FACTORED", -6: "MHE_E_NO_CONVERGE",
@@ -54,7 +56,7 @@ class mhe_problem(ctypes.Structure):
 
 class mhe_ip_opts(ctypes.Structure):
     _fields_ = [("w_lo", c_void_p), ("w_hi", c_void_p), ("mu0", c_double), ("mu_final", c_double),
-                ("max_newton", c_int)]
+                ("max_newton", c_int), ("method", c_int)]
 
 
 class mhe_info(ctypes.Structure):
@@ -547,16 +549,18 @@ class Solver:
         """mhe_set_graph: replay each entry point's launch sequence as a CUDA graph."""
         _check(lib().mhe_set_graph(self.ctx, int(bool(on))), "mhe_set_graph")
 
-    def ip_solve(self, A, B, Q, P0inv, l, a, x0, w_lo, w_hi, mu0=0.0, mu_final=0.0, max_newton=0, out=None):
-        """mhe_ip_solve: bounds w_lo <= w_t <= w_hi ([batch][nw] each) by a barrier interior-point loop whose
-        Newton steps are this context's factor + solve.  Returns (x, w, lam, newton steps)."""
+    def ip_solve(self, A, B, Q, P0inv, l, a, x0, w_lo, w_hi, mu0=0.0, mu_final=0.0, max_newton=0, out=None,
+                 method=0):
+        """mhe_ip_solve: bounds w_lo <= w_t <= w_hi ([batch][nw] each) by a primal-dual interior-point loop whose
+        Newton steps are this context's factor + solve (method MHE_IP_PREDICTOR_CORRECTOR or
+        MHE_IP_PATH_FOLLOWING).  Returns (x, w, lam, iterations)."""
         x, w, lam = out if out is not None else self.outputs()
         self._sizes(A=A, B=B, Q=Q, P0inv=P0inv, l=l, a=a, x0=x0, x=x, w=w, lam=lam)
         _need(w_lo, self.batch * self.nw, "w_lo")
         _need(w_hi, self.batch * self.nw, "w_hi")
         m = mhe_matrices(_ptr(A), _ptr(B), _ptr(Q), _ptr(P0inv))
         r = mhe_rhs(_ptr(l), _ptr(a), _ptr(x0))
-        o = mhe_ip_opts(_ptr(w_lo), _ptr(w_hi), float(mu0), float(mu_final), int(max_newton))
+        o = mhe_ip_opts(_ptr(w_lo), _ptr(w_hi), float(mu0), float(mu_final), int(max_newton), int(method))
         steps = c_int()
         _check(lib().mhe_ip_solve(self.ctx, ctypes.byref(m), ctypes.byref(r), ctypes.byref(o), _ptr(x), _ptr(w),
                                   _ptr(lam), ctypes.c_void_p(self.info.data_ptr()), ctypes.byref(steps)),

@@ -240,3 +240,15 @@ def test_team_width_variants_listed_and_validated(L):
     assert mhe.shape_teams(6, 3) == [8, 16, 32]
     assert mhe.shape_teams(12, 6) == [16, 32]
     assert mhe.shape_teams(5, 5) == []
+
+
+def test_ip_opts_fields_match_header():
+    """The binding's mhe_ip_opts has every field of the header's struct, in order,
+    and the header names both interior-point methods with the binding's values."""
+    txt = open(os.path.join(ROOT, "include", "mhe.h")).read()
+    end = txt.index("} mhe_ip_opts;")
+    body = txt[txt.rindex("typedef struct {", 0, end):end]
+    names = re.findall(r"^\s+(?:const\s+)?(?:int|double)\*?\s+(\w+);", body, re.M)
+    assert names == [f[0] for f in mhe.mhe_ip_opts._fields_]
+    assert f"MHE_IP_PREDICTOR_CORRECTOR = {mhe.MHE_IP_PREDICTOR_CORRECTOR}" in txt
+    assert f"MHE_IP_PATH_FOLLOWING = {mhe.MHE_IP_PATH_FOLLOWING}" in txt

@@ -1,6 +1,7 @@
 """The interior-point outer loop (mhe_ip_solve) for MHE with box-bounded
 process noise (Section II: constrained MHE, whose Newton steps are UFTOC
-problems solved by the tree).
+problems solved by the tree), in both of its methods: Mehrotra's
+predictor-corrector and barrier path following.
 
 Against the oracle's exact solution of the bounded problem (oracle/boxqp.py,
 a primal active-set method on the dense KKT system):
@@ -44,7 +45,10 @@ def _bounds(insts, frac, seed):
     return np.stack(los), np.stack(his), refs
 
 
-def _run(insts, lo, hi, prec=mhe.MHE_FP64, mu_final=0.0, **kw):
+METHODS = [mhe.MHE_IP_PREDICTOR_CORRECTOR, mhe.MHE_IP_PATH_FOLLOWING]
+
+
+def _run(insts, lo, hi, prec=mhe.MHE_FP64, mu_final=0.0, method=mhe.MHE_IP_PREDICTOR_CORRECTOR, **kw):
     import torch
     n, m = insts[0]["n"], insts[0]["m"]
     Ns = [p["N"] for p in insts]
@@ -52,20 +56,21 @@ def _run(insts, lo, hi, prec=mhe.MHE_FP64, mu_final=0.0, **kw):
     s = mhe.Solver(n, m, Ns, prec=prec, **kw)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64).reshape(-1)).cuda()  # noqa: E731
     x, w, lam, steps = s.ip_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], t(lo), t(hi),
-                                  mu_final=mu_final)
+                                  mu_final=mu_final, method=method)
     torch.cuda.synchronize()
     info = s.infos()
     s.close()
     return split(x, w, lam, Ns, n, m), steps, info
 
 
+@pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("n,m", [(4, 2), (3, 2), (6, 3)])
-def test_ip_matches_the_exact_bounded_solution(n, m):
+def test_ip_matches_the_exact_bounded_solution(n, m, method):
     Ns = [2, 5, 17, 33]
     insts = [synth.mhe_instance(2300 + 7 * i + n, n, m, m, N) for i, N in enumerate(Ns)]
     lo, hi, refs = _bounds(insts, 0.6, 5 + n)
     mu_final = 1e-9
-    got, steps, info = _run(insts, lo, hi, mu_final=mu_final)
+    got, steps, info = _run(insts, lo, hi, mu_final=mu_final, method=method)
     assert 0 < steps <= 200
     assert [int(v) for v in info["status"]] == [0] * len(Ns)
     for b, p in enumerate(insts):
@@ -134,17 +139,34 @@ def _barrier_certificate(prob, sol, lo, hi, mu_final):
     return worst
 
 
+@pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("n,m", [(12, 6), (20, 10)])
-def test_ip_optimality_conditions_at_larger_sizes(n, m):
+def test_ip_optimality_conditions_at_larger_sizes(n, m, method):
     rng = np.random.default_rng(31 + n)
     Ns = [int(v) for v in rng.integers(50, 300, size=12)]
     insts = [synth.mhe_instance(2500 + 3 * i + n, n, m, m, N) for i, N in enumerate(Ns)]
     lo, hi, refs = _bounds(insts, 0.5, 13 + n)
     mu_final = 1e-9
-    got, steps, info = _run(insts, lo, hi, mu_final=mu_final)
+    got, steps, info = _run(insts, lo, hi, mu_final=mu_final, method=method)
     assert [int(v) for v in info["status"]] == [0] * len(Ns)
     for b in (0, 5, 11):
         _barrier_certificate(refs[b][0], got[b], lo[b], hi[b], mu_final)
+
+
+def test_predictor_corrector_takes_fewer_factorisations():
+    """Mehrotra's predictor-corrector reaches the same solution as barrier path
+    following in fewer iterations (each one factorisation)."""
+    n, m = 6, 3
+    rng = np.random.default_rng(41)
+    Ns = [int(v) for v in rng.integers(20, 200, size=16)]
+    insts = [synth.mhe_instance(2550 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    lo, hi, _ = _bounds(insts, 0.5, 19)
+    pc, k_pc, i1 = _run(insts, lo, hi, mu_final=1e-9, method=mhe.MHE_IP_PREDICTOR_CORRECTOR)
+    pf, k_pf, i2 = _run(insts, lo, hi, mu_final=1e-9, method=mhe.MHE_IP_PATH_FOLLOWING)
+    assert [int(v) for v in i1["status"]] == [0] * len(Ns) and [int(v) for v in i2["status"]] == [0] * len(Ns)
+    assert 0 < k_pc < k_pf, (k_pc, k_pf)
+    for b in range(len(Ns)):
+        assert np.abs(pc[b]["w"] - pf[b]["w"]).max() <= 1e-5 * (1 + np.abs(pf[b]["w"]).max()), b
 
 
 def test_ip_on_a_tree_plan_equals_the_serial_plan():
@@ -170,4 +192,7 @@ def test_ip_argument_errors():
         s.ip_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], lo[:1], lo)
     with pytest.raises(mhe.MheError):
         s.ip_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], None, lo)
+    hi = torch.full((m,), 1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(mhe.MheError):
+        s.ip_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], lo, hi, method=7)
     s.close()
