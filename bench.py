@@ -956,6 +956,83 @@ def run_ip(args):
                 ip_solves_per_s=pc["ip_solves_per_s"], ms_per_ip_solve=pc["ms_per_ip_solve"])
 
 
+def run_link(args):
+    """The host link alone, for reading the end-to-end numbers: pinned host-to-device copies of 1 GiB spread
+    over a 24 GiB pinned buffer, alone, beside a 256 MiB device-to-host copy, and beside an 8 GiB memory-bound
+    kernel; then `--duration` seconds of back-to-back 1 GiB copies with nothing else on the GPU."""
+    import torch
+    GB = 1 << 30
+    H = torch.empty(24 * GB, dtype=torch.uint8, pin_memory=True)
+    H.fill_(1)
+    O = torch.empty(GB // 4, dtype=torch.uint8, pin_memory=True)
+    D = torch.empty(24 * GB, dtype=torch.uint8, device="cuda")
+    src = torch.empty(GB // 4, dtype=torch.uint8, device="cuda")
+    K1 = torch.ones(2 * GB, dtype=torch.float32, device="cuda")
+    K2 = torch.empty_like(K1)
+    s_in, s_out, s_k = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+
+    def summary(r):
+        r = np.array(r)
+        return dict(copies=int(r.size), min=round(float(r.min()), 1), p1=round(float(np.percentile(r, 1)), 1),
+                    p10=round(float(np.percentile(r, 10)), 1), median=round(float(np.median(r)), 1),
+                    max=round(float(r.max()), 1), below_150=round(float(np.mean(r < 150)), 4))
+
+    def spread(other=None):
+        rates = []
+        for _ in range(2):
+            for off in range(0, 24 * GB, GB):
+                if other:
+                    other()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(s_in):
+                    e0.record(s_in)
+                    D[off:off + GB].copy_(H[off:off + GB], non_blocking=True)
+                    e1.record(s_in)
+                e1.synchronize()
+                rates.append(GB / e0.elapsed_time(e1) / 1e6)
+        torch.cuda.synchronize()
+        return summary(rates)
+
+    def d2h():
+        with torch.cuda.stream(s_out):
+            O.copy_(src, non_blocking=True)
+
+    def kern():
+        with torch.cuda.stream(s_k):
+            torch.add(K1, 1.0, out=K2)
+
+    out = dict(alone=spread(), beside_d2h=spread(d2h), beside_kernel=spread(kern))
+    rates, stamps = [], []
+    t0 = time.perf_counter()
+    i = 0
+    with torch.cuda.stream(s_in):
+        while time.perf_counter() - t0 < args.duration:
+            evs = []
+            for k in range(16):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                off = ((i + k) % 16) * GB
+                e0.record(s_in)
+                D[(k % 2) * GB:(k % 2 + 1) * GB].copy_(H[off:off + GB], non_blocking=True)
+                e1.record(s_in)
+                evs.append((e0, e1))
+            evs[-1][1].synchronize()
+            now = time.perf_counter() - t0
+            for e0, e1 in evs:
+                rates.append(GB / e0.elapsed_time(e1) / 1e6)
+                stamps.append(now)
+            i += 16
+    r, st = np.array(rates), np.array(stamps)
+    series = summary(rates)
+    series["seconds"] = args.duration
+    series["min_per_second"] = [round(float(r[(st >= k) & (st < k + 1)].min()), 1)
+                                for k in range(int(args.duration)) if np.any((st >= k) & (st < k + 1))]
+    out["series"] = series
+    nodes = [d for d in os.listdir("/sys/devices/system/node") if d.startswith("node")] \
+        if os.path.isdir("/sys/devices/system/node") else []
+    out["numa_nodes"] = len(nodes)
+    return out
+
+
 def serve_setup(args, rates, T, seed=4):
     """The serving workload: a pool of estimators (nx ~ U{6,12,24}, nw = ny = nx/2, N ~ U{50,200,1000}),
     for each offered rate a seeded Poisson arrival sequence over T seconds (who and when), and every
@@ -1315,7 +1392,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks", "small", "ip"])
+                    choices=["batch", "long", "profile", "serve", "xl", "xl_profile", "alu_peaks", "small", "ip", "link"])
     ap.add_argument("--N", type=int, default=131072, help="long workload: the horizon")
     ap.add_argument("--sweep", action="store_true", help="long workload: the depth sweep over N, leaf, branching")
     ap.add_argument("--sweep-N", default="1024,16384,131072")
@@ -1387,6 +1464,12 @@ def main():
                               config=dict(workload="single MHE instance nx=4, nw=ny=2, N=64, FP64, seed 0",
                                           l2="inputs smaller than L2 (latency case; not flushed)"),
                               latency_ms=dict(p50=t["p50_ms"], p99=t["p99_ms"]), arms=res)))
+        return
+    if args.workload == "link":
+        res = run_link(args)
+        print(json.dumps(dict(metric="pinned host-to-device copy rate", value=res["series"]["median"], unit="GB/s",
+                              n_gpus=1, higher_is_better=True, data="synthetic", dtype="u8",
+                              config=dict(workload="host link: 1 GiB pinned copies"), link=res)))
         return
     if args.workload == "ip":
         res = run_ip(args)

@@ -253,9 +253,10 @@ int mhe_set_host_in_place(mhe_ctx* ctx, int on);
 /* The timeline of the last mhe_estimate_host call made with timing enabled
  * (mhe_timing_enable): per piece 8 values -- engine, first and last + 1
  * instance, the host's time of issue (ms after the call began), and the device
- * times (ms after the call's start event) at which its input copies were
- * issued, its inputs had arrived, its solve had finished, its outputs were
- * back (-1 where not available).  Writes up to cap pieces into out [cap][8],
+ * times (ms after the call's start event, recorded when the call began on a
+ * stream that carries nothing else) at which its input copies were issued, its
+ * inputs had arrived, its solve had finished, its outputs were back (-1 where
+ * not available).  Writes up to cap pieces into out [cap][8],
  * returns the number of pieces.  A profiling aid. */
 int mhe_pipe_timeline(mhe_ctx* ctx, double* out, int cap);
 

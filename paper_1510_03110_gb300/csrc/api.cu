@@ -105,7 +105,11 @@ struct HostPipe {
         cudaEvent_t ev[4];
     };
     std::vector<Piece> line;
+    // the origin of the timeline: recorded at the call on a stream of its own that
+    // carries nothing else, so that it fires at once (on the shared copy stream it
+    // would wait for the copies other pipelines queued before this call)
     cudaEvent_t t0 = nullptr;
+    cudaStream_t ost = nullptr;
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
     cudaEvent_t ev()
@@ -129,6 +133,7 @@ struct HostPipe {
             if (st[e]) cudaStreamDestroy(st[e]);
         }
         for (auto v : evpool) cudaEventDestroy(v);
+        if (ost) cudaStreamDestroy(ost);
         // the shared copy stream is not the pipeline's own: it is left to the process
         for (auto v : arrived)
             if (v) cudaEventDestroy(v);
@@ -662,8 +667,15 @@ int mhe_estimate_host_async(mhe_ctx* ctx, const mhe_problem* prob, double* x, do
     hp.line.clear();
     hp.evused = 0;
     if (tl) {
+        if (!hp.ost && cudaStreamCreateWithFlags(&hp.ost, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MHE_E_CUDA, "stream creation failed");
+        }
         hp.t0 = hp.ev();
-        cudaEventRecord(hp.t0, hp.cst);
+        cudaEventRecord(hp.t0, hp.ost);
+        // later events of the call are not stamped before the origin (the origin fires at once on
+        // its idle stream, so these waits hold back no queued work)
+        cudaStreamWaitEvent(hp.cst, hp.t0, 0);
         for (int e = 0; e < HostPipe::NE; ++e)
             if (hp.st[e]) cudaStreamWaitEvent(hp.st[e], hp.t0, 0);
     }
