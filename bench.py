@@ -945,7 +945,13 @@ def run_ip(args):
 
     pc, w_pc = arm(mhe.MHE_IP_PREDICTOR_CORRECTOR)
     pf, w_pf = arm(mhe.MHE_IP_PATH_FOLLOWING)
+    # the same with the context's factor and solve launches replayed as CUDA graphs
+    s.set_graph(True)
+    pcg, w_pcg = arm(mhe.MHE_IP_PREDICTOR_CORRECTOR)
+    s.set_graph(False)
     s.close()
+    pc["graph_replay"] = dict(ms_per_ip_solve=pcg["ms_per_ip_solve"], iterations=pcg["iterations"],
+                              all_ok=pcg["all_ok"], same_solution=bool(np.array_equal(w_pcg, w_pc)))
     pc.update(factorisations_per_iteration=1, solves_per_iteration=2)
     pf.update(factorisations_per_iteration=1, solves_per_iteration=1)
     return dict(workload="box-bounded MHE, interior-point loop: 256 instances nx=12, nw=ny=6, N ~ U[32,512], FP64",

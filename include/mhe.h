@@ -455,9 +455,10 @@ int mhe_set_graph(mhe_ctx* ctx, int on);
  * context's stream once per iteration and before it returns.  Errors:
  * MHE_E_ARG (NULL arguments, an unknown method), MHE_E_NOMEM, MHE_E_CUDA,
  * MHE_E_NO_CONVERGE (max_newton reached), and those of the factor and solve
- * entry points.  Contexts in MHE_FP64 suit it best: the Hessian term grows
- * like 1/mu near an active bound, which the FP32 tree resolves only with more
- * refinement. */
+ * entry points.  Any precision: in the mixed ones every Newton step is refined
+ * to the context's refine_tol against the FP64 residual (the Hessian term grows
+ * like 1/mu near an active bound; the last steps, being short, need one
+ * correction). */
 enum { MHE_IP_PREDICTOR_CORRECTOR = 0, MHE_IP_PATH_FOLLOWING = 1 };
 typedef struct {
     const double* w_lo;   /* [batch][nw] lower bounds of w_t (device) */

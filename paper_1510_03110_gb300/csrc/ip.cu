@@ -66,8 +66,8 @@ struct IpArgs {
     unsigned long long* ad;              // per instance: dual step length
     unsigned long long* dmax;            // per instance: max |z' - z|, bits of a non-negative double
     unsigned long long* zmax;            // per instance: max |z|
-    double* csum;                        // per instance: sum of s_l zl + s_h zh (predictor-corrector)
-    double* caff;                        // per instance: the same after the predictor's step
+    double* cpart;                       // per stage: sum of s_l zl + s_h zh (predictor-corrector)
+    double* apart;                       // per stage: the same after the predictor's step
     int* done;                           // per instance: converged, or stopped by a failed Newton step
     int* any;                            // some instance still iterating
     const mhe_info* info;                // the Newton step's per-instance records
@@ -183,8 +183,10 @@ __device__ double warp_sum(double v)
 // the largest step in (0, 1] keeping v + a dv >= 0 (v > 0)
 __device__ double step_to_boundary(double v, double dv) { return dv < 0 ? fmin(1.0, -v / dv) : 1.0; }
 
-// the predictor: per instance its step lengths to the boundary and the current
-// sum of the complementarity products (one warp per stage, blockDim.x = 32)
+// the predictor: per instance its step lengths to the boundary; per stage the
+// current sum of the complementarity products (one warp per stage, blockDim.x = 32;
+// the sums go to per-stage slots and are added in a fixed order later, so the
+// iterates do not depend on the order in which stages finish)
 __global__ void k_ip_aff_len(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
 {
     const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
@@ -206,10 +208,10 @@ __global__ void k_ip_aff_len(IpArgs r, long long S, const int* stage_inst, const
     if (ap < 1.0) atomicMin(r.ap + b, fbits(fmax(__double2float_rd(ap), 0.0f)));
     if (ad < 1.0) atomicMin(r.ad + b, fbits(fmax(__double2float_rd(ad), 0.0f)));
     c = warp_sum(c);
-    if (threadIdx.x == 0) atomicAdd(r.csum + b, c);
+    if (threadIdx.x == 0) r.cpart[s] = c;
 }
 
-// the predictor: the sum of the complementarity products its step lengths reach
+// the predictor: per stage the sum of the complementarity products its step lengths reach
 __global__ void k_ip_aff_mu(IpArgs r, long long S, const int* stage_inst, const int* stage_t)
 {
     const long long s = (long long)blockIdx.x * blockDim.y + threadIdx.y;
@@ -228,20 +230,42 @@ __global__ void k_ip_aff_mu(IpArgs r, long long S, const int* stage_inst, const 
         c += (sl + ap * d) * (zl + ad * dzl) + (sh - ap * d) * (zh + ad * dzh);
     }
     c = warp_sum(c);
-    if (threadIdx.x == 0) atomicAdd(r.caff + b, c);
+    if (threadIdx.x == 0) r.apart[s] = c;
 }
 
-// per instance: the corrector's centring target sigma mu (at least mu_final / 2)
-// into mu; the step lengths and sums cleared for the corrector
-__global__ void k_ip_sigma(IpArgs r)
+// per instance (one block of kSigmaThreads): the corrector's centring target
+// sigma mu (at least mu_final / 2) into mu, from the per-stage sums added in a
+// fixed order; the step lengths cleared for the corrector
+constexpr int kSigmaThreads = 256;
+__global__ void __launch_bounds__(kSigmaThreads) k_ip_sigma(IpArgs r)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double sc[kSigmaThreads], sa[kSigmaThreads];
+    const int b = blockIdx.x;
     if (b >= r.batch) return;
-    if (!r.done[b]) {
-        const double nb = 2.0 * (double)(r.N[b] - 1) * r.m;
+    const bool live = !r.done[b];
+    const long long s0 = r.in_off[b], ns = r.N[b] - 1;
+    double c = 0.0, a = 0.0;
+    if (live)
+        for (long long k = threadIdx.x; k < ns; k += kSigmaThreads) {
+            c += r.cpart[s0 + k];
+            a += r.apart[s0 + k];
+        }
+    sc[threadIdx.x] = c;
+    sa[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = kSigmaThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            sc[threadIdx.x] += sc[threadIdx.x + h];
+            sa[threadIdx.x] += sa[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    if (live) {
+        const double nb = 2.0 * (double)ns * r.m;
         double target = 0.0;
-        if (nb > 0 && r.csum[b] > 0.0) {
-            const double mu = r.csum[b] / nb, maff = fmax(r.caff[b], 0.0) / nb;
+        if (nb > 0 && sc[0] > 0.0) {
+            const double mu = sc[0] / nb, maff = fmax(sa[0], 0.0) / nb;
             const double ratio = fmin(maff / mu, 1.0);
             target = ratio * ratio * ratio * mu;
         }
@@ -249,8 +273,6 @@ __global__ void k_ip_sigma(IpArgs r)
     }
     r.ap[b] = fbits(1.0);
     r.ad[b] = fbits(1.0);
-    r.csum[b] = 0.0;
-    r.caff[b] = 0.0;
 }
 
 // the largest step in (0, 1] keeping v + a dv >= (1 - tau) v (v > 0)
@@ -327,8 +349,6 @@ __global__ void k_ip_clear(IpArgs r)
     r.ad[b] = fbits(1.0);
     r.dmax[b] = 0ULL;
     r.zmax[b] = 0ULL;
-    r.csum[b] = 0.0;
-    r.caff[b] = 0.0;
 }
 
 // per instance: a failed Newton step stops it; a full, short primal step with the
@@ -442,7 +462,8 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     double* dzl = dev_alloc<double>((size_t)Wn, pool);
     double* dzh = dev_alloc<double>((size_t)Wn, pool);
     unsigned char* d_bnd = dev_alloc<unsigned char>((size_t)Wn, pool);
-    double* mu = dev_alloc<double>(3 * (size_t)batch, pool);
+    double* mu = dev_alloc<double>(batch, pool);
+    double* cpart = pc ? dev_alloc<double>(2 * (size_t)S, pool) : nullptr;
     unsigned long long* red = dev_alloc<unsigned long long>(4 * (size_t)batch, pool);
     int* done = dev_alloc<int>(batch, pool);
     int* any = dev_alloc<int>(1, pool);
@@ -453,8 +474,9 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
         for (void* p : pool) cudaFree(p);
         if (h_any) cudaFreeHost(h_any);
     };
-    if (!d_sinst || !d_st || !d_xinst || !d_winst || !d_off || !d_N || !Qb || !lb || !xn || !wn || !zl || !zh || !dzl || !dzh || !d_bnd || !mu || !red ||
-        !done || !any || !step_info || !final_info || cudaHostAlloc(&h_any, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    if (!d_sinst || !d_st || !d_xinst || !d_winst || !d_off || !d_N || !Qb || !lb || !xn || !wn || !zl || !zh ||
+        !dzl || !dzh || !d_bnd || !mu || (pc && !cpart) || !red || !done || !any || !step_info || !final_info ||
+        cudaHostAlloc(&h_any, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         mhe::set_last_error("device allocation for the interior-point loop failed");
@@ -483,7 +505,7 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
     r.lo = ip->w_lo; r.hi = ip->w_hi;
     r.Qb = Qb; r.lb = lb; r.x = x; r.w = w; r.xn = xn; r.wn = wn;
     r.zl = zl; r.zh = zh; r.dzl = dzl; r.dzh = dzh;
-    r.mu = mu; r.csum = mu + batch; r.caff = mu + 2 * batch; r.ap = red; r.ad = red + batch; r.dmax = red + 2 * batch; r.zmax = red + 3 * batch;
+    r.mu = mu; r.cpart = cpart; r.apart = cpart ? cpart + S : nullptr; r.ap = red; r.ad = red + batch; r.dmax = red + 2 * batch; r.zmax = red + 3 * batch;
     r.done = done; r.any = any; r.mu_final = mu_final;
     r.info = step_info; r.final_info = final_info;
     k_ip_init<<<batch, 32, 0, st>>>(r, mu0);
@@ -508,7 +530,7 @@ extern "C" int mhe_ip_solve(mhe_ctx* ctx, const mhe_matrices* mats, const mhe_rh
                 k_ip_aff_len<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
                 k_ip_aff_mu<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st);
             }
-            k_ip_sigma<<<bgrid, 128, 0, st>>>(r);
+            k_ip_sigma<<<batch, kSigmaThreads, 0, st>>>(r);
             // corrector: the same factorisation, the right-hand side of the targets
             if (S > 0) k_ip_form<<<fgrid, fb, 0, st>>>(r, S, d_sinst, d_st, 2);
             rc = mhe_solve(ctx, &rq, xn, wn, lam, step_info);

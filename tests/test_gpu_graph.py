@@ -135,3 +135,32 @@ def test_default_stream_stays_eager():
     assert counts[0] == counts[1] == counts[2] > 0
     g.set_graph(False)
     g.close()
+
+
+def test_ip_solve_with_replayed_newton_steps_equals_eager():
+    """mhe_ip_solve on a context with graphs on: its factor and solve calls (the
+    same pointers every iteration) replay, with the same iterations and bits."""
+    import torch
+    n, m = 6, 3
+    Ns = [9, 40, 130]
+    insts = [synth.mhe_instance(3900 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    d = device_inputs(insts)
+    rng = np.random.default_rng(3)
+    lo = -0.05 - 0.02 * rng.random((len(Ns), m))
+    hi = 0.05 + 0.02 * rng.random((len(Ns), m))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64).reshape(-1)).cuda()  # noqa: E731
+    st = torch.cuda.Stream()
+    outs = []
+    for graph in (False, True):
+        s = mhe.Solver(n, m, Ns, stream=st)
+        s.set_graph(graph)
+        with torch.cuda.stream(st):
+            x, w, lam, k = s.ip_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], t(lo), t(hi))
+        st.synchronize()
+        assert list(s.infos()["status"]) == [0] * len(Ns)
+        outs.append((x.clone(), w.clone(), lam.clone(), k))
+        s.set_graph(False)
+        s.close()
+    assert outs[0][3] == outs[1][3] > 2
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert torch.equal(a, b)

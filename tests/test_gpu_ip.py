@@ -169,6 +169,27 @@ def test_predictor_corrector_takes_fewer_factorisations():
         assert np.abs(pc[b]["w"] - pf[b]["w"]).max() <= 1e-5 * (1 + np.abs(pf[b]["w"]).max()), b
 
 
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("n,m", [(4, 2), (12, 6)])
+def test_ip_in_mixed_precision_matches_fp64(n, m, method):
+    """An FP32 tree with FP64 refinement of every Newton step takes the FP64
+    context's iterations and ends on its solution, within the loop's own
+    stopping tolerance (a full step shorter than 1e-6 of the iterate)."""
+    Ns = [5, 17, 33, 120]
+    insts = [synth.mhe_instance(2800 + 7 * i + n, n, m, m, N) for i, N in enumerate(Ns)]
+    lo, hi, _ = _bounds(insts, 0.6, 23 + n)
+    f64, k64, i64 = _run(insts, lo, hi, mu_final=1e-9, method=method)
+    f32, k32, i32 = _run(insts, lo, hi, prec=mhe.MHE_FP32_IR, mu_final=1e-9, method=method,
+                         refine_tol=1e-12, max_refine=16)
+    assert [int(v) for v in i32["status"]] == [0] * len(Ns)
+    assert np.all(i32["relres"] <= 1e-12)
+    assert abs(k32 - k64) <= 2, (k32, k64)
+    for b, N in enumerate(Ns):
+        wb = f32[b]["w"][n:].reshape(N - 1, m)
+        assert np.all(wb > lo[b]) and np.all(wb < hi[b]), b
+        assert np.abs(f32[b]["w"] - f64[b]["w"]).max() <= 1e-6 * (1 + np.abs(f64[b]["w"]).max()), b
+
+
 def test_ip_on_a_tree_plan_equals_the_serial_plan():
     """The Newton steps go through whichever plan the context holds."""
     n, m = 6, 3
