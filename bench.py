@@ -871,7 +871,8 @@ def run_small(args):
 def run_ip(args):
     """MHE with box-bounded process noise (the interior-point loop, mhe_ip_solve): 256 instances of nx = 12,
     nw = ny = 6, N ~ U[32,512] (seed 6), FP64; the box around zero at half the largest |w_t[j]| of the
-    unconstrained solution (the library's own solve), shifted by 10%.  Timed: whole mhe_ip_solve calls in both
+    unconstrained solution (the library's own solve), shifted by 10%; the plan from the library's autotuner on
+    the unconstrained problem.  Timed: whole mhe_ip_solve calls in both
     methods (predictor-corrector: a factor and two solves of the tree per iteration; path following: a factor +
     solve per iteration; one host synchronisation per iteration), against the unconstrained solve of the same
     problems; checked: every input strictly inside its box, every instance converged."""
@@ -895,7 +896,11 @@ def run_ip(args):
     l = torch.empty(S * (n + m), dtype=torch.float64, device="cuda")
     mhe.mhe_assemble(n, m, m, C.view(S, -1), R, yt, wt, Q, l)
     stream = torch.cuda.Stream()
-    s = mhe.Solver(n, m, Ns, prec=mhe.MHE_FP64, stream=stream)
+    # the plan: the library's autotuner on the unconstrained problem (a Newton step has its sizes)
+    dims, _keep = mhe.make_dims(n, m, Ns, mhe.MHE_FP64)
+    tuned = mhe.mhe_autotune(dims, A, B, Q, P0, l, a, x0)
+    plan = {k: tuned[k] for k in ("leaf_len", "branching", "top_len", "down_pass", "team")}
+    s = mhe.Solver(n, m, Ns, prec=mhe.MHE_FP64, stream=stream, **plan)
     with torch.cuda.stream(stream):
         x, w, lam = s.factor_solve(A, B, Q, P0, l, a, x0)
     stream.synchronize()
@@ -955,7 +960,7 @@ def run_ip(args):
     pc.update(factorisations_per_iteration=1, solves_per_iteration=2)
     pf.update(factorisations_per_iteration=1, solves_per_iteration=1)
     return dict(workload="box-bounded MHE, interior-point loop: 256 instances nx=12, nw=ny=6, N ~ U[32,512], FP64",
-                instances=count, stages=S, bounded_inputs=int(S * m), ms_unconstrained_solve=round(ms_unc, 3),
+                instances=count, stages=S, bounded_inputs=int(S * m), plan=plan, ms_unconstrained_solve=round(ms_unc, 3),
                 predictor_corrector=pc, path_following=pf,
                 max_abs_w_difference_between_methods=float(np.abs(w_pc - w_pf).max()),
                 speedup_predictor_corrector=round(pf["ms_per_ip_solve"] / pc["ms_per_ip_solve"], 3),
