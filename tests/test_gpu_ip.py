@@ -202,6 +202,44 @@ def test_ip_on_a_tree_plan_equals_the_serial_plan():
         assert np.abs(tree[b]["w"] - ser[b]["w"]).max() <= 1e-6 * (1 + np.abs(ser[b]["w"]).max())
 
 
+@pytest.mark.parametrize("method", METHODS)
+def test_ip_with_arrival_only_instances(method):
+    """Instances with N = 1 (the arrival stage alone: nothing bounded) in a batch
+    with bounded ones: they end on the unconstrained step, the others inside their
+    boxes, every instance with status 0."""
+    n, m = 6, 3
+    Ns = [1, 12, 1, 40]
+    insts = [synth.mhe_instance(2900 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    lo, hi, refs = _bounds(insts, 0.5, 29)
+    got, steps, info = _run(insts, lo, hi, mu_final=1e-9, method=method)
+    assert [int(v) for v in info["status"]] == [0] * len(Ns)
+    for b, N in enumerate(Ns):
+        if N == 1:
+            assert rel_err(got[b], refs[b][1]) <= 1e-10, b
+        else:
+            wb = got[b]["w"][n:].reshape(N - 1, m)
+            assert np.all(wb > lo[b]) and np.all(wb < hi[b]), b
+
+
+def test_ip_iteration_limit_reports_no_convergence():
+    """max_newton reached before every instance has converged: MHE_E_NO_CONVERGE
+    for the call, and in info for each instance still iterating."""
+    import torch
+    n, m = 6, 3
+    Ns = [20, 60]
+    insts = [synth.mhe_instance(2950 + i, n, m, m, N) for i, N in enumerate(Ns)]
+    lo, hi, _ = _bounds(insts, 0.5, 31)
+    d = device_inputs(insts)
+    s = mhe.Solver(n, m, Ns)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64).reshape(-1)).cuda()  # noqa: E731
+    with pytest.raises(mhe.MheError) as e:
+        s.ip_solve(d["A"], d["B"], d["Q"], d["P0inv"], d["l"], d["a"], d["x0"], t(lo), t(hi), max_newton=2)
+    assert e.value.code == -6
+    torch.cuda.synchronize()
+    assert [int(v) for v in s.infos()["status"]] == [-6, -6]
+    s.close()
+
+
 def test_ip_argument_errors():
     import torch
     n, m = 4, 2
