@@ -681,6 +681,35 @@ MHE_DEV int stage_instance(const long long* gs0, int batch, long long gstage)
     return lo;
 }
 
+// The stage a team evaluates next, asked into L2 while it evaluates the current
+// one (the double-float MHE form: the stage's matrix pairs, l, a and the iterate's
+// vectors).  Every address lies in the arrays' extents for the stage; the
+// arrival stage is left out.
+template <int NX, int NW, int NY>
+MHE_DEV void resid_prefetch_df(const ResidArgs<float>& r, long long gstage)
+{
+    constexpr int NR = NW + NY, NQ = NX + NW;
+    const int b = stage_instance(r.gs0, r.batch, gstage);
+    if (r.active && !r.active[b]) return;
+    const int t = (int)(gstage - r.gs0[b]);
+    if (t == 0) return;
+    const long long s = r.in_off[b] + t - 1;
+    prefetch_l2(r.Ahi + s * NX * NX, (int)sizeof(float) * NX * NX);
+    prefetch_l2(r.Alo + s * NX * NX, (int)sizeof(float) * NX * NX);
+    prefetch_l2(r.Bhi + s * NX * NW, (int)sizeof(float) * NX * NW);
+    prefetch_l2(r.Blo + s * NX * NW, (int)sizeof(float) * NX * NW);
+    prefetch_l2(r.Chi + s * NY * NX, (int)sizeof(float) * NY * NX);
+    prefetch_l2(r.Clo + s * NY * NX, (int)sizeof(float) * NY * NX);
+    prefetch_l2(r.Rhi + s * NR * NR, (int)sizeof(float) * NR * NR);
+    prefetch_l2(r.Rlo + s * NR * NR, (int)sizeof(float) * NR * NR);
+    if (r.l) prefetch_l2(r.l + s * NQ, (int)sizeof(double) * NQ);
+    if (r.a) prefetch_l2(r.a + s * NX, (int)sizeof(double) * NX);
+    const long long gx = r.gs0[b] + b;
+    prefetch_l2(r.x + (gx + t) * NX, (int)sizeof(double) * 2 * NX);     // x_t, x_{t+1}
+    prefetch_l2(r.lam + (gx + t) * NX, (int)sizeof(double) * 2 * NX);   // lambda_t, lambda_{t+1}
+    prefetch_l2(r.w + r.w_off[b] + NX + (long long)(t - 1) * NW, (int)sizeof(double) * NW);
+}
+
 template <int NX, int NW, typename TR, int NY = 0>
 MHE_DEV void resid_stage(const ResidArgs<TR>& r, long long gstage, unsigned long long* sm)
 {
