@@ -59,9 +59,9 @@ struct IpArgs {
     double *Qb, *lb;                     // the Newton model's Q and l (caller stage layout)
     double *x, *w;                       // the iterate
     double *zl, *zh;                     // the bounds' multipliers (the layout of w; bounded entries only)
-    double *dzl, *dzh;                   // their steps
+    double *dzl, *dzh;                   // their steps (predictor-corrector: first the corrector's targets)
     const double *xn, *wn;               // the model's solution
-    double* mu;                          // per instance
+    double* mu;                          // per instance: the barrier parameter, or the centring target
     unsigned long long* ap;              // per instance: primal step length, float bits of a value in (0, 1]
     unsigned long long* ad;              // per instance: dual step length
     unsigned long long* dmax;            // per instance: max |z' - z|, bits of a non-negative double
