@@ -203,3 +203,42 @@ def test_server_marshalling(fake):
     assert r["status"] == 0 and r["iters"] == 2 and r["latency"] == 0.004 and r["x"].shape == (4,)
     srv.set_plan(8, 4, 2)
     srv.close()
+
+
+def _cpu_solver(nx, nw, N):
+    """A Solver with its context and info buffer stood in on the host (the fake
+    library never touches them), for marshalling checks."""
+    s = object.__new__(mhe.Solver)
+    s.nx, s.nw, s.N = nx, nw, np.asarray(N, dtype=np.int64)
+    s.batch = int(s.N.size)
+    s.X, s.S = int(np.sum(s.N + 1)), int(np.sum(s.N - 1))
+    s.W = int(np.sum(nx + (s.N - 1) * nw))
+    s.ctx, s.info = 1, torch.zeros(s.batch * mhe.INFO_DTYPE.itemsize, dtype=torch.uint8)
+    return s
+
+
+def test_ip_solve_marshalling(fake):
+    nx, nw = 4, 2
+    s = _cpu_solver(nx, nw, [3, 5])
+    nq = nx + nw
+    z = lambda k: torch.zeros(k, dtype=torch.float64)  # noqa: E731
+    arr = dict(A=z(s.S * nx * nx), B=z(s.S * nx * nw), Q=z(s.S * nq * nq), P0inv=z(s.batch * nx * nx),
+               l=z(s.S * nq), a=z(s.S * nx), x0=z(s.batch * nx))
+    out = (z(s.X * nx), z(s.W), z(s.X * nx))
+    lo, hi = z(s.batch * nw), torch.ones(s.batch * nw, dtype=torch.float64)
+    args = [arr[k] for k in ("A", "B", "Q", "P0inv", "l", "a", "x0")]
+    s.ip_solve(*args, lo, hi, mu0=0.5, mu_final=1e-8, max_newton=30, out=out, method=mhe.MHE_IP_PATH_FOLLOWING)
+    call = fake.calls["mhe_ip_solve"]
+    o = call[3]._obj
+    assert (o.w_lo, o.w_hi) == (lo.data_ptr(), hi.data_ptr())
+    assert (o.mu0, o.mu_final, o.max_newton, o.method) == (0.5, 1e-8, 30, mhe.MHE_IP_PATH_FOLLOWING)
+    assert call[4].value == out[0].data_ptr() and call[7].value == s.info.data_ptr()
+    s.ip_solve(*args, lo, hi, out=out)
+    assert fake.calls["mhe_ip_solve"][3]._obj.method == mhe.MHE_IP_PREDICTOR_CORRECTOR
+    # short bounds or outputs are refused before the library is called
+    del fake.calls["mhe_ip_solve"]
+    with pytest.raises(mhe.SizeError):
+        s.ip_solve(*args, lo[:-1], hi, out=out)
+    with pytest.raises(mhe.SizeError):
+        s.ip_solve(*args, lo, hi, out=(out[0], out[1][:-1], out[2]))
+    assert "mhe_ip_solve" not in fake.calls
